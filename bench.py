@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Throughput of the coupled EM-thermal-mechanical hot path on the full-scale
+1024 x 1024 x 128 voxel package (134 M cells, FP32 fields, FP64 reductions).
+
+One step = one pass of every stage of the path over the package:
+  EM burst slice (N_EM leapfrog steps, Joule accumulation fused)
+  -> burst-averaged Joule source -> N_TH forward-Euler thermal steps
+  -> thermoelastic solve slice (thermal load, Jacobi diagonal, N_CG PCG
+     iterations, von Mises and |u|).
+The slice sizes keep the full job's proportions (2 ns burst = 314,701 EM
+steps : 10^4 thermal steps : one solve of ~10^4 CG iterations, scaled by
+about 1/3300). value = grid-point updates per second over the whole step
+(EM cell-steps + thermal node-steps + CG node-iterations) / step time.
+
+Run: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank solves its own package (replicas, no collective on
+the data path); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_EM, N_TH, N_CG = 96, 3, 3
+METRIC = "Gcell-updates/s & % HBM roofline (EM+thermal); stress-CG s/solve; designs/hr, p50/p99"
+UNIT = "Gcell-updates/s"
+WORKLOAD = "full-scale layered package 1024x1024x128 (134M cells), FP32"
+
+
+def parse():
+    a = argparse.ArgumentParser()
+    a.add_argument("--gpus", type=int, default=1)
+    a.add_argument("--steps", type=int, default=5)
+    a.add_argument("--warmup", type=int, default=3)
+    a.add_argument("--impl", default="cosim", choices=["cosim", "reference"])
+    a.add_argument("--nx", type=int, default=1024)
+    a.add_argument("--ny", type=int, default=1024)
+    a.add_argument("--no-e2e", action="store_true")
+    a.add_argument("--no-cpu", action="store_true")
+    return a.parse_args()
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def em_alg_bytes(ctx, p):
+    """algorithmic HBM bytes of one EM step (FP32): E and H read + written once
+    per unknown (6 x 2 x 4 B per cell), the voxel byte, the FP64 Joule
+    accumulator read + written per node, and the CPML auxiliaries."""
+    cells, nodes = p.n_cells, p.n_nodes
+    L = p.cpml_cells
+    psi = 0
+    n = (p.nx, p.ny, p.nz)
+    for a in range(3):
+        sides = (p.em_bc[2 * a] == 2) + (p.em_bc[2 * a + 1] == 2)
+        if sides:
+            area = nodes // (n[a] + 1)
+            psi += sides * (L + 1) * area * 4 * 2 * 4  # 4 aux arrays (2 E + 2 H), read + write, FP32
+    return 48 * cells + cells + 16 * nodes + psi
+
+
+def traffic_from_profile(kernel_src):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(path))
+        h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        if t.get("em_step_kernel", {}).get("source_sha256_16") == h:
+            return t["em_step_kernel"]["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def gpu_arm(args, rank, world):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2603_07038_b300 import build as B
+    from paper_2603_07038_b300 import cosim as api
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    api.load()
+    p = W.layered_package(args.nx, args.ny, seed=2 + rank)
+    stream = torch.cuda.current_stream()
+    total_em = (args.warmup + args.steps + 4) * N_EM
+    ctx = api.Context(p, precision=api.COSIM_FP32, stream=stream, use_torch_allocator=True)
+    tables = p.source_tables(ctx.dt, total_em)
+    ctx.set_sources(tables)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(rec=None):
+        ctx.joule(api.COSIM_JOULE_RESET, want_total=False)
+        if rec is not None:
+            rec[0].record(stream)
+        ctx.em_steps(N_EM, accumulate_joule=True)
+        if rec is not None:
+            rec[1].record(stream)
+        ctx.joule(api.COSIM_JOULE_FINALIZE_AVG_POWER, want_total=False)
+        ctx.thermal_steps(N_TH)
+        if rec is not None:
+            rec[2].record(stream)
+        ctx.stress_solve(bc=api.COSIM_MECH_CLAMPED_BOTTOM, T_ref=300.0, rtol=1e-30, maxit=N_CG,
+                         check_every=N_CG, allow_not_converged=True)
+        if rec is not None:
+            rec[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", "") or "")
+    clocks = ClockSampler(("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else (uuid or dev))
+    clocks.start()
+    time.sleep(0.3)
+    l0 = ctx.query(api.COSIM_Q_LAUNCHES)
+    t0, t1 = ev(), ev()
+    recs = [[ev() for _ in range(4)] for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0.record(stream)
+    for s in range(args.steps):
+        step(recs[s])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    launches = int(ctx.query(api.COSIM_Q_LAUNCHES) - l0)
+    ms_total = t0.elapsed_time(t1)
+    em_ms = sum(r[0].elapsed_time(r[1]) for r in recs)
+    th_ms = sum(r[1].elapsed_time(r[2]) for r in recs)
+    cg_ms = sum(r[2].elapsed_time(r[3]) for r in recs)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    updates_step = p.n_cells * N_EM + p.n_nodes * N_TH + p.n_nodes * N_CG
+    value = world * updates_step / (ms_step * 1e-3) / 1e9
+    em_launch_ms = em_ms / (args.steps * N_EM)
+    alg = em_alg_bytes(ctx, p)
+    peaks = load_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6400.0
+    achieved = alg / (em_launch_ms * 1e-3) / 1e9
+    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2603_07038_b300", "csrc", "em.cuh"))
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded layered package generator)",
+        "config": {"workload": WORKLOAD, "nx": args.nx, "ny": args.ny, "nz": 128, "cells": p.n_cells,
+                   "nodes": p.n_nodes, "step": f"{N_EM} EM steps + Joule + {N_TH} thermal steps + "
+                                           f"stress slice ({N_CG} PCG iterations)",
+                   "signal_lines": len(p.sources), "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (state ~%.0f GB resident)" % (ctx.query(api.COSIM_Q_BYTES_RESIDENT) / 1e9)},
+        "phases": {"em_gcell_steps_s": round(p.n_cells * N_EM * args.steps / (em_ms * 1e-3) / 1e9, 3),
+                   "em_ms_per_step": round(em_launch_ms, 4),
+                   "thermal_gnode_steps_s": round(p.n_nodes * N_TH * args.steps / (th_ms * 1e-3) / 1e9, 3),
+                   "stress_slice_ms": round(cg_ms / args.steps, 3)},
+        "roofline": {"kernel": "em_step_kernel", "bound": "hbm", "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "alg_bytes_per_launch": alg,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.4 TB/s"},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e_arm(args, p, stream, world)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(args, p)
+    ctx.close()
+    return out
+
+
+def e2e_arm(args, p, stream, world, nsteps=2):
+    """Same step through the public C ABI with host buffers: every step
+    uploads the package from pinned host memory (cosim_create copies voxels,
+    spacings, materials; cosim_set_sources the ports), runs the pass and reads
+    the temperature and von Mises fields back into pinned host memory."""
+    import numpy as np
+    import torch
+
+    from paper_2603_07038_b300 import cosim as api
+    mat_pinned = torch.empty(p.mat.shape, dtype=torch.uint8).pin_memory()
+    mat_pinned.numpy()[...] = p.mat
+    p.mat = mat_pinned.numpy()
+    T_host = torch.empty(p.n_nodes, dtype=torch.float32).pin_memory().numpy()
+    VM_host = torch.empty(p.n_cells, dtype=torch.float32).pin_memory().numpy()
+    times = []
+    h2d = d2h = 0
+    for s in range(nsteps + 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ctx = api.Context(p, precision=api.COSIM_FP32, stream=stream, use_torch_allocator=True)
+        tables = p.source_tables(ctx.dt, N_EM)
+        ctx.set_sources(tables)
+        ctx.em_steps(N_EM, True)
+        ctx.joule(api.COSIM_JOULE_FINALIZE_AVG_POWER, want_total=False)
+        ctx.thermal_steps(N_TH)
+        ctx.stress_solve(bc=api.COSIM_MECH_CLAMPED_BOTTOM, T_ref=300.0, rtol=1e-30, maxit=N_CG,
+                         check_every=N_CG, allow_not_converged=True)
+        api.cosim_read_fields(ctx.h, api.COSIM_F_T, T_host)
+        api.cosim_read_fields(ctx.h, api.COSIM_F_VM, VM_host)
+        ctx.close()
+        torch.cuda.synchronize()
+        if s > 0:  # the first pass warms the caching allocator
+            times.append(time.perf_counter() - t)
+        h2d = (p.mat.nbytes + 8 * (p.nx + p.ny + p.nz) + 80 * len(p.materials)
+               + sum(e.nbytes + a.nbytes for _, e, a in tables))
+        d2h = T_host.nbytes + VM_host.nbytes
+    sec = statistics.median(times)
+    upd = p.n_cells * N_EM + p.n_nodes * N_TH + p.n_nodes * N_CG
+    return {"value": round(upd / sec / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "seconds_per_step": round(sec, 3),
+            "note": "cosim_create + set_sources + pass + cosim_read_fields(T, VM) to pinned host, per step"}
+
+
+# ---------------------------------------------------------------- oracle (CPU) arm
+
+def oracle_sample(p_full, n_em=2, n_th=2, n_mv=1, win=(96, 96)):
+    """Time the FP64 oracle on a corner window of the package (all 128 layers,
+    CPML faces included) and scale per grid point to the full step."""
+    import numpy as np
+
+    import oracle
+    import workloads as W
+    from workloads import constraints as BC
+    wp = W.crop(p_full, (0, 0, 0), (win[0], win[1], p_full.nz))
+    o = oracle.OracleSim(wp)
+    rng = np.random.default_rng(0)
+    for a in range(3):
+        o.E[a][:] = rng.standard_normal(o.g.n_nodes) * 1e-3
+    t = time.perf_counter()
+    o.em_steps(n_em)
+    t_em = (time.perf_counter() - t) / (n_em * wp.n_cells)
+    o.P = rng.random(o.g.n_nodes) * 1e-9
+    t = time.perf_counter()
+    o.thermal_steps(n_th)
+    t_th = (time.perf_counter() - t) / (n_th * wp.n_nodes)
+    fixed = BC.clamped_bottom(wp)
+    u = rng.standard_normal(3 * wp.n_nodes) * 1e-9
+    t = time.perf_counter()
+    for _ in range(n_mv):
+        o.matvec(fixed, u)
+    t_mv = (time.perf_counter() - t) / (n_mv * wp.n_nodes)
+    sec_full = N_EM * p_full.n_cells * t_em + N_TH * p_full.n_nodes * t_th + N_CG * p_full.n_nodes * t_mv
+    upd = p_full.n_cells * N_EM + p_full.n_nodes * N_TH + p_full.n_nodes * N_CG
+    sample = (f"FP64 oracle on the {win[0]}x{win[1]}x{p_full.nz} corner window: {n_em} EM steps, {n_th} thermal "
+              f"steps, {n_mv} HEX8 matvec (a CG iteration counted as its matvec), scaled per grid point to the "
+              f"full step")
+    return upd / sec_full / 1e9, sample
+
+
+def cpu_baseline(args, p):
+    v, sample = oracle_sample(p)
+    return {"value": round(v, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+
+def reference_arm(args):
+    import workloads as W
+    import oracle
+    oracle.build()
+    p = W.layered_package(args.nx, args.ny, seed=2)
+    for _ in range(args.warmup):
+        oracle_sample(p, 1, 1, 1, win=(64, 64))
+    vals = []
+    samples = ""
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, samples = oracle_sample(p, 1, 1, 1, win=(64, 64))
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    v = statistics.median(vals)
+    upd = p.n_cells * N_EM + p.n_nodes * N_TH + p.n_nodes * N_CG
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(upd / (v * 1e9) * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded layered package generator)",
+            "config": {"workload": WORKLOAD, "nx": args.nx, "ny": args.ny, "nz": 128,
+                       "step": f"{N_EM} EM steps + {N_TH} thermal steps + {N_CG} CG iterations (extrapolated)"},
+            "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": samples,
+                             "wall_s": round(wall, 1)},
+            "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(reference_arm(args)))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = gpu_arm(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

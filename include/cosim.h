@@ -1,0 +1,239 @@
+/*
+ * cosim.h -- C ABI of the B300 transient EM-thermal-mechanical package solver.
+ *
+ * One context owns the device state of one voxelised package on one GPU:
+ * material IDs, per-axis cell sizes, the E/H fields (with CPML auxiliaries),
+ * the Joule-energy accumulator, temperature, and the thermoelastic solution.
+ * Every call enqueues its work on the context's CUDA stream; only
+ * cosim_read_fields, cosim_stress_solve and the reductions that return a
+ * number to the host synchronise that stream.
+ *
+ * Units are SI. Grids: cells (i,j,k) with 0 <= i < nx ...; nodes 0 <= i <= nx.
+ * Node-sized host/device buffers exchanged through this ABI are dense arrays of
+ * (nx+1)(ny+1)(nz+1) values, x fastest; cell-sized ones have nx*ny*nz values.
+ * An E unknown of axis a is named by the lower node of its edge; an H unknown
+ * of axis a by the lowest corner node of its face (see the field list below).
+ *
+ * Errors: every function returns a cosim_status; nothing throws across the
+ * ABI. COSIM_ERR_INVALID leaves the context unchanged. COSIM_ERR_CUDA is
+ * sticky: the context must be destroyed. cosim_last_error() describes the
+ * most recent failure of a context in words.
+ */
+#ifndef COSIM_H
+#define COSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cosim_ctx cosim_ctx;
+
+typedef enum {
+  COSIM_OK = 0,
+  COSIM_ERR_INVALID = 1,        /* bad argument or descriptor */
+  COSIM_ERR_OOM = 2,            /* device allocation failed */
+  COSIM_ERR_CUDA = 3,           /* CUDA runtime error (sticky) */
+  COSIM_ERR_NOT_CONVERGED = 4,  /* stress solve hit maxit (result still readable) */
+  COSIM_ERR_TIMEOUT = 5,        /* bounded device wait expired */
+  COSIM_ERR_NONFINITE = 6       /* NaN/Inf detected in a reduction */
+} cosim_status;
+
+/* arithmetic of the field sweeps */
+enum { COSIM_FP64 = 0, COSIM_FP32 = 1 };
+
+/* EM wall conditions, per face (x-, x+, y-, y+, z-, z+) */
+enum { COSIM_BC_PEC = 0, COSIM_BC_PMC = 1, COSIM_BC_CPML = 2 };
+
+/* Voxel material (Sec. II and III-A). sigma0 is the conductivity at T0 and
+ * tcr the temperature coefficient of resistance of Eq. 6; k the thermal
+ * conductivity, rho_cp the volumetric heat capacity (Eq. 4); E, nu, alpha_L
+ * the isotropic elastic constants and linear CTE (Eqs. 7-8). */
+typedef struct {
+  double eps_r, mu_r, sigma0, tcr, T0, k, rho_cp, E, nu, alpha_L;
+} cosim_material;
+
+/* Problem statement (Sec. II, III). All pointers are host pointers; the
+ * library copies what it needs during cosim_create (caller keeps ownership).
+ *   dx[nx], dy[ny], dz[nz]: cell sizes [m] (non-uniform grid, Sec. II-A);
+ *   mat[nz*ny*nx]: voxel material index < nmat, x fastest;
+ *   em_bc[6]: COSIM_BC_* per face. CPML faces are terminated by PEC; an axis
+ *     with CPML needs at least 2*cpml_cells+2 cells;
+ *   cpml_cells, cpml_order (polynomial grading m), cpml_eps_r (background
+ *     relative permittivity used for sigma_max);
+ *   h_conv[6]: convective film coefficient per face [W/(m^2 K)] (0 = adiabatic,
+ *     the paper's thermal condition); T_amb [K]; T_init: initial temperature. */
+typedef struct {
+  int32_t nx, ny, nz;
+  const double *dx, *dy, *dz;
+  const uint8_t *mat;
+  int32_t nmat;
+  const cosim_material *mats;
+  int32_t em_bc[6];
+  int32_t cpml_cells;
+  double cpml_order;
+  double cpml_eps_r;
+  double h_conv[6];
+  double T_amb;
+  double T_init;
+} cosim_grid_desc;
+
+/* Soft current-density source (the J of Eq. 1-2) on n_edges edges of one
+ * axis. edge_ijk[3*e .. 3*e+2] = lower node (i, j, k) of edge e. amp[n] is J
+ * [A/m^2] applied during the E update of step n (time (n + 1/2) dt_em); zero
+ * for n >= nsteps. Host pointers, copied. */
+typedef struct {
+  int32_t axis;
+  int32_t n_edges;
+  const int32_t *edge_ijk;
+  int64_t nsteps;
+  const double *amp;
+} cosim_source;
+
+/* Optional device allocator (e.g. a framework's caching allocator).
+ * alloc returns a device pointer aligned to 256 bytes, or NULL. */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *user);
+  void (*free)(void *ptr, void *user);
+  void *user;
+} cosim_allocator;
+
+typedef struct {
+  int32_t precision;        /* COSIM_FP64 or COSIM_FP32 (fields, stencils, CG vectors) */
+  double cfl;               /* fraction of the Courant limit (<= 0: 0.99) ... */
+  double dt_em;             /* ... unless dt_em > 0 gives the EM step [s] explicitly */
+  double thermal_safety;    /* fraction of the thermal stability limit (<= 0: 0.9) */
+  void *stream;             /* cudaStream_t to enqueue on; NULL = default stream */
+  const cosim_allocator *allocator; /* NULL = cudaMalloc / cudaFree */
+} cosim_options;
+
+/* Create a context: validates the descriptor, copies geometry and materials
+ * to the device, derives the EM step (Courant limit of the finest cells at
+ * the fastest wave speed, times cfl) and the thermal stability limit,
+ * allocates and zeroes all fields (T = T_init). Sec. II-A, II-B. */
+cosim_status cosim_create(const cosim_grid_desc *desc, const cosim_options *opts, cosim_ctx **out);
+
+/* Replace the context's current sources (n may be 0). Sec. III-B excitation. */
+cosim_status cosim_set_sources(cosim_ctx *ctx, int32_t n, const cosim_source *src);
+
+/* Flag for cosim_em_steps: accumulate the Joule energy of each step. */
+#define COSIM_ACCUM_JOULE 1u
+
+/* Advance the Maxwell system nsteps leapfrog steps (Eqs. 1-3 in E/H form):
+ * H^{n+1/2} = H^{n-1/2} - dt/mu curl E^n;
+ * E^{n+1} = ca E^n + cb (curl H^{n+1/2} - J^{n+1/2}),
+ * ca = (eps - sigma dt/2)/(eps + sigma dt/2), cb = dt/(eps + sigma dt/2),
+ * eps and sigma area-weighted over the voxels of each edge, mu a series mean
+ * over each face; CPML auxiliaries in the CPML layers; tangential E held at
+ * zero on PEC walls. With COSIM_ACCUM_JOULE each step adds, for every edge,
+ * sigma_e V_e ((E^n + E^{n+1})/2)^2 dt / 2 to the Joule energy of both end
+ * nodes (P_total = D_sigma e^2, Sec. II-A). One kernel launch per step. */
+cosim_status cosim_em_steps(cosim_ctx *ctx, int64_t nsteps, uint32_t flags);
+
+/* Joule accumulator operations:
+ *   COSIM_JOULE_RESET: zero the per-node energy and the accumulated step count;
+ *   COSIM_JOULE_FINALIZE_AVG_POWER: thermal source P_i = Q_i / (n_steps dt_em)
+ *     [W per node] (burst-averaged power driving Eq. 5);
+ *   COSIM_JOULE_FINALIZE_ENERGY: T_i += Q_i / C_i (the burst's energy
+ *     deposited adiabatically, C_i the node heat capacity).
+ * total_joule_energy_out (nullable): sum_i Q_i [J], deterministic FP64 sum
+ * (synchronises the stream). */
+enum { COSIM_JOULE_RESET = 0, COSIM_JOULE_FINALIZE_AVG_POWER = 1, COSIM_JOULE_FINALIZE_ENERGY = 2 };
+cosim_status cosim_joule_accumulate(cosim_ctx *ctx, int32_t op, double *total_joule_energy_out);
+
+/* Forward-Euler heat diffusion steps (Eq. 5) driven by the current thermal
+ * source: T_i += dt/C_i (sum_j G_ij (T_j - T_i) + h_f A_i (T_amb - T_i) + P_i),
+ * G_ij = k_e A*_e / l_e over the 7-point nodal stencil (M_kk = V0a^T D_k V0,
+ * Eq. 4). dt <= 0 uses thermal_safety x the stability limit. */
+cosim_status cosim_thermal_steps(cosim_ctx *ctx, int64_t nsteps, double dt);
+
+/* Mechanical supports (Sec. III-B) */
+enum {
+  COSIM_MECH_CLAMPED_BOTTOM = 0,   /* all z = 0 nodes fixed in x, y, z */
+  COSIM_MECH_KINEMATIC_MOUNT = 1,  /* the paper's 3-node, 6-DOF minimum constraint */
+  COSIM_MECH_MASK = 2              /* node_mask[(nx+1)(ny+1)(nz+1)]: bit c = component c fixed */
+};
+
+typedef struct {
+  int32_t bc;                /* COSIM_MECH_* */
+  const uint8_t *node_mask;  /* host pointer, for COSIM_MECH_MASK only */
+  double T_ref;              /* stress-free temperature [K] */
+  double rtol;               /* stop at ||r|| <= rtol ||f|| (<= 0: 1e-9) */
+  int64_t maxit;             /* iteration cap (<= 0: 200000) */
+  int32_t check_every;       /* residual checked on the host every n iterations (<= 0: 32) */
+} cosim_stress_opts;
+
+typedef struct {
+  int64_t iters;
+  double relres;             /* ||f - K u|| / ||f|| as recursively updated by CG */
+  double seconds;            /* wall time of the solve */
+} cosim_stress_report;
+
+/* Thermoelastic static solve (Eqs. 7-9): HEX8 elements with exact (2x2x2
+ * Gauss) integration, K u = f with f the thermal load of dT = T - T_ref,
+ * Jacobi-preconditioned CG (FP64 dot products), then von Mises stress at
+ * every element centroid and |u| at every node. Synchronises the stream.
+ * Returns COSIM_ERR_NOT_CONVERGED if maxit is reached (u is still stored). */
+cosim_status cosim_stress_solve(cosim_ctx *ctx, const cosim_stress_opts *opts, cosim_stress_report *rep);
+
+/* y = K u for the supports in opts (constrained rows/columns eliminated,
+ * y_c = u_c on constrained DOFs). u, y: 3 node-sized arrays in SoA order
+ * (ux | uy | uz), in the context's precision (double for COSIM_FP64, float
+ * for COSIM_FP32), host or device memory per on_device. */
+cosim_status cosim_stress_apply(cosim_ctx *ctx, const cosim_stress_opts *opts, const void *u, void *y,
+                                int32_t on_device);
+
+/* Fields exchanged by cosim_read_fields / cosim_write_fields */
+enum {
+  COSIM_F_EX = 0, COSIM_F_EY = 1, COSIM_F_EZ = 2,   /* E on edges, node-sized */
+  COSIM_F_HX = 3, COSIM_F_HY = 4, COSIM_F_HZ = 5,   /* H on faces, node-sized */
+  COSIM_F_T = 6,      /* temperature [K], node-sized */
+  COSIM_F_Q = 7,      /* accumulated Joule energy [J], node-sized */
+  COSIM_F_P = 8,      /* thermal source [W per node], node-sized */
+  COSIM_F_UX = 9, COSIM_F_UY = 10, COSIM_F_UZ = 11, /* displacement [m], node-sized */
+  COSIM_F_VM = 12,    /* von Mises stress [Pa], cell-sized */
+  COSIM_F_UMAG = 13,  /* |u| [m], node-sized */
+  COSIM_F_FX = 14, COSIM_F_FY = 15, COSIM_F_FZ = 16, /* thermal load [N], node-sized */
+  COSIM_NUM_FIELDS = 17
+};
+
+/* Copy one field into dst (dense layout above), converting to dtype
+ * (COSIM_FP64 -> double, COSIM_FP32 -> float). bytes must equal the field's
+ * element count times the dtype size. dst is device memory if dst_is_device,
+ * else host memory. Synchronises the stream. Caller owns dst. */
+cosim_status cosim_read_fields(cosim_ctx *ctx, int32_t field, int32_t dtype, void *dst, size_t bytes,
+                               int32_t dst_is_device);
+
+/* Overwrite one field from src (same layout and size rules). Entries that are
+ * not unknowns (edges beyond the last cell, tangential E on PEC walls) are
+ * stored as zero. Writable: E, H, T, Q, P, UX..UZ. */
+cosim_status cosim_write_fields(cosim_ctx *ctx, int32_t field, int32_t dtype, const void *src, size_t bytes,
+                                int32_t src_is_device);
+
+enum {
+  COSIM_Q_DT_EM = 0,          /* EM step [s] */
+  COSIM_Q_DT_TH_LIMIT = 1,    /* thermal stability limit [s] */
+  COSIM_Q_STEP = 2,           /* EM steps taken */
+  COSIM_Q_BYTES_RESIDENT = 3, /* device bytes held by the context */
+  COSIM_Q_JOULE_STEPS = 4,    /* steps accumulated since the last reset */
+  COSIM_Q_N_CELLS = 5,
+  COSIM_Q_N_NODES = 6,
+  COSIM_Q_PRECISION = 7,
+  COSIM_Q_LAUNCHES = 8        /* CUDA kernels launched by the context so far */
+};
+cosim_status cosim_query(const cosim_ctx *ctx, int32_t what, double *out);
+
+/* Human-readable description of the context's last error ("" if none).
+ * Valid until the next call on the context. ctx may be NULL: then the last
+ * error of a failed cosim_create on this thread. */
+const char *cosim_last_error(const cosim_ctx *ctx);
+
+/* Free all device memory of the context (after synchronising its stream). */
+void cosim_destroy(cosim_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COSIM_H */

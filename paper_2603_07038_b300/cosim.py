@@ -1,0 +1,375 @@
+"""Python binding of libcosim: the C-ABI calls under the same names.
+
+Only argument marshalling lives here (ctypes structures, numpy/torch buffer
+pointers, the stream and allocator hand-off to PyTorch); every step of the
+solver runs in the CUDA library. There is no fallback: if libcosim.so is
+missing or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcosim.so")
+
+# ---- constants (mirror include/cosim.h)
+COSIM_OK, COSIM_ERR_INVALID, COSIM_ERR_OOM, COSIM_ERR_CUDA = 0, 1, 2, 3
+COSIM_ERR_NOT_CONVERGED, COSIM_ERR_TIMEOUT, COSIM_ERR_NONFINITE = 4, 5, 6
+COSIM_FP64, COSIM_FP32 = 0, 1
+COSIM_BC_PEC, COSIM_BC_PMC, COSIM_BC_CPML = 0, 1, 2
+COSIM_ACCUM_JOULE = 1
+COSIM_JOULE_RESET, COSIM_JOULE_FINALIZE_AVG_POWER, COSIM_JOULE_FINALIZE_ENERGY = 0, 1, 2
+COSIM_MECH_CLAMPED_BOTTOM, COSIM_MECH_KINEMATIC_MOUNT, COSIM_MECH_MASK = 0, 1, 2
+(COSIM_F_EX, COSIM_F_EY, COSIM_F_EZ, COSIM_F_HX, COSIM_F_HY, COSIM_F_HZ, COSIM_F_T, COSIM_F_Q, COSIM_F_P,
+ COSIM_F_UX, COSIM_F_UY, COSIM_F_UZ, COSIM_F_VM, COSIM_F_UMAG, COSIM_F_FX, COSIM_F_FY, COSIM_F_FZ) = range(17)
+(COSIM_Q_DT_EM, COSIM_Q_DT_TH_LIMIT, COSIM_Q_STEP, COSIM_Q_BYTES_RESIDENT, COSIM_Q_JOULE_STEPS,
+ COSIM_Q_N_CELLS, COSIM_Q_N_NODES, COSIM_Q_PRECISION, COSIM_Q_LAUNCHES) = range(9)
+
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT", 6: "NONFINITE"}
+
+EXPORTED = ["cosim_create", "cosim_set_sources", "cosim_em_steps", "cosim_joule_accumulate",
+            "cosim_thermal_steps", "cosim_stress_solve", "cosim_stress_apply", "cosim_read_fields",
+            "cosim_write_fields", "cosim_query", "cosim_last_error", "cosim_destroy"]
+
+
+class CosimError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"cosim {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class cosim_material(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("eps_r", "mu_r", "sigma0", "tcr", "T0", "k", "rho_cp", "E", "nu",
+                                           "alpha_L")]
+
+
+class cosim_grid_desc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dx", C.POINTER(C.c_double)), ("dy", C.POINTER(C.c_double)), ("dz", C.POINTER(C.c_double)),
+                ("mat", C.POINTER(C.c_uint8)), ("nmat", C.c_int32), ("mats", C.POINTER(cosim_material)),
+                ("em_bc", C.c_int32 * 6), ("cpml_cells", C.c_int32), ("cpml_order", C.c_double),
+                ("cpml_eps_r", C.c_double), ("h_conv", C.c_double * 6), ("T_amb", C.c_double),
+                ("T_init", C.c_double)]
+
+
+class cosim_source(C.Structure):
+    _fields_ = [("axis", C.c_int32), ("n_edges", C.c_int32), ("edge_ijk", C.POINTER(C.c_int32)),
+                ("nsteps", C.c_int64), ("amp", C.POINTER(C.c_double))]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class cosim_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+class cosim_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("cfl", C.c_double), ("dt_em", C.c_double),
+                ("thermal_safety", C.c_double), ("stream", C.c_void_p),
+                ("allocator", C.POINTER(cosim_allocator))]
+
+
+class cosim_stress_opts(C.Structure):
+    _fields_ = [("bc", C.c_int32), ("node_mask", C.POINTER(C.c_uint8)), ("T_ref", C.c_double),
+                ("rtol", C.c_double), ("maxit", C.c_int64), ("check_every", C.c_int32)]
+
+
+class cosim_stress_report(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("relres", C.c_double), ("seconds", C.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load libcosim.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2603_07038_b300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    st = C.c_int
+    P = C.c_void_p
+    L.cosim_create.argtypes = [C.POINTER(cosim_grid_desc), C.POINTER(cosim_options), C.POINTER(P)]
+    L.cosim_create.restype = st
+    L.cosim_set_sources.argtypes = [P, C.c_int32, C.POINTER(cosim_source)]
+    L.cosim_set_sources.restype = st
+    L.cosim_em_steps.argtypes = [P, C.c_int64, C.c_uint32]
+    L.cosim_em_steps.restype = st
+    L.cosim_joule_accumulate.argtypes = [P, C.c_int32, C.POINTER(C.c_double)]
+    L.cosim_joule_accumulate.restype = st
+    L.cosim_thermal_steps.argtypes = [P, C.c_int64, C.c_double]
+    L.cosim_thermal_steps.restype = st
+    L.cosim_stress_solve.argtypes = [P, C.POINTER(cosim_stress_opts), C.POINTER(cosim_stress_report)]
+    L.cosim_stress_solve.restype = st
+    L.cosim_stress_apply.argtypes = [P, C.POINTER(cosim_stress_opts), P, P, C.c_int32]
+    L.cosim_stress_apply.restype = st
+    L.cosim_read_fields.argtypes = [P, C.c_int32, C.c_int32, P, C.c_size_t, C.c_int32]
+    L.cosim_read_fields.restype = st
+    L.cosim_write_fields.argtypes = [P, C.c_int32, C.c_int32, P, C.c_size_t, C.c_int32]
+    L.cosim_write_fields.restype = st
+    L.cosim_query.argtypes = [P, C.c_int32, C.POINTER(C.c_double)]
+    L.cosim_query.restype = st
+    L.cosim_last_error.argtypes = [P]
+    L.cosim_last_error.restype = C.c_char_p
+    L.cosim_destroy.argtypes = [P]
+    L.cosim_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _check(status, ctx=None):
+    if status != COSIM_OK:
+        msg = load().cosim_last_error(ctx)
+        raise CosimError(status, msg.decode() if msg else "")
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# ---------------------------------------------------------------- marshalling
+
+class Desc:
+    """cosim_grid_desc built from a problem description (keeps buffers alive)."""
+
+    def __init__(self, problem):
+        p = problem
+        self._h = [np.ascontiguousarray(p.dx, np.float64), np.ascontiguousarray(p.dy, np.float64),
+                   np.ascontiguousarray(p.dz, np.float64)]
+        self._mat = np.ascontiguousarray(p.mat, np.uint8).reshape(-1)
+        rows = [m.as_row() for m in p.materials]
+        self._mats = (cosim_material * len(rows))(*[cosim_material(*r) for r in rows])
+        d = cosim_grid_desc()
+        d.nx, d.ny, d.nz = p.nx, p.ny, p.nz
+        d.dx, d.dy, d.dz = (_dp(a) for a in self._h)
+        d.mat = self._mat.ctypes.data_as(C.POINTER(C.c_uint8))
+        d.nmat = len(rows)
+        d.mats = self._mats
+        for f in range(6):
+            d.em_bc[f] = int(p.em_bc[f])
+            d.h_conv[f] = float(p.h_conv[f])
+        d.cpml_cells = int(p.cpml_cells)
+        d.cpml_order = float(p.cpml_order)
+        d.cpml_eps_r = float(p.cpml_eps_r)
+        d.T_amb = float(p.T_amb)
+        d.T_init = float(p.T_init)
+        self.c = d
+
+
+class TorchAllocator:
+    """Routes the library's device allocations through PyTorch's caching allocator."""
+
+    def __init__(self, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.cuda.current_device() if device is None else device
+        self.stream = stream
+        self._alloc = ALLOC_FN(self._a)
+        self._free = FREE_FN(self._f)
+        self.c = cosim_allocator(self._alloc, self._free, None)
+
+    def _a(self, nbytes, user):
+        try:
+            return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+        except Exception:
+            return None
+
+    def _f(self, ptr, user):
+        self.torch.cuda.caching_allocator_delete(ptr)
+
+
+def cosim_create(problem, precision=COSIM_FP32, cfl=0.99, dt_em=0.0, thermal_safety=0.9, stream=None,
+                 allocator=None):
+    """-> (ctx handle, keep-alive tuple). stream: a torch.cuda.Stream, an int handle, or None."""
+    L = load()
+    desc = Desc(problem)
+    o = cosim_options()
+    o.precision = precision
+    o.cfl = cfl
+    o.dt_em = dt_em
+    o.thermal_safety = thermal_safety
+    if stream is not None:
+        o.stream = stream if isinstance(stream, int) else stream.cuda_stream
+    if allocator is not None:
+        o.allocator = C.pointer(allocator.c)
+    h = C.c_void_p()
+    _check(L.cosim_create(C.byref(desc.c), C.byref(o), C.byref(h)), None)
+    return h, (desc, allocator)
+
+
+def cosim_set_sources(ctx, tables):
+    """tables: [(axis, edges int32 (n,3), amp float64 (nsteps,)), ...]"""
+    keep = []
+    arr = (cosim_source * max(1, len(tables)))()
+    for q, (axis, edges, amp) in enumerate(tables):
+        e = np.ascontiguousarray(edges, np.int32).reshape(-1)
+        a = np.ascontiguousarray(amp, np.float64)
+        keep += [e, a]
+        arr[q] = cosim_source(int(axis), len(e) // 3, e.ctypes.data_as(C.POINTER(C.c_int32)), len(a), _dp(a))
+    _check(load().cosim_set_sources(ctx, len(tables), arr), ctx)
+
+
+def cosim_em_steps(ctx, nsteps, flags=COSIM_ACCUM_JOULE):
+    _check(load().cosim_em_steps(ctx, int(nsteps), int(flags)), ctx)
+
+
+def cosim_joule_accumulate(ctx, op, want_total=True):
+    t = C.c_double(0.0)
+    _check(load().cosim_joule_accumulate(ctx, int(op), C.byref(t) if want_total else None), ctx)
+    return t.value
+
+
+def cosim_thermal_steps(ctx, nsteps, dt=0.0):
+    _check(load().cosim_thermal_steps(ctx, int(nsteps), float(dt)), ctx)
+
+
+def _stress_opts(bc, node_mask, T_ref, rtol, maxit, check_every):
+    o = cosim_stress_opts()
+    o.bc = bc
+    o.T_ref = T_ref
+    o.rtol = rtol
+    o.maxit = maxit
+    o.check_every = check_every
+    keep = None
+    if node_mask is not None:
+        keep = np.ascontiguousarray(node_mask, np.uint8)
+        o.node_mask = keep.ctypes.data_as(C.POINTER(C.c_uint8))
+    return o, keep
+
+
+def cosim_stress_solve(ctx, bc=COSIM_MECH_CLAMPED_BOTTOM, node_mask=None, T_ref=300.0, rtol=1e-9,
+                       maxit=200000, check_every=32, allow_not_converged=False):
+    o, keep = _stress_opts(bc, node_mask, T_ref, rtol, maxit, check_every)
+    rep = cosim_stress_report()
+    st = load().cosim_stress_solve(ctx, C.byref(o), C.byref(rep))
+    if not (allow_not_converged and st == COSIM_ERR_NOT_CONVERGED):
+        _check(st, ctx)
+    return dict(iters=rep.iters, relres=rep.relres, seconds=rep.seconds, status=st)
+
+
+def cosim_stress_apply(ctx, u, bc=COSIM_MECH_CLAMPED_BOTTOM, node_mask=None):
+    """u: (3, n_nodes) array of the context precision (numpy: host, torch CUDA: device) -> K u."""
+    o, keep = _stress_opts(bc, node_mask, 300.0, 0.0, 0, 0)
+    if isinstance(u, np.ndarray):
+        uu = np.ascontiguousarray(u)
+        y = np.empty_like(uu)
+        _check(load().cosim_stress_apply(ctx, C.byref(o), uu.ctypes.data, y.ctypes.data, 0), ctx)
+        return y
+    y = u.new_empty(u.shape)
+    _check(load().cosim_stress_apply(ctx, C.byref(o), u.contiguous().data_ptr(), y.data_ptr(), 1), ctx)
+    return y
+
+
+def cosim_read_fields(ctx, field, dst):
+    """dst: numpy float64/float32 array (host) or a torch CUDA tensor (device)."""
+    if isinstance(dst, np.ndarray):
+        assert dst.flags.c_contiguous
+        dt = COSIM_FP64 if dst.dtype == np.float64 else COSIM_FP32
+        _check(load().cosim_read_fields(ctx, field, dt, dst.ctypes.data, dst.nbytes, 0), ctx)
+    else:
+        import torch
+        assert dst.is_cuda and dst.is_contiguous()
+        dt = COSIM_FP64 if dst.dtype == torch.float64 else COSIM_FP32
+        _check(load().cosim_read_fields(ctx, field, dt, dst.data_ptr(), dst.numel() * dst.element_size(), 1), ctx)
+    return dst
+
+
+def cosim_write_fields(ctx, field, src):
+    if isinstance(src, np.ndarray):
+        s = np.ascontiguousarray(src)
+        dt = COSIM_FP64 if s.dtype == np.float64 else COSIM_FP32
+        _check(load().cosim_write_fields(ctx, field, dt, s.ctypes.data, s.nbytes, 0), ctx)
+    else:
+        import torch
+        s = src.contiguous()
+        dt = COSIM_FP64 if s.dtype == torch.float64 else COSIM_FP32
+        _check(load().cosim_write_fields(ctx, field, dt, s.data_ptr(), s.numel() * s.element_size(), 1), ctx)
+
+
+def cosim_query(ctx, what):
+    v = C.c_double()
+    _check(load().cosim_query(ctx, what, C.byref(v)), ctx)
+    return v.value
+
+
+def cosim_last_error(ctx=None):
+    m = load().cosim_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def cosim_destroy(ctx):
+    if ctx:
+        load().cosim_destroy(ctx)
+
+
+# ---------------------------------------------------------------- convenience
+
+class Context:
+    """Owns one cosim context; methods are the C-ABI calls with the handle bound."""
+
+    def __init__(self, problem, precision=COSIM_FP32, cfl=0.99, dt_em=0.0, thermal_safety=0.9, stream=None,
+                 use_torch_allocator=False):
+        self.problem = problem
+        alloc = TorchAllocator(stream=stream) if use_torch_allocator else None
+        self.h, self._keep = cosim_create(problem, precision, cfl, dt_em, thermal_safety, stream, alloc)
+        self.precision = precision
+        self.nx, self.ny, self.nz = problem.nx, problem.ny, problem.nz
+        self.n_nodes = (self.nx + 1) * (self.ny + 1) * (self.nz + 1)
+        self.n_cells = self.nx * self.ny * self.nz
+        self.dt = cosim_query(self.h, COSIM_Q_DT_EM)
+
+    @property
+    def node_shape(self):
+        return (self.nz + 1, self.ny + 1, self.nx + 1)
+
+    def set_sources(self, tables):
+        cosim_set_sources(self.h, tables)
+
+    def em_steps(self, n, accumulate_joule=True):
+        cosim_em_steps(self.h, n, COSIM_ACCUM_JOULE if accumulate_joule else 0)
+
+    def joule(self, op, want_total=True):
+        return cosim_joule_accumulate(self.h, op, want_total)
+
+    def thermal_steps(self, n, dt=0.0):
+        cosim_thermal_steps(self.h, n, dt)
+
+    def stress_solve(self, **kw):
+        return cosim_stress_solve(self.h, **kw)
+
+    def stress_apply(self, u, **kw):
+        return cosim_stress_apply(self.h, u, **kw)
+
+    def read(self, field, dtype=np.float64):
+        n = self.n_cells if field == COSIM_F_VM else self.n_nodes
+        return cosim_read_fields(self.h, field, np.empty(n, dtype))
+
+    def write(self, field, values):
+        cosim_write_fields(self.h, field, values)
+
+    def query(self, what):
+        return cosim_query(self.h, what)
+
+    def close(self):
+        if self.h:
+            cosim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,977 @@
+// C-ABI implementation of libcosim (see include/cosim.h): context state,
+// device allocation, derived tables and the launch sequence of every call.
+#include "../../include/cosim.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "em.cuh"
+#include "mech.cuh"
+#include "thermal.cuh"
+
+using namespace cosim;
+
+namespace {
+
+constexpr int kEmTX = 32, kEmTY = 8;  // EM tile: 31 x 7 owned nodes per CTA
+constexpr int kMvTX = 32, kMvTY = 8;  // matvec tile
+constexpr int kRedBlocks = 1184;      // fixed grid of the vector kernels (8 x 148)
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct cosim_ctx {
+  // problem
+  int nx = 0, ny = 0, nz = 0, px = 0;
+  long long plane = 0, npad = 0;  // padded node-array length
+  int prec = COSIM_FP32;
+  size_t rsz = 4;
+  std::vector<double> h[3];
+  std::vector<cosim_material> mats;
+  int em_bc[6] = {0, 0, 0, 0, 0, 0};
+  int L = 0;
+  double cpml_order = 3, cpml_eps_r = 1, h_conv[6] = {0, 0, 0, 0, 0, 0}, T_amb = 300, T_init = 300;
+  double dt = 0, dt_th_limit = -1, thermal_safety = 0.9;
+  cudaStream_t stream = nullptr;
+  cosim_allocator alloc{};
+  bool has_alloc = false;
+  // device memory
+  std::vector<std::pair<void *, size_t>> allocs;
+  size_t bytes = 0;
+  uint8_t *mat = nullptr;
+  void *dh[3]{}, *dih[3]{}, *didual[3]{};
+  void *mtab = nullptr, *cpml = nullptr;
+  void *E[2][3]{}, *H[2][3]{};
+  void *pE[2][3][2]{}, *pH[2][3][2]{};
+  int slo[3]{}, shi[3]{}, sn[3]{};
+  long long psi_len[3]{};
+  int par = 0;
+  long long step = 0, n_acc = 0;
+  long long launches = 0;  // kernels launched by this context
+  double *Q = nullptr;
+  void *T[2]{};
+  int tpar = 0;
+  void *P = nullptr;
+  void *scratch = nullptr;  // npad doubles: staging and per-node temporaries
+  double *part = nullptr;   // reduction partials, 3 x kRedBlocks (+ matvec CTAs)
+  int npart = 0;
+  double *scal = nullptr;   // misc device scalars
+  double *host_scal = nullptr;  // pinned
+  // sources
+  int *src_row = nullptr;
+  int4 *src_ent = nullptr;
+  void *src_amp = nullptr;
+  long long amp_len = 0;
+  // mechanics (allocated on first use)
+  bool mech_ready = false;
+  uint8_t *mask = nullptr;
+  void *U[3]{}, *F[3]{}, *Rv[3]{}, *Pv[3]{}, *Qv[3]{}, *Dinv[3]{};
+  void *VM = nullptr, *UMAG = nullptr;
+  CgScalars *cg = nullptr;
+  std::string err;
+};
+
+// ---------------------------------------------------------------- helpers
+
+#define CHECK_CUDA(ctx, call)                                                          \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+      return COSIM_ERR_CUDA;                                                           \
+    }                                                                                  \
+  } while (0)
+
+#define CHECK_LAUNCH(ctx) CHECK_CUDA(ctx, cudaGetLastError())
+
+static cosim_status fail(cosim_ctx *c, cosim_status s, const std::string &msg) {
+  c->err = msg;
+  return s;
+}
+
+static cosim_status dev_alloc(cosim_ctx *c, void **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return COSIM_OK;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (c->has_alloc) {
+    *p = c->alloc.alloc(bytes, c->alloc.user);
+    if (*p == nullptr) return fail(c, COSIM_ERR_OOM, "allocator returned NULL for " + std::to_string(bytes) + " bytes");
+  } else {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return fail(c, COSIM_ERR_OOM, "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+  }
+  c->allocs.emplace_back(*p, bytes);
+  c->bytes += bytes;
+  cudaError_t e = cudaMemsetAsync(*p, 0, bytes, c->stream);
+  if (e != cudaSuccess) return fail(c, COSIM_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  return COSIM_OK;
+}
+
+#define ALLOC(ctx, ptr, bytes)                                        \
+  do {                                                                \
+    cosim_status s_ = dev_alloc((ctx), (void **)&(ptr), (bytes));     \
+    if (s_ != COSIM_OK) return s_;                                    \
+  } while (0)
+
+template <typename R>
+static Geo<R> make_geo(const cosim_ctx *c) {
+  Geo<R> g;
+  g.nx = c->nx;
+  g.ny = c->ny;
+  g.nz = c->nz;
+  g.px = c->px;
+  g.plane = c->plane;
+  g.mat = c->mat;
+  for (int a = 0; a < 3; ++a) {
+    g.h[a] = (const R *)c->dh[a];
+    g.ih[a] = (const R *)c->dih[a];
+    g.idual[a] = (const R *)c->didual[a];
+  }
+  g.mtab = (const R *)c->mtab;
+  g.nmat = (int)c->mats.size();
+  return g;
+}
+
+static int n_of(const cosim_ctx *c, int a) { return a == 0 ? c->nx : (a == 1 ? c->ny : c->nz); }
+
+// host -> device copy ordered on the context stream (pageable sources are
+// staged by the driver before the call returns)
+static cosim_status h2d(cosim_ctx *c, void *dst, const void *src, size_t bytes) {
+  CHECK_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+  return COSIM_OK;
+}
+
+// upload a host double array converted to the context precision
+static cosim_status upload_real(cosim_ctx *c, void **dst, const std::vector<double> &v) {
+  ALLOC(c, *dst, v.size() * c->rsz);
+  if (c->prec == COSIM_FP64) return h2d(c, *dst, v.data(), v.size() * 8);
+  std::vector<float> f(v.begin(), v.end());
+  cosim_status st = h2d(c, *dst, f.data(), f.size() * 4);
+  if (st == COSIM_OK) CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  return st;
+}
+
+// CPML conductivity profile (kappa = 1, alpha = 0), polynomial grading of
+// order m inside each layer, sigma_max = 0.8 (m+1) / (eta0 * mean cell * sqrt(eps_r_bg)).
+static double cpml_sigma(const cosim_ctx *c, int a, double pos, const std::vector<double> &x) {
+  const int n = n_of(c, a), L = c->L;
+  const double m = c->cpml_order, eta0 = std::sqrt(kMu0 / kEps0);
+  double sig = 0;
+  if (L > 0 && c->em_bc[2 * a] == COSIM_BC_CPML) {
+    const double xi = x[L], d = x[L] - x[0];
+    if (pos < xi) sig = 0.8 * (m + 1) / (eta0 * (d / L) * std::sqrt(c->cpml_eps_r)) * std::pow((xi - pos) / d, m);
+  }
+  if (L > 0 && c->em_bc[2 * a + 1] == COSIM_BC_CPML) {
+    const double xi = x[n - L], d = x[n] - x[n - L];
+    if (pos > xi) sig = 0.8 * (m + 1) / (eta0 * (d / L) * std::sqrt(c->cpml_eps_r)) * std::pow((pos - xi) / d, m);
+  }
+  return sig;
+}
+
+// ---------------------------------------------------------------- create
+
+static cosim_status validate(const cosim_grid_desc *d, const cosim_options *o, std::string &why) {
+  if (!d) return why = "desc is NULL", COSIM_ERR_INVALID;
+  if (d->nx < 1 || d->ny < 1 || d->nz < 1) return why = "grid sizes must be >= 1", COSIM_ERR_INVALID;
+  if ((long long)(d->nx + 1) * (d->ny + 1) * (d->nz + 1) > (1LL << 36))
+    return why = "grid too large", COSIM_ERR_INVALID;
+  if (!d->dx || !d->dy || !d->dz || !d->mat || !d->mats) return why = "NULL array in desc", COSIM_ERR_INVALID;
+  if (d->nmat < 1 || d->nmat > kMaxMat) return why = "nmat must be in [1, 256]", COSIM_ERR_INVALID;
+  const double *hs[3] = {d->dx, d->dy, d->dz};
+  const int ns[3] = {d->nx, d->ny, d->nz};
+  for (int a = 0; a < 3; ++a)
+    for (int p = 0; p < ns[a]; ++p)
+      if (!(hs[a][p] > 0) || !std::isfinite(hs[a][p])) return why = "cell sizes must be finite and > 0", COSIM_ERR_INVALID;
+  for (int m = 0; m < d->nmat; ++m) {
+    const cosim_material &q = d->mats[m];
+    if (!(q.eps_r > 0) || !(q.mu_r > 0) || q.sigma0 < 0 || !(q.k >= 0) || !(q.rho_cp > 0) || !(q.E > 0) ||
+        !(q.nu > -1 && q.nu < 0.5))
+      return why = "material " + std::to_string(m) + " has out-of-range constants", COSIM_ERR_INVALID;
+  }
+  const size_t nc = (size_t)d->nx * d->ny * d->nz;
+  for (size_t q = 0; q < nc; ++q)
+    if (d->mat[q] >= d->nmat) return why = "voxel material id >= nmat", COSIM_ERR_INVALID;
+  bool any_cpml = false;
+  for (int f = 0; f < 6; ++f) {
+    if (d->em_bc[f] < 0 || d->em_bc[f] > 2) return why = "bad em_bc", COSIM_ERR_INVALID;
+    if (d->em_bc[f] == COSIM_BC_CPML) any_cpml = true;
+    if (d->h_conv[f] < 0) return why = "h_conv must be >= 0", COSIM_ERR_INVALID;
+  }
+  if (any_cpml) {
+    if (d->cpml_cells < 1 || d->cpml_cells > kMaxL) return why = "cpml_cells must be in [1, 32]", COSIM_ERR_INVALID;
+    if (!(d->cpml_eps_r > 0) || !(d->cpml_order >= 0)) return why = "bad CPML grading", COSIM_ERR_INVALID;
+    for (int a = 0; a < 3; ++a)
+      if ((d->em_bc[2 * a] == COSIM_BC_CPML || d->em_bc[2 * a + 1] == COSIM_BC_CPML) && ns[a] < 2 * d->cpml_cells + 2)
+        return why = "an axis with CPML needs >= 2*cpml_cells+2 cells", COSIM_ERR_INVALID;
+  }
+  if (o && o->precision != COSIM_FP64 && o->precision != COSIM_FP32) return why = "bad precision", COSIM_ERR_INVALID;
+  return COSIM_OK;
+}
+
+template <typename R>
+static cudaError_t set_smem_limits() {
+  const int mv = (kMaxMat * M_COLS + 2 * 3 * (kMvTY + 1) * (kMvTX + 1) + 24 * kMvTY * kMvTX) * (int)sizeof(R);
+  return cudaFuncSetAttribute(hex8_matvec_kernel<R, kMvTX, kMvTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, mv);
+}
+
+static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const cosim_options *o) {
+  c->nx = d->nx;
+  c->ny = d->ny;
+  c->nz = d->nz;
+  c->px = ((d->nx + 1) + 31) / 32 * 32;
+  c->plane = (long long)c->px * (d->ny + 1);
+  c->npad = c->plane * (d->nz + 1);
+  c->prec = o ? o->precision : COSIM_FP32;
+  c->rsz = c->prec == COSIM_FP64 ? 8 : 4;
+  c->stream = o ? (cudaStream_t)o->stream : nullptr;
+  if (o && o->allocator && o->allocator->alloc && o->allocator->free) {
+    c->alloc = *o->allocator;
+    c->has_alloc = true;
+  }
+  c->thermal_safety = (o && o->thermal_safety > 0) ? o->thermal_safety : 0.9;
+  c->h[0].assign(d->dx, d->dx + d->nx);
+  c->h[1].assign(d->dy, d->dy + d->ny);
+  c->h[2].assign(d->dz, d->dz + d->nz);
+  c->mats.assign(d->mats, d->mats + d->nmat);
+  for (int f = 0; f < 6; ++f) {
+    c->em_bc[f] = d->em_bc[f];
+    c->h_conv[f] = d->h_conv[f];
+  }
+  bool any_cpml = false;
+  for (int f = 0; f < 6; ++f) any_cpml |= d->em_bc[f] == COSIM_BC_CPML;
+  c->L = any_cpml ? d->cpml_cells : 0;
+  c->cpml_order = d->cpml_order;
+  c->cpml_eps_r = d->cpml_eps_r;
+  c->T_amb = d->T_amb;
+  c->T_init = d->T_init;
+
+  // EM step: Courant limit of the finest cells at the fastest wave speed
+  double vmax = 0;
+  for (auto &m : c->mats) vmax = std::max(vmax, 1.0 / std::sqrt(kEps0 * m.eps_r * kMu0 * m.mu_r));
+  double s = 0;
+  for (int a = 0; a < 3; ++a) {
+    const double hmin = *std::min_element(c->h[a].begin(), c->h[a].end());
+    s += 1.0 / (hmin * hmin);
+  }
+  const double cfl = (o && o->cfl > 0) ? o->cfl : 0.99;
+  c->dt = (o && o->dt_em > 0) ? o->dt_em : cfl / (vmax * std::sqrt(s));
+
+  // geometry tables
+  for (int a = 0; a < 3; ++a) {
+    const int n = n_of(c, a);
+    std::vector<double> ih(n), idual(n + 1);
+    for (int p = 0; p < n; ++p) ih[p] = 1.0 / c->h[a][p];
+    for (int p = 0; p <= n; ++p) {
+      const double dl = (p > 0 ? 0.5 * c->h[a][p - 1] : 0.0) + (p < n ? 0.5 * c->h[a][p] : 0.0);
+      idual[p] = 1.0 / dl;
+    }
+    cosim_status st;
+    if ((st = upload_real(c, &c->dh[a], c->h[a])) != COSIM_OK) return st;
+    if ((st = upload_real(c, &c->dih[a], ih)) != COSIM_OK) return st;
+    if ((st = upload_real(c, &c->didual[a], idual)) != COSIM_OK) return st;
+  }
+  // material table
+  std::vector<double> mt(c->mats.size() * M_COLS);
+  for (size_t m = 0; m < c->mats.size(); ++m) {
+    const cosim_material &q = c->mats[m];
+    const double lam = q.E * q.nu / ((1 + q.nu) * (1 - 2 * q.nu)), mu = q.E / (2 * (1 + q.nu));
+    double *r = &mt[m * M_COLS];
+    r[M_EPS] = kEps0 * q.eps_r;
+    r[M_SDT2] = q.sigma0 * c->dt * 0.5;
+    r[M_IMU] = 1.0 / (kMu0 * q.mu_r);
+    r[M_K] = q.k;
+    r[M_RHOCP] = q.rho_cp;
+    r[M_LAM] = lam;
+    r[M_MU] = mu;
+    r[M_BETA] = (3 * lam + 2 * mu) * q.alpha_L;
+  }
+  cosim_status st;
+  if ((st = upload_real(c, &c->mtab, mt)) != COSIM_OK) return st;
+  // voxels
+  const size_t ncell = (size_t)c->nx * c->ny * c->nz;
+  ALLOC(c, c->mat, ncell);
+  if ((st = h2d(c, c->mat, d->mat, ncell)) != COSIM_OK) return st;
+
+  // CPML slabs and coefficient table [axis][E,H][b,c][kMaxSlab]
+  std::vector<double> cp(12 * kMaxSlab);
+  for (int a = 0; a < 3; ++a) {
+    const int n = n_of(c, a);
+    c->slo[a] = (c->L > 0 && c->em_bc[2 * a] == COSIM_BC_CPML) ? c->L : 0;
+    c->shi[a] = (c->L > 0 && c->em_bc[2 * a + 1] == COSIM_BC_CPML) ? c->L : 0;
+    const int base = c->slo[a] > 0 ? c->slo[a] + 1 : 0;
+    c->sn[a] = base + (c->shi[a] > 0 ? c->shi[a] + 1 : 0);
+    std::vector<double> x(n + 1, 0.0);
+    for (int p = 0; p < n; ++p) x[p + 1] = x[p] + c->h[a][p];
+    for (int sidx = 0; sidx < kMaxSlab; ++sidx)
+      for (int type = 0; type < 2; ++type) {
+        double b = 1, cc = 0;
+        if (sidx < c->sn[a]) {
+          const int p = sidx < base ? sidx : (n - c->shi[a]) + (sidx - base);
+          const bool ok = type == 0 ? (p <= n) : (p < n);
+          if (ok) {
+            const double pos = type == 0 ? x[p] : 0.5 * (x[p] + x[p + 1]);
+            const double sig = cpml_sigma(c, a, pos, x);
+            if (sig > 0) {
+              b = std::exp(-sig * c->dt / kEps0);
+              cc = b - 1;
+            }
+          }
+        }
+        cp[((a * 2 + type) * 2 + 0) * kMaxSlab + sidx] = b;
+        cp[((a * 2 + type) * 2 + 1) * kMaxSlab + sidx] = cc;
+      }
+  }
+  if ((st = upload_real(c, &c->cpml, cp)) != COSIM_OK) return st;
+  c->psi_len[0] = (long long)(c->nz + 1) * (c->ny + 1) * c->sn[0];
+  c->psi_len[1] = (long long)(c->nz + 1) * c->sn[1] * c->px;
+  c->psi_len[2] = (long long)c->sn[2] * (c->ny + 1) * c->px;
+
+  // fields
+  for (int p = 0; p < 2; ++p)
+    for (int a = 0; a < 3; ++a) {
+      ALLOC(c, c->E[p][a], c->npad * c->rsz);
+      ALLOC(c, c->H[p][a], c->npad * c->rsz);
+      for (int s2 = 0; s2 < 2; ++s2)
+        if (c->psi_len[a] > 0) {
+          ALLOC(c, c->pE[p][a][s2], c->psi_len[a] * c->rsz);
+          ALLOC(c, c->pH[p][a][s2], c->psi_len[a] * c->rsz);
+        }
+    }
+  ALLOC(c, c->Q, c->npad * 8);
+  ALLOC(c, c->T[0], c->npad * c->rsz);
+  ALLOC(c, c->T[1], c->npad * c->rsz);
+  ALLOC(c, c->P, c->npad * c->rsz);
+  ALLOC(c, c->scratch, c->npad * 8);
+  const int mv_blocks = ((c->nx + 1) + kMvTX - 2) / (kMvTX - 1) * (((c->ny + 1) + kMvTY - 2) / (kMvTY - 1));
+  c->npart = std::max(kRedBlocks, mv_blocks);
+  ALLOC(c, c->part, 3 * (size_t)c->npart * 8);
+  ALLOC(c, c->scal, 64 * 8);
+  CHECK_CUDA(c, cudaMallocHost((void **)&c->host_scal, 64 * 8));
+  // the device holds the temperature rise T - T_init (zero after the memset):
+  // full relative precision for small Joule heating even in FP32
+  CHECK_CUDA(c, c->prec == COSIM_FP64 ? set_smem_limits<double>() : set_smem_limits<float>());
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  return COSIM_OK;
+}
+
+extern "C" cosim_status cosim_create(const cosim_grid_desc *desc, const cosim_options *opts, cosim_ctx **out) {
+  g_create_error.clear();
+  if (!out) {
+    g_create_error = "out is NULL";
+    return COSIM_ERR_INVALID;
+  }
+  *out = nullptr;
+  std::string why;
+  cosim_status st = validate(desc, opts, why);
+  if (st != COSIM_OK) {
+    g_create_error = why;
+    return st;
+  }
+  cosim_ctx *c = new cosim_ctx();
+  st = create_impl(c, desc, opts);
+  if (st != COSIM_OK) {
+    g_create_error = c->err;
+    cosim_destroy(c);
+    return st;
+  }
+  *out = c;
+  return COSIM_OK;
+}
+
+extern "C" void cosim_destroy(cosim_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto &a : c->allocs) {
+    if (c->has_alloc)
+      c->alloc.free(a.first, c->alloc.user);
+    else
+      cudaFree(a.first);
+  }
+  if (c->host_scal) cudaFreeHost(c->host_scal);
+  delete c;
+}
+
+extern "C" const char *cosim_last_error(const cosim_ctx *c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+// ---------------------------------------------------------------- sources
+
+static void free_one(cosim_ctx *c, void *p) {
+  if (!p) return;
+  for (size_t q = 0; q < c->allocs.size(); ++q)
+    if (c->allocs[q].first == p) {
+      c->bytes -= c->allocs[q].second;
+      if (c->has_alloc)
+        c->alloc.free(p, c->alloc.user);
+      else
+        cudaFree(p);
+      c->allocs.erase(c->allocs.begin() + q);
+      return;
+    }
+}
+
+extern "C" cosim_status cosim_set_sources(cosim_ctx *c, int32_t n, const cosim_source *src) {
+  if (!c) return COSIM_ERR_INVALID;
+  if (n < 0 || (n > 0 && !src)) return fail(c, COSIM_ERR_INVALID, "bad source list");
+  struct Ent { int row, i, axis, s; };
+  std::vector<Ent> ents;
+  long long amp_len = 0;
+  for (int s = 0; s < n; ++s) {
+    const cosim_source &q = src[s];
+    if (q.axis < 0 || q.axis > 2 || q.n_edges < 0 || (q.n_edges > 0 && !q.edge_ijk) || q.nsteps < 0 ||
+        (q.nsteps > 0 && !q.amp))
+      return fail(c, COSIM_ERR_INVALID, "bad source " + std::to_string(s));
+    for (int e = 0; e < q.n_edges; ++e) {
+      const int i = q.edge_ijk[3 * e], j = q.edge_ijk[3 * e + 1], k = q.edge_ijk[3 * e + 2];
+      const int nn[3] = {i, j, k};
+      bool ok = i >= 0 && j >= 0 && k >= 0 && i <= c->nx && j <= c->ny && k <= c->nz && nn[q.axis] < n_of(c, q.axis);
+      if (!ok) return fail(c, COSIM_ERR_INVALID, "source edge outside the grid");
+      ents.push_back({k * (c->ny + 1) + j, i, q.axis, s});
+    }
+    amp_len = std::max(amp_len, (long long)q.nsteps);
+  }
+  cudaStreamSynchronize(c->stream);
+  free_one(c, c->src_row);
+  free_one(c, c->src_ent);
+  free_one(c, c->src_amp);
+  c->src_row = nullptr;
+  c->src_ent = nullptr;
+  c->src_amp = nullptr;
+  c->amp_len = 0;
+  if (ents.empty()) return COSIM_OK;
+  const int nrow = (c->nz + 1) * (c->ny + 1);
+  std::vector<int> row(nrow + 1, 0);
+  for (auto &e : ents) row[e.row + 1]++;
+  for (int r = 0; r < nrow; ++r) row[r + 1] += row[r];
+  std::vector<int4> ent(ents.size());
+  std::vector<int> fill(row.begin(), row.end() - 1);
+  for (auto &e : ents) ent[fill[e.row]++] = make_int4(e.i, e.axis, e.s, 0);
+  std::vector<double> amp((size_t)n * amp_len, 0.0);
+  for (int s = 0; s < n; ++s)
+    for (long long t = 0; t < src[s].nsteps; ++t) amp[(size_t)s * amp_len + t] = src[s].amp[t];
+  ALLOC(c, c->src_row, row.size() * sizeof(int));
+  ALLOC(c, c->src_ent, ent.size() * sizeof(int4));
+  cosim_status st;
+  if ((st = h2d(c, c->src_row, row.data(), row.size() * sizeof(int))) != COSIM_OK) return st;
+  if ((st = h2d(c, c->src_ent, ent.data(), ent.size() * sizeof(int4))) != COSIM_OK) return st;
+  if ((st = upload_real(c, &c->src_amp, amp)) != COSIM_OK) return st;
+  c->amp_len = amp_len;
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  return COSIM_OK;
+}
+
+// ---------------------------------------------------------------- EM
+
+template <typename R>
+static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum) {
+  EmArgs<R> A;
+  A.g = make_geo<R>(c);
+  for (int a = 0; a < 3; ++a) {
+    A.slo[a] = c->slo[a];
+    A.shi[a] = c->shi[a];
+    A.sn[a] = c->sn[a];
+    A.fixlo[a] = c->em_bc[2 * a] != COSIM_BC_PMC;
+    A.fixhi[a] = c->em_bc[2 * a + 1] != COSIM_BC_PMC;
+  }
+  A.cpml = (const R *)c->cpml;
+  A.dt = (R)c->dt;
+  A.src_row = c->src_row;
+  A.src_ent = c->src_ent;
+  A.src_amp = (const R *)c->src_amp;
+  A.amp_len = c->amp_len;
+  A.Q = accum ? c->Q : nullptr;
+  const dim3 blk(kEmTX, kEmTY);
+  const dim3 grd((c->nx + 1 + kEmTX - 2) / (kEmTX - 1), (c->ny + 1 + kEmTY - 2) / (kEmTY - 1));
+  const size_t smem = ((size_t)c->mats.size() * M_COLS + 12 * kMaxSlab) * sizeof(R);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const int o = c->par, n = c->par ^ 1;
+    for (int a = 0; a < 3; ++a) {
+      A.Eo[a] = (const R *)c->E[o][a];
+      A.En[a] = (R *)c->E[n][a];
+      A.Ho[a] = (const R *)c->H[o][a];
+      A.Hn[a] = (R *)c->H[n][a];
+      for (int s2 = 0; s2 < 2; ++s2) {
+        A.pEo[a][s2] = (const R *)c->pE[o][a][s2];
+        A.pEn[a][s2] = (R *)c->pE[n][a][s2];
+        A.pHo[a][s2] = (const R *)c->pH[o][a][s2];
+        A.pHn[a][s2] = (R *)c->pH[n][a][s2];
+      }
+    }
+    A.step = c->step;
+    em_step_kernel<R, kEmTX, kEmTY><<<grd, blk, smem, c->stream>>>(A); ++c->launches;
+    CHECK_LAUNCH(c);
+    c->par ^= 1;
+    c->step++;
+    if (accum) c->n_acc++;
+  }
+  return COSIM_OK;
+}
+
+extern "C" cosim_status cosim_em_steps(cosim_ctx *c, int64_t nsteps, uint32_t flags) {
+  if (!c) return COSIM_ERR_INVALID;
+  if (nsteps < 0 || (flags & ~COSIM_ACCUM_JOULE)) return fail(c, COSIM_ERR_INVALID, "bad nsteps or flags");
+  const bool acc = flags & COSIM_ACCUM_JOULE;
+  return c->prec == COSIM_FP64 ? em_steps_t<double>(c, nsteps, acc) : em_steps_t<float>(c, nsteps, acc);
+}
+
+// ---------------------------------------------------------------- reductions
+
+static cosim_status sum_q(cosim_ctx *c, double *out) {
+  sum_partial_kernel<<<kRedBlocks, 256, 0, c->stream>>>(c->npad, c->Q, c->part); ++c->launches;
+  CHECK_LAUNCH(c);
+  reduce_final_kernel<<<1, 1024, 0, c->stream>>>(c->part, kRedBlocks, c->scal); ++c->launches;
+  CHECK_LAUNCH(c);
+  CHECK_CUDA(c, cudaMemcpyAsync(c->host_scal, c->scal, 8, cudaMemcpyDeviceToHost, c->stream));
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  *out = c->host_scal[0];
+  return COSIM_OK;
+}
+
+template <typename R>
+static cosim_status joule_t(cosim_ctx *c, int op) {
+  const dim3 blk(32, 8), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + 7) / 8);
+  const size_t smem = c->mats.size() * M_COLS * sizeof(R);
+  const double inv_t = c->n_acc > 0 ? 1.0 / (c->n_acc * c->dt) : 0.0;
+  joule_finalize_kernel<R><<<grd, blk, smem, c->stream>>>(make_geo<R>(c), c->Q, (R *)c->P, (R *)c->T[c->tpar],
+                                                          inv_t, op); ++c->launches;
+  CHECK_LAUNCH(c);
+  return COSIM_OK;
+}
+
+extern "C" cosim_status cosim_joule_accumulate(cosim_ctx *c, int32_t op, double *total) {
+  if (!c) return COSIM_ERR_INVALID;
+  if (op < 0 || op > 2) return fail(c, COSIM_ERR_INVALID, "bad joule op");
+  if (op == COSIM_JOULE_RESET) {
+    if (total) *total = 0;
+    CHECK_CUDA(c, cudaMemsetAsync(c->Q, 0, c->npad * 8, c->stream));
+    c->n_acc = 0;
+    return COSIM_OK;
+  }
+  cosim_status st = c->prec == COSIM_FP64 ? joule_t<double>(c, op) : joule_t<float>(c, op);
+  if (st != COSIM_OK) return st;
+  if (total) {
+    st = sum_q(c, total);
+    if (st != COSIM_OK) return st;
+    if (!std::isfinite(*total)) return fail(c, COSIM_ERR_NONFINITE, "non-finite Joule energy");
+  }
+  return COSIM_OK;
+}
+
+// ---------------------------------------------------------------- thermal
+
+template <typename R>
+static ThArgs<R> th_args(cosim_ctx *c) {
+  ThArgs<R> A;
+  A.g = make_geo<R>(c);
+  A.To = (const R *)c->T[c->tpar];
+  A.Tn = (R *)c->T[c->tpar ^ 1];
+  A.P = (const R *)c->P;
+  A.T_amb = (R)(c->T_amb - c->T_init);
+  for (int f = 0; f < 6; ++f) A.hconv[f] = (R)c->h_conv[f];
+  A.ratio_out = nullptr;
+  A.dt = 0;
+  return A;
+}
+
+template <typename R>
+static cosim_status thermal_limit_t(cosim_ctx *c) {
+  ThArgs<R> A = th_args<R>(c);
+  A.ratio_out = (R *)c->scratch;
+  const dim3 blk(32, 8), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + 7) / 8);
+  const size_t smem = c->mats.size() * M_COLS * sizeof(R);
+  thermal_kernel<R, 1><<<grd, blk, smem, c->stream>>>(A); ++c->launches;
+  CHECK_LAUNCH(c);
+  min_partial_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(A.g, (const R *)c->scratch, c->part); ++c->launches;
+  CHECK_LAUNCH(c);
+  min_final_kernel<<<1, 256, 0, c->stream>>>(c->part, kRedBlocks, c->scal); ++c->launches;
+  CHECK_LAUNCH(c);
+  CHECK_CUDA(c, cudaMemcpyAsync(c->host_scal, c->scal, 8, cudaMemcpyDeviceToHost, c->stream));
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->dt_th_limit = c->host_scal[0];
+  return COSIM_OK;
+}
+
+static cosim_status ensure_th_limit(cosim_ctx *c) {
+  if (c->dt_th_limit > 0) return COSIM_OK;
+  return c->prec == COSIM_FP64 ? thermal_limit_t<double>(c) : thermal_limit_t<float>(c);
+}
+
+template <typename R>
+static cosim_status thermal_steps_t(cosim_ctx *c, int64_t nsteps, double dt) {
+  const dim3 blk(32, 8), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + 7) / 8);
+  const size_t smem = c->mats.size() * M_COLS * sizeof(R);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    ThArgs<R> A = th_args<R>(c);
+    A.dt = (R)dt;
+    thermal_kernel<R, 0><<<grd, blk, smem, c->stream>>>(A); ++c->launches;
+    CHECK_LAUNCH(c);
+    c->tpar ^= 1;
+  }
+  return COSIM_OK;
+}
+
+extern "C" cosim_status cosim_thermal_steps(cosim_ctx *c, int64_t nsteps, double dt) {
+  if (!c) return COSIM_ERR_INVALID;
+  if (nsteps < 0 || !std::isfinite(dt)) return fail(c, COSIM_ERR_INVALID, "bad thermal step arguments");
+  if (dt <= 0) {
+    cosim_status st = ensure_th_limit(c);
+    if (st != COSIM_OK) return st;
+    dt = c->thermal_safety * c->dt_th_limit;
+  }
+  return c->prec == COSIM_FP64 ? thermal_steps_t<double>(c, nsteps, dt) : thermal_steps_t<float>(c, nsteps, dt);
+}
+
+// ---------------------------------------------------------------- mechanics
+
+static cosim_status mech_alloc(cosim_ctx *c) {
+  if (c->mech_ready) return COSIM_OK;
+  ALLOC(c, c->mask, c->npad);
+  for (int a = 0; a < 3; ++a) {
+    ALLOC(c, c->U[a], c->npad * c->rsz);
+    ALLOC(c, c->F[a], c->npad * c->rsz);
+    ALLOC(c, c->Rv[a], c->npad * c->rsz);
+    ALLOC(c, c->Pv[a], c->npad * c->rsz);
+    ALLOC(c, c->Qv[a], c->npad * c->rsz);
+    ALLOC(c, c->Dinv[a], c->npad * c->rsz);
+  }
+  ALLOC(c, c->VM, (size_t)c->nx * c->ny * c->nz * c->rsz);
+  ALLOC(c, c->UMAG, c->npad * c->rsz);
+  ALLOC(c, c->cg, sizeof(CgScalars));
+  c->mech_ready = true;
+  return COSIM_OK;
+}
+
+static cosim_status upload_mask(cosim_ctx *c, const cosim_stress_opts *o) {
+  if (o->bc < 0 || o->bc > 2) return fail(c, COSIM_ERR_INVALID, "bad mechanical support");
+  if (o->bc == COSIM_MECH_MASK && !o->node_mask) return fail(c, COSIM_ERR_INVALID, "node_mask is NULL");
+  std::vector<uint8_t> m(c->npad, 0);
+  auto at = [&](int i, int j, int k) -> uint8_t & { return m[(size_t)k * c->plane + (size_t)j * c->px + i]; };
+  if (o->bc == COSIM_MECH_CLAMPED_BOTTOM) {
+    for (int j = 0; j <= c->ny; ++j)
+      for (int i = 0; i <= c->nx; ++i) at(i, j, 0) = 7;
+  } else if (o->bc == COSIM_MECH_KINEMATIC_MOUNT) {
+    const int ic = c->nx / 2, jc = c->ny / 2;
+    at(ic, jc, 0) |= 7;
+    at(c->nx, jc, 0) |= 6;
+    at(ic, c->ny, 0) |= 4;
+  } else {
+    for (int k = 0; k <= c->nz; ++k)
+      for (int j = 0; j <= c->ny; ++j)
+        for (int i = 0; i <= c->nx; ++i)
+          at(i, j, k) = o->node_mask[((size_t)k * (c->ny + 1) + j) * (c->nx + 1) + i] & 7;
+  }
+  CHECK_CUDA(c, cudaMemcpyAsync(c->mask, m.data(), c->npad, cudaMemcpyHostToDevice, c->stream));
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  return COSIM_OK;
+}
+
+template <typename R>
+static cosim_status matvec_t(cosim_ctx *c, void *const u[3], void *const y[3], double *partial) {
+  MvArgs<R> A;
+  A.g = make_geo<R>(c);
+  for (int a = 0; a < 3; ++a) {
+    A.u[a] = (const R *)u[a];
+    A.y[a] = (R *)y[a];
+  }
+  A.mask = c->mask;
+  A.partial = partial;
+  const dim3 blk(kMvTX, kMvTY);
+  const dim3 grd((c->nx + 1 + kMvTX - 2) / (kMvTX - 1), (c->ny + 1 + kMvTY - 2) / (kMvTY - 1));
+  const size_t smem =
+      ((size_t)c->mats.size() * M_COLS + 2 * 3 * (kMvTY + 1) * (kMvTX + 1) + 24 * kMvTY * kMvTX) * sizeof(R);
+  hex8_matvec_kernel<R, kMvTX, kMvTY><<<grd, blk, smem, c->stream>>>(A); ++c->launches;
+  CHECK_LAUNCH(c);
+  return COSIM_OK;
+}
+
+static int mv_blocks(const cosim_ctx *c) {
+  return ((c->nx + 1 + kMvTX - 2) / (kMvTX - 1)) * ((c->ny + 1 + kMvTY - 2) / (kMvTY - 1));
+}
+
+template <typename R>
+static cosim_status stress_solve_t(cosim_ctx *c, const cosim_stress_opts *o, cosim_stress_report *rep) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const Geo<R> g = make_geo<R>(c);
+  const size_t smem = c->mats.size() * M_COLS * sizeof(R);
+  const dim3 blk(32, 8), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + 7) / 8, c->nz + 1);
+  R *const *U = (R *const *)c->U;
+  R *const *F = (R *const *)c->F;
+  R *const *Rv = (R *const *)c->Rv;
+  R *const *Pv = (R *const *)c->Pv;
+  R *const *Qv = (R *const *)c->Qv;
+  R *const *D = (R *const *)c->Dinv;
+  const R Tref = (R)(o->T_ref - c->T_init);  // device T is the rise over T_init
+  hex8_node_kernel<R, 0><<<grd, blk, smem, c->stream>>>(g, c->mask, nullptr, Tref, D[0], D[1], D[2]); ++c->launches;
+  CHECK_LAUNCH(c);
+  hex8_node_kernel<R, 1><<<grd, blk, smem, c->stream>>>(g, c->mask, (const R *)c->T[c->tpar], Tref, F[0], F[1], F[2]); ++c->launches;
+  CHECK_LAUNCH(c);
+  const long long n = c->npad;
+  double *pa = c->part, *pb = c->part + c->npart;
+  cg_init_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, F[0], F[1], F[2], D[0], D[1], D[2], U[0], U[1], U[2],
+                                                       Rv[0], Rv[1], Rv[2], Pv[0], Pv[1], Pv[2], pa, pb); ++c->launches;
+  CHECK_LAUNCH(c);
+  reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pa, kRedBlocks, &c->cg->rz[0]); ++c->launches;
+  reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pb, kRedBlocks, &c->cg->bb); ++c->launches;
+  CHECK_LAUNCH(c);
+  CHECK_CUDA(c, cudaMemcpyAsync(c->host_scal, &c->cg->bb, 8, cudaMemcpyDeviceToHost, c->stream));
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double bb = c->host_scal[0];
+  const double rtol = o->rtol > 0 ? o->rtol : 1e-9;
+  const int64_t maxit = o->maxit > 0 ? o->maxit : 200000;
+  const int every = o->check_every > 0 ? o->check_every : 32;
+  int64_t it = 0;
+  double relres = bb > 0 ? 1.0 : 0.0;
+  cosim_status result = COSIM_OK;
+  const int nmv = mv_blocks(c);
+  if (!std::isfinite(bb)) return fail(c, COSIM_ERR_NONFINITE, "non-finite thermal load");
+  while (bb > 0) {
+    const int parity = (int)(it & 1);
+    void *pv[3] = {Pv[0], Pv[1], Pv[2]}, *qv[3] = {Qv[0], Qv[1], Qv[2]};
+    cosim_status st = matvec_t<R>(c, pv, qv, pa);
+    if (st != COSIM_OK) return st;
+    reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pa, nmv, &c->cg->pq); ++c->launches;
+    cg_update_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, c->cg, parity, U[0], U[1], U[2], Rv[0], Rv[1], Rv[2],
+                                                           Pv[0], Pv[1], Pv[2], Qv[0], Qv[1], Qv[2], D[0], D[1],
+                                                           D[2], pa, pb); ++c->launches;
+    reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pa, kRedBlocks, &c->cg->rz[parity ^ 1]); ++c->launches;
+    reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pb, kRedBlocks, &c->cg->rr); ++c->launches;
+    CHECK_LAUNCH(c);
+    ++it;
+    if (it % every == 0 || it >= maxit) {
+      CHECK_CUDA(c, cudaMemcpyAsync(c->host_scal, &c->cg->rr, 8, cudaMemcpyDeviceToHost, c->stream));
+      CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+      const double rr = c->host_scal[0];
+      if (!std::isfinite(rr)) return fail(c, COSIM_ERR_NONFINITE, "non-finite CG residual");
+      relres = std::sqrt(rr / bb);
+      if (relres <= rtol) break;
+      if (it >= maxit) {
+        result = COSIM_ERR_NOT_CONVERGED;
+        c->err = "CG reached maxit";
+        break;
+      }
+    }
+    cg_direction_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, c->cg, parity, Pv[0], Pv[1], Pv[2], Rv[0], Rv[1],
+                                                              Rv[2], D[0], D[1], D[2]); ++c->launches;
+    CHECK_LAUNCH(c);
+  }
+  const dim3 grc((c->nx + 31) / 32, (c->ny + 7) / 8, c->nz);
+  von_mises_kernel<R><<<grc, blk, smem, c->stream>>>(g, U[0], U[1], U[2], (const R *)c->T[c->tpar], Tref, (R *)c->VM); ++c->launches;
+  umag_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, U[0], U[1], U[2], (R *)c->UMAG); ++c->launches;
+  CHECK_LAUNCH(c);
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (rep) {
+    rep->iters = it;
+    rep->relres = relres;
+    rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return result;
+}
+
+extern "C" cosim_status cosim_stress_solve(cosim_ctx *c, const cosim_stress_opts *o, cosim_stress_report *rep) {
+  if (!c) return COSIM_ERR_INVALID;
+  if (!o) return fail(c, COSIM_ERR_INVALID, "opts is NULL");
+  if (c->nz < 1) return fail(c, COSIM_ERR_INVALID, "grid too thin");
+  cosim_status st = mech_alloc(c);
+  if (st != COSIM_OK) return st;
+  if ((st = upload_mask(c, o)) != COSIM_OK) return st;
+  return c->prec == COSIM_FP64 ? stress_solve_t<double>(c, o, rep) : stress_solve_t<float>(c, o, rep);
+}
+
+extern "C" cosim_status cosim_stress_apply(cosim_ctx *c, const cosim_stress_opts *o, const void *u, void *y,
+                                           int32_t on_device) {
+  if (!c) return COSIM_ERR_INVALID;
+  if (!o || !u || !y) return fail(c, COSIM_ERR_INVALID, "NULL argument");
+  cosim_status st = mech_alloc(c);
+  if (st != COSIM_OK) return st;
+  if ((st = upload_mask(c, o)) != COSIM_OK) return st;
+  const size_t nn = (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
+  // stage the dense SoA input into the padded direction vector, output through Kp
+  for (int a = 0; a < 3; ++a) {
+    const char *src = (const char *)u + a * nn * c->rsz;
+    CHECK_CUDA(c, cudaMemcpy2DAsync(c->Pv[a], c->px * c->rsz, src, (c->nx + 1) * c->rsz, (c->nx + 1) * c->rsz,
+                                    (size_t)(c->ny + 1) * (c->nz + 1),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  }
+  st = c->prec == COSIM_FP64 ? matvec_t<double>(c, c->Pv, c->Qv, nullptr) : matvec_t<float>(c, c->Pv, c->Qv, nullptr);
+  if (st != COSIM_OK) return st;
+  for (int a = 0; a < 3; ++a) {
+    char *dst = (char *)y + a * nn * c->rsz;
+    CHECK_CUDA(c, cudaMemcpy2DAsync(dst, (c->nx + 1) * c->rsz, c->Qv[a], c->px * c->rsz, (c->nx + 1) * c->rsz,
+                                    (size_t)(c->ny + 1) * (c->nz + 1),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  }
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  return COSIM_OK;
+}
+
+// ---------------------------------------------------------------- field I/O
+
+// dense <-> padded copies with type conversion. For E/H fields on write,
+// entries that are not unknowns are stored as zero.
+template <typename S, typename D>
+__global__ void pack_kernel(const S *src, D *dst, int nx1, int ny1, int nz1, int px, double add) {
+  const long long n = (long long)nx1 * ny1 * nz1;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % nx1);
+    const long long r = q / nx1;
+    dst[q] = add != 0.0 ? (D)((double)src[r * px + i] + add) : (D)src[r * px + i];
+  }
+}
+
+struct FieldMask {  // which node-sized entries of an E/H field are unknowns
+  int kind;         // -1 none, 0..2 E axis, 3..5 H axis
+  int n[3];
+  int fixlo[3], fixhi[3];
+  __device__ bool keep(int i, int j, int k) const {
+    if (kind < 0) return true;
+    const int p[3] = {i, j, k};
+    const int a = kind % 3;
+    if (kind < 3) {
+      if (p[a] >= n[a]) return false;
+      for (int b = 0; b < 3; ++b) {
+        if (b == a) continue;
+        if ((p[b] == 0 && fixlo[b]) || (p[b] == n[b] && fixhi[b])) return false;
+      }
+      return true;
+    }
+    const int b = (a + 1) % 3, cc = (a + 2) % 3;
+    return p[b] < n[b] && p[cc] < n[cc];
+  }
+};
+
+template <typename S, typename D>
+__global__ void unpack_kernel(const S *src, D *dst, int nx1, int ny1, int nz1, int px, FieldMask fm, double sub) {
+  const long long n = (long long)nx1 * ny1 * nz1;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % nx1);
+    const long long r = q / nx1;
+    const int j = (int)(r % ny1), k = (int)(r / ny1);
+    dst[r * px + i] = fm.keep(i, j, k) ? (sub != 0.0 ? (D)((double)src[q] - sub) : (D)src[q]) : D(0);
+  }
+}
+
+static void *field_ptr(cosim_ctx *c, int f, int *elem_bytes, bool *cells, bool *is_double) {
+  *cells = false;
+  *is_double = c->prec == COSIM_FP64;
+  *elem_bytes = (int)c->rsz;
+  switch (f) {
+    case COSIM_F_EX: case COSIM_F_EY: case COSIM_F_EZ: return c->E[c->par][f];
+    case COSIM_F_HX: case COSIM_F_HY: case COSIM_F_HZ: return c->H[c->par][f - 3];
+    case COSIM_F_T: return c->T[c->tpar];
+    case COSIM_F_Q: *is_double = true; *elem_bytes = 8; return c->Q;
+    case COSIM_F_P: return c->P;
+    case COSIM_F_UX: case COSIM_F_UY: case COSIM_F_UZ: return c->mech_ready ? c->U[f - COSIM_F_UX] : nullptr;
+    case COSIM_F_VM: *cells = true; return c->mech_ready ? c->VM : nullptr;
+    case COSIM_F_UMAG: return c->mech_ready ? c->UMAG : nullptr;
+    case COSIM_F_FX: case COSIM_F_FY: case COSIM_F_FZ: return c->mech_ready ? c->F[f - COSIM_F_FX] : nullptr;
+    default: return nullptr;
+  }
+}
+
+template <typename S, typename D>
+static void launch_pack(cosim_ctx *c, const void *src, void *dst, bool cells, double add) {
+  const int nx1 = cells ? c->nx : c->nx + 1, ny1 = cells ? c->ny : c->ny + 1, nz1 = cells ? c->nz : c->nz + 1;
+  const int px = cells ? c->nx : c->px;
+  pack_kernel<S, D><<<kRedBlocks, 256, 0, c->stream>>>((const S *)src, (D *)dst, nx1, ny1, nz1, px, add); ++c->launches;
+}
+
+extern "C" cosim_status cosim_read_fields(cosim_ctx *c, int32_t field, int32_t dtype, void *dst, size_t bytes,
+                                          int32_t dst_is_device) {
+  if (!c) return COSIM_ERR_INVALID;
+  int eb;
+  bool cells, sdbl;
+  void *src = field_ptr(c, field, &eb, &cells, &sdbl);
+  if (!src) return fail(c, COSIM_ERR_INVALID, "unknown field, or field not computed yet");
+  if (dtype != COSIM_FP64 && dtype != COSIM_FP32) return fail(c, COSIM_ERR_INVALID, "bad dtype");
+  const size_t n = cells ? (size_t)c->nx * c->ny * c->nz : (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
+  const size_t ob = dtype == COSIM_FP64 ? 8 : 4;
+  if (!dst || bytes != n * ob) return fail(c, COSIM_ERR_INVALID, "dst size mismatch");
+  void *out = dst_is_device ? dst : c->scratch;
+  const double add = field == COSIM_F_T ? c->T_init : 0.0;
+  if (sdbl && dtype == COSIM_FP64) launch_pack<double, double>(c, src, out, cells, add);
+  else if (sdbl) launch_pack<double, float>(c, src, out, cells, add);
+  else if (dtype == COSIM_FP64) launch_pack<float, double>(c, src, out, cells, add);
+  else launch_pack<float, float>(c, src, out, cells, add);
+  CHECK_LAUNCH(c);
+  if (!dst_is_device) CHECK_CUDA(c, cudaMemcpyAsync(dst, c->scratch, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  return COSIM_OK;
+}
+
+extern "C" cosim_status cosim_write_fields(cosim_ctx *c, int32_t field, int32_t dtype, const void *src, size_t bytes,
+                                           int32_t src_is_device) {
+  if (!c) return COSIM_ERR_INVALID;
+  if (field == COSIM_F_VM || field == COSIM_F_UMAG || (field >= COSIM_F_FX && field <= COSIM_F_FZ))
+    return fail(c, COSIM_ERR_INVALID, "field is not writable");
+  if (field >= COSIM_F_UX && field <= COSIM_F_UZ) {
+    cosim_status st = mech_alloc(c);
+    if (st != COSIM_OK) return st;
+  }
+  int eb;
+  bool cells, ddbl;
+  void *dst = field_ptr(c, field, &eb, &cells, &ddbl);
+  if (!dst) return fail(c, COSIM_ERR_INVALID, "unknown field");
+  if (dtype != COSIM_FP64 && dtype != COSIM_FP32) return fail(c, COSIM_ERR_INVALID, "bad dtype");
+  const size_t n = (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
+  const size_t ib = dtype == COSIM_FP64 ? 8 : 4;
+  if (!src || bytes != n * ib) return fail(c, COSIM_ERR_INVALID, "src size mismatch");
+  const void *in = src;
+  if (!src_is_device) {
+    CHECK_CUDA(c, cudaMemcpyAsync(c->scratch, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    in = c->scratch;
+  }
+  FieldMask fm;
+  fm.kind = field <= COSIM_F_HZ ? field : -1;
+  for (int a = 0; a < 3; ++a) {
+    fm.n[a] = n_of(c, a);
+    fm.fixlo[a] = c->em_bc[2 * a] != COSIM_BC_PMC;
+    fm.fixhi[a] = c->em_bc[2 * a + 1] != COSIM_BC_PMC;
+  }
+  const int nx1 = c->nx + 1, ny1 = c->ny + 1, nz1 = c->nz + 1;
+  const double sub = field == COSIM_F_T ? c->T_init : 0.0;
+  if (ddbl && dtype == COSIM_FP64)
+    unpack_kernel<double, double><<<kRedBlocks, 256, 0, c->stream>>>((const double *)in, (double *)dst, nx1, ny1, nz1, c->px, fm, sub);
+  else if (ddbl)
+    unpack_kernel<float, double><<<kRedBlocks, 256, 0, c->stream>>>((const float *)in, (double *)dst, nx1, ny1, nz1, c->px, fm, sub);
+  else if (dtype == COSIM_FP64)
+    unpack_kernel<double, float><<<kRedBlocks, 256, 0, c->stream>>>((const double *)in, (float *)dst, nx1, ny1, nz1, c->px, fm, sub);
+  else
+    unpack_kernel<float, float><<<kRedBlocks, 256, 0, c->stream>>>((const float *)in, (float *)dst, nx1, ny1, nz1, c->px, fm, sub);
+  ++c->launches;
+  CHECK_LAUNCH(c);
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  return COSIM_OK;
+}
+
+extern "C" cosim_status cosim_query(const cosim_ctx *c, int32_t what, double *out) {
+  if (!c || !out) return COSIM_ERR_INVALID;
+  switch (what) {
+    case COSIM_Q_DT_EM: *out = c->dt; break;
+    case COSIM_Q_DT_TH_LIMIT: {
+      cosim_status st = ensure_th_limit(const_cast<cosim_ctx *>(c));
+      if (st != COSIM_OK) return st;
+      *out = c->dt_th_limit;
+      break;
+    }
+    case COSIM_Q_STEP: *out = (double)c->step; break;
+    case COSIM_Q_BYTES_RESIDENT: *out = (double)c->bytes; break;
+    case COSIM_Q_JOULE_STEPS: *out = (double)c->n_acc; break;
+    case COSIM_Q_N_CELLS: *out = (double)c->nx * c->ny * c->nz; break;
+    case COSIM_Q_N_NODES: *out = (double)(c->nx + 1) * (c->ny + 1) * (c->nz + 1); break;
+    case COSIM_Q_PRECISION: *out = c->prec; break;
+    case COSIM_Q_LAUNCHES: *out = (double)c->launches; break;
+    default: return COSIM_ERR_INVALID;
+  }
+  return COSIM_OK;
+}

@@ -1,0 +1,492 @@
+// Linear thermoelasticity on the voxel grid (Sec. II-B, Eqs. 7-9).
+//
+// Elements are the voxels (bricks hx*hy*hz), nodes carry (ux, uy, uz).
+// K_e = int B^T E_c B dV with 2x2x2 Gauss points, which integrates a brick's
+// stiffness exactly. The kernels evaluate K_e u_e without forming K_e, in
+// the basis of the eight trilinear monomials {1, xi, eta, zeta, xi eta,
+// eta zeta, zeta xi, xi eta zeta}: a 2x2x2 butterfly (Walsh-Hadamard) maps the
+// nodal values to monomial coefficients, the displacement gradient of each
+// monomial group is a 3x3 matrix with a few nonzeros, the monomials are
+// orthogonal on the reference cube (mean 1, 1/3, 1/9 of their squares), so
+// the element energy is a weighted sum of isotropic energies
+// W(G) = lambda tr(G)^2 + mu G:(G + G^T) over the groups, and its gradient
+// maps back through the transposed butterfly. About 300 flops per element.
+#pragma once
+#include "common.cuh"
+
+namespace cosim {
+
+// q[m] = sum_a P_m(s_a) v[a]; a = ax + 2 ay + 4 az, m bit d set <=> factor s_d
+template <typename R>
+__device__ __forceinline__ void modal_fwd(R v[8]) {
+#pragma unroll
+  for (int b = 1; b < 8; b <<= 1)
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      if (!(a & b)) {
+        const R lo = v[a], hi = v[a | b];
+        v[a] = hi + lo;
+        v[a | b] = hi - lo;
+      }
+}
+
+// r[a] = sum_m P_m(s_a) F[m] (transpose of modal_fwd)
+template <typename R>
+__device__ __forceinline__ void modal_bwd(R v[8]) {
+#pragma unroll
+  for (int b = 1; b < 8; b <<= 1)
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      if (!(a & b)) {
+        const R s = v[a], d = v[a | b];
+        v[a] = s - d;
+        v[a | b] = s + d;
+      }
+}
+
+// One monomial group: G (3x3 gradient coefficients), weight w = <phi^2>,
+// slot[d] = monomial receiving column d of the energy gradient (-1: none).
+template <typename R>
+__device__ __forceinline__ void group_term(const R G[3][3], R lam, R mu, R w, const R g[3], const int slot[3],
+                                           R F[3][8]) {
+  const R tr = G[0][0] + G[1][1] + G[2][2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (slot[d] >= 0) {
+        const R S = (c == d ? lam * tr : R(0)) + mu * (G[c][d] + G[d][c]);
+        F[c][slot[d]] += w * S * g[d];
+      }
+}
+
+// u[c][a] (nodal displacement of one element) -> K_e u_e in place.
+template <typename R>
+__device__ __forceinline__ void hex8_apply(R u[3][8], R lam, R mu, R hx, R hy, R hz) {
+  const R g[3] = {R(2) / hx, R(2) / hy, R(2) / hz};
+  const R g8[3] = {g[0] * R(0.125), g[1] * R(0.125), g[2] * R(0.125)};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) modal_fwd(u[c]);
+  R F[3][8];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) F[c][m] = 0;
+  const R third = R(1) / R(3), ninth = R(1) / R(9);
+  R G[3][3];
+  {  // constant gradient: columns from the linear monomials xi, eta, zeta
+    const int slot[3] = {1, 2, 4};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      G[c][0] = g8[0] * u[c][1];
+      G[c][1] = g8[1] * u[c][2];
+      G[c][2] = g8[2] * u[c][4];
+    }
+    group_term(G, lam, mu, R(1), g, slot, F);
+  }
+  {  // terms linear in xi: d/deta of (xi eta), d/dzeta of (zeta xi)
+    const int slot[3] = {-1, 3, 5};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      G[c][0] = 0;
+      G[c][1] = g8[1] * u[c][3];
+      G[c][2] = g8[2] * u[c][5];
+    }
+    group_term(G, lam, mu, third, g, slot, F);
+  }
+  {  // linear in eta: d/dxi of (xi eta), d/dzeta of (eta zeta)
+    const int slot[3] = {3, -1, 6};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      G[c][0] = g8[0] * u[c][3];
+      G[c][1] = 0;
+      G[c][2] = g8[2] * u[c][6];
+    }
+    group_term(G, lam, mu, third, g, slot, F);
+  }
+  {  // linear in zeta: d/dxi of (zeta xi), d/deta of (eta zeta)
+    const int slot[3] = {5, 6, -1};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      G[c][0] = g8[0] * u[c][5];
+      G[c][1] = g8[1] * u[c][6];
+      G[c][2] = 0;
+    }
+    group_term(G, lam, mu, third, g, slot, F);
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {  // bilinear monomials from (xi eta zeta)
+    int slot[3] = {-1, -1, -1};
+    slot[d] = 7;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int e = 0; e < 3; ++e) G[c][e] = (e == d) ? g8[d] * u[c][7] : R(0);
+    group_term(G, lam, mu, ninth, g, slot, F);
+  }
+  const R s = R(0.125) * hx * hy * hz;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    modal_bwd(F[c]);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) u[c][a] = s * F[c][a];
+  }
+}
+
+template <typename R>
+struct MvArgs {
+  Geo<R> g;
+  const R *u[3];
+  R *y[3];
+  const uint8_t *mask;  // per node: bit c set = component c constrained
+  double *partial;      // per-CTA sum of u.y (null: not needed)
+};
+
+// y = K u with constrained DOFs eliminated (their columns are dropped by
+// zeroing u there, their rows give y_c = u_c). CTAs own (TX-1) x (TY-1) node
+// columns and march through the element layers; each thread computes one
+// element of the tile plus a one-element halo at -x/-y, writes its 24 nodal
+// forces to shared memory, and the owner of each node sums its four in-plane
+// elements; the forces of the layer's top face are carried to the next
+// layer in registers. No atomics: deterministic.
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) hex8_matvec_kernel(const MvArgs<R> A) {
+  extern __shared__ unsigned char smem_raw[];
+  const Geo<R> &g = A.g;
+  R *s_mt = reinterpret_cast<R *>(smem_raw);
+  R *su = s_mt + g.nmat * M_COLS;          // [2 planes][3][TY+1][TX+1]
+  R *sr = su + 2 * 3 * (TY + 1) * (TX + 1); // [24][TY][TX]
+  stage_table(s_mt, g.mtab, g.nmat * M_COLS);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int X0 = blockIdx.x * (TX - 1) - 1, Y0 = blockIdx.y * (TY - 1) - 1;
+  const int ex = X0 + tx, ey = Y0 + ty;
+  const bool elem_xy = ex >= 0 && ex < nx && ey >= 0 && ey < ny;
+  const int X = ex + 1, Y = ey + 1;
+  const bool own = tx < TX - 1 && ty < TY - 1 && X <= nx && Y <= ny;
+  const R hx = elem_xy ? g.h[0][ex] : R(1), hy = elem_xy ? g.h[1][ey] : R(1);
+
+  auto su_at = [&](int buf, int c, int qy, int qx) -> R & {
+    return su[((buf * 3 + c) * (TY + 1) + qy) * (TX + 1) + qx];
+  };
+  auto stage = [&](int kp, int buf) {
+    for (int q = tid; q < (TX + 1) * (TY + 1); q += TX * TY) {
+      const int qx = q % (TX + 1), qy = q / (TX + 1);
+      const int Xn = X0 + qx, Yn = Y0 + qy;
+      R v0 = 0, v1 = 0, v2 = 0;
+      if (Xn >= 0 && Xn <= nx && Yn >= 0 && Yn <= ny) {
+        const long long id = g.nid(Xn, Yn, kp);
+        const uint8_t mk = A.mask[id];
+        v0 = (mk & 1) ? R(0) : A.u[0][id];
+        v1 = (mk & 2) ? R(0) : A.u[1][id];
+        v2 = (mk & 4) ? R(0) : A.u[2][id];
+      }
+      su_at(buf, 0, qy, qx) = v0;
+      su_at(buf, 1, qy, qx) = v1;
+      su_at(buf, 2, qy, qx) = v2;
+    }
+  };
+  auto sr_at = [&](int slot, int qy, int qx) -> R & { return sr[(slot * TY + qy) * TX + qx]; };
+
+  stage(0, 0);
+  R acc[3] = {0, 0, 0};
+  double dot = 0.0;
+  for (int k = 0; k < nz; ++k) {
+    stage(k + 1, (k + 1) & 1);
+    __syncthreads();
+    R r[3][8];
+    if (elem_xy) {
+      const int m = g.cell(ex, ey, k);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+          r[c][a] = su_at((k + (a >> 2)) & 1, c, ty + ((a >> 1) & 1), tx + (a & 1));
+      hex8_apply(r, s_mt[m * M_COLS + M_LAM], s_mt[m * M_COLS + M_MU], hx, hy, g.h[2][k]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int a = 0; a < 8; ++a) r[c][a] = 0;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) sr_at(c * 8 + a, ty, tx) = r[c][a];
+    __syncthreads();
+    if (own) {
+      const long long id = g.nid(X, Y, k);
+      const uint8_t mk = A.mask[id];
+      R part = 0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const R bottom = (sr_at(c * 8 + 3, ty, tx) + sr_at(c * 8 + 2, ty, tx + 1)) +
+                         (sr_at(c * 8 + 1, ty + 1, tx) + sr_at(c * 8 + 0, ty + 1, tx + 1));
+        const R top = (sr_at(c * 8 + 7, ty, tx) + sr_at(c * 8 + 6, ty, tx + 1)) +
+                      (sr_at(c * 8 + 5, ty + 1, tx) + sr_at(c * 8 + 4, ty + 1, tx + 1));
+        const R uc = A.u[c][id];
+        const R yv = ((mk >> c) & 1) ? uc : acc[c] + bottom;
+        A.y[c][id] = yv;
+        part += yv * uc;
+        acc[c] = top;
+      }
+      dot += (double)part;
+    }
+  }
+  if (own) {
+    const long long id = g.nid(X, Y, nz);
+    const uint8_t mk = A.mask[id];
+    R part = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const R uc = A.u[c][id];
+      const R yv = ((mk >> c) & 1) ? uc : acc[c];
+      A.y[c][id] = yv;
+      part += yv * uc;
+    }
+    dot += (double)part;
+  }
+  if (A.partial != nullptr) {
+    const double s = block_sum(dot);
+    if (tid == 0) A.partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// Node-gather kernels over the <=8 elements around node (i,j,k):
+// element e = (i-1+dx, j-1+dy, k-1+dz), the node is its corner (1-dx, 1-dy, 1-dz).
+//
+// MODE 0 (Jacobi diagonal, stores 1/diag): K_e(a c, a c) =
+//   (lambda + mu) V/(9 h_c^2) + mu V/9 (1/hx^2 + 1/hy^2 + 1/hz^2) for every corner a.
+// MODE 1 (thermal load, Eq. 8 right-hand side): f_{a,c} = beta_e int dN_a/dx_c dT dV,
+//   beta = (3 lambda + 2 mu) alpha_L, dT trilinear from nodal T - T_ref; with the
+//   monomial coefficients t of dT, int dN_a/dx_c dT dV = V (2/h_c)(s_c/8)
+//   [t_0 + s_d1 t_d1/3 + s_d2 t_d2/3 + s_d1 s_d2 t_d1d2/9], (d1, d2) the other axes.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(256) hex8_node_kernel(Geo<R> g, const uint8_t *mask, const R *T, R T_ref,
+                                                         R *o0, R *o1, R *o2) {
+  extern __shared__ unsigned char smem_raw[];
+  R *s_mt = reinterpret_cast<R *>(smem_raw);
+  stage_table(s_mt, g.mtab, g.nmat * M_COLS);
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i > g.nx || j > g.ny) return;
+  R acc[3] = {0, 0, 0};
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        const int ei = i - 1 + dx, ej = j - 1 + dy, ek = k - 1 + dz;
+        const int m = g.cell(ei, ej, ek);
+        if (m < 0) continue;
+        const R h[3] = {g.h[0][ei], g.h[1][ej], g.h[2][ek]};
+        const R V = h[0] * h[1] * h[2];
+        const R lam = s_mt[m * M_COLS + M_LAM], mu = s_mt[m * M_COLS + M_MU];
+        if (MODE == 0) {
+          const R lap = R(1) / (h[0] * h[0]) + R(1) / (h[1] * h[1]) + R(1) / (h[2] * h[2]);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) acc[c] += (lam + mu) * V / (R(9) * h[c] * h[c]) + mu * V * lap / R(9);
+        } else {
+          R t[8];
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+            t[a] = T[g.nid(ei + (a & 1), ej + ((a >> 1) & 1), ek + ((a >> 2) & 1))] - T_ref;
+          modal_fwd(t);
+          const R s[3] = {R(1 - 2 * dx), R(1 - 2 * dy), R(1 - 2 * dz)};  // node's corner signs
+          const int lin[3] = {1, 2, 4};
+          const R beta = s_mt[m * M_COLS + M_BETA];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const int d1 = (c + 1) % 3, d2 = (c + 2) % 3;
+            const R br = t[0] + s[d1] * t[lin[d1]] * (R(1) / R(3)) + s[d2] * t[lin[d2]] * (R(1) / R(3)) +
+                         s[d1] * s[d2] * t[lin[d1] | lin[d2]] * (R(1) / R(9));
+            // t holds 8x the monomial coefficients: fold 1/8 here
+            acc[c] += beta * V * (R(2) / h[c]) * s[c] * R(0.125) * R(0.125) * br;
+          }
+        }
+      }
+  const long long id = g.nid(i, j, k);
+  const uint8_t mk = mask[id];
+  R *out[3] = {o0, o1, o2};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const bool fixed = (mk >> c) & 1;
+    if (MODE == 0)
+      out[c][id] = fixed ? R(1) : R(1) / acc[c];
+    else
+      out[c][id] = fixed ? R(0) : acc[c];
+  }
+}
+
+// Eq. 9 at the centroid of every element: strain from the constant part of
+// the gradient (linear monomials), dT_c = mean of the 8 nodal dT,
+// sigma = lambda tr(eps) I + 2 mu eps - beta dT_c I. Cell-sized output.
+template <typename R>
+__global__ void __launch_bounds__(256) von_mises_kernel(Geo<R> g, const R *u0, const R *u1, const R *u2, const R *T,
+                                                         R T_ref, R *vm) {
+  extern __shared__ unsigned char smem_raw[];
+  R *s_mt = reinterpret_cast<R *>(smem_raw);
+  stage_table(s_mt, g.mtab, g.nmat * M_COLS);
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const R *u[3] = {u0, u1, u2};
+  const R h[3] = {g.h[0][i], g.h[1][j], g.h[2][k]};
+  R G[3][3];
+  R tm = 0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R v[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) v[a] = u[c][g.nid(i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1))];
+    modal_fwd(v);
+    G[c][0] = v[1] * R(0.25) / h[0];  // (2/h) * (sum / 8)
+    G[c][1] = v[2] * R(0.25) / h[1];
+    G[c][2] = v[4] * R(0.25) / h[2];
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) tm += T[g.nid(i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1))] - T_ref;
+  const int m = g.cell(i, j, k);
+  const R lam = s_mt[m * M_COLS + M_LAM], mu = s_mt[m * M_COLS + M_MU], beta = s_mt[m * M_COLS + M_BETA];
+  const R tr = G[0][0] + G[1][1] + G[2][2];
+  const R th = lam * tr - beta * R(0.125) * tm;
+  const R sx = th + 2 * mu * G[0][0], sy = th + 2 * mu * G[1][1], sz = th + 2 * mu * G[2][2];
+  const R txy = mu * (G[0][1] + G[1][0]), tyz = mu * (G[1][2] + G[2][1]), tzx = mu * (G[2][0] + G[0][2]);
+  const R v2 = R(0.5) * ((sx - sy) * (sx - sy) + (sy - sz) * (sy - sz) + (sz - sx) * (sz - sx)) +
+               R(3) * (txy * txy + tyz * tyz + tzx * tzx);
+  vm[((long long)k * g.ny + j) * g.nx + i] = sqrt(v2);
+}
+
+// ---- Jacobi-PCG vector kernels over the padded SoA node arrays (padding is 0).
+// Grid-stride with a fixed grid: the per-CTA partial sums, and therefore the
+// reductions, are deterministic. Dot products accumulate in FP64.
+
+struct CgScalars {  // device-resident scalars, FP64
+  double rz[2];     // r.z of the current / next iteration (ping-pong by parity)
+  double pq;        // p.Kp
+  double rr;        // r.r
+  double bb;        // f.f
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) cg_init_kernel(long long n, const R *f0, const R *f1, const R *f2,
+                                                       const R *d0, const R *d1, const R *d2, R *x0, R *x1,
+                                                       R *x2, R *r0, R *r1, R *r2, R *p0, R *p1, R *p2,
+                                                       double *part_rz, double *part_bb) {
+  double rz = 0, bb = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const R a0 = f0[q], a1 = f1[q], a2 = f2[q];
+    const R z0 = d0[q] * a0, z1 = d1[q] * a1, z2 = d2[q] * a2;
+    x0[q] = 0; x1[q] = 0; x2[q] = 0;
+    r0[q] = a0; r1[q] = a1; r2[q] = a2;
+    p0[q] = z0; p1[q] = z1; p2[q] = z2;
+    rz += (double)(a0 * z0 + a1 * z1 + a2 * z2);
+    bb += (double)(a0 * a0 + a1 * a1 + a2 * a2);
+  }
+  rz = block_sum(rz);
+  bb = block_sum(bb);
+  if (threadIdx.x == 0) {
+    part_rz[blockIdx.x] = rz;
+    part_bb[blockIdx.x] = bb;
+  }
+}
+
+// x += alpha p, r -= alpha q, alpha = rz/pq; partial sums of r.(D^-1 r) and r.r
+template <typename R>
+__global__ void __launch_bounds__(256) cg_update_kernel(long long n, const CgScalars *sc, int parity, R *x0, R *x1,
+                                                         R *x2, R *r0, R *r1, R *r2, const R *p0, const R *p1,
+                                                         const R *p2, const R *q0, const R *q1, const R *q2,
+                                                         const R *d0, const R *d1, const R *d2, double *part_rz,
+                                                         double *part_rr) {
+  const R alpha = (R)(sc->rz[parity] / sc->pq);
+  double rz = 0, rr = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    x0[q] += alpha * p0[q];
+    x1[q] += alpha * p1[q];
+    x2[q] += alpha * p2[q];
+    const R a0 = r0[q] - alpha * q0[q], a1 = r1[q] - alpha * q1[q], a2 = r2[q] - alpha * q2[q];
+    r0[q] = a0; r1[q] = a1; r2[q] = a2;
+    rz += (double)(a0 * d0[q] * a0 + a1 * d1[q] * a1 + a2 * d2[q] * a2);
+    rr += (double)(a0 * a0 + a1 * a1 + a2 * a2);
+  }
+  rz = block_sum(rz);
+  rr = block_sum(rr);
+  if (threadIdx.x == 0) {
+    part_rz[blockIdx.x] = rz;
+    part_rr[blockIdx.x] = rr;
+  }
+}
+
+// p = D^-1 r + beta p, beta = rz_new / rz_old
+template <typename R>
+__global__ void __launch_bounds__(256) cg_direction_kernel(long long n, const CgScalars *sc, int parity, R *p0,
+                                                            R *p1, R *p2, const R *r0, const R *r1, const R *r2,
+                                                            const R *d0, const R *d1, const R *d2) {
+  const R beta = (R)(sc->rz[parity ^ 1] / sc->rz[parity]);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    p0[q] = d0[q] * r0[q] + beta * p0[q];
+    p1[q] = d1[q] * r1[q] + beta * p1[q];
+    p2[q] = d2[q] * r2[q] + beta * p2[q];
+  }
+}
+
+// final stage of a two-stage reduction: one CTA sums the partials in a fixed order
+__global__ void __launch_bounds__(1024) reduce_final_kernel(const double *part, int n, double *out) {
+  double s = 0;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) s += part[q];
+  s = block_sum(s);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// sum of a padded FP64 array (first stage)
+__global__ void __launch_bounds__(256) sum_partial_kernel(long long n, const double *a, double *part) {
+  double s = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    s += a[q];
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// min of a node-sized ratio array restricted to real nodes (first stage)
+template <typename R>
+__global__ void __launch_bounds__(256) min_partial_kernel(Geo<R> g, const R *a, double *part) {
+  __shared__ double s_min[256];
+  double m = 1e300;
+  const long long n = g.plane * (g.nz + 1);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % g.px);
+    const int j = (int)((q / g.px) % (g.ny + 1));
+    if (i <= g.nx && j <= g.ny) m = fmin(m, (double)a[q]);
+  }
+  s_min[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s_min[threadIdx.x] = fmin(s_min[threadIdx.x], s_min[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s_min[0];
+}
+
+__global__ void __launch_bounds__(256) min_final_kernel(const double *part, int n, double *out) {
+  __shared__ double s_min[256];
+  double m = 1e300;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) m = fmin(m, part[q]);
+  s_min[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s_min[threadIdx.x] = fmin(s_min[threadIdx.x], s_min[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s_min[0];
+}
+
+// |u| per node
+template <typename R>
+__global__ void __launch_bounds__(256) umag_kernel(long long n, const R *u0, const R *u1, const R *u2, R *out) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    out[q] = sqrt(u0[q] * u0[q] + u1[q] * u1[q] + u2[q] * u2[q]);
+}
+
+}  // namespace cosim
