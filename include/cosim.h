@@ -60,7 +60,7 @@ typedef struct {
  *   dx[nx], dy[ny], dz[nz]: cell sizes [m] (non-uniform grid, Sec. II-A);
  *   mat[nz*ny*nx]: voxel material index < nmat, x fastest;
  *   em_bc[6]: COSIM_BC_* per face. CPML faces are terminated by PEC; an axis
- *     with CPML needs at least 2*cpml_cells+2 cells;
+ *     needs at least (number of its CPML faces) * cpml_cells + 2 cells;
  *   cpml_cells, cpml_order (polynomial grading m), cpml_eps_r (background
  *     relative permittivity used for sigma_max);
  *   h_conv[6]: convective film coefficient per face [W/(m^2 K)] (0 = adiabatic,

@@ -210,9 +210,11 @@ static cosim_status validate(const cosim_grid_desc *d, const cosim_options *o, s
   if (any_cpml) {
     if (d->cpml_cells < 1 || d->cpml_cells > kMaxL) return why = "cpml_cells must be in [1, 32]", COSIM_ERR_INVALID;
     if (!(d->cpml_eps_r > 0) || !(d->cpml_order >= 0)) return why = "bad CPML grading", COSIM_ERR_INVALID;
-    for (int a = 0; a < 3; ++a)
-      if ((d->em_bc[2 * a] == COSIM_BC_CPML || d->em_bc[2 * a + 1] == COSIM_BC_CPML) && ns[a] < 2 * d->cpml_cells + 2)
-        return why = "an axis with CPML needs >= 2*cpml_cells+2 cells", COSIM_ERR_INVALID;
+    for (int a = 0; a < 3; ++a) {
+      const int layers = (d->em_bc[2 * a] == COSIM_BC_CPML) + (d->em_bc[2 * a + 1] == COSIM_BC_CPML);
+      if (ns[a] < layers * d->cpml_cells + 2)
+        return why = "an axis needs >= (CPML faces x cpml_cells) + 2 cells", COSIM_ERR_INVALID;
+    }
   }
   if (o && o->precision != COSIM_FP64 && o->precision != COSIM_FP32) return why = "bad precision", COSIM_ERR_INVALID;
   return COSIM_OK;

@@ -91,7 +91,9 @@ def test_invalid_material_id_rejected(lib):
 def test_thin_cpml_axis_rejected(lib):
     p = W.uniform_box(10, 40, 40, em_bc=(2, 2, 0, 0, 0, 0), cpml_cells=8)
     st, msg = _create_status(p)
-    assert st == api.COSIM_ERR_INVALID and "2*cpml_cells+2" in msg
+    assert st == api.COSIM_ERR_INVALID and "CPML faces x cpml_cells" in msg
+    # one CPML face needs only cpml_cells + 2 cells: validation passes and creation
+    # proceeds to the device (not exercised here without a GPU)
 
 
 def test_null_handle_calls_are_invalid(lib):
