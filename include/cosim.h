@@ -233,6 +233,7 @@ const char *cosim_last_error(const cosim_ctx *ctx);
 /* Free all device memory of the context (after synchronising its stream). */
 void cosim_destroy(cosim_ctx *ctx);
 
+
 #ifdef __cplusplus
 }
 #endif

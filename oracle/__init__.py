@@ -118,7 +118,11 @@ class Grid:
         g.cpml_cells = int(p.cpml_cells)
         g.cpml_order = float(p.cpml_order)
         g.cpml_eps_r = float(p.cpml_eps_r)
-        g.T_amb = float(p.T_amb)
+        # temperatures are handled as the rise over T_init (Eq. 5 is unchanged by
+        # a constant shift of T and T_amb); this keeps FP64 resolution on rises
+        # far below the absolute temperature
+        g.T_amb = float(p.T_amb) - float(p.T_init)
+        self.T0 = float(p.T_init)
         self.g = g
         self.ref = C.byref(g)
 
@@ -174,7 +178,8 @@ class OracleSim:
         self.psi = np.zeros(12 * nn) if CPML in p.em_bc else None
         self.Q = np.zeros(nn)
         self.P = np.zeros(nn)
-        self.T = np.full(nn, float(p.T_init))
+        self.theta = np.zeros(nn)  # T - T_init
+        self.T0 = float(p.T_init)
         self.step = 0
         self.n_acc = 0
         self._src = []
@@ -243,8 +248,17 @@ class OracleSim:
     def joule_finalize_energy(self) -> float:
         """Deposit the burst's Joule energy as an instantaneous temperature rise."""
         C_node = self.capacity()
-        self.T = self.T + self.Q / C_node
+        self.theta = self.theta + self.Q / C_node
         return float(self.Q.sum())
+
+    @property
+    def T(self):
+        """absolute temperature [K] (a copy; assign to set)"""
+        return self.theta + self.T0
+
+    @T.setter
+    def T(self, values):
+        self.theta = np.asarray(values, np.float64) - self.T0
 
     # --- thermal -------------------------------------------------------------
     def capacity(self):
@@ -258,11 +272,13 @@ class OracleSim:
     def thermal_steps(self, n: int, dt: float | None = None, safety: float = 0.9, source=True):
         dt = safety * self.thermal_dt_limit() if not dt else float(dt)
         L = lib()
-        T2 = np.empty_like(self.T)
+        th = np.ascontiguousarray(self.theta, np.float64).copy()
+        T2 = np.empty_like(th)
         P = _dp(self.P) if source else None
         for _ in range(n):
-            L.og_thermal_step(self.g.ref, dt, _dp(self.T), P, _dp(T2))
-            self.T, T2 = T2, self.T
+            L.og_thermal_step(self.g.ref, dt, _dp(th), P, _dp(T2))
+            th, T2 = T2, th
+        self.theta = th
         return dt
 
     # --- mechanics -----------------------------------------------------------
@@ -276,10 +292,12 @@ class OracleSim:
         lib().og_hex8_diag(self.g.ref, _u8(fixed), _dp(d))
         return d
 
+    def _rise(self, T):
+        return self.theta if T is None else np.ascontiguousarray(np.asarray(T, np.float64) - self.T0)
+
     def thermal_load(self, fixed, T_ref, T=None):
         f = np.zeros(3 * self.g.n_nodes)
-        T = self.T if T is None else np.ascontiguousarray(T, np.float64)
-        lib().og_thermal_load(self.g.ref, _u8(fixed), _dp(T), float(T_ref), _dp(f))
+        lib().og_thermal_load(self.g.ref, _u8(fixed), _dp(self._rise(T)), float(T_ref) - self.T0, _dp(f))
         return f
 
     def pcg(self, fixed, f, rtol=1e-13, maxit=100000):
@@ -291,10 +309,10 @@ class OracleSim:
         return u, it.value, rr.value
 
     def von_mises(self, u, T_ref, T=None):
-        T = self.T if T is None else np.ascontiguousarray(T, np.float64)
         vm = np.zeros(self.p.n_cells)
         um = np.zeros(self.g.n_nodes)
-        lib().og_von_mises(self.g.ref, _dp(np.ascontiguousarray(u)), _dp(T), float(T_ref), _dp(vm), _dp(um))
+        lib().og_von_mises(self.g.ref, _dp(np.ascontiguousarray(u)), _dp(self._rise(T)), float(T_ref) - self.T0,
+                           _dp(vm), _dp(um))
         return vm, um
 
     def stress_solve(self, fixed, T_ref, rtol=1e-13, maxit=100000):

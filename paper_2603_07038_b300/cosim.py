@@ -309,6 +309,7 @@ def cosim_destroy(ctx):
         load().cosim_destroy(ctx)
 
 
+
 # ---------------------------------------------------------------- convenience
 
 class Context:

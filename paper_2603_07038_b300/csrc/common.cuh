@@ -70,6 +70,22 @@ __device__ __forceinline__ void stage_table(R *dst, const R *src, int n) {
   for (int q = t; q < n; q += nt) dst[q] = src[q];
 }
 
+// Asynchronous global -> shared copy of N (4 or 8) bytes; when ok is false the
+// destination is zero-filled and nothing is read (src must still be a valid
+// address). Completion is tracked with commit/wait groups.
+template <int N>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem, bool ok) {
+  static_assert(N == 4 || N == 8, "cp.async size");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = ok ? N : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(s), "l"(gmem), "n"(N), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // Sum of v over the block (any shape up to 1024 threads); the result is valid
 // in thread 0. Fixed summation order: deterministic run to run.
 __device__ __forceinline__ double block_sum(double v) {

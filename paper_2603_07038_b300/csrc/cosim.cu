@@ -212,7 +212,7 @@ static cosim_status validate(const cosim_grid_desc *d, const cosim_options *o, s
     if (!(d->cpml_eps_r > 0) || !(d->cpml_order >= 0)) return why = "bad CPML grading", COSIM_ERR_INVALID;
     for (int a = 0; a < 3; ++a) {
       const int layers = (d->em_bc[2 * a] == COSIM_BC_CPML) + (d->em_bc[2 * a + 1] == COSIM_BC_CPML);
-      if (ns[a] < layers * d->cpml_cells + 2)
+      if (layers > 0 && ns[a] < layers * d->cpml_cells + 2)
         return why = "an axis needs >= (CPML faces x cpml_cells) + 2 cells", COSIM_ERR_INVALID;
     }
   }
@@ -223,7 +223,11 @@ static cosim_status validate(const cosim_grid_desc *d, const cosim_options *o, s
 template <typename R>
 static cudaError_t set_smem_limits() {
   const int mv = (kMaxMat * M_COLS + 2 * 3 * (kMvTY + 1) * (kMvTX + 1) + 24 * kMvTY * kMvTX) * (int)sizeof(R);
-  return cudaFuncSetAttribute(hex8_matvec_kernel<R, kMvTX, kMvTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, mv);
+  cudaError_t e =
+      cudaFuncSetAttribute(hex8_matvec_kernel<R, kMvTX, kMvTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, mv);
+  if (e != cudaSuccess) return e;
+  const int em = (int)(em_stage_offset<R, kEmTX, kEmTY>(kMaxMat) + kEmStages * sizeof(EmStage<R, kEmTX, kEmTY>));
+  return cudaFuncSetAttribute(em_step_kernel<R, kEmTX, kEmTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, em);
 }
 
 static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const cosim_options *o) {
@@ -333,7 +337,9 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
         cp[((a * 2 + type) * 2 + 1) * kMaxSlab + sidx] = cc;
       }
   }
-  if ((st = upload_real(c, &c->cpml, cp)) != COSIM_OK) return st;
+  ALLOC(c, c->cpml, cp.size() * 8);  // FP64 in both precisions (see em.cuh)
+  if ((st = h2d(c, c->cpml, cp.data(), cp.size() * 8)) != COSIM_OK) return st;
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
   c->psi_len[0] = (long long)(c->nz + 1) * (c->ny + 1) * c->sn[0];
   c->psi_len[1] = (long long)(c->nz + 1) * c->sn[1] * c->px;
   c->psi_len[2] = (long long)c->sn[2] * (c->ny + 1) * c->px;
@@ -345,8 +351,8 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
       ALLOC(c, c->H[p][a], c->npad * c->rsz);
       for (int s2 = 0; s2 < 2; ++s2)
         if (c->psi_len[a] > 0) {
-          ALLOC(c, c->pE[p][a][s2], c->psi_len[a] * c->rsz);
-          ALLOC(c, c->pH[p][a][s2], c->psi_len[a] * c->rsz);
+          ALLOC(c, c->pE[p][a][s2], c->psi_len[a] * 8);
+          ALLOC(c, c->pH[p][a][s2], c->psi_len[a] * 8);
         }
     }
   ALLOC(c, c->Q, c->npad * 8);
@@ -486,7 +492,7 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum) {
     A.fixlo[a] = c->em_bc[2 * a] != COSIM_BC_PMC;
     A.fixhi[a] = c->em_bc[2 * a + 1] != COSIM_BC_PMC;
   }
-  A.cpml = (const R *)c->cpml;
+  A.cpml = (const double *)c->cpml;
   A.dt = (R)c->dt;
   A.src_row = c->src_row;
   A.src_ent = c->src_ent;
@@ -495,7 +501,8 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum) {
   A.Q = accum ? c->Q : nullptr;
   const dim3 blk(kEmTX, kEmTY);
   const dim3 grd((c->nx + 1 + kEmTX - 2) / (kEmTX - 1), (c->ny + 1 + kEmTY - 2) / (kEmTY - 1));
-  const size_t smem = ((size_t)c->mats.size() * M_COLS + 12 * kMaxSlab) * sizeof(R);
+  const size_t smem = em_stage_offset<R, kEmTX, kEmTY>((int)c->mats.size()) +
+                      kEmStages * sizeof(EmStage<R, kEmTX, kEmTY>);
   for (int64_t s = 0; s < nsteps; ++s) {
     const int o = c->par, n = c->par ^ 1;
     for (int a = 0; a < 3; ++a) {
@@ -504,10 +511,10 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum) {
       A.Ho[a] = (const R *)c->H[o][a];
       A.Hn[a] = (R *)c->H[n][a];
       for (int s2 = 0; s2 < 2; ++s2) {
-        A.pEo[a][s2] = (const R *)c->pE[o][a][s2];
-        A.pEn[a][s2] = (R *)c->pE[n][a][s2];
-        A.pHo[a][s2] = (const R *)c->pH[o][a][s2];
-        A.pHn[a][s2] = (R *)c->pH[n][a][s2];
+        A.pEo[a][s2] = (const double *)c->pE[o][a][s2];
+        A.pEn[a][s2] = (double *)c->pE[n][a][s2];
+        A.pHo[a][s2] = (const double *)c->pH[o][a][s2];
+        A.pHn[a][s2] = (double *)c->pH[n][a][s2];
       }
     }
     A.step = c->step;

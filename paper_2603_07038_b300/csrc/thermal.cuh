@@ -25,61 +25,41 @@ struct ThArgs {
   R *ratio_out;     // dt-limit kernel: C_i / (sum G + film) per node
 };
 
-// Terms of node (i,j,k) from its eight voxels c[dz][dy][dx] = (i-1+dx, j-1+dy, k-1+dz).
+// Voxel-layer sums of one node column (thread (i, j)) for the layer of cells
+// kk, between node planes kk and kk+1. Each of the four voxels
+// (i-1+dx, j-1+dy, kk) contributes k_c times its quarter cross-section to the
+// edges it borders and rho_cp V / 8 to the node capacities. A node at plane k
+// adds the sums of layers k-1 and k, so each layer is evaluated once and
+// carried to the next plane in registers.
 template <typename R>
-struct NodeTerms {
-  R C;           // heat capacity
-  R G[6];        // conductances to -x, +x, -y, +y, -z, +z
-  R film;        // sum of h_f * A_f over convective faces at the node
+struct LayerSums {
+  R ax_p, ax_m;  // x-edges i -> i+1 and i-1 -> i: sum k_c * hy_c * hz / 4
+  R ay_p, ay_m;  // y-edges j -> j+1 and j-1 -> j: sum k_c * hx_c * hz / 4
+  R gz;          // z-edge kk -> kk+1 conductance: sum k_c hx_c hy_c / 4 / hz
+  R cap;         // sum rho_cp V / 8
 };
 
 template <typename R>
-__device__ __forceinline__ NodeTerms<R> node_terms(const R *s_mt, const int c[2][2][2], const R hx[2],
-                                                   const R hy[2], const R hz[2], const R ih[6],
-                                                   const bool onface[6], const R hconv[6]) {
-  NodeTerms<R> t;
-  R k[2][2][2], C = 0;
-#pragma unroll
-  for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
-        const int m = c[dz][dy][dx];
-        k[dz][dy][dx] = mconst(s_mt, m, M_K);
-        C += mconst(s_mt, m, M_RHOCP) * hx[dx] * hy[dy] * hz[dz];
-      }
-  t.C = R(0.125) * C;
-  const R q = R(0.25);
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    t.G[0 + s] = q * ih[0 + s] *
-                 (k[0][0][s] * hy[0] * hz[0] + k[0][1][s] * hy[1] * hz[0] + k[1][0][s] * hy[0] * hz[1] +
-                  k[1][1][s] * hy[1] * hz[1]);
-    t.G[2 + s] = q * ih[2 + s] *
-                 (k[0][s][0] * hx[0] * hz[0] + k[0][s][1] * hx[1] * hz[0] + k[1][s][0] * hx[0] * hz[1] +
-                  k[1][s][1] * hx[1] * hz[1]);
-    t.G[4 + s] = q * ih[4 + s] *
-                 (k[s][0][0] * hx[0] * hy[0] + k[s][0][1] * hx[1] * hy[0] + k[s][1][0] * hx[0] * hy[1] +
-                  k[s][1][1] * hx[1] * hy[1]);
-  }
-  const R ax = R(0.25) * (hy[0] + hy[1]) * (hz[0] + hz[1]);
-  const R ay = R(0.25) * (hx[0] + hx[1]) * (hz[0] + hz[1]);
-  const R az = R(0.25) * (hx[0] + hx[1]) * (hy[0] + hy[1]);
-  R f = 0;
-  if (onface[0]) f += hconv[0] * ax;
-  if (onface[1]) f += hconv[1] * ax;
-  if (onface[2]) f += hconv[2] * ay;
-  if (onface[3]) f += hconv[3] * ay;
-  if (onface[4]) f += hconv[4] * az;
-  if (onface[5]) f += hconv[5] * az;
-  t.film = f;
-  return t;
+__device__ __forceinline__ LayerSums<R> layer_sums(const R *s_mt, int m00, int m01, int m10, int m11, R hxm, R hx0,
+                                                   R hym, R hy0, R hz, R ihz) {
+  // m<dy><dx>: voxel (i-1+dx, j-1+dy, kk); missing voxels contribute zero
+  const R k00 = mconst(s_mt, m00, M_K), k01 = mconst(s_mt, m01, M_K);
+  const R k10 = mconst(s_mt, m10, M_K), k11 = mconst(s_mt, m11, M_K);
+  const R q = R(0.25) * hz;
+  LayerSums<R> L;
+  L.ax_p = q * (k01 * hym + k11 * hy0);
+  L.ax_m = q * (k00 * hym + k10 * hy0);
+  L.ay_p = q * (k10 * hxm + k11 * hx0);
+  L.ay_m = q * (k00 * hxm + k01 * hx0);
+  L.gz = R(0.25) * ihz * (hym * (k00 * hxm + k01 * hx0) + hy0 * (k10 * hxm + k11 * hx0));
+  L.cap = R(0.125) * hz *
+          (hym * (mconst(s_mt, m00, M_RHOCP) * hxm + mconst(s_mt, m01, M_RHOCP) * hx0) +
+           hy0 * (mconst(s_mt, m10, M_RHOCP) * hxm + mconst(s_mt, m11, M_RHOCP) * hx0));
+  return L;
 }
 
-// One forward-Euler step (Eq. 5). Thread per (i, j) column, marching in z;
-// the voxel IDs of the layer below are carried in registers.
-// MODE 0: step T; MODE 1: write the per-node stability ratio instead.
+// One forward-Euler step (Eq. 5). Thread per (i, j) node column, marching in z.
+// MODE 0: step T; MODE 1: write the per-node stability ratio C / (sum G + film).
 template <typename R, int MODE>
 __global__ void __launch_bounds__(256) thermal_kernel(const ThArgs<R> A) {
   extern __shared__ unsigned char smem_raw[];
@@ -91,52 +71,44 @@ __global__ void __launch_bounds__(256) thermal_kernel(const ThArgs<R> A) {
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   if (i > nx || j > ny) return;
-  R hx[2], hy[2], ih[6];
-  hx[0] = i > 0 ? g.h[0][i - 1] : R(0);
-  hx[1] = i < nx ? g.h[0][i] : R(0);
-  hy[0] = j > 0 ? g.h[1][j - 1] : R(0);
-  hy[1] = j < ny ? g.h[1][j] : R(0);
-  ih[0] = i > 0 ? g.ih[0][i - 1] : R(0);
-  ih[1] = i < nx ? g.ih[0][i] : R(0);
-  ih[2] = j > 0 ? g.ih[1][j - 1] : R(0);
-  ih[3] = j < ny ? g.ih[1][j] : R(0);
-  int c[2][2][2];
-  c[0][0][0] = c[0][0][1] = c[0][1][0] = c[0][1][1] = -1;
+  const R hxm = i > 0 ? g.h[0][i - 1] : R(0), hx0 = i < nx ? g.h[0][i] : R(0);
+  const R hym = j > 0 ? g.h[1][j - 1] : R(0), hy0 = j < ny ? g.h[1][j] : R(0);
+  const R ihxm = i > 0 ? g.ih[0][i - 1] : R(0), ihx0 = i < nx ? g.ih[0][i] : R(0);
+  const R ihym = j > 0 ? g.ih[1][j - 1] : R(0), ihy0 = j < ny ? g.ih[1][j] : R(0);
+  // convective faces touching this column: x/y walls (per plane: times the dual z length)
+  const R fxy = ((i == 0 ? A.hconv[0] : R(0)) + (i == nx ? A.hconv[1] : R(0))) * R(0.5) * (hym + hy0) +
+                ((j == 0 ? A.hconv[2] : R(0)) + (j == ny ? A.hconv[3] : R(0))) * R(0.5) * (hxm + hx0);
+  const R az = R(0.25) * (hxm + hx0) * (hym + hy0);  // z-face share of the node
+  LayerSums<R> lo = {0, 0, 0, 0, 0, 0};
   const long long id0 = g.nid(i, j, 0);
-  R T_km1 = 0, T_c = A.To[id0];
+  R T_km1 = 0, T_c = MODE == 0 ? A.To[id0] : R(0);
   for (int k = 0; k <= nz; ++k) {
     const long long id = id0 + (long long)k * g.plane;
-    c[1][0][0] = g.cell(i - 1, j - 1, k);
-    c[1][0][1] = g.cell(i, j - 1, k);
-    c[1][1][0] = g.cell(i - 1, j, k);
-    c[1][1][1] = g.cell(i, j, k);
-    R hz[2];
-    hz[0] = k > 0 ? g.h[2][k - 1] : R(0);
-    hz[1] = k < nz ? g.h[2][k] : R(0);
-    ih[4] = k > 0 ? g.ih[2][k - 1] : R(0);
-    ih[5] = k < nz ? g.ih[2][k] : R(0);
-    const bool onface[6] = {i == 0, i == nx, j == 0, j == ny, k == 0, k == nz};
-    const NodeTerms<R> t = node_terms(s_mt, c, hx, hy, hz, ih, onface, A.hconv);
+    const R hz = k < nz ? g.h[2][k] : R(0), ihz = k < nz ? g.ih[2][k] : R(0);
+    const R hzm = k > 0 ? g.h[2][k - 1] : R(0);
+    const LayerSums<R> up = layer_sums(s_mt, g.cell(i - 1, j - 1, k), g.cell(i, j - 1, k), g.cell(i - 1, j, k),
+                                       g.cell(i, j, k), hxm, hx0, hym, hy0, hz, ihz);
+    const R Gxp = (lo.ax_p + up.ax_p) * ihx0, Gxm = (lo.ax_m + up.ax_m) * ihxm;
+    const R Gyp = (lo.ay_p + up.ay_p) * ihy0, Gym = (lo.ay_m + up.ay_m) * ihym;
+    const R Gzp = up.gz, Gzm = lo.gz;
+    const R C = lo.cap + up.cap;
+    R film = fxy * R(0.5) * (hzm + hz);
+    if (k == 0) film += A.hconv[4] * az;
+    if (k == nz) film += A.hconv[5] * az;
     if (MODE == 1) {
-      R gs = t.film;
-#pragma unroll
-      for (int s = 0; s < 6; ++s) gs += t.G[s];
-      A.ratio_out[id] = t.C / gs;
+      A.ratio_out[id] = C / (Gxp + Gxm + Gyp + Gym + Gzp + Gzm + film);
     } else {
       const R T_kp1 = k < nz ? A.To[id + g.plane] : R(0);
       const R T_xm = i > 0 ? A.To[id - 1] : R(0), T_xp = i < nx ? A.To[id + 1] : R(0);
       const R T_ym = j > 0 ? A.To[id - g.px] : R(0), T_yp = j < ny ? A.To[id + g.px] : R(0);
-      R flux = t.G[0] * (T_xm - T_c) + t.G[1] * (T_xp - T_c) + t.G[2] * (T_ym - T_c) + t.G[3] * (T_yp - T_c) +
-               t.G[4] * (T_km1 - T_c) + t.G[5] * (T_kp1 - T_c) + t.film * (A.T_amb - T_c);
+      R flux = Gxm * (T_xm - T_c) + Gxp * (T_xp - T_c) + Gym * (T_ym - T_c) + Gyp * (T_yp - T_c) +
+               Gzm * (T_km1 - T_c) + Gzp * (T_kp1 - T_c) + film * (A.T_amb - T_c);
       if (A.P != nullptr) flux += A.P[id];
-      A.Tn[id] = T_c + A.dt * flux / t.C;
+      A.Tn[id] = T_c + A.dt * flux / C;
       T_km1 = T_c;
       T_c = T_kp1;
     }
-    c[0][0][0] = c[1][0][0];
-    c[0][0][1] = c[1][0][1];
-    c[0][1][0] = c[1][1][0];
-    c[0][1][1] = c[1][1][1];
+    lo = up;
   }
 }
 

@@ -18,6 +18,16 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / (n if n > 0 else 1.0)
 
 
+def field_rel_l2(got3, ref3):
+    """relative L2 of a vector field (all three components together) and the
+    per-component error norms measured against that same field norm"""
+    ref = np.concatenate([np.asarray(r, np.float64) for r in ref3])
+    n = np.linalg.norm(ref)
+    n = n if n > 0 else 1.0
+    per = [np.linalg.norm(np.asarray(g, np.float64) - np.asarray(r, np.float64)) / n for g, r in zip(got3, ref3)]
+    return float(np.sqrt(sum(e * e for e in per))), per
+
+
 def context(p, precision, dt=0.0):
     build()
     return api.Context(p, precision=precision, dt_em=dt)

@@ -12,7 +12,7 @@ import pytest
 import oracle
 import workloads as W
 from paper_2603_07038_b300 import cosim as api
-from tests.gpu_helpers import FP32, FP64, context, interleaved_to_soa, read_eh, rel_l2
+from tests.gpu_helpers import FP32, FP64, context, field_rel_l2, interleaved_to_soa, read_eh, rel_l2
 from workloads import constraints as BC
 
 pytestmark = pytest.mark.gpu
@@ -72,14 +72,17 @@ def test_config1_fp64_full_path(ref1000):
 
 
 def test_config1_fp32_10k_steps(ref10k):
+    """E and H are compared as vector fields (all components together); the
+    per-component error norms are measured against the same field norm. The
+    port's field is vertical (|Ez| is ~400x |Ex| here), so a component-wise
+    ratio would divide cross-component rounding by a tiny norm."""
     g = run_gpu(ref10k, FP32, 10_000, 1e-6)
-    errs = {}
-    for a in range(3):
-        errs[f"E{a}"] = rel_l2(g["E"][a], ref10k["E"][a])
-        errs[f"H{a}"] = rel_l2(g["H"][a], ref10k["H"][a])
-    errs["Q"] = rel_l2(g["Q"], ref10k["Q"])
-    errs["dT"] = rel_l2(g["T"] - 300, ref10k["T"] - 300)
-    print("FP32 10^4-step relative L2 errors:", {k: f"{v:.2e}" for k, v in errs.items()})
+    eE, perE = field_rel_l2(g["E"], ref10k["E"])
+    eH, perH = field_rel_l2(g["H"], ref10k["H"])
+    errs = {"E": eE, "H": eH, "Q": rel_l2(g["Q"], ref10k["Q"]), "dT": rel_l2(g["T"] - 300, ref10k["T"] - 300)}
+    print("FP32 10^4-step relative L2 errors:", {k: f"{v:.2e}" for k, v in errs.items()},
+          "E components", [f"{v:.1e}" for v in perE], "H components", [f"{v:.1e}" for v in perH],
+          "component-wise Ex", f"{rel_l2(g['E'][0], ref10k['E'][0]):.1e}")
     assert max(errs.values()) < 1e-4, errs
     assert np.max(ref10k["T"] - 300) > 0  # the burst did heat the package
 

@@ -22,7 +22,7 @@ def hetero(seed, nx=6, ny=5, nz=4, h_conv=(0.0,) * 6):
 def test_uniform_temperature_is_stationary():
     p = hetero(1)
     o = oracle.OracleSim(p)
-    o.T[:] = 412.5
+    o.T = np.full(o.g.n_nodes, 412.5)
     o.thermal_steps(20, source=False)
     assert np.all(o.T == 412.5)
 
@@ -47,10 +47,10 @@ def test_convective_face_loss():
     step is dt * h * (whole top area) * (T - T_amb)."""
     p = hetero(4, h_conv=(0, 0, 0, 0, 0, 2.5e4))
     o = oracle.OracleSim(p)
-    o.T[:] = 350.0
+    o.T = np.full(o.g.n_nodes, 350.0)
     C = Metric(p).node_capacity()
     dt = o.thermal_steps(1, source=False)
-    lost = (C * (350.0 - o.T)).sum()
+    lost = (C * (50.0 - o.theta)).sum()  # the oracle's state is the rise over T_init = 300 K
     area = p.dx.sum() * p.dy.sum()
     assert abs(lost / (dt * 2.5e4 * area * 50.0) - 1) < 1e-12
 
