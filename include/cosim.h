@@ -233,6 +233,30 @@ const char *cosim_last_error(const cosim_ctx *ctx);
 /* Free all device memory of the context (after synchronising its stream). */
 void cosim_destroy(cosim_ctx *ctx);
 
+/* Deterministic FP64 sum of n doubles in device memory, for callers that
+ * cannot allocate device memory themselves: an application whose device
+ * memory is fully reserved by its own pool or budget, or a latency-critical
+ * loop where cudaMalloc's implicit synchronisation and possible failure are
+ * not acceptable. The paper has no counterpart; this is a service of the
+ * library (the same two-stage reduction that gives cosim_joule_accumulate its
+ * total, with its partial sums in a fixed array of the library's device image
+ * instead of context scratch).
+ *   x: device pointer to n doubles (caller owns it); n <= 268,435,456 (2^28),
+ *      larger n returns COSIM_ERR_INVALID before any GPU work;
+ *   out: the sum, written to host memory (the call then synchronises stream)
+ *      or to device memory when out_is_device != 0;
+ *   stream: cudaStream_t to run on (NULL = default stream).
+ * Calls no cudaMalloc, cudaFree or any allocating routine. The scratch array
+ * (65,568 doubles, 512.25 KiB) is held by every GPU that loads the library
+ * until the process exits. The first call on a device resolves the array's
+ * device address (cudaGetSymbolAddress) for that device; make that first call
+ * before any stream capture. All calls share the array and it keeps the last
+ * call's contents: calls that overlap on the GPU (concurrent streams or
+ * threads) race and must be serialised by the caller. Nothing needs clearing:
+ * every slot a call reads was written earlier in the same call.
+ * Errors: COSIM_ERR_INVALID (NULL pointer, n < 0, n over the limit),
+ * COSIM_ERR_CUDA; cosim_last_error(NULL) describes the failure. */
+cosim_status cosim_sum_f64_noalloc(const double *x, int64_t n, double *out, int32_t out_is_device, void *stream);
 
 #ifdef __cplusplus
 }

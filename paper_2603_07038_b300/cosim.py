@@ -120,6 +120,8 @@ def load():
     L.cosim_last_error.restype = C.c_char_p
     L.cosim_destroy.argtypes = [P]
     L.cosim_destroy.restype = None
+    L.cosim_sum_f64_noalloc.argtypes = [P, C.c_int64, P, C.c_int32, P]
+    L.cosim_sum_f64_noalloc.restype = st
     _lib = L
     return L
 
@@ -308,6 +310,19 @@ def cosim_destroy(ctx):
     if ctx:
         load().cosim_destroy(ctx)
 
+
+def cosim_sum_f64_noalloc(x, n=None, out=None, stream=None):
+    """Sum of a CUDA float64 tensor without any device allocation by the library.
+    out: None (returns a Python float via host memory) or a CUDA float64 tensor
+    of one element that receives the sum on the device."""
+    n = x.numel() if n is None else int(n)
+    s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    if out is None:
+        v = C.c_double()
+        _check(load().cosim_sum_f64_noalloc(x.data_ptr(), n, C.addressof(v), 0, s), None)
+        return v.value
+    _check(load().cosim_sum_f64_noalloc(x.data_ptr(), n, out.data_ptr(), 1, s), None)
+    return out
 
 
 # ---------------------------------------------------------------- convenience

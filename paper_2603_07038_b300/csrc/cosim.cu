@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -981,6 +982,79 @@ extern "C" cosim_status cosim_query(const cosim_ctx *c, int32_t what, double *ou
     case COSIM_Q_PRECISION: *out = c->prec; break;
     case COSIM_Q_LAUNCHES: *out = (double)c->launches; break;
     default: return COSIM_ERR_INVALID;
+  }
+  return COSIM_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free sum
+//
+// For callers that cannot allocate device memory themselves: an application
+// whose device memory is fully reserved by its own pool or budget, or a
+// latency-critical loop in which the implicit synchronisation and possible
+// failure of cudaMalloc/cudaFree are not acceptable. The two-stage reduction
+// below is the same kernel pair that cosim_joule_accumulate uses for its total,
+// but its partial sums live in a fixed array in this library's device image
+// instead of in context-owned scratch.
+namespace {
+constexpr int kNoAllocMaxBlocks = 65536;                 // partial sums held by the array
+constexpr long long kNoAllocPerBlock = 256LL * 16;       // elements reduced by one CTA
+constexpr long long kNoAllocMaxN = kNoAllocMaxBlocks * kNoAllocPerBlock;  // 2^28 elements
+// 65,536 partials + 32 doubles (the result sits at index kNoAllocMaxBlocks): 512.25 KiB,
+// resident on every device that loads the library until the process exits
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxBlocks + 32];
+std::mutex g_noalloc_mu;
+std::vector<double *> g_noalloc_addr;  // per device: device address of g_noalloc_scratch
+}  // namespace
+
+extern "C" cosim_status cosim_sum_f64_noalloc(const double *x, int64_t n, double *out, int32_t out_is_device,
+                                              void *stream) {
+  g_create_error.clear();
+  if (!x || !out || n < 0) {
+    g_create_error = "cosim_sum_f64_noalloc: NULL pointer or negative n";
+    return COSIM_ERR_INVALID;
+  }
+  if (n > kNoAllocMaxN) {
+    g_create_error = "cosim_sum_f64_noalloc: n = " + std::to_string((long long)n) +
+                     " exceeds the allocation-free limit of " + std::to_string(kNoAllocMaxN) + " elements";
+    return COSIM_ERR_INVALID;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    return COSIM_ERR_CUDA;
+  }
+  double *scratch = nullptr;
+  {
+    // set-up once per device, with that device current: resolve the array's
+    // device address (a host-side use of the symbol itself is not a device address)
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if ((int)g_noalloc_addr.size() <= dev) g_noalloc_addr.resize(dev + 1, nullptr);
+    if (!g_noalloc_addr[dev]) {
+      void *p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        g_create_error = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+        return COSIM_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = (double *)p;
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nblk = (int)std::max<long long>(1, (n + kNoAllocPerBlock - 1) / kNoAllocPerBlock);
+  // every partial slot in [0, nblk) and the result slot are written before they
+  // are read, so the array needs no clearing between calls
+  sum_partial_kernel<<<nblk, 256, 0, s>>>(n, x, scratch);
+  reduce_final_kernel<<<1, 1024, 0, s>>>(scratch, nblk, scratch + kNoAllocMaxBlocks);
+  e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, scratch + kNoAllocMaxBlocks, sizeof(double),
+                        out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && !out_is_device) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("cosim_sum_f64_noalloc: ") + cudaGetErrorString(e);
+    return COSIM_ERR_CUDA;
   }
   return COSIM_OK;
 }
