@@ -113,8 +113,11 @@ class ClockSampler:
 
 def em_alg_bytes(ctx, p):
     """algorithmic HBM bytes of one EM step (FP32): E and H read + written once
-    per unknown (6 x 2 x 4 B per cell), the voxel byte, the FP64 Joule
-    accumulator read + written per node, and the CPML auxiliaries."""
+    per unknown (6 x 2 x 4 B per cell), the voxel byte, the FP32 short-window
+    Joule accumulator read + written per node (plus the FP64 fold every 32
+    steps: 16 B per node / 32), and the CPML state in the slabs (4 field
+    components x (chi high part, chi low part, previous derivative) x
+    read + write x 4 B)."""
     cells, nodes = p.n_cells, p.n_nodes
     L = p.cpml_cells
     psi = 0
@@ -123,8 +126,8 @@ def em_alg_bytes(ctx, p):
         sides = (p.em_bc[2 * a] == 2) + (p.em_bc[2 * a + 1] == 2)
         if sides:
             area = nodes // (n[a] + 1)
-            psi += sides * (L + 1) * area * 4 * 2 * 4  # 4 aux arrays (2 E + 2 H), read + write, FP32
-    return 48 * cells + cells + 16 * nodes + psi
+            psi += sides * (L + 1) * area * 4 * 3 * 2 * 4
+    return 48 * cells + cells + 8 * nodes + nodes // 2 + psi
 
 
 def traffic_from_profile(kernel_src):

@@ -161,21 +161,31 @@ typedef struct {
   const uint8_t *node_mask;  /* host pointer, for COSIM_MECH_MASK only */
   double T_ref;              /* stress-free temperature [K] */
   double rtol;               /* stop at ||r|| <= rtol ||f|| (<= 0: 1e-9) */
-  int64_t maxit;             /* iteration cap (<= 0: 200000) */
+  int64_t maxit;             /* iteration cap (<= 0: 200000; with refine: per inner solve) */
   int32_t check_every;       /* residual checked on the host every n iterations (<= 0: 32) */
+  int32_t refine;            /* 1: FP64 iterative refinement around the context-precision CG */
+  double inner_rtol;         /* refine: relative tolerance of each inner CG solve (<= 0: 1e-4) */
+  int32_t max_refine;        /* refine: outer step cap (<= 0: 30) */
 } cosim_stress_opts;
 
 typedef struct {
-  int64_t iters;
-  double relres;             /* ||f - K u|| / ||f|| as recursively updated by CG */
+  int64_t iters;             /* CG iterations (summed over inner solves when refining) */
+  double relres;             /* ||f - K u|| / ||f||: recursively updated by CG, or the true FP64
+                                residual of the refined solution when refine = 1 */
   double seconds;            /* wall time of the solve */
+  int64_t refine_steps;      /* outer refinement steps taken (0 without refine) */
 } cosim_stress_report;
 
 /* Thermoelastic static solve (Eqs. 7-9): HEX8 elements with exact (2x2x2
  * Gauss) integration, K u = f with f the thermal load of dT = T - T_ref,
  * Jacobi-preconditioned CG (FP64 dot products), then von Mises stress at
  * every element centroid and |u| at every node. Synchronises the stream.
- * Returns COSIM_ERR_NOT_CONVERGED if maxit is reached (u is still stored). */
+ * With refine = 1 the solve is mixed precision: the FP64 residual
+ * r = f - K u (FP64 load, FP64 matvec, FP64 u) drives inner CG solves
+ * K d = r in the context's precision to inner_rtol, u += d, until
+ * ||r|| <= rtol ||f|| (relres then reports that true FP64 residual).
+ * Returns COSIM_ERR_NOT_CONVERGED if maxit (or max_refine) is reached (u is
+ * still stored). */
 cosim_status cosim_stress_solve(cosim_ctx *ctx, const cosim_stress_opts *opts, cosim_stress_report *rep);
 
 /* y = K u for the supports in opts (constrained rows/columns eliminated,

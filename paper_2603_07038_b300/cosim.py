@@ -76,11 +76,13 @@ class cosim_options(C.Structure):
 
 class cosim_stress_opts(C.Structure):
     _fields_ = [("bc", C.c_int32), ("node_mask", C.POINTER(C.c_uint8)), ("T_ref", C.c_double),
-                ("rtol", C.c_double), ("maxit", C.c_int64), ("check_every", C.c_int32)]
+                ("rtol", C.c_double), ("maxit", C.c_int64), ("check_every", C.c_int32),
+                ("refine", C.c_int32), ("inner_rtol", C.c_double), ("max_refine", C.c_int32)]
 
 
 class cosim_stress_report(C.Structure):
-    _fields_ = [("iters", C.c_int64), ("relres", C.c_double), ("seconds", C.c_double)]
+    _fields_ = [("iters", C.c_int64), ("relres", C.c_double), ("seconds", C.c_double),
+                ("refine_steps", C.c_int64)]
 
 
 _lib = None
@@ -247,13 +249,18 @@ def _stress_opts(bc, node_mask, T_ref, rtol, maxit, check_every):
 
 
 def cosim_stress_solve(ctx, bc=COSIM_MECH_CLAMPED_BOTTOM, node_mask=None, T_ref=300.0, rtol=1e-9,
-                       maxit=200000, check_every=32, allow_not_converged=False):
+                       maxit=200000, check_every=32, allow_not_converged=False, refine=False, inner_rtol=0.0,
+                       max_refine=0):
     o, keep = _stress_opts(bc, node_mask, T_ref, rtol, maxit, check_every)
+    o.refine = 1 if refine else 0
+    o.inner_rtol = inner_rtol
+    o.max_refine = max_refine
     rep = cosim_stress_report()
     st = load().cosim_stress_solve(ctx, C.byref(o), C.byref(rep))
     if not (allow_not_converged and st == COSIM_ERR_NOT_CONVERGED):
         _check(st, ctx)
-    return dict(iters=rep.iters, relres=rep.relres, seconds=rep.seconds, status=st)
+    return dict(iters=rep.iters, relres=rep.relres, seconds=rep.seconds, status=st,
+                refine_steps=rep.refine_steps)
 
 
 def cosim_stress_apply(ctx, u, bc=COSIM_MECH_CLAMPED_BOTTOM, node_mask=None):

@@ -49,13 +49,18 @@ struct cosim_ctx {
   void *dh[3]{}, *dih[3]{}, *didual[3]{};
   void *mtab = nullptr, *cpml = nullptr;
   void *E[2][3]{}, *H[2][3]{};
-  void *pE[2][3][2]{}, *pH[2][3][2]{};
+  // CPML state per parity / derivative axis / slot: chi = dF + psi and dF of the previous step;
+  // FP32 contexts also hold the low part of chi (lE, lH)
+  void *xE[2][3][2]{}, *dE[2][3][2]{}, *xH[2][3][2]{}, *dH[2][3][2]{};
+  void *lE[2][3][2]{}, *lH[2][3][2]{};
   int slo[3]{}, shi[3]{}, sn[3]{};
   long long psi_len[3]{};
   int par = 0;
   long long step = 0, n_acc = 0;
   long long launches = 0;  // kernels launched by this context
-  double *Q = nullptr;
+  double *Q = nullptr;      // Joule energy per node, FP64
+  void *Qs = nullptr;       // short-window Joule accumulator (context precision)
+  bool qs_dirty = false;    // Qs may hold energy not yet folded into Q
   void *T[2]{};
   int tpar = 0;
   void *P = nullptr;
@@ -75,6 +80,11 @@ struct cosim_ctx {
   void *U[3]{}, *F[3]{}, *Rv[3]{}, *Pv[3]{}, *Qv[3]{}, *Dinv[3]{};
   void *VM = nullptr, *UMAG = nullptr;
   CgScalars *cg = nullptr;
+  // FP64 geometry (aliases of the tables above for FP64 contexts) and the
+  // FP64 vectors of the mixed-precision refinement (allocated on first use)
+  void *dh64[3]{}, *dih64[3]{}, *didual64[3]{}, *mtab64 = nullptr;
+  bool refine_ready = false;
+  double *U64[3]{}, *F64[3]{}, *R64[3]{};
   std::string err;
 };
 
@@ -162,6 +172,32 @@ static cosim_status upload_real(cosim_ctx *c, void **dst, const std::vector<doub
   return st;
 }
 
+// upload a host double array as FP64
+static cosim_status upload_f64(cosim_ctx *c, void **dst, const std::vector<double> &v) {
+  ALLOC(c, *dst, v.size() * 8);
+  cosim_status st = h2d(c, *dst, v.data(), v.size() * 8);
+  if (st == COSIM_OK) CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  return st;
+}
+
+static Geo<double> make_geo64(const cosim_ctx *c) {
+  Geo<double> g;
+  g.nx = c->nx;
+  g.ny = c->ny;
+  g.nz = c->nz;
+  g.px = c->px;
+  g.plane = c->plane;
+  g.mat = c->mat;
+  for (int a = 0; a < 3; ++a) {
+    g.h[a] = (const double *)c->dh64[a];
+    g.ih[a] = (const double *)c->dih64[a];
+    g.idual[a] = (const double *)c->didual64[a];
+  }
+  g.mtab = (const double *)c->mtab64;
+  g.nmat = (int)c->mats.size();
+  return g;
+}
+
 // CPML conductivity profile (kappa = 1, alpha = 0), polynomial grading of
 // order m inside each layer, sigma_max = 0.8 (m+1) / (eta0 * mean cell * sqrt(eps_r_bg)).
 static double cpml_sigma(const cosim_ctx *c, int a, double pos, const std::vector<double> &x) {
@@ -228,7 +264,10 @@ static cudaError_t set_smem_limits() {
       cudaFuncSetAttribute(hex8_matvec_kernel<R, kMvTX, kMvTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, mv);
   if (e != cudaSuccess) return e;
   const int em = (int)(em_stage_offset<R, kEmTX, kEmTY>(kMaxMat) + kEmStages * sizeof(EmStage<R, kEmTX, kEmTY>));
-  return cudaFuncSetAttribute(em_step_kernel<R, kEmTX, kEmTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, em);
+  e = cudaFuncSetAttribute(em_step_kernel<R, int, kEmTX, kEmTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, em);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(em_step_kernel<R, long long, kEmTX, kEmTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              em);
 }
 
 static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const cosim_options *o) {
@@ -286,9 +325,20 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
     if ((st = upload_real(c, &c->dh[a], c->h[a])) != COSIM_OK) return st;
     if ((st = upload_real(c, &c->dih[a], ih)) != COSIM_OK) return st;
     if ((st = upload_real(c, &c->didual[a], idual)) != COSIM_OK) return st;
+    // FP64 copies for the mixed-precision stress refinement
+    if (c->prec == COSIM_FP64) {
+      c->dh64[a] = c->dh[a];
+      c->dih64[a] = c->dih[a];
+      c->didual64[a] = c->didual[a];
+    } else {
+      if ((st = upload_f64(c, &c->dh64[a], c->h[a])) != COSIM_OK) return st;
+      if ((st = upload_f64(c, &c->dih64[a], ih)) != COSIM_OK) return st;
+      if ((st = upload_f64(c, &c->didual64[a], idual)) != COSIM_OK) return st;
+    }
   }
-  // material table
-  std::vector<double> mt(c->mats.size() * M_COLS);
+  // material table, plus an all-zero row (index nmat) that the EM kernel uses
+  // for voxels outside the grid
+  std::vector<double> mt((c->mats.size() + 1) * M_COLS, 0.0);
   for (size_t m = 0; m < c->mats.size(); ++m) {
     const cosim_material &q = c->mats[m];
     const double lam = q.E * q.nu / ((1 + q.nu) * (1 - 2 * q.nu)), mu = q.E / (2 * (1 + q.nu));
@@ -304,13 +354,17 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
   }
   cosim_status st;
   if ((st = upload_real(c, &c->mtab, mt)) != COSIM_OK) return st;
+  if (c->prec == COSIM_FP64)
+    c->mtab64 = c->mtab;
+  else if ((st = upload_f64(c, &c->mtab64, mt)) != COSIM_OK)
+    return st;
   // voxels
   const size_t ncell = (size_t)c->nx * c->ny * c->nz;
   ALLOC(c, c->mat, ncell);
   if ((st = h2d(c, c->mat, d->mat, ncell)) != COSIM_OK) return st;
 
-  // CPML slabs and coefficient table [axis][E,H][b,c][kMaxSlab]
-  std::vector<double> cp(12 * kMaxSlab);
+  // CPML slabs and the table of 1 - b per [axis][E,H][kMaxSlab]
+  std::vector<double> cp(kCpmlTable);
   for (int a = 0; a < 3; ++a) {
     const int n = n_of(c, a);
     c->slo[a] = (c->L > 0 && c->em_bc[2 * a] == COSIM_BC_CPML) ? c->L : 0;
@@ -321,25 +375,20 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
     for (int p = 0; p < n; ++p) x[p + 1] = x[p] + c->h[a][p];
     for (int sidx = 0; sidx < kMaxSlab; ++sidx)
       for (int type = 0; type < 2; ++type) {
-        double b = 1, cc = 0;
+        double omb = 0;  // 1 - b, b = exp(-sigma dt / eps0); c = b - 1 (kappa = 1, alpha = 0)
         if (sidx < c->sn[a]) {
           const int p = sidx < base ? sidx : (n - c->shi[a]) + (sidx - base);
           const bool ok = type == 0 ? (p <= n) : (p < n);
           if (ok) {
             const double pos = type == 0 ? x[p] : 0.5 * (x[p] + x[p + 1]);
             const double sig = cpml_sigma(c, a, pos, x);
-            if (sig > 0) {
-              b = std::exp(-sig * c->dt / kEps0);
-              cc = b - 1;
-            }
+            if (sig > 0) omb = -std::expm1(-sig * c->dt / kEps0);
           }
         }
-        cp[((a * 2 + type) * 2 + 0) * kMaxSlab + sidx] = b;
-        cp[((a * 2 + type) * 2 + 1) * kMaxSlab + sidx] = cc;
+        cp[(a * 2 + type) * kMaxSlab + sidx] = omb;
       }
   }
-  ALLOC(c, c->cpml, cp.size() * 8);  // FP64 in both precisions (see em.cuh)
-  if ((st = h2d(c, c->cpml, cp.data(), cp.size() * 8)) != COSIM_OK) return st;
+  if ((st = upload_real(c, &c->cpml, cp)) != COSIM_OK) return st;
   CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
   c->psi_len[0] = (long long)(c->nz + 1) * (c->ny + 1) * c->sn[0];
   c->psi_len[1] = (long long)(c->nz + 1) * c->sn[1] * c->px;
@@ -352,11 +401,18 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
       ALLOC(c, c->H[p][a], c->npad * c->rsz);
       for (int s2 = 0; s2 < 2; ++s2)
         if (c->psi_len[a] > 0) {
-          ALLOC(c, c->pE[p][a][s2], c->psi_len[a] * 8);
-          ALLOC(c, c->pH[p][a][s2], c->psi_len[a] * 8);
+          ALLOC(c, c->xE[p][a][s2], c->psi_len[a] * c->rsz);
+          ALLOC(c, c->dE[p][a][s2], c->psi_len[a] * c->rsz);
+          ALLOC(c, c->xH[p][a][s2], c->psi_len[a] * c->rsz);
+          ALLOC(c, c->dH[p][a][s2], c->psi_len[a] * c->rsz);
+          if (c->rsz == 4) {
+            ALLOC(c, c->lE[p][a][s2], c->psi_len[a] * c->rsz);
+            ALLOC(c, c->lH[p][a][s2], c->psi_len[a] * c->rsz);
+          }
         }
     }
   ALLOC(c, c->Q, c->npad * 8);
+  ALLOC(c, c->Qs, c->npad * c->rsz);
   ALLOC(c, c->T[0], c->npad * c->rsz);
   ALLOC(c, c->T[1], c->npad * c->rsz);
   ALLOC(c, c->P, c->npad * c->rsz);
@@ -368,7 +424,8 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
   CHECK_CUDA(c, cudaMallocHost((void **)&c->host_scal, 64 * 8));
   // the device holds the temperature rise T - T_init (zero after the memset):
   // full relative precision for small Joule heating even in FP32
-  CHECK_CUDA(c, c->prec == COSIM_FP64 ? set_smem_limits<double>() : set_smem_limits<float>());
+  CHECK_CUDA(c, set_smem_limits<double>());
+  CHECK_CUDA(c, set_smem_limits<float>());
   CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
   return COSIM_OK;
 }
@@ -482,6 +539,8 @@ extern "C" cosim_status cosim_set_sources(cosim_ctx *c, int32_t n, const cosim_s
 
 // ---------------------------------------------------------------- EM
 
+constexpr int kJouleWindow = 32;  // EM steps per short-window Joule accumulation
+
 template <typename R>
 static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum) {
   EmArgs<R> A;
@@ -493,13 +552,30 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum) {
     A.fixlo[a] = c->em_bc[2 * a] != COSIM_BC_PMC;
     A.fixhi[a] = c->em_bc[2 * a + 1] != COSIM_BC_PMC;
   }
-  A.cpml = (const double *)c->cpml;
+  A.cpml = (const R *)c->cpml;
+  // interior tiles: every thread's node i = i0..i0+TX-1 (i0 = b (TX-1) - 1)
+  // satisfies slo < i < nx - shi, so also 0 < i < nx, and the +x neighbour
+  // i0 + TX stays <= nx; likewise in y
+  auto interior = [](int n, int lo, int hi, int T, int &b0, int &b1) {
+    b0 = b1 = 0;
+    const int nb = (n + 1 + T - 2) / (T - 1);
+    for (int b = 0; b < nb; ++b) {
+      const int i0 = b * (T - 1) - 1;
+      if (i0 >= lo + 1 && i0 + T <= n - hi) {
+        if (b1 == 0) b0 = b;
+        b1 = b + 1;
+      }
+    }
+  };
+  interior(c->nx, c->slo[0], c->shi[0], kEmTX, A.ibx0, A.ibx1);
+  interior(c->ny, c->slo[1], c->shi[1], kEmTY, A.iby0, A.iby1);
   A.dt = (R)c->dt;
   A.src_row = c->src_row;
   A.src_ent = c->src_ent;
   A.src_amp = (const R *)c->src_amp;
   A.amp_len = c->amp_len;
-  A.Q = accum ? c->Q : nullptr;
+  A.Qs = accum ? (R *)c->Qs : nullptr;
+  A.Q = c->Q;
   const dim3 blk(kEmTX, kEmTY);
   const dim3 grd((c->nx + 1 + kEmTX - 2) / (kEmTX - 1), (c->ny + 1 + kEmTY - 2) / (kEmTY - 1));
   const size_t smem = em_stage_offset<R, kEmTX, kEmTY>((int)c->mats.size()) +
@@ -512,18 +588,34 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum) {
       A.Ho[a] = (const R *)c->H[o][a];
       A.Hn[a] = (R *)c->H[n][a];
       for (int s2 = 0; s2 < 2; ++s2) {
-        A.pEo[a][s2] = (const double *)c->pE[o][a][s2];
-        A.pEn[a][s2] = (double *)c->pE[n][a][s2];
-        A.pHo[a][s2] = (const double *)c->pH[o][a][s2];
-        A.pHn[a][s2] = (double *)c->pH[n][a][s2];
+        A.xEo[a][s2] = (const R *)c->xE[o][a][s2];
+        A.dEo[a][s2] = (const R *)c->dE[o][a][s2];
+        A.xEn[a][s2] = (R *)c->xE[n][a][s2];
+        A.dEn[a][s2] = (R *)c->dE[n][a][s2];
+        A.xHo[a][s2] = (const R *)c->xH[o][a][s2];
+        A.dHo[a][s2] = (const R *)c->dH[o][a][s2];
+        A.xHn[a][s2] = (R *)c->xH[n][a][s2];
+        A.dHn[a][s2] = (R *)c->dH[n][a][s2];
+        A.lEo[a][s2] = (const R *)c->lE[o][a][s2];
+        A.lEn[a][s2] = (R *)c->lE[n][a][s2];
+        A.lHo[a][s2] = (const R *)c->lH[o][a][s2];
+        A.lHn[a][s2] = (R *)c->lH[n][a][s2];
       }
     }
     A.step = c->step;
-    em_step_kernel<R, kEmTX, kEmTY><<<grd, blk, smem, c->stream>>>(A); ++c->launches;
+    A.fold = accum && ((c->n_acc + 1) % kJouleWindow == 0);
+    if (c->npad < (1LL << 31))
+      em_step_kernel<R, int, kEmTX, kEmTY><<<grd, blk, smem, c->stream>>>(A);
+    else
+      em_step_kernel<R, long long, kEmTX, kEmTY><<<grd, blk, smem, c->stream>>>(A);
+    ++c->launches;
     CHECK_LAUNCH(c);
     c->par ^= 1;
     c->step++;
-    if (accum) c->n_acc++;
+    if (accum) {
+      c->n_acc++;
+      c->qs_dirty = !A.fold;
+    }
   }
   return COSIM_OK;
 }
@@ -533,6 +625,30 @@ extern "C" cosim_status cosim_em_steps(cosim_ctx *c, int64_t nsteps, uint32_t fl
   if (nsteps < 0 || (flags & ~COSIM_ACCUM_JOULE)) return fail(c, COSIM_ERR_INVALID, "bad nsteps or flags");
   const bool acc = flags & COSIM_ACCUM_JOULE;
   return c->prec == COSIM_FP64 ? em_steps_t<double>(c, nsteps, acc) : em_steps_t<float>(c, nsteps, acc);
+}
+
+// move the short-window Joule energy into the FP64 total (Q += Qs, Qs = 0)
+template <typename R>
+__global__ void __launch_bounds__(256) joule_flush_kernel(long long n, double *Q, R *Qs) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const R v = Qs[q];
+    if (v != R(0)) {
+      Q[q] += (double)v;
+      Qs[q] = R(0);
+    }
+  }
+}
+
+static cosim_status joule_flush(cosim_ctx *c) {
+  if (!c->qs_dirty) return COSIM_OK;
+  if (c->prec == COSIM_FP64)
+    joule_flush_kernel<double><<<kRedBlocks, 256, 0, c->stream>>>(c->npad, c->Q, (double *)c->Qs);
+  else
+    joule_flush_kernel<float><<<kRedBlocks, 256, 0, c->stream>>>(c->npad, c->Q, (float *)c->Qs);
+  ++c->launches;
+  CHECK_LAUNCH(c);
+  c->qs_dirty = false;
+  return COSIM_OK;
 }
 
 // ---------------------------------------------------------------- reductions
@@ -565,8 +681,14 @@ extern "C" cosim_status cosim_joule_accumulate(cosim_ctx *c, int32_t op, double 
   if (op == COSIM_JOULE_RESET) {
     if (total) *total = 0;
     CHECK_CUDA(c, cudaMemsetAsync(c->Q, 0, c->npad * 8, c->stream));
+    CHECK_CUDA(c, cudaMemsetAsync(c->Qs, 0, c->npad * c->rsz, c->stream));
+    c->qs_dirty = false;
     c->n_acc = 0;
     return COSIM_OK;
+  }
+  {
+    cosim_status fs = joule_flush(c);
+    if (fs != COSIM_OK) return fs;
   }
   cosim_status st = c->prec == COSIM_FP64 ? joule_t<double>(c, op) : joule_t<float>(c, op);
   if (st != COSIM_OK) return st;
@@ -687,9 +809,9 @@ static cosim_status upload_mask(cosim_ctx *c, const cosim_stress_opts *o) {
 }
 
 template <typename R>
-static cosim_status matvec_t(cosim_ctx *c, void *const u[3], void *const y[3], double *partial) {
+static cosim_status matvec_g(cosim_ctx *c, const Geo<R> &g, void *const u[3], void *const y[3], double *partial) {
   MvArgs<R> A;
-  A.g = make_geo<R>(c);
+  A.g = g;
   for (int a = 0; a < 3; ++a) {
     A.u[a] = (const R *)u[a];
     A.y[a] = (R *)y[a];
@@ -705,27 +827,27 @@ static cosim_status matvec_t(cosim_ctx *c, void *const u[3], void *const y[3], d
   return COSIM_OK;
 }
 
+template <typename R>
+static cosim_status matvec_t(cosim_ctx *c, void *const u[3], void *const y[3], double *partial) {
+  return matvec_g<R>(c, make_geo<R>(c), u, y, partial);
+}
+
 static int mv_blocks(const cosim_ctx *c) {
   return ((c->nx + 1 + kMvTX - 2) / (kMvTX - 1)) * ((c->ny + 1 + kMvTY - 2) / (kMvTY - 1));
 }
 
+// Jacobi-PCG on K U = F in the context precision, U from zero, with the
+// Jacobi inverse diagonal already in Dinv. Stops at ||r|| <= rtol ||F|| (the
+// recursively updated residual, checked every `every` iterations) or maxit.
 template <typename R>
-static cosim_status stress_solve_t(cosim_ctx *c, const cosim_stress_opts *o, cosim_stress_report *rep) {
-  const auto t0 = std::chrono::steady_clock::now();
-  const Geo<R> g = make_geo<R>(c);
-  const size_t smem = c->mats.size() * M_COLS * sizeof(R);
-  const dim3 blk(32, 8), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + 7) / 8, c->nz + 1);
+static cosim_status pcg_run(cosim_ctx *c, double rtol, int64_t maxit, int every, int64_t *iters, double *relres,
+                            bool *converged) {
   R *const *U = (R *const *)c->U;
   R *const *F = (R *const *)c->F;
   R *const *Rv = (R *const *)c->Rv;
   R *const *Pv = (R *const *)c->Pv;
   R *const *Qv = (R *const *)c->Qv;
   R *const *D = (R *const *)c->Dinv;
-  const R Tref = (R)(o->T_ref - c->T_init);  // device T is the rise over T_init
-  hex8_node_kernel<R, 0><<<grd, blk, smem, c->stream>>>(g, c->mask, nullptr, Tref, D[0], D[1], D[2]); ++c->launches;
-  CHECK_LAUNCH(c);
-  hex8_node_kernel<R, 1><<<grd, blk, smem, c->stream>>>(g, c->mask, (const R *)c->T[c->tpar], Tref, F[0], F[1], F[2]); ++c->launches;
-  CHECK_LAUNCH(c);
   const long long n = c->npad;
   double *pa = c->part, *pb = c->part + c->npart;
   cg_init_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, F[0], F[1], F[2], D[0], D[1], D[2], U[0], U[1], U[2],
@@ -737,14 +859,11 @@ static cosim_status stress_solve_t(cosim_ctx *c, const cosim_stress_opts *o, cos
   CHECK_CUDA(c, cudaMemcpyAsync(c->host_scal, &c->cg->bb, 8, cudaMemcpyDeviceToHost, c->stream));
   CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
   const double bb = c->host_scal[0];
-  const double rtol = o->rtol > 0 ? o->rtol : 1e-9;
-  const int64_t maxit = o->maxit > 0 ? o->maxit : 200000;
-  const int every = o->check_every > 0 ? o->check_every : 32;
+  if (!std::isfinite(bb)) return fail(c, COSIM_ERR_NONFINITE, "non-finite right-hand side");
   int64_t it = 0;
-  double relres = bb > 0 ? 1.0 : 0.0;
-  cosim_status result = COSIM_OK;
+  *relres = bb > 0 ? 1.0 : 0.0;
+  *converged = !(bb > 0);
   const int nmv = mv_blocks(c);
-  if (!std::isfinite(bb)) return fail(c, COSIM_ERR_NONFINITE, "non-finite thermal load");
   while (bb > 0) {
     const int parity = (int)(it & 1);
     void *pv[3] = {Pv[0], Pv[1], Pv[2]}, *qv[3] = {Qv[0], Qv[1], Qv[2]};
@@ -763,17 +882,115 @@ static cosim_status stress_solve_t(cosim_ctx *c, const cosim_stress_opts *o, cos
       CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
       const double rr = c->host_scal[0];
       if (!std::isfinite(rr)) return fail(c, COSIM_ERR_NONFINITE, "non-finite CG residual");
-      relres = std::sqrt(rr / bb);
-      if (relres <= rtol) break;
-      if (it >= maxit) {
-        result = COSIM_ERR_NOT_CONVERGED;
-        c->err = "CG reached maxit";
+      *relres = std::sqrt(rr / bb);
+      if (*relres <= rtol) {
+        *converged = true;
         break;
       }
+      if (it >= maxit) break;
     }
     cg_direction_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, c->cg, parity, Pv[0], Pv[1], Pv[2], Rv[0], Rv[1],
                                                               Rv[2], D[0], D[1], D[2]); ++c->launches;
     CHECK_LAUNCH(c);
+  }
+  *iters = it;
+  return COSIM_OK;
+}
+
+static cosim_status refine_alloc(cosim_ctx *c) {
+  if (c->refine_ready) return COSIM_OK;
+  for (int a = 0; a < 3; ++a) {
+    ALLOC(c, c->U64[a], c->npad * 8);
+    ALLOC(c, c->F64[a], c->npad * 8);
+    ALLOC(c, c->R64[a], c->npad * 8);
+  }
+  c->refine_ready = true;
+  return COSIM_OK;
+}
+
+template <typename R>
+static cosim_status stress_solve_t(cosim_ctx *c, const cosim_stress_opts *o, cosim_stress_report *rep) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const Geo<R> g = make_geo<R>(c);
+  const size_t smem = c->mats.size() * M_COLS * sizeof(R);
+  const dim3 blk(32, 8), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + 7) / 8, c->nz + 1);
+  R *const *U = (R *const *)c->U;
+  R *const *F = (R *const *)c->F;
+  R *const *D = (R *const *)c->Dinv;
+  const long long n = c->npad;
+  const R Tref = (R)(o->T_ref - c->T_init);  // device T is the rise over T_init
+  hex8_node_kernel<R, 0><<<grd, blk, smem, c->stream>>>(g, c->mask, nullptr, Tref, D[0], D[1], D[2]); ++c->launches;
+  CHECK_LAUNCH(c);
+  const double rtol = o->rtol > 0 ? o->rtol : 1e-9;
+  const int64_t maxit = o->maxit > 0 ? o->maxit : 200000;
+  const int every = o->check_every > 0 ? o->check_every : 32;
+  int64_t iters = 0, steps = 0;
+  double relres = 0;
+  bool converged = false;
+  cosim_status result = COSIM_OK;
+  if (!o->refine) {
+    hex8_node_kernel<R, 1><<<grd, blk, smem, c->stream>>>(g, c->mask, (const R *)c->T[c->tpar], Tref, F[0], F[1],
+                                                          F[2]); ++c->launches;
+    CHECK_LAUNCH(c);
+    cosim_status st = pcg_run<R>(c, rtol, maxit, every, &iters, &relres, &converged);
+    if (st != COSIM_OK) return st;
+  } else {
+    // FP64 outer loop: r = f - K u with the FP64 load, FP64 matvec and FP64 u;
+    // inner solves K d = r in the context precision; u += d.
+    cosim_status st = refine_alloc(c);
+    if (st != COSIM_OK) return st;
+    const Geo<double> g64 = make_geo64(c);
+    const size_t smem64 = c->mats.size() * M_COLS * sizeof(double);
+    double *T64 = (double *)c->scratch;  // temperature rise in FP64
+    const R *Tc = (const R *)c->T[c->tpar];
+    cast3_kernel<R, double><<<kRedBlocks, 256, 0, c->stream>>>(n, Tc, Tc, Tc, T64, T64, T64); ++c->launches;
+    hex8_node_kernel<double, 1><<<grd, blk, smem64, c->stream>>>(g64, c->mask, T64, o->T_ref - c->T_init, c->F64[0],
+                                                                 c->F64[1], c->F64[2]); ++c->launches;
+    CHECK_LAUNCH(c);
+    for (int a = 0; a < 3; ++a) CHECK_CUDA(c, cudaMemsetAsync(c->U64[a], 0, n * 8, c->stream));
+    const double inner = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
+    const int max_refine = o->max_refine > 0 ? o->max_refine : 30;
+    double ff = -1;
+    while (true) {
+      void *u64[3] = {c->U64[0], c->U64[1], c->U64[2]}, *r64[3] = {c->R64[0], c->R64[1], c->R64[2]};
+      if ((st = matvec_g<double>(c, g64, u64, r64, nullptr)) != COSIM_OK) return st;
+      residual64_kernel<<<kRedBlocks, 256, 0, c->stream>>>(n, c->F64[0], c->F64[1], c->F64[2], c->R64[0], c->R64[1],
+                                                            c->R64[2], c->part); ++c->launches;
+      reduce_final_kernel<<<1, 1024, 0, c->stream>>>(c->part, kRedBlocks, c->scal); ++c->launches;
+      CHECK_LAUNCH(c);
+      CHECK_CUDA(c, cudaMemcpyAsync(c->host_scal, c->scal, 8, cudaMemcpyDeviceToHost, c->stream));
+      CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+      const double rr = c->host_scal[0];
+      if (!std::isfinite(rr)) return fail(c, COSIM_ERR_NONFINITE, "non-finite refinement residual");
+      if (ff < 0) ff = rr;  // u = 0 on the first pass: r = f
+      relres = ff > 0 ? std::sqrt(rr / ff) : 0.0;
+      if (relres <= rtol) {
+        converged = true;
+        break;
+      }
+      if (steps >= max_refine) break;
+      cast3_kernel<double, R><<<kRedBlocks, 256, 0, c->stream>>>(n, c->R64[0], c->R64[1], c->R64[2], F[0], F[1],
+                                                                 F[2]); ++c->launches;
+      CHECK_LAUNCH(c);
+      int64_t it = 0;
+      double rel_in = 0;
+      bool conv_in = false;
+      if ((st = pcg_run<R>(c, inner, maxit, every, &it, &rel_in, &conv_in)) != COSIM_OK) return st;
+      iters += it;
+      ++steps;
+      add_correction_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, c->U64[0], c->U64[1], c->U64[2], U[0], U[1],
+                                                                  U[2]); ++c->launches;
+      CHECK_LAUNCH(c);
+    }
+    cast3_kernel<double, R><<<kRedBlocks, 256, 0, c->stream>>>(n, c->U64[0], c->U64[1], c->U64[2], U[0], U[1],
+                                                               U[2]); ++c->launches;
+    cast3_kernel<double, R><<<kRedBlocks, 256, 0, c->stream>>>(n, c->F64[0], c->F64[1], c->F64[2], F[0], F[1],
+                                                               F[2]); ++c->launches;
+    CHECK_LAUNCH(c);
+  }
+  if (!converged) {
+    result = COSIM_ERR_NOT_CONVERGED;
+    c->err = o->refine ? "refinement did not reach rtol" : "CG reached maxit";
   }
   const dim3 grc((c->nx + 31) / 32, (c->ny + 7) / 8, c->nz);
   von_mises_kernel<R><<<grc, blk, smem, c->stream>>>(g, U[0], U[1], U[2], (const R *)c->T[c->tpar], Tref, (R *)c->VM); ++c->launches;
@@ -781,9 +998,10 @@ static cosim_status stress_solve_t(cosim_ctx *c, const cosim_stress_opts *o, cos
   CHECK_LAUNCH(c);
   CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
   if (rep) {
-    rep->iters = it;
+    rep->iters = iters;
     rep->relres = relres;
     rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    rep->refine_steps = steps;
   }
   return result;
 }
@@ -907,6 +1125,10 @@ extern "C" cosim_status cosim_read_fields(cosim_ctx *c, int32_t field, int32_t d
   const size_t n = cells ? (size_t)c->nx * c->ny * c->nz : (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
   const size_t ob = dtype == COSIM_FP64 ? 8 : 4;
   if (!dst || bytes != n * ob) return fail(c, COSIM_ERR_INVALID, "dst size mismatch");
+  if (field == COSIM_F_Q) {
+    cosim_status fs = joule_flush(c);
+    if (fs != COSIM_OK) return fs;
+  }
   void *out = dst_is_device ? dst : c->scratch;
   const double add = field == COSIM_F_T ? c->T_init : 0.0;
   if (sdbl && dtype == COSIM_FP64) launch_pack<double, double>(c, src, out, cells, add);
@@ -936,6 +1158,10 @@ extern "C" cosim_status cosim_write_fields(cosim_ctx *c, int32_t field, int32_t 
   const size_t n = (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
   const size_t ib = dtype == COSIM_FP64 ? 8 : 4;
   if (!src || bytes != n * ib) return fail(c, COSIM_ERR_INVALID, "src size mismatch");
+  if (field == COSIM_F_Q) {  // the written values replace the whole accumulated energy
+    CHECK_CUDA(c, cudaMemsetAsync(c->Qs, 0, c->npad * c->rsz, c->stream));
+    c->qs_dirty = false;
+  }
   const void *in = src;
   if (!src_is_device) {
     CHECK_CUDA(c, cudaMemcpyAsync(c->scratch, src, bytes, cudaMemcpyHostToDevice, c->stream));

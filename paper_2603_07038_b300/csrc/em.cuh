@@ -16,8 +16,12 @@
 // node, i.e. (sum_c w_c sigma_c dt/2) * l_e * ebar^2 per end node, where w_c is
 // the quarter cross-section of voxel c around the edge. The node sums the six
 // halves of its incident edges (x from the thread at i-1, y from j-1 through
-// shared memory, z from its own previous plane) and adds them to its FP64
-// accumulator.
+// shared memory, z from its own previous plane) into a short-window
+// accumulator that is folded into the FP64 total every few steps (FP64 runs at
+// a small fraction of the FP32 rate on this GPU, so none is used per step).
+//
+// Inputs of plane k+2 are copied to shared memory with cp.async while plane k
+// is computed (three stages), so each CTA keeps two planes of loads in flight.
 //
 // Material averaging (per edge: area-weighted eps, sigma over the <=4 voxels;
 // per face: series mean of mu over the 2 voxels) is recomputed from the 1-byte
@@ -34,15 +38,22 @@ struct EmArgs {
   R *En[3];
   const R *Ho[3];
   R *Hn[3];
-  // CPML auxiliaries for derivative axis d, slot s (field component (d+1+s)%3).
-  // Always FP64: inside a layer psi tends to -dF for slowly varying fields, so
-  // dF + psi cancels and an FP32 psi would lose the residue.
-  const double *pEo[3][2];
-  double *pEn[3][2];
-  const double *pHo[3][2];
-  double *pHn[3][2];
+  // CPML state for derivative axis d, slot s (field component (d+1+s)%3).
+  // The CPML recursion psi^n = b psi^{n-1} + c dF^n with c = b - 1 (kappa = 1,
+  // alpha = 0) is carried in the equivalent form
+  //   chi^n = dF^n + psi^n = b (chi^{n-1} + dF^n - dF^{n-1}),
+  // storing chi and the previous derivative dF^{n-1}. Inside a layer psi tends
+  // to -dF for slowly varying fields, so dF + psi cancels and FP32 kept no bits
+  // of the residue; chi is that residue itself. Near the inner edge of a layer
+  // b is close to 1 and chi sums the derivative changes of thousands of steps,
+  // so in FP32 it is carried as an unevaluated pair chi = hi + lo (lEo..lHn,
+  // null in FP64 contexts) updated with error-free transformations.
+  const R *xEo[3][2], *dEo[3][2], *lEo[3][2];
+  R *xEn[3][2], *dEn[3][2], *lEn[3][2];
+  const R *xHo[3][2], *dHo[3][2], *lHo[3][2];
+  R *xHn[3][2], *dHn[3][2], *lHn[3][2];
   int slo[3], shi[3], sn[3];  // CPML cells at the low / high end, slab extent
-  const double *cpml;         // [axis][E,H][b,c][kMaxSlab]
+  const R *cpml;              // 1 - b per [axis][E,H][kMaxSlab] (computed as -expm1 on the host)
   int fixlo[3], fixhi[3];     // wall holds tangential E at zero (PEC or CPML backing)
   R dt;
   const int *src_row;         // per (k,j) row: first source entry, (nz+1)(ny+1)+1 ints
@@ -50,7 +61,14 @@ struct EmArgs {
   const R *src_amp;           // [source][amp_len]
   long long amp_len;
   long long step;
-  double *Q;                  // Joule energy per node (null: not accumulating)
+  // Joule energy: each step adds to the short-window accumulator Qs (context
+  // precision); on fold steps the owner moves Qs into the FP64 total Q instead,
+  // so FP64 arithmetic runs once per window rather than every step.
+  R *Qs;                      // null: not accumulating
+  double *Q;
+  int fold;
+  // tiles [ibx0, ibx1) x [iby0, iby1) lie off the lateral walls and CPML slabs
+  int ibx0, ibx1, iby0, iby1;
 };
 
 // index of position p (node or cell) of an axis inside its CPML slabs, or -1
@@ -67,49 +85,88 @@ __device__ __forceinline__ long long psi_index(const EmArgs<R> &A, int d, int s,
   return ((long long)s * (A.g.ny + 1) + j) * A.g.px + i;
 }
 
-// psi <- b psi + c dF in FP64, returns dF + psi_new (written only by the owner)
+// chi^n = b (chi^{n-1} + dF^n - dF^{n-1}), evaluated as t - (1-b) t; returns
+// chi^n = dF + psi (new values written only by the owner)
 template <typename R>
-__device__ __forceinline__ double psi_update(const EmArgs<R> &A, const double *s_cp, int d, int type, int slot,
-                                             int s, int i, int j, int k, R deriv, bool write) {
+__device__ __forceinline__ R chi_update(const EmArgs<R> &A, const R *s_cp, int d, int type, int slot, int s, int i,
+                                        int j, int k, R deriv, bool write) {
   const long long q = psi_index(A, d, s, i, j, k);
-  const double b = s_cp[((d * 2 + type) * 2 + 0) * kMaxSlab + s];
-  const double c = s_cp[((d * 2 + type) * 2 + 1) * kMaxSlab + s];
-  const double *po = type == 0 ? A.pEo[d][slot] : A.pHo[d][slot];
-  const double v = b * po[q] + c * (double)deriv;
-  if (write) (type == 0 ? A.pEn[d][slot] : A.pHn[d][slot])[q] = v;
-  return (double)deriv + v;
+  const R omb = s_cp[(d * 2 + type) * kMaxSlab + s];
+  const R *xo = type == 0 ? A.xEo[d][slot] : A.xHo[d][slot];
+  const R *dd = type == 0 ? A.dEo[d][slot] : A.dHo[d][slot];
+  if constexpr (sizeof(R) == 8) {
+    const R t = xo[q] + (deriv - dd[q]);
+    const R chi = t - omb * t;
+    if (write) {
+      (type == 0 ? A.xEn[d][slot] : A.xHn[d][slot])[q] = chi;
+      (type == 0 ? A.dEn[d][slot] : A.dHn[d][slot])[q] = deriv;
+    }
+    return chi;
+  } else {
+    // (hi + lo + D)(1 - omb) with Knuth's TwoSum for the additions, an FMA
+    // product error for omb * hi, and a final renormalisation (Fast2Sum).
+    const R hi = xo[q];
+    const R lo = (type == 0 ? A.lEo[d][slot] : A.lHo[d][slot])[q];
+    const R D = deriv - dd[q];
+    const R sh = hi + D;
+    const R bv = sh - hi;
+    const R e1 = (hi - (sh - bv)) + (D - bv);
+    const R l1 = lo + e1;
+    const R p = __fmul_rn(omb, sh);
+    const R pe = __fmaf_rn(omb, sh, -p);
+    const R s2 = sh - p;
+    const R bv2 = s2 - sh;
+    const R e2 = (sh - (s2 - bv2)) + (-p - bv2);
+    const R l2 = (l1 + e2) - pe - __fmul_rn(omb, l1);
+    const R h3 = s2 + l2;
+    const R l3 = l2 - (h3 - s2);
+    if (write) {
+      (type == 0 ? A.xEn[d][slot] : A.xHn[d][slot])[q] = h3;
+      (type == 0 ? A.lEn[d][slot] : A.lHn[d][slot])[q] = l3;
+      (type == 0 ? A.dEn[d][slot] : A.dHn[d][slot])[q] = deriv;
+    }
+    return h3;
+  }
 }
 
 // (dF1 + psi1) - (dF2 + psi2) for the two derivatives of one curl component;
-// FP64 only where a CPML slab is present (s1/s2 >= 0).
+// the CPML state is touched only inside a slab (s1/s2 >= 0).
 template <typename R>
-__device__ __forceinline__ R curl_with_psi(const EmArgs<R> &A, const double *s_cp, int type, int comp, int d1,
-                                           int s1, int d2, int s2, int i, int j, int k, R v1, R v2, bool write) {
+__device__ __forceinline__ R curl_with_psi(const EmArgs<R> &A, const R *s_cp, int type, int comp, int d1, int s1,
+                                           int d2, int s2, int i, int j, int k, R v1, R v2, bool write) {
   (void)comp;
   if (s1 < 0 && s2 < 0) return v1 - v2;
-  const double a = s1 >= 0 ? psi_update(A, s_cp, d1, type, 1, s1, i, j, k, v1, write) : (double)v1;
-  const double b = s2 >= 0 ? psi_update(A, s_cp, d2, type, 0, s2, i, j, k, v2, write) : (double)v2;
-  return (R)(a - b);
+  const R a = s1 >= 0 ? chi_update(A, s_cp, d1, type, 1, s1, i, j, k, v1, write) : v1;
+  const R b = s2 >= 0 ? chi_update(A, s_cp, d2, type, 0, s2, i, j, k, v2, write) : v2;
+  return a - b;
 }
 
-// E^{n+1} of one edge from the four voxels (m0..m3 with area weights w0..w3,
-// quarter factor folded in), W = dual-face area, l = edge length:
-//   E' = ca E + cb (curl - J),  ca = (Se - Ss)/(Se + Ss),  cb = dt W/(Se + Ss)
-// (Se = sum w eps, Ss = sum w sigma dt/2), evaluated in the equivalent
-// incremental form E' = E + r (dt W (curl - J) - 2 Ss E), r = 1/(Se + Ss),
-// which keeps the decay 1 - ca of weakly lossy media at full precision.
-// Returns E^{n+1}; *half_q receives the edge's Joule energy share per end node.
+// Reciprocal of a positive normal number: in FP32 the hardware approximation
+// refined by one Newton-Raphson step (r' = r + r (1 - x r)), within about an
+// ulp of 1/x; in FP64 the exact division.
+__device__ __forceinline__ float em_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return __fmaf_rn(r, __fmaf_rn(-x, r, 1.0f), r);
+}
+__device__ __forceinline__ double em_rcp(double x) { return 1.0 / x; }
+
+// E^{n+1} of one edge from the area-weighted sums over its <= 4 voxels, all
+// taken without the quarter factor of the voxel cross-sections (it cancels):
+//   Se = sum w eps, Ss = sum w sigma dt/2 (w = product of the two transverse
+//   cell sizes of the voxel), dtW = dt x (sum of those products) = 4 dt x the
+//   dual-face area, lq = edge length / 4.
+// The update E' = ca E + cb (curl - J) (ca = (Se - Ss)/(Se + Ss),
+// cb = dt W/(Se + Ss)) is evaluated in the equivalent incremental form
+// E' = E + r (dtW (curl - J) - 2 Ss E), r = 1/(Se + Ss), which keeps the decay
+// 1 - ca of weakly lossy media at full precision. *half_q receives the edge's
+// Joule energy per end node, (Ss/4) l ebar^2 with ebar = (E + E')/2.
 template <typename R>
-__device__ __forceinline__ R edge_update(const R *s_mt, int m0, R w0, int m1, R w1, int m2, R w2, int m3, R w3,
-                                         R W, R l, R dt, R e_old, R curl, R J, R *half_q) {
-  const R Se = w0 * mconst(s_mt, m0, M_EPS) + w1 * mconst(s_mt, m1, M_EPS) + w2 * mconst(s_mt, m2, M_EPS) +
-               w3 * mconst(s_mt, m3, M_EPS);
-  const R Ss = w0 * mconst(s_mt, m0, M_SDT2) + w1 * mconst(s_mt, m1, M_SDT2) + w2 * mconst(s_mt, m2, M_SDT2) +
-               w3 * mconst(s_mt, m3, M_SDT2);
-  const R r = R(1) / (Se + Ss);
-  const R e_new = e_old + r * (dt * W * (curl - J) - R(2) * Ss * e_old);
+__device__ __forceinline__ R e_update(R e_old, R dtW, R drive, R Se, R Ss, R lq, R *half_q) {
+  const R r = em_rcp(Se + Ss);
+  const R e_new = e_old + r * (dtW * drive - R(2) * Ss * e_old);
   const R eb = R(0.5) * (e_old + e_new);
-  *half_q = Ss * l * eb * eb;
+  *half_q = Ss * lq * eb * eb;
   return e_new;
 }
 
@@ -119,105 +176,161 @@ template <typename R, int TX, int TY>
 struct EmStage {
   R E[3][TY + 1][TX + 1];
   R H[3][TY][TX];
-  double Q[TY][TX];
+  R Qs[TY][TX];
 };
 
+constexpr int kCpmlTable = 6 * kMaxSlab;  // (1 - b) per [axis][E,H][slab position]
+
+// Shared-memory offset of the stages: the CPML table, then nmat + 1 material
+// rows (row nmat is all zero and stands for voxels outside the grid).
 template <typename R, int TX, int TY>
 __host__ __device__ constexpr size_t em_stage_offset(int nmat) {
-  return (12 * kMaxSlab * sizeof(double) + (size_t)nmat * M_COLS * sizeof(R) + 15) & ~size_t(15);
+  return ((kCpmlTable + (size_t)(nmat + 1) * M_COLS) * sizeof(R) + 15) & ~size_t(15);
 }
 
-constexpr int kEmStages = 3;  // planes k (in use), k+1 (ready), k+2 (in flight)
+constexpr int kEmStages = 4;  // planes k, k+1 (in use), k+2, k+3 (in flight)
 
-template <typename R, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) em_step_kernel(const EmArgs<R> A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double *s_cp = reinterpret_cast<double *>(smem_raw);
-  R *s_mt = reinterpret_cast<R *>(s_cp + 12 * kMaxSlab);
+// Body of the fused step for one CTA tile. BORDER = false is the interior
+// specialisation: every node of the tile and its +x/+y neighbours lies inside
+// the grid, off the lateral walls and outside the x/y CPML slabs, so the
+// bounds, wall and lateral-CPML tests fold away at compile time (only the
+// z-direction slab and walls remain, decided per plane for the whole CTA).
+// I: index type of node offsets (int when the padded node arrays have fewer
+// than 2^31 elements, long long otherwise).
+template <typename R, typename I, int TX, int TY, bool BORDER>
+__device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
+                                        EmStage<R, TX, TY> *stg, R (*sHxz)[TY][TX], R (*sQy)[TX]) {
   const Geo<R> &g = A.g;
-  EmStage<R, TX, TY> *stg = reinterpret_cast<EmStage<R, TX, TY> *>(smem_raw + em_stage_offset<R, TX, TY>(g.nmat));
-  __shared__ R sH[3][TY][TX];
-  __shared__ R sP[2][TY][TX];
-  stage_table(s_mt, g.mtab, g.nmat * M_COLS);
-  stage_table(s_cp, A.cpml, 12 * kMaxSlab);
-
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int tx = threadIdx.x, ty = threadIdx.y;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int vd = g.nmat * M_COLS;  // row offset of the all-zero material
   const int i0 = blockIdx.x * (TX - 1) - 1, j0 = blockIdx.y * (TY - 1) - 1;  // node of thread (0, 0)
   const int i = i0 + tx, j = j0 + ty;
-  const bool act = (i >= 0 && i <= nx && j >= 0 && j <= ny);
+  const bool act = !BORDER || (i >= 0 && i <= nx && j >= 0 && j <= ny);
   const bool own = act && tx > 0 && ty > 0;
-  const bool need_ex = act && ty > 0 && i < nx;  // own, or the halo column
-  const bool need_ey = act && tx > 0 && j < ny;  // own, or the halo row
-  const bool need_ez = own;
+  const bool need_ex = act && ty > 0 && (!BORDER || i < nx);  // own, or the halo column
+  const bool need_ey = act && tx > 0 && (!BORDER || j < ny);  // own, or the halo row
+  const bool in_x = !BORDER || i < nx, in_y = !BORDER || j < ny;
+  const bool accum = A.Qs != nullptr;
 
-  // Plane k of E^n (tile + neighbours), H^{n-1/2} and Q (owned nodes) -> stage s.
-  // Positions outside the grid are zero-filled without a read.
+  // Plane k of E^n (tile + neighbours), H^{n-1/2} and Qs (owned nodes) -> stage s.
+  // Each thread copies its own node; the last column / row / corner threads
+  // also copy the +x / +y / +xy neighbour. Positions outside the grid are
+  // zero-filled without a read.
+  const bool xc = tx == TX - 1, yr = ty == TY - 1;
+  const bool ok_xc = xc && (!BORDER || (i + 1 <= nx && j >= 0 && j <= ny));
+  const bool ok_yr = yr && (!BORDER || (i >= 0 && i <= nx && j + 1 <= ny));
+  const bool ok_cr = xc && yr && (!BORDER || (i + 1 <= nx && j + 1 <= ny));
+  const I plane = (I)g.plane;
+  const I o_own = act ? (I)g.nid(i, j, 0) : I(0);
+  const I o_xc = ok_xc ? (I)g.nid(i + 1, j, 0) : I(0);
+  const I o_yr = ok_yr ? (I)g.nid(i, j + 1, 0) : I(0);
+  const I o_cr = ok_cr ? (I)g.nid(i + 1, j + 1, 0) : I(0);
   auto load_stage = [&](int k, int s) {
     EmStage<R, TX, TY> &S = stg[s];
     const bool kin = k <= nz;
-    constexpr int NE = (TY + 1) * (TX + 1);
-    for (int q = tid; q < 3 * NE; q += TX * TY) {
-      const int c = q / NE, r = q - c * NE;
-      const int yy = r / (TX + 1), xx = r - yy * (TX + 1);
-      const int ii = i0 + xx, jj = j0 + yy;
-      const bool ok = kin && ii >= 0 && ii <= nx && jj >= 0 && jj <= ny;
-      cp_async<sizeof(R)>(&S.E[c][yy][xx], ok ? A.Eo[c] + g.nid(ii, jj, k) : A.Eo[c], ok);
-    }
-    const bool okh = kin && act;
-    const long long idk = okh ? g.nid(i, j, k) : 0;
+    const I kp = kin ? (I)k * plane : I(0);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) cp_async<sizeof(R)>(&S.H[c][ty][tx], A.Ho[c] + idk, okh);
-    if (A.Q != nullptr) cp_async<8>(&S.Q[ty][tx], A.Q + (kin && own ? idk : 0), kin && own);
+    for (int c = 0; c < 3; ++c) {
+      cp_async<sizeof(R)>(&S.E[c][ty][tx], A.Eo[c] + (o_own + kp), kin && act);
+      cp_async<sizeof(R)>(&S.H[c][ty][tx], A.Ho[c] + (o_own + kp), kin && act);
+    }
+    if (xc) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) cp_async<sizeof(R)>(&S.E[c][ty][TX], A.Eo[c] + (o_xc + kp), kin && ok_xc);
+    }
+    if (yr) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) cp_async<sizeof(R)>(&S.E[c][TY][tx], A.Eo[c] + (o_yr + kp), kin && ok_yr);
+    }
+    if (xc && yr) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) cp_async<sizeof(R)>(&S.E[c][TY][TX], A.Eo[c] + (o_cr + kp), kin && ok_cr);
+    }
+    if (accum) cp_async<sizeof(R)>(&S.Qs[ty][tx], A.Qs + (o_own + kp), kin && own);
     cp_async_commit();
   };
+  // Material rows (id x M_COLS) of voxels (i-1+dx, j-1+dy, k); the zero row
+  // outside the grid.
+  const bool cx0 = !BORDER || (i - 1 >= 0 && i - 1 < nx), cx1 = !BORDER || (i >= 0 && i < nx);
+  const bool cy0 = !BORDER || (j - 1 >= 0 && j - 1 < ny), cy1 = !BORDER || (j >= 0 && j < ny);
+  const I co = (I)(j - 1) * nx + (i - 1);  // voxel (i-1, j-1) of layer 0
+  const I cplane = (I)nx * ny;
+  auto voxels = [&](int k, int &m00, int &m01, int &m10, int &m11) {
+    const bool kz = k < nz;  // k >= 0 always
+    const uint8_t *b = g.mat + (co + (kz ? (I)k * cplane : I(0)));
+    m00 = (kz && cx0 && cy0) ? (int)__ldg(b) * M_COLS : vd;
+    m01 = (kz && cx1 && cy0) ? (int)__ldg(b + 1) * M_COLS : vd;
+    m10 = (kz && cx0 && cy1) ? (int)__ldg(b + nx) * M_COLS : vd;
+    m11 = (kz && cx1 && cy1) ? (int)__ldg(b + nx + 1) * M_COLS : vd;
+  };
 
-  const R hxm = (act && i > 0) ? g.h[0][i - 1] : R(0), hx0 = (act && i < nx) ? g.h[0][i] : R(0);
-  const R hym = (act && j > 0) ? g.h[1][j - 1] : R(0), hy0 = (act && j < ny) ? g.h[1][j] : R(0);
-  const R ihx = (act && i < nx) ? g.ih[0][i] : R(0), ihy = (act && j < ny) ? g.ih[1][j] : R(0);
+  const R hxm = (act && (!BORDER || i > 0)) ? g.h[0][i - 1] : R(0), hx0 = (act && in_x) ? g.h[0][i] : R(0);
+  const R hym = (act && (!BORDER || j > 0)) ? g.h[1][j - 1] : R(0), hy0 = (act && in_y) ? g.h[1][j] : R(0);
+  const R ihx = (act && in_x) ? g.ih[0][i] : R(0), ihy = (act && in_y) ? g.ih[1][j] : R(0);
   const R idx = act ? g.idual[0][i] : R(0), idy = act ? g.idual[1][j] : R(0);
-  const bool fix_x = (i == 0 && A.fixlo[0]) || (i == nx && A.fixhi[0]);
-  const bool fix_y = (j == 0 && A.fixlo[1]) || (j == ny && A.fixhi[1]);
-  // CPML slab positions along x and y (E: nodes, H: cells)
-  const int sxE = slab_index(i, nx, A.slo[0], A.shi[0]);
-  const int syE = slab_index(j, ny, A.slo[1], A.shi[1]);
-  const int sxH = (i < nx) ? sxE : -1;
-  const int syH = (j < ny) ? syE : -1;
+  const bool fix_x = BORDER && ((i == 0 && A.fixlo[0]) || (i == nx && A.fixhi[0]));
+  const bool fix_y = BORDER && ((j == 0 && A.fixlo[1]) || (j == ny && A.fixhi[1]));
+  // CPML slab positions along x and y (E: nodes, H: cells); none inside
+  const int sxE = BORDER ? slab_index(i, nx, A.slo[0], A.shi[0]) : -1;
+  const int syE = BORDER ? slab_index(j, ny, A.slo[1], A.shi[1]) : -1;
+  const int sxH = in_x ? sxE : -1;
+  const int syH = in_y ? syE : -1;
   const R dt = A.dt;
   const R half_dt = R(0.5) * dt;
-  const long long plane = g.plane;
-  const long long id0 = act ? g.nid(i, j, 0) : 0;
+  // per-thread geometry of the face and edge coefficients
+  const R hdx = half_dt * idx, hdy = half_dt * idy;
+  const R dtWx_y = dt * (hym + hy0), dtWy_x = dt * (hxm + hx0);
+  const R lqx = R(0.25) * hx0, lqy = R(0.25) * hy0;
+  const I id0 = o_own;
 
   load_stage(0, 0);
   load_stage(1, 1);
-  // voxels (i-1+dx, j-1+dy) of the layer below (b..) and above (a..) the node plane
-  int b00 = -1, b01 = -1, b10 = -1, b11 = -1;
-  int a00 = g.cell(i - 1, j - 1, 0), a01 = g.cell(i, j - 1, 0), a10 = g.cell(i - 1, j, 0), a11 = g.cell(i, j, 0);
+  load_stage(2, 2);
+  int a00, a01, a10, a11;  // material rows of voxel layer k (the layer above node plane k)
+  voxels(0, a00, a01, a10, a11);
   int r0 = 0, r1 = 0;  // source entries of row (k, j)
   if (A.src_row != nullptr && act) {
     r0 = __ldg(A.src_row + j);
     r1 = __ldg(A.src_row + j + 1);
   }
   R hx_km1 = 0, hy_km1 = 0, qz_km1 = 0;
+  // layer k-1 partial sums of the x / y edges and 1/mu of voxel (i, j, k-1);
+  // zero below the grid
+  R pxe_b = 0, pxs_b = 0, pye_b = 0, pys_b = 0, u11_b = 0;
+  R q_pend = 0;  // Joule sum of node (i, j, k-1) still missing the y-edge share from j-1
+  // z spacing of the current plane, loaded one plane ahead
+  R hz0 = nz > 0 ? g.h[2][0] : R(0), ihz = nz > 0 ? g.ih[2][0] : R(0), idz = g.idual[2][0], hzm = 0;
 
   for (int k = 0; k <= nz; ++k) {
-    load_stage(k + 2, (k + 2) % kEmStages);
-    // next layer's voxels and source row, consumed in the next iteration
-    const int n00 = g.cell(i - 1, j - 1, k + 1), n01 = g.cell(i, j - 1, k + 1);
-    const int n10 = g.cell(i - 1, j, k + 1), n11 = g.cell(i, j, k + 1);
+    load_stage(k + 3, (k + 3) & (kEmStages - 1));
+    // next plane's voxels, source row and z spacing, consumed in the next iteration
+    int n00, n01, n10, n11;
+    voxels(k + 1, n00, n01, n10, n11);
     int nr0 = 0, nr1 = 0;
     if (A.src_row != nullptr && act && k < nz) {
       const int row = (k + 1) * (ny + 1) + j;
       nr0 = __ldg(A.src_row + row);
       nr1 = __ldg(A.src_row + row + 1);
     }
-    cp_async_wait<1>();  // planes k and k+1 have landed
+    const R hz0_n = (k + 1 < nz) ? g.h[2][k + 1] : R(0), ihz_n = (k + 1 < nz) ? g.ih[2][k + 1] : R(0);
+    const R idz_n = (k < nz) ? g.idual[2][k + 1] : R(0);
+    cp_async_wait<2>();  // planes k and k+1 have landed
     __syncthreads();
-    const EmStage<R, TX, TY> &S0 = stg[k % kEmStages];
-    const EmStage<R, TX, TY> &S1 = stg[(k + 1) % kEmStages];
-    const long long id = id0 + (long long)k * plane;
-    const R hzm = (k > 0) ? g.h[2][k - 1] : R(0), hz0 = (k < nz) ? g.h[2][k] : R(0);
-    const R ihz = (k < nz) ? g.ih[2][k] : R(0), idz = g.idual[2][k];
+    const I id = id0 + (I)k * plane;
+    // Joule energy of node (i, j, k-1): its y-edge share from j-1 is now visible
+    if (accum && own && k > 0) {
+      const R s = q_pend + sQy[ty - 1][tx];
+      if (A.fold) {
+        A.Q[id - plane] += (double)s;
+        A.Qs[id - plane] = R(0);
+      } else {
+        A.Qs[id - plane] = s;
+      }
+    }
+    const EmStage<R, TX, TY> &S0 = stg[k & (kEmStages - 1)];
+    const EmStage<R, TX, TY> &S1 = stg[(k + 1) & (kEmStages - 1)];
+    const R hdz = half_dt * idz;
     const bool fix_z = (k == 0 && A.fixlo[2]) || (k == nz && A.fixhi[2]);
     const int szE = slab_index(k, nz, A.slo[2], A.shi[2]);
     const int szH = (k < nz) ? szE : -1;
@@ -226,71 +339,83 @@ __global__ void __launch_bounds__(TX *TY) em_step_kernel(const EmArgs<R> A) {
     const R ex_up = S1.E[0][ty][tx], ey_up = S1.E[1][ty][tx];
     const R ez_jp = S0.E[2][ty + 1][tx], ex_jp = S0.E[0][ty + 1][tx];
     const R ez_ip = S0.E[2][ty][tx + 1], ey_ip = S0.E[1][ty][tx + 1];
-    const double q_old = (A.Q != nullptr) ? S0.Q[ty][tx] : 0.0;
+    const R hx_o = S0.H[0][ty][tx], hy_o = S0.H[1][ty][tx], hz_o = S0.H[2][ty][tx];
+    const R q_old = accum ? S0.Qs[ty][tx] : R(0);
 
-    // ---- H^{n+1/2} at (i,j,k): H -= dt/mu (curl E + psi terms)
+    // material constants of voxel layer k
+    const R e00 = s_mt[a00 + M_EPS], e01 = s_mt[a01 + M_EPS], e10 = s_mt[a10 + M_EPS], e11 = s_mt[a11 + M_EPS];
+    const R s00 = s_mt[a00 + M_SDT2], s01 = s_mt[a01 + M_SDT2], s10 = s_mt[a10 + M_SDT2], s11 = s_mt[a11 + M_SDT2];
+    const R u01 = s_mt[a01 + M_IMU], u10 = s_mt[a10 + M_IMU], u11 = s_mt[a11 + M_IMU];
+
+    // ---- H^{n+1/2} at (i,j,k): H -= dt/mu (curl E + psi terms); dt/mu of a
+    // face is the series mean over the two voxels its dual edge crosses
     R Hx = 0, Hy = 0, Hz = 0;
     if (act) {
-      if (j < ny && k < nz) {  // Hx: (curl E)_x = dEz/dy - dEy/dz
+      if (in_y && k < nz) {  // Hx: (curl E)_x = dEz/dy - dEy/dz, voxels (i-1..i, j, k)
         const R d1 = (ez_jp - ez) * ihy, d2 = (ey_up - ey) * ihz;
         const R curl = curl_with_psi(A, s_cp, 1, 0, 1, syH, 2, szH, i, j, k, d1, d2, own);
-        const R coef = half_dt * idx * (hxm * mconst(s_mt, a10, M_IMU) + hx0 * mconst(s_mt, a11, M_IMU));
-        Hx = S0.H[0][ty][tx] - coef * curl;
+        Hx = hx_o - hdx * (hxm * u10 + hx0 * u11) * curl;
       }
-      if (i < nx && k < nz) {  // Hy: dEx/dz - dEz/dx
+      if (in_x && k < nz) {  // Hy: dEx/dz - dEz/dx, voxels (i, j-1..j, k)
         const R d1 = (ex_up - ex) * ihz, d2 = (ez_ip - ez) * ihx;
         const R curl = curl_with_psi(A, s_cp, 1, 1, 2, szH, 0, sxH, i, j, k, d1, d2, own);
-        const R coef = half_dt * idy * (hym * mconst(s_mt, a01, M_IMU) + hy0 * mconst(s_mt, a11, M_IMU));
-        Hy = S0.H[1][ty][tx] - coef * curl;
+        Hy = hy_o - hdy * (hym * u01 + hy0 * u11) * curl;
       }
-      if (i < nx && j < ny) {  // Hz: dEy/dx - dEx/dy
+      if (in_x && in_y) {  // Hz: dEy/dx - dEx/dy, voxels (i, j, k-1..k)
         const R d1 = (ey_ip - ey) * ihx, d2 = (ex_jp - ex) * ihy;
         const R curl = curl_with_psi(A, s_cp, 1, 2, 0, sxH, 1, syH, i, j, k, d1, d2, own);
-        const R coef = half_dt * idz * (hzm * mconst(s_mt, b11, M_IMU) + hz0 * mconst(s_mt, a11, M_IMU));
-        Hz = S0.H[2][ty][tx] - coef * curl;
+        Hz = hz_o - hdz * (hzm * u11_b + hz0 * u11) * curl;
       }
     }
-    sH[0][ty][tx] = Hx;
-    sH[1][ty][tx] = Hy;
-    sH[2][ty][tx] = Hz;
+    sHxz[0][ty][tx] = Hx;
+    sHxz[1][ty][tx] = Hz;
+    const R hy_l = __shfl_up_sync(0xffffffffu, Hy, 1);  // H of node i-1 (same warp)
+    const R hz_l = __shfl_up_sync(0xffffffffu, Hz, 1);
     __syncthreads();
 
-    // ---- source current on this node's edges
-    R J[3] = {0, 0, 0};
+    // ---- source current on this node's edges (three scalars selected by
+    // axis: a dynamically indexed array would live in local memory)
+    R Jx = 0, Jy = 0, Jz = 0;
     for (int e = r0; e < r1; ++e) {
       const int4 s = A.src_ent[e];
-      if (s.x == i && A.step < A.amp_len) J[s.y] += A.src_amp[(long long)s.z * A.amp_len + A.step];
+      if (s.x == i && A.step < A.amp_len) {
+        const R a = A.src_amp[(long long)s.z * A.amp_len + A.step];
+        Jx += s.y == 0 ? a : R(0);
+        Jy += s.y == 1 ? a : R(0);
+        Jz += s.y == 2 ? a : R(0);
+      }
     }
 
-    // ---- E^{n+1} on the node's edges and their Joule shares
+    // ---- E^{n+1} on the node's edges and their Joule shares. Layer-k partial
+    // sums of the x / y edges (voxel pairs across y / x); the layer k-1 halves
+    // were formed one plane earlier.
+    const R pxe_a = hym * e01 + hy0 * e11, pxs_a = hym * s01 + hy0 * s11;
+    const R pye_a = hxm * e10 + hx0 * e11, pys_a = hxm * s10 + hx0 * s11;
     R exn = ex, eyn = ey, ezn = ez, qx = 0, qy = 0, qz = 0;
     if (need_ex && !(fix_y || fix_z)) {  // Ex: dHz/dy - dHy/dz, voxels (i, j-1..j, k-1..k)
-      const R d1 = (sH[2][ty][tx] - sH[2][ty - 1][tx]) * idy;
-      const R d2 = (sH[1][ty][tx] - hy_km1) * idz;
+      const R d1 = (Hz - sHxz[1][ty - 1][tx]) * idy;
+      const R d2 = (Hy - hy_km1) * idz;
       const R curl = curl_with_psi(A, s_cp, 0, 0, 1, syE, 2, szE, i, j, k, d1, d2, own);
-      const R q = R(0.25);
-      exn = edge_update(s_mt, b01, q * hym * hzm, b11, q * hy0 * hzm, a01, q * hym * hz0, a11, q * hy0 * hz0,
-                        q * (hym + hy0) * (hzm + hz0), hx0, dt, ex, curl, J[0], &qx);
+      exn = e_update(ex, dtWx_y * (hzm + hz0), curl - Jx, hzm * pxe_b + hz0 * pxe_a, hzm * pxs_b + hz0 * pxs_a, lqx,
+                     &qx);
     }
     if (need_ey && !(fix_x || fix_z)) {  // Ey: dHx/dz - dHz/dx, voxels (i-1..i, j, k-1..k)
-      const R d1 = (sH[0][ty][tx] - hx_km1) * idz;
-      const R d2 = (sH[2][ty][tx] - sH[2][ty][tx - 1]) * idx;
+      const R d1 = (Hx - hx_km1) * idz;
+      const R d2 = (Hz - hz_l) * idx;
       const R curl = curl_with_psi(A, s_cp, 0, 1, 2, szE, 0, sxE, i, j, k, d1, d2, own);
-      const R q = R(0.25);
-      eyn = edge_update(s_mt, b10, q * hxm * hzm, b11, q * hx0 * hzm, a10, q * hxm * hz0, a11, q * hx0 * hz0,
-                        q * (hxm + hx0) * (hzm + hz0), hy0, dt, ey, curl, J[1], &qy);
+      eyn = e_update(ey, dtWy_x * (hzm + hz0), curl - Jy, hzm * pye_b + hz0 * pye_a, hzm * pys_b + hz0 * pys_a, lqy,
+                     &qy);
     }
-    if (need_ez && k < nz && !(fix_x || fix_y)) {  // Ez: dHy/dx - dHx/dy, voxels (i-1..i, j-1..j, k)
-      const R d1 = (sH[1][ty][tx] - sH[1][ty][tx - 1]) * idx;
-      const R d2 = (sH[0][ty][tx] - sH[0][ty - 1][tx]) * idy;
+    if (own && k < nz && !(fix_x || fix_y)) {  // Ez: dHy/dx - dHx/dy, voxels (i-1..i, j-1..j, k)
+      const R d1 = (Hy - hy_l) * idx;
+      const R d2 = (Hx - sHxz[0][ty - 1][tx]) * idy;
       const R curl = curl_with_psi(A, s_cp, 0, 2, 0, sxE, 1, syE, i, j, k, d1, d2, own);
-      const R q = R(0.25);
-      ezn = edge_update(s_mt, a00, q * hxm * hym, a01, q * hx0 * hym, a10, q * hxm * hy0, a11, q * hx0 * hy0,
-                        q * (hxm + hx0) * (hym + hy0), hz0, dt, ez, curl, J[2], &qz);
+      const R Se = hym * (hxm * e00 + hx0 * e01) + hy0 * (hxm * e10 + hx0 * e11);
+      const R Ss = hym * (hxm * s00 + hx0 * s01) + hy0 * (hxm * s10 + hx0 * s11);
+      ezn = e_update(ez, dtWx_y * (hxm + hx0), curl - Jz, Se, Ss, R(0.25) * hz0, &qz);
     }
-    sP[0][ty][tx] = qx;
-    sP[1][ty][tx] = qy;
-    __syncthreads();
+    const R qx_l = __shfl_up_sync(0xffffffffu, qx, 1);  // x-edge share from node i-1
+    sQy[ty][tx] = qy;
 
     if (own) {
       A.Hn[0][id] = Hx;
@@ -299,26 +424,61 @@ __global__ void __launch_bounds__(TX *TY) em_step_kernel(const EmArgs<R> A) {
       A.En[0][id] = exn;
       A.En[1][id] = eyn;
       if (k < nz) A.En[2][id] = ezn;
-      if (A.Q != nullptr) {
-        const R s = (qx + sP[0][ty][tx - 1]) + (qy + sP[1][ty - 1][tx]) + (qz + qz_km1);
-        A.Q[id] = q_old + (double)s;
-      }
     }
+    q_pend = q_old + ((qx + qx_l) + qy + (qz + qz_km1));
     hx_km1 = Hx;
     hy_km1 = Hy;
     qz_km1 = qz;
-    b00 = a00;
-    b01 = a01;
-    b10 = a10;
-    b11 = a11;
+    pxe_b = pxe_a;
+    pxs_b = pxs_a;
+    pye_b = pye_a;
+    pys_b = pys_a;
+    u11_b = u11;
     a00 = n00;
     a01 = n01;
     a10 = n10;
     a11 = n11;
     r0 = nr0;
     r1 = nr1;
+    hzm = hz0;
+    hz0 = hz0_n;
+    ihz = ihz_n;
+    idz = idz_n;
+  }
+  __syncthreads();
+  if (accum && own) {  // Joule energy of the top plane k = nz
+    const I id = id0 + (I)nz * plane;
+    const R s = q_pend + sQy[ty - 1][tx];
+    if (A.fold) {
+      A.Q[id] += (double)s;
+      A.Qs[id] = R(0);
+    } else {
+      A.Qs[id] = s;
+    }
   }
   cp_async_wait<0>();
+}
+
+// One launch per step over all tiles; tiles in [ibx0, ibx1) x [iby0, iby1)
+// take the interior specialisation.
+template <typename R, typename I, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? 3 : 2) em_step_kernel(const EmArgs<R> A) {
+  static_assert(TX == 32, "a tile row is one warp: x neighbours are exchanged by shuffles");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *s_cp = reinterpret_cast<R *>(smem_raw);
+  R *s_mt = s_cp + kCpmlTable;
+  EmStage<R, TX, TY> *stg =
+      reinterpret_cast<EmStage<R, TX, TY> *>(smem_raw + em_stage_offset<R, TX, TY>(A.g.nmat));
+  __shared__ R sHxz[2][TY][TX];  // Hx, Hz of the plane, read by the +y neighbour
+  __shared__ R sQy[TY][TX];      // Joule share of the y-edge, read by the +y neighbour one plane later
+  stage_table(s_mt, A.g.mtab, (A.g.nmat + 1) * M_COLS);
+  stage_table(s_cp, A.cpml, kCpmlTable);
+  const bool interior = (int)blockIdx.x >= A.ibx0 && (int)blockIdx.x < A.ibx1 && (int)blockIdx.y >= A.iby0 &&
+                        (int)blockIdx.y < A.iby1;
+  if (interior)
+    em_tile<R, I, TX, TY, false>(A, s_cp, s_mt, stg, sHxz, sQy);
+  else
+    em_tile<R, I, TX, TY, true>(A, s_cp, s_mt, stg, sHxz, sQy);
 }
 
 }  // namespace cosim

@@ -482,6 +482,46 @@ __global__ void __launch_bounds__(256) min_final_kernel(const double *part, int 
   if (threadIdx.x == 0) *out = s_min[0];
 }
 
+// ---- mixed-precision iterative refinement (FP64 outer residual, context-precision CG)
+
+// d_c = (D) s_c for three SoA arrays
+template <typename S, typename D>
+__global__ void __launch_bounds__(256) cast3_kernel(long long n, const S *s0, const S *s1, const S *s2, D *d0, D *d1,
+                                                     D *d2) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    d0[q] = (D)s0[q];
+    d1[q] = (D)s1[q];
+    d2[q] = (D)s2[q];
+  }
+}
+
+// r = f - Ku in FP64 (Ku given in r, overwritten); per-CTA partial sums of r.r
+__global__ void __launch_bounds__(256) residual64_kernel(long long n, const double *f0, const double *f1,
+                                                          const double *f2, double *r0, double *r1, double *r2,
+                                                          double *part_rr) {
+  double rr = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const double a0 = f0[q] - r0[q], a1 = f1[q] - r1[q], a2 = f2[q] - r2[q];
+    r0[q] = a0;
+    r1[q] = a1;
+    r2[q] = a2;
+    rr += a0 * a0 + a1 * a1 + a2 * a2;
+  }
+  rr = block_sum(rr);
+  if (threadIdx.x == 0) part_rr[blockIdx.x] = rr;
+}
+
+// u += d (FP64 solution, correction in the context precision)
+template <typename R>
+__global__ void __launch_bounds__(256) add_correction_kernel(long long n, double *u0, double *u1, double *u2,
+                                                              const R *d0, const R *d1, const R *d2) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    u0[q] += (double)d0[q];
+    u1[q] += (double)d1[q];
+    u2[q] += (double)d2[q];
+  }
+}
+
 // |u| per node
 template <typename R>
 __global__ void __launch_bounds__(256) umag_kernel(long long n, const R *u0, const R *u1, const R *u2, R *out) {

@@ -81,13 +81,34 @@ __global__ void __launch_bounds__(256) thermal_kernel(const ThArgs<R> A) {
   const R az = R(0.25) * (hxm + hx0) * (hym + hy0);  // z-face share of the node
   LayerSums<R> lo = {0, 0, 0, 0, 0, 0};
   const long long id0 = g.nid(i, j, 0);
+  // Software pipeline: the values of plane k+1 (its voxels, the in-plane and
+  // upper neighbours of T, the source) are requested one iteration ahead so
+  // that their memory latency overlaps the arithmetic of plane k.
+  auto load_plane = [&](int k, int m[4], R t[6], R &p) {
+    m[0] = g.cell(i - 1, j - 1, k);
+    m[1] = g.cell(i, j - 1, k);
+    m[2] = g.cell(i - 1, j, k);
+    m[3] = g.cell(i, j, k);
+    if (MODE == 0 && k <= nz) {
+      const long long id = id0 + (long long)k * g.plane;
+      t[0] = k < nz ? A.To[id + g.plane] : R(0);
+      t[1] = i > 0 ? A.To[id - 1] : R(0);
+      t[2] = i < nx ? A.To[id + 1] : R(0);
+      t[3] = j > 0 ? A.To[id - g.px] : R(0);
+      t[4] = j < ny ? A.To[id + g.px] : R(0);
+      p = A.P != nullptr ? A.P[id] : R(0);
+    }
+  };
+  int m_cur[4], m_nxt[4];
+  R t_cur[6] = {0, 0, 0, 0, 0, 0}, t_nxt[6] = {0, 0, 0, 0, 0, 0}, p_cur = 0, p_nxt = 0;
+  load_plane(0, m_cur, t_cur, p_cur);
   R T_km1 = 0, T_c = MODE == 0 ? A.To[id0] : R(0);
   for (int k = 0; k <= nz; ++k) {
     const long long id = id0 + (long long)k * g.plane;
+    if (k < nz) load_plane(k + 1, m_nxt, t_nxt, p_nxt);
     const R hz = k < nz ? g.h[2][k] : R(0), ihz = k < nz ? g.ih[2][k] : R(0);
     const R hzm = k > 0 ? g.h[2][k - 1] : R(0);
-    const LayerSums<R> up = layer_sums(s_mt, g.cell(i - 1, j - 1, k), g.cell(i, j - 1, k), g.cell(i - 1, j, k),
-                                       g.cell(i, j, k), hxm, hx0, hym, hy0, hz, ihz);
+    const LayerSums<R> up = layer_sums(s_mt, m_cur[0], m_cur[1], m_cur[2], m_cur[3], hxm, hx0, hym, hy0, hz, ihz);
     const R Gxp = (lo.ax_p + up.ax_p) * ihx0, Gxm = (lo.ax_m + up.ax_m) * ihxm;
     const R Gyp = (lo.ay_p + up.ay_p) * ihy0, Gym = (lo.ay_m + up.ay_m) * ihym;
     const R Gzp = up.gz, Gzm = lo.gz;
@@ -98,17 +119,20 @@ __global__ void __launch_bounds__(256) thermal_kernel(const ThArgs<R> A) {
     if (MODE == 1) {
       A.ratio_out[id] = C / (Gxp + Gxm + Gyp + Gym + Gzp + Gzm + film);
     } else {
-      const R T_kp1 = k < nz ? A.To[id + g.plane] : R(0);
-      const R T_xm = i > 0 ? A.To[id - 1] : R(0), T_xp = i < nx ? A.To[id + 1] : R(0);
-      const R T_ym = j > 0 ? A.To[id - g.px] : R(0), T_yp = j < ny ? A.To[id + g.px] : R(0);
-      R flux = Gxm * (T_xm - T_c) + Gxp * (T_xp - T_c) + Gym * (T_ym - T_c) + Gyp * (T_yp - T_c) +
-               Gzm * (T_km1 - T_c) + Gzp * (T_kp1 - T_c) + film * (A.T_amb - T_c);
-      if (A.P != nullptr) flux += A.P[id];
+      const R T_kp1 = t_cur[0];
+      const R flux = Gxm * (t_cur[1] - T_c) + Gxp * (t_cur[2] - T_c) + Gym * (t_cur[3] - T_c) +
+                     Gyp * (t_cur[4] - T_c) + Gzm * (T_km1 - T_c) + Gzp * (T_kp1 - T_c) +
+                     film * (A.T_amb - T_c) + p_cur;
       A.Tn[id] = T_c + A.dt * flux / C;
       T_km1 = T_c;
       T_c = T_kp1;
     }
     lo = up;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) m_cur[q] = m_nxt[q];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) t_cur[q] = t_nxt[q];
+    p_cur = p_nxt;
   }
 }
 

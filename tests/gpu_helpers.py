@@ -37,19 +37,20 @@ def unknown_masks(p):
     """boolean node-shaped masks of the E and H unknowns (edges inside the grid
     not held by a PEC wall; faces inside the grid)."""
     n = (p.nx, p.ny, p.nz)
-    K, J, I = np.meshgrid(np.arange(p.nz + 1), np.arange(p.ny + 1), np.arange(p.nx + 1), indexing="ij")
+    K, J, I = np.ogrid[0:p.nz + 1, 0:p.ny + 1, 0:p.nx + 1]
     P = (I, J, K)
+    shape = (p.nz + 1, p.ny + 1, p.nx + 1)
     em, hm = [], []
     for a in range(3):
         b, c = (a + 1) % 3, (a + 2) % 3
-        ok = P[a] < n[a]
+        ok = np.broadcast_to(P[a] < n[a], shape).copy()
         for d in (b, c):
             if p.em_bc[2 * d] != W.BC_PMC:
                 ok &= P[d] != 0
             if p.em_bc[2 * d + 1] != W.BC_PMC:
                 ok &= P[d] != n[d]
         em.append(ok.reshape(-1))
-        hm.append(((P[b] < n[b]) & (P[c] < n[c])).reshape(-1))
+        hm.append(np.broadcast_to((P[b] < n[b]) & (P[c] < n[c]), shape).reshape(-1))
     return em, hm
 
 
@@ -74,13 +75,18 @@ def read_eh(ctx):
     return ([ctx.read(api.COSIM_F_EX + a) for a in range(3)], [ctx.read(api.COSIM_F_HX + a) for a in range(3)])
 
 
-def hetero_problem(nx, ny, nz, seed, em_bc, cpml=4, conductor=True):
-    """odd-sized non-uniform grid, four materials including a good conductor"""
+def hetero_problem(nx, ny, nz, seed, em_bc, cpml=4, conductor=True, uniform_x=False):
+    """odd-sized non-uniform grid, four materials including a good conductor.
+    uniform_x keeps the y and z spacings random but makes x uniform, so the
+    oracle's element-matrix cache (keyed on the cell shape) hits along x rows."""
     rng = np.random.default_rng(seed)
     mats = [W.DIELECTRIC, W.COPPER if conductor else W.UNDERFILL, W.SILICON, W.UNDERFILL]
     mat = rng.integers(0, 4, (nz, ny, nx)).astype(np.uint8)
+    dx = rng.uniform(3e-6, 8e-6, nx)
+    if uniform_x:
+        dx[:] = 5e-6
     return W.Problem(name=f"hetero{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz,
-                     dx=rng.uniform(3e-6, 8e-6, nx), dy=rng.uniform(3e-6, 8e-6, ny),
+                     dx=dx, dy=rng.uniform(3e-6, 8e-6, ny),
                      dz=rng.uniform(1e-6, 4e-6, nz), mat=mat, materials=mats, em_bc=tuple(em_bc),
                      cpml_cells=cpml, cpml_eps_r=3.5, h_conv=(0.0, 2e4, 0.0, 0.0, 0.0, 1e4),
                      T_amb=300.0, T_init=300.0)

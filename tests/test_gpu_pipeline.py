@@ -31,7 +31,7 @@ def run_oracle(nsteps):
     return dict(p=p, o=o, tables=tables, E=E, H=H, Q=Q, total=tot, T=o.T.copy(), res=res)
 
 
-def run_gpu(ref, precision, nsteps, rtol):
+def run_gpu(ref, precision, nsteps, rtol, refine=False):
     p = ref["p"]
     ctx = context(p, precision, ref["o"].dt)
     ctx.set_sources(ref["tables"])
@@ -41,7 +41,8 @@ def run_gpu(ref, precision, nsteps, rtol):
     tot = ctx.joule(api.COSIM_JOULE_FINALIZE_AVG_POWER)
     ctx.thermal_steps(p.thermal_steps)
     T = ctx.read(api.COSIM_F_T)
-    rep = ctx.stress_solve(bc=api.COSIM_MECH_CLAMPED_BOTTOM, T_ref=300.0, rtol=rtol)
+    rep = ctx.stress_solve(bc=api.COSIM_MECH_CLAMPED_BOTTOM, T_ref=300.0, rtol=rtol, refine=refine,
+                           inner_rtol=1e-4 if refine else 0.0)
     u = np.stack([ctx.read(api.COSIM_F_UX + c) for c in range(3)])
     vm = ctx.read(api.COSIM_F_VM)
     ctx.close()
@@ -95,3 +96,38 @@ def test_config1_fp64_10k_steps(ref10k):
     assert rel_l2(g["T"] - 300, ref10k["T"] - 300) < 1e-9
     assert rel_l2(g["u"], interleaved_to_soa(ref10k["res"]["u"])) < 1e-6
     assert rel_l2(g["vm"], ref10k["res"]["vm"]) < 1e-6
+
+
+def test_config1_precision_ladder(ref10k):
+    """Precision ladder on the 32x32x16 package after 10^4 EM steps: FP64
+    kernels, FP32 kernels (FP64 Joule totals and CG dots), and FP32 kernels
+    with the stress solve in FP64 iterative refinement. Prints the per-field
+    relative L2 error of each against the FP64 oracle and of FP32 against the
+    FP64 GPU run; the refined FP32 solve must reach the FP64 bars for the
+    displacement and von Mises stress (1e-6 at a 1e-9 true residual)."""
+    runs = {"fp64": run_gpu(ref10k, FP64, 10_000, 1e-9),
+            "fp32": run_gpu(ref10k, FP32, 10_000, 1e-6),
+            "fp32+ir": run_gpu(ref10k, FP32, 10_000, 1e-9, refine=True)}
+    ref_u = interleaved_to_soa(ref10k["res"]["u"])
+
+    def errors(g, r):
+        return {"E": field_rel_l2(g["E"], r["E"])[0], "H": field_rel_l2(g["H"], r["H"])[0],
+                "Q": rel_l2(g["Q"], r["Q"]), "P_total": abs(g["total"] / r["total"] - 1),
+                "dT": rel_l2(g["T"] - 300, r["T"] - 300), "u": rel_l2(g["u"], r["u"]),
+                "vm": rel_l2(g["vm"], r["vm"])}
+
+    oracle_ref = dict(E=ref10k["E"], H=ref10k["H"], Q=ref10k["Q"], total=ref10k["total"], T=ref10k["T"],
+                      u=ref_u, vm=ref10k["res"]["vm"])
+    table = {k: errors(g, oracle_ref) for k, g in runs.items()}
+    table["fp32 vs fp64 GPU"] = errors(runs["fp32"], runs["fp64"])
+    cols = list(table["fp64"].keys())
+    print("\nprecision ladder, relative L2 vs the FP64 oracle (10^4 EM steps):")
+    print("| run | " + " | ".join(cols) + " | CG iters | refine steps |")
+    for k, e in table.items():
+        rep = runs[k]["rep"] if k in runs else None
+        extra = f" {rep['iters']} | {rep.get('refine_steps', 0)} |" if rep else " | |"
+        print(f"| {k} | " + " | ".join(f"{e[c]:.1e}" for c in cols) + " |" + extra)
+    assert max(table["fp64"].values()) < 1e-6
+    assert max(table["fp32"][c] for c in ("E", "H", "Q", "P_total", "dT")) < 1e-4
+    assert table["fp32+ir"]["u"] < 1e-6 and table["fp32+ir"]["vm"] < 1e-6
+    assert runs["fp32+ir"]["rep"]["relres"] <= 1e-9

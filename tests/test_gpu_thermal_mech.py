@@ -70,7 +70,7 @@ def test_hex8_matvec_random(precision, tol, shape):
 
 
 def _thermal_load_problem(precision, bc):
-    p = hetero_problem(23, 13, 8, seed=11, em_bc=(0,) * 6, cpml=0)
+    p = hetero_problem(23, 13, 8, seed=11, em_bc=(0,) * 6, cpml=0, uniform_x=True)
     o = oracle.OracleSim(p)
     ctx = context(p, precision, o.dt)
     rng = np.random.default_rng(5)
@@ -111,6 +111,20 @@ def test_stress_solve_fp32_converges():
     assert rep["relres"] <= 1e-6
     u = np.stack([ctx.read(api.COSIM_F_UX + c) for c in range(3)])
     assert rel_l2(u, interleaved_to_soa(ref["u"])) < 1e-4
+    ctx.close()
+
+
+@pytest.mark.parametrize("bc", [api.COSIM_MECH_CLAMPED_BOTTOM, api.COSIM_MECH_KINEMATIC_MOUNT])
+def test_stress_solve_fp32_in_fp64_refinement(bc):
+    """FP32 vectors and matvecs inside FP64 iterative refinement: the true FP64
+    residual reaches 1e-9 and displacement / von Mises match the oracle to 1e-6."""
+    p, o, ctx, fixed = _thermal_load_problem(FP32, bc)
+    ref = o.stress_solve(fixed, 300.0, rtol=1e-13)
+    rep = ctx.stress_solve(bc=bc, T_ref=300.0, rtol=1e-9, refine=True, inner_rtol=1e-4, check_every=8)
+    assert rep["relres"] <= 1e-9 and rep["refine_steps"] >= 2
+    u = np.stack([ctx.read(api.COSIM_F_UX + c) for c in range(3)])
+    assert rel_l2(u, interleaved_to_soa(ref["u"])) < 1e-6
+    assert rel_l2(ctx.read(api.COSIM_F_VM), ref["vm"]) < 1e-6
     ctx.close()
 
 

@@ -284,8 +284,8 @@ def crop(p: Problem, lo, hi) -> Problem:
     """Sub-window [lo, hi) (cell indices per axis) of a problem.
 
     Faces of the window that are faces of the original domain keep their
-    boundary choice; cut faces become PEC with no convection. Sources are
-    dropped (windows are used with prescribed initial fields)."""
+    boundary choice; cut faces become PEC with no convection. Source edges
+    inside the window are kept, shifted to window coordinates."""
     (i0, j0, k0), (i1, j1, k1) = lo, hi
     bc = list(p.em_bc)
     h = list(p.h_conv)
@@ -294,9 +294,16 @@ def crop(p: Problem, lo, hi) -> Problem:
             bc[2 * f], h[2 * f] = BC_PEC, 0.0
         if b != n:
             bc[2 * f + 1], h[2 * f + 1] = BC_PEC, 0.0
+    srcs = []
+    for s in p.sources:
+        e = np.asarray(s.edges, np.int64) - np.array([i0, j0, k0])
+        hi_e = np.array([i1 - i0, j1 - j0, k1 - k0])
+        inside = np.all(e >= 0, axis=1) & np.all(e <= hi_e, axis=1) & (e[:, s.axis] < hi_e[s.axis])
+        if inside.any():
+            srcs.append(Source(axis=s.axis, edges=e[inside].astype(np.int32), waveform=s.waveform))
     return _check(replace(
         p, name=p.name + f"[{i0}:{i1},{j0}:{j1},{k0}:{k1}]",
         nx=i1 - i0, ny=j1 - j0, nz=k1 - k0,
         dx=p.dx[i0:i1].copy(), dy=p.dy[j0:j1].copy(), dz=p.dz[k0:k1].copy(),
         mat=np.ascontiguousarray(p.mat[k0:k1, j0:j1, i0:i1]),
-        em_bc=tuple(bc), h_conv=tuple(h), sources=[]))
+        em_bc=tuple(bc), h_conv=tuple(h), sources=srcs))
