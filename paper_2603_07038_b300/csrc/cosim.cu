@@ -2,6 +2,9 @@
 // device allocation, derived tables and the launch sequence of every call.
 #include "../../include/cosim.h"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -20,7 +23,10 @@ using namespace cosim;
 
 namespace {
 
-constexpr int kEmTX = 32, kEmTY = 8;  // EM tile: 31 x 7 owned nodes per CTA
+#ifndef COSIM_EM_TY
+#define COSIM_EM_TY 8
+#endif
+constexpr int kEmTX = 32, kEmTY = COSIM_EM_TY;  // EM tile: 31 x (TY-1) owned nodes per CTA
 constexpr int kMvTX = 32, kMvTY = 8;  // matvec tile
 constexpr int kRedBlocks = 1184;      // fixed grid of the vector kernels (8 x 148)
 thread_local std::string g_create_error;
@@ -53,6 +59,9 @@ struct cosim_ctx {
   // FP32 contexts also hold the low part of chi (lE, lH)
   void *xE[2][3][2]{}, *dE[2][3][2]{}, *xH[2][3][2]{}, *dH[2][3][2]{};
   void *lE[2][3][2]{}, *lH[2][3][2]{};
+  // TMA descriptors of E, H (per parity and component) and the Joule window
+  CUtensorMap tmE[2][3], tmH[2][3], tmQ;
+  int *dev_err = nullptr;  // device word: a bounded in-kernel wait gave up
   int slo[3]{}, shi[3]{}, sn[3]{};
   long long psi_len[3]{};
   int par = 0;
@@ -263,11 +272,35 @@ static cudaError_t set_smem_limits() {
   cudaError_t e =
       cudaFuncSetAttribute(hex8_matvec_kernel<R, kMvTX, kMvTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, mv);
   if (e != cudaSuccess) return e;
-  const int em = (int)(em_stage_offset<R, kEmTX, kEmTY>(kMaxMat) + kEmStages * sizeof(EmStage<R, kEmTX, kEmTY>));
+  const int em =
+      (int)(em_stage_offset<R, kEmTX, kEmTY>(kMaxMat) + kEmStages * sizeof(EmStage<R, kEmTX, kEmTY>) + 128);
   e = cudaFuncSetAttribute(em_step_kernel<R, int, kEmTX, kEmTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, em);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(em_step_kernel<R, long long, kEmTX, kEmTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               em);
+}
+
+// TMA descriptor of a padded node array (x fastest, pitch px, planes of
+// px (ny+1)): extents nx+1, ny+1, nz+1 (reads past them return zero), box of
+// em_box_x x rows x 1 nodes for the EM kernel's plane staging.
+static cosim_status encode_node_map(cosim_ctx *c, CUtensorMap *m, void *base, int rows) {
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q{};
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || fn == nullptr) {
+    cudaGetLastError();
+    return fail(c, COSIM_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  }
+  const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  const cuuint64_t dims[3] = {(cuuint64_t)c->nx + 1, (cuuint64_t)c->ny + 1, (cuuint64_t)c->nz + 1};
+  const cuuint64_t strides[2] = {(cuuint64_t)c->px * c->rsz, (cuuint64_t)c->plane * c->rsz};
+  const cuuint32_t box[3] = {(cuuint32_t)em_box_x<kEmTX>(), (cuuint32_t)rows, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = encode(m, c->rsz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base,
+                            dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(c, COSIM_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return COSIM_OK;
 }
 
 static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const cosim_options *o) {
@@ -413,6 +446,13 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
     }
   ALLOC(c, c->Q, c->npad * 8);
   ALLOC(c, c->Qs, c->npad * c->rsz);
+  ALLOC(c, c->dev_err, sizeof(int));
+  for (int p = 0; p < 2; ++p)
+    for (int a = 0; a < 3; ++a) {
+      if ((st = encode_node_map(c, &c->tmE[p][a], c->E[p][a], kEmTY + 1)) != COSIM_OK) return st;
+      if ((st = encode_node_map(c, &c->tmH[p][a], c->H[p][a], kEmTY)) != COSIM_OK) return st;
+    }
+  if ((st = encode_node_map(c, &c->tmQ, c->Qs, kEmTY)) != COSIM_OK) return st;
   ALLOC(c, c->T[0], c->npad * c->rsz);
   ALLOC(c, c->T[1], c->npad * c->rsz);
   ALLOC(c, c->P, c->npad * c->rsz);
@@ -576,10 +616,12 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum) {
   A.amp_len = c->amp_len;
   A.Qs = accum ? (R *)c->Qs : nullptr;
   A.Q = c->Q;
+  A.tmQ = c->tmQ;
+  A.err = c->dev_err;
   const dim3 blk(kEmTX, kEmTY);
   const dim3 grd((c->nx + 1 + kEmTX - 2) / (kEmTX - 1), (c->ny + 1 + kEmTY - 2) / (kEmTY - 1));
   const size_t smem = em_stage_offset<R, kEmTX, kEmTY>((int)c->mats.size()) +
-                      kEmStages * sizeof(EmStage<R, kEmTX, kEmTY>);
+                      kEmStages * sizeof(EmStage<R, kEmTX, kEmTY>) + 128;  // + alignment slack
   for (int64_t s = 0; s < nsteps; ++s) {
     const int o = c->par, n = c->par ^ 1;
     for (int a = 0; a < 3; ++a) {
@@ -601,6 +643,8 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum) {
         A.lHo[a][s2] = (const R *)c->lH[o][a][s2];
         A.lHn[a][s2] = (R *)c->lH[n][a][s2];
       }
+      A.tmE[a] = c->tmE[o][a];
+      A.tmH[a] = c->tmH[o][a];
     }
     A.step = c->step;
     A.fold = accum && ((c->n_acc + 1) % kJouleWindow == 0);
@@ -1114,6 +1158,17 @@ static void launch_pack(cosim_ctx *c, const void *src, void *dst, bool cells, do
   pack_kernel<S, D><<<kRedBlocks, 256, 0, c->stream>>>((const S *)src, (D *)dst, nx1, ny1, nz1, px, add); ++c->launches;
 }
 
+// A kernel whose bounded wait for staged data expired sets c->dev_err; report it
+// (and clear it) at the next synchronising call.
+static cosim_status check_device_wait(cosim_ctx *c) {
+  int h = 0;
+  CHECK_CUDA(c, cudaMemcpy(&h, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h == 0) return COSIM_OK;
+  CHECK_CUDA(c, cudaMemset(c->dev_err, 0, sizeof(int)));
+  return fail(c, COSIM_ERR_TIMEOUT, h == 2 ? "EM kernel: a TMA alignment precondition failed; no step was taken"
+                                           : "a bounded in-kernel wait for staged data expired; results are invalid");
+}
+
 extern "C" cosim_status cosim_read_fields(cosim_ctx *c, int32_t field, int32_t dtype, void *dst, size_t bytes,
                                           int32_t dst_is_device) {
   if (!c) return COSIM_ERR_INVALID;
@@ -1138,7 +1193,7 @@ extern "C" cosim_status cosim_read_fields(cosim_ctx *c, int32_t field, int32_t d
   CHECK_LAUNCH(c);
   if (!dst_is_device) CHECK_CUDA(c, cudaMemcpyAsync(dst, c->scratch, bytes, cudaMemcpyDeviceToHost, c->stream));
   CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
-  return COSIM_OK;
+  return check_device_wait(c);
 }
 
 extern "C" cosim_status cosim_write_fields(cosim_ctx *c, int32_t field, int32_t dtype, const void *src, size_t bytes,

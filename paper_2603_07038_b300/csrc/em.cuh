@@ -20,13 +20,17 @@
 // accumulator that is folded into the FP64 total every few steps (FP64 runs at
 // a small fraction of the FP32 rate on this GPU, so none is used per step).
 //
-// Inputs of plane k+2 are copied to shared memory with cp.async while plane k
-// is computed (three stages), so each CTA keeps two planes of loads in flight.
+// Inputs of planes k+2 and k+3 are copied to shared memory by TMA (one thread
+// issues a 2-D box per array and plane, completion tracked by one mbarrier per
+// stage, four stages) while plane k is computed. Waits on those barriers are
+// bounded: a copy that never arrives sets an error word instead of hanging.
 //
 // Material averaging (per edge: area-weighted eps, sigma over the <=4 voxels;
 // per face: series mean of mu over the 2 voxels) is recomputed from the 1-byte
 // voxel IDs every step instead of streaming per-edge coefficient arrays.
 #pragma once
+#include <cuda.h>  // CUtensorMap
+
 #include "common.cuh"
 
 namespace cosim {
@@ -69,6 +73,10 @@ struct EmArgs {
   int fold;
   // tiles [ibx0, ibx1) x [iby0, iby1) lie off the lateral walls and CPML slabs
   int ibx0, ibx1, iby0, iby1;
+  // TMA descriptors of E^n, H^{n-1/2} (per component) and Qs: 3-D node
+  // arrays (x, y, z) with boxes of kEmBoxX x (TY+1 for E, TY otherwise) x 1
+  CUtensorMap tmE[3], tmH[3], tmQ;
+  int *err;  // set to 1 when a bounded wait for a staged plane gave up
 };
 
 // index of position p (node or cell) of an axis inside its CPML slabs, or -1
@@ -170,13 +178,24 @@ __device__ __forceinline__ R e_update(R e_old, R dtW, R drive, R Se, R Ss, R lq,
   return e_new;
 }
 
-// One plane of the CTA's inputs, staged in shared memory: E^n of the tile plus
-// its +x/+y neighbours, H^{n-1/2} and the Joule accumulator of the owned nodes.
+// One plane of the CTA's inputs, staged in shared memory by TMA: E^n of the
+// tile plus its +x/+y neighbours, H^{n-1/2} and the Joule accumulator. A TMA
+// box must start at an x coordinate that is a multiple of 16 bytes, so the
+// box starts at the tile's first node rounded down to a multiple of 4 and is
+// kEmBoxX = TX + 4 nodes wide; threads index it from that remainder.
+template <int TX>
+__host__ __device__ constexpr int em_box_x() { return TX + 4; }
+// A TMA destination in shared memory must be 128-byte aligned: every box is
+// padded to a multiple of 128 bytes.
+template <typename R, int ROWS, int BX>
+struct alignas(128) EmBox {
+  R v[ROWS][BX];
+};
 template <typename R, int TX, int TY>
 struct EmStage {
-  R E[3][TY + 1][TX + 1];
-  R H[3][TY][TX];
-  R Qs[TY][TX];
+  EmBox<R, TY + 1, em_box_x<TX>()> E[3];
+  EmBox<R, TY, em_box_x<TX>()> H[3];
+  EmBox<R, TY, em_box_x<TX>()> Qs;
 };
 
 constexpr int kCpmlTable = 6 * kMaxSlab;  // (1 - b) per [axis][E,H][slab position]
@@ -185,10 +204,24 @@ constexpr int kCpmlTable = 6 * kMaxSlab;  // (1 - b) per [axis][E,H][slab positi
 // rows (row nmat is all zero and stands for voxels outside the grid).
 template <typename R, int TX, int TY>
 __host__ __device__ constexpr size_t em_stage_offset(int nmat) {
-  return ((kCpmlTable + (size_t)(nmat + 1) * M_COLS) * sizeof(R) + 15) & ~size_t(15);
+  return ((kCpmlTable + (size_t)(nmat + 1) * M_COLS) * sizeof(R) + 127) & ~size_t(127);
 }
 
-constexpr int kEmStages = 4;  // planes k, k+1 (in use), k+2, k+3 (in flight)
+// Shared-memory stages (a power of two) and the prefetch distance: at plane k
+// the copy of plane k + kEmAhead is issued and planes k, k+1 must have landed.
+#ifndef COSIM_EM_STAGES
+#define COSIM_EM_STAGES 4
+#endif
+#ifndef COSIM_EM_AHEAD
+#define COSIM_EM_AHEAD 3
+#endif
+#ifndef COSIM_EM_MIN_CTAS
+#define COSIM_EM_MIN_CTAS 3  // resident CTAs per SM the FP32 kernel is compiled for
+#endif
+constexpr int kEmStages = COSIM_EM_STAGES;
+constexpr int kEmAhead = COSIM_EM_AHEAD;
+static_assert((kEmStages & (kEmStages - 1)) == 0, "stage count must be a power of two");
+static_assert(kEmAhead >= 2 && kEmAhead <= kEmStages - 1, "prefetch distance must leave the stage of plane k-1 free");
 
 // Body of the fused step for one CTA tile. BORDER = false is the interior
 // specialisation: every node of the tile and its +x/+y neighbours lies inside
@@ -199,7 +232,8 @@ constexpr int kEmStages = 4;  // planes k, k+1 (in use), k+2, k+3 (in flight)
 // than 2^31 elements, long long otherwise).
 template <typename R, typename I, int TX, int TY, bool BORDER>
 __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
-                                        EmStage<R, TX, TY> *stg, R (*sHxz)[TY][TX], R (*sQy)[TX]) {
+                                        EmStage<R, TX, TY> *stg, R (*sHxz)[TY][TX], R (*sQy)[TX], uint64_t *bars,
+                                        int *s_abort) {
   const Geo<R> &g = A.g;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -213,43 +247,30 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
   const bool in_x = !BORDER || i < nx, in_y = !BORDER || j < ny;
   const bool accum = A.Qs != nullptr;
 
-  // Plane k of E^n (tile + neighbours), H^{n-1/2} and Qs (owned nodes) -> stage s.
-  // Each thread copies its own node; the last column / row / corner threads
-  // also copy the +x / +y / +xy neighbour. Positions outside the grid are
-  // zero-filled without a read.
-  const bool xc = tx == TX - 1, yr = ty == TY - 1;
-  const bool ok_xc = xc && (!BORDER || (i + 1 <= nx && j >= 0 && j <= ny));
-  const bool ok_yr = yr && (!BORDER || (i >= 0 && i <= nx && j + 1 <= ny));
-  const bool ok_cr = xc && yr && (!BORDER || (i + 1 <= nx && j + 1 <= ny));
-  const I plane = (I)g.plane;
-  const I o_own = act ? (I)g.nid(i, j, 0) : I(0);
-  const I o_xc = ok_xc ? (I)g.nid(i + 1, j, 0) : I(0);
-  const I o_yr = ok_yr ? (I)g.nid(i, j + 1, 0) : I(0);
-  const I o_cr = ok_cr ? (I)g.nid(i + 1, j + 1, 0) : I(0);
-  auto load_stage = [&](int k, int s) {
+  // Plane k of E^n (tile + neighbours), H^{n-1/2} and Qs -> stage k mod
+  // kEmStages, by TMA: one thread announces the bytes on the stage's mbarrier
+  // and issues the seven box copies; positions outside the grid arrive as zero.
+  // Box x starts at the tile's first node rounded down to a multiple of 4
+  // (two's complement: i0 = -1 gives x0 = -4); threads read from column tx + xr.
+  const int xr = i0 & 3, x0 = i0 - xr;
+  const bool leader = tx == 0 && ty == 0;
+  // transaction bytes of one stage: the boxes themselves, not their padding
+  const unsigned stage_bytes =
+      (unsigned)((6 * TY + 3 + (accum ? TY : 0)) * em_box_x<TX>() * (int)sizeof(R));
+  auto issue = [&](int k) {
+    if (k > nz) return;
+    const int s = k & (kEmStages - 1);
     EmStage<R, TX, TY> &S = stg[s];
-    const bool kin = k <= nz;
-    const I kp = kin ? (I)k * plane : I(0);
+    mbar_arrive_expect_tx(&bars[s], stage_bytes);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      cp_async<sizeof(R)>(&S.E[c][ty][tx], A.Eo[c] + (o_own + kp), kin && act);
-      cp_async<sizeof(R)>(&S.H[c][ty][tx], A.Ho[c] + (o_own + kp), kin && act);
+      tma_load_3d(&S.E[c].v[0][0], &A.tmE[c], x0, j0, k, &bars[s]);
+      tma_load_3d(&S.H[c].v[0][0], &A.tmH[c], x0, j0, k, &bars[s]);
     }
-    if (xc) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) cp_async<sizeof(R)>(&S.E[c][ty][TX], A.Eo[c] + (o_xc + kp), kin && ok_xc);
-    }
-    if (yr) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) cp_async<sizeof(R)>(&S.E[c][TY][tx], A.Eo[c] + (o_yr + kp), kin && ok_yr);
-    }
-    if (xc && yr) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) cp_async<sizeof(R)>(&S.E[c][TY][TX], A.Eo[c] + (o_cr + kp), kin && ok_cr);
-    }
-    if (accum) cp_async<sizeof(R)>(&S.Qs[ty][tx], A.Qs + (o_own + kp), kin && own);
-    cp_async_commit();
+    if (accum) tma_load_3d(&S.Qs.v[0][0], &A.tmQ, x0, j0, k, &bars[s]);
   };
+  const I plane = (I)g.plane;
+  const I o_own = act ? (I)g.nid(i, j, 0) : I(0);
   // Material rows (id x M_COLS) of voxels (i-1+dx, j-1+dy, k); the zero row
   // outside the grid.
   const bool cx0 = !BORDER || (i - 1 >= 0 && i - 1 < nx), cx1 = !BORDER || (i >= 0 && i < nx);
@@ -284,9 +305,10 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
   const R lqx = R(0.25) * hx0, lqy = R(0.25) * hy0;
   const I id0 = o_own;
 
-  load_stage(0, 0);
-  load_stage(1, 1);
-  load_stage(2, 2);
+  if (leader) {
+#pragma unroll
+    for (int q = 0; q < kEmAhead; ++q) issue(q);
+  }
   int a00, a01, a10, a11;  // material rows of voxel layer k (the layer above node plane k)
   voxels(0, a00, a01, a10, a11);
   int r0 = 0, r1 = 0;  // source entries of row (k, j)
@@ -303,7 +325,10 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
   R hz0 = nz > 0 ? g.h[2][0] : R(0), ihz = nz > 0 ? g.ih[2][0] : R(0), idz = g.idual[2][0], hzm = 0;
 
   for (int k = 0; k <= nz; ++k) {
-    load_stage(k + 3, (k + 3) & (kEmStages - 1));
+    if (leader) {  // the stage of plane k-1 is free: every thread passed the last barrier
+      fence_proxy_async_smem();
+      issue(k + kEmAhead);
+    }
     // next plane's voxels, source row and z spacing, consumed in the next iteration
     int n00, n01, n10, n11;
     voxels(k + 1, n00, n01, n10, n11);
@@ -315,8 +340,20 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
     }
     const R hz0_n = (k + 1 < nz) ? g.h[2][k + 1] : R(0), ihz_n = (k + 1 < nz) ? g.ih[2][k + 1] : R(0);
     const R idz_n = (k < nz) ? g.idual[2][k + 1] : R(0);
-    cp_async_wait<2>();  // planes k and k+1 have landed
+    {  // planes k and k+1 have landed (phase parity: use count of the stage)
+      bool ok = mbar_wait(&bars[k & (kEmStages - 1)], (unsigned)(k / kEmStages) & 1u);
+      if (k + 1 <= nz) ok = mbar_wait(&bars[(k + 1) & (kEmStages - 1)], (unsigned)((k + 1) / kEmStages) & 1u) && ok;
+      if (!ok) *s_abort = 1;
+    }
     __syncthreads();
+    if (*s_abort) {  // a copy did not arrive in time: drain what is in flight (bounded), flag, leave
+      if (leader) {
+        for (int q = k; q <= k + kEmAhead && q <= nz; ++q)
+          mbar_wait(&bars[q & (kEmStages - 1)], (unsigned)(q / kEmStages) & 1u);
+        atomicExch(A.err, 1);
+      }
+      return;
+    }
     const I id = id0 + (I)k * plane;
     // Joule energy of node (i, j, k-1): its y-edge share from j-1 is now visible
     if (accum && own && k > 0) {
@@ -335,12 +372,13 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
     const int szE = slab_index(k, nz, A.slo[2], A.shi[2]);
     const int szH = (k < nz) ? szE : -1;
 
-    const R ex = S0.E[0][ty][tx], ey = S0.E[1][ty][tx], ez = S0.E[2][ty][tx];
-    const R ex_up = S1.E[0][ty][tx], ey_up = S1.E[1][ty][tx];
-    const R ez_jp = S0.E[2][ty + 1][tx], ex_jp = S0.E[0][ty + 1][tx];
-    const R ez_ip = S0.E[2][ty][tx + 1], ey_ip = S0.E[1][ty][tx + 1];
-    const R hx_o = S0.H[0][ty][tx], hy_o = S0.H[1][ty][tx], hz_o = S0.H[2][ty][tx];
-    const R q_old = accum ? S0.Qs[ty][tx] : R(0);
+    const int cx = tx + xr;  // this node's column in the staged boxes
+    const R ex = S0.E[0].v[ty][cx], ey = S0.E[1].v[ty][cx], ez = S0.E[2].v[ty][cx];
+    const R ex_up = S1.E[0].v[ty][cx], ey_up = S1.E[1].v[ty][cx];
+    const R ez_jp = S0.E[2].v[ty + 1][cx], ex_jp = S0.E[0].v[ty + 1][cx];
+    const R ez_ip = S0.E[2].v[ty][cx + 1], ey_ip = S0.E[1].v[ty][cx + 1];
+    const R hx_o = S0.H[0].v[ty][cx], hy_o = S0.H[1].v[ty][cx], hz_o = S0.H[2].v[ty][cx];
+    const R q_old = accum ? S0.Qs.v[ty][cx] : R(0);
 
     // material constants of voxel layer k
     const R e00 = s_mt[a00 + M_EPS], e01 = s_mt[a01 + M_EPS], e10 = s_mt[a10 + M_EPS], e11 = s_mt[a11 + M_EPS];
@@ -456,29 +494,48 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
       A.Qs[id] = s;
     }
   }
-  cp_async_wait<0>();
 }
 
 // One launch per step over all tiles; tiles in [ibx0, ibx1) x [iby0, iby1)
 // take the interior specialisation.
 template <typename R, typename I, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? 3 : 2) em_step_kernel(const EmArgs<R> A) {
+__global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? COSIM_EM_MIN_CTAS : 2)
+    em_step_kernel(const __grid_constant__ EmArgs<R> A) {
   static_assert(TX == 32, "a tile row is one warp: x neighbours are exchanged by shuffles");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R *s_cp = reinterpret_cast<R *>(smem_raw);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // the launch adds 128 bytes so that the tables and stages can start on a
+  // 128-byte boundary of the shared window (TMA destinations must)
+  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  R *s_cp = reinterpret_cast<R *>(smem);
   R *s_mt = s_cp + kCpmlTable;
-  EmStage<R, TX, TY> *stg =
-      reinterpret_cast<EmStage<R, TX, TY> *>(smem_raw + em_stage_offset<R, TX, TY>(A.g.nmat));
+  EmStage<R, TX, TY> *stg = reinterpret_cast<EmStage<R, TX, TY> *>(smem + em_stage_offset<R, TX, TY>(A.g.nmat));
   __shared__ R sHxz[2][TY][TX];  // Hx, Hz of the plane, read by the +y neighbour
   __shared__ R sQy[TY][TX];      // Joule share of the y-edge, read by the +y neighbour one plane later
+  __shared__ uint64_t s_bar[kEmStages];  // one transaction barrier per stage
+  __shared__ int s_abort;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    // TMA preconditions checked once per CTA: 128-byte aligned destinations
+    // and 64-byte aligned descriptors; otherwise flag the error and leave
+    // without issuing a copy
+    bool ok = (smem_u32(stg) & 127u) == 0 && (sizeof(EmStage<R, TX, TY>) & 127u) == 0;
+    for (int c = 0; c < 3; ++c)
+      ok = ok && ((size_t)&A.tmE[c] & 63u) == 0 && ((size_t)&A.tmH[c] & 63u) == 0;
+    ok = ok && ((size_t)&A.tmQ & 63u) == 0;
+    s_abort = ok ? 0 : 1;
+    if (!ok) atomicExch(A.err, 2);
+    for (int q = 0; q < kEmStages; ++q) mbar_init(&s_bar[q], 1);
+    fence_mbar_init();
+  }
   stage_table(s_mt, A.g.mtab, (A.g.nmat + 1) * M_COLS);
   stage_table(s_cp, A.cpml, kCpmlTable);
+  __syncthreads();
+  if (s_abort) return;
   const bool interior = (int)blockIdx.x >= A.ibx0 && (int)blockIdx.x < A.ibx1 && (int)blockIdx.y >= A.iby0 &&
                         (int)blockIdx.y < A.iby1;
   if (interior)
-    em_tile<R, I, TX, TY, false>(A, s_cp, s_mt, stg, sHxz, sQy);
+    em_tile<R, I, TX, TY, false>(A, s_cp, s_mt, stg, sHxz, sQy, s_bar, &s_abort);
   else
-    em_tile<R, I, TX, TY, true>(A, s_cp, s_mt, stg, sHxz, sQy);
+    em_tile<R, I, TX, TY, true>(A, s_cp, s_mt, stg, sHxz, sQy, s_bar, &s_abort);
 }
 
 }  // namespace cosim
