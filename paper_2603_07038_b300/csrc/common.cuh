@@ -5,7 +5,8 @@
 //     3-D arrays, x fastest, row pitch `px` = nx+1 rounded up to 32 elements
 //     (128-byte aligned rows for FP32), planes of px*(ny+1) elements; the
 //     padding columns i > nx are kept at zero;
-//   * voxel materials: uint8 nz*ny*nx, x fastest (1 byte per cell);
+//   * voxel materials: uint8, x fastest, row pitch vpx = nx rounded up to 16
+//     bytes (TMA needs 16-byte strides), planes of vpx*ny (1 byte per cell);
 //   * per-axis spacing tables h, 1/h, 1/dual-length (a few KB);
 //   * a per-material constant table staged in shared memory by each kernel.
 #pragma once
@@ -38,7 +39,8 @@ struct Geo {
   int nx, ny, nz;
   int px;              // x pitch of node arrays
   long long plane;     // px * (ny + 1)
-  const uint8_t *mat;  // nz * ny * nx
+  const uint8_t *mat;  // nz planes of ny rows of pitch vpx
+  int vpx;             // voxel row pitch (bytes)
   const R *h[3];       // cell sizes, n entries per axis
   const R *ih[3];      // 1 / cell size, n entries
   const R *idual[3];   // 1 / dual length at nodes, n + 1 entries
@@ -51,7 +53,7 @@ struct Geo {
   // material of voxel (i,j,k), or -1 outside the grid
   __device__ __forceinline__ int cell(int i, int j, int k) const {
     return (i >= 0 && i < nx && j >= 0 && j < ny && k >= 0 && k < nz)
-               ? (int)__ldg(mat + ((long long)k * ny + j) * nx + i)
+               ? (int)__ldg(mat + ((long long)k * ny + j) * vpx + i)
                : -1;
   }
 };
@@ -111,6 +113,21 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int x, 
       "[%5];\n" ::"r"(smem_u32(dst)),
       "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
+}
+// 1-D box of a rank-1 tensor map at element x (same alignment rule as above)
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *tmap, int x, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.1d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2}], [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(smem_u32(bar))
+      : "memory");
+}
+// contiguous bulk copy (both addresses 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
   unsigned ok;

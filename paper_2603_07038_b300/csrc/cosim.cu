@@ -29,6 +29,7 @@ namespace {
 constexpr int kEmTX = 32, kEmTY = COSIM_EM_TY;  // EM tile: 31 x (TY-1) owned nodes per CTA
 constexpr int kMvTX = 32, kMvTY = 8;  // matvec tile
 constexpr int kRedBlocks = 1184;      // fixed grid of the vector kernels (8 x 148)
+constexpr int kSrcPadLo = 4, kSrcPadHi = 16;  // zero ints around the source-row offsets
 thread_local std::string g_create_error;
 
 }  // namespace
@@ -79,7 +80,11 @@ struct cosim_ctx {
   double *scal = nullptr;   // misc device scalars
   double *host_scal = nullptr;  // pinned
   // sources
-  int *src_row = nullptr;
+  int *src_row = nullptr;       // = src_row_buf + kSrcPadLo
+  int *src_row_buf = nullptr;   // allocation: kSrcPadLo zeros, the offsets, kSrcPadHi zeros
+  CUtensorMap tmV;   // voxel IDs (x, y, z), box em_vox_box_x x (TY+1) x 1
+  void *zt = nullptr;  // per node plane k: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1) (zero outside)
+  int vpx = 0;         // voxel row pitch
   int4 *src_ent = nullptr;
   void *src_amp = nullptr;
   long long amp_len = 0;
@@ -152,6 +157,7 @@ static Geo<R> make_geo(const cosim_ctx *c) {
   g.px = c->px;
   g.plane = c->plane;
   g.mat = c->mat;
+  g.vpx = c->vpx;
   for (int a = 0; a < 3; ++a) {
     g.h[a] = (const R *)c->dh[a];
     g.ih[a] = (const R *)c->dih[a];
@@ -197,6 +203,7 @@ static Geo<double> make_geo64(const cosim_ctx *c) {
   g.px = c->px;
   g.plane = c->plane;
   g.mat = c->mat;
+  g.vpx = c->vpx;
   for (int a = 0; a < 3; ++a) {
     g.h[a] = (const double *)c->dh64[a];
     g.ih[a] = (const double *)c->dih64[a];
@@ -283,7 +290,8 @@ static cudaError_t set_smem_limits() {
 // TMA descriptor of a padded node array (x fastest, pitch px, planes of
 // px (ny+1)): extents nx+1, ny+1, nz+1 (reads past them return zero), box of
 // em_box_x x rows x 1 nodes for the EM kernel's plane staging.
-static cosim_status encode_node_map(cosim_ctx *c, CUtensorMap *m, void *base, int rows) {
+static cosim_status encode_map(cosim_ctx *c, CUtensorMap *m, CUtensorMapDataType type, int rank, void *base,
+                               const cuuint64_t *dims, const cuuint64_t *strides, const cuuint32_t *box) {
   void *fn = nullptr;
   cudaDriverEntryPointQueryResult q{};
   cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
@@ -292,16 +300,28 @@ static cosim_status encode_node_map(cosim_ctx *c, CUtensorMap *m, void *base, in
     return fail(c, COSIM_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   }
   const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  const cuuint64_t dims[3] = {(cuuint64_t)c->nx + 1, (cuuint64_t)c->ny + 1, (cuuint64_t)c->nz + 1};
-  const cuuint64_t strides[2] = {(cuuint64_t)c->px * c->rsz, (cuuint64_t)c->plane * c->rsz};
-  const cuuint32_t box[3] = {(cuuint32_t)em_box_x<kEmTX>(), (cuuint32_t)rows, 1};
   const cuuint32_t es[3] = {1, 1, 1};
-  const CUresult r = encode(m, c->rsz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base,
-                            dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUresult r = encode(m, type, rank, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(c, COSIM_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return COSIM_OK;
 }
+static cosim_status encode_node_map(cosim_ctx *c, CUtensorMap *m, void *base, int rows) {
+  const cuuint64_t dims[3] = {(cuuint64_t)c->nx + 1, (cuuint64_t)c->ny + 1, (cuuint64_t)c->nz + 1};
+  const cuuint64_t strides[2] = {(cuuint64_t)c->px * c->rsz, (cuuint64_t)c->plane * c->rsz};
+  const cuuint32_t box[3] = {(cuuint32_t)em_box_x<kEmTX>(), (cuuint32_t)rows, 1};
+  return encode_map(c, m, c->rsz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base,
+                    dims, strides, box);
+}
+// voxel IDs: (x, y, z) = (nx, ny, nz) bytes with row pitch vpx
+static cosim_status encode_voxel_map(cosim_ctx *c) {
+  const cuuint64_t dims[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)c->vpx, (cuuint64_t)c->vpx * c->ny};
+  const cuuint32_t box[3] = {(cuuint32_t)em_vox_box_x<kEmTX>(), (cuuint32_t)kEmTY + 1, 1};
+  return encode_map(c, &c->tmV, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, c->mat, dims, strides, box);
+}
+
 
 static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const cosim_options *o) {
   c->nx = d->nx;
@@ -391,10 +411,24 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
     c->mtab64 = c->mtab;
   else if ((st = upload_f64(c, &c->mtab64, mt)) != COSIM_OK)
     return st;
-  // voxels
-  const size_t ncell = (size_t)c->nx * c->ny * c->nz;
-  ALLOC(c, c->mat, ncell);
-  if ((st = h2d(c, c->mat, d->mat, ncell)) != COSIM_OK) return st;
+  // voxels: rows padded to a 16-byte pitch (a TMA stride rule); the padding
+  // bytes are zero and never read as material
+  c->vpx = (c->nx + 15) / 16 * 16;
+  ALLOC(c, c->mat, (size_t)c->vpx * c->ny * c->nz);
+  CHECK_CUDA(c, cudaMemcpy2DAsync(c->mat, c->vpx, d->mat, c->nx, c->nx, (size_t)c->ny * c->nz,
+                                  cudaMemcpyHostToDevice, c->stream));
+  // per node plane k: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1), zero where the
+  // cell does not exist; one 16/32-byte record copied per plane by the EM kernel
+  {
+    std::vector<double> zt(4 * (size_t)(c->nz + 1), 0.0);
+    for (int k = 0; k <= c->nz; ++k) {
+      zt[4 * k + 0] = k < c->nz ? c->h[2][k] : 0.0;
+      zt[4 * k + 1] = k < c->nz ? 1.0 / c->h[2][k] : 0.0;
+      zt[4 * k + 2] = 1.0 / ((k > 0 ? 0.5 * c->h[2][k - 1] : 0.0) + (k < c->nz ? 0.5 * c->h[2][k] : 0.0));
+      zt[4 * k + 3] = k > 0 ? c->h[2][k - 1] : 0.0;
+    }
+    if ((st = upload_real(c, &c->zt, zt)) != COSIM_OK) return st;
+  }
 
   // CPML slabs and the table of 1 - b per [axis][E,H][kMaxSlab]
   std::vector<double> cp(kCpmlTable);
@@ -453,6 +487,7 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
       if ((st = encode_node_map(c, &c->tmH[p][a], c->H[p][a], kEmTY)) != COSIM_OK) return st;
     }
   if ((st = encode_node_map(c, &c->tmQ, c->Qs, kEmTY)) != COSIM_OK) return st;
+  if ((st = encode_voxel_map(c)) != COSIM_OK) return st;
   ALLOC(c, c->T[0], c->npad * c->rsz);
   ALLOC(c, c->T[1], c->npad * c->rsz);
   ALLOC(c, c->P, c->npad * c->rsz);
@@ -548,10 +583,11 @@ extern "C" cosim_status cosim_set_sources(cosim_ctx *c, int32_t n, const cosim_s
     amp_len = std::max(amp_len, (long long)q.nsteps);
   }
   cudaStreamSynchronize(c->stream);
-  free_one(c, c->src_row);
+  free_one(c, c->src_row_buf);
   free_one(c, c->src_ent);
   free_one(c, c->src_amp);
   c->src_row = nullptr;
+  c->src_row_buf = nullptr;
   c->src_ent = nullptr;
   c->src_amp = nullptr;
   c->amp_len = 0;
@@ -566,7 +602,11 @@ extern "C" cosim_status cosim_set_sources(cosim_ctx *c, int32_t n, const cosim_s
   std::vector<double> amp((size_t)n * amp_len, 0.0);
   for (int s = 0; s < n; ++s)
     for (long long t = 0; t < src[s].nsteps; ++t) amp[(size_t)s * amp_len + t] = src[s].amp[t];
-  ALLOC(c, c->src_row, row.size() * sizeof(int));
+  // padded so that the EM kernel's 16-byte aligned bulk copy of the rows
+  // j0 .. j0+TY of a plane (start rounded down to 4 entries, from j0 = -1)
+  // stays inside the allocation
+  ALLOC(c, c->src_row_buf, (row.size() + kSrcPadLo + kSrcPadHi) * sizeof(int));
+  c->src_row = c->src_row_buf + kSrcPadLo;
   ALLOC(c, c->src_ent, ent.size() * sizeof(int4));
   cosim_status st;
   if ((st = h2d(c, c->src_row, row.data(), row.size() * sizeof(int))) != COSIM_OK) return st;
@@ -617,6 +657,8 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum) {
   A.Qs = accum ? (R *)c->Qs : nullptr;
   A.Q = c->Q;
   A.tmQ = c->tmQ;
+  A.tmV = c->tmV;
+  A.zt = (const R *)c->zt;
   A.err = c->dev_err;
   const dim3 blk(kEmTX, kEmTY);
   const dim3 grd((c->nx + 1 + kEmTX - 2) / (kEmTX - 1), (c->ny + 1 + kEmTY - 2) / (kEmTY - 1));

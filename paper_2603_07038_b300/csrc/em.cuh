@@ -60,7 +60,8 @@ struct EmArgs {
   const R *cpml;              // 1 - b per [axis][E,H][kMaxSlab] (computed as -expm1 on the host)
   int fixlo[3], fixhi[3];     // wall holds tangential E at zero (PEC or CPML backing)
   R dt;
-  const int *src_row;         // per (k,j) row: first source entry, (nz+1)(ny+1)+1 ints
+  const int *src_row;         // per (k,j) row: first source entry, (nz+1)(ny+1)+1 ints,
+                              // readable from index -4 to 15 past the end (zero padding)
   const int4 *src_ent;        // (i, axis, source index, 0)
   const R *src_amp;           // [source][amp_len]
   long long amp_len;
@@ -76,7 +77,9 @@ struct EmArgs {
   // TMA descriptors of E^n, H^{n-1/2} (per component) and Qs: 3-D node
   // arrays (x, y, z) with boxes of kEmBoxX x (TY+1 for E, TY otherwise) x 1
   CUtensorMap tmE[3], tmH[3], tmQ;
-  int *err;  // set to 1 when a bounded wait for a staged plane gave up
+  CUtensorMap tmV;  // voxel IDs (x, y, z), box em_vox_box_x x (TY+1) x 1
+  const R *zt;      // per node plane: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
+  int *err;         // set to 1 when a bounded wait for a staged plane gave up
 };
 
 // index of position p (node or cell) of an axis inside its CPML slabs, or -1
@@ -191,11 +194,20 @@ template <typename R, int ROWS, int BX>
 struct alignas(128) EmBox {
   R v[ROWS][BX];
 };
+// voxel box: columns i0-1 .. i0+TX-1 from x rounded down to 16 bytes
+template <int TX>
+__host__ __device__ constexpr int em_vox_box_x() { return (TX + 1 + 15 + 15) / 16 * 16; }
+// source-row box: rows j0 .. j0+TY (+1 for the end offset) from a multiple of 4
+template <int TY>
+__host__ __device__ constexpr int em_src_box() { return (TY + 1 + 3 + 3) / 4 * 4; }
 template <typename R, int TX, int TY>
 struct EmStage {
   EmBox<R, TY + 1, em_box_x<TX>()> E[3];
   EmBox<R, TY, em_box_x<TX>()> H[3];
   EmBox<R, TY, em_box_x<TX>()> Qs;
+  EmBox<uint8_t, TY + 1, em_vox_box_x<TX>()> V;  // voxel IDs of layer k, rows j0-1 .. j0+TY-1
+  EmBox<int, 1, em_src_box<TY>()> S;             // source-row offsets of plane k
+  EmBox<R, 1, 4> Z;                              // hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
 };
 
 constexpr int kCpmlTable = 6 * kMaxSlab;  // (1 - b) per [axis][E,H][slab position]
@@ -254,37 +266,39 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
   // (two's complement: i0 = -1 gives x0 = -4); threads read from column tx + xr.
   const int xr = i0 & 3, x0 = i0 - xr;
   const bool leader = tx == 0 && ty == 0;
+  // The voxel box starts at column i0 - 1 rounded down to 16 bytes, the
+  // source-row box at entry k (ny+1) + j0 rounded down to 4 ints.
+  const int xvr = (i0 - 1) & 15, xv0 = (i0 - 1) - xvr;
+  const bool has_src = A.src_row != nullptr;
   // transaction bytes of one stage: the boxes themselves, not their padding
-  const unsigned stage_bytes =
-      (unsigned)((6 * TY + 3 + (accum ? TY : 0)) * em_box_x<TX>() * (int)sizeof(R));
+  const unsigned fixed_bytes = (unsigned)((6 * TY + 3 + (accum ? TY : 0)) * em_box_x<TX>() * (int)sizeof(R) +
+                                          4 * (int)sizeof(R) + (has_src ? em_src_box<TY>() * 4 : 0));
+  const unsigned vox_bytes = (unsigned)((TY + 1) * em_vox_box_x<TX>());
   auto issue = [&](int k) {
     if (k > nz) return;
     const int s = k & (kEmStages - 1);
     EmStage<R, TX, TY> &S = stg[s];
-    mbar_arrive_expect_tx(&bars[s], stage_bytes);
+    mbar_arrive_expect_tx(&bars[s], fixed_bytes + (k < nz ? vox_bytes : 0u));
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       tma_load_3d(&S.E[c].v[0][0], &A.tmE[c], x0, j0, k, &bars[s]);
       tma_load_3d(&S.H[c].v[0][0], &A.tmH[c], x0, j0, k, &bars[s]);
     }
     if (accum) tma_load_3d(&S.Qs.v[0][0], &A.tmQ, x0, j0, k, &bars[s]);
+    if (k < nz) tma_load_3d(&S.V.v[0][0], &A.tmV, xv0, j0 - 1, k, &bars[s]);
+    bulk_load(&S.Z.v[0][0], A.zt + 4 * (size_t)k, 4 * sizeof(R), &bars[s]);
+    if (has_src) {  // 16-byte aligned: src_row itself is, the start is a multiple of 4 from -4
+      const int base = k * (ny + 1) + j0;
+      bulk_load(&S.S.v[0][0], A.src_row + (base - (base & 3)), em_src_box<TY>() * 4, &bars[s]);
+    }
   };
   const I plane = (I)g.plane;
   const I o_own = act ? (I)g.nid(i, j, 0) : I(0);
-  // Material rows (id x M_COLS) of voxels (i-1+dx, j-1+dy, k); the zero row
-  // outside the grid.
+  // Material rows (id x M_COLS) of voxels (i-1+dx, j-1+dy, k) from the staged
+  // voxel box; the zero row outside the grid.
   const bool cx0 = !BORDER || (i - 1 >= 0 && i - 1 < nx), cx1 = !BORDER || (i >= 0 && i < nx);
   const bool cy0 = !BORDER || (j - 1 >= 0 && j - 1 < ny), cy1 = !BORDER || (j >= 0 && j < ny);
-  const I co = (I)(j - 1) * nx + (i - 1);  // voxel (i-1, j-1) of layer 0
-  const I cplane = (I)nx * ny;
-  auto voxels = [&](int k, int &m00, int &m01, int &m10, int &m11) {
-    const bool kz = k < nz;  // k >= 0 always
-    const uint8_t *b = g.mat + (co + (kz ? (I)k * cplane : I(0)));
-    m00 = (kz && cx0 && cy0) ? (int)__ldg(b) * M_COLS : vd;
-    m01 = (kz && cx1 && cy0) ? (int)__ldg(b + 1) * M_COLS : vd;
-    m10 = (kz && cx0 && cy1) ? (int)__ldg(b + nx) * M_COLS : vd;
-    m11 = (kz && cx1 && cy1) ? (int)__ldg(b + nx + 1) * M_COLS : vd;
-  };
+  const int cv = tx + xvr;  // column of voxel i-1 in the box
 
   const R hxm = (act && (!BORDER || i > 0)) ? g.h[0][i - 1] : R(0), hx0 = (act && in_x) ? g.h[0][i] : R(0);
   const R hym = (act && (!BORDER || j > 0)) ? g.h[1][j - 1] : R(0), hy0 = (act && in_y) ? g.h[1][j] : R(0);
@@ -309,37 +323,17 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
 #pragma unroll
     for (int q = 0; q < kEmAhead; ++q) issue(q);
   }
-  int a00, a01, a10, a11;  // material rows of voxel layer k (the layer above node plane k)
-  voxels(0, a00, a01, a10, a11);
-  int r0 = 0, r1 = 0;  // source entries of row (k, j)
-  if (A.src_row != nullptr && act) {
-    r0 = __ldg(A.src_row + j);
-    r1 = __ldg(A.src_row + j + 1);
-  }
   R hx_km1 = 0, hy_km1 = 0, qz_km1 = 0;
   // layer k-1 partial sums of the x / y edges and 1/mu of voxel (i, j, k-1);
   // zero below the grid
   R pxe_b = 0, pxs_b = 0, pye_b = 0, pys_b = 0, u11_b = 0;
   R q_pend = 0;  // Joule sum of node (i, j, k-1) still missing the y-edge share from j-1
-  // z spacing of the current plane, loaded one plane ahead
-  R hz0 = nz > 0 ? g.h[2][0] : R(0), ihz = nz > 0 ? g.ih[2][0] : R(0), idz = g.idual[2][0], hzm = 0;
 
   for (int k = 0; k <= nz; ++k) {
     if (leader) {  // the stage of plane k-1 is free: every thread passed the last barrier
       fence_proxy_async_smem();
       issue(k + kEmAhead);
     }
-    // next plane's voxels, source row and z spacing, consumed in the next iteration
-    int n00, n01, n10, n11;
-    voxels(k + 1, n00, n01, n10, n11);
-    int nr0 = 0, nr1 = 0;
-    if (A.src_row != nullptr && act && k < nz) {
-      const int row = (k + 1) * (ny + 1) + j;
-      nr0 = __ldg(A.src_row + row);
-      nr1 = __ldg(A.src_row + row + 1);
-    }
-    const R hz0_n = (k + 1 < nz) ? g.h[2][k + 1] : R(0), ihz_n = (k + 1 < nz) ? g.ih[2][k + 1] : R(0);
-    const R idz_n = (k < nz) ? g.idual[2][k + 1] : R(0);
     {  // planes k and k+1 have landed (phase parity: use count of the stage)
       bool ok = mbar_wait(&bars[k & (kEmStages - 1)], (unsigned)(k / kEmStages) & 1u);
       if (k + 1 <= nz) ok = mbar_wait(&bars[(k + 1) & (kEmStages - 1)], (unsigned)((k + 1) / kEmStages) & 1u) && ok;
@@ -367,6 +361,19 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
     }
     const EmStage<R, TX, TY> &S0 = stg[k & (kEmStages - 1)];
     const EmStage<R, TX, TY> &S1 = stg[(k + 1) & (kEmStages - 1)];
+    const R hz0 = S0.Z.v[0][0], ihz = S0.Z.v[0][1], idz = S0.Z.v[0][2], hzm = S0.Z.v[0][3];
+    // material rows of voxel layer k (the layer above node plane k)
+    const bool kz = k < nz;
+    const int a00 = (kz && cx0 && cy0) ? (int)S0.V.v[ty][cv] * M_COLS : vd;
+    const int a01 = (kz && cx1 && cy0) ? (int)S0.V.v[ty][cv + 1] * M_COLS : vd;
+    const int a10 = (kz && cx0 && cy1) ? (int)S0.V.v[ty + 1][cv] * M_COLS : vd;
+    const int a11 = (kz && cx1 && cy1) ? (int)S0.V.v[ty + 1][cv + 1] * M_COLS : vd;
+    int r0 = 0, r1 = 0;  // source entries of row (k, j)
+    if (has_src && act) {
+      const int base = k * (ny + 1) + j0, sr = (base & 3) + ty;
+      r0 = S0.S.v[0][sr];
+      r1 = S0.S.v[0][sr + 1];
+    }
     const R hdz = half_dt * idz;
     const bool fix_z = (k == 0 && A.fixlo[2]) || (k == nz && A.fixhi[2]);
     const int szE = slab_index(k, nz, A.slo[2], A.shi[2]);
@@ -472,16 +479,6 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
     pye_b = pye_a;
     pys_b = pys_a;
     u11_b = u11;
-    a00 = n00;
-    a01 = n01;
-    a10 = n10;
-    a11 = n11;
-    r0 = nr0;
-    r1 = nr1;
-    hzm = hz0;
-    hz0 = hz0_n;
-    ihz = ihz_n;
-    idz = idz_n;
   }
   __syncthreads();
   if (accum && own) {  // Joule energy of the top plane k = nz
