@@ -152,6 +152,18 @@ __device__ __forceinline__ R curl_with_psi(const EmArgs<R> &A, const R *s_cp, in
   return a - b;
 }
 
+static_assert(M_EPS == 0 && M_SDT2 == 1 && M_IMU == 2 && M_COLS % 4 == 0,
+              "the EM kernel reads eps, sigma dt/2, 1/mu of a material row with one aligned vector load");
+// Four consecutive values from 16-byte aligned shared memory in one vector load.
+__device__ __forceinline__ void load4(const float *p, float &a, float &b, float &c, float &d) {
+  const float4 v = *reinterpret_cast<const float4 *>(p);
+  a = v.x, b = v.y, c = v.z, d = v.w;
+}
+__device__ __forceinline__ void load4(const double *p, double &a, double &b, double &c, double &d) {
+  const double2 v = reinterpret_cast<const double2 *>(p)[0], w = reinterpret_cast<const double2 *>(p)[1];
+  a = v.x, b = v.y, c = w.x, d = w.y;
+}
+
 // Reciprocal of a positive normal number: in FP32 the hardware approximation
 // refined by one Newton-Raphson step (r' = r + r (1 - x r)), within about an
 // ulp of 1/x; in FP64 the exact division.
@@ -361,7 +373,8 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
     }
     const EmStage<R, TX, TY> &S0 = stg[k & (kEmStages - 1)];
     const EmStage<R, TX, TY> &S1 = stg[(k + 1) & (kEmStages - 1)];
-    const R hz0 = S0.Z.v[0][0], ihz = S0.Z.v[0][1], idz = S0.Z.v[0][2], hzm = S0.Z.v[0][3];
+    R hz0, ihz, idz, hzm;
+    load4(&S0.Z.v[0][0], hz0, ihz, idz, hzm);
     // material rows of voxel layer k (the layer above node plane k)
     const bool kz = k < nz;
     const int a00 = (kz && cx0 && cy0) ? (int)S0.V.v[ty][cv] * M_COLS : vd;
@@ -388,9 +401,12 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
     const R q_old = accum ? S0.Qs.v[ty][cx] : R(0);
 
     // material constants of voxel layer k
-    const R e00 = s_mt[a00 + M_EPS], e01 = s_mt[a01 + M_EPS], e10 = s_mt[a10 + M_EPS], e11 = s_mt[a11 + M_EPS];
-    const R s00 = s_mt[a00 + M_SDT2], s01 = s_mt[a01 + M_SDT2], s10 = s_mt[a10 + M_SDT2], s11 = s_mt[a11 + M_SDT2];
-    const R u01 = s_mt[a01 + M_IMU], u10 = s_mt[a10 + M_IMU], u11 = s_mt[a11 + M_IMU];
+    // (columns M_EPS, M_SDT2, M_IMU, M_K are adjacent: one vector load per voxel)
+    R e00, s00, u00, k00, e01, s01, u01, k01, e10, s10, u10, k10, e11, s11, u11, k11;
+    load4(s_mt + a00, e00, s00, u00, k00);
+    load4(s_mt + a01, e01, s01, u01, k01);
+    load4(s_mt + a10, e10, s10, u10, k10);
+    load4(s_mt + a11, e11, s11, u11, k11);
 
     // ---- H^{n+1/2} at (i,j,k): H -= dt/mu (curl E + psi terms); dt/mu of a
     // face is the series mean over the two voxels its dual edge crosses
@@ -444,14 +460,16 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
       exn = e_update(ex, dtWx_y * (hzm + hz0), curl - Jx, hzm * pxe_b + hz0 * pxe_a, hzm * pxs_b + hz0 * pxs_a, lqx,
                      &qx);
     }
-    if (need_ey && !(fix_x || fix_z)) {  // Ey: dHx/dz - dHz/dx, voxels (i-1..i, j, k-1..k)
+    // (interior tiles also run Ey / Ez on the halo lane tx = 0 and discard
+    // them: the warp stays convergent; only the owners store)
+    if ((BORDER ? need_ey : true) && !(fix_x || fix_z)) {  // Ey: dHx/dz - dHz/dx, voxels (i-1..i, j, k-1..k)
       const R d1 = (Hx - hx_km1) * idz;
       const R d2 = (Hz - hz_l) * idx;
       const R curl = curl_with_psi(A, s_cp, 0, 1, 2, szE, 0, sxE, i, j, k, d1, d2, own);
       eyn = e_update(ey, dtWy_x * (hzm + hz0), curl - Jy, hzm * pye_b + hz0 * pye_a, hzm * pys_b + hz0 * pys_a, lqy,
                      &qy);
     }
-    if (own && k < nz && !(fix_x || fix_y)) {  // Ez: dHy/dx - dHx/dy, voxels (i-1..i, j-1..j, k)
+    if ((BORDER ? own : ty > 0) && k < nz && !(fix_x || fix_y)) {  // Ez: dHy/dx - dHx/dy, voxels (i-1..i, j-1..j, k)
       const R d1 = (Hy - hy_l) * idx;
       const R d2 = (Hx - sHxz[0][ty - 1][tx]) * idy;
       const R curl = curl_with_psi(A, s_cp, 0, 2, 0, sxE, 1, syE, i, j, k, d1, d2, own);
