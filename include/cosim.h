@@ -132,6 +132,21 @@ cosim_status cosim_set_sources(cosim_ctx *ctx, int32_t n, const cosim_source *sr
  * nodes (P_total = D_sigma e^2, Sec. II-A). One kernel launch per step. */
 cosim_status cosim_em_steps(cosim_ctx *ctx, int64_t nsteps, uint32_t flags);
 
+/* Record nsteps EM steps (flags as for cosim_em_steps) into a CUDA graph held
+ * by the context, without running them. nsteps must be a positive multiple of
+ * 32 (the Joule window) and at most 2^30; with COSIM_ACCUM_JOULE the context
+ * must sit on a window boundary (steps accumulated since the last reset a
+ * multiple of 32). The context stream must be a non-default stream. Replaces
+ * any earlier graph; cosim_set_sources and cosim_destroy discard it. The paper
+ * has no counterpart: this is how the library batches launches on one GPU. */
+cosim_status cosim_em_graph_capture(cosim_ctx *ctx, int64_t nsteps, uint32_t flags);
+
+/* Launch the captured graph count times on the context stream (asynchronous):
+ * identical results, bit for bit, to cosim_em_steps(ctx, nsteps, flags)
+ * called count times. COSIM_ERR_INVALID if no graph is held or the context's
+ * E/H parity or Joule window position differs from the captured one. */
+cosim_status cosim_em_graph_launch(cosim_ctx *ctx, int64_t count);
+
 /* Joule accumulator operations:
  *   COSIM_JOULE_RESET: zero the per-node energy and the accumulated step count;
  *   COSIM_JOULE_FINALIZE_AVG_POWER: thermal source P_i = Q_i / (n_steps dt_em)

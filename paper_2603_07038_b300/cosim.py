@@ -104,6 +104,10 @@ def load():
     L.cosim_set_sources.restype = st
     L.cosim_em_steps.argtypes = [P, C.c_int64, C.c_uint32]
     L.cosim_em_steps.restype = st
+    L.cosim_em_graph_capture.argtypes = [P, C.c_int64, C.c_uint32]
+    L.cosim_em_graph_capture.restype = st
+    L.cosim_em_graph_launch.argtypes = [P, C.c_int64]
+    L.cosim_em_graph_launch.restype = st
     L.cosim_joule_accumulate.argtypes = [P, C.c_int32, C.POINTER(C.c_double)]
     L.cosim_joule_accumulate.restype = st
     L.cosim_thermal_steps.argtypes = [P, C.c_int64, C.c_double]
@@ -222,6 +226,14 @@ def cosim_set_sources(ctx, tables):
 
 def cosim_em_steps(ctx, nsteps, flags=COSIM_ACCUM_JOULE):
     _check(load().cosim_em_steps(ctx, int(nsteps), int(flags)), ctx)
+
+
+def cosim_em_graph_capture(ctx, nsteps, flags=COSIM_ACCUM_JOULE):
+    _check(load().cosim_em_graph_capture(ctx, int(nsteps), int(flags)), ctx)
+
+
+def cosim_em_graph_launch(ctx, count=1):
+    _check(load().cosim_em_graph_launch(ctx, int(count)), ctx)
 
 
 def cosim_joule_accumulate(ctx, op, want_total=True):
@@ -357,6 +369,12 @@ class Context:
 
     def em_steps(self, n, accumulate_joule=True):
         cosim_em_steps(self.h, n, COSIM_ACCUM_JOULE if accumulate_joule else 0)
+
+    def em_graph_capture(self, n, accumulate_joule=True):
+        cosim_em_graph_capture(self.h, n, COSIM_ACCUM_JOULE if accumulate_joule else 0)
+
+    def em_graph_launch(self, count=1):
+        cosim_em_graph_launch(self.h, count)
 
     def joule(self, op, want_total=True):
         return cosim_joule_accumulate(self.h, op, want_total)

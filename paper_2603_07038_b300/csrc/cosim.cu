@@ -67,6 +67,13 @@ struct cosim_ctx {
   long long psi_len[3]{};
   int par = 0;
   long long step = 0, n_acc = 0;
+  long long *dstep = nullptr;  // device copy of the source time index (advanced per call)
+  // captured EM graph (cosim_em_graph_capture): steps per replay, Joule flag,
+  // the E/H parity it starts from, kernels per replay
+  cudaGraphExec_t gexec = nullptr;
+  int64_t g_nsteps = 0, g_launches = 0;
+  bool g_accum = false;
+  int g_par = 0;
   long long launches = 0;  // kernels launched by this context
   double *Q = nullptr;      // Joule energy per node, FP64
   void *Qs = nullptr;       // short-window Joule accumulator (context precision)
@@ -481,6 +488,7 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
   ALLOC(c, c->Q, c->npad * 8);
   ALLOC(c, c->Qs, c->npad * c->rsz);
   ALLOC(c, c->dev_err, sizeof(int));
+  ALLOC(c, c->dstep, sizeof(long long));
   for (int p = 0; p < 2; ++p)
     for (int a = 0; a < 3; ++a) {
       if ((st = encode_node_map(c, &c->tmE[p][a], c->E[p][a], kEmTY + 1)) != COSIM_OK) return st;
@@ -529,9 +537,12 @@ extern "C" cosim_status cosim_create(const cosim_grid_desc *desc, const cosim_op
   return COSIM_OK;
 }
 
+static void drop_graph(cosim_ctx *c);
+
 extern "C" void cosim_destroy(cosim_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  drop_graph(c);
   for (auto &a : c->allocs) {
     if (c->has_alloc)
       c->alloc.free(a.first, c->alloc.user);
@@ -565,6 +576,7 @@ static void free_one(cosim_ctx *c, void *p) {
 extern "C" cosim_status cosim_set_sources(cosim_ctx *c, int32_t n, const cosim_source *src) {
   if (!c) return COSIM_ERR_INVALID;
   if (n < 0 || (n > 0 && !src)) return fail(c, COSIM_ERR_INVALID, "bad source list");
+  drop_graph(c);  // a captured graph holds the source table pointers
   struct Ent { int row, i, axis, s; };
   std::vector<Ent> ents;
   long long amp_len = 0;
@@ -688,7 +700,8 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum) {
       A.tmE[a] = c->tmE[o][a];
       A.tmH[a] = c->tmH[o][a];
     }
-    A.step = c->step;
+    A.step_base = c->dstep;
+    A.step_off = (int)s;
     A.fold = accum && ((c->n_acc + 1) % kJouleWindow == 0);
     if (c->npad < (1LL << 31))
       em_step_kernel<R, int, kEmTX, kEmTY><<<grd, blk, smem, c->stream>>>(A);
@@ -703,14 +716,97 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum) {
       c->qs_dirty = !A.fold;
     }
   }
+  if (nsteps > 0) {
+    step_advance_kernel<<<1, 1, 0, c->stream>>>(c->dstep, nsteps);
+    ++c->launches;
+    CHECK_LAUNCH(c);
+  }
+  return COSIM_OK;
+}
+
+static cosim_status em_steps_any(cosim_ctx *c, int64_t nsteps, bool acc) {
+  // groups of at most 2^30 steps keep the per-launch offset an int
+  while (nsteps > 0) {
+    const int64_t n = std::min<int64_t>(nsteps, 1LL << 30);
+    const cosim_status st = c->prec == COSIM_FP64 ? em_steps_t<double>(c, n, acc) : em_steps_t<float>(c, n, acc);
+    if (st != COSIM_OK) return st;
+    nsteps -= n;
+  }
   return COSIM_OK;
 }
 
 extern "C" cosim_status cosim_em_steps(cosim_ctx *c, int64_t nsteps, uint32_t flags) {
   if (!c) return COSIM_ERR_INVALID;
   if (nsteps < 0 || (flags & ~COSIM_ACCUM_JOULE)) return fail(c, COSIM_ERR_INVALID, "bad nsteps or flags");
+  return em_steps_any(c, nsteps, flags & COSIM_ACCUM_JOULE);
+}
+
+static void drop_graph(cosim_ctx *c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->g_nsteps = 0;
+}
+
+extern "C" cosim_status cosim_em_graph_capture(cosim_ctx *c, int64_t nsteps, uint32_t flags) {
+  if (!c) return COSIM_ERR_INVALID;
+  if (nsteps <= 0 || nsteps % kJouleWindow != 0 || nsteps > (1LL << 30) || (flags & ~COSIM_ACCUM_JOULE))
+    return fail(c, COSIM_ERR_INVALID, "graph steps must be a positive multiple of 32 (the Joule window), <= 2^30");
+  if (c->stream == nullptr) return fail(c, COSIM_ERR_INVALID, "graph capture needs a non-default stream");
   const bool acc = flags & COSIM_ACCUM_JOULE;
-  return c->prec == COSIM_FP64 ? em_steps_t<double>(c, nsteps, acc) : em_steps_t<float>(c, nsteps, acc);
+  if (acc && c->n_acc % kJouleWindow != 0)
+    return fail(c, COSIM_ERR_INVALID, "capture with Joule accumulation must start on a 32-step window boundary");
+  drop_graph(c);
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  // capturing records the launches without running them: keep the host
+  // bookkeeping as it was and apply it per replay instead
+  const long long step = c->step, n_acc = c->n_acc, launches = c->launches;
+  const int par = c->par;
+  const bool dirty = c->qs_dirty;
+  CHECK_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  cosim_status st = em_steps_any(c, nsteps, acc);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  const long long captured = c->launches - launches;
+  c->step = step, c->n_acc = n_acc, c->launches = launches, c->par = par, c->qs_dirty = dirty;
+  if (st != COSIM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess || graph == nullptr) {
+    cudaGetLastError();
+    return fail(c, COSIM_ERR_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(e));
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&c->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    c->gexec = nullptr;
+    cudaGetLastError();
+    return fail(c, COSIM_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+  }
+  c->g_nsteps = nsteps;
+  c->g_accum = acc;
+  c->g_par = par;
+  c->g_launches = captured;
+  return COSIM_OK;
+}
+
+extern "C" cosim_status cosim_em_graph_launch(cosim_ctx *c, int64_t count) {
+  if (!c) return COSIM_ERR_INVALID;
+  if (count < 0) return fail(c, COSIM_ERR_INVALID, "bad count");
+  if (!c->gexec) return fail(c, COSIM_ERR_INVALID, "no captured EM graph");
+  if (c->par != c->g_par) return fail(c, COSIM_ERR_INVALID, "the E/H parity differs from the captured one");
+  if (c->g_accum && c->n_acc % kJouleWindow != 0)
+    return fail(c, COSIM_ERR_INVALID, "Joule window position differs from the captured one");
+  for (int64_t r = 0; r < count; ++r) {
+    CHECK_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
+    c->step += c->g_nsteps;
+    c->launches += c->g_launches;
+    if (c->g_accum) {
+      c->n_acc += c->g_nsteps;
+      c->qs_dirty = false;  // the last step of a 32-step window folds
+    }
+  }
+  return COSIM_OK;
 }
 
 // move the short-window Joule energy into the FP64 total (Q += Qs, Qs = 0)

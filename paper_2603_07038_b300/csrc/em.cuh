@@ -65,7 +65,11 @@ struct EmArgs {
   const int4 *src_ent;        // (i, axis, source index, 0)
   const R *src_amp;           // [source][amp_len]
   long long amp_len;
-  long long step;
+  // source time index of this launch = *step_base + step_off: the base lives
+  // in device memory and is advanced once per call, so a captured CUDA graph
+  // of several steps replays with the right source samples
+  const long long *step_base;
+  int step_off;
   // Joule energy: each step adds to the short-window accumulator Qs (context
   // precision); on fold steps the owner moves Qs into the FP64 total Q instead,
   // so FP64 arithmetic runs once per window rather than every step.
@@ -439,8 +443,9 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
     R Jx = 0, Jy = 0, Jz = 0;
     for (int e = r0; e < r1; ++e) {
       const int4 s = A.src_ent[e];
-      if (s.x == i && A.step < A.amp_len) {
-        const R a = A.src_amp[(long long)s.z * A.amp_len + A.step];
+      const long long step = *A.step_base + A.step_off;
+      if (s.x == i && step < A.amp_len) {
+        const R a = A.src_amp[(long long)s.z * A.amp_len + step];
         Jx += s.y == 0 ? a : R(0);
         Jy += s.y == 1 ? a : R(0);
         Jz += s.y == 2 ? a : R(0);
@@ -552,5 +557,8 @@ __global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? COSIM_EM_MIN_CTAS : 2
   else
     em_tile<R, I, TX, TY, true>(A, s_cp, s_mt, stg, sHxz, sQy, s_bar, &s_abort);
 }
+
+// advance the device-resident source time index after a group of steps
+__global__ void step_advance_kernel(long long *step_base, long long n) { *step_base += n; }
 
 }  // namespace cosim

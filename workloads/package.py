@@ -66,10 +66,13 @@ class Source:
     edges: np.ndarray
     waveform: Callable
 
-    def amp_table(self, dt: float, nsteps: int) -> np.ndarray:
+    def amp_table(self, dt: float, nsteps: int, t0: float = 0.0) -> np.ndarray:
+        """J at t0 + (n + 1/2) dt, n < nsteps (t0: start of the simulated window)."""
         if hasattr(self.waveform, "table"):
+            if t0 != 0.0:
+                raise ValueError("a sampled waveform has no time offset")
             return self.waveform.table(dt, nsteps)
-        t = (np.arange(nsteps, dtype=np.float64) + 0.5) * dt
+        t = t0 + (np.arange(nsteps, dtype=np.float64) + 0.5) * dt
         return np.asarray(self.waveform(t), dtype=np.float64)
 
 
@@ -106,10 +109,12 @@ class Problem:
     def material_table(self) -> np.ndarray:
         return np.array([m.as_row() for m in self.materials], dtype=np.float64)
 
-    def source_tables(self, dt: float, nsteps: int):
-        """[(axis, edges int32 (n,3), amp float64 (nsteps,)), ...]"""
+    def source_tables(self, dt: float, nsteps: int, t0: float = 0.0):
+        """[(axis, edges int32 (n,3), amp float64 (nsteps,)), ...]; t0 shifts
+        the sampled window of every waveform (a burst window that starts
+        later than t = 0)."""
         return [(s.axis, np.ascontiguousarray(s.edges, dtype=np.int32),
-                 s.amp_table(dt, nsteps)) for s in self.sources]
+                 s.amp_table(dt, nsteps, t0)) for s in self.sources]
 
 
 def _check(p: Problem) -> Problem:
@@ -184,14 +189,25 @@ Z_DIE = (104, 128)     # chiplets (Si) in underfill
 ROUTING_Z = tuple(8 * r + 4 for r in range(8))
 
 
-def _dz_profile() -> np.ndarray:
-    thin = set(ROUTING_Z) | set(range(*Z_BUMP)) | {Z_INT[0], Z_INT[1] - 1}
-    return np.array([2e-6 if k in thin else 5e-6 for k in range(128)], np.float64)
+def _stack(nz: int = 128):
+    """z ranges (substrate, interposer, bumps, dies) and routing-layer planes
+    of an nz-cell stack: the 128-cell stack's proportions (1/2, 1/4, 1/16,
+    3/16), eight routing layers spread through the substrate. nz = 128 gives
+    the constants above."""
+    f = lambda z: (z * nz) // 128  # noqa: E731
+    return ((0, f(Z_SUB[1])), (f(Z_INT[0]), f(Z_INT[1])), (f(Z_BUMP[0]), f(Z_BUMP[1])), (f(Z_DIE[0]), nz),
+            tuple(f(z) for z in ROUTING_Z))
+
+
+def _dz_profile(nz: int = 128) -> np.ndarray:
+    _, z_int, z_bump, _, routing = _stack(nz)
+    thin = set(routing) | set(range(*z_bump)) | {z_int[0], z_int[1] - 1}
+    return np.array([2e-6 if k in thin else 5e-6 for k in range(nz)], np.float64)
 
 
 def layered_package(nx: int = 1024, ny: int = 1024, seed: int = 2, n_lines: int = 32,
                     tsv_pitch: int = 5, bump_pitch: int = 4, chiplet: int | None = None,
-                    em_steps: int | None = None) -> Problem:
+                    em_steps: int | None = None, nz: int = 128) -> Problem:
     """Layered package on an nx x ny x 128 voxel grid (10 um lateral, 2-5 um z).
 
     z 0-63: dielectric substrate with 8 Manhattan routing layers (one Cu cell
@@ -200,23 +216,29 @@ def layered_package(nx: int = 1024, ny: int = 1024, seed: int = 2, n_lines: int 
     1x1-voxel Cu TSVs at ``tsv_pitch``; z 96-103: underfill with 2x2-voxel Cu
     micro-bumps at ``bump_pitch`` under the chiplets; z 104-127: four Si
     chiplets (``chiplet`` voxels square, 2x2 arrangement) in underfill.
-    ``n_lines`` routing segments carry PRBS7 10 Gb/s ports.
+    ``n_lines`` routing segments carry PRBS7 10 Gb/s ports. ``nz`` other than
+    128 scales the stack's regions in proportion (``_stack``).
     """
-    nz = 128
+    if nz < 64:
+        raise ValueError("the layered stack needs nz >= 64")
+    z_sub, z_int, z_bump, z_die, routing = _stack(nz)
     rng = np.random.default_rng(seed)
     mat = np.empty((nz, ny, nx), np.uint8)
-    mat[Z_SUB[0]:Z_SUB[1]] = M_DIEL
-    mat[Z_INT[0]:Z_INT[1]] = M_SI
-    mat[Z_BUMP[0]:Z_DIE[1]] = M_UF
+    mat[z_sub[0]:z_sub[1]] = M_DIEL
+    mat[z_int[0]:z_int[1]] = M_SI
+    mat[z_bump[0]:z_die[1]] = M_UF
     segments = []  # (z, axis, along0, along1, across0, width)
-    for r, z in enumerate(ROUTING_Z):
+    for r, z in enumerate(routing):
         axis = r % 2               # 0: tracks run along x, 1: along y
         n_along, n_across = (nx, ny) if axis == 0 else (ny, nx)
         for c0 in range(1, n_across - 2, 5):
             w = int(rng.integers(1, 3))
             pos = int(rng.integers(0, 40))
+            # segment lengths 48-320 voxels; axes shorter than 256 voxels
+            # (small designs) draw proportionally shorter segments
+            seg_lo, seg_hi = (48, 320) if n_along >= 256 else (max(8, n_along // 6), max(16, n_along // 2))
             while pos < n_along:
-                seg = int(rng.integers(48, 320))
+                seg = int(rng.integers(seg_lo, seg_hi))
                 a0, a1 = pos, min(n_along, pos + seg)
                 if axis == 0:
                     mat[z, c0:c0 + w, a0:a1] = M_CU
@@ -228,7 +250,7 @@ def layered_package(nx: int = 1024, ny: int = 1024, seed: int = 2, n_lines: int 
     ii = (np.arange(nx) % tsv_pitch) == tsv_pitch // 2
     jj = (np.arange(ny) % tsv_pitch) == tsv_pitch // 2
     tsv = np.logical_and.outer(jj, ii)
-    mat[Z_INT[0]:Z_INT[1]][:, tsv] = M_CU
+    mat[z_int[0]:z_int[1]][:, tsv] = M_CU
     # chiplets and bumps
     if chiplet is None:
         chiplet = max(2, (300 * min(nx, ny)) // 1024)
@@ -239,18 +261,19 @@ def layered_package(nx: int = 1024, ny: int = 1024, seed: int = 2, n_lines: int 
     for cx in (mx, mx + chiplet + gap):
         for cy in (my, my + chiplet + gap):
             foot[cy:cy + chiplet, cx:cx + chiplet] = True
-    mat[Z_DIE[0]:Z_DIE[1]][:, foot] = M_SI
+    mat[z_die[0]:z_die[1]][:, foot] = M_SI
     bi = np.isin(np.arange(nx) % bump_pitch, (1, 2))
     bj = np.isin(np.arange(ny) % bump_pitch, (1, 2))
     bump = np.logical_and.outer(bj, bi) & foot
-    mat[Z_BUMP[0]:Z_BUMP[1]][:, bump] = M_CU
+    mat[z_bump[0]:z_bump[1]][:, bump] = M_CU
     dx = np.full(nx, 10e-6)
     dy = np.full(ny, 10e-6)
-    dz = _dz_profile()
+    dz = _dz_profile(nz)
     # signal lines: long segments away from the CPML, ports at their start
     L = 8
+    min_len = min(64, min(nx, ny) // 3)  # small grids: shorter port segments
     cand = [s for s in segments
-            if s[3] - s[2] >= 64 and s[2] > L and s[4] > L
+            if s[3] - s[2] >= min_len and s[2] > L and s[4] > L
             and s[4] + s[5] < (ny if s[1] == 0 else nx) - L
             and s[3] < (nx if s[1] == 0 else ny) - L]
     pick = rng.choice(len(cand), size=min(n_lines, len(cand)), replace=False)
