@@ -77,6 +77,8 @@ def lib():
         L.og_thermal_load.argtypes = [G, u8, dp, d, dp]
         L.og_pcg.argtypes = [G, u8, dp, dp, d, C.c_int64, C.POINTER(C.c_int64), dp]
         L.og_von_mises.argtypes = [G, dp, dp, d, dp, dp]
+        L.og_joule_power_T.argtypes = [G, pp3, pp3, dp, d, dp]
+        L.og_coupled_step.argtypes = [G, d, pp3, pp3, dp, C.c_void_p, dp, d, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -234,6 +236,34 @@ class OracleSim:
     def em_steps(self, n: int, accumulate_joule: bool = True):
         for _ in range(n):
             self.em_step(accumulate_joule)
+
+    # --- two-way electro-thermal coupling (Sec. II-A) ------------------------
+    def joule_power_T(self, Eold, Enew, theta=None) -> np.ndarray:
+        """Joule power per node [W] of one step with the conductivities at the
+        temperature theta + T_init (theta defaults to the current rise)."""
+        P = np.zeros(self.g.n_nodes)
+        th = self.theta if theta is None else np.ascontiguousarray(theta, np.float64)
+        lib().og_joule_power_T(self.g.ref, _p3([np.ascontiguousarray(e) for e in Eold]),
+                               _p3([np.ascontiguousarray(e) for e in Enew]), _dp(th), self.T0, _dp(P))
+        return P
+
+    def coupled_steps(self, n: int, accumulate_joule: bool = True):
+        """n synchronized steps: sigma(T^n), H and E, P^{n+1}, thermal step at
+        the EM dt (og_coupled_step). self.P holds the last step's power."""
+        L = lib()
+        psi = _dp(self.psi) if self.psi is not None else None
+        th = np.ascontiguousarray(self.theta, np.float64).copy()
+        th2 = np.empty_like(th)
+        for _ in range(n):
+            J = self._J(self.step)
+            L.og_coupled_step(self.g.ref, self.dt, _p3(self.E), _p3(self.H), psi,
+                              C.cast(_p3(J), C.c_void_p) if J is not None else None,
+                              _dp(th), self.T0, _dp(self.P), _dp(th2), _dp(self.Q) if accumulate_joule else None)
+            th, th2 = th2, th
+            self.step += 1
+            if accumulate_joule:
+                self.n_acc += 1
+        self.theta = th
 
     def joule_reset(self):
         self.Q[:] = 0.0

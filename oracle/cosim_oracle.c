@@ -23,6 +23,10 @@
  * with M = D_eps + dt/2 D_sigma, N = 2 D_eps - dt^2 S, K = D_eps - dt/2 D_sigma
  * and S = C^T D_{1/mu} C (Eq. 2-3), (dJ/dt)^n ~ (J^{n+1/2} - J^{n-1/2})/dt.
  * Joule power (Sec. II-A, P_total = D_sigma e^2) uses the time-centred edge field.
+ * Two-way coupling (Sec. II-A): sigma(T) = sigma0 / (1 + alpha (T - T0)) per
+ * voxel at the edge temperature (mean of the end nodes); the synchronized
+ * step (og_coupled_step) advances EM with D_sigma(T^n) and then T with the
+ * same dt and that step's Joule power.
  * Thermal (Eqs. 4-5): nodal forward Euler with M_kk = V0a^T D_k V0 (7-point).
  * Mechanics (Sec. II-B, Eqs. 7-9): HEX8, 2x2x2 Gauss, isotropic E_c(lambda,mu),
  * thermal strain alpha*dT*[1,1,1,0,0,0], von Mises at the element centroid.
@@ -258,8 +262,12 @@ void og_h_update(const og_grid *g, double dt, double *const E[3], double *const 
  *   ca = (Se - Ss dt/2) / (Se + Ss dt/2),  cb = dt W / (Se + Ss dt/2).
  * (curl H)_a = dH_c/db - dH_b/dc over dual lengths; an H unknown outside the
  * domain (beyond a wall) counts as zero. J may be NULL. */
-void og_e_update(const og_grid *g, double dt, double *const H[3], double *const E[3], double *psi,
-                 double *const J[3]) {
+static double edge_sigma_T(const og_grid *g, int a, const int n[3], const double *theta, double T_off);
+
+/* theta == NULL: the voxels' own conductivities; otherwise the conductivities
+ * at temperature T = theta + T_off (edge_sigma_T, Sec. II-A coupling). */
+static void e_update(const og_grid *g, double dt, double *const H[3], double *const E[3], double *psi,
+                     double *const J[3], const double *theta, double T_off) {
   cpml_tabs t;
   if (psi) cpml_build(g, 0, dt, &t);
   for (int a = 0; a < 3; a++) {
@@ -289,6 +297,7 @@ void og_e_update(const og_grid *g, double dt, double *const H[3], double *const 
           }
           double W, Se, Ss, Sk;
           edge_sums(g, a, n, &W, &Se, &Ss, &Sk);
+          if (theta) Ss = edge_sigma_T(g, a, n, theta, T_off);
           double den = Se + 0.5 * dt * Ss;
           double ca = (Se - 0.5 * dt * Ss) / den;
           double cb_ = dt * W / den;
@@ -297,6 +306,11 @@ void og_e_update(const og_grid *g, double dt, double *const H[3], double *const 
         }
   }
   if (psi) cpml_free(&t);
+}
+
+void og_e_update(const og_grid *g, double dt, double *const H[3], double *const E[3], double *psi,
+                 double *const J[3]) {
+  e_update(g, dt, H, E, psi, J, NULL, 0.0);
 }
 
 /* Joule heat of one step (Sec. II-A, P_total = D_sigma e^2): every edge
@@ -722,4 +736,87 @@ void og_von_mises(const og_grid *g, const double *u, const double *T, double Tre
   size_t nn = n_nodes(g);
   for (size_t d = 0; d < nn; d++)
     umag[d] = sqrt(u[3 * d] * u[3 * d] + u[3 * d + 1] * u[3 * d + 1] + u[3 * d + 2] * u[3 * d + 2]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Two-way electro-thermal coupling (Sec. II-A)                              */
+
+/* Electrical conductivity of material m at absolute temperature T_abs, the
+ * coupling law of Sec. II-A: sigma(T) = sigma0 / (1 + alpha (T - T0)), alpha
+ * the temperature coefficient of resistance. */
+static double sigma_at(const og_grid *g, int m, double T_abs) {
+  return prop(g, m, T_SIGMA) / (1.0 + prop(g, m, T_TCR) * (T_abs - prop(g, m, T_T0)));
+}
+
+/* Ss = sum_c w_c sigma_c(T_e) over the voxels of the edge of axis a at node n
+ * (the voxels and weights of edge_sums, in the same order), every voxel's
+ * conductivity taken at the edge temperature T_e = mean of the edge's two end
+ * nodes, T = theta + T_off. With alpha = 0 this is edge_sums' Ss exactly. */
+static double edge_sigma_T(const og_grid *g, int a, const int n[3], const double *theta, double T_off) {
+  int m1[3] = {n[0], n[1], n[2]};
+  m1[a] += 1;
+  const double Te = 0.5 * (theta[nid(g, n)] + theta[nid(g, m1)]) + T_off;
+  int b = (a + 1) % 3, c = (a + 2) % 3;
+  double Ss = 0.0;
+  for (int db = -1; db <= 0; db++)
+    for (int dc = -1; dc <= 0; dc++) {
+      int cell[3];
+      cell[a] = n[a];
+      cell[b] = n[b] + db;
+      cell[c] = n[c] + dc;
+      if (cell[b] < 0 || cell[b] >= n_of(g, b) || cell[c] < 0 || cell[c] >= n_of(g, c)) continue;
+      double w = 0.25 * g->h[b][cell[b]] * g->h[c][cell[c]];
+      Ss += w * sigma_at(g, voxel(g, cell), Te);
+    }
+  return Ss;
+}
+
+/* Joule power of one step with the conductivities at temperature theta
+ * (P_total = D_sigma(T) e^2 of Sec. II-A with the time-centred field): each
+ * edge's p_e = sigma_e(T) V_e ebar^2 [W], half to each end node; P is zeroed
+ * first. */
+void og_joule_power_T(const og_grid *g, double *const Eold[3], double *const Enew[3], const double *theta,
+                      double T_off, double *P) {
+  memset(P, 0, sizeof(double) * n_nodes(g));
+  for (int a = 0; a < 3; a++) {
+    int n[3];
+    for (n[2] = 0; n[2] <= g->nz; n[2]++)
+      for (n[1] = 0; n[1] <= g->ny; n[1]++)
+        for (n[0] = 0; n[0] <= g->nx; n[0]++) {
+          if (!e_valid(g, a, n)) continue;
+          size_t id = nid(g, n);
+          double eb = 0.5 * (Eold[a][id] + Enew[a][id]);
+          double p = edge_sigma_T(g, a, n, theta, T_off) * g->h[a][n[a]] * eb * eb;
+          int m[3] = {n[0], n[1], n[2]};
+          m[a] += 1;
+          P[id] += 0.5 * p;
+          P[nid(g, m)] += 0.5 * p;
+        }
+  }
+}
+
+/* One step of the synchronized electro-thermal marching of Sec. II-A, in the
+ * paper's order: the conductivities are taken at T^n (D_sigma(T^n) in M and
+ * K of Eq. 3), H and E advance one leapfrog step (Eqs. 2-3 in E/H form), the
+ * step's Joule power P^{n+1} = D_sigma(T^n) ebar^2 is formed, and the
+ * temperature takes one forward-Euler step of Eq. 5 with the same dt and
+ * that power: theta_out = theta + dt/C (sum G (theta_j - theta) + film + P).
+ * theta = T - T_off (kelvin); P receives P^{n+1} [W per node]; Q, if not
+ * NULL, accumulates the step's Joule energy dt P. */
+void og_coupled_step(const og_grid *g, double dt, double *const E[3], double *const H[3], double *psi,
+                     double *const J[3], const double *theta, double T_off, double *P, double *theta_out,
+                     double *Q) {
+  size_t nn = n_nodes(g);
+  og_h_update(g, dt, E, H, psi);
+  double *Eold[3];
+  for (int a = 0; a < 3; a++) {
+    Eold[a] = (double *)malloc(sizeof(double) * nn);
+    memcpy(Eold[a], E[a], sizeof(double) * nn);
+  }
+  e_update(g, dt, H, E, psi, J, theta, T_off);
+  og_joule_power_T(g, Eold, E, theta, T_off, P);
+  og_thermal_step(g, dt, theta, P, theta_out);
+  if (Q)
+    for (size_t i = 0; i < nn; i++) Q[i] += dt * P[i];
+  for (int a = 0; a < 3; a++) free(Eold[a]);
 }
