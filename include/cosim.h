@@ -120,6 +120,16 @@ cosim_status cosim_set_sources(cosim_ctx *ctx, int32_t n, const cosim_source *sr
 
 /* Flag for cosim_em_steps: accumulate the Joule energy of each step. */
 #define COSIM_ACCUM_JOULE 1u
+/* Flag for cosim_em_steps: the synchronized electro-thermal marching of
+ * Sec. II-A. Each step takes every edge's conductivity at the current
+ * temperature, sigma(T) = sigma0 / (1 + tcr (T - T0)) per voxel (material
+ * fields sigma0, tcr, T0) at the edge temperature (mean of its two end nodes),
+ * area-weighted over the edge's voxels as for sigma0; forms the step's Joule
+ * power P^{n+1} = D_sigma(T^n) ebar^2 per node (readable as COSIM_F_P, W);
+ * and advances the temperature one forward-Euler step of Eq. 5 with the EM
+ * time step and that power (convective faces included). Two launches per
+ * step. Combines with COSIM_ACCUM_JOULE. */
+#define COSIM_COUPLED_THERMAL 2u
 
 /* Advance the Maxwell system nsteps leapfrog steps (Eqs. 1-3 in E/H form):
  * H^{n+1/2} = H^{n-1/2} - dt/mu curl E^n;
@@ -129,7 +139,8 @@ cosim_status cosim_set_sources(cosim_ctx *ctx, int32_t n, const cosim_source *sr
  * over each face; CPML auxiliaries in the CPML layers; tangential E held at
  * zero on PEC walls. With COSIM_ACCUM_JOULE each step adds, for every edge,
  * sigma_e V_e ((E^n + E^{n+1})/2)^2 dt / 2 to the Joule energy of both end
- * nodes (P_total = D_sigma e^2, Sec. II-A). One kernel launch per step. */
+ * nodes (P_total = D_sigma e^2, Sec. II-A). One kernel launch per step (two
+ * with COSIM_COUPLED_THERMAL). flags: COSIM_ACCUM_JOULE, COSIM_COUPLED_THERMAL. */
 cosim_status cosim_em_steps(cosim_ctx *ctx, int64_t nsteps, uint32_t flags);
 
 /* Record nsteps EM steps (flags as for cosim_em_steps) into a CUDA graph held

@@ -21,6 +21,7 @@ COSIM_ERR_NOT_CONVERGED, COSIM_ERR_TIMEOUT, COSIM_ERR_NONFINITE = 4, 5, 6
 COSIM_FP64, COSIM_FP32 = 0, 1
 COSIM_BC_PEC, COSIM_BC_PMC, COSIM_BC_CPML = 0, 1, 2
 COSIM_ACCUM_JOULE = 1
+COSIM_COUPLED_THERMAL = 2
 COSIM_JOULE_RESET, COSIM_JOULE_FINALIZE_AVG_POWER, COSIM_JOULE_FINALIZE_ENERGY = 0, 1, 2
 COSIM_MECH_CLAMPED_BOTTOM, COSIM_MECH_KINEMATIC_MOUNT, COSIM_MECH_MASK = 0, 1, 2
 (COSIM_F_EX, COSIM_F_EY, COSIM_F_EZ, COSIM_F_HX, COSIM_F_HY, COSIM_F_HZ, COSIM_F_T, COSIM_F_Q, COSIM_F_P,
@@ -367,11 +368,15 @@ class Context:
     def set_sources(self, tables):
         cosim_set_sources(self.h, tables)
 
-    def em_steps(self, n, accumulate_joule=True):
-        cosim_em_steps(self.h, n, COSIM_ACCUM_JOULE if accumulate_joule else 0)
+    def em_steps(self, n, accumulate_joule=True, coupled=False):
+        """coupled: the synchronized electro-thermal marching (sigma(T), a
+        thermal step with the EM dt after every EM step)."""
+        cosim_em_steps(self.h, n, (COSIM_ACCUM_JOULE if accumulate_joule else 0)
+                       | (COSIM_COUPLED_THERMAL if coupled else 0))
 
-    def em_graph_capture(self, n, accumulate_joule=True):
-        cosim_em_graph_capture(self.h, n, COSIM_ACCUM_JOULE if accumulate_joule else 0)
+    def em_graph_capture(self, n, accumulate_joule=True, coupled=False):
+        cosim_em_graph_capture(self.h, n, (COSIM_ACCUM_JOULE if accumulate_joule else 0)
+                               | (COSIM_COUPLED_THERMAL if coupled else 0))
 
     def em_graph_launch(self, count=1):
         cosim_em_graph_launch(self.h, count)

@@ -31,7 +31,9 @@ enum : int {
   M_LAM = 5,   // Lame lambda
   M_MU = 6,    // Lame mu (shear modulus)
   M_BETA = 7,  // (3 lambda + 2 mu) alpha_L: thermal stress per kelvin
-  M_COLS = 8
+  M_TCR = 8,   // alpha: temperature coefficient of resistance
+  M_TC0 = 9,   // 1 + alpha (T_init - T0): sigma(T) = sigma0 / (M_TC0 + M_TCR (T - T_init))
+  M_COLS = 12  // (two spare columns keep rows 16-byte aligned)
 };
 
 template <typename R>

@@ -61,7 +61,7 @@ struct cosim_ctx {
   void *xE[2][3][2]{}, *dE[2][3][2]{}, *xH[2][3][2]{}, *dH[2][3][2]{};
   void *lE[2][3][2]{}, *lH[2][3][2]{};
   // TMA descriptors of E, H (per parity and component) and the Joule window
-  CUtensorMap tmE[2][3], tmH[2][3], tmQ;
+  CUtensorMap tmE[2][3], tmH[2][3], tmQ, tmT[2];
   int *dev_err = nullptr;  // device word: a bounded in-kernel wait gave up
   int slo[3]{}, shi[3]{}, sn[3]{};
   long long psi_len[3]{};
@@ -72,8 +72,8 @@ struct cosim_ctx {
   // the E/H parity it starts from, kernels per replay
   cudaGraphExec_t gexec = nullptr;
   int64_t g_nsteps = 0, g_launches = 0;
-  bool g_accum = false;
-  int g_par = 0;
+  bool g_accum = false, g_coupled = false;
+  int g_par = 0, g_tpar = 0;
   long long launches = 0;  // kernels launched by this context
   double *Q = nullptr;      // Joule energy per node, FP64
   void *Qs = nullptr;       // short-window Joule accumulator (context precision)
@@ -288,10 +288,13 @@ static cudaError_t set_smem_limits() {
   if (e != cudaSuccess) return e;
   const int em =
       (int)(em_stage_offset<R, kEmTX, kEmTY>(kMaxMat) + kEmStages * sizeof(EmStage<R, kEmTX, kEmTY>) + 128);
-  e = cudaFuncSetAttribute(em_step_kernel<R, int, kEmTX, kEmTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, em);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(em_step_kernel<R, long long, kEmTX, kEmTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              em);
+  const void *kernels[4] = {(const void *)em_step_kernel<R, int, kEmTX, kEmTY, false>,
+                            (const void *)em_step_kernel<R, long long, kEmTX, kEmTY, false>,
+                            (const void *)em_step_kernel<R, int, kEmTX, kEmTY, true>,
+                            (const void *)em_step_kernel<R, long long, kEmTX, kEmTY, true>};
+  for (const void *k : kernels)
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, em)) != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 // TMA descriptor of a padded node array (x fastest, pitch px, planes of
@@ -411,7 +414,10 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
     r[M_LAM] = lam;
     r[M_MU] = mu;
     r[M_BETA] = (3 * lam + 2 * mu) * q.alpha_L;
+    r[M_TCR] = q.tcr;
+    r[M_TC0] = 1.0 + q.tcr * (c->T_init - q.T0);
   }
+  mt[c->mats.size() * M_COLS + M_TC0] = 1.0;  // the zero row: sigma(T) = 0 / 1
   cosim_status st;
   if ((st = upload_real(c, &c->mtab, mt)) != COSIM_OK) return st;
   if (c->prec == COSIM_FP64)
@@ -499,6 +505,8 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
   ALLOC(c, c->T[0], c->npad * c->rsz);
   ALLOC(c, c->T[1], c->npad * c->rsz);
   ALLOC(c, c->P, c->npad * c->rsz);
+  for (int p = 0; p < 2; ++p)
+    if ((st = encode_node_map(c, &c->tmT[p], c->T[p], kEmTY + 1)) != COSIM_OK) return st;
   ALLOC(c, c->scratch, c->npad * 8);
   const int mv_blocks = ((c->nx + 1) + kMvTX - 2) / (kMvTX - 1) * (((c->ny + 1) + kMvTY - 2) / (kMvTY - 1));
   c->npart = std::max(kRedBlocks, mv_blocks);
@@ -634,7 +642,17 @@ extern "C" cosim_status cosim_set_sources(cosim_ctx *c, int32_t n, const cosim_s
 constexpr int kJouleWindow = 32;  // EM steps per short-window Joule accumulation
 
 template <typename R>
-static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum) {
+static ThArgs<R> th_args(cosim_ctx *c);
+
+template <typename R, typename I, bool CPL>
+static void launch_em(const dim3 &grd, const dim3 &blk, size_t smem, cudaStream_t st, const EmArgs<R> &A) {
+  em_step_kernel<R, I, kEmTX, kEmTY, CPL><<<grd, blk, smem, st>>>(A);
+}
+
+// coupled: the synchronized marching of Sec. II-A (sigma(T^n) in the EM step,
+// then one thermal step with the EM dt and that step's Joule power)
+template <typename R>
+static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum, bool coupled) {
   EmArgs<R> A;
   A.g = make_geo<R>(c);
   for (int a = 0; a < 3; ++a) {
@@ -703,12 +721,27 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum) {
     A.step_base = c->dstep;
     A.step_off = (int)s;
     A.fold = accum && ((c->n_acc + 1) % kJouleWindow == 0);
-    if (c->npad < (1LL << 31))
-      em_step_kernel<R, int, kEmTX, kEmTY><<<grd, blk, smem, c->stream>>>(A);
+    A.tmT = c->tmT[c->tpar];
+    A.Pout = (R *)c->P;
+    A.inv_dt = (R)(1.0 / c->dt);
+    const bool small = c->npad < (1LL << 31);
+    if (coupled)
+      small ? launch_em<R, int, true>(grd, blk, smem, c->stream, A)
+            : launch_em<R, long long, true>(grd, blk, smem, c->stream, A);
     else
-      em_step_kernel<R, long long, kEmTX, kEmTY><<<grd, blk, smem, c->stream>>>(A);
+      small ? launch_em<R, int, false>(grd, blk, smem, c->stream, A)
+            : launch_em<R, long long, false>(grd, blk, smem, c->stream, A);
     ++c->launches;
     CHECK_LAUNCH(c);
+    if (coupled) {  // T^{n+1} = T^n + dt/C (-M_kk T^n + P^{n+1}) with the EM dt (Eq. 5)
+      ThArgs<R> TA = th_args<R>(c);
+      TA.dt = (R)c->dt;
+      const dim3 tb(32, 8), tg((c->nx + 1 + 31) / 32, (c->ny + 1 + 7) / 8);
+      thermal_kernel<R, 0><<<tg, tb, c->mats.size() * M_COLS * sizeof(R), c->stream>>>(TA);
+      ++c->launches;
+      CHECK_LAUNCH(c);
+      c->tpar ^= 1;
+    }
     c->par ^= 1;
     c->step++;
     if (accum) {
@@ -724,11 +757,12 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum) {
   return COSIM_OK;
 }
 
-static cosim_status em_steps_any(cosim_ctx *c, int64_t nsteps, bool acc) {
+static cosim_status em_steps_any(cosim_ctx *c, int64_t nsteps, bool acc, bool coupled) {
   // groups of at most 2^30 steps keep the per-launch offset an int
   while (nsteps > 0) {
     const int64_t n = std::min<int64_t>(nsteps, 1LL << 30);
-    const cosim_status st = c->prec == COSIM_FP64 ? em_steps_t<double>(c, n, acc) : em_steps_t<float>(c, n, acc);
+    const cosim_status st =
+        c->prec == COSIM_FP64 ? em_steps_t<double>(c, n, acc, coupled) : em_steps_t<float>(c, n, acc, coupled);
     if (st != COSIM_OK) return st;
     nsteps -= n;
   }
@@ -737,8 +771,9 @@ static cosim_status em_steps_any(cosim_ctx *c, int64_t nsteps, bool acc) {
 
 extern "C" cosim_status cosim_em_steps(cosim_ctx *c, int64_t nsteps, uint32_t flags) {
   if (!c) return COSIM_ERR_INVALID;
-  if (nsteps < 0 || (flags & ~COSIM_ACCUM_JOULE)) return fail(c, COSIM_ERR_INVALID, "bad nsteps or flags");
-  return em_steps_any(c, nsteps, flags & COSIM_ACCUM_JOULE);
+  if (nsteps < 0 || (flags & ~(COSIM_ACCUM_JOULE | COSIM_COUPLED_THERMAL)))
+    return fail(c, COSIM_ERR_INVALID, "bad nsteps or flags");
+  return em_steps_any(c, nsteps, flags & COSIM_ACCUM_JOULE, flags & COSIM_COUPLED_THERMAL);
 }
 
 static void drop_graph(cosim_ctx *c) {
@@ -749,7 +784,8 @@ static void drop_graph(cosim_ctx *c) {
 
 extern "C" cosim_status cosim_em_graph_capture(cosim_ctx *c, int64_t nsteps, uint32_t flags) {
   if (!c) return COSIM_ERR_INVALID;
-  if (nsteps <= 0 || nsteps % kJouleWindow != 0 || nsteps > (1LL << 30) || (flags & ~COSIM_ACCUM_JOULE))
+  if (nsteps <= 0 || nsteps % kJouleWindow != 0 || nsteps > (1LL << 30) ||
+      (flags & ~(COSIM_ACCUM_JOULE | COSIM_COUPLED_THERMAL)))
     return fail(c, COSIM_ERR_INVALID, "graph steps must be a positive multiple of 32 (the Joule window), <= 2^30");
   if (c->stream == nullptr) return fail(c, COSIM_ERR_INVALID, "graph capture needs a non-default stream");
   const bool acc = flags & COSIM_ACCUM_JOULE;
@@ -763,11 +799,13 @@ extern "C" cosim_status cosim_em_graph_capture(cosim_ctx *c, int64_t nsteps, uin
   const int par = c->par;
   const bool dirty = c->qs_dirty;
   CHECK_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  cosim_status st = em_steps_any(c, nsteps, acc);
+  const bool cpl = flags & COSIM_COUPLED_THERMAL;
+  const int tpar = c->tpar;
+  cosim_status st = em_steps_any(c, nsteps, acc, cpl);
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
   const long long captured = c->launches - launches;
-  c->step = step, c->n_acc = n_acc, c->launches = launches, c->par = par, c->qs_dirty = dirty;
+  c->step = step, c->n_acc = n_acc, c->launches = launches, c->par = par, c->qs_dirty = dirty, c->tpar = tpar;
   if (st != COSIM_OK) {
     if (graph) cudaGraphDestroy(graph);
     return st;
@@ -785,7 +823,9 @@ extern "C" cosim_status cosim_em_graph_capture(cosim_ctx *c, int64_t nsteps, uin
   }
   c->g_nsteps = nsteps;
   c->g_accum = acc;
+  c->g_coupled = cpl;
   c->g_par = par;
+  c->g_tpar = tpar;
   c->g_launches = captured;
   return COSIM_OK;
 }
@@ -795,6 +835,8 @@ extern "C" cosim_status cosim_em_graph_launch(cosim_ctx *c, int64_t count) {
   if (count < 0) return fail(c, COSIM_ERR_INVALID, "bad count");
   if (!c->gexec) return fail(c, COSIM_ERR_INVALID, "no captured EM graph");
   if (c->par != c->g_par) return fail(c, COSIM_ERR_INVALID, "the E/H parity differs from the captured one");
+  if (c->g_coupled && c->tpar != c->g_tpar)
+    return fail(c, COSIM_ERR_INVALID, "the temperature buffer parity differs from the captured one");
   if (c->g_accum && c->n_acc % kJouleWindow != 0)
     return fail(c, COSIM_ERR_INVALID, "Joule window position differs from the captured one");
   for (int64_t r = 0; r < count; ++r) {

@@ -82,6 +82,12 @@ struct EmArgs {
   // arrays (x, y, z) with boxes of kEmBoxX x (TY+1 for E, TY otherwise) x 1
   CUtensorMap tmE[3], tmH[3], tmQ;
   CUtensorMap tmV;  // voxel IDs (x, y, z), box em_vox_box_x x (TY+1) x 1
+  // two-way coupling (the CPL specialisation, Sec. II-A): the temperature
+  // rise T^n - T_init (node array, staged like E), the step's Joule power per
+  // node written to Pout [W], 1 / dt
+  CUtensorMap tmT;
+  R *Pout;
+  R inv_dt;
   const R *zt;      // per node plane: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
   int *err;         // set to 1 when a bounded wait for a staged plane gave up
 };
@@ -224,6 +230,7 @@ struct EmStage {
   EmBox<uint8_t, TY + 1, em_vox_box_x<TX>()> V;  // voxel IDs of layer k, rows j0-1 .. j0+TY-1
   EmBox<int, 1, em_src_box<TY>()> S;             // source-row offsets of plane k
   EmBox<R, 1, 4> Z;                              // hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
+  EmBox<R, TY + 1, em_box_x<TX>()> T;            // temperature rise (coupled steps only)
 };
 
 constexpr int kCpmlTable = 6 * kMaxSlab;  // (1 - b) per [axis][E,H][slab position]
@@ -258,7 +265,7 @@ static_assert(kEmAhead >= 2 && kEmAhead <= kEmStages - 1, "prefetch distance mus
 // z-direction slab and walls remain, decided per plane for the whole CTA).
 // I: index type of node offsets (int when the padded node arrays have fewer
 // than 2^31 elements, long long otherwise).
-template <typename R, typename I, int TX, int TY, bool BORDER>
+template <typename R, typename I, int TX, int TY, bool BORDER, bool CPL>
 __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
                                         EmStage<R, TX, TY> *stg, R (*sHxz)[TY][TX], R (*sQy)[TX], uint64_t *bars,
                                         int *s_abort) {
@@ -287,8 +294,9 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
   const int xvr = (i0 - 1) & 15, xv0 = (i0 - 1) - xvr;
   const bool has_src = A.src_row != nullptr;
   // transaction bytes of one stage: the boxes themselves, not their padding
-  const unsigned fixed_bytes = (unsigned)((6 * TY + 3 + (accum ? TY : 0)) * em_box_x<TX>() * (int)sizeof(R) +
-                                          4 * (int)sizeof(R) + (has_src ? em_src_box<TY>() * 4 : 0));
+  const unsigned fixed_bytes =
+      (unsigned)((6 * TY + 3 + (accum ? TY : 0) + (CPL ? TY + 1 : 0)) * em_box_x<TX>() * (int)sizeof(R) +
+                 4 * (int)sizeof(R) + (has_src ? em_src_box<TY>() * 4 : 0));
   const unsigned vox_bytes = (unsigned)((TY + 1) * em_vox_box_x<TX>());
   auto issue = [&](int k) {
     if (k > nz) return;
@@ -301,6 +309,7 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
       tma_load_3d(&S.H[c].v[0][0], &A.tmH[c], x0, j0, k, &bars[s]);
     }
     if (accum) tma_load_3d(&S.Qs.v[0][0], &A.tmQ, x0, j0, k, &bars[s]);
+    if (CPL) tma_load_3d(&S.T.v[0][0], &A.tmT, x0, j0, k, &bars[s]);
     if (k < nz) tma_load_3d(&S.V.v[0][0], &A.tmV, xv0, j0 - 1, k, &bars[s]);
     bulk_load(&S.Z.v[0][0], A.zt + 4 * (size_t)k, 4 * sizeof(R), &bars[s]);
     if (has_src) {  // 16-byte aligned: src_row itself is, the start is a multiple of 4 from -4
@@ -344,6 +353,13 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
   // zero below the grid
   R pxe_b = 0, pxs_b = 0, pye_b = 0, pys_b = 0, u11_b = 0;
   R q_pend = 0;  // Joule sum of node (i, j, k-1) still missing the y-edge share from j-1
+  R e_pend = 0;  // the same without the accumulator's earlier energy (this step's only)
+  int b01 = vd, b10 = vd, b11 = vd;  // coupled steps: material rows of layer k-1
+  // sigma dt / 2 of a voxel at the edge temperature rise te (coupled steps):
+  // sigma0 dt/2 / (1 + alpha (T_init + te - T0)) = M_SDT2 / (M_TC0 + M_TCR te)
+  auto sig = [&](int row, R te) -> R {
+    return s_mt[row + M_SDT2] * em_rcp(s_mt[row + M_TC0] + s_mt[row + M_TCR] * te);
+  };
 
   for (int k = 0; k <= nz; ++k) {
     if (leader) {  // the stage of plane k-1 is free: every thread passed the last barrier
@@ -375,6 +391,7 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
         A.Qs[id - plane] = s;
       }
     }
+    if (CPL && own && k > 0) A.Pout[id - plane] = (e_pend + sQy[ty - 1][tx]) * A.inv_dt;
     const EmStage<R, TX, TY> &S0 = stg[k & (kEmStages - 1)];
     const EmStage<R, TX, TY> &S1 = stg[(k + 1) & (kEmStages - 1)];
     R hz0, ihz, idz, hzm;
@@ -403,6 +420,14 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
     const R ez_ip = S0.E[2].v[ty][cx + 1], ey_ip = S0.E[1].v[ty][cx + 1];
     const R hx_o = S0.H[0].v[ty][cx], hy_o = S0.H[1].v[ty][cx], hz_o = S0.H[2].v[ty][cx];
     const R q_old = accum ? S0.Qs.v[ty][cx] : R(0);
+    // coupled steps: temperature rise at this node and its +x, +y, +z neighbours
+    R th = 0, th_ip = 0, th_jp = 0, th_kp = 0;
+    if (CPL) {
+      th = S0.T.v[ty][cx];
+      th_ip = S0.T.v[ty][cx + 1];
+      th_jp = S0.T.v[ty + 1][cx];
+      th_kp = k < nz ? S1.T.v[ty][cx] : R(0);
+    }
 
     // material constants of voxel layer k
     // (columns M_EPS, M_SDT2, M_IMU, M_K are adjacent: one vector load per voxel)
@@ -462,8 +487,12 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
       const R d1 = (Hz - sHxz[1][ty - 1][tx]) * idy;
       const R d2 = (Hy - hy_km1) * idz;
       const R curl = curl_with_psi(A, s_cp, 0, 0, 1, syE, 2, szE, i, j, k, d1, d2, own);
-      exn = e_update(ex, dtWx_y * (hzm + hz0), curl - Jx, hzm * pxe_b + hz0 * pxe_a, hzm * pxs_b + hz0 * pxs_a, lqx,
-                     &qx);
+      R Ss = hzm * pxs_b + hz0 * pxs_a;
+      if (CPL) {
+        const R te = R(0.5) * (th + th_ip);
+        Ss = hzm * (hym * sig(b01, te) + hy0 * sig(b11, te)) + hz0 * (hym * sig(a01, te) + hy0 * sig(a11, te));
+      }
+      exn = e_update(ex, dtWx_y * (hzm + hz0), curl - Jx, hzm * pxe_b + hz0 * pxe_a, Ss, lqx, &qx);
     }
     // (interior tiles also run Ey / Ez on the halo lane tx = 0 and discard
     // them: the warp stays convergent; only the owners store)
@@ -471,15 +500,23 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
       const R d1 = (Hx - hx_km1) * idz;
       const R d2 = (Hz - hz_l) * idx;
       const R curl = curl_with_psi(A, s_cp, 0, 1, 2, szE, 0, sxE, i, j, k, d1, d2, own);
-      eyn = e_update(ey, dtWy_x * (hzm + hz0), curl - Jy, hzm * pye_b + hz0 * pye_a, hzm * pys_b + hz0 * pys_a, lqy,
-                     &qy);
+      R Ss = hzm * pys_b + hz0 * pys_a;
+      if (CPL) {
+        const R te = R(0.5) * (th + th_jp);
+        Ss = hzm * (hxm * sig(b10, te) + hx0 * sig(b11, te)) + hz0 * (hxm * sig(a10, te) + hx0 * sig(a11, te));
+      }
+      eyn = e_update(ey, dtWy_x * (hzm + hz0), curl - Jy, hzm * pye_b + hz0 * pye_a, Ss, lqy, &qy);
     }
     if ((BORDER ? own : ty > 0) && k < nz && !(fix_x || fix_y)) {  // Ez: dHy/dx - dHx/dy, voxels (i-1..i, j-1..j, k)
       const R d1 = (Hy - hy_l) * idx;
       const R d2 = (Hx - sHxz[0][ty - 1][tx]) * idy;
       const R curl = curl_with_psi(A, s_cp, 0, 2, 0, sxE, 1, syE, i, j, k, d1, d2, own);
       const R Se = hym * (hxm * e00 + hx0 * e01) + hy0 * (hxm * e10 + hx0 * e11);
-      const R Ss = hym * (hxm * s00 + hx0 * s01) + hy0 * (hxm * s10 + hx0 * s11);
+      R Ss = hym * (hxm * s00 + hx0 * s01) + hy0 * (hxm * s10 + hx0 * s11);
+      if (CPL) {
+        const R te = R(0.5) * (th + th_kp);
+        Ss = hym * (hxm * sig(a00, te) + hx0 * sig(a01, te)) + hy0 * (hxm * sig(a10, te) + hx0 * sig(a11, te));
+      }
       ezn = e_update(ez, dtWx_y * (hxm + hx0), curl - Jz, Se, Ss, R(0.25) * hz0, &qz);
     }
     const R qx_l = __shfl_up_sync(0xffffffffu, qx, 1);  // x-edge share from node i-1
@@ -493,7 +530,8 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
       A.En[1][id] = eyn;
       if (k < nz) A.En[2][id] = ezn;
     }
-    q_pend = q_old + ((qx + qx_l) + qy + (qz + qz_km1));
+    e_pend = (qx + qx_l) + qy + (qz + qz_km1);
+    q_pend = q_old + e_pend;
     hx_km1 = Hx;
     hy_km1 = Hy;
     qz_km1 = qz;
@@ -502,6 +540,11 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
     pye_b = pye_a;
     pys_b = pys_a;
     u11_b = u11;
+    if (CPL) {
+      b01 = a01;
+      b10 = a10;
+      b11 = a11;
+    }
   }
   __syncthreads();
   if (accum && own) {  // Joule energy of the top plane k = nz
@@ -514,11 +557,12 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
       A.Qs[id] = s;
     }
   }
+  if (CPL && own) A.Pout[id0 + (I)nz * plane] = (e_pend + sQy[ty - 1][tx]) * A.inv_dt;
 }
 
 // One launch per step over all tiles; tiles in [ibx0, ibx1) x [iby0, iby1)
 // take the interior specialisation.
-template <typename R, typename I, int TX, int TY>
+template <typename R, typename I, int TX, int TY, bool CPL>
 __global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? COSIM_EM_MIN_CTAS : 2)
     em_step_kernel(const __grid_constant__ EmArgs<R> A) {
   static_assert(TX == 32, "a tile row is one warp: x neighbours are exchanged by shuffles");
@@ -553,9 +597,9 @@ __global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? COSIM_EM_MIN_CTAS : 2
   const bool interior = (int)blockIdx.x >= A.ibx0 && (int)blockIdx.x < A.ibx1 && (int)blockIdx.y >= A.iby0 &&
                         (int)blockIdx.y < A.iby1;
   if (interior)
-    em_tile<R, I, TX, TY, false>(A, s_cp, s_mt, stg, sHxz, sQy, s_bar, &s_abort);
+    em_tile<R, I, TX, TY, false, CPL>(A, s_cp, s_mt, stg, sHxz, sQy, s_bar, &s_abort);
   else
-    em_tile<R, I, TX, TY, true>(A, s_cp, s_mt, stg, sHxz, sQy, s_bar, &s_abort);
+    em_tile<R, I, TX, TY, true, CPL>(A, s_cp, s_mt, stg, sHxz, sQy, s_bar, &s_abort);
 }
 
 // advance the device-resident source time index after a group of steps
