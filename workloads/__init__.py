@@ -10,6 +10,8 @@ from .package import (  # noqa: F401
     Material, Source, Problem,
     COPPER, DIELECTRIC, SILICON, UNDERFILL,
     BC_PEC, BC_PMC, BC_CPML,
-    tiny_package, layered_package, full_package, uniform_box, crop,
+    tiny_package, layered_package, full_package, uniform_box, crop, paper_setup_package,
 )
-from .waveforms import GaussianDerivative, PRBSBurst, Sampled  # noqa: F401
+from .waveforms import (  # noqa: F401
+    GaussianDerivative, PRBSBurst, Sampled, Jitter, Ricker, Sine, GaussianPulseTrain, Scaled,
+)

@@ -330,3 +330,81 @@ def crop(p: Problem, lo, hi) -> Problem:
         dx=p.dx[i0:i1].copy(), dy=p.dy[j0:j1].copy(), dz=p.dz[k0:k1].copy(),
         mat=np.ascontiguousarray(p.mat[k0:k1, j0:j1, i0:i1]),
         em_bc=tuple(bc), h_conv=tuple(h), sources=srcs))
+
+
+def paper_setup_package(nx: int = 192, ny: int = 192, nz: int = 64, seed: int = 7, n_pairs: int = 8,
+                        n_gsg: int = 8, port_current: float = 10e-3) -> Problem:
+    """The paper's boundary and excitation scheme (Sec. III-B) on the layered
+    synthetic stack (``layered_package`` geometry):
+
+    * EM walls: PMC on the four sides and the top, PEC ground plane at z = 0;
+      thermal: adiabatic on every face (no film); no CPML;
+    * substrate: ``n_pairs`` differential port pairs, x-oriented, on adjacent
+      x-running tracks of the top x-routing layer, polarity alternating along
+      y, driven by the Ricker trigger (t0 = 40 ps);
+    * bump arrays: ``n_gsg`` ground-signal-ground triples along x under the
+      "logic" chiplets (the two with the lower y) carrying the 5 GHz sine,
+      and as many under the "HBM" chiplets carrying the 40 GHz 3-bit data
+      burst; within a triple the signal bump carries +J and each ground bump
+      -J/2 (x-directed edges), so the feed sinks its own current;
+    * every port has its own seeded jitter (+-20 % amplitude, +-10 % width,
+      +-10 ps timing); the two halves of a differential pair are jittered
+      independently, so they do not cancel exactly.
+    The observation window is 300 ps."""
+    from .waveforms import GaussianPulseTrain, Jitter, Ricker, Scaled, Sine
+    base = layered_package(nx, ny, seed=seed, nz=nz, n_lines=0)
+    mat = base.mat
+    z_sub, z_int, z_bump, z_die, routing = _stack(nz)
+    rng = np.random.default_rng(seed + 101)
+    dx, dy, dz = base.dx, base.dy, base.dz
+    sources = []
+    port = 0
+    # differential pairs: rows j, j + 5 of the top x-running routing layer
+    zr = [z for r, z in enumerate(routing) if r % 2 == 0][-1]
+    layer = mat[zr] == M_CU
+    cand = []
+    for j in range(6, ny - 12, 5):
+        for i in range(nx // 8, nx - nx // 8):
+            if layer[j, i] and layer[j + 5, i]:
+                cand.append((i, j))
+                break
+    pick = rng.choice(len(cand), size=min(n_pairs, len(cand)), replace=False) if cand else []
+    for q in sorted(int(x) for x in pick):
+        i, j = cand[q]
+        for n_side, jj in enumerate((j, j + 5)):
+            sign = 1.0 if (n_side + q) % 2 == 0 else -1.0  # alternating polarity along y
+            edges = [(i, jj + dj, k) for dj in (0, 1) for k in (zr, zr + 1)]
+            j0 = port_current / (dy[jj] * dz[zr])
+            sources.append(Source(axis=0, edges=np.array(edges, np.int32),
+                                  waveform=Scaled(Ricker(j0, jitter=Jitter.seeded(seed * 7919 + port)), sign)))
+            port += 1
+    # G-S-G triples on the bump layer, x-directed, 2x2-voxel bumps at 4-voxel pitch
+    kb = (z_bump[0] + z_bump[1]) // 2
+    bumps = mat[kb] == M_CU
+    # bump corners (voxel (i, j) with bump voxels at i, i+1 and j, j+1)
+    corners = [(i, j) for j in range(1, ny - 2) for i in range(1, nx - 10)
+               if bumps[j, i] and bumps[j + 1, i + 1] and not bumps[j, i - 1] and not bumps[j - 1, i]]
+    trip = [(i, j) for (i, j) in corners if bumps[j, i + 4] and bumps[j, i + 8]]
+    logic = [t for t in trip if t[1] < ny // 2]
+    hbm = [t for t in trip if t[1] >= ny // 2]
+    for group, kind in ((logic, "sine"), (hbm, "burst")):
+        if not group:
+            continue
+        sel = rng.choice(len(group), size=min(n_gsg, len(group)), replace=False)
+        for q in sorted(int(x) for x in sel):
+            i, j = group[q]
+            jit = Jitter.seeded(seed * 7919 + port)
+            j0 = port_current / (2 * dy[j] * dz[kb])
+            if kind == "sine":
+                w = Sine(j0, jitter=jit)
+            else:
+                bits = tuple(int(b) for b in rng.integers(0, 2, 3))
+                w = GaussianPulseTrain(j0, bits=bits if any(bits) else (1, 0, 1), jitter=jit)
+            for di, share in ((0, -0.5), (4, 1.0), (8, -0.5)):  # ground, signal, ground
+                edges = [(i + di + ex, j + ey, kb) for ex in (0, 1) for ey in (0, 1, 2)]
+                sources.append(Source(axis=0, edges=np.array(edges, np.int32), waveform=Scaled(w, share)))
+            port += 1
+    p = replace(base, name=f"paper_setup_{nx}x{ny}x{nz}",
+                em_bc=(BC_PMC, BC_PMC, BC_PMC, BC_PMC, BC_PEC, BC_PMC), cpml_cells=0,
+                h_conv=(0.0,) * 6, sources=sources, em_steps=0)
+    return _check(p)

@@ -82,3 +82,94 @@ class Sampled:
         m = min(nsteps, len(self.values))
         v[:m] = self.values[:m]
         return v
+
+
+# ---- the paper's transient excitation scheme (Sec. III-B): a broadband
+# trigger, background logic noise and a high-speed data burst, each with
+# deterministic per-port jitter of amplitude, pulse width and timing.
+
+@dataclass(frozen=True)
+class Jitter:
+    """Per-port variation: amplitude factor, width factor, time shift [s]."""
+    amp: float = 1.0
+    width: float = 1.0
+    shift: float = 0.0
+
+    @staticmethod
+    def seeded(seed: int, amp=0.20, width=0.10, shift=10e-12) -> "Jitter":
+        """Uniform in +-amp (relative), +-width (relative), +-shift (s)."""
+        r = np.random.default_rng(seed).uniform(-1.0, 1.0, 3)
+        return Jitter(1.0 + amp * r[0], 1.0 + width * r[1], shift * r[2])
+
+
+@dataclass
+class Ricker:
+    """Ricker wavelet J(t) = J0 (1 - 2 a) exp(-a), a = (pi f (t - t0))^2.
+
+    Peak J0 at t0; zero mean; its envelope exp(-a) falls to e^-9 at
+    |t - t0| = 3 / (pi f), so f = 50 GHz confines it to t0 +- 19 ps (the
+    paper's 20-60 ps trigger with t0 = 40 ps). Jitter scales J0, divides f by
+    the width factor and shifts t0."""
+    j0: float
+    t0: float = 40e-12
+    f: float = 50e9
+    jitter: Jitter = Jitter()
+
+    def __call__(self, t):
+        t = np.asarray(t, dtype=np.float64)
+        f = self.f / self.jitter.width
+        a = (np.pi * f * (t - (self.t0 + self.jitter.shift))) ** 2
+        return self.j0 * self.jitter.amp * (1.0 - 2.0 * a) * np.exp(-a)
+
+
+@dataclass
+class Sine:
+    """Continuous J0 sin(2 pi f (t - shift)) on [t_on, t_off) (the paper's
+    5 GHz logic noise on 0-300 ps); width jitter scales the period."""
+    j0: float
+    f: float = 5e9
+    t_on: float = 0.0
+    t_off: float = 300e-12
+    jitter: Jitter = Jitter()
+
+    def __call__(self, t):
+        t = np.asarray(t, dtype=np.float64)
+        f = self.f / self.jitter.width
+        on = (t >= self.t_on) & (t < self.t_off)
+        return np.where(on, self.j0 * self.jitter.amp * np.sin(2.0 * np.pi * f * (t - self.jitter.shift)), 0.0)
+
+
+@dataclass
+class GaussianPulseTrain:
+    """A carrier J0 sin(2 pi f_c t) modulated by n_bits Gaussian pulses, one
+    per bit slot of [t_on, t_off) (centred in the slot, sigma = slot/6, so a
+    pulse has fallen to e^-4.5 at the slot edges) and present where the bit
+    is 1 (the paper's 40 GHz data burst, 3 bits on 80-230 ps). Jitter scales
+    J0 and the pulse width and shifts the whole train."""
+    j0: float
+    bits: tuple = (1, 0, 1)
+    f_c: float = 40e9
+    t_on: float = 80e-12
+    t_off: float = 230e-12
+    jitter: Jitter = Jitter()
+
+    def __call__(self, t):
+        t = np.asarray(t, dtype=np.float64) - self.jitter.shift
+        slot = (self.t_off - self.t_on) / len(self.bits)
+        s = slot / 6.0 * self.jitter.width
+        env = np.zeros_like(t)
+        for b, bit in enumerate(self.bits):
+            if bit:
+                c = self.t_on + (b + 0.5) * slot
+                env += np.exp(-0.5 * ((t - c) / s) ** 2)
+        return self.j0 * self.jitter.amp * env * np.sin(2.0 * np.pi * self.f_c * t)
+
+
+@dataclass
+class Scaled:
+    """sign * waveform(t): a port's share of a differential or G-S-G feed."""
+    waveform: object
+    sign: float
+
+    def __call__(self, t):
+        return self.sign * self.waveform(t)
