@@ -292,12 +292,23 @@ def serving_arm(args, workers=4):
     rate = 0.8 / per_design
     arr = S.poisson_arrivals(len(specs), rate, seed=11)
     rep = S.serve(specs, arr, runner.run, workers=workers, footprint=S.footprint_bytes)
+    # the plain form on the same GPU: one design at a time, step-by-step
+    # launches, default launch shapes, everything queued at t = 0
+    plain = S.DesignRunner(specs, workers=1, use_graph=False, autotune=False)
+    plain.run(specs[0], 0)
+    rep_plain = S.serve(specs, [0.0] * len(specs), plain.run, workers=1, footprint=S.footprint_bytes)
+    same = all(abs(rep["records"][q].result["joule_J"] / rep_plain["records"][q].result["joule_J"] - 1) < 1e-5
+               and rep["records"][q].result["cg_iters"] == rep_plain["records"][q].result["cg_iters"]
+               for q in range(len(specs)))
     cells = sum(s.cells for s in specs)
     return {"variant": "burst-length-scaled (%d EM steps per request, not the 2 ns burst), ~80%% offered load"
                        % specs[0].em_steps,
             "requests": len(specs), "workers": workers, "arrival_rate_per_s": round(rate, 3),
             "p50_s": round(rep["p50_s"], 4), "p99_s": round(rep["p99_s"], 4),
             "designs_per_hour": round(rep["designs_per_hour"], 1), "makespan_s": round(rep["makespan_s"], 3),
+            "plain_designs_per_hour": round(rep_plain["designs_per_hour"], 1),
+            "plain_note": "same requests one at a time, no graphs, default launch shapes, all queued at t=0",
+            "plain_results_match": bool(same),
             "mean_cells": int(cells / len(specs)), "em_path": "captured CUDA graph, 32-step windows"}
 
 

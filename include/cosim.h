@@ -158,6 +158,24 @@ cosim_status cosim_em_graph_capture(cosim_ctx *ctx, int64_t nsteps, uint32_t fla
  * E/H parity or Joule window position differs from the captured one. */
 cosim_status cosim_em_graph_launch(cosim_ctx *ctx, int64_t count);
 
+/* Flags for cosim_autotune. FORCE: time the variants again even if this
+ * grid shape was tuned before in this process. FIXED: no timing; take the
+ * heights from *em_tile_y (8, or 4 for FP32) and *th_block_y (4, 8, 16). */
+#define COSIM_TUNE_FORCE 1u
+#define COSIM_TUNE_FIXED 2u
+
+/* Pick the launch shapes for this context's grid by timing the variants on
+ * the context itself: the EM tile height (8 or 4 rows of threads; FP32
+ * contexts, steps without COSIM_COUPLED_THERMAL) and the thermal kernel's
+ * block height (4, 8 or 16). Timing launches only read the current fields
+ * and write spare buffers, so the context's state and step count are
+ * unchanged; results are identical for every choice. The choice is cached
+ * per (nx, ny, nz, precision) for the process; a later context of the same
+ * shape takes it without timing. Synchronises the context stream; discards
+ * a captured EM graph. Outputs (nullable) receive the chosen heights. The
+ * paper has no counterpart: this is how the library fits tiles to B300. */
+cosim_status cosim_autotune(cosim_ctx *ctx, uint32_t flags, int32_t *em_tile_y, int32_t *th_block_y);
+
 /* Joule accumulator operations:
  *   COSIM_JOULE_RESET: zero the per-node energy and the accumulated step count;
  *   COSIM_JOULE_FINALIZE_AVG_POWER: thermal source P_i = Q_i / (n_steps dt_em)
@@ -257,7 +275,9 @@ enum {
   COSIM_Q_N_CELLS = 5,
   COSIM_Q_N_NODES = 6,
   COSIM_Q_PRECISION = 7,
-  COSIM_Q_LAUNCHES = 8        /* CUDA kernels launched by the context so far */
+  COSIM_Q_LAUNCHES = 8,       /* CUDA kernels launched by the context so far */
+  COSIM_Q_EM_TILE_Y = 9,      /* EM tile height in use (8, or 4 after autotuning an FP32 context) */
+  COSIM_Q_TH_BLOCK_Y = 10     /* thermal kernel block height in use */
 };
 cosim_status cosim_query(const cosim_ctx *ctx, int32_t what, double *out);
 

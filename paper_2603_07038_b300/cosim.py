@@ -27,7 +27,8 @@ COSIM_MECH_CLAMPED_BOTTOM, COSIM_MECH_KINEMATIC_MOUNT, COSIM_MECH_MASK = 0, 1, 2
 (COSIM_F_EX, COSIM_F_EY, COSIM_F_EZ, COSIM_F_HX, COSIM_F_HY, COSIM_F_HZ, COSIM_F_T, COSIM_F_Q, COSIM_F_P,
  COSIM_F_UX, COSIM_F_UY, COSIM_F_UZ, COSIM_F_VM, COSIM_F_UMAG, COSIM_F_FX, COSIM_F_FY, COSIM_F_FZ) = range(17)
 (COSIM_Q_DT_EM, COSIM_Q_DT_TH_LIMIT, COSIM_Q_STEP, COSIM_Q_BYTES_RESIDENT, COSIM_Q_JOULE_STEPS,
- COSIM_Q_N_CELLS, COSIM_Q_N_NODES, COSIM_Q_PRECISION, COSIM_Q_LAUNCHES) = range(9)
+ COSIM_Q_N_CELLS, COSIM_Q_N_NODES, COSIM_Q_PRECISION, COSIM_Q_LAUNCHES, COSIM_Q_EM_TILE_Y,
+ COSIM_Q_TH_BLOCK_Y) = range(11)
 
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT", 6: "NONFINITE"}
 
@@ -109,6 +110,8 @@ def load():
     L.cosim_em_graph_capture.restype = st
     L.cosim_em_graph_launch.argtypes = [P, C.c_int64]
     L.cosim_em_graph_launch.restype = st
+    L.cosim_autotune.argtypes = [P, C.c_uint32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.cosim_autotune.restype = st
     L.cosim_joule_accumulate.argtypes = [P, C.c_int32, C.POINTER(C.c_double)]
     L.cosim_joule_accumulate.restype = st
     L.cosim_thermal_steps.argtypes = [P, C.c_int64, C.c_double]
@@ -235,6 +238,17 @@ def cosim_em_graph_capture(ctx, nsteps, flags=COSIM_ACCUM_JOULE):
 
 def cosim_em_graph_launch(ctx, count=1):
     _check(load().cosim_em_graph_launch(ctx, int(count)), ctx)
+
+
+COSIM_TUNE_FORCE, COSIM_TUNE_FIXED = 1, 2
+
+
+def cosim_autotune(ctx, force=False, fixed=None):
+    """-> (EM tile height, thermal block height). fixed=(ty, by) sets them without timing."""
+    ty, by = C.c_int32(fixed[0] if fixed else 0), C.c_int32(fixed[1] if fixed else 0)
+    flags = (COSIM_TUNE_FORCE if force else 0) | (COSIM_TUNE_FIXED if fixed else 0)
+    _check(load().cosim_autotune(ctx, flags, C.byref(ty), C.byref(by)), ctx)
+    return ty.value, by.value
 
 
 def cosim_joule_accumulate(ctx, op, want_total=True):
@@ -380,6 +394,9 @@ class Context:
 
     def em_graph_launch(self, count=1):
         cosim_em_graph_launch(self.h, count)
+
+    def autotune(self, force=False, fixed=None):
+        return cosim_autotune(self.h, force, fixed)
 
     def joule(self, op, want_total=True):
         return cosim_joule_accumulate(self.h, op, want_total)

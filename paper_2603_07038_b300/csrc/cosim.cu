@@ -10,7 +10,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -23,10 +25,11 @@ using namespace cosim;
 
 namespace {
 
-#ifndef COSIM_EM_TY
-#define COSIM_EM_TY 8
-#endif
-constexpr int kEmTX = 32, kEmTY = COSIM_EM_TY;  // EM tile: 31 x (TY-1) owned nodes per CTA
+// EM tile: 31 x (TY-1) owned nodes per CTA of 32 x TY threads. TY = 8 always
+// exists; FP32 plain steps may also use TY = 4 (more, smaller CTAs for small
+// grids), chosen per grid shape by cosim_autotune.
+constexpr int kEmTX = 32, kEmTY = 8, kEmTYSmall = 4;
+constexpr int em_ty_index(int ty) { return ty == kEmTY ? 0 : 1; }
 constexpr int kMvTX = 32, kMvTY = 8;  // matvec tile
 constexpr int kRedBlocks = 1184;      // fixed grid of the vector kernels (8 x 148)
 constexpr int kSrcPadLo = 4, kSrcPadHi = 16;  // zero ints around the source-row offsets
@@ -61,7 +64,8 @@ struct cosim_ctx {
   void *xE[2][3][2]{}, *dE[2][3][2]{}, *xH[2][3][2]{}, *dH[2][3][2]{};
   void *lE[2][3][2]{}, *lH[2][3][2]{};
   // TMA descriptors of E, H (per parity and component) and the Joule window
-  CUtensorMap tmE[2][3], tmH[2][3], tmQ, tmT[2];
+  // per EM tile height (index em_ty_index): boxes of TY or TY + 1 rows
+  CUtensorMap tmE[2][2][3], tmH[2][2][3], tmQ[2], tmT[2][2];
   int *dev_err = nullptr;  // device word: a bounded in-kernel wait gave up
   int slo[3]{}, shi[3]{}, sn[3]{};
   long long psi_len[3]{};
@@ -89,7 +93,9 @@ struct cosim_ctx {
   // sources
   int *src_row = nullptr;       // = src_row_buf + kSrcPadLo
   int *src_row_buf = nullptr;   // allocation: kSrcPadLo zeros, the offsets, kSrcPadHi zeros
-  CUtensorMap tmV;   // voxel IDs (x, y, z), box em_vox_box_x x (TY+1) x 1
+  CUtensorMap tmV[2];  // voxel IDs (x, y, z), box em_vox_box_x x (TY+1) x 1 per tile height
+  int em_ty = kEmTY;   // EM tile height of FP32 plain steps
+  int th_by = 8;       // thermal kernel block height
   void *zt = nullptr;  // per node plane k: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1) (zero outside)
   int vpx = 0;         // voxel row pitch
   int4 *src_ent = nullptr;
@@ -294,6 +300,14 @@ static cudaError_t set_smem_limits() {
                             (const void *)em_step_kernel<R, long long, kEmTX, kEmTY, true>};
   for (const void *k : kernels)
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, em)) != cudaSuccess) return e;
+  if constexpr (sizeof(R) == 4) {
+    const int em4 = (int)(em_stage_offset<R, kEmTX, kEmTYSmall>(kMaxMat) +
+                          kEmStages * sizeof(EmStage<R, kEmTX, kEmTYSmall>) + 128);
+    const void *small[2] = {(const void *)em_step_kernel<R, int, kEmTX, kEmTYSmall, false>,
+                            (const void *)em_step_kernel<R, long long, kEmTX, kEmTYSmall, false>};
+    for (const void *k : small)
+      if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, em4)) != cudaSuccess) return e;
+  }
   return cudaSuccess;
 }
 
@@ -325,11 +339,11 @@ static cosim_status encode_node_map(cosim_ctx *c, CUtensorMap *m, void *base, in
                     dims, strides, box);
 }
 // voxel IDs: (x, y, z) = (nx, ny, nz) bytes with row pitch vpx
-static cosim_status encode_voxel_map(cosim_ctx *c) {
+static cosim_status encode_voxel_map(cosim_ctx *c, CUtensorMap *m, int rows) {
   const cuuint64_t dims[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->nz};
   const cuuint64_t strides[2] = {(cuuint64_t)c->vpx, (cuuint64_t)c->vpx * c->ny};
-  const cuuint32_t box[3] = {(cuuint32_t)em_vox_box_x<kEmTX>(), (cuuint32_t)kEmTY + 1, 1};
-  return encode_map(c, &c->tmV, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, c->mat, dims, strides, box);
+  const cuuint32_t box[3] = {(cuuint32_t)em_vox_box_x<kEmTX>(), (cuuint32_t)rows, 1};
+  return encode_map(c, m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, c->mat, dims, strides, box);
 }
 
 
@@ -495,18 +509,23 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
   ALLOC(c, c->Qs, c->npad * c->rsz);
   ALLOC(c, c->dev_err, sizeof(int));
   ALLOC(c, c->dstep, sizeof(long long));
-  for (int p = 0; p < 2; ++p)
-    for (int a = 0; a < 3; ++a) {
-      if ((st = encode_node_map(c, &c->tmE[p][a], c->E[p][a], kEmTY + 1)) != COSIM_OK) return st;
-      if ((st = encode_node_map(c, &c->tmH[p][a], c->H[p][a], kEmTY)) != COSIM_OK) return st;
-    }
-  if ((st = encode_node_map(c, &c->tmQ, c->Qs, kEmTY)) != COSIM_OK) return st;
-  if ((st = encode_voxel_map(c)) != COSIM_OK) return st;
+  for (int t = 0; t < 2; ++t) {
+    const int ty = t == 0 ? kEmTY : kEmTYSmall;
+    for (int p = 0; p < 2; ++p)
+      for (int a = 0; a < 3; ++a) {
+        if ((st = encode_node_map(c, &c->tmE[t][p][a], c->E[p][a], ty + 1)) != COSIM_OK) return st;
+        if ((st = encode_node_map(c, &c->tmH[t][p][a], c->H[p][a], ty)) != COSIM_OK) return st;
+      }
+    if ((st = encode_node_map(c, &c->tmQ[t], c->Qs, ty)) != COSIM_OK) return st;
+    if ((st = encode_voxel_map(c, &c->tmV[t], ty + 1)) != COSIM_OK) return st;
+  }
   ALLOC(c, c->T[0], c->npad * c->rsz);
   ALLOC(c, c->T[1], c->npad * c->rsz);
   ALLOC(c, c->P, c->npad * c->rsz);
-  for (int p = 0; p < 2; ++p)
-    if ((st = encode_node_map(c, &c->tmT[p], c->T[p], kEmTY + 1)) != COSIM_OK) return st;
+  for (int t = 0; t < 2; ++t)
+    for (int p = 0; p < 2; ++p)
+      if ((st = encode_node_map(c, &c->tmT[t][p], c->T[p], (t == 0 ? kEmTY : kEmTYSmall) + 1)) != COSIM_OK)
+        return st;
   ALLOC(c, c->scratch, c->npad * 8);
   const int mv_blocks = ((c->nx + 1) + kMvTX - 2) / (kMvTX - 1) * (((c->ny + 1) + kMvTY - 2) / (kMvTY - 1));
   c->npart = std::max(kRedBlocks, mv_blocks);
@@ -644,15 +663,19 @@ constexpr int kJouleWindow = 32;  // EM steps per short-window Joule accumulatio
 template <typename R>
 static ThArgs<R> th_args(cosim_ctx *c);
 
-template <typename R, typename I, bool CPL>
+template <typename R, typename I, int TY, bool CPL>
 static void launch_em(const dim3 &grd, const dim3 &blk, size_t smem, cudaStream_t st, const EmArgs<R> &A) {
-  em_step_kernel<R, I, kEmTX, kEmTY, CPL><<<grd, blk, smem, st>>>(A);
+  em_step_kernel<R, I, kEmTX, TY, CPL><<<grd, blk, smem, st>>>(A);
 }
 
 // coupled: the synchronized marching of Sec. II-A (sigma(T^n) in the EM step,
-// then one thermal step with the EM dt and that step's Joule power)
-template <typename R>
-static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum, bool coupled) {
+// then one thermal step with the EM dt and that step's Joule power).
+// probe: the autotuner's timing launches: every launch reads the current
+// E/H/CPML buffers and writes the spare ones, nothing else changes (no
+// parity flip, no accumulation, no counters), so the state stays as it was.
+template <typename R, int TY>
+static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool coupled, bool probe = false) {
+  constexpr int t = em_ty_index(TY);
   EmArgs<R> A;
   A.g = make_geo<R>(c);
   for (int a = 0; a < 3; ++a) {
@@ -678,7 +701,7 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum, bool co
     }
   };
   interior(c->nx, c->slo[0], c->shi[0], kEmTX, A.ibx0, A.ibx1);
-  interior(c->ny, c->slo[1], c->shi[1], kEmTY, A.iby0, A.iby1);
+  interior(c->ny, c->slo[1], c->shi[1], TY, A.iby0, A.iby1);
   A.dt = (R)c->dt;
   A.src_row = c->src_row;
   A.src_ent = c->src_ent;
@@ -686,14 +709,14 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum, bool co
   A.amp_len = c->amp_len;
   A.Qs = accum ? (R *)c->Qs : nullptr;
   A.Q = c->Q;
-  A.tmQ = c->tmQ;
-  A.tmV = c->tmV;
+  A.tmQ = c->tmQ[t];
+  A.tmV = c->tmV[t];
   A.zt = (const R *)c->zt;
   A.err = c->dev_err;
-  const dim3 blk(kEmTX, kEmTY);
-  const dim3 grd((c->nx + 1 + kEmTX - 2) / (kEmTX - 1), (c->ny + 1 + kEmTY - 2) / (kEmTY - 1));
-  const size_t smem = em_stage_offset<R, kEmTX, kEmTY>((int)c->mats.size()) +
-                      kEmStages * sizeof(EmStage<R, kEmTX, kEmTY>) + 128;  // + alignment slack
+  const dim3 blk(kEmTX, TY);
+  const dim3 grd((c->nx + 1 + kEmTX - 2) / (kEmTX - 1), (c->ny + 1 + TY - 2) / (TY - 1));
+  const size_t smem = em_stage_offset<R, kEmTX, TY>((int)c->mats.size()) +
+                      kEmStages * sizeof(EmStage<R, kEmTX, TY>) + 128;  // + alignment slack
   for (int64_t s = 0; s < nsteps; ++s) {
     const int o = c->par, n = c->par ^ 1;
     for (int a = 0; a < 3; ++a) {
@@ -715,28 +738,34 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum, bool co
         A.lHo[a][s2] = (const R *)c->lH[o][a][s2];
         A.lHn[a][s2] = (R *)c->lH[n][a][s2];
       }
-      A.tmE[a] = c->tmE[o][a];
-      A.tmH[a] = c->tmH[o][a];
+      A.tmE[a] = c->tmE[t][o][a];
+      A.tmH[a] = c->tmH[t][o][a];
     }
     A.step_base = c->dstep;
     A.step_off = (int)s;
     A.fold = accum && ((c->n_acc + 1) % kJouleWindow == 0);
-    A.tmT = c->tmT[c->tpar];
+    A.tmT = c->tmT[t][c->tpar];
     A.Pout = (R *)c->P;
     A.inv_dt = (R)(1.0 / c->dt);
     const bool small = c->npad < (1LL << 31);
-    if (coupled)
-      small ? launch_em<R, int, true>(grd, blk, smem, c->stream, A)
-            : launch_em<R, long long, true>(grd, blk, smem, c->stream, A);
-    else
-      small ? launch_em<R, int, false>(grd, blk, smem, c->stream, A)
-            : launch_em<R, long long, false>(grd, blk, smem, c->stream, A);
-    ++c->launches;
+    if constexpr (TY == kEmTY) {
+      if (coupled)
+        small ? launch_em<R, int, TY, true>(grd, blk, smem, c->stream, A)
+              : launch_em<R, long long, TY, true>(grd, blk, smem, c->stream, A);
+      else
+        small ? launch_em<R, int, TY, false>(grd, blk, smem, c->stream, A)
+              : launch_em<R, long long, TY, false>(grd, blk, smem, c->stream, A);
+    } else {  // the small tile exists for FP32 plain steps only
+      small ? launch_em<R, int, TY, false>(grd, blk, smem, c->stream, A)
+            : launch_em<R, long long, TY, false>(grd, blk, smem, c->stream, A);
+    }
     CHECK_LAUNCH(c);
+    if (probe) continue;
+    ++c->launches;
     if (coupled) {  // T^{n+1} = T^n + dt/C (-M_kk T^n + P^{n+1}) with the EM dt (Eq. 5)
       ThArgs<R> TA = th_args<R>(c);
       TA.dt = (R)c->dt;
-      const dim3 tb(32, 8), tg((c->nx + 1 + 31) / 32, (c->ny + 1 + 7) / 8);
+      const dim3 tb(32, c->th_by), tg((c->nx + 1 + 31) / 32, (c->ny + 1 + c->th_by - 1) / c->th_by);
       thermal_kernel<R, 0><<<tg, tb, c->mats.size() * M_COLS * sizeof(R), c->stream>>>(TA);
       ++c->launches;
       CHECK_LAUNCH(c);
@@ -749,12 +778,19 @@ static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum, bool co
       c->qs_dirty = !A.fold;
     }
   }
-  if (nsteps > 0) {
+  if (nsteps > 0 && !probe) {
     step_advance_kernel<<<1, 1, 0, c->stream>>>(c->dstep, nsteps);
     ++c->launches;
     CHECK_LAUNCH(c);
   }
   return COSIM_OK;
+}
+
+template <typename R>
+static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum, bool coupled) {
+  if constexpr (sizeof(R) == 4)
+    if (!coupled && c->em_ty == kEmTYSmall) return em_steps_tile<R, kEmTYSmall>(c, nsteps, accum, coupled);
+  return em_steps_tile<R, kEmTY>(c, nsteps, accum, coupled);
 }
 
 static cosim_status em_steps_any(cosim_ctx *c, int64_t nsteps, bool acc, bool coupled) {
@@ -965,7 +1001,7 @@ static cosim_status ensure_th_limit(cosim_ctx *c) {
 
 template <typename R>
 static cosim_status thermal_steps_t(cosim_ctx *c, int64_t nsteps, double dt) {
-  const dim3 blk(32, 8), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + 7) / 8);
+  const dim3 blk(32, c->th_by), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + c->th_by - 1) / c->th_by);
   const size_t smem = c->mats.size() * M_COLS * sizeof(R);
   for (int64_t s = 0; s < nsteps; ++s) {
     ThArgs<R> A = th_args<R>(c);
@@ -1425,6 +1461,96 @@ extern "C" cosim_status cosim_write_fields(cosim_ctx *c, int32_t field, int32_t 
   return COSIM_OK;
 }
 
+// ---------------------------------------------------------------- autotuning
+
+// tuned (EM tile height, thermal block height) per (nx, ny, nz, precision)
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;
+
+template <typename R>
+static cosim_status autotune_t(cosim_ctx *c, int *em_ty, int *th_by) {
+  cudaEvent_t e0, e1;
+  CHECK_CUDA(c, cudaEventCreate(&e0));
+  CHECK_CUDA(c, cudaEventCreate(&e1));
+  cosim_status st = COSIM_OK;
+  auto time_ms = [&](auto &&launch, int reps) -> float {
+    float ms = 1e30f;
+    if ((st = launch(2)) != COSIM_OK) return ms;  // warm-up
+    cudaEventRecord(e0, c->stream);
+    if ((st = launch(reps)) != COSIM_OK) return ms;
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms / reps;
+  };
+  // EM tile height (FP32 plain steps): probe launches leave the state as it is
+  int best_ty = kEmTY;
+  if constexpr (sizeof(R) == 4) {
+    const float t8 = time_ms([&](int n) { return em_steps_tile<R, kEmTY>(c, n, false, false, true); }, 5);
+    const float t4 = time_ms([&](int n) { return em_steps_tile<R, kEmTYSmall>(c, n, false, false, true); }, 5);
+    if (st == COSIM_OK && t4 < t8) best_ty = kEmTYSmall;
+  }
+  // thermal block height: dt = 0 launches write the spare buffer with T itself
+  int best_by = 8;
+  float best = 1e30f;
+  for (int by : {4, 8, 16}) {
+    const dim3 blk(32, by), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + by - 1) / by);
+    const size_t smem = c->mats.size() * M_COLS * sizeof(R);
+    const float t = time_ms(
+        [&](int n) {
+          ThArgs<R> A = th_args<R>(c);
+          A.dt = 0;
+          for (int q = 0; q < n; ++q) thermal_kernel<R, 0><<<grd, blk, smem, c->stream>>>(A);
+          CHECK_LAUNCH(c);
+          return COSIM_OK;
+        },
+        5);
+    if (t < best) best = t, best_by = by;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != COSIM_OK) return st;
+  *em_ty = best_ty;
+  *th_by = best_by;
+  return COSIM_OK;
+}
+
+extern "C" cosim_status cosim_autotune(cosim_ctx *c, uint32_t flags, int32_t *em_tile_y, int32_t *th_block_y) {
+  if (!c) return COSIM_ERR_INVALID;
+  if (flags & ~(COSIM_TUNE_FORCE | COSIM_TUNE_FIXED)) return fail(c, COSIM_ERR_INVALID, "bad autotune flags");
+  const auto key = std::make_tuple(c->nx, c->ny, c->nz, (int)c->prec);
+  int ty = 0, by = 0;
+  if (flags & COSIM_TUNE_FIXED) {
+    if (!em_tile_y || !th_block_y) return fail(c, COSIM_ERR_INVALID, "FIXED needs both heights");
+    ty = *em_tile_y, by = *th_block_y;
+    const bool ok_ty = ty == kEmTY || (ty == kEmTYSmall && c->prec != COSIM_FP64);
+    if (!ok_ty || (by != 4 && by != 8 && by != 16)) return fail(c, COSIM_ERR_INVALID, "unsupported launch shape");
+    CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+    drop_graph(c);
+    c->em_ty = ty;
+    c->th_by = by;
+    return COSIM_OK;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end() && !(flags & COSIM_TUNE_FORCE)) ty = it->second.first, by = it->second.second;
+  }
+  if (ty == 0) {
+    CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+    const cosim_status st = c->prec == COSIM_FP64 ? autotune_t<double>(c, &ty, &by) : autotune_t<float>(c, &ty, &by);
+    if (st != COSIM_OK) return st;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = {ty, by};
+  }
+  drop_graph(c);  // a captured graph holds the old launch shapes
+  c->em_ty = ty;
+  c->th_by = by;
+  if (em_tile_y) *em_tile_y = ty;
+  if (th_block_y) *th_block_y = by;
+  return COSIM_OK;
+}
+
 extern "C" cosim_status cosim_query(const cosim_ctx *c, int32_t what, double *out) {
   if (!c || !out) return COSIM_ERR_INVALID;
   switch (what) {
@@ -1442,6 +1568,8 @@ extern "C" cosim_status cosim_query(const cosim_ctx *c, int32_t what, double *ou
     case COSIM_Q_N_NODES: *out = (double)(c->nx + 1) * (c->ny + 1) * (c->nz + 1); break;
     case COSIM_Q_PRECISION: *out = c->prec; break;
     case COSIM_Q_LAUNCHES: *out = (double)c->launches; break;
+    case COSIM_Q_EM_TILE_Y: *out = c->prec == COSIM_FP64 ? kEmTY : c->em_ty; break;
+    case COSIM_Q_TH_BLOCK_Y: *out = c->th_by; break;
     default: return COSIM_ERR_INVALID;
   }
   return COSIM_OK;

@@ -251,7 +251,7 @@ __host__ __device__ constexpr size_t em_stage_offset(int nmat) {
 #define COSIM_EM_AHEAD 3
 #endif
 #ifndef COSIM_EM_MIN_CTAS
-#define COSIM_EM_MIN_CTAS 3  // resident CTAs per SM the FP32 kernel is compiled for
+#define COSIM_EM_MIN_CTAS 3  // resident CTAs of 8 warps per SM the FP32 kernel is compiled for (scaled for other heights)
 #endif
 constexpr int kEmStages = COSIM_EM_STAGES;
 constexpr int kEmAhead = COSIM_EM_AHEAD;
@@ -563,7 +563,7 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
 // One launch per step over all tiles; tiles in [ibx0, ibx1) x [iby0, iby1)
 // take the interior specialisation.
 template <typename R, typename I, int TX, int TY, bool CPL>
-__global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? COSIM_EM_MIN_CTAS : 2)
+__global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? COSIM_EM_MIN_CTAS * 8 / TY : 2)
     em_step_kernel(const __grid_constant__ EmArgs<R> A) {
   static_assert(TX == 32, "a tile row is one warp: x neighbours are exchanged by shuffles");
   extern __shared__ __align__(128) unsigned char smem_raw[];

@@ -61,7 +61,7 @@ __device__ __forceinline__ LayerSums<R> layer_sums(const R *s_mt, int m00, int m
 // One forward-Euler step (Eq. 5). Thread per (i, j) node column, marching in z.
 // MODE 0: step T; MODE 1: write the per-node stability ratio C / (sum G + film).
 template <typename R, int MODE>
-__global__ void __launch_bounds__(256) thermal_kernel(const ThArgs<R> A) {
+__global__ void __launch_bounds__(512) thermal_kernel(const ThArgs<R> A) {  // blocks of 32 x (4, 8 or 16)
   extern __shared__ unsigned char smem_raw[];
   R *s_mt = reinterpret_cast<R *>(smem_raw);
   const Geo<R> &g = A.g;

@@ -176,7 +176,7 @@ class DesignRunner:
     the timed phases; ``keep_fields`` also returns T, u and von Mises."""
 
     def __init__(self, specs: Sequence[DesignSpec], workers: int, precision=None, keep_fields=False,
-                 use_graph=True):
+                 use_graph=True, autotune=True):
         import torch
 
         import workloads as W
@@ -188,6 +188,13 @@ class DesignRunner:
         self.problems = {s: W.layered_package(s.nx, s.ny, seed=s.seed, nz=s.nz, tsv_pitch=s.tsv_pitch, n_lines=8)
                          for s in specs}
         self.streams = [torch.cuda.Stream() for _ in range(workers)]
+        self.autotune = autotune
+        if autotune:  # tune each grid shape once, before any request runs
+            for shape in {(s.nx, s.ny, s.nz): s for s in specs}.values():
+                c = api.Context(self.problems[shape], precision=self.precision, stream=self.streams[0],
+                                use_torch_allocator=True)
+                c.autotune()
+                c.close()
 
     def run(self, spec: DesignSpec, worker: int) -> dict:
         api = self.api
@@ -200,6 +207,8 @@ class DesignRunner:
         # device and stall the designs running beside this one
         ctx = api.Context(p, precision=self.precision, stream=stream, use_torch_allocator=True)
         try:
+            if self.autotune:
+                ctx.autotune()  # the shape's cached choice
             ctx.set_sources(p.source_tables(ctx.dt, n_em, spec.t0))
             ctx.joule(api.COSIM_JOULE_RESET, want_total=False)
             if self.use_graph:
