@@ -292,6 +292,9 @@ def serving_arm(args, workers=4):
     rate = 0.8 / per_design
     arr = S.poisson_arrivals(len(specs), rate, seed=11)
     rep = S.serve(specs, arr, runner.run, workers=workers, footprint=S.footprint_bytes)
+    # the served form as a closed batch (everything queued at t = 0), the
+    # like-for-like comparison with the plain form below
+    rep_batch = S.serve(specs, [0.0] * len(specs), runner.run, workers=workers, footprint=S.footprint_bytes)
     # the plain form on the same GPU: one design at a time, step-by-step
     # launches, default launch shapes, everything queued at t = 0
     plain = S.DesignRunner(specs, workers=1, use_graph=False, autotune=False)
@@ -306,6 +309,7 @@ def serving_arm(args, workers=4):
             "requests": len(specs), "workers": workers, "arrival_rate_per_s": round(rate, 3),
             "p50_s": round(rep["p50_s"], 4), "p99_s": round(rep["p99_s"], 4),
             "designs_per_hour": round(rep["designs_per_hour"], 1), "makespan_s": round(rep["makespan_s"], 3),
+            "batch_designs_per_hour": round(rep_batch["designs_per_hour"], 1),
             "plain_designs_per_hour": round(rep_plain["designs_per_hour"], 1),
             "plain_note": "same requests one at a time, no graphs, default launch shapes, all queued at t=0",
             "plain_results_match": bool(same),
