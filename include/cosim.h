@@ -160,14 +160,15 @@ cosim_status cosim_em_graph_launch(cosim_ctx *ctx, int64_t count);
 
 /* Flags for cosim_autotune. FORCE: time the variants again even if this
  * grid shape was tuned before in this process. FIXED: no timing; take the
- * heights from *em_tile_y (8, or 4 for FP32) and *th_block_y (4, 8, 16). */
+ * shapes from *em_tile_y (8, or 4 for FP32) and *th_block_y (0, 4, 8, 16). */
 #define COSIM_TUNE_FORCE 1u
 #define COSIM_TUNE_FIXED 2u
 
 /* Pick the launch shapes for this context's grid by timing the variants on
  * the context itself: the EM tile height (8 or 4 rows of threads; FP32
- * contexts, steps without COSIM_COUPLED_THERMAL) and the thermal kernel's
- * block height (4, 8 or 16). Timing launches only read the current fields
+ * contexts, steps without COSIM_COUPLED_THERMAL) and the thermal step kernel
+ * (0: TMA-staged 32 x 8 tiles, the default; 4, 8, 16: a per-thread-load
+ * kernel with blocks of that height). Timing launches only read the current fields
  * and write spare buffers, so the context's state and step count are
  * unchanged; results are identical for every choice. The choice is cached
  * per (nx, ny, nz, precision) for the process; a later context of the same
@@ -277,7 +278,7 @@ enum {
   COSIM_Q_PRECISION = 7,
   COSIM_Q_LAUNCHES = 8,       /* CUDA kernels launched by the context so far */
   COSIM_Q_EM_TILE_Y = 9,      /* EM tile height in use (8, or 4 after autotuning an FP32 context) */
-  COSIM_Q_TH_BLOCK_Y = 10     /* thermal kernel block height in use */
+  COSIM_Q_TH_BLOCK_Y = 10     /* thermal step kernel in use: 0 TMA-staged tiles, 4/8/16 classic block height */
 };
 cosim_status cosim_query(const cosim_ctx *ctx, int32_t what, double *out);
 

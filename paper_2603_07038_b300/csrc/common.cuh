@@ -140,6 +140,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
+// A TMA destination in shared memory must be 128-byte aligned: every staged
+// box is padded to a multiple of 128 bytes.
+template <typename R, int ROWS, int BX>
+struct alignas(128) EmBox {
+  R v[ROWS][BX];
+};
+
 // Wait for the phase of parity `parity` to complete; gives up (returns false)
 // after about a second of SM clock so that a lost copy cannot hang the GPU.
 constexpr long long kWaitCycles = 2LL << 30;

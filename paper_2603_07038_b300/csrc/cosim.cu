@@ -95,7 +95,8 @@ struct cosim_ctx {
   int *src_row_buf = nullptr;   // allocation: kSrcPadLo zeros, the offsets, kSrcPadHi zeros
   CUtensorMap tmV[2];  // voxel IDs (x, y, z), box em_vox_box_x x (TY+1) x 1 per tile height
   int em_ty = kEmTY;   // EM tile height of FP32 plain steps
-  int th_by = 8;       // thermal kernel block height
+  int th_by = 0;       // thermal step kernel: 0 = TMA-staged tiles, 4/8/16 = classic block height
+  CUtensorMap thT[2], thP, thV;  // the TMA thermal kernel's T (per buffer), P and voxel boxes
   void *zt = nullptr;  // per node plane k: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1) (zero outside)
   int vpx = 0;         // voxel row pitch
   int4 *src_ent = nullptr;
@@ -300,6 +301,10 @@ static cudaError_t set_smem_limits() {
                             (const void *)em_step_kernel<R, long long, kEmTX, kEmTY, true>};
   for (const void *k : kernels)
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, em)) != cudaSuccess) return e;
+  const int th = (int)(th_stage_offset<R>(kMaxMat) + kThStages * sizeof(ThStage<R>) + 128);
+  if ((e = cudaFuncSetAttribute(thermal_tma_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, th)) !=
+      cudaSuccess)
+    return e;
   if constexpr (sizeof(R) == 4) {
     const int em4 = (int)(em_stage_offset<R, kEmTX, kEmTYSmall>(kMaxMat) +
                           kEmStages * sizeof(EmStage<R, kEmTX, kEmTYSmall>) + 128);
@@ -331,10 +336,10 @@ static cosim_status encode_map(cosim_ctx *c, CUtensorMap *m, CUtensorMapDataType
   if (r != CUDA_SUCCESS) return fail(c, COSIM_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return COSIM_OK;
 }
-static cosim_status encode_node_map(cosim_ctx *c, CUtensorMap *m, void *base, int rows) {
+static cosim_status encode_node_map(cosim_ctx *c, CUtensorMap *m, void *base, int rows, int cols = em_box_x<kEmTX>()) {
   const cuuint64_t dims[3] = {(cuuint64_t)c->nx + 1, (cuuint64_t)c->ny + 1, (cuuint64_t)c->nz + 1};
   const cuuint64_t strides[2] = {(cuuint64_t)c->px * c->rsz, (cuuint64_t)c->plane * c->rsz};
-  const cuuint32_t box[3] = {(cuuint32_t)em_box_x<kEmTX>(), (cuuint32_t)rows, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)cols, (cuuint32_t)rows, 1};
   return encode_map(c, m, c->rsz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base,
                     dims, strides, box);
 }
@@ -526,6 +531,10 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
     for (int p = 0; p < 2; ++p)
       if ((st = encode_node_map(c, &c->tmT[t][p], c->T[p], (t == 0 ? kEmTY : kEmTYSmall) + 1)) != COSIM_OK)
         return st;
+  for (int p = 0; p < 2; ++p)
+    if ((st = encode_node_map(c, &c->thT[p], c->T[p], kThTY + 2, 40)) != COSIM_OK) return st;
+  if ((st = encode_node_map(c, &c->thP, c->P, kThTY, 32)) != COSIM_OK) return st;
+  if ((st = encode_voxel_map(c, &c->thV, kThTY + 1)) != COSIM_OK) return st;
   ALLOC(c, c->scratch, c->npad * 8);
   const int mv_blocks = ((c->nx + 1) + kMvTX - 2) / (kMvTX - 1) * (((c->ny + 1) + kMvTY - 2) / (kMvTY - 1));
   c->npart = std::max(kRedBlocks, mv_blocks);
@@ -663,6 +672,33 @@ constexpr int kJouleWindow = 32;  // EM steps per short-window Joule accumulatio
 template <typename R>
 static ThArgs<R> th_args(cosim_ctx *c);
 
+// One thermal step T[tpar] -> T[tpar ^ 1] with time step dt (tpar is not
+// flipped here): th_by = 0 launches the TMA-staged kernel, 4/8/16 the classic
+// kernel with that block height. Every choice gives identical results.
+template <typename R>
+static cosim_status launch_thermal(cosim_ctx *c, R dt, bool count = true) {
+  ThArgs<R> A = th_args<R>(c);
+  A.dt = dt;
+  if (c->th_by == 0) {
+    ThTmaArgs<R> T;
+    T.a = A;
+    T.tmT = c->thT[c->tpar];
+    T.tmP = c->thP;
+    T.tmV = c->thV;
+    T.zt = (const R *)c->zt;
+    T.err = c->dev_err;
+    const dim3 blk(32, kThTY), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + kThTY - 1) / kThTY);
+    const size_t smem = th_stage_offset<R>((int)c->mats.size()) + kThStages * sizeof(ThStage<R>) + 128;
+    thermal_tma_kernel<R><<<grd, blk, smem, c->stream>>>(T);
+  } else {
+    const dim3 blk(32, c->th_by), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + c->th_by - 1) / c->th_by);
+    thermal_kernel<R, 0><<<grd, blk, c->mats.size() * M_COLS * sizeof(R), c->stream>>>(A);
+  }
+  CHECK_LAUNCH(c);
+  if (count) ++c->launches;
+  return COSIM_OK;
+}
+
 template <typename R, typename I, int TY, bool CPL>
 static void launch_em(const dim3 &grd, const dim3 &blk, size_t smem, cudaStream_t st, const EmArgs<R> &A) {
   em_step_kernel<R, I, kEmTX, TY, CPL><<<grd, blk, smem, st>>>(A);
@@ -763,12 +799,8 @@ static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool
     if (probe) continue;
     ++c->launches;
     if (coupled) {  // T^{n+1} = T^n + dt/C (-M_kk T^n + P^{n+1}) with the EM dt (Eq. 5)
-      ThArgs<R> TA = th_args<R>(c);
-      TA.dt = (R)c->dt;
-      const dim3 tb(32, c->th_by), tg((c->nx + 1 + 31) / 32, (c->ny + 1 + c->th_by - 1) / c->th_by);
-      thermal_kernel<R, 0><<<tg, tb, c->mats.size() * M_COLS * sizeof(R), c->stream>>>(TA);
-      ++c->launches;
-      CHECK_LAUNCH(c);
+      const cosim_status ts = launch_thermal<R>(c, (R)c->dt);
+      if (ts != COSIM_OK) return ts;
       c->tpar ^= 1;
     }
     c->par ^= 1;
@@ -1001,13 +1033,9 @@ static cosim_status ensure_th_limit(cosim_ctx *c) {
 
 template <typename R>
 static cosim_status thermal_steps_t(cosim_ctx *c, int64_t nsteps, double dt) {
-  const dim3 blk(32, c->th_by), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + c->th_by - 1) / c->th_by);
-  const size_t smem = c->mats.size() * M_COLS * sizeof(R);
   for (int64_t s = 0; s < nsteps; ++s) {
-    ThArgs<R> A = th_args<R>(c);
-    A.dt = (R)dt;
-    thermal_kernel<R, 0><<<grd, blk, smem, c->stream>>>(A); ++c->launches;
-    CHECK_LAUNCH(c);
+    const cosim_status st = launch_thermal<R>(c, (R)dt);
+    if (st != COSIM_OK) return st;
     c->tpar ^= 1;
   }
   return COSIM_OK;
@@ -1490,23 +1518,25 @@ static cosim_status autotune_t(cosim_ctx *c, int *em_ty, int *th_by) {
     const float t4 = time_ms([&](int n) { return em_steps_tile<R, kEmTYSmall>(c, n, false, false, true); }, 5);
     if (st == COSIM_OK && t4 < t8) best_ty = kEmTYSmall;
   }
-  // thermal block height: dt = 0 launches write the spare buffer with T itself
-  int best_by = 8;
+  // thermal step kernel (TMA tiles, or the classic kernel with 4/8/16-row
+  // blocks): dt = 0 launches write the spare buffer with T itself
+  const int keep_by = c->th_by;
+  int best_by = 0;
   float best = 1e30f;
-  for (int by : {4, 8, 16}) {
-    const dim3 blk(32, by), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + by - 1) / by);
-    const size_t smem = c->mats.size() * M_COLS * sizeof(R);
+  for (int by : {0, 4, 8, 16}) {
+    c->th_by = by;
     const float t = time_ms(
         [&](int n) {
-          ThArgs<R> A = th_args<R>(c);
-          A.dt = 0;
-          for (int q = 0; q < n; ++q) thermal_kernel<R, 0><<<grd, blk, smem, c->stream>>>(A);
-          CHECK_LAUNCH(c);
+          for (int q = 0; q < n; ++q) {
+            const cosim_status ts = launch_thermal<R>(c, R(0), false);
+            if (ts != COSIM_OK) return ts;
+          }
           return COSIM_OK;
         },
         5);
     if (t < best) best = t, best_by = by;
   }
+  c->th_by = keep_by;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != COSIM_OK) return st;
@@ -1524,7 +1554,8 @@ extern "C" cosim_status cosim_autotune(cosim_ctx *c, uint32_t flags, int32_t *em
     if (!em_tile_y || !th_block_y) return fail(c, COSIM_ERR_INVALID, "FIXED needs both heights");
     ty = *em_tile_y, by = *th_block_y;
     const bool ok_ty = ty == kEmTY || (ty == kEmTYSmall && c->prec != COSIM_FP64);
-    if (!ok_ty || (by != 4 && by != 8 && by != 16)) return fail(c, COSIM_ERR_INVALID, "unsupported launch shape");
+    if (!ok_ty || (by != 0 && by != 4 && by != 8 && by != 16))
+      return fail(c, COSIM_ERR_INVALID, "unsupported launch shape");
     CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
     drop_graph(c);
     c->em_ty = ty;

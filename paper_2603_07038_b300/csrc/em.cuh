@@ -210,12 +210,6 @@ __device__ __forceinline__ R e_update(R e_old, R dtW, R drive, R Se, R Ss, R lq,
 // kEmBoxX = TX + 4 nodes wide; threads index it from that remainder.
 template <int TX>
 __host__ __device__ constexpr int em_box_x() { return TX + 4; }
-// A TMA destination in shared memory must be 128-byte aligned: every box is
-// padded to a multiple of 128 bytes.
-template <typename R, int ROWS, int BX>
-struct alignas(128) EmBox {
-  R v[ROWS][BX];
-};
 // voxel box: columns i0-1 .. i0+TX-1 from x rounded down to 16 bytes
 template <int TX>
 __host__ __device__ constexpr int em_vox_box_x() { return (TX + 1 + 15 + 15) / 16 * 16; }

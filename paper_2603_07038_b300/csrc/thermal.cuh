@@ -9,6 +9,8 @@
 // Conductances and capacities are recomputed from the voxel IDs on the fly
 // (1 byte per cell streamed) instead of being stored per node.
 #pragma once
+#include <cuda.h>  // CUtensorMap
+
 #include "common.cuh"
 
 namespace cosim {
@@ -133,6 +135,143 @@ __global__ void __launch_bounds__(512) thermal_kernel(const ThArgs<R> A) {  // b
 #pragma unroll
     for (int q = 0; q < 6; ++q) t_cur[q] = t_nxt[q];
     p_cur = p_nxt;
+  }
+}
+
+// ---- the same step with TMA-staged planes. A CTA of 32 x kThTY threads owns
+// a 32 x kThTY tile of node columns (no halo compute: the update of a node
+// reads only old temperatures) and marches in z. Per plane one thread copies
+// into shared memory the temperature with a one-node halo (x from i0 - 4, the
+// 16-byte rule; y from j0 - 1), the source power of the tile and the voxel IDs
+// of the layer above (x from i0 - 16), plus the plane's z record; four
+// stages, one mbarrier each, bounded waits. The arithmetic per node is that
+// of thermal_kernel<R, 0>, term for term, so both give identical results.
+constexpr int kThTY = 8;
+constexpr int kThStages = 4, kThAhead = 3;
+template <typename R>
+struct ThStage {
+  EmBox<R, kThTY + 2, 40> T;     // rows j0-1 .. j0+kThTY, columns i0-4 .. i0+35
+  EmBox<R, kThTY, 32> P;         // the tile's nodes
+  EmBox<uint8_t, kThTY + 1, 48> V;  // voxel rows j0-1 .. j0+kThTY-1, columns i0-16 ..
+  EmBox<R, 1, 4> Z;              // hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
+};
+template <typename R>
+__host__ __device__ constexpr size_t th_stage_offset(int nmat) {
+  return ((size_t)(nmat + 1) * M_COLS * sizeof(R) + 127) & ~size_t(127);
+}
+
+template <typename R>
+struct ThTmaArgs {
+  ThArgs<R> a;               // geometry, T in / out, P, dt, films
+  CUtensorMap tmT, tmP, tmV;  // boxes 40 x (kThTY+2), 32 x kThTY, 48 x (kThTY+1) (x, y, 1 plane)
+  const R *zt;               // per node plane: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
+  int *err;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(32 * kThTY, 4) thermal_tma_kernel(const __grid_constant__ ThTmaArgs<R> TA) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  const ThArgs<R> &A = TA.a;
+  const Geo<R> &g = A.g;
+  R *s_mt = reinterpret_cast<R *>(smem);
+  ThStage<R> *stg = reinterpret_cast<ThStage<R> *>(smem + th_stage_offset<R>(g.nmat));
+  __shared__ uint64_t bars[kThStages];
+  __shared__ int s_abort;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const bool leader = tx == 0 && ty == 0;
+  if (leader) {
+    bool ok = (smem_u32(stg) & 127u) == 0 && (sizeof(ThStage<R>) & 127u) == 0 && ((size_t)&TA.tmT & 63u) == 0 &&
+              ((size_t)&TA.tmP & 63u) == 0 && ((size_t)&TA.tmV & 63u) == 0;
+    s_abort = ok ? 0 : 1;
+    if (!ok) atomicExch(TA.err, 2);
+    for (int q = 0; q < kThStages; ++q) mbar_init(&bars[q], 1);
+    fence_mbar_init();
+  }
+  stage_table(s_mt, g.mtab, (g.nmat + 1) * M_COLS);  // row nmat: all zero (outside the grid)
+  __syncthreads();
+  if (s_abort) return;
+  const int nx = g.nx, ny = g.ny, nz = g.nz, vd = g.nmat;
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * kThTY;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool act = i <= nx && j <= ny;
+  const bool has_p = A.P != nullptr;
+  const unsigned fixed_bytes =
+      (unsigned)(((kThTY + 2) * 40 + (has_p ? kThTY * 32 : 0)) * (int)sizeof(R) + 4 * (int)sizeof(R));
+  const unsigned vox_bytes = (unsigned)((kThTY + 1) * 48);
+  auto issue = [&](int k) {
+    if (k > nz) return;
+    const int s = k % kThStages;
+    ThStage<R> &S = stg[s];
+    mbar_arrive_expect_tx(&bars[s], fixed_bytes + (k < nz ? vox_bytes : 0u));
+    tma_load_3d(&S.T.v[0][0], &TA.tmT, i0 - 4, j0 - 1, k, &bars[s]);
+    if (has_p) tma_load_3d(&S.P.v[0][0], &TA.tmP, i0, j0, k, &bars[s]);
+    if (k < nz) tma_load_3d(&S.V.v[0][0], &TA.tmV, i0 - 16, j0 - 1, k, &bars[s]);
+    bulk_load(&S.Z.v[0][0], TA.zt + 4 * (size_t)k, 4 * sizeof(R), &bars[s]);
+  };
+  const R hxm = (act && i > 0) ? g.h[0][i - 1] : R(0), hx0 = (act && i < nx) ? g.h[0][i] : R(0);
+  const R hym = (act && j > 0) ? g.h[1][j - 1] : R(0), hy0 = (act && j < ny) ? g.h[1][j] : R(0);
+  const R ihxm = (act && i > 0) ? g.ih[0][i - 1] : R(0), ihx0 = (act && i < nx) ? g.ih[0][i] : R(0);
+  const R ihym = (act && j > 0) ? g.ih[1][j - 1] : R(0), ihy0 = (act && j < ny) ? g.ih[1][j] : R(0);
+  const R fxy = ((i == 0 ? A.hconv[0] : R(0)) + (i == nx ? A.hconv[1] : R(0))) * R(0.5) * (hym + hy0) +
+                ((j == 0 ? A.hconv[2] : R(0)) + (j == ny ? A.hconv[3] : R(0))) * R(0.5) * (hxm + hx0);
+  const R az = R(0.25) * (hxm + hx0) * (hym + hy0);
+  const bool cx0 = i - 1 >= 0 && i - 1 < nx, cx1 = i < nx, cy0 = j - 1 >= 0 && j - 1 < ny, cy1 = j < ny;
+  const long long id0 = act ? g.nid(i, j, 0) : 0;
+  const int cT = tx + 4, cV = tx + 15, r1 = ty + 1;  // columns / row of this node in the boxes
+  LayerSums<R> lo = {0, 0, 0, 0, 0, 0};
+  R T_km1 = 0;
+  if (leader)
+    for (int q = 0; q < kThAhead; ++q) issue(q);
+  for (int k = 0; k <= nz; ++k) {
+    {
+      bool ok = mbar_wait(&bars[k % kThStages], (unsigned)(k / kThStages) & 1u);
+      if (k + 1 <= nz) ok = mbar_wait(&bars[(k + 1) % kThStages], (unsigned)((k + 1) / kThStages) & 1u) && ok;
+      if (!ok) s_abort = 1;
+    }
+    __syncthreads();  // every thread is done with plane k-1: its stage can be refilled
+    if (s_abort) {
+      if (leader) {
+        for (int q = k; q <= k + kThAhead && q <= nz; ++q)
+          mbar_wait(&bars[q % kThStages], (unsigned)(q / kThStages) & 1u);
+        atomicExch(TA.err, 1);
+      }
+      return;
+    }
+    if (leader) {
+      fence_proxy_async_smem();
+      issue(k + kThAhead);
+    }
+    const ThStage<R> &S0 = stg[k % kThStages];
+    const ThStage<R> &S1 = stg[(k + 1) % kThStages];
+    R hz, ihz, idz_unused, hzm;
+    {
+      const R *z = &S0.Z.v[0][0];
+      hz = z[0], ihz = z[1], idz_unused = z[2], hzm = z[3];
+      (void)idz_unused;
+    }
+    const bool kz = k < nz;
+    const int m00 = (kz && cx0 && cy0) ? (int)S0.V.v[ty][cV] : vd;
+    const int m01 = (kz && cx1 && cy0) ? (int)S0.V.v[ty][cV + 1] : vd;
+    const int m10 = (kz && cx0 && cy1) ? (int)S0.V.v[r1][cV] : vd;
+    const int m11 = (kz && cx1 && cy1) ? (int)S0.V.v[r1][cV + 1] : vd;
+    const LayerSums<R> up = layer_sums(s_mt, m00, m01, m10, m11, hxm, hx0, hym, hy0, hz, ihz);
+    const R Gxp = (lo.ax_p + up.ax_p) * ihx0, Gxm = (lo.ax_m + up.ax_m) * ihxm;
+    const R Gyp = (lo.ay_p + up.ay_p) * ihy0, Gym = (lo.ay_m + up.ay_m) * ihym;
+    const R Gzp = up.gz, Gzm = lo.gz;
+    const R C = lo.cap + up.cap;
+    R film = fxy * R(0.5) * (hzm + hz);
+    if (k == 0) film += A.hconv[4] * az;
+    if (k == nz) film += A.hconv[5] * az;
+    const R T_c = S0.T.v[r1][cT];
+    const R T_kp1 = kz ? S1.T.v[r1][cT] : R(0);
+    const R p = has_p ? S0.P.v[ty][tx] : R(0);
+    const R flux = Gxm * (S0.T.v[r1][cT - 1] - T_c) + Gxp * (S0.T.v[r1][cT + 1] - T_c) +
+                   Gym * (S0.T.v[ty][cT] - T_c) + Gyp * (S0.T.v[r1 + 1][cT] - T_c) + Gzm * (T_km1 - T_c) +
+                   Gzp * (T_kp1 - T_c) + film * (A.T_amb - T_c) + p;
+    if (act) A.Tn[id0 + (long long)k * g.plane] = T_c + A.dt * flux / C;
+    T_km1 = T_c;
+    lo = up;
   }
 }
 
