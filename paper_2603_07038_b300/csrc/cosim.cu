@@ -97,6 +97,7 @@ struct cosim_ctx {
   int em_ty = kEmTY;   // EM tile height of FP32 plain steps
   int th_by = 0;       // thermal step kernel: 0 = TMA-staged tiles, 4/8/16 = classic block height
   CUtensorMap thT[2], thP, thV;  // the TMA thermal kernel's T (per buffer), P and voxel boxes
+  CUtensorMap mvU[3], mvM, mvV;  // the TMA matvec's boxes of the CG direction Pv, the constraint bits, voxels
   void *zt = nullptr;  // per node plane k: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1) (zero outside)
   int vpx = 0;         // voxel row pitch
   int4 *src_ent = nullptr;
@@ -301,6 +302,10 @@ static cudaError_t set_smem_limits() {
                             (const void *)em_step_kernel<R, long long, kEmTX, kEmTY, true>};
   for (const void *k : kernels)
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, em)) != cudaSuccess) return e;
+  const int mvt = (int)(mv_stage_offset<R, kMvTX, kMvTY>(kMaxMat) + kMvStages * sizeof(MvStage<R, kMvTX, kMvTY>) + 128);
+  if ((e = cudaFuncSetAttribute(hex8_matvec_tma_kernel<R, kMvTX, kMvTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                mvt)) != cudaSuccess)
+    return e;
   const int th = (int)(th_stage_offset<R>(kMaxMat) + kThStages * sizeof(ThStage<R>) + 128);
   if ((e = cudaFuncSetAttribute(thermal_tma_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, th)) !=
       cudaSuccess)
@@ -1068,6 +1073,17 @@ static cosim_status mech_alloc(cosim_ctx *c) {
   ALLOC(c, c->VM, (size_t)c->nx * c->ny * c->nz * c->rsz);
   ALLOC(c, c->UMAG, c->npad * c->rsz);
   ALLOC(c, c->cg, sizeof(CgScalars));
+  cosim_status st;
+  for (int a = 0; a < 3; ++a)
+    if ((st = encode_node_map(c, &c->mvU[a], c->Pv[a], kMvTY + 1, kMvTX + 4)) != COSIM_OK) return st;
+  {
+    const cuuint64_t dims[3] = {(cuuint64_t)c->nx + 1, (cuuint64_t)c->ny + 1, (cuuint64_t)c->nz + 1};
+    const cuuint64_t strides[2] = {(cuuint64_t)c->px, (cuuint64_t)c->plane};
+    const cuuint32_t box[3] = {(cuuint32_t)kMvTX + 16, (cuuint32_t)kMvTY + 1, 1};
+    if ((st = encode_map(c, &c->mvM, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, c->mask, dims, strides, box)) != COSIM_OK)
+      return st;
+  }
+  if ((st = encode_voxel_map(c, &c->mvV, kMvTY)) != COSIM_OK) return st;
   c->mech_ready = true;
   return COSIM_OK;
 }
@@ -1108,9 +1124,23 @@ static cosim_status matvec_g(cosim_ctx *c, const Geo<R> &g, void *const u[3], vo
   A.partial = partial;
   const dim3 blk(kMvTX, kMvTY);
   const dim3 grd((c->nx + 1 + kMvTX - 2) / (kMvTX - 1), (c->ny + 1 + kMvTY - 2) / (kMvTY - 1));
-  const size_t smem =
-      ((size_t)c->mats.size() * M_COLS + 2 * 3 * (kMvTY + 1) * (kMvTX + 1) + 24 * kMvTY * kMvTX) * sizeof(R);
-  hex8_matvec_kernel<R, kMvTX, kMvTY><<<grd, blk, smem, c->stream>>>(A); ++c->launches;
+  // the CG direction in the context precision has TMA descriptors: staged kernel
+  if (sizeof(R) == (size_t)c->rsz && u[0] == c->Pv[0] && u[1] == c->Pv[1] && u[2] == c->Pv[2]) {
+    MvTmaArgs<R> T;
+    T.a = A;
+    for (int a = 0; a < 3; ++a) T.tmU[a] = c->mvU[a];
+    T.tmM = c->mvM;
+    T.tmV = c->mvV;
+    T.zt = (const R *)c->zt;
+    T.err = c->dev_err;
+    const size_t smem = mv_stage_offset<R, kMvTX, kMvTY>((int)c->mats.size()) +
+                        kMvStages * sizeof(MvStage<R, kMvTX, kMvTY>) + 128;
+    hex8_matvec_tma_kernel<R, kMvTX, kMvTY><<<grd, blk, smem, c->stream>>>(T); ++c->launches;
+  } else {
+    const size_t smem =
+        ((size_t)c->mats.size() * M_COLS + 2 * 3 * (kMvTY + 1) * (kMvTX + 1) + 24 * kMvTY * kMvTX) * sizeof(R);
+    hex8_matvec_kernel<R, kMvTX, kMvTY><<<grd, blk, smem, c->stream>>>(A); ++c->launches;
+  }
   CHECK_LAUNCH(c);
   return COSIM_OK;
 }

@@ -12,6 +12,8 @@
 // W(G) = lambda tr(G)^2 + mu G:(G + G^T) over the groups, and its gradient
 // maps back through the transposed butterfly. About 300 flops per element.
 #pragma once
+#include <cuda.h>  // CUtensorMap
+
 #include "common.cuh"
 
 namespace cosim {
@@ -240,6 +242,172 @@ __global__ void __launch_bounds__(TX *TY) hex8_matvec_kernel(const MvArgs<R> A) 
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const R uc = A.u[c][id];
+      const R yv = ((mk >> c) & 1) ? uc : acc[c];
+      A.y[c][id] = yv;
+      part += yv * uc;
+    }
+    dot += (double)part;
+  }
+  if (A.partial != nullptr) {
+    const double s = block_sum(dot);
+    if (tid == 0) A.partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// ---- the same matvec with TMA-staged planes: per node plane one thread
+// copies the three components of u (36 x (TY+1) node boxes from x rounded
+// down to a multiple of 4), the constraint bits of those nodes (48-byte rows
+// from x rounded down to 16), the voxel IDs of the element layer and the
+// plane's z record into four mbarrier-tracked shared-memory stages while the
+// threads work on earlier planes. Elements, gather and arithmetic are those
+// of hex8_matvec_kernel, term for term: the results are identical.
+constexpr int kMvStages = 4, kMvAhead = 3;
+template <typename R, int TX, int TY>
+struct MvStage {
+  EmBox<R, TY + 1, TX + 4> U[3];         // nodes X0 .. X0+TX, Y0 .. Y0+TY (from x rounded to 4)
+  EmBox<uint8_t, TY + 1, TX + 16> M;     // constraint bits of the same nodes (from x rounded to 16)
+  EmBox<uint8_t, TY, TX + 16> V;         // voxel IDs of elements X0 .. X0+TX-1, Y0 .. Y0+TY-1
+  EmBox<R, 1, 4> Z;                      // hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
+};
+template <typename R, int TX, int TY>
+__host__ __device__ constexpr size_t mv_stage_offset(int nmat) {
+  return (((size_t)(nmat + 1) * M_COLS + 24 * TY * TX) * sizeof(R) + 127) & ~size_t(127);
+}
+
+template <typename R>
+struct MvTmaArgs {
+  MvArgs<R> a;
+  CUtensorMap tmU[3], tmM, tmV;
+  const R *zt;
+  int *err;
+};
+
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) hex8_matvec_tma_kernel(const __grid_constant__ MvTmaArgs<R> TA) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  const MvArgs<R> &A = TA.a;
+  const Geo<R> &g = A.g;
+  R *s_mt = reinterpret_cast<R *>(smem);
+  R *sr = s_mt + (g.nmat + 1) * M_COLS;  // [24][TY][TX]
+  MvStage<R, TX, TY> *stg = reinterpret_cast<MvStage<R, TX, TY> *>(smem + mv_stage_offset<R, TX, TY>(g.nmat));
+  __shared__ uint64_t bars[kMvStages];
+  __shared__ int s_abort;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const bool leader = tid == 0;
+  if (leader) {
+    bool ok = (smem_u32(stg) & 127u) == 0 && (sizeof(MvStage<R, TX, TY>) & 127u) == 0 &&
+              ((size_t)&TA.tmU[0] & 63u) == 0 && ((size_t)&TA.tmM & 63u) == 0 && ((size_t)&TA.tmV & 63u) == 0;
+    s_abort = ok ? 0 : 1;
+    if (!ok) atomicExch(TA.err, 2);
+    for (int q = 0; q < kMvStages; ++q) mbar_init(&bars[q], 1);
+    fence_mbar_init();
+  }
+  stage_table(s_mt, g.mtab, g.nmat * M_COLS);
+  __syncthreads();
+  if (s_abort) return;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int X0 = blockIdx.x * (TX - 1) - 1, Y0 = blockIdx.y * (TY - 1) - 1;
+  const int xr = X0 & 3, xu0 = X0 - xr;      // u boxes
+  const int xmr = X0 & 15, xm0 = X0 - xmr;   // mask and voxel boxes
+  const int ex = X0 + tx, ey = Y0 + ty;
+  const bool elem_xy = ex >= 0 && ex < nx && ey >= 0 && ey < ny;
+  const int X = ex + 1, Y = ey + 1;
+  const bool own = tx < TX - 1 && ty < TY - 1 && X <= nx && Y <= ny;
+  const R hx = elem_xy ? g.h[0][ex] : R(1), hy = elem_xy ? g.h[1][ey] : R(1);
+  const unsigned fixed_bytes =
+      (unsigned)(3 * (TY + 1) * (TX + 4) * (int)sizeof(R) + (TY + 1) * (TX + 16) + 4 * (int)sizeof(R));
+  const unsigned vox_bytes = (unsigned)(TY * (TX + 16));
+  auto issue = [&](int k) {
+    if (k > nz) return;
+    const int s = k % kMvStages;
+    MvStage<R, TX, TY> &S = stg[s];
+    mbar_arrive_expect_tx(&bars[s], fixed_bytes + (k < nz ? vox_bytes : 0u));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tma_load_3d(&S.U[c].v[0][0], &TA.tmU[c], xu0, Y0, k, &bars[s]);
+    tma_load_3d(&S.M.v[0][0], &TA.tmM, xm0, Y0, k, &bars[s]);
+    if (k < nz) tma_load_3d(&S.V.v[0][0], &TA.tmV, xm0, Y0, k, &bars[s]);
+    bulk_load(&S.Z.v[0][0], TA.zt + 4 * (size_t)k, 4 * sizeof(R), &bars[s]);
+  };
+  auto sr_at = [&](int slot, int qy, int qx) -> R & { return sr[(slot * TY + qy) * TX + qx]; };
+  // u at box position (qy, qx) of a stage with its constrained components zeroed
+  auto u_at = [&](const MvStage<R, TX, TY> &S, int c, int qy, int qx) -> R {
+    const uint8_t mk = S.M.v[qy][qx - xr + xmr];
+    return ((mk >> c) & 1) ? R(0) : S.U[c].v[qy][qx];
+  };
+  if (leader)
+    for (int q = 0; q < kMvAhead; ++q) issue(q);
+  R acc[3] = {0, 0, 0};
+  double dot = 0.0;
+  const int cu = tx + xr;  // element corner (ex, ey) column in the u boxes
+  for (int k = 0; k < nz; ++k) {
+    {
+      bool ok = mbar_wait(&bars[k % kMvStages], (unsigned)(k / kMvStages) & 1u);
+      ok = mbar_wait(&bars[(k + 1) % kMvStages], (unsigned)((k + 1) / kMvStages) & 1u) && ok;
+      if (!ok) s_abort = 1;
+    }
+    __syncthreads();  // planes k, k+1 landed; every thread is done with plane k-1 and with sr
+    if (s_abort) {
+      if (leader) {
+        for (int q = k; q <= k + kMvAhead && q <= nz; ++q)
+          mbar_wait(&bars[q % kMvStages], (unsigned)(q / kMvStages) & 1u);
+        atomicExch(TA.err, 1);
+      }
+      return;
+    }
+    if (leader) {
+      fence_proxy_async_smem();
+      issue(k + kMvAhead);
+    }
+    const MvStage<R, TX, TY> &S0 = stg[k % kMvStages];
+    const MvStage<R, TX, TY> &S1 = stg[(k + 1) % kMvStages];
+    R r[3][8];
+    if (elem_xy) {
+      const int m = S0.V.v[ty][tx + xmr];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+          r[c][a] = u_at((a >> 2) ? S1 : S0, c, ty + ((a >> 1) & 1), cu + (a & 1));
+      hex8_apply(r, s_mt[m * M_COLS + M_LAM], s_mt[m * M_COLS + M_MU], hx, hy, S0.Z.v[0][0]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int a = 0; a < 8; ++a) r[c][a] = 0;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) sr_at(c * 8 + a, ty, tx) = r[c][a];
+    __syncthreads();
+    if (own) {
+      const long long id = g.nid(X, Y, k);
+      const uint8_t mk = S0.M.v[ty + 1][cu + 1 - xr + xmr];
+      R part = 0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const R bottom = (sr_at(c * 8 + 3, ty, tx) + sr_at(c * 8 + 2, ty, tx + 1)) +
+                         (sr_at(c * 8 + 1, ty + 1, tx) + sr_at(c * 8 + 0, ty + 1, tx + 1));
+        const R top = (sr_at(c * 8 + 7, ty, tx) + sr_at(c * 8 + 6, ty, tx + 1)) +
+                      (sr_at(c * 8 + 5, ty + 1, tx) + sr_at(c * 8 + 4, ty + 1, tx + 1));
+        const R uc = S0.U[c].v[ty + 1][cu + 1];
+        const R yv = ((mk >> c) & 1) ? uc : acc[c] + bottom;
+        A.y[c][id] = yv;
+        part += yv * uc;
+        acc[c] = top;
+      }
+      dot += (double)part;
+    }
+  }
+  if (own) {  // the top node plane: plane nz is still staged (nothing was issued after it)
+    const MvStage<R, TX, TY> &S = stg[nz % kMvStages];
+    const long long id = g.nid(X, Y, nz);
+    const uint8_t mk = S.M.v[ty + 1][cu + 1 - xr + xmr];
+    R part = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const R uc = S.U[c].v[ty + 1][cu + 1];
       const R yv = ((mk >> c) & 1) ? uc : acc[c];
       A.y[c][id] = yv;
       part += yv * uc;
