@@ -149,6 +149,19 @@ def traffic_from_profile(kernel_src):
     return None
 
 
+def whole_job(ms_local, units_per_step, steps, world, device="cuda"):
+    """Each rank times its own replica of the workload; the job's time is the
+    slowest rank's (all-reduce MAX when world > 1) and its rate is all ranks'
+    units over that time, in G units/s. Returns (ms_total, rate)."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_step / (ms / steps * 1e-3) / 1e9
+
+
 def gpu_arm(args, rank, world):
     import numpy as np
     import torch
@@ -218,12 +231,9 @@ def gpu_arm(args, rank, world):
     em_ms = sum(r[0].elapsed_time(r[1]) for r in recs)
     th_ms = sum(r[1].elapsed_time(r[2]) for r in recs)
     cg_ms = sum(r[2].elapsed_time(r[3]) for r in recs)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
     updates_step = p.n_cells * N_EM + p.n_nodes * N_TH + p.n_nodes * N_CG
+    ms_total, value = whole_job(ms_total, updates_step, args.steps, world)
+    ms_step = ms_total / args.steps
     # the paper's own marching (Sec. II-A), outside the timed region: EM steps
     # with sigma(T) and a thermal step at the EM dt after each
     ctx.em_steps(N_CPL, coupled=True)
@@ -233,7 +243,6 @@ def gpu_arm(args, rank, world):
     c1.record(stream)
     torch.cuda.synchronize()
     cpl_ms = c0.elapsed_time(c1) / N_CPL
-    value = world * updates_step / (ms_step * 1e-3) / 1e9
     em_launch_ms = em_ms / (args.steps * N_EM)
     alg = em_alg_bytes(ctx, p)
     peaks = load_peaks()
