@@ -542,10 +542,12 @@ template <typename R>
 __global__ void __launch_bounds__(256) cg_init_kernel(long long n, const R *f0, const R *f1, const R *f2,
                                                        const R *d0, const R *d1, const R *d2, R *x0, R *x1,
                                                        R *x2, R *r0, R *r1, R *r2, R *p0, R *p1, R *p2,
-                                                       double *part_rz, double *part_bb) {
+                                                       double *part_rz, double *part_bb, R scale) {
+  // scale: a power of two that brings the right-hand side to order one
+  // (exact: the iteration is then the unscaled one times that factor)
   double rz = 0, bb = 0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-    const R a0 = f0[q], a1 = f1[q], a2 = f2[q];
+    const R a0 = scale * f0[q], a1 = scale * f1[q], a2 = scale * f2[q];
     const R z0 = d0[q] * a0, z1 = d1[q] * a1, z2 = d2[q] * a2;
     x0[q] = 0; x1[q] = 0; x2[q] = 0;
     r0[q] = a0; r1[q] = a1; r2[q] = a2;
@@ -584,6 +586,16 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long n, const CgSca
   if (threadIdx.x == 0) {
     part_rz[blockIdx.x] = rz;
     part_rr[blockIdx.x] = rr;
+  }
+}
+
+// x *= s for the three components (undoes the right-hand-side scaling)
+template <typename R>
+__global__ void __launch_bounds__(256) scale3_kernel(long long n, R *x0, R *x1, R *x2, R s) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    x0[q] *= s;
+    x1[q] *= s;
+    x2[q] *= s;
   }
 }
 
