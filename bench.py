@@ -50,6 +50,7 @@ def parse():
     a.add_argument("--no-e2e", action="store_true")
     a.add_argument("--no-cpu", action="store_true")
     a.add_argument("--no-serve", action="store_true")
+    a.add_argument("--no-cg-solve", action="store_true")
     a.add_argument("--serve-n", type=int, default=16)
     a.add_argument("--serve-em-steps", type=int, default=512)
     return a.parse_args()
@@ -243,6 +244,7 @@ def gpu_arm(args, rank, world):
     c1.record(stream)
     torch.cuda.synchronize()
     cpl_ms = c0.elapsed_time(c1) / N_CPL
+    cg = None if args.no_cg_solve else stress_cg_solve(ctx, p, stream)
     em_launch_ms = em_ms / (args.steps * N_EM)
     alg = em_alg_bytes(ctx, p)
     peaks = load_peaks()
@@ -263,7 +265,9 @@ def gpu_arm(args, rank, world):
                    "thermal_gnode_steps_s": round(p.n_nodes * N_TH * args.steps / (th_ms * 1e-3) / 1e9, 3),
                    "stress_slice_ms": round(cg_ms / args.steps, 3),
                    "coupled_ms_per_step": round(cpl_ms, 4),
-                   "coupled_gcell_steps_s": round(p.n_cells / (cpl_ms * 1e-3) / 1e9, 3)},
+                   "coupled_gcell_steps_s": round(p.n_cells / (cpl_ms * 1e-3) / 1e9, 3),
+                   "stress_cg_s_per_solve": cg["s_per_solve"] if cg else None},
+        "stress_cg": cg,
         "roofline": {"kernel": "em_step_kernel", "bound": "hbm", "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "alg_bytes_per_launch": alg,
@@ -279,6 +283,39 @@ def gpu_arm(args, rank, world):
     if rank == 0 and not args.no_serve:
         out["serving"] = serving_arm(args)
     return out
+
+
+def stress_cg_solve(ctx, p, stream, rise=60.0, rtol=1e-6, maxit=20000):
+    """One whole stress solve (after the timed region): FP32 Jacobi-PCG with
+    FP64 dot products to a 1e-6 relative residual, bottom face clamped, under
+    a synthetic hot spot (a Gaussian rise of `rise` K centred on the package,
+    width sqrt(0.05) of each lateral extent, falling linearly from the top to
+    a fifth of it at the bottom) built on the device and written through the
+    C ABI. The EM burst of a bench step heats the package by nano-kelvins
+    only, so that load would not exercise the solver's convergence."""
+    import torch
+
+    from paper_2603_07038_b300 import cosim as api
+    f64 = dict(dtype=torch.float64, device="cuda")
+    gx = torch.exp(-((torch.arange(p.nx + 1, **f64) / p.nx - 0.5) ** 2) / 0.05)
+    gy = torch.exp(-((torch.arange(p.ny + 1, **f64) / p.ny - 0.5) ** 2) / 0.05)
+    gz = torch.linspace(0.2, 1.0, p.nz + 1, **f64)
+    T = 300.0 + rise * gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+    ctx.write(api.COSIM_F_T, T.reshape(-1))
+    del T
+    torch.cuda.empty_cache()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    rep = ctx.stress_solve(bc=api.COSIM_MECH_CLAMPED_BOTTOM, T_ref=300.0, rtol=rtol, maxit=maxit, check_every=64,
+                           allow_not_converged=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) * 1e-3
+    return {"s_per_solve": round(sec, 3), "iters": int(rep["iters"]), "relres": float(rep["relres"]),
+            "converged": rep["status"] == api.COSIM_OK, "ms_per_iter": round(sec * 1e3 / max(rep["iters"], 1), 3),
+            "dofs": 3 * p.n_nodes, "precision": "FP32 vectors and matvec, FP64 dots",
+            "load": "synthetic %.0f K hot spot, bottom clamped, rtol %g" % (rise, rtol)}
 
 
 def serving_arm(args, workers=4):

@@ -158,6 +158,71 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
   return true;
 }
 
+// ---- Arithmetic written once for one node (R) or two adjacent nodes (the
+// pair type R2: float2 / double2). Every operation rounds once, to nearest,
+// and the pair forms act element by element, so a kernel that handles a node
+// pair per thread gives bit for bit the results of one that handles a single
+// node. FP32 pairs use the packed FP32 instructions of sm_100 and later (one
+// instruction for both nodes); FP64 pairs are two scalar operations.
+template <typename R>
+struct Pair2;
+template <>
+struct Pair2<float> {
+  using T = float2;
+};
+template <>
+struct Pair2<double> {
+  using T = double2;
+};
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+// a - b, evaluated as a + (-b) (the same IEEE result)
+__device__ __forceinline__ float sub_(float a, float b) { return __fadd_rn(a, -b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dadd_rn(a, -b); }
+__device__ __forceinline__ float2 fma_(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul_(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add_(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub_(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ double2 fma_(double2 a, double2 b, double2 c) {
+  return make_double2(fma_(a.x, b.x, c.x), fma_(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 mul_(double2 a, double2 b) { return make_double2(mul_(a.x, b.x), mul_(a.y, b.y)); }
+__device__ __forceinline__ double2 add_(double2 a, double2 b) { return make_double2(add_(a.x, b.x), add_(a.y, b.y)); }
+__device__ __forceinline__ double2 sub_(double2 a, double2 b) { return make_double2(sub_(a.x, b.x), sub_(a.y, b.y)); }
+// broadcast a scalar to V (a scalar or a pair)
+__device__ __forceinline__ void splat_(float s, float &v) { v = s; }
+__device__ __forceinline__ void splat_(float s, float2 &v) { v = make_float2(s, s); }
+__device__ __forceinline__ void splat_(double s, double &v) { v = s; }
+__device__ __forceinline__ void splat_(double s, double2 &v) { v = make_double2(s, s); }
+template <typename V, typename R>
+__device__ __forceinline__ V bc_(R s) {
+  V v;
+  splat_(s, v);
+  return v;
+}
+// Reciprocal of a positive normal number: in FP32 the hardware approximation
+// refined by one Newton-Raphson step, r' = r + r (1 - x r) (within about an
+// ulp of 1/x); in FP64 the correctly rounded quotient.
+__device__ __forceinline__ float rcp_approx_(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rcp_(float x) {
+  const float r = rcp_approx_(x);
+  return __fmaf_rn(r, __fmaf_rn(-x, r, 1.0f), r);
+}
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float2 rcp_(float2 x) {
+  const float2 r = make_float2(rcp_approx_(x.x), rcp_approx_(x.y));
+  return __ffma2_rn(r, __ffma2_rn(make_float2(-x.x, -x.y), r, make_float2(1.0f, 1.0f)), r);
+}
+__device__ __forceinline__ double2 rcp_(double2 x) { return make_double2(rcp_(x.x), rcp_(x.y)); }
+
 // Sum of v over the block (any shape up to 1024 threads); the result is valid
 // in thread 0. Fixed summation order: deterministic run to run.
 __device__ __forceinline__ double block_sum(double v) {

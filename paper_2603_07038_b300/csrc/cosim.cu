@@ -349,10 +349,10 @@ static cosim_status encode_node_map(cosim_ctx *c, CUtensorMap *m, void *base, in
                     dims, strides, box);
 }
 // voxel IDs: (x, y, z) = (nx, ny, nz) bytes with row pitch vpx
-static cosim_status encode_voxel_map(cosim_ctx *c, CUtensorMap *m, int rows) {
+static cosim_status encode_voxel_map(cosim_ctx *c, CUtensorMap *m, int rows, int cols = em_vox_box_x<kEmTX>()) {
   const cuuint64_t dims[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->nz};
   const cuuint64_t strides[2] = {(cuuint64_t)c->vpx, (cuuint64_t)c->vpx * c->ny};
-  const cuuint32_t box[3] = {(cuuint32_t)em_vox_box_x<kEmTX>(), (cuuint32_t)rows, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)cols, (cuuint32_t)rows, 1};
   return encode_map(c, m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, c->mat, dims, strides, box);
 }
 
@@ -537,9 +537,9 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
       if ((st = encode_node_map(c, &c->tmT[t][p], c->T[p], (t == 0 ? kEmTY : kEmTYSmall) + 1)) != COSIM_OK)
         return st;
   for (int p = 0; p < 2; ++p)
-    if ((st = encode_node_map(c, &c->thT[p], c->T[p], kThTY + 2, 40)) != COSIM_OK) return st;
-  if ((st = encode_node_map(c, &c->thP, c->P, kThTY, 32)) != COSIM_OK) return st;
-  if ((st = encode_voxel_map(c, &c->thV, kThTY + 1)) != COSIM_OK) return st;
+    if ((st = encode_node_map(c, &c->thT[p], c->T[p], kThTY + 2, kThBoxT)) != COSIM_OK) return st;
+  if ((st = encode_node_map(c, &c->thP, c->P, kThTY, kThTX)) != COSIM_OK) return st;
+  if ((st = encode_voxel_map(c, &c->thV, kThTY + 1, kThBoxV)) != COSIM_OK) return st;
   ALLOC(c, c->scratch, c->npad * 8);
   const int mv_blocks = ((c->nx + 1) + kMvTX - 2) / (kMvTX - 1) * (((c->ny + 1) + kMvTY - 2) / (kMvTY - 1));
   c->npart = std::max(kRedBlocks, mv_blocks);
@@ -690,14 +690,13 @@ static cosim_status launch_thermal(cosim_ctx *c, R dt, bool count = true) {
     T.tmT = c->thT[c->tpar];
     T.tmP = c->thP;
     T.tmV = c->thV;
-    T.zt = (const R *)c->zt;
     T.err = c->dev_err;
-    const dim3 blk(32, kThTY), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + kThTY - 1) / kThTY);
+    const dim3 blk(32, kThTY), grd((c->nx + 1 + kThTX - 1) / kThTX, (c->ny + 1 + kThTY - 1) / kThTY);
     const size_t smem = th_stage_offset<R>((int)c->mats.size()) + kThStages * sizeof(ThStage<R>) + 128;
     thermal_tma_kernel<R><<<grd, blk, smem, c->stream>>>(T);
   } else {
     const dim3 blk(32, c->th_by), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + c->th_by - 1) / c->th_by);
-    thermal_kernel<R, 0><<<grd, blk, c->mats.size() * M_COLS * sizeof(R), c->stream>>>(A);
+    thermal_kernel<R, 0><<<grd, blk, (c->mats.size() + 1) * sizeof(typename Pair2<R>::T), c->stream>>>(A);
   }
   CHECK_LAUNCH(c);
   if (count) ++c->launches;
@@ -1006,6 +1005,7 @@ static ThArgs<R> th_args(cosim_ctx *c) {
   A.To = (const R *)c->T[c->tpar];
   A.Tn = (R *)c->T[c->tpar ^ 1];
   A.P = (const R *)c->P;
+  A.zt = (const R *)c->zt;
   A.T_amb = (R)(c->T_amb - c->T_init);
   for (int f = 0; f < 6; ++f) A.hconv[f] = (R)c->h_conv[f];
   A.ratio_out = nullptr;
@@ -1018,7 +1018,7 @@ static cosim_status thermal_limit_t(cosim_ctx *c) {
   ThArgs<R> A = th_args<R>(c);
   A.ratio_out = (R *)c->scratch;
   const dim3 blk(32, 8), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + 7) / 8);
-  const size_t smem = c->mats.size() * M_COLS * sizeof(R);
+  const size_t smem = (c->mats.size() + 1) * sizeof(typename Pair2<R>::T);
   thermal_kernel<R, 1><<<grd, blk, smem, c->stream>>>(A); ++c->launches;
   CHECK_LAUNCH(c);
   min_partial_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(A.g, (const R *)c->scratch, c->part); ++c->launches;

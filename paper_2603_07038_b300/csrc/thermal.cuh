@@ -8,6 +8,10 @@
 // h A_i (T_amb - T_i), A_i the node's share of the face.
 // Conductances and capacities are recomputed from the voxel IDs on the fly
 // (1 byte per cell streamed) instead of being stored per node.
+//
+// The arithmetic of a node is written once (th_layer, th_coeffs, th_update)
+// for a scalar or for a pair of adjacent nodes; both kernels below use it, so
+// every launch shape gives the same bits.
 #pragma once
 #include <cuda.h>  // CUtensorMap
 
@@ -21,67 +25,158 @@ struct ThArgs {
   const R *To;
   R *Tn;
   const R *P;       // W per node, may be null
+  const R *zt;      // per node plane k: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1) (zero outside the grid)
   R dt;
   R T_amb;
   R hconv[6];
   R *ratio_out;     // dt-limit kernel: C_i / (sum G + film) per node
 };
 
-// Voxel-layer sums of one node column (thread (i, j)) for the layer of cells
-// kk, between node planes kk and kk+1. Each of the four voxels
-// (i-1+dx, j-1+dy, kk) contributes k_c times its quarter cross-section to the
-// edges it borders and rho_cp V / 8 to the node capacities. A node at plane k
-// adds the sums of layers k-1 and k, so each layer is evaluated once and
-// carried to the next plane in registers.
+// Per-material {k, rho_cp} pairs (rows 0 .. nmat, row nmat all zero) from the
+// device material table into shared memory (call by all threads, then sync).
 template <typename R>
-struct LayerSums {
-  R ax_p, ax_m;  // x-edges i -> i+1 and i-1 -> i: sum k_c * hy_c * hz / 4
-  R ay_p, ay_m;  // y-edges j -> j+1 and j-1 -> j: sum k_c * hx_c * hz / 4
-  R gz;          // z-edge kk -> kk+1 conductance: sum k_c hx_c hy_c / 4 / hz
-  R cap;         // sum rho_cp V / 8
+__device__ __forceinline__ void stage_kc(typename Pair2<R>::T *dst, const R *mtab, int nmat) {
+  const int nt = blockDim.x * blockDim.y * blockDim.z;
+  const int t = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+  for (int m = t; m <= nmat; m += nt) {
+    typename Pair2<R>::T v;
+    v.x = mtab[m * M_COLS + M_K];
+    v.y = mtab[m * M_COLS + M_RHOCP];
+    dst[m] = v;
+  }
+}
+
+// Constants of a node column (i, j); V is R for one node or R2 for a pair.
+// Cell sizes and quarter inverse lengths of cells outside the grid are zero,
+// which removes every term of a voxel outside the grid whatever its material
+// value (any finite value).
+template <typename V>
+struct ThCol {
+  V hxm, hx0, hym, hy0;  // sizes of the cells i-1, i (x) and j-1, j (y)
+  V qxm, qx0, qym, qy0;  // a quarter of their inverse sizes
+  V fxy;                 // lateral film: sum of (h_conv x half the face's other extent) / 2
+  V az;                  // the node's share of a z face
 };
 
 template <typename R>
-__device__ __forceinline__ LayerSums<R> layer_sums(const R *s_mt, int m00, int m01, int m10, int m11, R hxm, R hx0,
-                                                   R hym, R hy0, R hz, R ihz) {
-  // m<dy><dx>: voxel (i-1+dx, j-1+dy, kk); missing voxels contribute zero
-  const R k00 = mconst(s_mt, m00, M_K), k01 = mconst(s_mt, m01, M_K);
-  const R k10 = mconst(s_mt, m10, M_K), k11 = mconst(s_mt, m11, M_K);
-  const R q = R(0.25) * hz;
-  LayerSums<R> L;
-  L.ax_p = q * (k01 * hym + k11 * hy0);
-  L.ax_m = q * (k00 * hym + k10 * hy0);
-  L.ay_p = q * (k10 * hxm + k11 * hx0);
-  L.ay_m = q * (k00 * hxm + k01 * hx0);
-  L.gz = R(0.25) * ihz * (hym * (k00 * hxm + k01 * hx0) + hy0 * (k10 * hxm + k11 * hx0));
-  L.cap = R(0.125) * hz *
-          (hym * (mconst(s_mt, m00, M_RHOCP) * hxm + mconst(s_mt, m01, M_RHOCP) * hx0) +
-           hy0 * (mconst(s_mt, m10, M_RHOCP) * hxm + mconst(s_mt, m11, M_RHOCP) * hx0));
+__device__ __forceinline__ ThCol<R> th_column(const Geo<R> &g, const ThArgs<R> &A, int i, int j) {
+  const int nx = g.nx, ny = g.ny;
+  const bool in = i >= 0 && i <= nx && j >= 0 && j <= ny;
+  ThCol<R> c;
+  c.hxm = (in && i > 0) ? g.h[0][i - 1] : R(0);
+  c.hx0 = (in && i < nx) ? g.h[0][i] : R(0);
+  c.hym = (in && j > 0) ? g.h[1][j - 1] : R(0);
+  c.hy0 = (in && j < ny) ? g.h[1][j] : R(0);
+  c.qxm = (in && i > 0) ? mul_(R(0.25), g.ih[0][i - 1]) : R(0);
+  c.qx0 = (in && i < nx) ? mul_(R(0.25), g.ih[0][i]) : R(0);
+  c.qym = (in && j > 0) ? mul_(R(0.25), g.ih[1][j - 1]) : R(0);
+  c.qy0 = (in && j < ny) ? mul_(R(0.25), g.ih[1][j]) : R(0);
+  const R hcx = add_(i == 0 ? A.hconv[0] : R(0), i == nx ? A.hconv[1] : R(0));
+  const R hcy = add_(j == 0 ? A.hconv[2] : R(0), j == ny ? A.hconv[3] : R(0));
+  c.fxy = mul_(R(0.25), fma_(hcx, add_(c.hym, c.hy0), mul_(hcy, add_(c.hxm, c.hx0))));
+  c.az = mul_(R(0.25), mul_(add_(c.hxm, c.hx0), add_(c.hym, c.hy0)));
+  return c;
+}
+
+template <typename R>
+__device__ __forceinline__ ThCol<typename Pair2<R>::T> th_pair(const ThCol<R> &a, const ThCol<R> &b) {
+  ThCol<typename Pair2<R>::T> c;
+  c.hxm = {a.hxm, b.hxm}, c.hx0 = {a.hx0, b.hx0}, c.hym = {a.hym, b.hym}, c.hy0 = {a.hy0, b.hy0};
+  c.qxm = {a.qxm, b.qxm}, c.qx0 = {a.qx0, b.qx0}, c.qym = {a.qym, b.qym}, c.qy0 = {a.qy0, b.qy0};
+  c.fxy = {a.fxy, b.fxy}, c.az = {a.az, b.az};
+  return c;
+}
+
+// Sums of one voxel layer seen from a node column: the voxels
+// (i-1+dx, j-1+dy) of the layer (k<dy><dx> conductivities, c<dy><dx>
+// capacities) give, before the layer height and the quarter factor,
+//   kxm / kxp: the x-edges i-1 -> i and i -> i+1 (k_c times the cell's y size),
+//   kym / kyp: the y-edges j-1 -> j and j -> j+1 (k_c times the x size),
+//   gzs: the z-edge sum of k_c hx hy, cs: the capacity sum of rho_cp hx hy.
+// A node at plane k adds the sums of the layers k-1 and k, so each layer is
+// formed once and carried to the next plane in registers.
+template <typename V>
+struct ThLayer {
+  V kxm, kxp, kym, kyp, gzs, cs;
+};
+
+template <typename V>
+__device__ __forceinline__ ThLayer<V> th_layer(V k00, V k01, V k10, V k11, V c00, V c01, V c10, V c11,
+                                               const ThCol<V> &c) {
+  ThLayer<V> L;
+  L.kxm = fma_(k00, c.hym, mul_(k10, c.hy0));
+  L.kxp = fma_(k01, c.hym, mul_(k11, c.hy0));
+  L.kym = fma_(k00, c.hxm, mul_(k01, c.hx0));
+  L.kyp = fma_(k10, c.hxm, mul_(k11, c.hx0));
+  L.gzs = fma_(c.hym, L.kym, mul_(c.hy0, L.kyp));
+  L.cs = fma_(c.hym, fma_(c00, c.hxm, mul_(c01, c.hx0)), mul_(c.hy0, fma_(c10, c.hxm, mul_(c11, c.hx0))));
   return L;
+}
+
+template <typename V, typename R>
+__device__ __forceinline__ ThLayer<V> th_layer_zero() {
+  const V z = bc_<V>(R(0));
+  return {z, z, z, z, z, z};
+}
+
+// Conductances of the six edges, the film coefficient and the capacity of a
+// node at plane k from the layers below (lo, height hzm) and above (up, hz);
+// gz carries the z-edge conductance: in, the edge below (the previous plane's
+// upper edge); out, this plane's upper edge.
+template <typename V>
+struct ThCoeffs {
+  V Gxm, Gxp, Gym, Gyp, Gzm, Gzp, film, C;
+};
+
+template <typename V, typename R>
+__device__ __forceinline__ ThCoeffs<V> th_coeffs(const ThCol<V> &c, const ThLayer<V> &lo, const ThLayer<V> &up,
+                                                 R hz, R ihz, R hzm, bool bottom, bool top, const R *hconv, V &gz) {
+  ThCoeffs<V> q;
+  const V vz = bc_<V>(hz), vzm = bc_<V>(hzm);
+  q.Gxm = mul_(fma_(vzm, lo.kxm, mul_(vz, up.kxm)), c.qxm);
+  q.Gxp = mul_(fma_(vzm, lo.kxp, mul_(vz, up.kxp)), c.qx0);
+  q.Gym = mul_(fma_(vzm, lo.kym, mul_(vz, up.kym)), c.qym);
+  q.Gyp = mul_(fma_(vzm, lo.kyp, mul_(vz, up.kyp)), c.qy0);
+  q.Gzm = gz;
+  q.Gzp = mul_(up.gzs, bc_<V>(mul_(R(0.25), ihz)));
+  gz = q.Gzp;
+  q.C = mul_(fma_(vzm, lo.cs, mul_(vz, up.cs)), bc_<V>(R(0.125)));
+  q.film = mul_(c.fxy, bc_<V>(add_(hzm, hz)));
+  if (bottom) q.film = fma_(bc_<V>(hconv[4]), c.az, q.film);
+  if (top) q.film = fma_(bc_<V>(hconv[5]), c.az, q.film);
+  return q;
+}
+
+// Forward-Euler step of the node (Eq. 5): T + dt (sum G (T_nb - T) + film
+// (T_amb - T) + P) / C.
+template <typename V, typename R>
+__device__ __forceinline__ V th_update(const ThCoeffs<V> &q, V Tc, V Tim, V Tip, V Tjm, V Tjp, V Tkm, V Tkp, V p,
+                                       R T_amb, R dt) {
+  V f = fma_(q.Gxm, sub_(Tim, Tc), p);
+  f = fma_(q.Gxp, sub_(Tip, Tc), f);
+  f = fma_(q.Gym, sub_(Tjm, Tc), f);
+  f = fma_(q.Gyp, sub_(Tjp, Tc), f);
+  f = fma_(q.Gzm, sub_(Tkm, Tc), f);
+  f = fma_(q.Gzp, sub_(Tkp, Tc), f);
+  f = fma_(q.film, sub_(bc_<V>(T_amb), Tc), f);
+  return fma_(mul_(bc_<V>(dt), f), rcp_(q.C), Tc);
 }
 
 // One forward-Euler step (Eq. 5). Thread per (i, j) node column, marching in z.
 // MODE 0: step T; MODE 1: write the per-node stability ratio C / (sum G + film).
 template <typename R, int MODE>
 __global__ void __launch_bounds__(512) thermal_kernel(const ThArgs<R> A) {  // blocks of 32 x (4, 8 or 16)
-  extern __shared__ unsigned char smem_raw[];
-  R *s_mt = reinterpret_cast<R *>(smem_raw);
+  using R2 = typename Pair2<R>::T;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  R2 *s_kc = reinterpret_cast<R2 *>(smem_raw);
   const Geo<R> &g = A.g;
-  stage_table(s_mt, g.mtab, g.nmat * M_COLS);
+  stage_kc<R>(s_kc, g.mtab, g.nmat);
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int nx = g.nx, ny = g.ny, nz = g.nz, vd = g.nmat;
   if (i > nx || j > ny) return;
-  const R hxm = i > 0 ? g.h[0][i - 1] : R(0), hx0 = i < nx ? g.h[0][i] : R(0);
-  const R hym = j > 0 ? g.h[1][j - 1] : R(0), hy0 = j < ny ? g.h[1][j] : R(0);
-  const R ihxm = i > 0 ? g.ih[0][i - 1] : R(0), ihx0 = i < nx ? g.ih[0][i] : R(0);
-  const R ihym = j > 0 ? g.ih[1][j - 1] : R(0), ihy0 = j < ny ? g.ih[1][j] : R(0);
-  // convective faces touching this column: x/y walls (per plane: times the dual z length)
-  const R fxy = ((i == 0 ? A.hconv[0] : R(0)) + (i == nx ? A.hconv[1] : R(0))) * R(0.5) * (hym + hy0) +
-                ((j == 0 ? A.hconv[2] : R(0)) + (j == ny ? A.hconv[3] : R(0))) * R(0.5) * (hxm + hx0);
-  const R az = R(0.25) * (hxm + hx0) * (hym + hy0);  // z-face share of the node
-  LayerSums<R> lo = {0, 0, 0, 0, 0, 0};
+  const ThCol<R> c = th_column(g, A, i, j);
   const long long id0 = g.nid(i, j, 0);
   // Software pipeline: the values of plane k+1 (its voxels, the in-plane and
   // upper neighbours of T, the source) are requested one iteration ahead so
@@ -91,6 +186,8 @@ __global__ void __launch_bounds__(512) thermal_kernel(const ThArgs<R> A) {  // b
     m[1] = g.cell(i, j - 1, k);
     m[2] = g.cell(i - 1, j, k);
     m[3] = g.cell(i, j, k);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) m[q] = m[q] < 0 ? vd : m[q];
     if (MODE == 0 && k <= nz) {
       const long long id = id0 + (long long)k * g.plane;
       t[0] = k < nz ? A.To[id + g.plane] : R(0);
@@ -104,28 +201,20 @@ __global__ void __launch_bounds__(512) thermal_kernel(const ThArgs<R> A) {  // b
   int m_cur[4], m_nxt[4];
   R t_cur[6] = {0, 0, 0, 0, 0, 0}, t_nxt[6] = {0, 0, 0, 0, 0, 0}, p_cur = 0, p_nxt = 0;
   load_plane(0, m_cur, t_cur, p_cur);
-  R T_km1 = 0, T_c = MODE == 0 ? A.To[id0] : R(0);
+  R T_km1 = 0, T_c = MODE == 0 ? A.To[id0] : R(0), gz = 0;
+  ThLayer<R> lo = th_layer_zero<R, R>();
   for (int k = 0; k <= nz; ++k) {
     const long long id = id0 + (long long)k * g.plane;
     if (k < nz) load_plane(k + 1, m_nxt, t_nxt, p_nxt);
-    const R hz = k < nz ? g.h[2][k] : R(0), ihz = k < nz ? g.ih[2][k] : R(0);
-    const R hzm = k > 0 ? g.h[2][k - 1] : R(0);
-    const LayerSums<R> up = layer_sums(s_mt, m_cur[0], m_cur[1], m_cur[2], m_cur[3], hxm, hx0, hym, hy0, hz, ihz);
-    const R Gxp = (lo.ax_p + up.ax_p) * ihx0, Gxm = (lo.ax_m + up.ax_m) * ihxm;
-    const R Gyp = (lo.ay_p + up.ay_p) * ihy0, Gym = (lo.ay_m + up.ay_m) * ihym;
-    const R Gzp = up.gz, Gzm = lo.gz;
-    const R C = lo.cap + up.cap;
-    R film = fxy * R(0.5) * (hzm + hz);
-    if (k == 0) film += A.hconv[4] * az;
-    if (k == nz) film += A.hconv[5] * az;
+    const R hz = A.zt[4 * k], ihz = A.zt[4 * k + 1], hzm = A.zt[4 * k + 3];
+    const R2 v0 = s_kc[m_cur[0]], v1 = s_kc[m_cur[1]], v2 = s_kc[m_cur[2]], v3 = s_kc[m_cur[3]];
+    const ThLayer<R> up = th_layer<R>(v0.x, v1.x, v2.x, v3.x, v0.y, v1.y, v2.y, v3.y, c);
+    const ThCoeffs<R> q = th_coeffs<R, R>(c, lo, up, hz, ihz, hzm, k == 0, k == nz, A.hconv, gz);
     if (MODE == 1) {
-      A.ratio_out[id] = C / (Gxp + Gxm + Gyp + Gym + Gzp + Gzm + film);
+      A.ratio_out[id] = q.C / (q.Gxp + q.Gxm + q.Gyp + q.Gym + q.Gzp + q.Gzm + q.film);
     } else {
       const R T_kp1 = t_cur[0];
-      const R flux = Gxm * (t_cur[1] - T_c) + Gxp * (t_cur[2] - T_c) + Gym * (t_cur[3] - T_c) +
-                     Gyp * (t_cur[4] - T_c) + Gzm * (T_km1 - T_c) + Gzp * (T_kp1 - T_c) +
-                     film * (A.T_amb - T_c) + p_cur;
-      A.Tn[id] = T_c + A.dt * flux / C;
+      A.Tn[id] = th_update<R, R>(q, T_c, t_cur[1], t_cur[2], t_cur[3], t_cur[4], T_km1, T_kp1, p_cur, A.T_amb, A.dt);
       T_km1 = T_c;
       T_c = T_kp1;
     }
@@ -138,43 +227,47 @@ __global__ void __launch_bounds__(512) thermal_kernel(const ThArgs<R> A) {  // b
   }
 }
 
-// ---- the same step with TMA-staged planes. A CTA of 32 x kThTY threads owns
-// a 32 x kThTY tile of node columns (no halo compute: the update of a node
-// reads only old temperatures) and marches in z. Per plane one thread copies
-// into shared memory the temperature with a one-node halo (x from i0 - 4, the
-// 16-byte rule; y from j0 - 1), the source power of the tile and the voxel IDs
-// of the layer above (x from i0 - 16), plus the plane's z record; four
-// stages, one mbarrier each, bounded waits. The arithmetic per node is that
-// of thermal_kernel<R, 0>, term for term, so both give identical results.
-constexpr int kThTY = 8;
+// ---- the same step with TMA-staged planes and two nodes per thread. A CTA
+// of 32 x kThTY threads owns a 64 x kThTY tile of node columns (thread tx:
+// nodes i0 + 2 tx and i0 + 2 tx + 1 of row j0 + ty; no halo compute: the
+// update of a node reads only old temperatures) and marches in z. Per plane
+// one thread copies into shared memory the temperature with a one-node halo
+// (x from i0 - 4, the 16-byte rule; y from j0 - 1), the tile's source power
+// and the voxel IDs of the layer above (x from i0 - 16), plus the plane's z
+// record; four stages, one mbarrier each, bounded waits. Positions outside
+// the grid arrive as zero (a valid material ID and a finite temperature that
+// the zero geometry factors then remove).
+constexpr int kThTY = 8, kThTX = 64;
 constexpr int kThStages = 4, kThAhead = 3;
+constexpr int kThBoxT = kThTX + 8;   // temperature box width: columns i0-4 .. i0+67
+constexpr int kThBoxV = kThTX + 32;  // voxel box width: columns i0-16 .. i0+79
 template <typename R>
 struct ThStage {
-  EmBox<R, kThTY + 2, 40> T;     // rows j0-1 .. j0+kThTY, columns i0-4 .. i0+35
-  EmBox<R, kThTY, 32> P;         // the tile's nodes
-  EmBox<uint8_t, kThTY + 1, 48> V;  // voxel rows j0-1 .. j0+kThTY-1, columns i0-16 ..
-  EmBox<R, 1, 4> Z;              // hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
+  EmBox<R, kThTY + 2, kThBoxT> T;        // rows j0-1 .. j0+kThTY
+  EmBox<R, kThTY, kThTX> P;              // the tile's nodes
+  EmBox<uint8_t, kThTY + 1, kThBoxV> V;  // voxel rows j0-1 .. j0+kThTY-1
+  EmBox<R, 1, 4> Z;                      // hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
 };
 template <typename R>
 __host__ __device__ constexpr size_t th_stage_offset(int nmat) {
-  return ((size_t)(nmat + 1) * M_COLS * sizeof(R) + 127) & ~size_t(127);
+  return ((size_t)(nmat + 1) * sizeof(typename Pair2<R>::T) + 127) & ~size_t(127);
 }
 
 template <typename R>
 struct ThTmaArgs {
-  ThArgs<R> a;               // geometry, T in / out, P, dt, films
-  CUtensorMap tmT, tmP, tmV;  // boxes 40 x (kThTY+2), 32 x kThTY, 48 x (kThTY+1) (x, y, 1 plane)
-  const R *zt;               // per node plane: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
+  ThArgs<R> a;                // geometry, T in / out, P, z records, dt, films
+  CUtensorMap tmT, tmP, tmV;  // boxes kThBoxT x (kThTY+2), kThTX x kThTY, kThBoxV x (kThTY+1) (one plane)
   int *err;
 };
 
 template <typename R>
-__global__ void __launch_bounds__(32 * kThTY, 4) thermal_tma_kernel(const __grid_constant__ ThTmaArgs<R> TA) {
+__global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? 4 : 2) thermal_tma_kernel(const __grid_constant__ ThTmaArgs<R> TA) {
+  using R2 = typename Pair2<R>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const ThArgs<R> &A = TA.a;
   const Geo<R> &g = A.g;
-  R *s_mt = reinterpret_cast<R *>(smem);
+  R2 *s_kc = reinterpret_cast<R2 *>(smem);
   ThStage<R> *stg = reinterpret_cast<ThStage<R> *>(smem + th_stage_offset<R>(g.nmat));
   __shared__ uint64_t bars[kThStages];
   __shared__ int s_abort;
@@ -188,52 +281,46 @@ __global__ void __launch_bounds__(32 * kThTY, 4) thermal_tma_kernel(const __grid
     for (int q = 0; q < kThStages; ++q) mbar_init(&bars[q], 1);
     fence_mbar_init();
   }
-  stage_table(s_mt, g.mtab, (g.nmat + 1) * M_COLS);  // row nmat: all zero (outside the grid)
+  stage_kc<R>(s_kc, g.mtab, g.nmat);
   __syncthreads();
   if (s_abort) return;
-  const int nx = g.nx, ny = g.ny, nz = g.nz, vd = g.nmat;
-  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * kThTY;
-  const int i = i0 + tx, j = j0 + ty;
-  const bool act = i <= nx && j <= ny;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int i0 = blockIdx.x * kThTX, j0 = blockIdx.y * kThTY;
+  const int ia = i0 + 2 * tx, j = j0 + ty;  // nodes ia (.x) and ia + 1 (.y) of row j
+  const bool act_a = ia <= nx && j <= ny, act_b = ia + 1 <= nx && j <= ny;
   const bool has_p = A.P != nullptr;
-  const unsigned fixed_bytes =
-      (unsigned)(((kThTY + 2) * 40 + (has_p ? kThTY * 32 : 0)) * (int)sizeof(R) + 4 * (int)sizeof(R));
-  const unsigned vox_bytes = (unsigned)((kThTY + 1) * 48);
+  const unsigned stage_bytes = (unsigned)(((kThTY + 2) * kThBoxT + (has_p ? kThTY * kThTX : 0)) * (int)sizeof(R) +
+                                          4 * (int)sizeof(R) + (kThTY + 1) * kThBoxV);
   auto issue = [&](int k) {
     if (k > nz) return;
-    const int s = k % kThStages;
+    const int s = k & (kThStages - 1);
     ThStage<R> &S = stg[s];
-    mbar_arrive_expect_tx(&bars[s], fixed_bytes + (k < nz ? vox_bytes : 0u));
+    mbar_arrive_expect_tx(&bars[s], stage_bytes);
     tma_load_3d(&S.T.v[0][0], &TA.tmT, i0 - 4, j0 - 1, k, &bars[s]);
     if (has_p) tma_load_3d(&S.P.v[0][0], &TA.tmP, i0, j0, k, &bars[s]);
-    if (k < nz) tma_load_3d(&S.V.v[0][0], &TA.tmV, i0 - 16, j0 - 1, k, &bars[s]);
-    bulk_load(&S.Z.v[0][0], TA.zt + 4 * (size_t)k, 4 * sizeof(R), &bars[s]);
+    // the voxel layer above plane k; at k = nz the box lies wholly above the
+    // grid and arrives as zeros
+    tma_load_3d(&S.V.v[0][0], &TA.tmV, i0 - 16, j0 - 1, k, &bars[s]);
+    bulk_load(&S.Z.v[0][0], A.zt + 4 * (size_t)k, 4 * sizeof(R), &bars[s]);
   };
-  const R hxm = (act && i > 0) ? g.h[0][i - 1] : R(0), hx0 = (act && i < nx) ? g.h[0][i] : R(0);
-  const R hym = (act && j > 0) ? g.h[1][j - 1] : R(0), hy0 = (act && j < ny) ? g.h[1][j] : R(0);
-  const R ihxm = (act && i > 0) ? g.ih[0][i - 1] : R(0), ihx0 = (act && i < nx) ? g.ih[0][i] : R(0);
-  const R ihym = (act && j > 0) ? g.ih[1][j - 1] : R(0), ihy0 = (act && j < ny) ? g.ih[1][j] : R(0);
-  const R fxy = ((i == 0 ? A.hconv[0] : R(0)) + (i == nx ? A.hconv[1] : R(0))) * R(0.5) * (hym + hy0) +
-                ((j == 0 ? A.hconv[2] : R(0)) + (j == ny ? A.hconv[3] : R(0))) * R(0.5) * (hxm + hx0);
-  const R az = R(0.25) * (hxm + hx0) * (hym + hy0);
-  const bool cx0 = i - 1 >= 0 && i - 1 < nx, cx1 = i < nx, cy0 = j - 1 >= 0 && j - 1 < ny, cy1 = j < ny;
-  const long long id0 = act ? g.nid(i, j, 0) : 0;
-  const int cT = tx + 4, cV = tx + 15, r1 = ty + 1;  // columns / row of this node in the boxes
-  LayerSums<R> lo = {0, 0, 0, 0, 0, 0};
-  R T_km1 = 0;
+  const ThCol<R2> c = th_pair<R>(th_column(g, A, ia, j), th_column(g, A, ia + 1, j));
+  const int cT = 2 * tx + 4, cV = 2 * tx + 15, r1 = ty + 1;  // columns / row of node ia in the boxes
+  R *tp = A.Tn + (act_a ? g.nid(ia, j, 0) : 0);
+  ThLayer<R2> lo = th_layer_zero<R2, R>();
+  R2 T_km1 = bc_<R2>(R(0)), gz = bc_<R2>(R(0));
   if (leader)
     for (int q = 0; q < kThAhead; ++q) issue(q);
+  bool ok0 = mbar_wait(&bars[0], 0u);
   for (int k = 0; k <= nz; ++k) {
-    {
-      bool ok = mbar_wait(&bars[k % kThStages], (unsigned)(k / kThStages) & 1u);
-      if (k + 1 <= nz) ok = mbar_wait(&bars[(k + 1) % kThStages], (unsigned)((k + 1) / kThStages) & 1u) && ok;
+    {  // plane k landed one iteration earlier (or above, for k = 0); wait for plane k+1
+      const bool ok = (k + 1 > nz || mbar_wait(&bars[(k + 1) & (kThStages - 1)], (unsigned)((k + 1) / kThStages) & 1u)) && ok0;
       if (!ok) s_abort = 1;
     }
     __syncthreads();  // every thread is done with plane k-1: its stage can be refilled
     if (s_abort) {
       if (leader) {
-        for (int q = k; q <= k + kThAhead && q <= nz; ++q)
-          mbar_wait(&bars[q % kThStages], (unsigned)(q / kThStages) & 1u);
+        for (int q = k; q < k + kThAhead && q <= nz; ++q)  // the planes issued so far
+          mbar_wait(&bars[q & (kThStages - 1)], (unsigned)(q / kThStages) & 1u);
         atomicExch(TA.err, 1);
       }
       return;
@@ -242,35 +329,28 @@ __global__ void __launch_bounds__(32 * kThTY, 4) thermal_tma_kernel(const __grid
       fence_proxy_async_smem();
       issue(k + kThAhead);
     }
-    const ThStage<R> &S0 = stg[k % kThStages];
-    const ThStage<R> &S1 = stg[(k + 1) % kThStages];
-    R hz, ihz, idz_unused, hzm;
-    {
-      const R *z = &S0.Z.v[0][0];
-      hz = z[0], ihz = z[1], idz_unused = z[2], hzm = z[3];
-      (void)idz_unused;
-    }
-    const bool kz = k < nz;
-    const int m00 = (kz && cx0 && cy0) ? (int)S0.V.v[ty][cV] : vd;
-    const int m01 = (kz && cx1 && cy0) ? (int)S0.V.v[ty][cV + 1] : vd;
-    const int m10 = (kz && cx0 && cy1) ? (int)S0.V.v[r1][cV] : vd;
-    const int m11 = (kz && cx1 && cy1) ? (int)S0.V.v[r1][cV + 1] : vd;
-    const LayerSums<R> up = layer_sums(s_mt, m00, m01, m10, m11, hxm, hx0, hym, hy0, hz, ihz);
-    const R Gxp = (lo.ax_p + up.ax_p) * ihx0, Gxm = (lo.ax_m + up.ax_m) * ihxm;
-    const R Gyp = (lo.ay_p + up.ay_p) * ihy0, Gym = (lo.ay_m + up.ay_m) * ihym;
-    const R Gzp = up.gz, Gzm = lo.gz;
-    const R C = lo.cap + up.cap;
-    R film = fxy * R(0.5) * (hzm + hz);
-    if (k == 0) film += A.hconv[4] * az;
-    if (k == nz) film += A.hconv[5] * az;
-    const R T_c = S0.T.v[r1][cT];
-    const R T_kp1 = kz ? S1.T.v[r1][cT] : R(0);
-    const R p = has_p ? S0.P.v[ty][tx] : R(0);
-    const R flux = Gxm * (S0.T.v[r1][cT - 1] - T_c) + Gxp * (S0.T.v[r1][cT + 1] - T_c) +
-                   Gym * (S0.T.v[ty][cT] - T_c) + Gyp * (S0.T.v[r1 + 1][cT] - T_c) + Gzm * (T_km1 - T_c) +
-                   Gzp * (T_kp1 - T_c) + film * (A.T_amb - T_c) + p;
-    if (act) A.Tn[id0 + (long long)k * g.plane] = T_c + A.dt * flux / C;
-    T_km1 = T_c;
+    const ThStage<R> &S0 = stg[k & (kThStages - 1)];
+    const ThStage<R> &S1 = stg[(k + 1) & (kThStages - 1)];
+    const R hz = S0.Z.v[0][0], ihz = S0.Z.v[0][1], hzm = S0.Z.v[0][3];
+    // {k, rho_cp} of the voxels ia-1, ia, ia+1 in rows j-1 (a) and j (b)
+    const R2 a0 = s_kc[S0.V.v[ty][cV]], a1 = s_kc[S0.V.v[ty][cV + 1]], a2 = s_kc[S0.V.v[ty][cV + 2]];
+    const R2 b0 = s_kc[S0.V.v[r1][cV]], b1 = s_kc[S0.V.v[r1][cV + 1]], b2 = s_kc[S0.V.v[r1][cV + 2]];
+    const ThLayer<R2> up = th_layer<R2>(R2{a0.x, a1.x}, R2{a1.x, a2.x}, R2{b0.x, b1.x}, R2{b1.x, b2.x},
+                                        R2{a0.y, a1.y}, R2{a1.y, a2.y}, R2{b0.y, b1.y}, R2{b1.y, b2.y}, c);
+    const ThCoeffs<R2> q = th_coeffs<R2, R>(c, lo, up, hz, ihz, hzm, k == 0, k == nz, A.hconv, gz);
+    const R2 Tc = *reinterpret_cast<const R2 *>(&S0.T.v[r1][cT]);
+    const R2 Tjm = *reinterpret_cast<const R2 *>(&S0.T.v[ty][cT]);
+    const R2 Tjp = *reinterpret_cast<const R2 *>(&S0.T.v[r1 + 1][cT]);
+    const R2 Tkp = k < nz ? *reinterpret_cast<const R2 *>(&S1.T.v[r1][cT]) : bc_<R2>(R(0));
+    const R2 Tim = {S0.T.v[r1][cT - 1], Tc.x}, Tip = {Tc.y, S0.T.v[r1][cT + 2]};
+    const R2 p = has_p ? *reinterpret_cast<const R2 *>(&S0.P.v[ty][2 * tx]) : bc_<R2>(R(0));
+    const R2 Tn = th_update<R2, R>(q, Tc, Tim, Tip, Tjm, Tjp, T_km1, Tkp, p, A.T_amb, A.dt);
+    if (act_b)
+      *reinterpret_cast<R2 *>(tp) = Tn;
+    else if (act_a)
+      *tp = Tn.x;
+    tp += g.plane;
+    T_km1 = Tc;
     lo = up;
   }
 }
