@@ -193,6 +193,19 @@ __device__ __forceinline__ double2 fma_(double2 a, double2 b, double2 c) {
 __device__ __forceinline__ double2 mul_(double2 a, double2 b) { return make_double2(mul_(a.x, b.x), mul_(a.y, b.y)); }
 __device__ __forceinline__ double2 add_(double2 a, double2 b) { return make_double2(add_(a.x, b.x), add_(a.y, b.y)); }
 __device__ __forceinline__ double2 sub_(double2 a, double2 b) { return make_double2(sub_(a.x, b.x), sub_(a.y, b.y)); }
+__device__ __forceinline__ float neg_(float a) { return -a; }
+__device__ __forceinline__ double neg_(double a) { return -a; }
+__device__ __forceinline__ float2 neg_(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ double2 neg_(double2 a) { return make_double2(-a.x, -a.y); }
+// load / store of V at p (a pair: two adjacent elements, p aligned to the pair)
+template <typename V, typename R>
+__device__ __forceinline__ V ldv_(const R *p) {
+  return *reinterpret_cast<const V *>(p);
+}
+template <typename V, typename R>
+__device__ __forceinline__ void stv_(R *p, const V &v) {
+  *reinterpret_cast<V *>(p) = v;
+}
 // broadcast a scalar to V (a scalar or a pair)
 __device__ __forceinline__ void splat_(float s, float &v) { v = s; }
 __device__ __forceinline__ void splat_(float s, float2 &v) { v = make_float2(s, s); }

@@ -66,6 +66,8 @@ struct cosim_ctx {
   // TMA descriptors of E, H (per parity and component) and the Joule window
   // per EM tile height (index em_ty_index): boxes of TY or TY + 1 rows
   CUtensorMap tmE[2][2][3], tmH[2][2][3], tmQ[2], tmT[2][2];
+  // the same for the interior tile pairs (boxes em2_box_x wide)
+  CUtensorMap tmE2[2][2][3], tmH2[2][2][3], tmQ2[2], tmT2[2][2];
   int *dev_err = nullptr;  // device word: a bounded in-kernel wait gave up
   int slo[3]{}, shi[3]{}, sn[3]{};
   long long psi_len[3]{};
@@ -93,7 +95,7 @@ struct cosim_ctx {
   // sources
   int *src_row = nullptr;       // = src_row_buf + kSrcPadLo
   int *src_row_buf = nullptr;   // allocation: kSrcPadLo zeros, the offsets, kSrcPadHi zeros
-  CUtensorMap tmV[2];  // voxel IDs (x, y, z), box em_vox_box_x x (TY+1) x 1 per tile height
+  CUtensorMap tmV[2], tmV2[2];  // voxel IDs (x, y, z), boxes em_vox_box_x / em2_vox_box_x x (TY+1) x 1 per tile height
   int em_ty = kEmTY;   // EM tile height of FP32 plain steps
   int th_by = 0;       // thermal step kernel: 0 = TMA-staged tiles, 4/8/16 = classic block height
   CUtensorMap thT[2], thP, thV;  // the TMA thermal kernel's T (per buffer), P and voxel boxes
@@ -294,8 +296,7 @@ static cudaError_t set_smem_limits() {
   cudaError_t e =
       cudaFuncSetAttribute(hex8_matvec_kernel<R, kMvTX, kMvTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, mv);
   if (e != cudaSuccess) return e;
-  const int em =
-      (int)(em_stage_offset<R, kEmTX, kEmTY>(kMaxMat) + kEmStages * sizeof(EmStage<R, kEmTX, kEmTY>) + 128);
+  const int em = (int)em_smem_bytes<R, kEmTY>(kMaxMat);
   const void *kernels[4] = {(const void *)em_step_kernel<R, int, kEmTX, kEmTY, false>,
                             (const void *)em_step_kernel<R, long long, kEmTX, kEmTY, false>,
                             (const void *)em_step_kernel<R, int, kEmTX, kEmTY, true>,
@@ -311,8 +312,7 @@ static cudaError_t set_smem_limits() {
       cudaSuccess)
     return e;
   if constexpr (sizeof(R) == 4) {
-    const int em4 = (int)(em_stage_offset<R, kEmTX, kEmTYSmall>(kMaxMat) +
-                          kEmStages * sizeof(EmStage<R, kEmTX, kEmTYSmall>) + 128);
+    const int em4 = (int)em_smem_bytes<R, kEmTYSmall>(kMaxMat);
     const void *small[2] = {(const void *)em_step_kernel<R, int, kEmTX, kEmTYSmall, false>,
                             (const void *)em_step_kernel<R, long long, kEmTX, kEmTYSmall, false>};
     for (const void *k : small)
@@ -525,16 +525,22 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
       for (int a = 0; a < 3; ++a) {
         if ((st = encode_node_map(c, &c->tmE[t][p][a], c->E[p][a], ty + 1)) != COSIM_OK) return st;
         if ((st = encode_node_map(c, &c->tmH[t][p][a], c->H[p][a], ty)) != COSIM_OK) return st;
+        if ((st = encode_node_map(c, &c->tmE2[t][p][a], c->E[p][a], ty + 1, em2_box_x())) != COSIM_OK) return st;
+        if ((st = encode_node_map(c, &c->tmH2[t][p][a], c->H[p][a], ty, em2_box_x())) != COSIM_OK) return st;
       }
     if ((st = encode_node_map(c, &c->tmQ[t], c->Qs, ty)) != COSIM_OK) return st;
     if ((st = encode_voxel_map(c, &c->tmV[t], ty + 1)) != COSIM_OK) return st;
+    if ((st = encode_node_map(c, &c->tmQ2[t], c->Qs, ty, em2_box_x())) != COSIM_OK) return st;
+    if ((st = encode_voxel_map(c, &c->tmV2[t], ty + 1, em2_vox_box_x())) != COSIM_OK) return st;
   }
   ALLOC(c, c->T[0], c->npad * c->rsz);
   ALLOC(c, c->T[1], c->npad * c->rsz);
   ALLOC(c, c->P, c->npad * c->rsz);
   for (int t = 0; t < 2; ++t)
     for (int p = 0; p < 2; ++p)
-      if ((st = encode_node_map(c, &c->tmT[t][p], c->T[p], (t == 0 ? kEmTY : kEmTYSmall) + 1)) != COSIM_OK)
+      if ((st = encode_node_map(c, &c->tmT[t][p], c->T[p], (t == 0 ? kEmTY : kEmTYSmall) + 1)) != COSIM_OK ||
+          (st = encode_node_map(c, &c->tmT2[t][p], c->T[p], (t == 0 ? kEmTY : kEmTYSmall) + 1, em2_box_x())) !=
+              COSIM_OK)
         return st;
   for (int p = 0; p < 2; ++p)
     if ((st = encode_node_map(c, &c->thT[p], c->T[p], kThTY + 2, kThBoxT)) != COSIM_OK) return st;
@@ -726,22 +732,29 @@ static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool
     A.fixhi[a] = c->em_bc[2 * a + 1] != COSIM_BC_PMC;
   }
   A.cpml = (const R *)c->cpml;
-  // interior tiles: every thread's node i = i0..i0+TX-1 (i0 = b (TX-1) - 1)
-  // satisfies slo < i < nx - shi, so also 0 < i < nx, and the +x neighbour
-  // i0 + TX stays <= nx; likewise in y
-  auto interior = [](int n, int lo, int hi, int T, int &b0, int &b1) {
-    b0 = b1 = 0;
-    const int nb = (n + 1 + T - 2) / (T - 1);
-    for (int b = 0; b < nb; ++b) {
-      const int i0 = b * (T - 1) - 1;
-      if (i0 >= lo + 1 && i0 + T <= n - hi) {
-        if (b1 == 0) b0 = b;
-        b1 = b + 1;
-      }
+  // Tiles of 31 x (TY-1) owned nodes. Interior rows: every thread's node
+  // j = j0..j0+TY-1 (j0 = b (TY-1) - 1) satisfies slo < j < ny - shi, so also
+  // 0 < j < ny, and the +y neighbour j0 + TY stays <= ny. Interior pairs: the
+  // single tiles bx, bx+1 (bx even) whose lane nodes i0 = 31 bx - 2 ..
+  // i0 + 63 and +x neighbour i0 + 64 satisfy the same in x.
+  A.nbx = (c->nx + 1 + kEmTX - 2) / (kEmTX - 1);
+  A.nby = (c->ny + 1 + TY - 2) / (TY - 1);
+  A.iby0 = A.iby1 = 0;
+  for (int b = 0; b < A.nby; ++b) {
+    const int j0 = b * (TY - 1) - 1;
+    if (j0 >= c->slo[1] + 1 && j0 + TY <= c->ny - c->shi[1]) {
+      if (A.iby1 == 0) A.iby0 = b;
+      A.iby1 = b + 1;
     }
-  };
-  interior(c->nx, c->slo[0], c->shi[0], kEmTX, A.ibx0, A.ibx1);
-  interior(c->ny, c->slo[1], c->shi[1], TY, A.iby0, A.iby1);
+  }
+  A.ibx0 = A.npx = 0;
+  for (int b = 0; b + 1 < A.nbx && (kEmTX - 1) * b + 62 <= c->nx - c->shi[0]; b += 2)
+    if ((kEmTX - 1) * b - 2 >= c->slo[0] + 1) {
+      if (A.npx == 0) A.ibx0 = b;
+      ++A.npx;
+    }
+  if (A.npx == 0 || A.iby1 == A.iby0) A.npx = A.iby0 = A.iby1 = 0;
+  A.n_border = A.nbx * A.nby - 2 * A.npx * (A.iby1 - A.iby0);
   A.dt = (R)c->dt;
   A.src_row = c->src_row;
   A.src_ent = c->src_ent;
@@ -751,12 +764,13 @@ static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool
   A.Q = c->Q;
   A.tmQ = c->tmQ[t];
   A.tmV = c->tmV[t];
+  A.tmQ2 = c->tmQ2[t];
+  A.tmV2 = c->tmV2[t];
   A.zt = (const R *)c->zt;
   A.err = c->dev_err;
   const dim3 blk(kEmTX, TY);
-  const dim3 grd((c->nx + 1 + kEmTX - 2) / (kEmTX - 1), (c->ny + 1 + TY - 2) / (TY - 1));
-  const size_t smem = em_stage_offset<R, kEmTX, TY>((int)c->mats.size()) +
-                      kEmStages * sizeof(EmStage<R, kEmTX, TY>) + 128;  // + alignment slack
+  const dim3 grd(A.n_border + A.npx * (A.iby1 - A.iby0));
+  const size_t smem = em_smem_bytes<R, TY>((int)c->mats.size());
   for (int64_t s = 0; s < nsteps; ++s) {
     const int o = c->par, n = c->par ^ 1;
     for (int a = 0; a < 3; ++a) {
@@ -779,12 +793,15 @@ static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool
         A.lHn[a][s2] = (R *)c->lH[n][a][s2];
       }
       A.tmE[a] = c->tmE[t][o][a];
+      A.tmE2[a] = c->tmE2[t][o][a];
+      A.tmH2[a] = c->tmH2[t][o][a];
       A.tmH[a] = c->tmH[t][o][a];
     }
     A.step_base = c->dstep;
     A.step_off = (int)s;
     A.fold = accum && ((c->n_acc + 1) % kJouleWindow == 0);
     A.tmT = c->tmT[t][c->tpar];
+    A.tmT2 = c->tmT2[t][c->tpar];
     A.Pout = (R *)c->P;
     A.inv_dt = (R)(1.0 / c->dt);
     const bool small = c->npad < (1LL << 31);

@@ -1,27 +1,37 @@
 // Fused leapfrog step of the Maxwell system (Sec. II-A, Eqs. 1-3 in E/H form)
 // with the Joule heat of the step (P_total = D_sigma e^2), one launch per step.
 //
-// Each CTA owns a (TX-1) x (TY-1) tile of nodes in x-y and marches through
+// The node grid is cut into tiles of 31 x (TY-1) nodes in x-y; each CTA
+// marches its tile (or, in the interior, a pair of x-adjacent tiles) through
 // every node plane k = 0..nz. Its threads cover the tile plus one halo column
-// (i-1) and row (j-1): at plane k every thread forms H^{n+1/2}(i,j,k) from
-// E^n (own plane and plane k+1), shares it through shared memory, and forms
-// E^{n+1} on its edges from the H of the thread to its -x/-y side and from its
+// (i-1) and row (j-1): at plane k a thread forms H^{n+1/2}(i,j,k) from E^n
+// (own plane and plane k+1), shares it through shared memory, and forms
+// E^{n+1} on its edges from the H of the node to its -x/-y side and from its
 // own H of plane k-1 (kept in registers). Halo threads recompute the H and the
 // single E edge their neighbours need (for Joule) but write nothing.
 // E, H and the CPML auxiliaries are double-buffered (read *_o, write *_n), so
 // CTAs never see each other's half-updated values.
 //
+// Interior tile pairs (every node off the lateral walls and outside the x/y
+// CPML slabs) run two nodes per thread: a warp row covers 64 nodes (62 owned
+// plus a halo pair), and the arithmetic of both nodes is issued as packed FP32
+// instructions. The border tiles run one node per thread with the wall and
+// lateral-CPML logic. Every formula is written once against the element-wise
+// helpers of common.cuh, which round exactly like the scalar operations, so a
+// node gets the same bits whichever kind of tile it falls in (and whatever
+// the tile height).
+//
 // Joule heat: the edge from node n to n+e_a dissipates sigma_e V_e ebar^2 in
 // one step, ebar = (E^n + E^{n+1})/2; half of dt times that goes to each end
 // node, i.e. (sum_c w_c sigma_c dt/2) * l_e * ebar^2 per end node, where w_c is
 // the quarter cross-section of voxel c around the edge. The node sums the six
-// halves of its incident edges (x from the thread at i-1, y from j-1 through
+// halves of its incident edges (x from the node at i-1, y from j-1 through
 // shared memory, z from its own previous plane) into a short-window
 // accumulator that is folded into the FP64 total every few steps (FP64 runs at
 // a small fraction of the FP32 rate on this GPU, so none is used per step).
 //
-// Inputs of planes k+2 and k+3 are copied to shared memory by TMA (one thread
-// issues a 2-D box per array and plane, completion tracked by one mbarrier per
+// Inputs of planes k+1..k+3 are copied to shared memory by TMA (one thread
+// issues a box per array and plane, completion tracked by one mbarrier per
 // stage, four stages) while plane k is computed. Waits on those barriers are
 // bounded: a copy that never arrives sets an error word instead of hanging.
 //
@@ -76,16 +86,21 @@ struct EmArgs {
   R *Qs;                      // null: not accumulating
   double *Q;
   int fold;
-  // tiles [ibx0, ibx1) x [iby0, iby1) lie off the lateral walls and CPML slabs
-  int ibx0, ibx1, iby0, iby1;
+  // Tiles (31 x (TY-1) owned nodes, tile (bx, by)): nbx x nby in all. The
+  // single tiles 2 npx wide from ibx0 (even) and rows [iby0, iby1) are run as
+  // npx x (iby1 - iby0) interior pairs (CTAs n_border ..); the other n_border
+  // tiles are border tiles (CTAs 0 .. n_border - 1).
+  int nbx, nby, ibx0, npx, iby0, iby1, n_border;
   // TMA descriptors of E^n, H^{n-1/2} (per component) and Qs: 3-D node
-  // arrays (x, y, z) with boxes of kEmBoxX x (TY+1 for E, TY otherwise) x 1
+  // arrays (x, y, z) with boxes of em_box_x x (TY+1 for E, TY otherwise) x 1
+  // for border tiles and the *2 ones, em2_box_x wide, for interior pairs
   CUtensorMap tmE[3], tmH[3], tmQ;
-  CUtensorMap tmV;  // voxel IDs (x, y, z), box em_vox_box_x x (TY+1) x 1
+  CUtensorMap tmE2[3], tmH2[3], tmQ2;
+  CUtensorMap tmV, tmV2;  // voxel IDs (x, y, z), boxes em_vox_box_x / em2_vox_box_x x (TY+1) x 1
   // two-way coupling (the CPL specialisation, Sec. II-A): the temperature
   // rise T^n - T_init (node array, staged like E), the step's Joule power per
   // node written to Pout [W], 1 / dt
-  CUtensorMap tmT;
+  CUtensorMap tmT, tmT2;
   R *Pout;
   R inv_dt;
   const R *zt;      // per node plane: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
@@ -106,64 +121,69 @@ __device__ __forceinline__ long long psi_index(const EmArgs<R> &A, int d, int s,
   return ((long long)s * (A.g.ny + 1) + j) * A.g.px + i;
 }
 
-// chi^n = b (chi^{n-1} + dF^n - dF^{n-1}), evaluated as t - (1-b) t; returns
-// chi^n = dF + psi (new values written only by the owner)
-template <typename R>
-__device__ __forceinline__ R chi_update(const EmArgs<R> &A, const R *s_cp, int d, int type, int slot, int s, int i,
-                                        int j, int k, R deriv, bool write) {
-  const long long q = psi_index(A, d, s, i, j, k);
-  const R omb = s_cp[(d * 2 + type) * kMaxSlab + s];
+// chi^n = b (chi^{n-1} + dF^n - dF^{n-1}) at element q of the slab arrays of
+// axis d, slot `slot`, for V one node or an x-adjacent node pair (q even);
+// omb = 1 - b. Returns chi^n = dF + psi; the owner writes the new state.
+template <typename R, typename V>
+__device__ __forceinline__ V chi_update(const EmArgs<R> &A, V omb, int d, int type, int slot, long long q, V deriv,
+                                        bool write) {
   const R *xo = type == 0 ? A.xEo[d][slot] : A.xHo[d][slot];
   const R *dd = type == 0 ? A.dEo[d][slot] : A.dHo[d][slot];
+  R *xn = type == 0 ? A.xEn[d][slot] : A.xHn[d][slot];
+  R *dn = type == 0 ? A.dEn[d][slot] : A.dHn[d][slot];
   if constexpr (sizeof(R) == 8) {
-    const R t = xo[q] + (deriv - dd[q]);
-    const R chi = t - omb * t;
+    const V t = add_(ldv_<V>(xo + q), sub_(deriv, ldv_<V>(dd + q)));
+    const V chi = fma_(neg_(omb), t, t);
     if (write) {
-      (type == 0 ? A.xEn[d][slot] : A.xHn[d][slot])[q] = chi;
-      (type == 0 ? A.dEn[d][slot] : A.dHn[d][slot])[q] = deriv;
+      stv_(xn + q, chi);
+      stv_(dn + q, deriv);
     }
     return chi;
   } else {
     // (hi + lo + D)(1 - omb) with Knuth's TwoSum for the additions, an FMA
     // product error for omb * hi, and a final renormalisation (Fast2Sum).
-    const R hi = xo[q];
-    const R lo = (type == 0 ? A.lEo[d][slot] : A.lHo[d][slot])[q];
-    const R D = deriv - dd[q];
-    const R sh = hi + D;
-    const R bv = sh - hi;
-    const R e1 = (hi - (sh - bv)) + (D - bv);
-    const R l1 = lo + e1;
-    const R p = __fmul_rn(omb, sh);
-    const R pe = __fmaf_rn(omb, sh, -p);
-    const R s2 = sh - p;
-    const R bv2 = s2 - sh;
-    const R e2 = (sh - (s2 - bv2)) + (-p - bv2);
-    const R l2 = (l1 + e2) - pe - __fmul_rn(omb, l1);
-    const R h3 = s2 + l2;
-    const R l3 = l2 - (h3 - s2);
+    const V hi = ldv_<V>(xo + q);
+    const V lo = ldv_<V>((type == 0 ? A.lEo[d][slot] : A.lHo[d][slot]) + q);
+    const V D = sub_(deriv, ldv_<V>(dd + q));
+    const V sh = add_(hi, D);
+    const V bv = sub_(sh, hi);
+    const V e1 = add_(sub_(hi, sub_(sh, bv)), sub_(D, bv));
+    const V l1 = add_(lo, e1);
+    const V p = mul_(omb, sh);
+    const V pe = fma_(omb, sh, neg_(p));
+    const V s2 = sub_(sh, p);
+    const V bv2 = sub_(s2, sh);
+    const V e2 = add_(sub_(sh, sub_(s2, bv2)), sub_(neg_(p), bv2));
+    const V l2 = sub_(sub_(add_(l1, e2), pe), mul_(omb, l1));
+    const V h3 = add_(s2, l2);
+    const V l3 = sub_(l2, sub_(h3, s2));
     if (write) {
-      (type == 0 ? A.xEn[d][slot] : A.xHn[d][slot])[q] = h3;
-      (type == 0 ? A.lEn[d][slot] : A.lHn[d][slot])[q] = l3;
-      (type == 0 ? A.dEn[d][slot] : A.dHn[d][slot])[q] = deriv;
+      stv_(xn + q, h3);
+      stv_((type == 0 ? A.lEn[d][slot] : A.lHn[d][slot]) + q, l3);
+      stv_(dn + q, deriv);
     }
     return h3;
   }
 }
 
-// (dF1 + psi1) - (dF2 + psi2) for the two derivatives of one curl component;
-// the CPML state is touched only inside a slab (s1/s2 >= 0).
+// (dF1 + psi1) - (dF2 + psi2) for the two derivatives of one curl component
+// of a single node; the CPML state is touched only inside a slab (s1/s2 >= 0).
 template <typename R>
-__device__ __forceinline__ R curl_with_psi(const EmArgs<R> &A, const R *s_cp, int type, int comp, int d1, int s1,
-                                           int d2, int s2, int i, int j, int k, R v1, R v2, bool write) {
-  (void)comp;
-  if (s1 < 0 && s2 < 0) return v1 - v2;
-  const R a = s1 >= 0 ? chi_update(A, s_cp, d1, type, 1, s1, i, j, k, v1, write) : v1;
-  const R b = s2 >= 0 ? chi_update(A, s_cp, d2, type, 0, s2, i, j, k, v2, write) : v2;
-  return a - b;
+__device__ __forceinline__ R curl_with_psi(const EmArgs<R> &A, const R *s_cp, int type, int d1, int s1, int d2,
+                                           int s2, int i, int j, int k, R v1, R v2, bool write) {
+  if (s1 < 0 && s2 < 0) return sub_(v1, v2);
+  const R a = s1 >= 0 ? chi_update<R, R>(A, s_cp[(d1 * 2 + type) * kMaxSlab + s1], d1, type, 1,
+                                         psi_index(A, d1, s1, i, j, k), v1, write)
+                      : v1;
+  const R b = s2 >= 0 ? chi_update<R, R>(A, s_cp[(d2 * 2 + type) * kMaxSlab + s2], d2, type, 0,
+                                         psi_index(A, d2, s2, i, j, k), v2, write)
+                      : v2;
+  return sub_(a, b);
 }
 
 static_assert(M_EPS == 0 && M_SDT2 == 1 && M_IMU == 2 && M_COLS % 4 == 0,
               "the EM kernel reads eps, sigma dt/2, 1/mu of a material row with one aligned vector load");
+static_assert(M_TC0 == M_TCR + 1 && M_TCR % 2 == 0, "alpha and its offset are read as one aligned pair");
 // Four consecutive values from 16-byte aligned shared memory in one vector load.
 __device__ __forceinline__ void load4(const float *p, float &a, float &b, float &c, float &d) {
   const float4 v = *reinterpret_cast<const float4 *>(p);
@@ -174,18 +194,9 @@ __device__ __forceinline__ void load4(const double *p, double &a, double &b, dou
   a = v.x, b = v.y, c = w.x, d = w.y;
 }
 
-// Reciprocal of a positive normal number: in FP32 the hardware approximation
-// refined by one Newton-Raphson step (r' = r + r (1 - x r)), within about an
-// ulp of 1/x; in FP64 the exact division.
-__device__ __forceinline__ float em_rcp(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return __fmaf_rn(r, __fmaf_rn(-x, r, 1.0f), r);
-}
-__device__ __forceinline__ double em_rcp(double x) { return 1.0 / x; }
-
-// E^{n+1} of one edge from the area-weighted sums over its <= 4 voxels, all
-// taken without the quarter factor of the voxel cross-sections (it cancels):
+// E^{n+1} of an edge (V: one node or a node pair) from the area-weighted sums
+// over its <= 4 voxels, all taken without the quarter factor of the voxel
+// cross-sections (it cancels):
 //   Se = sum w eps, Ss = sum w sigma dt/2 (w = product of the two transverse
 //   cell sizes of the voxel), dtW = dt x (sum of those products) = 4 dt x the
 //   dual-face area, lq = edge length / 4.
@@ -194,20 +205,42 @@ __device__ __forceinline__ double em_rcp(double x) { return 1.0 / x; }
 // E' = E + r (dtW (curl - J) - 2 Ss E), r = 1/(Se + Ss), which keeps the decay
 // 1 - ca of weakly lossy media at full precision. *half_q receives the edge's
 // Joule energy per end node, (Ss/4) l ebar^2 with ebar = (E + E')/2.
-template <typename R>
-__device__ __forceinline__ R e_update(R e_old, R dtW, R drive, R Se, R Ss, R lq, R *half_q) {
-  const R r = em_rcp(Se + Ss);
-  const R e_new = e_old + r * (dtW * drive - R(2) * Ss * e_old);
-  const R eb = R(0.5) * (e_old + e_new);
-  *half_q = Ss * lq * eb * eb;
+template <typename V, typename R>
+__device__ __forceinline__ V e_update(V e_old, V dtW, V drive, V Se, V Ss, V lq, V *half_q) {
+  const V r = rcp_(add_(Se, Ss));
+  const V t = fma_(dtW, drive, mul_(mul_(bc_<V>(R(-2)), Ss), e_old));
+  const V e_new = fma_(r, t, e_old);
+  const V eb = mul_(bc_<V>(R(0.5)), add_(e_old, e_new));
+  *half_q = mul_(mul_(mul_(Ss, lq), eb), eb);
   return e_new;
+}
+
+// H^{n+1/2} = H^{n-1/2} - (dt/2 / dual length) (series mean of 1/mu) curl:
+// hd = dt/2 x the inverse dual length, (ha, ua), (hb, ub) the two voxels'
+// lengths along the dual edge and their 1/mu.
+template <typename V>
+__device__ __forceinline__ V h_update(V h_old, V hd, V ha, V ua, V hb, V ub, V curl) {
+  return fma_(neg_(mul_(hd, fma_(ha, ua, mul_(hb, ub)))), curl, h_old);
+}
+
+// sigma dt/2 of a voxel at the edge temperature rise te (coupled steps):
+// sigma0 dt/2 / (1 + alpha (T_init + te - T0)) = M_SDT2 / (M_TC0 + M_TCR te)
+template <typename V>
+__device__ __forceinline__ V sig_t(V sdt2, V tcr, V tc0, V te) {
+  return mul_(sdt2, rcp_(fma_(tcr, te, tc0)));
+}
+
+// derivative (b - a) / h
+template <typename V>
+__device__ __forceinline__ V dif_(V b, V a, V ih) {
+  return mul_(sub_(b, a), ih);
 }
 
 // One plane of the CTA's inputs, staged in shared memory by TMA: E^n of the
 // tile plus its +x/+y neighbours, H^{n-1/2} and the Joule accumulator. A TMA
 // box must start at an x coordinate that is a multiple of 16 bytes, so the
 // box starts at the tile's first node rounded down to a multiple of 4 and is
-// kEmBoxX = TX + 4 nodes wide; threads index it from that remainder.
+// TX + 4 nodes wide; threads index it from that remainder.
 template <int TX>
 __host__ __device__ constexpr int em_box_x() { return TX + 4; }
 // voxel box: columns i0-1 .. i0+TX-1 from x rounded down to 16 bytes
@@ -216,6 +249,10 @@ __host__ __device__ constexpr int em_vox_box_x() { return (TX + 1 + 15 + 15) / 1
 // source-row box: rows j0 .. j0+TY (+1 for the end offset) from a multiple of 4
 template <int TY>
 __host__ __device__ constexpr int em_src_box() { return (TY + 1 + 3 + 3) / 4 * 4; }
+// interior pairs: 64 nodes per warp row (+ the +x neighbour, + the rounding)
+constexpr int kEm2Nodes = 64;
+__host__ __device__ constexpr int em2_box_x() { return em_box_x<kEm2Nodes>(); }
+__host__ __device__ constexpr int em2_vox_box_x() { return em_vox_box_x<kEm2Nodes>(); }
 template <typename R, int TX, int TY>
 struct EmStage {
   EmBox<R, TY + 1, em_box_x<TX>()> E[3];
@@ -231,9 +268,15 @@ constexpr int kCpmlTable = 6 * kMaxSlab;  // (1 - b) per [axis][E,H][slab positi
 
 // Shared-memory offset of the stages: the CPML table, then nmat + 1 material
 // rows (row nmat is all zero and stands for voxels outside the grid).
-template <typename R, int TX, int TY>
+template <typename R>
 __host__ __device__ constexpr size_t em_stage_offset(int nmat) {
   return ((kCpmlTable + (size_t)(nmat + 1) * M_COLS) * sizeof(R) + 127) & ~size_t(127);
+}
+// bytes of one stage slot: large enough for either tile kind
+template <typename R, int TY>
+__host__ __device__ constexpr size_t em_stage_bytes() {
+  return sizeof(EmStage<R, kEm2Nodes, TY>) > sizeof(EmStage<R, 32, TY>) ? sizeof(EmStage<R, kEm2Nodes, TY>)
+                                                                        : sizeof(EmStage<R, 32, TY>);
 }
 
 // Shared-memory stages (a power of two) and the prefetch distance: at plane k
@@ -245,42 +288,59 @@ __host__ __device__ constexpr size_t em_stage_offset(int nmat) {
 #define COSIM_EM_AHEAD 3
 #endif
 #ifndef COSIM_EM_MIN_CTAS
-#define COSIM_EM_MIN_CTAS 3  // resident CTAs of 8 warps per SM the FP32 kernel is compiled for (scaled for other heights)
+#define COSIM_EM_MIN_CTAS 2  // resident CTAs of 8 warps per SM the FP32 kernel is compiled for (scaled for other heights)
 #endif
 constexpr int kEmStages = COSIM_EM_STAGES;
 constexpr int kEmAhead = COSIM_EM_AHEAD;
 static_assert((kEmStages & (kEmStages - 1)) == 0, "stage count must be a power of two");
 static_assert(kEmAhead >= 2 && kEmAhead <= kEmStages - 1, "prefetch distance must leave the stage of plane k-1 free");
+template <typename R, int TY>
+__host__ __device__ constexpr size_t em_smem_bytes(int nmat) {
+  return em_stage_offset<R>(nmat) + kEmStages * em_stage_bytes<R, TY>() + 128;  // + alignment slack
+}
 
-// Body of the fused step for one CTA tile. BORDER = false is the interior
-// specialisation: every node of the tile and its +x/+y neighbours lies inside
-// the grid, off the lateral walls and outside the x/y CPML slabs, so the
-// bounds, wall and lateral-CPML tests fold away at compile time (only the
-// z-direction slab and walls remain, decided per plane for the whole CTA).
-// I: index type of node offsets (int when the padded node arrays have fewer
-// than 2^31 elements, long long otherwise).
-template <typename R, typename I, int TX, int TY, bool BORDER, bool CPL>
-__device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
-                                        EmStage<R, TX, TY> *stg, R (*sHxz)[TY][TX], R (*sQy)[TX], uint64_t *bars,
-                                        int *s_abort) {
+// Bounded waits for the planes a CTA reads at plane k: plane k+1 (plane k was
+// waited for one plane earlier, plane 0 before the loop). Sets *s_abort when
+// a copy did not arrive in time.
+__device__ __forceinline__ void em_wait_next(uint64_t *bars, int k, int nz, int *s_abort) {
+  if (k + 1 <= nz && !mbar_wait(&bars[(k + 1) & (kEmStages - 1)], (unsigned)((k + 1) / kEmStages) & 1u))
+    *s_abort = 1;
+}
+// after a failed wait at plane k: let the copies issued so far (planes up to
+// k + kEmAhead) land (bounded), flag the error and let the CTA leave
+__device__ __forceinline__ void em_abort(uint64_t *bars, int k, int nz, int *err) {
+  for (int q = k; q <= k + kEmAhead && q <= nz; ++q) mbar_wait(&bars[q & (kEmStages - 1)], (unsigned)(q / kEmStages) & 1u);
+  atomicExch(err, 1);
+}
+
+// ---- border tiles: one node per thread. Tile (bx, by) owns the nodes
+// i = 31 bx .. 31 bx + 30, j = (TY-1) by .. (TY-1) by + TY - 2; thread (tx, ty)
+// holds node (31 bx - 1 + tx, (TY-1) by - 1 + ty). Nodes outside the grid,
+// on the walls and inside the CPML slabs are all handled here.
+template <typename R, typename I, int TY, bool CPL>
+__device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
+                                               EmStage<R, 32, TY> *stg, R (*sHxz)[TY][32], R (*sQy)[32],
+                                               uint64_t *bars, int *s_abort, int bx, int by) {
+  constexpr int TX = 32;
   const Geo<R> &g = A.g;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int vd = g.nmat * M_COLS;  // row offset of the all-zero material
-  const int i0 = blockIdx.x * (TX - 1) - 1, j0 = blockIdx.y * (TY - 1) - 1;  // node of thread (0, 0)
+  const int i0 = bx * (TX - 1) - 1, j0 = by * (TY - 1) - 1;  // node of thread (0, 0)
   const int i = i0 + tx, j = j0 + ty;
-  const bool act = !BORDER || (i >= 0 && i <= nx && j >= 0 && j <= ny);
+  const bool act = i >= 0 && i <= nx && j >= 0 && j <= ny;
   const bool own = act && tx > 0 && ty > 0;
-  const bool need_ex = act && ty > 0 && (!BORDER || i < nx);  // own, or the halo column
-  const bool need_ey = act && tx > 0 && (!BORDER || j < ny);  // own, or the halo row
-  const bool in_x = !BORDER || i < nx, in_y = !BORDER || j < ny;
+  const bool need_ex = act && ty > 0 && i < nx;  // own, or the halo column
+  const bool need_ey = act && tx > 0 && j < ny;  // own, or the halo row
+  const bool in_x = i < nx, in_y = j < ny;
   const bool accum = A.Qs != nullptr;
 
-  // Plane k of E^n (tile + neighbours), H^{n-1/2} and Qs -> stage k mod
-  // kEmStages, by TMA: one thread announces the bytes on the stage's mbarrier
-  // and issues the seven box copies; positions outside the grid arrive as zero.
-  // Box x starts at the tile's first node rounded down to a multiple of 4
-  // (two's complement: i0 = -1 gives x0 = -4); threads read from column tx + xr.
+  // Plane k of E^n (tile + neighbours), H^{n-1/2}, Qs, voxels, z record and
+  // source rows -> stage k mod kEmStages, by TMA: one thread announces the
+  // bytes on the stage's mbarrier and issues the copies; positions outside the
+  // grid arrive as zero. Box x starts at the tile's first node rounded down to
+  // a multiple of 4 (two's complement: i0 = -1 gives x0 = -4); threads read
+  // from column tx + xr.
   const int xr = i0 & 3, x0 = i0 - xr;
   const bool leader = tx == 0 && ty == 0;
   // The voxel box starts at column i0 - 1 rounded down to 16 bytes, the
@@ -288,15 +348,14 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
   const int xvr = (i0 - 1) & 15, xv0 = (i0 - 1) - xvr;
   const bool has_src = A.src_row != nullptr;
   // transaction bytes of one stage: the boxes themselves, not their padding
-  const unsigned fixed_bytes =
+  const unsigned stage_bytes =
       (unsigned)((6 * TY + 3 + (accum ? TY : 0) + (CPL ? TY + 1 : 0)) * em_box_x<TX>() * (int)sizeof(R) +
-                 4 * (int)sizeof(R) + (has_src ? em_src_box<TY>() * 4 : 0));
-  const unsigned vox_bytes = (unsigned)((TY + 1) * em_vox_box_x<TX>());
+                 4 * (int)sizeof(R) + (has_src ? em_src_box<TY>() * 4 : 0) + (TY + 1) * em_vox_box_x<TX>());
   auto issue = [&](int k) {
     if (k > nz) return;
     const int s = k & (kEmStages - 1);
     EmStage<R, TX, TY> &S = stg[s];
-    mbar_arrive_expect_tx(&bars[s], fixed_bytes + (k < nz ? vox_bytes : 0u));
+    mbar_arrive_expect_tx(&bars[s], stage_bytes);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       tma_load_3d(&S.E[c].v[0][0], &A.tmE[c], x0, j0, k, &bars[s]);
@@ -304,7 +363,9 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
     }
     if (accum) tma_load_3d(&S.Qs.v[0][0], &A.tmQ, x0, j0, k, &bars[s]);
     if (CPL) tma_load_3d(&S.T.v[0][0], &A.tmT, x0, j0, k, &bars[s]);
-    if (k < nz) tma_load_3d(&S.V.v[0][0], &A.tmV, xv0, j0 - 1, k, &bars[s]);
+    // the voxel layer above plane k; at k = nz the box lies above the grid
+    // and arrives as zeros (the thread masks select the zero material row)
+    tma_load_3d(&S.V.v[0][0], &A.tmV, xv0, j0 - 1, k, &bars[s]);
     bulk_load(&S.Z.v[0][0], A.zt + 4 * (size_t)k, 4 * sizeof(R), &bars[s]);
     if (has_src) {  // 16-byte aligned: src_row itself is, the start is a multiple of 4 from -4
       const int base = k * (ny + 1) + j0;
@@ -312,36 +373,36 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
     }
   };
   const I plane = (I)g.plane;
-  const I o_own = act ? (I)g.nid(i, j, 0) : I(0);
+  const I id0 = act ? (I)g.nid(i, j, 0) : I(0);
   // Material rows (id x M_COLS) of voxels (i-1+dx, j-1+dy, k) from the staged
   // voxel box; the zero row outside the grid.
-  const bool cx0 = !BORDER || (i - 1 >= 0 && i - 1 < nx), cx1 = !BORDER || (i >= 0 && i < nx);
-  const bool cy0 = !BORDER || (j - 1 >= 0 && j - 1 < ny), cy1 = !BORDER || (j >= 0 && j < ny);
+  const bool cx0 = i - 1 >= 0 && i - 1 < nx, cx1 = i >= 0 && i < nx;
+  const bool cy0 = j - 1 >= 0 && j - 1 < ny, cy1 = j >= 0 && j < ny;
   const int cv = tx + xvr;  // column of voxel i-1 in the box
 
-  const R hxm = (act && (!BORDER || i > 0)) ? g.h[0][i - 1] : R(0), hx0 = (act && in_x) ? g.h[0][i] : R(0);
-  const R hym = (act && (!BORDER || j > 0)) ? g.h[1][j - 1] : R(0), hy0 = (act && in_y) ? g.h[1][j] : R(0);
+  const R hxm = (act && i > 0) ? g.h[0][i - 1] : R(0), hx0 = (act && in_x) ? g.h[0][i] : R(0);
+  const R hym = (act && j > 0) ? g.h[1][j - 1] : R(0), hy0 = (act && in_y) ? g.h[1][j] : R(0);
   const R ihx = (act && in_x) ? g.ih[0][i] : R(0), ihy = (act && in_y) ? g.ih[1][j] : R(0);
   const R idx = act ? g.idual[0][i] : R(0), idy = act ? g.idual[1][j] : R(0);
-  const bool fix_x = BORDER && ((i == 0 && A.fixlo[0]) || (i == nx && A.fixhi[0]));
-  const bool fix_y = BORDER && ((j == 0 && A.fixlo[1]) || (j == ny && A.fixhi[1]));
+  const bool fix_x = (i == 0 && A.fixlo[0]) || (i == nx && A.fixhi[0]);
+  const bool fix_y = (j == 0 && A.fixlo[1]) || (j == ny && A.fixhi[1]);
   // CPML slab positions along x and y (E: nodes, H: cells); none inside
-  const int sxE = BORDER ? slab_index(i, nx, A.slo[0], A.shi[0]) : -1;
-  const int syE = BORDER ? slab_index(j, ny, A.slo[1], A.shi[1]) : -1;
+  const int sxE = slab_index(i, nx, A.slo[0], A.shi[0]);
+  const int syE = slab_index(j, ny, A.slo[1], A.shi[1]);
   const int sxH = in_x ? sxE : -1;
   const int syH = in_y ? syE : -1;
   const R dt = A.dt;
-  const R half_dt = R(0.5) * dt;
+  const R half_dt = mul_(R(0.5), dt);
   // per-thread geometry of the face and edge coefficients
-  const R hdx = half_dt * idx, hdy = half_dt * idy;
-  const R dtWx_y = dt * (hym + hy0), dtWy_x = dt * (hxm + hx0);
-  const R lqx = R(0.25) * hx0, lqy = R(0.25) * hy0;
-  const I id0 = o_own;
+  const R hdx = mul_(half_dt, idx), hdy = mul_(half_dt, idy);
+  const R dtWx_y = mul_(dt, add_(hym, hy0)), dtWy_x = mul_(dt, add_(hxm, hx0));
+  const R lqx = mul_(R(0.25), hx0), lqy = mul_(R(0.25), hy0);
 
   if (leader) {
 #pragma unroll
     for (int q = 0; q < kEmAhead; ++q) issue(q);
   }
+  if (!mbar_wait(&bars[0], 0u)) *s_abort = 1;
   R hx_km1 = 0, hy_km1 = 0, qz_km1 = 0;
   // layer k-1 partial sums of the x / y edges and 1/mu of voxel (i, j, k-1);
   // zero below the grid
@@ -349,35 +410,23 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
   R q_pend = 0;  // Joule sum of node (i, j, k-1) still missing the y-edge share from j-1
   R e_pend = 0;  // the same without the accumulator's earlier energy (this step's only)
   int b01 = vd, b10 = vd, b11 = vd;  // coupled steps: material rows of layer k-1
-  // sigma dt / 2 of a voxel at the edge temperature rise te (coupled steps):
-  // sigma0 dt/2 / (1 + alpha (T_init + te - T0)) = M_SDT2 / (M_TC0 + M_TCR te)
-  auto sig = [&](int row, R te) -> R {
-    return s_mt[row + M_SDT2] * em_rcp(s_mt[row + M_TC0] + s_mt[row + M_TCR] * te);
-  };
+  auto sig = [&](int row, R te) -> R { return sig_t(s_mt[row + M_SDT2], s_mt[row + M_TCR], s_mt[row + M_TC0], te); };
 
   for (int k = 0; k <= nz; ++k) {
     if (leader) {  // the stage of plane k-1 is free: every thread passed the last barrier
       fence_proxy_async_smem();
       issue(k + kEmAhead);
     }
-    {  // planes k and k+1 have landed (phase parity: use count of the stage)
-      bool ok = mbar_wait(&bars[k & (kEmStages - 1)], (unsigned)(k / kEmStages) & 1u);
-      if (k + 1 <= nz) ok = mbar_wait(&bars[(k + 1) & (kEmStages - 1)], (unsigned)((k + 1) / kEmStages) & 1u) && ok;
-      if (!ok) *s_abort = 1;
-    }
+    em_wait_next(bars, k, nz, s_abort);
     __syncthreads();
     if (*s_abort) {  // a copy did not arrive in time: drain what is in flight (bounded), flag, leave
-      if (leader) {
-        for (int q = k; q <= k + kEmAhead && q <= nz; ++q)
-          mbar_wait(&bars[q & (kEmStages - 1)], (unsigned)(q / kEmStages) & 1u);
-        atomicExch(A.err, 1);
-      }
+      if (leader) em_abort(bars, k, nz, A.err);
       return;
     }
     const I id = id0 + (I)k * plane;
     // Joule energy of node (i, j, k-1): its y-edge share from j-1 is now visible
     if (accum && own && k > 0) {
-      const R s = q_pend + sQy[ty - 1][tx];
+      const R s = add_(q_pend, sQy[ty - 1][tx]);
       if (A.fold) {
         A.Q[id - plane] += (double)s;
         A.Qs[id - plane] = R(0);
@@ -385,7 +434,7 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
         A.Qs[id - plane] = s;
       }
     }
-    if (CPL && own && k > 0) A.Pout[id - plane] = (e_pend + sQy[ty - 1][tx]) * A.inv_dt;
+    if (CPL && own && k > 0) A.Pout[id - plane] = mul_(add_(e_pend, sQy[ty - 1][tx]), A.inv_dt);
     const EmStage<R, TX, TY> &S0 = stg[k & (kEmStages - 1)];
     const EmStage<R, TX, TY> &S1 = stg[(k + 1) & (kEmStages - 1)];
     R hz0, ihz, idz, hzm;
@@ -402,10 +451,10 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
       r0 = S0.S.v[0][sr];
       r1 = S0.S.v[0][sr + 1];
     }
-    const R hdz = half_dt * idz;
+    const R hdz = mul_(half_dt, idz);
     const bool fix_z = (k == 0 && A.fixlo[2]) || (k == nz && A.fixhi[2]);
     const int szE = slab_index(k, nz, A.slo[2], A.shi[2]);
-    const int szH = (k < nz) ? szE : -1;
+    const int szH = kz ? szE : -1;
 
     const int cx = tx + xr;  // this node's column in the staged boxes
     const R ex = S0.E[0].v[ty][cx], ey = S0.E[1].v[ty][cx], ez = S0.E[2].v[ty][cx];
@@ -420,7 +469,7 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
       th = S0.T.v[ty][cx];
       th_ip = S0.T.v[ty][cx + 1];
       th_jp = S0.T.v[ty + 1][cx];
-      th_kp = k < nz ? S1.T.v[ty][cx] : R(0);
+      th_kp = kz ? S1.T.v[ty][cx] : R(0);
     }
 
     // material constants of voxel layer k
@@ -431,24 +480,21 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
     load4(s_mt + a10, e10, s10, u10, k10);
     load4(s_mt + a11, e11, s11, u11, k11);
 
-    // ---- H^{n+1/2} at (i,j,k): H -= dt/mu (curl E + psi terms); dt/mu of a
-    // face is the series mean over the two voxels its dual edge crosses
+    // ---- H^{n+1/2} at (i,j,k); dt/mu of a face is the series mean over the
+    // two voxels its dual edge crosses
     R Hx = 0, Hy = 0, Hz = 0;
     if (act) {
-      if (in_y && k < nz) {  // Hx: (curl E)_x = dEz/dy - dEy/dz, voxels (i-1..i, j, k)
-        const R d1 = (ez_jp - ez) * ihy, d2 = (ey_up - ey) * ihz;
-        const R curl = curl_with_psi(A, s_cp, 1, 0, 1, syH, 2, szH, i, j, k, d1, d2, own);
-        Hx = hx_o - hdx * (hxm * u10 + hx0 * u11) * curl;
+      if (in_y && kz) {  // Hx: (curl E)_x = dEz/dy - dEy/dz, voxels (i-1..i, j, k)
+        const R curl = curl_with_psi(A, s_cp, 1, 1, syH, 2, szH, i, j, k, dif_(ez_jp, ez, ihy), dif_(ey_up, ey, ihz), own);
+        Hx = h_update(hx_o, hdx, hxm, u10, hx0, u11, curl);
       }
-      if (in_x && k < nz) {  // Hy: dEx/dz - dEz/dx, voxels (i, j-1..j, k)
-        const R d1 = (ex_up - ex) * ihz, d2 = (ez_ip - ez) * ihx;
-        const R curl = curl_with_psi(A, s_cp, 1, 1, 2, szH, 0, sxH, i, j, k, d1, d2, own);
-        Hy = hy_o - hdy * (hym * u01 + hy0 * u11) * curl;
+      if (in_x && kz) {  // Hy: dEx/dz - dEz/dx, voxels (i, j-1..j, k)
+        const R curl = curl_with_psi(A, s_cp, 1, 2, szH, 0, sxH, i, j, k, dif_(ex_up, ex, ihz), dif_(ez_ip, ez, ihx), own);
+        Hy = h_update(hy_o, hdy, hym, u01, hy0, u11, curl);
       }
       if (in_x && in_y) {  // Hz: dEy/dx - dEx/dy, voxels (i, j, k-1..k)
-        const R d1 = (ey_ip - ey) * ihx, d2 = (ex_jp - ex) * ihy;
-        const R curl = curl_with_psi(A, s_cp, 1, 2, 0, sxH, 1, syH, i, j, k, d1, d2, own);
-        Hz = hz_o - hdz * (hzm * u11_b + hz0 * u11) * curl;
+        const R curl = curl_with_psi(A, s_cp, 1, 0, sxH, 1, syH, i, j, k, dif_(ey_ip, ey, ihx), dif_(ex_jp, ex, ihy), own);
+        Hz = h_update(hz_o, hdz, hzm, u11_b, hz0, u11, curl);
       }
     }
     sHxz[0][ty][tx] = Hx;
@@ -465,53 +511,53 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
       const long long step = *A.step_base + A.step_off;
       if (s.x == i && step < A.amp_len) {
         const R a = A.src_amp[(long long)s.z * A.amp_len + step];
-        Jx += s.y == 0 ? a : R(0);
-        Jy += s.y == 1 ? a : R(0);
-        Jz += s.y == 2 ? a : R(0);
+        Jx = add_(Jx, s.y == 0 ? a : R(0));
+        Jy = add_(Jy, s.y == 1 ? a : R(0));
+        Jz = add_(Jz, s.y == 2 ? a : R(0));
       }
     }
 
     // ---- E^{n+1} on the node's edges and their Joule shares. Layer-k partial
     // sums of the x / y edges (voxel pairs across y / x); the layer k-1 halves
     // were formed one plane earlier.
-    const R pxe_a = hym * e01 + hy0 * e11, pxs_a = hym * s01 + hy0 * s11;
-    const R pye_a = hxm * e10 + hx0 * e11, pys_a = hxm * s10 + hx0 * s11;
+    const R pxe_a = fma_(hym, e01, mul_(hy0, e11)), pxs_a = fma_(hym, s01, mul_(hy0, s11));
+    const R pye_a = fma_(hxm, e10, mul_(hx0, e11)), pys_a = fma_(hxm, s10, mul_(hx0, s11));
     R exn = ex, eyn = ey, ezn = ez, qx = 0, qy = 0, qz = 0;
     if (need_ex && !(fix_y || fix_z)) {  // Ex: dHz/dy - dHy/dz, voxels (i, j-1..j, k-1..k)
-      const R d1 = (Hz - sHxz[1][ty - 1][tx]) * idy;
-      const R d2 = (Hy - hy_km1) * idz;
-      const R curl = curl_with_psi(A, s_cp, 0, 0, 1, syE, 2, szE, i, j, k, d1, d2, own);
-      R Ss = hzm * pxs_b + hz0 * pxs_a;
+      const R curl = curl_with_psi(A, s_cp, 0, 1, syE, 2, szE, i, j, k, dif_(Hz, sHxz[1][ty - 1][tx], idy),
+                                   dif_(Hy, hy_km1, idz), own);
+      R Ss = fma_(hzm, pxs_b, mul_(hz0, pxs_a));
       if (CPL) {
-        const R te = R(0.5) * (th + th_ip);
-        Ss = hzm * (hym * sig(b01, te) + hy0 * sig(b11, te)) + hz0 * (hym * sig(a01, te) + hy0 * sig(a11, te));
+        const R te = mul_(R(0.5), add_(th, th_ip));
+        Ss = fma_(hzm, fma_(hym, sig(b01, te), mul_(hy0, sig(b11, te))),
+                  mul_(hz0, fma_(hym, sig(a01, te), mul_(hy0, sig(a11, te)))));
       }
-      exn = e_update(ex, dtWx_y * (hzm + hz0), curl - Jx, hzm * pxe_b + hz0 * pxe_a, Ss, lqx, &qx);
+      exn = e_update<R, R>(ex, mul_(dtWx_y, add_(hzm, hz0)), sub_(curl, Jx), fma_(hzm, pxe_b, mul_(hz0, pxe_a)), Ss,
+                           lqx, &qx);
     }
-    // (interior tiles also run Ey / Ez on the halo lane tx = 0 and discard
-    // them: the warp stays convergent; only the owners store)
-    if ((BORDER ? need_ey : true) && !(fix_x || fix_z)) {  // Ey: dHx/dz - dHz/dx, voxels (i-1..i, j, k-1..k)
-      const R d1 = (Hx - hx_km1) * idz;
-      const R d2 = (Hz - hz_l) * idx;
-      const R curl = curl_with_psi(A, s_cp, 0, 1, 2, szE, 0, sxE, i, j, k, d1, d2, own);
-      R Ss = hzm * pys_b + hz0 * pys_a;
+    if (need_ey && !(fix_x || fix_z)) {  // Ey: dHx/dz - dHz/dx, voxels (i-1..i, j, k-1..k)
+      const R curl = curl_with_psi(A, s_cp, 0, 2, szE, 0, sxE, i, j, k, dif_(Hx, hx_km1, idz), dif_(Hz, hz_l, idx),
+                                   own);
+      R Ss = fma_(hzm, pys_b, mul_(hz0, pys_a));
       if (CPL) {
-        const R te = R(0.5) * (th + th_jp);
-        Ss = hzm * (hxm * sig(b10, te) + hx0 * sig(b11, te)) + hz0 * (hxm * sig(a10, te) + hx0 * sig(a11, te));
+        const R te = mul_(R(0.5), add_(th, th_jp));
+        Ss = fma_(hzm, fma_(hxm, sig(b10, te), mul_(hx0, sig(b11, te))),
+                  mul_(hz0, fma_(hxm, sig(a10, te), mul_(hx0, sig(a11, te)))));
       }
-      eyn = e_update(ey, dtWy_x * (hzm + hz0), curl - Jy, hzm * pye_b + hz0 * pye_a, Ss, lqy, &qy);
+      eyn = e_update<R, R>(ey, mul_(dtWy_x, add_(hzm, hz0)), sub_(curl, Jy), fma_(hzm, pye_b, mul_(hz0, pye_a)), Ss,
+                           lqy, &qy);
     }
-    if ((BORDER ? own : ty > 0) && k < nz && !(fix_x || fix_y)) {  // Ez: dHy/dx - dHx/dy, voxels (i-1..i, j-1..j, k)
-      const R d1 = (Hy - hy_l) * idx;
-      const R d2 = (Hx - sHxz[0][ty - 1][tx]) * idy;
-      const R curl = curl_with_psi(A, s_cp, 0, 2, 0, sxE, 1, syE, i, j, k, d1, d2, own);
-      const R Se = hym * (hxm * e00 + hx0 * e01) + hy0 * (hxm * e10 + hx0 * e11);
-      R Ss = hym * (hxm * s00 + hx0 * s01) + hy0 * (hxm * s10 + hx0 * s11);
+    if (own && kz && !(fix_x || fix_y)) {  // Ez: dHy/dx - dHx/dy, voxels (i-1..i, j-1..j, k)
+      const R curl = curl_with_psi(A, s_cp, 0, 0, sxE, 1, syE, i, j, k, dif_(Hy, hy_l, idx),
+                                   dif_(Hx, sHxz[0][ty - 1][tx], idy), own);
+      const R Se = fma_(hym, fma_(hxm, e00, mul_(hx0, e01)), mul_(hy0, fma_(hxm, e10, mul_(hx0, e11))));
+      R Ss = fma_(hym, fma_(hxm, s00, mul_(hx0, s01)), mul_(hy0, fma_(hxm, s10, mul_(hx0, s11))));
       if (CPL) {
-        const R te = R(0.5) * (th + th_kp);
-        Ss = hym * (hxm * sig(a00, te) + hx0 * sig(a01, te)) + hy0 * (hxm * sig(a10, te) + hx0 * sig(a11, te));
+        const R te = mul_(R(0.5), add_(th, th_kp));
+        Ss = fma_(hym, fma_(hxm, sig(a00, te), mul_(hx0, sig(a01, te))),
+                  mul_(hy0, fma_(hxm, sig(a10, te), mul_(hx0, sig(a11, te)))));
       }
-      ezn = e_update(ez, dtWx_y * (hxm + hx0), curl - Jz, Se, Ss, R(0.25) * hz0, &qz);
+      ezn = e_update<R, R>(ez, mul_(dtWx_y, add_(hxm, hx0)), sub_(curl, Jz), Se, Ss, mul_(R(0.25), hz0), &qz);
     }
     const R qx_l = __shfl_up_sync(0xffffffffu, qx, 1);  // x-edge share from node i-1
     sQy[ty][tx] = qy;
@@ -522,10 +568,10 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
       A.Hn[2][id] = Hz;
       A.En[0][id] = exn;
       A.En[1][id] = eyn;
-      if (k < nz) A.En[2][id] = ezn;
+      if (kz) A.En[2][id] = ezn;
     }
-    e_pend = (qx + qx_l) + qy + (qz + qz_km1);
-    q_pend = q_old + e_pend;
+    e_pend = add_(add_(add_(qx, qx_l), qy), add_(qz, qz_km1));
+    q_pend = add_(q_old, e_pend);
     hx_km1 = Hx;
     hy_km1 = Hy;
     qz_km1 = qz;
@@ -543,7 +589,7 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
   __syncthreads();
   if (accum && own) {  // Joule energy of the top plane k = nz
     const I id = id0 + (I)nz * plane;
-    const R s = q_pend + sQy[ty - 1][tx];
+    const R s = add_(q_pend, sQy[ty - 1][tx]);
     if (A.fold) {
       A.Q[id] += (double)s;
       A.Qs[id] = R(0);
@@ -551,34 +597,326 @@ __device__ __forceinline__ void em_tile(const EmArgs<R> &A, const R *s_cp, const
       A.Qs[id] = s;
     }
   }
-  if (CPL && own) A.Pout[id0 + (I)nz * plane] = (e_pend + sQy[ty - 1][tx]) * A.inv_dt;
+  if (CPL && own) A.Pout[id0 + (I)nz * plane] = mul_(add_(e_pend, sQy[ty - 1][tx]), A.inv_dt);
 }
 
-// One launch per step over all tiles; tiles in [ibx0, ibx1) x [iby0, iby1)
-// take the interior specialisation.
+// ---- interior tile pairs: two nodes per thread. Pair (bx, by) (bx even)
+// owns the nodes of the single tiles bx and bx+1, i = 31 bx .. 31 bx + 61;
+// thread (tx, ty) holds the nodes i0 + 2 tx (.x) and i0 + 2 tx + 1 (.y),
+// i0 = 31 bx - 2 (lane 0 is the halo pair), of row j0 + ty. Every node, its
+// +x/+y neighbours and its voxels lie inside the grid, off the lateral walls
+// and outside the x/y CPML slabs; only the z slab and walls remain, decided
+// per plane for the whole CTA.
+template <typename R, typename I, int TY, bool CPL>
+__device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
+                                             EmStage<R, kEm2Nodes, TY> *stg, typename Pair2<R>::T (*sHxz)[TY][32],
+                                             typename Pair2<R>::T (*sQy)[32], uint64_t *bars, int *s_abort, int bx,
+                                             int by) {
+  using R2 = typename Pair2<R>::T;
+  constexpr int BX = em2_box_x(), BV = em2_vox_box_x();
+  const Geo<R> &g = A.g;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int ny = g.ny, nz = g.nz;
+  const int vd = g.nmat * M_COLS;
+  const int i0 = bx * 31 - 2, j0 = by * (TY - 1) - 1;
+  const int ia = i0 + 2 * tx, j = j0 + ty;
+  const bool own = tx > 0 && ty > 0;
+  const bool accum = A.Qs != nullptr;
+  const bool leader = tx == 0 && ty == 0;
+  // node boxes from i0 rounded down to 4 (i0 is even: a pair starts at an
+  // even column, 8 / 16-byte aligned), the voxel box from i0 - 1 rounded down
+  // to 16, the source-row box as for border tiles
+  const int xr = i0 & 3, x0 = i0 - xr;
+  const int xvr = (i0 - 1) & 15, xv0 = (i0 - 1) - xvr;
+  const bool has_src = A.src_row != nullptr;
+  const unsigned stage_bytes =
+      (unsigned)((6 * TY + 3 + (accum ? TY : 0) + (CPL ? TY + 1 : 0)) * BX * (int)sizeof(R) + 4 * (int)sizeof(R) +
+                 (has_src ? em_src_box<TY>() * 4 : 0) + (TY + 1) * BV);
+  auto issue = [&](int k) {
+    if (k > nz) return;
+    const int s = k & (kEmStages - 1);
+    EmStage<R, kEm2Nodes, TY> &S = stg[s];
+    mbar_arrive_expect_tx(&bars[s], stage_bytes);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      tma_load_3d(&S.E[c].v[0][0], &A.tmE2[c], x0, j0, k, &bars[s]);
+      tma_load_3d(&S.H[c].v[0][0], &A.tmH2[c], x0, j0, k, &bars[s]);
+    }
+    if (accum) tma_load_3d(&S.Qs.v[0][0], &A.tmQ2, x0, j0, k, &bars[s]);
+    if (CPL) tma_load_3d(&S.T.v[0][0], &A.tmT2, x0, j0, k, &bars[s]);
+    tma_load_3d(&S.V.v[0][0], &A.tmV2, xv0, j0 - 1, k, &bars[s]);
+    bulk_load(&S.Z.v[0][0], A.zt + 4 * (size_t)k, 4 * sizeof(R), &bars[s]);
+    if (has_src) {
+      const int base = k * (ny + 1) + j0;
+      bulk_load(&S.S.v[0][0], A.src_row + (base - (base & 3)), em_src_box<TY>() * 4, &bars[s]);
+    }
+  };
+  const I plane = (I)g.plane;
+  const I id0 = (I)g.nid(ia, j, 0);
+  const int cv = 2 * tx + xvr;  // column of voxel ia - 1 in the voxel box
+  const int cx = 2 * tx + xr;   // column of node ia in the node boxes
+  const R2 z2 = bc_<R2>(R(0));
+
+  // geometry: x per node, y per row (the same arithmetic as the border path)
+  const R2 hxm = {g.h[0][ia - 1], g.h[0][ia]}, hx0 = {g.h[0][ia], g.h[0][ia + 1]};
+  const R2 ihx = {g.ih[0][ia], g.ih[0][ia + 1]}, idx = {g.idual[0][ia], g.idual[0][ia + 1]};
+  const R hym_s = g.h[1][j - 1], hy0_s = g.h[1][j];
+  const R2 hym = bc_<R2>(hym_s), hy0 = bc_<R2>(hy0_s), ihy = bc_<R2>(g.ih[1][j]), idy = bc_<R2>(g.idual[1][j]);
+  const R dt = A.dt;
+  const R half_dt = mul_(R(0.5), dt);
+  const R2 hdx = mul_(bc_<R2>(half_dt), idx), hdy = bc_<R2>(mul_(half_dt, g.idual[1][j]));
+  const R2 dtWx_y = bc_<R2>(mul_(dt, add_(hym_s, hy0_s))), dtWy_x = mul_(bc_<R2>(dt), add_(hxm, hx0));
+  const R2 lqx = mul_(bc_<R2>(R(0.25)), hx0), lqy = bc_<R2>(mul_(R(0.25), hy0_s));
+
+  if (leader) {
+#pragma unroll
+    for (int q = 0; q < kEmAhead; ++q) issue(q);
+  }
+  if (!mbar_wait(&bars[0], 0u)) *s_abort = 1;
+  R2 hx_km1 = z2, hy_km1 = z2, qz_km1 = z2;
+  R2 pxe_b = z2, pxs_b = z2, pye_b = z2, pys_b = z2, u11_b = z2;
+  R2 q_pend = z2, e_pend = z2;
+  int p0b = vd, p0c = vd, p1a = vd, p1b = vd, p1c = vd;  // coupled steps: material rows of layer k-1
+  // sigma dt/2 of the voxels ra (node .x) and rb (node .y) at the edge temperatures te
+  auto sigp = [&](int ra, int rb, R2 te) -> R2 {
+    return sig_t(R2{s_mt[ra + M_SDT2], s_mt[rb + M_SDT2]}, R2{s_mt[ra + M_TCR], s_mt[rb + M_TCR]},
+                 R2{s_mt[ra + M_TC0], s_mt[rb + M_TC0]}, te);
+  };
+
+  for (int k = 0; k <= nz; ++k) {
+    if (leader) {
+      fence_proxy_async_smem();
+      issue(k + kEmAhead);
+    }
+    em_wait_next(bars, k, nz, s_abort);
+    __syncthreads();
+    if (*s_abort) {
+      if (leader) em_abort(bars, k, nz, A.err);
+      return;
+    }
+    const I id = id0 + (I)k * plane;
+    if (accum && own && k > 0) {
+      const R2 s = add_(q_pend, sQy[ty - 1][tx]);
+      if (A.fold) {
+        double2 *qp = reinterpret_cast<double2 *>(A.Q + (id - plane));
+        double2 qv = *qp;
+        qv.x += (double)s.x;
+        qv.y += (double)s.y;
+        *qp = qv;
+        stv_(A.Qs + (id - plane), z2);
+      } else {
+        stv_(A.Qs + (id - plane), s);
+      }
+    }
+    if (CPL && own && k > 0) stv_(A.Pout + (id - plane), mul_(add_(e_pend, sQy[ty - 1][tx]), bc_<R2>(A.inv_dt)));
+    const EmStage<R, kEm2Nodes, TY> &S0 = stg[k & (kEmStages - 1)];
+    const EmStage<R, kEm2Nodes, TY> &S1 = stg[(k + 1) & (kEmStages - 1)];
+    R hz0s, ihzs, idzs, hzms;
+    load4(&S0.Z.v[0][0], hz0s, ihzs, idzs, hzms);
+    const R2 hz0 = bc_<R2>(hz0s), ihz = bc_<R2>(ihzs), idz = bc_<R2>(idzs), hzm = bc_<R2>(hzms);
+    const bool kz = k < nz;
+    // voxels ia-1 (a), ia (b), ia+1 (c) of rows j-1 (0) and j (1) in layer k;
+    // at k = nz the zero-filled box gives material 0, which the zero layer
+    // height then removes
+    const int r0a = (int)S0.V.v[ty][cv] * M_COLS, r0b = (int)S0.V.v[ty][cv + 1] * M_COLS,
+              r0c = (int)S0.V.v[ty][cv + 2] * M_COLS;
+    const int r1a = (int)S0.V.v[ty + 1][cv] * M_COLS, r1b = (int)S0.V.v[ty + 1][cv + 1] * M_COLS,
+              r1c = (int)S0.V.v[ty + 1][cv + 2] * M_COLS;
+    int r0 = 0, r1 = 0;  // source entries of row (k, j)
+    if (has_src) {
+      const int base = k * (ny + 1) + j0, sr = (base & 3) + ty;
+      r0 = S0.S.v[0][sr];
+      r1 = S0.S.v[0][sr + 1];
+    }
+    const R2 hdz = bc_<R2>(mul_(half_dt, idzs));
+    const bool fix_z = (k == 0 && A.fixlo[2]) || (k == nz && A.fixhi[2]);
+    const int szE = slab_index(k, nz, A.slo[2], A.shi[2]);
+    const int szH = kz ? szE : -1;
+
+    const R2 ex = ldv_<R2>(&S0.E[0].v[ty][cx]), ey = ldv_<R2>(&S0.E[1].v[ty][cx]), ez = ldv_<R2>(&S0.E[2].v[ty][cx]);
+    const R2 ex_up = ldv_<R2>(&S1.E[0].v[ty][cx]), ey_up = ldv_<R2>(&S1.E[1].v[ty][cx]);
+    const R2 ez_jp = ldv_<R2>(&S0.E[2].v[ty + 1][cx]), ex_jp = ldv_<R2>(&S0.E[0].v[ty + 1][cx]);
+    const R2 ez_ip = {ez.y, S0.E[2].v[ty][cx + 2]}, ey_ip = {ey.y, S0.E[1].v[ty][cx + 2]};
+    const R2 hx_o = ldv_<R2>(&S0.H[0].v[ty][cx]), hy_o = ldv_<R2>(&S0.H[1].v[ty][cx]),
+             hz_o = ldv_<R2>(&S0.H[2].v[ty][cx]);
+    const R2 q_old = accum ? ldv_<R2>(&S0.Qs.v[ty][cx]) : z2;
+    R2 th = z2, th_ip = z2, th_jp = z2, th_kp = z2;
+    if (CPL) {
+      th = ldv_<R2>(&S0.T.v[ty][cx]);
+      th_ip = R2{th.y, S0.T.v[ty][cx + 2]};
+      th_jp = ldv_<R2>(&S0.T.v[ty + 1][cx]);
+      th_kp = kz ? ldv_<R2>(&S1.T.v[ty][cx]) : z2;
+    }
+
+    R e0a, s0a, u0a, k0a, e0b, s0b, u0b, k0b, e0c, s0c, u0c, k0c;
+    R e1a, s1a, u1a, k1a, e1b, s1b, u1b, k1b, e1c, s1c, u1c, k1c;
+    load4(s_mt + r0a, e0a, s0a, u0a, k0a);
+    load4(s_mt + r0b, e0b, s0b, u0b, k0b);
+    load4(s_mt + r0c, e0c, s0c, u0c, k0c);
+    load4(s_mt + r1a, e1a, s1a, u1a, k1a);
+    load4(s_mt + r1b, e1b, s1b, u1b, k1b);
+    load4(s_mt + r1c, e1c, s1c, u1c, k1c);
+    // the voxels (i-1+dx, j-1+dy) of each node as pairs <dy><dx>
+    const R2 e00 = {e0a, e0b}, e01 = {e0b, e0c}, e10 = {e1a, e1b}, e11 = {e1b, e1c};
+    const R2 s00 = {s0a, s0b}, s01 = {s0b, s0c}, s10 = {s1a, s1b}, s11 = {s1b, s1c};
+    const R2 u01 = {u0b, u0c}, u10 = {u1a, u1b}, u11 = {u1b, u1c};
+
+    // CPML state of the z slab for the node pair (derivative axis z)
+    auto chi_z = [&](int type, int slot, int s, R2 v) -> R2 {
+      const long long q = ((long long)s * (ny + 1) + j) * g.px + ia;
+      return chi_update<R, R2>(A, bc_<R2>(s_cp[(2 * 2 + type) * kMaxSlab + s]), 2, type, slot, q, v, own);
+    };
+
+    // ---- H^{n+1/2}
+    R2 Hx = z2, Hy = z2;
+    if (kz) {
+      const R2 d1 = dif_(ez_jp, ez, ihy), d2 = dif_(ey_up, ey, ihz);
+      Hx = h_update(hx_o, hdx, hxm, u10, hx0, u11, szH >= 0 ? sub_(d1, chi_z(1, 0, szH, d2)) : sub_(d1, d2));
+      const R2 f1 = dif_(ex_up, ex, ihz), f2 = dif_(ez_ip, ez, ihx);
+      Hy = h_update(hy_o, hdy, hym, u01, hy0, u11, szH >= 0 ? sub_(chi_z(1, 1, szH, f1), f2) : sub_(f1, f2));
+    }
+    const R2 Hz = h_update(hz_o, hdz, hzm, u11_b, hz0, u11, sub_(dif_(ey_ip, ey, ihx), dif_(ex_jp, ex, ihy)));
+    sHxz[0][ty][tx] = Hx;
+    sHxz[1][ty][tx] = Hz;
+    const R2 hy_l = {__shfl_up_sync(0xffffffffu, Hy.y, 1), Hy.x};  // H of nodes ia-1, ia
+    const R2 hz_l = {__shfl_up_sync(0xffffffffu, Hz.y, 1), Hz.x};
+    __syncthreads();
+
+    // ---- source currents on the pair's edges
+    R2 Jx = z2, Jy = z2, Jz = z2;
+    for (int e = r0; e < r1; ++e) {
+      const int4 s = A.src_ent[e];
+      const long long step = *A.step_base + A.step_off;
+      if ((s.x == ia || s.x == ia + 1) && step < A.amp_len) {
+        const R a = A.src_amp[(long long)s.z * A.amp_len + step];
+        if (s.x == ia) {
+          Jx.x = add_(Jx.x, s.y == 0 ? a : R(0));
+          Jy.x = add_(Jy.x, s.y == 1 ? a : R(0));
+          Jz.x = add_(Jz.x, s.y == 2 ? a : R(0));
+        } else {
+          Jx.y = add_(Jx.y, s.y == 0 ? a : R(0));
+          Jy.y = add_(Jy.y, s.y == 1 ? a : R(0));
+          Jz.y = add_(Jz.y, s.y == 2 ? a : R(0));
+        }
+      }
+    }
+
+    // ---- E^{n+1} and the Joule shares
+    const R2 pxe_a = fma_(hym, e01, mul_(hy0, e11)), pxs_a = fma_(hym, s01, mul_(hy0, s11));
+    const R2 pye_a = fma_(hxm, e10, mul_(hx0, e11)), pys_a = fma_(hxm, s10, mul_(hx0, s11));
+    R2 exn = ex, eyn = ey, ezn = ez, qx = z2, qy = z2, qz = z2;
+    if (ty > 0 && !fix_z) {  // Ex (owners and the halo lane, whose x-edge share lane 1 needs)
+      const R2 d1 = dif_(Hz, sHxz[1][ty - 1][tx], idy), d2 = dif_(Hy, hy_km1, idz);
+      const R2 curl = szE >= 0 ? sub_(d1, chi_z(0, 0, szE, d2)) : sub_(d1, d2);
+      R2 Ss = fma_(hzm, pxs_b, mul_(hz0, pxs_a));
+      if (CPL) {
+        const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_ip));
+        Ss = fma_(hzm, fma_(hym, sigp(p0b, p0c, te), mul_(hy0, sigp(p1b, p1c, te))),
+                  mul_(hz0, fma_(hym, sigp(r0b, r0c, te), mul_(hy0, sigp(r1b, r1c, te)))));
+      }
+      exn = e_update<R2, R>(ex, mul_(dtWx_y, add_(hzm, hz0)), sub_(curl, Jx), fma_(hzm, pxe_b, mul_(hz0, pxe_a)), Ss,
+                            lqx, &qx);
+    }
+    if (!fix_z) {  // Ey (every row: the halo row's y-edge share goes to row ty+1)
+      const R2 d1 = dif_(Hx, hx_km1, idz), d2 = dif_(Hz, hz_l, idx);
+      const R2 curl = szE >= 0 ? sub_(chi_z(0, 1, szE, d1), d2) : sub_(d1, d2);
+      R2 Ss = fma_(hzm, pys_b, mul_(hz0, pys_a));
+      if (CPL) {
+        const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_jp));
+        Ss = fma_(hzm, fma_(hxm, sigp(p1a, p1b, te), mul_(hx0, sigp(p1b, p1c, te))),
+                  mul_(hz0, fma_(hxm, sigp(r1a, r1b, te), mul_(hx0, sigp(r1b, r1c, te)))));
+      }
+      eyn = e_update<R2, R>(ey, mul_(dtWy_x, add_(hzm, hz0)), sub_(curl, Jy), fma_(hzm, pye_b, mul_(hz0, pye_a)), Ss,
+                            lqy, &qy);
+    }
+    if (ty > 0 && kz) {  // Ez
+      const R2 curl = sub_(dif_(Hy, hy_l, idx), dif_(Hx, sHxz[0][ty - 1][tx], idy));
+      const R2 Se = fma_(hym, fma_(hxm, e00, mul_(hx0, e01)), mul_(hy0, fma_(hxm, e10, mul_(hx0, e11))));
+      R2 Ss = fma_(hym, fma_(hxm, s00, mul_(hx0, s01)), mul_(hy0, fma_(hxm, s10, mul_(hx0, s11))));
+      if (CPL) {
+        const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_kp));
+        Ss = fma_(hym, fma_(hxm, sigp(r0a, r0b, te), mul_(hx0, sigp(r0b, r0c, te))),
+                  mul_(hy0, fma_(hxm, sigp(r1a, r1b, te), mul_(hx0, sigp(r1b, r1c, te)))));
+      }
+      ezn = e_update<R2, R>(ez, mul_(dtWx_y, add_(hxm, hx0)), sub_(curl, Jz), Se, Ss, bc_<R2>(mul_(R(0.25), hz0s)),
+                            &qz);
+    }
+    const R2 qx_l = {__shfl_up_sync(0xffffffffu, qx.y, 1), qx.x};  // x-edge shares from nodes ia-1, ia
+    sQy[ty][tx] = qy;
+
+    if (own) {
+      stv_(A.Hn[0] + id, Hx);
+      stv_(A.Hn[1] + id, Hy);
+      stv_(A.Hn[2] + id, Hz);
+      stv_(A.En[0] + id, exn);
+      stv_(A.En[1] + id, eyn);
+      if (kz) stv_(A.En[2] + id, ezn);
+    }
+    e_pend = add_(add_(add_(qx, qx_l), qy), add_(qz, qz_km1));
+    q_pend = add_(q_old, e_pend);
+    hx_km1 = Hx;
+    hy_km1 = Hy;
+    qz_km1 = qz;
+    pxe_b = pxe_a;
+    pxs_b = pxs_a;
+    pye_b = pye_a;
+    pys_b = pys_a;
+    u11_b = u11;
+    if (CPL) {
+      p0b = r0b, p0c = r0c, p1a = r1a, p1b = r1b, p1c = r1c;
+    }
+  }
+  __syncthreads();
+  if (accum && own) {  // Joule energy of the top plane k = nz
+    const I id = id0 + (I)nz * plane;
+    const R2 s = add_(q_pend, sQy[ty - 1][tx]);
+    if (A.fold) {
+      double2 *qp = reinterpret_cast<double2 *>(A.Q + id);
+      double2 qv = *qp;
+      qv.x += (double)s.x;
+      qv.y += (double)s.y;
+      *qp = qv;
+      stv_(A.Qs + id, z2);
+    } else {
+      stv_(A.Qs + id, s);
+    }
+  }
+  if (CPL && own) stv_(A.Pout + (id0 + (I)nz * plane), mul_(add_(e_pend, sQy[ty - 1][tx]), bc_<R2>(A.inv_dt)));
+}
+
+// Resident CTAs per SM the kernel is compiled for: FP32 8-row tiles at
+// COSIM_EM_MIN_CTAS (scaled for other heights), FP64 one.
+__host__ __device__ constexpr int em_min_ctas(int rsz, int ty) { return rsz == 4 ? COSIM_EM_MIN_CTAS * 8 / ty : 1; }
+
+// One launch per step: CTAs 0 .. n_border-1 take the border tiles (the frame
+// around the interior rectangle, row by row), the rest the interior pairs.
 template <typename R, typename I, int TX, int TY, bool CPL>
-__global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? COSIM_EM_MIN_CTAS * 8 / TY : 2)
+__global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
     em_step_kernel(const __grid_constant__ EmArgs<R> A) {
   static_assert(TX == 32, "a tile row is one warp: x neighbours are exchanged by shuffles");
+  using R2 = typename Pair2<R>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // the launch adds 128 bytes so that the tables and stages can start on a
   // 128-byte boundary of the shared window (TMA destinations must)
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   R *s_cp = reinterpret_cast<R *>(smem);
   R *s_mt = s_cp + kCpmlTable;
-  EmStage<R, TX, TY> *stg = reinterpret_cast<EmStage<R, TX, TY> *>(smem + em_stage_offset<R, TX, TY>(A.g.nmat));
-  __shared__ R sHxz[2][TY][TX];  // Hx, Hz of the plane, read by the +y neighbour
-  __shared__ R sQy[TY][TX];      // Joule share of the y-edge, read by the +y neighbour one plane later
+  unsigned char *stg = smem + em_stage_offset<R>(A.g.nmat);
+  __shared__ R2 sHxz[2][TY][TX];  // Hx, Hz of the plane, read by the +y neighbour
+  __shared__ R2 sQy[TY][TX];      // Joule share of the y-edge, read by the +y neighbour one plane later
   __shared__ uint64_t s_bar[kEmStages];  // one transaction barrier per stage
   __shared__ int s_abort;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     // TMA preconditions checked once per CTA: 128-byte aligned destinations
     // and 64-byte aligned descriptors; otherwise flag the error and leave
     // without issuing a copy
-    bool ok = (smem_u32(stg) & 127u) == 0 && (sizeof(EmStage<R, TX, TY>) & 127u) == 0;
+    bool ok = (smem_u32(stg) & 127u) == 0 && (sizeof(EmStage<R, TX, TY>) & 127u) == 0 &&
+              (sizeof(EmStage<R, kEm2Nodes, TY>) & 127u) == 0;
     for (int c = 0; c < 3; ++c)
-      ok = ok && ((size_t)&A.tmE[c] & 63u) == 0 && ((size_t)&A.tmH[c] & 63u) == 0;
-    ok = ok && ((size_t)&A.tmQ & 63u) == 0;
+      ok = ok && ((size_t)&A.tmE[c] & 63u) == 0 && ((size_t)&A.tmH[c] & 63u) == 0 &&
+           ((size_t)&A.tmE2[c] & 63u) == 0 && ((size_t)&A.tmH2[c] & 63u) == 0;
+    ok = ok && ((size_t)&A.tmQ & 63u) == 0 && ((size_t)&A.tmQ2 & 63u) == 0 && ((size_t)&A.tmV & 63u) == 0 &&
+         ((size_t)&A.tmV2 & 63u) == 0 && ((size_t)&A.tmT & 63u) == 0 && ((size_t)&A.tmT2 & 63u) == 0;
     s_abort = ok ? 0 : 1;
     if (!ok) atomicExch(A.err, 2);
     for (int q = 0; q < kEmStages; ++q) mbar_init(&s_bar[q], 1);
@@ -588,12 +926,35 @@ __global__ void __launch_bounds__(TX *TY, sizeof(R) == 4 ? COSIM_EM_MIN_CTAS * 8
   stage_table(s_cp, A.cpml, kCpmlTable);
   __syncthreads();
   if (s_abort) return;
-  const bool interior = (int)blockIdx.x >= A.ibx0 && (int)blockIdx.x < A.ibx1 && (int)blockIdx.y >= A.iby0 &&
-                        (int)blockIdx.y < A.iby1;
-  if (interior)
-    em_tile<R, I, TX, TY, false, CPL>(A, s_cp, s_mt, stg, sHxz, sQy, s_bar, &s_abort);
-  else
-    em_tile<R, I, TX, TY, true, CPL>(A, s_cp, s_mt, stg, sHxz, sQy, s_bar, &s_abort);
+  int b = (int)blockIdx.x;
+  if (b < A.n_border) {
+    // border tile b: the rows below the interior rectangle, then the left and
+    // right parts of its rows, then the rows above it
+    const int nbx = A.nbx, below = A.iby0 * nbx, w = nbx - 2 * A.npx, mid = (A.iby1 - A.iby0) * w;
+    int bx, by;
+    if (b < below) {
+      by = b / nbx;
+      bx = b - by * nbx;
+    } else if ((b -= below) < mid) {
+      by = b / w;
+      bx = b - by * w;
+      by += A.iby0;
+      if (bx >= A.ibx0) bx += 2 * A.npx;
+    } else {
+      b -= mid;
+      by = b / nbx;
+      bx = b - by * nbx;
+      by += A.iby1;
+    }
+    em_tile_border<R, I, TY, CPL>(A, s_cp, s_mt, reinterpret_cast<EmStage<R, TX, TY> *>(stg),
+                                  reinterpret_cast<R(*)[TY][TX]>(&sHxz[0][0][0]), reinterpret_cast<R(*)[TX]>(&sQy[0][0]),
+                                  s_bar, &s_abort, bx, by);
+  } else {
+    b -= A.n_border;
+    const int py = b / A.npx, px = b - py * A.npx;
+    em_tile_pair<R, I, TY, CPL>(A, s_cp, s_mt, reinterpret_cast<EmStage<R, kEm2Nodes, TY> *>(stg), sHxz, sQy, s_bar,
+                                &s_abort, A.ibx0 + 2 * px, A.iby0 + py);
+  }
 }
 
 // advance the device-resident source time index after a group of steps
