@@ -732,29 +732,28 @@ static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool
     A.fixhi[a] = c->em_bc[2 * a + 1] != COSIM_BC_PMC;
   }
   A.cpml = (const R *)c->cpml;
-  // Tiles of 31 x (TY-1) owned nodes. Interior rows: every thread's node
-  // j = j0..j0+TY-1 (j0 = b (TY-1) - 1) satisfies slo < j < ny - shi, so also
-  // 0 < j < ny, and the +y neighbour j0 + TY stays <= ny. Interior pairs: the
-  // single tiles bx, bx+1 (bx even) whose lane nodes i0 = 31 bx - 2 ..
-  // i0 + 63 and +x neighbour i0 + 64 satisfy the same in x.
+  // Tiling (see EmArgs). Interior rows: every thread's node j = j0..j0+TY-1
+  // (j0 = b (TY-1) - 1) satisfies slo < j < ny - shi, so also 0 < j < ny,
+  // and the +y neighbour j0 + TY stays <= ny. Interior pairs: the lane nodes
+  // i0 = xs - 2 .. i0 + 63 and the +x neighbour i0 + 64 satisfy the same in
+  // x; xs is even (i0 = xb0 - 2 the first even node above slo).
+  const int nby = (c->ny + 1 + TY - 2) / (TY - 1);
   A.nbx = (c->nx + 1 + kEmTX - 2) / (kEmTX - 1);
-  A.nby = (c->ny + 1 + TY - 2) / (TY - 1);
   A.iby0 = A.iby1 = 0;
-  for (int b = 0; b < A.nby; ++b) {
+  for (int b = 0; b < nby; ++b) {
     const int j0 = b * (TY - 1) - 1;
     if (j0 >= c->slo[1] + 1 && j0 + TY <= c->ny - c->shi[1]) {
       if (A.iby1 == 0) A.iby0 = b;
       A.iby1 = b + 1;
     }
   }
-  A.ibx0 = A.npx = 0;
-  for (int b = 0; b + 1 < A.nbx && (kEmTX - 1) * b + 62 <= c->nx - c->shi[0]; b += 2)
-    if ((kEmTX - 1) * b - 2 >= c->slo[0] + 1) {
-      if (A.npx == 0) A.ibx0 = b;
-      ++A.npx;
-    }
+  A.xb0 = (c->slo[0] + 4) & ~1;  // smallest even xs with xs - 2 >= slo + 1
+  A.npx = std::max(0, (c->nx - c->shi[0] - A.xb0) / 62);
   if (A.npx == 0 || A.iby1 == A.iby0) A.npx = A.iby0 = A.iby1 = 0;
-  A.n_border = A.nbx * A.nby - 2 * A.npx * (A.iby1 - A.iby0);
+  A.xb1 = A.xb0 + 62 * A.npx;
+  A.nl = A.npx ? (A.xb0 + kEmTX - 2) / (kEmTX - 1) : 0;
+  A.nr = A.npx ? (c->nx + 1 - A.xb1 + kEmTX - 2) / (kEmTX - 1) : 0;
+  A.n_border = (nby - (A.iby1 - A.iby0)) * A.nbx + (A.iby1 - A.iby0) * (A.nl + A.nr);
   A.dt = (R)c->dt;
   A.src_row = c->src_row;
   A.src_ent = c->src_ent;

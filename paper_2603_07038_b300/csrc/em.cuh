@@ -86,11 +86,13 @@ struct EmArgs {
   R *Qs;                      // null: not accumulating
   double *Q;
   int fold;
-  // Tiles (31 x (TY-1) owned nodes, tile (bx, by)): nbx x nby in all. The
-  // single tiles 2 npx wide from ibx0 (even) and rows [iby0, iby1) are run as
-  // npx x (iby1 - iby0) interior pairs (CTAs n_border ..); the other n_border
-  // tiles are border tiles (CTAs 0 .. n_border - 1).
-  int nbx, nby, ibx0, npx, iby0, iby1, n_border;
+  // Tiling of the node grid. Rows of TY-1 owned nodes (row tile by owns
+  // j = (TY-1) by .. (TY-1) by + TY - 2). In the rows [iby0, iby1) the nodes
+  // xb0 .. xb1-1 (xb0 even, xb1 = xb0 + 62 npx) are owned by npx interior
+  // pairs per row (CTAs n_border ..); the rest of those rows by nl border
+  // tiles of up to 31 nodes from x = 0 and nr from x = xb1. Rows outside
+  // [iby0, iby1) are cut into nbx border tiles of 31 nodes from x = 0.
+  int nbx, xb0, xb1, npx, nl, nr, iby0, iby1, n_border;
   // TMA descriptors of E^n, H^{n-1/2} (per component) and Qs: 3-D node
   // arrays (x, y, z) with boxes of em_box_x x (TY+1 for E, TY otherwise) x 1
   // for border tiles and the *2 ones, em2_box_x wide, for interior pairs
@@ -121,18 +123,46 @@ __device__ __forceinline__ long long psi_index(const EmArgs<R> &A, int d, int s,
   return ((long long)s * (A.g.ny + 1) + j) * A.g.px + i;
 }
 
-// chi^n = b (chi^{n-1} + dF^n - dF^{n-1}) at element q of the slab arrays of
-// axis d, slot `slot`, for V one node or an x-adjacent node pair (q even);
-// omb = 1 - b. Returns chi^n = dF + psi; the owner writes the new state.
+// CPML state of one derivative at element q of the slab arrays of axis d,
+// slot `slot` (V: one node, or an x-adjacent node pair at an even q): chi,
+// its low part (FP32 contexts) and the previous derivative. The loads of a
+// plane's states are issued together, ahead of their use, so that their
+// latencies overlap.
+template <typename V>
+struct ChiIn {
+  V hi, lo, d;
+};
+template <typename V>
+struct Psi {
+  int s;        // slab position, -1: none (no state is read or written)
+  long long q;  // element of the slab arrays
+  ChiIn<V> c;
+};
 template <typename R, typename V>
-__device__ __forceinline__ V chi_update(const EmArgs<R> &A, V omb, int d, int type, int slot, long long q, V deriv,
-                                        bool write) {
-  const R *xo = type == 0 ? A.xEo[d][slot] : A.xHo[d][slot];
-  const R *dd = type == 0 ? A.dEo[d][slot] : A.dHo[d][slot];
+__device__ __forceinline__ Psi<V> psi_pre(const EmArgs<R> &A, int d, int type, int slot, int s, long long q) {
+  Psi<V> p;
+  p.s = s;
+  p.q = q;
+  if (s >= 0) {
+    p.c.hi = ldv_<V>((type == 0 ? A.xEo[d][slot] : A.xHo[d][slot]) + q);
+    p.c.d = ldv_<V>((type == 0 ? A.dEo[d][slot] : A.dHo[d][slot]) + q);
+    if constexpr (sizeof(R) == 4) p.c.lo = ldv_<V>((type == 0 ? A.lEo[d][slot] : A.lHo[d][slot]) + q);
+  }
+  return p;
+}
+
+// chi^n = b (chi^{n-1} + dF^n - dF^{n-1}), omb = 1 - b, from the state in p;
+// returns chi^n = dF + psi (the derivative itself outside the slabs); the
+// owner writes the new state.
+template <typename R, typename V>
+__device__ __forceinline__ V psi_apply(const EmArgs<R> &A, V omb, int d, int type, int slot, const Psi<V> &p, V deriv,
+                                       bool write) {
+  if (p.s < 0) return deriv;
+  const long long q = p.q;
   R *xn = type == 0 ? A.xEn[d][slot] : A.xHn[d][slot];
   R *dn = type == 0 ? A.dEn[d][slot] : A.dHn[d][slot];
   if constexpr (sizeof(R) == 8) {
-    const V t = add_(ldv_<V>(xo + q), sub_(deriv, ldv_<V>(dd + q)));
+    const V t = add_(p.c.hi, sub_(deriv, p.c.d));
     const V chi = fma_(neg_(omb), t, t);
     if (write) {
       stv_(xn + q, chi);
@@ -142,18 +172,17 @@ __device__ __forceinline__ V chi_update(const EmArgs<R> &A, V omb, int d, int ty
   } else {
     // (hi + lo + D)(1 - omb) with Knuth's TwoSum for the additions, an FMA
     // product error for omb * hi, and a final renormalisation (Fast2Sum).
-    const V hi = ldv_<V>(xo + q);
-    const V lo = ldv_<V>((type == 0 ? A.lEo[d][slot] : A.lHo[d][slot]) + q);
-    const V D = sub_(deriv, ldv_<V>(dd + q));
+    const V hi = p.c.hi, lo = p.c.lo;
+    const V D = sub_(deriv, p.c.d);
     const V sh = add_(hi, D);
     const V bv = sub_(sh, hi);
     const V e1 = add_(sub_(hi, sub_(sh, bv)), sub_(D, bv));
     const V l1 = add_(lo, e1);
-    const V p = mul_(omb, sh);
-    const V pe = fma_(omb, sh, neg_(p));
-    const V s2 = sub_(sh, p);
+    const V pr = mul_(omb, sh);
+    const V pe = fma_(omb, sh, neg_(pr));
+    const V s2 = sub_(sh, pr);
     const V bv2 = sub_(s2, sh);
-    const V e2 = add_(sub_(sh, sub_(s2, bv2)), sub_(neg_(p), bv2));
+    const V e2 = add_(sub_(sh, sub_(s2, bv2)), sub_(neg_(pr), bv2));
     const V l2 = sub_(sub_(add_(l1, e2), pe), mul_(omb, l1));
     const V h3 = add_(s2, l2);
     const V l3 = sub_(l2, sub_(h3, s2));
@@ -166,18 +195,18 @@ __device__ __forceinline__ V chi_update(const EmArgs<R> &A, V omb, int d, int ty
   }
 }
 
-// (dF1 + psi1) - (dF2 + psi2) for the two derivatives of one curl component
-// of a single node; the CPML state is touched only inside a slab (s1/s2 >= 0).
+// single node: the state of derivative axis d, slab position s (or none)
 template <typename R>
-__device__ __forceinline__ R curl_with_psi(const EmArgs<R> &A, const R *s_cp, int type, int d1, int s1, int d2,
-                                           int s2, int i, int j, int k, R v1, R v2, bool write) {
-  if (s1 < 0 && s2 < 0) return sub_(v1, v2);
-  const R a = s1 >= 0 ? chi_update<R, R>(A, s_cp[(d1 * 2 + type) * kMaxSlab + s1], d1, type, 1,
-                                         psi_index(A, d1, s1, i, j, k), v1, write)
-                      : v1;
-  const R b = s2 >= 0 ? chi_update<R, R>(A, s_cp[(d2 * 2 + type) * kMaxSlab + s2], d2, type, 0,
-                                         psi_index(A, d2, s2, i, j, k), v2, write)
-                      : v2;
+__device__ __forceinline__ Psi<R> psi_node(const EmArgs<R> &A, int d, int type, int slot, int s, int i, int j, int k) {
+  return psi_pre<R, R>(A, d, type, slot, s, s >= 0 ? psi_index(A, d, s, i, j, k) : 0);
+}
+// (dF1 + psi1) - (dF2 + psi2) of one curl component of a single node: the
+// first derivative's state is in slot 1, the second's in slot 0
+template <typename R>
+__device__ __forceinline__ R curl_psi(const EmArgs<R> &A, const R *s_cp, int type, int d1, const Psi<R> &p1, int d2,
+                                      const Psi<R> &p2, R v1, R v2, bool write) {
+  const R a = p1.s >= 0 ? psi_apply<R, R>(A, s_cp[(d1 * 2 + type) * kMaxSlab + p1.s], d1, type, 1, p1, v1, write) : v1;
+  const R b = p2.s >= 0 ? psi_apply<R, R>(A, s_cp[(d2 * 2 + type) * kMaxSlab + p2.s], d2, type, 0, p2, v2, write) : v2;
   return sub_(a, b);
 }
 
@@ -313,23 +342,24 @@ __device__ __forceinline__ void em_abort(uint64_t *bars, int k, int nz, int *err
   atomicExch(err, 1);
 }
 
-// ---- border tiles: one node per thread. Tile (bx, by) owns the nodes
-// i = 31 bx .. 31 bx + 30, j = (TY-1) by .. (TY-1) by + TY - 2; thread (tx, ty)
-// holds node (31 bx - 1 + tx, (TY-1) by - 1 + ty). Nodes outside the grid,
-// on the walls and inside the CPML slabs are all handled here.
+// ---- border tiles: one node per thread. The tile starting at node xs of row
+// tile by owns the nodes i = xs .. min(xs + 30, xe - 1), j = (TY-1) by ..
+// (TY-1) by + TY - 2; thread (tx, ty) holds node (xs - 1 + tx, (TY-1) by - 1
+// + ty). Nodes outside the grid, on the walls and inside the CPML slabs are
+// all handled here.
 template <typename R, typename I, int TY, bool CPL>
 __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
                                                EmStage<R, 32, TY> *stg, R (*sHxz)[TY][32], R (*sQy)[32],
-                                               uint64_t *bars, int *s_abort, int bx, int by) {
+                                               uint64_t *bars, int *s_abort, int xs, int xe, int by) {
   constexpr int TX = 32;
   const Geo<R> &g = A.g;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int vd = g.nmat * M_COLS;  // row offset of the all-zero material
-  const int i0 = bx * (TX - 1) - 1, j0 = by * (TY - 1) - 1;  // node of thread (0, 0)
+  const int i0 = xs - 1, j0 = by * (TY - 1) - 1;  // node of thread (0, 0)
   const int i = i0 + tx, j = j0 + ty;
   const bool act = i >= 0 && i <= nx && j >= 0 && j <= ny;
-  const bool own = act && tx > 0 && ty > 0;
+  const bool own = act && tx > 0 && ty > 0 && i < xe;
   const bool need_ex = act && ty > 0 && i < nx;  // own, or the halo column
   const bool need_ey = act && tx > 0 && j < ny;  // own, or the halo row
   const bool in_x = i < nx, in_y = j < ny;
@@ -482,25 +512,30 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
 
     // ---- H^{n+1/2} at (i,j,k); dt/mu of a face is the series mean over the
     // two voxels its dual edge crosses
+    const bool hx_on = act && in_y && kz, hy_on = act && in_x && kz, hz_on = act && in_x && in_y;
+    const Psi<R> pHx1 = psi_node(A, 1, 1, 1, hx_on ? syH : -1, i, j, k), pHx2 = psi_node(A, 2, 1, 0, hx_on ? szH : -1, i, j, k);
+    const Psi<R> pHy1 = psi_node(A, 2, 1, 1, hy_on ? szH : -1, i, j, k), pHy2 = psi_node(A, 0, 1, 0, hy_on ? sxH : -1, i, j, k);
+    const Psi<R> pHz1 = psi_node(A, 0, 1, 1, hz_on ? sxH : -1, i, j, k), pHz2 = psi_node(A, 1, 1, 0, hz_on ? syH : -1, i, j, k);
     R Hx = 0, Hy = 0, Hz = 0;
-    if (act) {
-      if (in_y && kz) {  // Hx: (curl E)_x = dEz/dy - dEy/dz, voxels (i-1..i, j, k)
-        const R curl = curl_with_psi(A, s_cp, 1, 1, syH, 2, szH, i, j, k, dif_(ez_jp, ez, ihy), dif_(ey_up, ey, ihz), own);
-        Hx = h_update(hx_o, hdx, hxm, u10, hx0, u11, curl);
-      }
-      if (in_x && kz) {  // Hy: dEx/dz - dEz/dx, voxels (i, j-1..j, k)
-        const R curl = curl_with_psi(A, s_cp, 1, 2, szH, 0, sxH, i, j, k, dif_(ex_up, ex, ihz), dif_(ez_ip, ez, ihx), own);
-        Hy = h_update(hy_o, hdy, hym, u01, hy0, u11, curl);
-      }
-      if (in_x && in_y) {  // Hz: dEy/dx - dEx/dy, voxels (i, j, k-1..k)
-        const R curl = curl_with_psi(A, s_cp, 1, 0, sxH, 1, syH, i, j, k, dif_(ey_ip, ey, ihx), dif_(ex_jp, ex, ihy), own);
-        Hz = h_update(hz_o, hdz, hzm, u11_b, hz0, u11, curl);
-      }
-    }
+    if (hx_on)  // Hx: (curl E)_x = dEz/dy - dEy/dz, voxels (i-1..i, j, k)
+      Hx = h_update(hx_o, hdx, hxm, u10, hx0, u11,
+                    curl_psi(A, s_cp, 1, 1, pHx1, 2, pHx2, dif_(ez_jp, ez, ihy), dif_(ey_up, ey, ihz), own));
+    if (hy_on)  // Hy: dEx/dz - dEz/dx, voxels (i, j-1..j, k)
+      Hy = h_update(hy_o, hdy, hym, u01, hy0, u11,
+                    curl_psi(A, s_cp, 1, 2, pHy1, 0, pHy2, dif_(ex_up, ex, ihz), dif_(ez_ip, ez, ihx), own));
+    if (hz_on)  // Hz: dEy/dx - dEx/dy, voxels (i, j, k-1..k)
+      Hz = h_update(hz_o, hdz, hzm, u11_b, hz0, u11,
+                    curl_psi(A, s_cp, 1, 0, pHz1, 1, pHz2, dif_(ey_ip, ey, ihx), dif_(ex_jp, ex, ihy), own));
     sHxz[0][ty][tx] = Hx;
     sHxz[1][ty][tx] = Hz;
     const R hy_l = __shfl_up_sync(0xffffffffu, Hy, 1);  // H of node i-1 (same warp)
     const R hz_l = __shfl_up_sync(0xffffffffu, Hz, 1);
+    // the E side's CPML states, in flight across the barrier
+    const bool ex_on = need_ex && !(fix_y || fix_z), ey_on = need_ey && !(fix_x || fix_z);
+    const bool ez_on = own && kz && !(fix_x || fix_y);
+    const Psi<R> pEx1 = psi_node(A, 1, 0, 1, ex_on ? syE : -1, i, j, k), pEx2 = psi_node(A, 2, 0, 0, ex_on ? szE : -1, i, j, k);
+    const Psi<R> pEy1 = psi_node(A, 2, 0, 1, ey_on ? szE : -1, i, j, k), pEy2 = psi_node(A, 0, 0, 0, ey_on ? sxE : -1, i, j, k);
+    const Psi<R> pEz1 = psi_node(A, 0, 0, 1, ez_on ? sxE : -1, i, j, k), pEz2 = psi_node(A, 1, 0, 0, ez_on ? syE : -1, i, j, k);
     __syncthreads();
 
     // ---- source current on this node's edges (three scalars selected by
@@ -523,9 +558,9 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
     const R pxe_a = fma_(hym, e01, mul_(hy0, e11)), pxs_a = fma_(hym, s01, mul_(hy0, s11));
     const R pye_a = fma_(hxm, e10, mul_(hx0, e11)), pys_a = fma_(hxm, s10, mul_(hx0, s11));
     R exn = ex, eyn = ey, ezn = ez, qx = 0, qy = 0, qz = 0;
-    if (need_ex && !(fix_y || fix_z)) {  // Ex: dHz/dy - dHy/dz, voxels (i, j-1..j, k-1..k)
-      const R curl = curl_with_psi(A, s_cp, 0, 1, syE, 2, szE, i, j, k, dif_(Hz, sHxz[1][ty - 1][tx], idy),
-                                   dif_(Hy, hy_km1, idz), own);
+    if (ex_on) {  // Ex: dHz/dy - dHy/dz, voxels (i, j-1..j, k-1..k)
+      const R curl = curl_psi(A, s_cp, 0, 1, pEx1, 2, pEx2, dif_(Hz, sHxz[1][ty - 1][tx], idy), dif_(Hy, hy_km1, idz),
+                              own);
       R Ss = fma_(hzm, pxs_b, mul_(hz0, pxs_a));
       if (CPL) {
         const R te = mul_(R(0.5), add_(th, th_ip));
@@ -535,9 +570,8 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
       exn = e_update<R, R>(ex, mul_(dtWx_y, add_(hzm, hz0)), sub_(curl, Jx), fma_(hzm, pxe_b, mul_(hz0, pxe_a)), Ss,
                            lqx, &qx);
     }
-    if (need_ey && !(fix_x || fix_z)) {  // Ey: dHx/dz - dHz/dx, voxels (i-1..i, j, k-1..k)
-      const R curl = curl_with_psi(A, s_cp, 0, 2, szE, 0, sxE, i, j, k, dif_(Hx, hx_km1, idz), dif_(Hz, hz_l, idx),
-                                   own);
+    if (ey_on) {  // Ey: dHx/dz - dHz/dx, voxels (i-1..i, j, k-1..k)
+      const R curl = curl_psi(A, s_cp, 0, 2, pEy1, 0, pEy2, dif_(Hx, hx_km1, idz), dif_(Hz, hz_l, idx), own);
       R Ss = fma_(hzm, pys_b, mul_(hz0, pys_a));
       if (CPL) {
         const R te = mul_(R(0.5), add_(th, th_jp));
@@ -547,9 +581,9 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
       eyn = e_update<R, R>(ey, mul_(dtWy_x, add_(hzm, hz0)), sub_(curl, Jy), fma_(hzm, pye_b, mul_(hz0, pye_a)), Ss,
                            lqy, &qy);
     }
-    if (own && kz && !(fix_x || fix_y)) {  // Ez: dHy/dx - dHx/dy, voxels (i-1..i, j-1..j, k)
-      const R curl = curl_with_psi(A, s_cp, 0, 0, sxE, 1, syE, i, j, k, dif_(Hy, hy_l, idx),
-                                   dif_(Hx, sHxz[0][ty - 1][tx], idy), own);
+    if (ez_on) {  // Ez: dHy/dx - dHx/dy, voxels (i-1..i, j-1..j, k)
+      const R curl = curl_psi(A, s_cp, 0, 0, pEz1, 1, pEz2, dif_(Hy, hy_l, idx), dif_(Hx, sHxz[0][ty - 1][tx], idy),
+                              own);
       const R Se = fma_(hym, fma_(hxm, e00, mul_(hx0, e01)), mul_(hy0, fma_(hxm, e10, mul_(hx0, e11))));
       R Ss = fma_(hym, fma_(hxm, s00, mul_(hx0, s01)), mul_(hy0, fma_(hxm, s10, mul_(hx0, s11))));
       if (CPL) {
@@ -600,17 +634,17 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
   if (CPL && own) A.Pout[id0 + (I)nz * plane] = mul_(add_(e_pend, sQy[ty - 1][tx]), A.inv_dt);
 }
 
-// ---- interior tile pairs: two nodes per thread. Pair (bx, by) (bx even)
-// owns the nodes of the single tiles bx and bx+1, i = 31 bx .. 31 bx + 61;
-// thread (tx, ty) holds the nodes i0 + 2 tx (.x) and i0 + 2 tx + 1 (.y),
-// i0 = 31 bx - 2 (lane 0 is the halo pair), of row j0 + ty. Every node, its
+// ---- interior tile pairs: two nodes per thread. The pair tile starting at
+// node xs (even) of row tile by owns the nodes i = xs .. xs + 61; thread
+// (tx, ty) holds the nodes i0 + 2 tx (.x) and i0 + 2 tx + 1 (.y), i0 = xs - 2
+// (lane 0 is the halo pair), of row j0 + ty. Every node, its
 // +x/+y neighbours and its voxels lie inside the grid, off the lateral walls
 // and outside the x/y CPML slabs; only the z slab and walls remain, decided
 // per plane for the whole CTA.
 template <typename R, typename I, int TY, bool CPL>
 __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
                                              EmStage<R, kEm2Nodes, TY> *stg, typename Pair2<R>::T (*sHxz)[TY][32],
-                                             typename Pair2<R>::T (*sQy)[32], uint64_t *bars, int *s_abort, int bx,
+                                             typename Pair2<R>::T (*sQy)[32], uint64_t *bars, int *s_abort, int xs,
                                              int by) {
   using R2 = typename Pair2<R>::T;
   constexpr int BX = em2_box_x(), BV = em2_vox_box_x();
@@ -618,7 +652,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int ny = g.ny, nz = g.nz;
   const int vd = g.nmat * M_COLS;
-  const int i0 = bx * 31 - 2, j0 = by * (TY - 1) - 1;
+  const int i0 = xs - 2, j0 = by * (TY - 1) - 1;
   const int ia = i0 + 2 * tx, j = j0 + ty;
   const bool own = tx > 0 && ty > 0;
   const bool accum = A.Qs != nullptr;
@@ -761,19 +795,22 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
     const R2 s00 = {s0a, s0b}, s01 = {s0b, s0c}, s10 = {s1a, s1b}, s11 = {s1b, s1c};
     const R2 u01 = {u0b, u0c}, u10 = {u1a, u1b}, u11 = {u1b, u1c};
 
-    // CPML state of the z slab for the node pair (derivative axis z)
-    auto chi_z = [&](int type, int slot, int s, R2 v) -> R2 {
-      const long long q = ((long long)s * (ny + 1) + j) * g.px + ia;
-      return chi_update<R, R2>(A, bc_<R2>(s_cp[(2 * 2 + type) * kMaxSlab + s]), 2, type, slot, q, v, own);
+    // CPML states of the z slab for the node pair (derivative axis z)
+    auto psi_z = [&](int type, int slot, int s) -> Psi<R2> {
+      return psi_pre<R, R2>(A, 2, type, slot, s, s >= 0 ? ((long long)s * (ny + 1) + j) * g.px + ia : 0);
+    };
+    auto chi_z = [&](int type, int slot, const Psi<R2> &p, R2 v) -> R2 {
+      return psi_apply<R, R2>(A, bc_<R2>(s_cp[(2 * 2 + type) * kMaxSlab + p.s]), 2, type, slot, p, v, own);
     };
 
     // ---- H^{n+1/2}
     R2 Hx = z2, Hy = z2;
     if (kz) {
+      const Psi<R2> pHx = psi_z(1, 0, szH), pHy = psi_z(1, 1, szH);
       const R2 d1 = dif_(ez_jp, ez, ihy), d2 = dif_(ey_up, ey, ihz);
-      Hx = h_update(hx_o, hdx, hxm, u10, hx0, u11, szH >= 0 ? sub_(d1, chi_z(1, 0, szH, d2)) : sub_(d1, d2));
+      Hx = h_update(hx_o, hdx, hxm, u10, hx0, u11, szH >= 0 ? sub_(d1, chi_z(1, 0, pHx, d2)) : sub_(d1, d2));
       const R2 f1 = dif_(ex_up, ex, ihz), f2 = dif_(ez_ip, ez, ihx);
-      Hy = h_update(hy_o, hdy, hym, u01, hy0, u11, szH >= 0 ? sub_(chi_z(1, 1, szH, f1), f2) : sub_(f1, f2));
+      Hy = h_update(hy_o, hdy, hym, u01, hy0, u11, szH >= 0 ? sub_(chi_z(1, 1, pHy, f1), f2) : sub_(f1, f2));
     }
     const R2 Hz = h_update(hz_o, hdz, hzm, u11_b, hz0, u11, sub_(dif_(ey_ip, ey, ihx), dif_(ex_jp, ex, ihy)));
     sHxz[0][ty][tx] = Hx;
@@ -807,7 +844,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
     R2 exn = ex, eyn = ey, ezn = ez, qx = z2, qy = z2, qz = z2;
     if (ty > 0 && !fix_z) {  // Ex (owners and the halo lane, whose x-edge share lane 1 needs)
       const R2 d1 = dif_(Hz, sHxz[1][ty - 1][tx], idy), d2 = dif_(Hy, hy_km1, idz);
-      const R2 curl = szE >= 0 ? sub_(d1, chi_z(0, 0, szE, d2)) : sub_(d1, d2);
+      const R2 curl = szE >= 0 ? sub_(d1, chi_z(0, 0, psi_z(0, 0, szE), d2)) : sub_(d1, d2);
       R2 Ss = fma_(hzm, pxs_b, mul_(hz0, pxs_a));
       if (CPL) {
         const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_ip));
@@ -819,7 +856,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
     }
     if (!fix_z) {  // Ey (every row: the halo row's y-edge share goes to row ty+1)
       const R2 d1 = dif_(Hx, hx_km1, idz), d2 = dif_(Hz, hz_l, idx);
-      const R2 curl = szE >= 0 ? sub_(chi_z(0, 1, szE, d1), d2) : sub_(d1, d2);
+      const R2 curl = szE >= 0 ? sub_(chi_z(0, 1, psi_z(0, 1, szE), d1), d2) : sub_(d1, d2);
       R2 Ss = fma_(hzm, pys_b, mul_(hz0, pys_a));
       if (CPL) {
         const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_jp));
@@ -928,32 +965,37 @@ __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
   if (s_abort) return;
   int b = (int)blockIdx.x;
   if (b < A.n_border) {
-    // border tile b: the rows below the interior rectangle, then the left and
-    // right parts of its rows, then the rows above it
-    const int nbx = A.nbx, below = A.iby0 * nbx, w = nbx - 2 * A.npx, mid = (A.iby1 - A.iby0) * w;
-    int bx, by;
+    // border tile b: the rows below the interior rows, then the left and
+    // right parts of the interior rows, then the rows above them
+    const int nbx = A.nbx, below = A.iby0 * nbx, w = A.nl + A.nr, mid = (A.iby1 - A.iby0) * w;
+    int xs, xe = A.g.nx + 1, by;
     if (b < below) {
       by = b / nbx;
-      bx = b - by * nbx;
+      xs = (TX - 1) * (b - by * nbx);
     } else if ((b -= below) < mid) {
       by = b / w;
-      bx = b - by * w;
+      const int c = b - by * w;
       by += A.iby0;
-      if (bx >= A.ibx0) bx += 2 * A.npx;
+      if (c < A.nl) {
+        xs = (TX - 1) * c;
+        xe = A.xb0;
+      } else {
+        xs = A.xb1 + (TX - 1) * (c - A.nl);
+      }
     } else {
       b -= mid;
       by = b / nbx;
-      bx = b - by * nbx;
+      xs = (TX - 1) * (b - by * nbx);
       by += A.iby1;
     }
     em_tile_border<R, I, TY, CPL>(A, s_cp, s_mt, reinterpret_cast<EmStage<R, TX, TY> *>(stg),
                                   reinterpret_cast<R(*)[TY][TX]>(&sHxz[0][0][0]), reinterpret_cast<R(*)[TX]>(&sQy[0][0]),
-                                  s_bar, &s_abort, bx, by);
+                                  s_bar, &s_abort, xs, xe, by);
   } else {
     b -= A.n_border;
     const int py = b / A.npx, px = b - py * A.npx;
     em_tile_pair<R, I, TY, CPL>(A, s_cp, s_mt, reinterpret_cast<EmStage<R, kEm2Nodes, TY> *>(stg), sHxz, sQy, s_bar,
-                                &s_abort, A.ibx0 + 2 * px, A.iby0 + py);
+                                &s_abort, A.xb0 + 62 * px, A.iby0 + py);
   }
 }
 
