@@ -564,6 +564,9 @@ __global__ void __launch_bounds__(256) cg_init_kernel(long long n, const R *f0, 
 }
 
 // x += alpha p, r -= alpha q, alpha = rz/pq; partial sums of r.(D^-1 r) and r.r
+// (each node's three-component terms in the context precision, accumulated in
+// FP64). FP32 vectors are streamed four nodes per load (n is a multiple of 4:
+// the padded node arrays have rows of a multiple of 32).
 template <typename R>
 __global__ void __launch_bounds__(256) cg_update_kernel(long long n, const CgScalars *sc, int parity, R *x0, R *x1,
                                                          R *x2, R *r0, R *r1, R *r2, const R *p0, const R *p1,
@@ -572,14 +575,42 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long n, const CgSca
                                                          double *part_rr) {
   const R alpha = (R)(sc->rz[parity] / sc->pq);
   double rz = 0, rr = 0;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-    x0[q] += alpha * p0[q];
-    x1[q] += alpha * p1[q];
-    x2[q] += alpha * p2[q];
-    const R a0 = r0[q] - alpha * q0[q], a1 = r1[q] - alpha * q1[q], a2 = r2[q] - alpha * q2[q];
-    r0[q] = a0; r1[q] = a1; r2[q] = a2;
-    rz += (double)(a0 * d0[q] * a0 + a1 * d1[q] * a1 + a2 * d2[q] * a2);
-    rr += (double)(a0 * a0 + a1 * a1 + a2 * a2);
+  const long long stride = (long long)gridDim.x * blockDim.x, first = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if constexpr (sizeof(R) == 4) {
+    R *X[3] = {x0, x1, x2}, *Rr[3] = {r0, r1, r2};
+    const R *P[3] = {p0, p1, p2}, *Q[3] = {q0, q1, q2}, *D[3] = {d0, d1, d2};
+    for (long long v = first; v < (n >> 2); v += stride) {
+      float4 a[3], dd[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float4 pv = reinterpret_cast<const float4 *>(P[c])[v], qv = reinterpret_cast<const float4 *>(Q[c])[v];
+        float4 xv = reinterpret_cast<const float4 *>(X[c])[v], rv = reinterpret_cast<const float4 *>(Rr[c])[v];
+        dd[c] = reinterpret_cast<const float4 *>(D[c])[v];
+        xv.x += alpha * pv.x, xv.y += alpha * pv.y, xv.z += alpha * pv.z, xv.w += alpha * pv.w;
+        rv.x -= alpha * qv.x, rv.y -= alpha * qv.y, rv.z -= alpha * qv.z, rv.w -= alpha * qv.w;
+        reinterpret_cast<float4 *>(X[c])[v] = xv;
+        reinterpret_cast<float4 *>(Rr[c])[v] = rv;
+        a[c] = rv;
+      }
+      rz += (double)(a[0].x * dd[0].x * a[0].x + a[1].x * dd[1].x * a[1].x + a[2].x * dd[2].x * a[2].x);
+      rz += (double)(a[0].y * dd[0].y * a[0].y + a[1].y * dd[1].y * a[1].y + a[2].y * dd[2].y * a[2].y);
+      rz += (double)(a[0].z * dd[0].z * a[0].z + a[1].z * dd[1].z * a[1].z + a[2].z * dd[2].z * a[2].z);
+      rz += (double)(a[0].w * dd[0].w * a[0].w + a[1].w * dd[1].w * a[1].w + a[2].w * dd[2].w * a[2].w);
+      rr += (double)(a[0].x * a[0].x + a[1].x * a[1].x + a[2].x * a[2].x);
+      rr += (double)(a[0].y * a[0].y + a[1].y * a[1].y + a[2].y * a[2].y);
+      rr += (double)(a[0].z * a[0].z + a[1].z * a[1].z + a[2].z * a[2].z);
+      rr += (double)(a[0].w * a[0].w + a[1].w * a[1].w + a[2].w * a[2].w);
+    }
+  } else {
+    for (long long q = first; q < n; q += stride) {
+      x0[q] += alpha * p0[q];
+      x1[q] += alpha * p1[q];
+      x2[q] += alpha * p2[q];
+      const R a0 = r0[q] - alpha * q0[q], a1 = r1[q] - alpha * q1[q], a2 = r2[q] - alpha * q2[q];
+      r0[q] = a0; r1[q] = a1; r2[q] = a2;
+      rz += (double)(a0 * d0[q] * a0 + a1 * d1[q] * a1 + a2 * d2[q] * a2);
+      rr += (double)(a0 * a0 + a1 * a1 + a2 * a2);
+    }
   }
   rz = block_sum(rz);
   rr = block_sum(rr);
@@ -599,20 +630,35 @@ __global__ void __launch_bounds__(256) scale3_kernel(long long n, R *x0, R *x1, 
   }
 }
 
-// p = D^-1 r + beta p, beta = rz_new / rz_old
+// p = D^-1 r + beta p, beta = rz_new / rz_old (FP32: four nodes per load)
 template <typename R>
 __global__ void __launch_bounds__(256) cg_direction_kernel(long long n, const CgScalars *sc, int parity, R *p0,
                                                             R *p1, R *p2, const R *r0, const R *r1, const R *r2,
                                                             const R *d0, const R *d1, const R *d2) {
   const R beta = (R)(sc->rz[parity ^ 1] / sc->rz[parity]);
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-    p0[q] = d0[q] * r0[q] + beta * p0[q];
-    p1[q] = d1[q] * r1[q] + beta * p1[q];
-    p2[q] = d2[q] * r2[q] + beta * p2[q];
+  const long long stride = (long long)gridDim.x * blockDim.x, first = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if constexpr (sizeof(R) == 4) {
+    R *P[3] = {p0, p1, p2};
+    const R *Rr[3] = {r0, r1, r2}, *D[3] = {d0, d1, d2};
+    for (long long v = first; v < (n >> 2); v += stride) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float4 pv = reinterpret_cast<const float4 *>(P[c])[v];
+        const float4 rv = reinterpret_cast<const float4 *>(Rr[c])[v], dv = reinterpret_cast<const float4 *>(D[c])[v];
+        pv.x = dv.x * rv.x + beta * pv.x, pv.y = dv.y * rv.y + beta * pv.y;
+        pv.z = dv.z * rv.z + beta * pv.z, pv.w = dv.w * rv.w + beta * pv.w;
+        reinterpret_cast<float4 *>(P[c])[v] = pv;
+      }
+    }
+  } else {
+    for (long long q = first; q < n; q += stride) {
+      p0[q] = d0[q] * r0[q] + beta * p0[q];
+      p1[q] = d1[q] * r1[q] + beta * p1[q];
+      p2[q] = d2[q] * r2[q] + beta * p2[q];
+    }
   }
 }
 
-// final stage of a two-stage reduction: one CTA sums the partials in a fixed order
 __global__ void __launch_bounds__(1024) reduce_final_kernel(const double *part, int n, double *out) {
   double s = 0;
   for (int q = threadIdx.x; q < n; q += blockDim.x) s += part[q];

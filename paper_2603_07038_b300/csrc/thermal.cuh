@@ -261,7 +261,7 @@ struct ThTmaArgs {
 };
 
 template <typename R>
-__global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? 4 : 2) thermal_tma_kernel(const __grid_constant__ ThTmaArgs<R> TA) {
+__global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? 3 : 2) thermal_tma_kernel(const __grid_constant__ ThTmaArgs<R> TA) {
   using R2 = typename Pair2<R>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
