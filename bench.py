@@ -136,13 +136,22 @@ def em_alg_bytes(ctx, p):
     return 48 * cells + cells + 8 * nodes + nodes // 2 + psi
 
 
-def traffic_from_profile(kernel_src):
+def kernel_source_hash(paths):
+    """First 16 hex digits of the SHA-256 of the kernel's source files, in order."""
+    h = hashlib.sha256()
+    for q in paths:
+        h.update(open(q, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(kernel_srcs):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+    the current kernel source (em.cuh and the common.cuh it includes); else
+    None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         t = json.load(open(path))
-        h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        h = kernel_source_hash(kernel_srcs)
         if t.get("em_step_kernel", {}).get("source_sha256_16") == h:
             return t["em_step_kernel"]["dram_bytes_per_launch"]
     except Exception:
@@ -250,7 +259,8 @@ def gpu_arm(args, rank, world):
     peaks = load_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6400.0
     achieved = alg / (em_launch_ms * 1e-3) / 1e9
-    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2603_07038_b300", "csrc", "em.cuh"))
+    csrc = os.path.join(ROOT, "paper_2603_07038_b300", "csrc")
+    traffic = traffic_from_profile([os.path.join(csrc, "em.cuh"), os.path.join(csrc, "common.cuh")])
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
