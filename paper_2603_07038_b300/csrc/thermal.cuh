@@ -227,20 +227,27 @@ __global__ void __launch_bounds__(512) thermal_kernel(const ThArgs<R> A) {  // b
   }
 }
 
-// ---- the same step with TMA-staged planes and two nodes per thread. A CTA
-// of 32 x kThTY threads owns a 64 x kThTY tile of node columns (thread tx:
-// nodes i0 + 2 tx and i0 + 2 tx + 1 of row j0 + ty; no halo compute: the
-// update of a node reads only old temperatures) and marches in z. Per plane
-// one thread copies into shared memory the temperature with a one-node halo
-// (x from i0 - 4, the 16-byte rule; y from j0 - 1), the tile's source power
-// and the voxel IDs of the layer above (x from i0 - 16), plus the plane's z
-// record; four stages, one mbarrier each, bounded waits. Positions outside
-// the grid arrive as zero (a valid material ID and a finite temperature that
-// the zero geometry factors then remove).
-constexpr int kThTY = 8, kThTX = 64;
+// ---- the same step with TMA-staged planes and kThNP node pairs per thread.
+// A CTA of 32 x kThTY threads owns a kThTX x kThTY tile of node columns
+// (thread tx: nodes i0 + 2 kThNP tx .. i0 + 2 kThNP tx + 2 kThNP - 1 of row
+// j0 + ty; no halo compute: the update of a node reads only old
+// temperatures) and marches in z. Per plane one thread copies into shared
+// memory the temperature with a one-node halo (x from i0 - 4, the 16-byte
+// rule; y from j0 - 1), the tile's source power and the voxel IDs of the
+// layer above (x from i0 - 16), plus the plane's z record; four stages, one
+// mbarrier each, bounded waits. Positions outside the grid arrive as zero (a
+// valid material ID and a finite temperature that the zero geometry factors
+// then remove). More nodes per thread share the per-plane waits, barrier and
+// addressing; each pair's arithmetic is the pair form of th_layer /
+// th_coeffs / th_update.
+#ifndef COSIM_TH_NP
+#define COSIM_TH_NP 1
+#endif
+constexpr int kThNP = COSIM_TH_NP;    // node pairs per thread
+constexpr int kThTY = 8, kThTX = 64 * kThNP;
 constexpr int kThStages = 4, kThAhead = 3;
-constexpr int kThBoxT = kThTX + 8;   // temperature box width: columns i0-4 .. i0+67
-constexpr int kThBoxV = kThTX + 32;  // voxel box width: columns i0-16 .. i0+79
+constexpr int kThBoxT = kThTX + 8;   // temperature box width: columns i0-4 .. i0+kThTX+3
+constexpr int kThBoxV = kThTX + 32;  // voxel box width: columns i0-16 .. i0+kThTX+15
 template <typename R>
 struct ThStage {
   EmBox<R, kThTY + 2, kThBoxT> T;        // rows j0-1 .. j0+kThTY
@@ -261,8 +268,10 @@ struct ThTmaArgs {
 };
 
 template <typename R>
-__global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? 3 : 2) thermal_tma_kernel(const __grid_constant__ ThTmaArgs<R> TA) {
+__global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? (kThNP == 1 ? 3 : 2) : (kThNP == 1 ? 2 : 1))
+    thermal_tma_kernel(const __grid_constant__ ThTmaArgs<R> TA) {
   using R2 = typename Pair2<R>::T;
+  constexpr int NP = kThNP;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const ThArgs<R> &A = TA.a;
@@ -286,8 +295,8 @@ __global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? 3 : 2) thermal_tm
   if (s_abort) return;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int i0 = blockIdx.x * kThTX, j0 = blockIdx.y * kThTY;
-  const int ia = i0 + 2 * tx, j = j0 + ty;  // nodes ia (.x) and ia + 1 (.y) of row j
-  const bool act_a = ia <= nx && j <= ny, act_b = ia + 1 <= nx && j <= ny;
+  const int ia = i0 + 2 * NP * tx, j = j0 + ty;  // first node of the thread, row j
+  const int n_act = j <= ny ? max(0, min(2 * NP, nx + 1 - ia)) : 0;  // nodes of the thread inside the grid
   const bool has_p = A.P != nullptr;
   const unsigned stage_bytes = (unsigned)(((kThTY + 2) * kThBoxT + (has_p ? kThTY * kThTX : 0)) * (int)sizeof(R) +
                                           4 * (int)sizeof(R) + (kThTY + 1) * kThBoxV);
@@ -303,11 +312,18 @@ __global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? 3 : 2) thermal_tm
     tma_load_3d(&S.V.v[0][0], &TA.tmV, i0 - 16, j0 - 1, k, &bars[s]);
     bulk_load(&S.Z.v[0][0], A.zt + 4 * (size_t)k, 4 * sizeof(R), &bars[s]);
   };
-  const ThCol<R2> c = th_pair<R>(th_column(g, A, ia, j), th_column(g, A, ia + 1, j));
-  const int cT = 2 * tx + 4, cV = 2 * tx + 15, r1 = ty + 1;  // columns / row of node ia in the boxes
-  R *tp = A.Tn + (act_a ? g.nid(ia, j, 0) : 0);
-  ThLayer<R2> lo = th_layer_zero<R2, R>();
-  R2 T_km1 = bc_<R2>(R(0)), gz = bc_<R2>(R(0));
+  ThCol<R2> c[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) c[q] = th_pair<R>(th_column(g, A, ia + 2 * q, j), th_column(g, A, ia + 2 * q + 1, j));
+  const int cT = 2 * NP * tx + 4, cV = 2 * NP * tx + 15, r1 = ty + 1;  // columns / row of node ia in the boxes
+  R *tp = A.Tn + (n_act > 0 ? g.nid(ia, j, 0) : 0);
+  ThLayer<R2> lo[NP];
+  R2 T_km1[NP], gz[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    lo[q] = th_layer_zero<R2, R>();
+    T_km1[q] = gz[q] = bc_<R2>(R(0));
+  }
   if (leader)
     for (int q = 0; q < kThAhead; ++q) issue(q);
   bool ok0 = mbar_wait(&bars[0], 0u);
@@ -332,26 +348,39 @@ __global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? 3 : 2) thermal_tm
     const ThStage<R> &S0 = stg[k & (kThStages - 1)];
     const ThStage<R> &S1 = stg[(k + 1) & (kThStages - 1)];
     const R hz = S0.Z.v[0][0], ihz = S0.Z.v[0][1], hzm = S0.Z.v[0][3];
-    // {k, rho_cp} of the voxels ia-1, ia, ia+1 in rows j-1 (a) and j (b)
-    const R2 a0 = s_kc[S0.V.v[ty][cV]], a1 = s_kc[S0.V.v[ty][cV + 1]], a2 = s_kc[S0.V.v[ty][cV + 2]];
-    const R2 b0 = s_kc[S0.V.v[r1][cV]], b1 = s_kc[S0.V.v[r1][cV + 1]], b2 = s_kc[S0.V.v[r1][cV + 2]];
-    const ThLayer<R2> up = th_layer<R2>(R2{a0.x, a1.x}, R2{a1.x, a2.x}, R2{b0.x, b1.x}, R2{b1.x, b2.x},
-                                        R2{a0.y, a1.y}, R2{a1.y, a2.y}, R2{b0.y, b1.y}, R2{b1.y, b2.y}, c);
-    const ThCoeffs<R2> q = th_coeffs<R2, R>(c, lo, up, hz, ihz, hzm, k == 0, k == nz, A.hconv, gz);
-    const R2 Tc = *reinterpret_cast<const R2 *>(&S0.T.v[r1][cT]);
-    const R2 Tjm = *reinterpret_cast<const R2 *>(&S0.T.v[ty][cT]);
-    const R2 Tjp = *reinterpret_cast<const R2 *>(&S0.T.v[r1 + 1][cT]);
-    const R2 Tkp = k < nz ? *reinterpret_cast<const R2 *>(&S1.T.v[r1][cT]) : bc_<R2>(R(0));
-    const R2 Tim = {S0.T.v[r1][cT - 1], Tc.x}, Tip = {Tc.y, S0.T.v[r1][cT + 2]};
-    const R2 p = has_p ? *reinterpret_cast<const R2 *>(&S0.P.v[ty][2 * tx]) : bc_<R2>(R(0));
-    const R2 Tn = th_update<R2, R>(q, Tc, Tim, Tip, Tjm, Tjp, T_km1, Tkp, p, A.T_amb, A.dt);
-    if (act_b)
-      *reinterpret_cast<R2 *>(tp) = Tn;
-    else if (act_a)
-      *tp = Tn.x;
+    // {k, rho_cp} of the voxels ia-1 .. ia+2NP-1 in rows j-1 (a) and j (b)
+    R2 a[2 * NP + 1], b[2 * NP + 1];
+#pragma unroll
+    for (int q = 0; q <= 2 * NP; ++q) {
+      a[q] = s_kc[S0.V.v[ty][cV + q]];
+      b[q] = s_kc[S0.V.v[r1][cV + q]];
+    }
+    R2 Tc[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) Tc[q] = ldv_<R2>(&S0.T.v[r1][cT + 2 * q]);
+    const R T_left = S0.T.v[r1][cT - 1], T_right = S0.T.v[r1][cT + 2 * NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const int o = cT + 2 * q;
+      const ThLayer<R2> up = th_layer<R2>(R2{a[2 * q].x, a[2 * q + 1].x}, R2{a[2 * q + 1].x, a[2 * q + 2].x},
+                                          R2{b[2 * q].x, b[2 * q + 1].x}, R2{b[2 * q + 1].x, b[2 * q + 2].x},
+                                          R2{a[2 * q].y, a[2 * q + 1].y}, R2{a[2 * q + 1].y, a[2 * q + 2].y},
+                                          R2{b[2 * q].y, b[2 * q + 1].y}, R2{b[2 * q + 1].y, b[2 * q + 2].y}, c[q]);
+      const ThCoeffs<R2> cf = th_coeffs<R2, R>(c[q], lo[q], up, hz, ihz, hzm, k == 0, k == nz, A.hconv, gz[q]);
+      const R2 Tjm = ldv_<R2>(&S0.T.v[ty][o]), Tjp = ldv_<R2>(&S0.T.v[r1 + 1][o]);
+      const R2 Tkp = k < nz ? ldv_<R2>(&S1.T.v[r1][o]) : bc_<R2>(R(0));
+      const R2 Tim = {q == 0 ? T_left : Tc[q - 1].y, Tc[q].x};
+      const R2 Tip = {Tc[q].y, q == NP - 1 ? T_right : Tc[q + 1].x};
+      const R2 p = has_p ? ldv_<R2>(&S0.P.v[ty][2 * NP * tx + 2 * q]) : bc_<R2>(R(0));
+      const R2 Tn = th_update<R2, R>(cf, Tc[q], Tim, Tip, Tjm, Tjp, T_km1[q], Tkp, p, A.T_amb, A.dt);
+      if (n_act >= 2 * q + 2)
+        stv_(tp + 2 * q, Tn);
+      else if (n_act == 2 * q + 1)
+        tp[2 * q] = Tn.x;
+      T_km1[q] = Tc[q];
+      lo[q] = up;
+    }
     tp += g.plane;
-    T_km1 = Tc;
-    lo = up;
   }
 }
 
