@@ -323,9 +323,21 @@ constexpr int kEmStages = COSIM_EM_STAGES;
 constexpr int kEmAhead = COSIM_EM_AHEAD;
 static_assert((kEmStages & (kEmStages - 1)) == 0, "stage count must be a power of two");
 static_assert(kEmAhead >= 2 && kEmAhead <= kEmStages - 1, "prefetch distance must leave the stage of plane k-1 free");
+// Border tiles (FP32) keep the H side's CPML states of the next plane in a
+// per-thread shared-memory ring filled by cp.async: 2 planes x 6 states x
+// (chi high, chi low, previous derivative).
+constexpr int kPsiH = 6;
+template <typename R, int TY>
+__host__ __device__ constexpr size_t em_psi_ring_bytes() {
+  return sizeof(R) == 4 ? (size_t)32 * TY * 2 * kPsiH * 3 * sizeof(R) : 0;
+}
 template <typename R, int TY>
 __host__ __device__ constexpr size_t em_smem_bytes(int nmat) {
-  return em_stage_offset<R>(nmat) + kEmStages * em_stage_bytes<R, TY>() + 128;  // + alignment slack
+  return em_stage_offset<R>(nmat) +
+         (kEmStages * em_stage_bytes<R, TY>() > kEmStages * sizeof(EmStage<R, 32, TY>) + em_psi_ring_bytes<R, TY>()
+              ? kEmStages * em_stage_bytes<R, TY>()
+              : kEmStages * sizeof(EmStage<R, 32, TY>) + em_psi_ring_bytes<R, TY>()) +
+         128;  // + alignment slack
 }
 
 // Bounded waits for the planes a CTA reads at plane k: plane k+1 (plane k was
@@ -428,10 +440,47 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
   const R dtWx_y = mul_(dt, add_(hym, hy0)), dtWy_x = mul_(dt, add_(hxm, hx0));
   const R lqx = mul_(R(0.25), hx0), lqy = mul_(R(0.25), hy0);
 
+  // The H side's CPML states of plane kk (d, slot; slab position s or -1):
+  // Hx (y: slot 1, z: slot 0), Hy (z: slot 1, x: slot 0), Hz (x: slot 1,
+  // y: slot 0). FP32 border tiles request them one plane ahead by cp.async
+  // into this thread's slots of the ring behind the stages.
+  auto h_state = [&](int e, int kk, int &d, int &slot) -> int {
+    const bool kzz = kk < nz;
+    const int szz = kzz ? slab_index(kk, nz, A.slo[2], A.shi[2]) : -1;
+    const bool hx_on = act && in_y && kzz, hy_on = act && in_x && kzz, hz_on = act && in_x && in_y && kk <= nz;
+    switch (e) {
+      case 0: d = 1, slot = 1; return hx_on ? syH : -1;
+      case 1: d = 2, slot = 0; return hx_on ? szz : -1;
+      case 2: d = 2, slot = 1; return hy_on ? szz : -1;
+      case 3: d = 0, slot = 0; return hy_on ? sxH : -1;
+      case 4: d = 0, slot = 1; return hz_on ? sxH : -1;
+      default: d = 1, slot = 0; return hz_on ? syH : -1;
+    }
+  };
+  R *ring = reinterpret_cast<R *>(stg + kEmStages) + (ty * 32 + tx) * (2 * kPsiH * 3);
+  auto prefetch_h = [&](int kk) {
+    if constexpr (sizeof(R) == 4) {
+      R *r = ring + (kk & 1) * (kPsiH * 3);
+#pragma unroll
+      for (int e = 0; e < kPsiH; ++e) {
+        int d, slot;
+        const int sp = h_state(e, kk, d, slot);
+        if (sp >= 0) {
+          const long long q = psi_index(A, d, sp, i, j, kk);
+          cp_async<4>(r + 3 * e, A.xHo[d][slot] + q, true);
+          cp_async<4>(r + 3 * e + 1, A.lHo[d][slot] + q, true);
+          cp_async<4>(r + 3 * e + 2, A.dHo[d][slot] + q, true);
+        }
+      }
+      cp_async_commit();
+    }
+  };
+
   if (leader) {
 #pragma unroll
     for (int q = 0; q < kEmAhead; ++q) issue(q);
   }
+  prefetch_h(0);
   if (!mbar_wait(&bars[0], 0u)) *s_abort = 1;
   R hx_km1 = 0, hy_km1 = 0, qz_km1 = 0;
   // layer k-1 partial sums of the x / y edges and 1/mu of voxel (i, j, k-1);
@@ -450,9 +499,11 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
     em_wait_next(bars, k, nz, s_abort);
     __syncthreads();
     if (*s_abort) {  // a copy did not arrive in time: drain what is in flight (bounded), flag, leave
+      if constexpr (sizeof(R) == 4) cp_async_wait<0>();
       if (leader) em_abort(bars, k, nz, A.err);
       return;
     }
+    prefetch_h(k + 1);
     const I id = id0 + (I)k * plane;
     // Joule energy of node (i, j, k-1): its y-edge share from j-1 is now visible
     if (accum && own && k > 0) {
@@ -484,7 +535,6 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
     const R hdz = mul_(half_dt, idz);
     const bool fix_z = (k == 0 && A.fixlo[2]) || (k == nz && A.fixhi[2]);
     const int szE = slab_index(k, nz, A.slo[2], A.shi[2]);
-    const int szH = kz ? szE : -1;
 
     const int cx = tx + xr;  // this node's column in the staged boxes
     const R ex = S0.E[0].v[ty][cx], ey = S0.E[1].v[ty][cx], ez = S0.E[2].v[ty][cx];
@@ -513,9 +563,28 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
     // ---- H^{n+1/2} at (i,j,k); dt/mu of a face is the series mean over the
     // two voxels its dual edge crosses
     const bool hx_on = act && in_y && kz, hy_on = act && in_x && kz, hz_on = act && in_x && in_y;
-    const Psi<R> pHx1 = psi_node(A, 1, 1, 1, hx_on ? syH : -1, i, j, k), pHx2 = psi_node(A, 2, 1, 0, hx_on ? szH : -1, i, j, k);
-    const Psi<R> pHy1 = psi_node(A, 2, 1, 1, hy_on ? szH : -1, i, j, k), pHy2 = psi_node(A, 0, 1, 0, hy_on ? sxH : -1, i, j, k);
-    const Psi<R> pHz1 = psi_node(A, 0, 1, 1, hz_on ? sxH : -1, i, j, k), pHz2 = psi_node(A, 1, 1, 0, hz_on ? syH : -1, i, j, k);
+    Psi<R> ph[kPsiH];
+    if constexpr (sizeof(R) == 4) {  // this plane's states landed in the ring (the group of plane k+1 may still fly)
+      cp_async_wait<1>();
+      const R *r = ring + (k & 1) * (kPsiH * 3);
+#pragma unroll
+      for (int e = 0; e < kPsiH; ++e) {
+        int d, slot;
+        ph[e].s = h_state(e, k, d, slot);
+        ph[e].q = ph[e].s >= 0 ? psi_index(A, d, ph[e].s, i, j, k) : 0;
+        ph[e].c.hi = r[3 * e];
+        ph[e].c.lo = r[3 * e + 1];
+        ph[e].c.d = r[3 * e + 2];
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < kPsiH; ++e) {
+        int d, slot;
+        const int sp = h_state(e, k, d, slot);
+        ph[e] = psi_node(A, d, 1, slot, sp, i, j, k);
+      }
+    }
+    const Psi<R> &pHx1 = ph[0], &pHx2 = ph[1], &pHy1 = ph[2], &pHy2 = ph[3], &pHz1 = ph[4], &pHz2 = ph[5];
     R Hx = 0, Hy = 0, Hz = 0;
     if (hx_on)  // Hx: (curl E)_x = dEz/dy - dEy/dz, voxels (i-1..i, j, k)
       Hx = h_update(hx_o, hdx, hxm, u10, hx0, u11,

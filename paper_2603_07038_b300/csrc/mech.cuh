@@ -62,10 +62,11 @@ __device__ __forceinline__ void group_term(const R G[3][3], R lam, R mu, R w, co
       }
 }
 
-// u[c][a] (nodal displacement of one element) -> K_e u_e in place.
+// u[c][a] (nodal displacement of one element) -> K_e u_e in place; ih* are
+// the element's inverse sizes (2 ih = 2/h exactly: scaling by two is exact).
 template <typename R>
-__device__ __forceinline__ void hex8_apply(R u[3][8], R lam, R mu, R hx, R hy, R hz) {
-  const R g[3] = {R(2) / hx, R(2) / hy, R(2) / hz};
+__device__ __forceinline__ void hex8_apply(R u[3][8], R lam, R mu, R hx, R hy, R hz, R ihx, R ihy, R ihz) {
+  const R g[3] = {R(2) * ihx, R(2) * ihy, R(2) * ihz};
   const R g8[3] = {g[0] * R(0.125), g[1] * R(0.125), g[2] * R(0.125)};
 #pragma unroll
   for (int c = 0; c < 3; ++c) modal_fwd(u[c]);
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(TX *TY) hex8_matvec_kernel(const MvArgs<R> A) 
   const int X = ex + 1, Y = ey + 1;
   const bool own = tx < TX - 1 && ty < TY - 1 && X <= nx && Y <= ny;
   const R hx = elem_xy ? g.h[0][ex] : R(1), hy = elem_xy ? g.h[1][ey] : R(1);
+  const R ihx = elem_xy ? g.ih[0][ex] : R(1), ihy = elem_xy ? g.ih[1][ey] : R(1);
 
   auto su_at = [&](int buf, int c, int qy, int qx) -> R & {
     return su[((buf * 3 + c) * (TY + 1) + qy) * (TX + 1) + qx];
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(TX *TY) hex8_matvec_kernel(const MvArgs<R> A) 
 #pragma unroll
         for (int a = 0; a < 8; ++a)
           r[c][a] = su_at((k + (a >> 2)) & 1, c, ty + ((a >> 1) & 1), tx + (a & 1));
-      hex8_apply(r, s_mt[m * M_COLS + M_LAM], s_mt[m * M_COLS + M_MU], hx, hy, g.h[2][k]);
+      hex8_apply(r, s_mt[m * M_COLS + M_LAM], s_mt[m * M_COLS + M_MU], hx, hy, g.h[2][k], ihx, ihy, g.ih[2][k]);
     } else {
 #pragma unroll
       for (int c = 0; c < 3; ++c)
@@ -315,6 +317,7 @@ __global__ void __launch_bounds__(TX *TY) hex8_matvec_tma_kernel(const __grid_co
   const int X = ex + 1, Y = ey + 1;
   const bool own = tx < TX - 1 && ty < TY - 1 && X <= nx && Y <= ny;
   const R hx = elem_xy ? g.h[0][ex] : R(1), hy = elem_xy ? g.h[1][ey] : R(1);
+  const R ihx = elem_xy ? g.ih[0][ex] : R(1), ihy = elem_xy ? g.ih[1][ey] : R(1);
   const unsigned fixed_bytes =
       (unsigned)(3 * (TY + 1) * (TX + 4) * (int)sizeof(R) + (TY + 1) * (TX + 16) + 4 * (int)sizeof(R));
   const unsigned vox_bytes = (unsigned)(TY * (TX + 16));
@@ -369,7 +372,8 @@ __global__ void __launch_bounds__(TX *TY) hex8_matvec_tma_kernel(const __grid_co
 #pragma unroll
         for (int a = 0; a < 8; ++a)
           r[c][a] = u_at((a >> 2) ? S1 : S0, c, ty + ((a >> 1) & 1), cu + (a & 1));
-      hex8_apply(r, s_mt[m * M_COLS + M_LAM], s_mt[m * M_COLS + M_MU], hx, hy, S0.Z.v[0][0]);
+      hex8_apply(r, s_mt[m * M_COLS + M_LAM], s_mt[m * M_COLS + M_MU], hx, hy, S0.Z.v[0][0], ihx, ihy,
+                 S0.Z.v[0][1]);
     } else {
 #pragma unroll
       for (int c = 0; c < 3; ++c)
