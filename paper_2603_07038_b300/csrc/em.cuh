@@ -361,7 +361,7 @@ __device__ __forceinline__ void em_abort(uint64_t *bars, int k, int nz, int *err
 // all handled here.
 template <typename R, typename I, int TY, bool CPL>
 __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
-                                               EmStage<R, 32, TY> *stg, R (*sHxz)[TY][32], R (*sQy)[32],
+                                               EmStage<R, 32, TY> *stg, R (*sHxz)[2][TY][32], R (*sQy)[TY][32],
                                                uint64_t *bars, int *s_abort, int xs, int xe, int by) {
   constexpr int TX = 32;
   const Geo<R> &g = A.g;
@@ -497,25 +497,9 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
       issue(k + kEmAhead);
     }
     em_wait_next(bars, k, nz, s_abort);
-    __syncthreads();
-    if (*s_abort) {  // a copy did not arrive in time: drain what is in flight (bounded), flag, leave
-      if constexpr (sizeof(R) == 4) cp_async_wait<0>();
-      if (leader) em_abort(bars, k, nz, A.err);
-      return;
-    }
     prefetch_h(k + 1);
+    const int par = k & 1;  // parity of the double-buffered exchange arrays
     const I id = id0 + (I)k * plane;
-    // Joule energy of node (i, j, k-1): its y-edge share from j-1 is now visible
-    if (accum && own && k > 0) {
-      const R s = add_(q_pend, sQy[ty - 1][tx]);
-      if (A.fold) {
-        A.Q[id - plane] += (double)s;
-        A.Qs[id - plane] = R(0);
-      } else {
-        A.Qs[id - plane] = s;
-      }
-    }
-    if (CPL && own && k > 0) A.Pout[id - plane] = mul_(add_(e_pend, sQy[ty - 1][tx]), A.inv_dt);
     const EmStage<R, TX, TY> &S0 = stg[k & (kEmStages - 1)];
     const EmStage<R, TX, TY> &S1 = stg[(k + 1) & (kEmStages - 1)];
     R hz0, ihz, idz, hzm;
@@ -595,8 +579,8 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
     if (hz_on)  // Hz: dEy/dx - dEx/dy, voxels (i, j, k-1..k)
       Hz = h_update(hz_o, hdz, hzm, u11_b, hz0, u11,
                     curl_psi(A, s_cp, 1, 0, pHz1, 1, pHz2, dif_(ey_ip, ey, ihx), dif_(ex_jp, ex, ihy), own));
-    sHxz[0][ty][tx] = Hx;
-    sHxz[1][ty][tx] = Hz;
+    sHxz[par][0][ty][tx] = Hx;
+    sHxz[par][1][ty][tx] = Hz;
     const R hy_l = __shfl_up_sync(0xffffffffu, Hy, 1);  // H of node i-1 (same warp)
     const R hz_l = __shfl_up_sync(0xffffffffu, Hz, 1);
     // the E side's CPML states, in flight across the barrier
@@ -605,7 +589,26 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
     const Psi<R> pEx1 = psi_node(A, 1, 0, 1, ex_on ? syE : -1, i, j, k), pEx2 = psi_node(A, 2, 0, 0, ex_on ? szE : -1, i, j, k);
     const Psi<R> pEy1 = psi_node(A, 2, 0, 1, ey_on ? szE : -1, i, j, k), pEy2 = psi_node(A, 0, 0, 0, ey_on ? sxE : -1, i, j, k);
     const Psi<R> pEz1 = psi_node(A, 0, 0, 1, ez_on ? sxE : -1, i, j, k), pEz2 = psi_node(A, 1, 0, 0, ez_on ? syE : -1, i, j, k);
+    // the one barrier of the plane: H of this plane and the y-edge Joule
+    // shares of the previous one are visible; every thread is past its reads
+    // of plane k-1's stage
     __syncthreads();
+    if (*s_abort) {  // a copy did not arrive in time: drain what is in flight (bounded), flag, leave
+      if constexpr (sizeof(R) == 4) cp_async_wait<0>();
+      if (leader) em_abort(bars, k, nz, A.err);
+      return;
+    }
+    // Joule energy of node (i, j, k-1): its y-edge share from j-1 is now visible
+    if (accum && own && k > 0) {
+      const R s = add_(q_pend, sQy[par ^ 1][ty - 1][tx]);
+      if (A.fold) {
+        A.Q[id - plane] += (double)s;
+        A.Qs[id - plane] = R(0);
+      } else {
+        A.Qs[id - plane] = s;
+      }
+    }
+    if (CPL && own && k > 0) A.Pout[id - plane] = mul_(add_(e_pend, sQy[par ^ 1][ty - 1][tx]), A.inv_dt);
 
     // ---- source current on this node's edges (three scalars selected by
     // axis: a dynamically indexed array would live in local memory)
@@ -628,7 +631,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
     const R pye_a = fma_(hxm, e10, mul_(hx0, e11)), pys_a = fma_(hxm, s10, mul_(hx0, s11));
     R exn = ex, eyn = ey, ezn = ez, qx = 0, qy = 0, qz = 0;
     if (ex_on) {  // Ex: dHz/dy - dHy/dz, voxels (i, j-1..j, k-1..k)
-      const R curl = curl_psi(A, s_cp, 0, 1, pEx1, 2, pEx2, dif_(Hz, sHxz[1][ty - 1][tx], idy), dif_(Hy, hy_km1, idz),
+      const R curl = curl_psi(A, s_cp, 0, 1, pEx1, 2, pEx2, dif_(Hz, sHxz[par][1][ty - 1][tx], idy), dif_(Hy, hy_km1, idz),
                               own);
       R Ss = fma_(hzm, pxs_b, mul_(hz0, pxs_a));
       if (CPL) {
@@ -651,7 +654,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
                            lqy, &qy);
     }
     if (ez_on) {  // Ez: dHy/dx - dHx/dy, voxels (i-1..i, j-1..j, k)
-      const R curl = curl_psi(A, s_cp, 0, 0, pEz1, 1, pEz2, dif_(Hy, hy_l, idx), dif_(Hx, sHxz[0][ty - 1][tx], idy),
+      const R curl = curl_psi(A, s_cp, 0, 0, pEz1, 1, pEz2, dif_(Hy, hy_l, idx), dif_(Hx, sHxz[par][0][ty - 1][tx], idy),
                               own);
       const R Se = fma_(hym, fma_(hxm, e00, mul_(hx0, e01)), mul_(hy0, fma_(hxm, e10, mul_(hx0, e11))));
       R Ss = fma_(hym, fma_(hxm, s00, mul_(hx0, s01)), mul_(hy0, fma_(hxm, s10, mul_(hx0, s11))));
@@ -663,7 +666,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
       ezn = e_update<R, R>(ez, mul_(dtWx_y, add_(hxm, hx0)), sub_(curl, Jz), Se, Ss, mul_(R(0.25), hz0), &qz);
     }
     const R qx_l = __shfl_up_sync(0xffffffffu, qx, 1);  // x-edge share from node i-1
-    sQy[ty][tx] = qy;
+    sQy[par][ty][tx] = qy;
 
     if (own) {
       A.Hn[0][id] = Hx;
@@ -692,7 +695,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
   __syncthreads();
   if (accum && own) {  // Joule energy of the top plane k = nz
     const I id = id0 + (I)nz * plane;
-    const R s = add_(q_pend, sQy[ty - 1][tx]);
+    const R s = add_(q_pend, sQy[nz & 1][ty - 1][tx]);
     if (A.fold) {
       A.Q[id] += (double)s;
       A.Qs[id] = R(0);
@@ -700,7 +703,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
       A.Qs[id] = s;
     }
   }
-  if (CPL && own) A.Pout[id0 + (I)nz * plane] = mul_(add_(e_pend, sQy[ty - 1][tx]), A.inv_dt);
+  if (CPL && own) A.Pout[id0 + (I)nz * plane] = mul_(add_(e_pend, sQy[nz & 1][ty - 1][tx]), A.inv_dt);
 }
 
 // ---- interior tile pairs: two nodes per thread. The pair tile starting at
@@ -712,8 +715,8 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
 // per plane for the whole CTA.
 template <typename R, typename I, int TY, bool CPL>
 __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
-                                             EmStage<R, kEm2Nodes, TY> *stg, typename Pair2<R>::T (*sHxz)[TY][32],
-                                             typename Pair2<R>::T (*sQy)[32], uint64_t *bars, int *s_abort, int xs,
+                                             EmStage<R, kEm2Nodes, TY> *stg, typename Pair2<R>::T (*sHxz)[2][TY][32],
+                                             typename Pair2<R>::T (*sQy)[TY][32], uint64_t *bars, int *s_abort, int xs,
                                              int by) {
   using R2 = typename Pair2<R>::T;
   constexpr int BX = em2_box_x(), BV = em2_vox_box_x();
@@ -792,26 +795,8 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
       issue(k + kEmAhead);
     }
     em_wait_next(bars, k, nz, s_abort);
-    __syncthreads();
-    if (*s_abort) {
-      if (leader) em_abort(bars, k, nz, A.err);
-      return;
-    }
+    const int par = k & 1;  // parity of the double-buffered exchange arrays
     const I id = id0 + (I)k * plane;
-    if (accum && own && k > 0) {
-      const R2 s = add_(q_pend, sQy[ty - 1][tx]);
-      if (A.fold) {
-        double2 *qp = reinterpret_cast<double2 *>(A.Q + (id - plane));
-        double2 qv = *qp;
-        qv.x += (double)s.x;
-        qv.y += (double)s.y;
-        *qp = qv;
-        stv_(A.Qs + (id - plane), z2);
-      } else {
-        stv_(A.Qs + (id - plane), s);
-      }
-    }
-    if (CPL && own && k > 0) stv_(A.Pout + (id - plane), mul_(add_(e_pend, sQy[ty - 1][tx]), bc_<R2>(A.inv_dt)));
     const EmStage<R, kEm2Nodes, TY> &S0 = stg[k & (kEmStages - 1)];
     const EmStage<R, kEm2Nodes, TY> &S1 = stg[(k + 1) & (kEmStages - 1)];
     R hz0s, ihzs, idzs, hzms;
@@ -882,11 +867,30 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
       Hy = h_update(hy_o, hdy, hym, u01, hy0, u11, szH >= 0 ? sub_(chi_z(1, 1, pHy, f1), f2) : sub_(f1, f2));
     }
     const R2 Hz = h_update(hz_o, hdz, hzm, u11_b, hz0, u11, sub_(dif_(ey_ip, ey, ihx), dif_(ex_jp, ex, ihy)));
-    sHxz[0][ty][tx] = Hx;
-    sHxz[1][ty][tx] = Hz;
+    sHxz[par][0][ty][tx] = Hx;
+    sHxz[par][1][ty][tx] = Hz;
     const R2 hy_l = {__shfl_up_sync(0xffffffffu, Hy.y, 1), Hy.x};  // H of nodes ia-1, ia
     const R2 hz_l = {__shfl_up_sync(0xffffffffu, Hz.y, 1), Hz.x};
+    // the one barrier of the plane (see the border tiles)
     __syncthreads();
+    if (*s_abort) {
+      if (leader) em_abort(bars, k, nz, A.err);
+      return;
+    }
+    if (accum && own && k > 0) {
+      const R2 s = add_(q_pend, sQy[par ^ 1][ty - 1][tx]);
+      if (A.fold) {
+        double2 *qp = reinterpret_cast<double2 *>(A.Q + (id - plane));
+        double2 qv = *qp;
+        qv.x += (double)s.x;
+        qv.y += (double)s.y;
+        *qp = qv;
+        stv_(A.Qs + (id - plane), z2);
+      } else {
+        stv_(A.Qs + (id - plane), s);
+      }
+    }
+    if (CPL && own && k > 0) stv_(A.Pout + (id - plane), mul_(add_(e_pend, sQy[par ^ 1][ty - 1][tx]), bc_<R2>(A.inv_dt)));
 
     // ---- source currents on the pair's edges
     R2 Jx = z2, Jy = z2, Jz = z2;
@@ -912,7 +916,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
     const R2 pye_a = fma_(hxm, e10, mul_(hx0, e11)), pys_a = fma_(hxm, s10, mul_(hx0, s11));
     R2 exn = ex, eyn = ey, ezn = ez, qx = z2, qy = z2, qz = z2;
     if (ty > 0 && !fix_z) {  // Ex (owners and the halo lane, whose x-edge share lane 1 needs)
-      const R2 d1 = dif_(Hz, sHxz[1][ty - 1][tx], idy), d2 = dif_(Hy, hy_km1, idz);
+      const R2 d1 = dif_(Hz, sHxz[par][1][ty - 1][tx], idy), d2 = dif_(Hy, hy_km1, idz);
       const R2 curl = szE >= 0 ? sub_(d1, chi_z(0, 0, psi_z(0, 0, szE), d2)) : sub_(d1, d2);
       R2 Ss = fma_(hzm, pxs_b, mul_(hz0, pxs_a));
       if (CPL) {
@@ -936,7 +940,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
                             lqy, &qy);
     }
     if (ty > 0 && kz) {  // Ez
-      const R2 curl = sub_(dif_(Hy, hy_l, idx), dif_(Hx, sHxz[0][ty - 1][tx], idy));
+      const R2 curl = sub_(dif_(Hy, hy_l, idx), dif_(Hx, sHxz[par][0][ty - 1][tx], idy));
       const R2 Se = fma_(hym, fma_(hxm, e00, mul_(hx0, e01)), mul_(hy0, fma_(hxm, e10, mul_(hx0, e11))));
       R2 Ss = fma_(hym, fma_(hxm, s00, mul_(hx0, s01)), mul_(hy0, fma_(hxm, s10, mul_(hx0, s11))));
       if (CPL) {
@@ -948,7 +952,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
                             &qz);
     }
     const R2 qx_l = {__shfl_up_sync(0xffffffffu, qx.y, 1), qx.x};  // x-edge shares from nodes ia-1, ia
-    sQy[ty][tx] = qy;
+    sQy[par][ty][tx] = qy;
 
     if (own) {
       stv_(A.Hn[0] + id, Hx);
@@ -975,7 +979,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
   __syncthreads();
   if (accum && own) {  // Joule energy of the top plane k = nz
     const I id = id0 + (I)nz * plane;
-    const R2 s = add_(q_pend, sQy[ty - 1][tx]);
+    const R2 s = add_(q_pend, sQy[nz & 1][ty - 1][tx]);
     if (A.fold) {
       double2 *qp = reinterpret_cast<double2 *>(A.Q + id);
       double2 qv = *qp;
@@ -987,7 +991,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
       stv_(A.Qs + id, s);
     }
   }
-  if (CPL && own) stv_(A.Pout + (id0 + (I)nz * plane), mul_(add_(e_pend, sQy[ty - 1][tx]), bc_<R2>(A.inv_dt)));
+  if (CPL && own) stv_(A.Pout + (id0 + (I)nz * plane), mul_(add_(e_pend, sQy[nz & 1][ty - 1][tx]), bc_<R2>(A.inv_dt)));
 }
 
 // Resident CTAs per SM the kernel is compiled for: FP32 8-row tiles at
@@ -1008,8 +1012,9 @@ __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
   R *s_cp = reinterpret_cast<R *>(smem);
   R *s_mt = s_cp + kCpmlTable;
   unsigned char *stg = smem + em_stage_offset<R>(A.g.nmat);
-  __shared__ R2 sHxz[2][TY][TX];  // Hx, Hz of the plane, read by the +y neighbour
-  __shared__ R2 sQy[TY][TX];      // Joule share of the y-edge, read by the +y neighbour one plane later
+  // double-buffered by plane parity, so that a plane needs one barrier
+  __shared__ R2 sHxz[2][2][TY][TX];  // Hx, Hz of the plane, read by the +y neighbour
+  __shared__ R2 sQy[2][TY][TX];      // Joule share of the y-edge, read by the +y neighbour one plane later
   __shared__ uint64_t s_bar[kEmStages];  // one transaction barrier per stage
   __shared__ int s_abort;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -1058,7 +1063,8 @@ __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
       by += A.iby1;
     }
     em_tile_border<R, I, TY, CPL>(A, s_cp, s_mt, reinterpret_cast<EmStage<R, TX, TY> *>(stg),
-                                  reinterpret_cast<R(*)[TY][TX]>(&sHxz[0][0][0]), reinterpret_cast<R(*)[TX]>(&sQy[0][0]),
+                                  reinterpret_cast<R(*)[2][TY][TX]>(&sHxz[0][0][0][0]),
+                                  reinterpret_cast<R(*)[TY][TX]>(&sQy[0][0][0]),
                                   s_bar, &s_abort, xs, xe, by);
   } else {
     b -= A.n_border;
