@@ -303,8 +303,8 @@ static cudaError_t set_smem_limits() {
                             (const void *)em_step_kernel<R, long long, kEmTX, kEmTY, true>};
   for (const void *k : kernels)
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, em)) != cudaSuccess) return e;
-  const int mvt = (int)(mv_stage_offset<R, kMvTX, kMvTY>(kMaxMat) + kMvStages * sizeof(MvStage<R, kMvTX, kMvTY>) + 128);
-  if ((e = cudaFuncSetAttribute(hex8_matvec_tma_kernel<R, kMvTX, kMvTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const int mvt = (int)(mv_stage_offset<R, kMvTY>(kMaxMat) + kMvStages * sizeof(MvStage<R, kMvTY>) + 128);
+  if ((e = cudaFuncSetAttribute(hex8_matvec_tma_kernel<R, kMvTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 mvt)) != cudaSuccess)
     return e;
   const int th = (int)(th_stage_offset<R>(kMaxMat) + kThStages * sizeof(ThStage<R>) + 128);
@@ -1091,15 +1091,15 @@ static cosim_status mech_alloc(cosim_ctx *c) {
   ALLOC(c, c->cg, sizeof(CgScalars));
   cosim_status st;
   for (int a = 0; a < 3; ++a)
-    if ((st = encode_node_map(c, &c->mvU[a], c->Pv[a], kMvTY + 1, kMvTX + 4)) != COSIM_OK) return st;
+    if ((st = encode_node_map(c, &c->mvU[a], c->Pv[a], kMvTY + 1, kMvElems + 4)) != COSIM_OK) return st;
   {
     const cuuint64_t dims[3] = {(cuuint64_t)c->nx + 1, (cuuint64_t)c->ny + 1, (cuuint64_t)c->nz + 1};
     const cuuint64_t strides[2] = {(cuuint64_t)c->px, (cuuint64_t)c->plane};
-    const cuuint32_t box[3] = {(cuuint32_t)kMvTX + 16, (cuuint32_t)kMvTY + 1, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)kMvElems + 16, (cuuint32_t)kMvTY + 1, 1};
     if ((st = encode_map(c, &c->mvM, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, c->mask, dims, strides, box)) != COSIM_OK)
       return st;
   }
-  if ((st = encode_voxel_map(c, &c->mvV, kMvTY)) != COSIM_OK) return st;
+  if ((st = encode_voxel_map(c, &c->mvV, kMvTY, kMvElems + 16)) != COSIM_OK) return st;
   c->mech_ready = true;
   return COSIM_OK;
 }
@@ -1149,9 +1149,9 @@ static cosim_status matvec_g(cosim_ctx *c, const Geo<R> &g, void *const u[3], vo
     T.tmV = c->mvV;
     T.zt = (const R *)c->zt;
     T.err = c->dev_err;
-    const size_t smem = mv_stage_offset<R, kMvTX, kMvTY>((int)c->mats.size()) +
-                        kMvStages * sizeof(MvStage<R, kMvTX, kMvTY>) + 128;
-    hex8_matvec_tma_kernel<R, kMvTX, kMvTY><<<grd, blk, smem, c->stream>>>(T); ++c->launches;
+    const size_t smem = mv_stage_offset<R, kMvTY>((int)c->mats.size()) + kMvStages * sizeof(MvStage<R, kMvTY>) + 128;
+    const dim3 grd2((c->nx + 1 + kMvElems - 2) / (kMvElems - 1), (c->ny + 1 + kMvTY - 2) / (kMvTY - 1));
+    hex8_matvec_tma_kernel<R, kMvTY><<<grd2, blk, smem, c->stream>>>(T); ++c->launches;
   } else {
     const size_t smem =
         ((size_t)c->mats.size() * M_COLS + 2 * 3 * (kMvTY + 1) * (kMvTX + 1) + 24 * kMvTY * kMvTX) * sizeof(R);
@@ -1166,8 +1166,9 @@ static cosim_status matvec_t(cosim_ctx *c, void *const u[3], void *const y[3], d
   return matvec_g<R>(c, make_geo<R>(c), u, y, partial);
 }
 
+// CTAs of the TMA matvec (the one the PCG uses: its p.Kp partial sums)
 static int mv_blocks(const cosim_ctx *c) {
-  return ((c->nx + 1 + kMvTX - 2) / (kMvTX - 1)) * ((c->ny + 1 + kMvTY - 2) / (kMvTY - 1));
+  return ((c->nx + 1 + kMvElems - 2) / (kMvElems - 1)) * ((c->ny + 1 + kMvTY - 2) / (kMvTY - 1));
 }
 
 // Jacobi-PCG on K U = F in the context precision, U from zero, with the

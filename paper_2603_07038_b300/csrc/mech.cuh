@@ -18,121 +18,133 @@
 
 namespace cosim {
 
+// The element arithmetic is written once for one element (V = R) or two
+// x-adjacent elements (V = the pair type), with the element-wise helpers of
+// common.cuh: every operation rounds once and the pair forms act element by
+// element, so both matvec kernels give the same bits per element.
+
 // q[m] = sum_a P_m(s_a) v[a]; a = ax + 2 ay + 4 az, m bit d set <=> factor s_d
-template <typename R>
-__device__ __forceinline__ void modal_fwd(R v[8]) {
+template <typename V>
+__device__ __forceinline__ void modal_fwd(V v[8]) {
 #pragma unroll
   for (int b = 1; b < 8; b <<= 1)
 #pragma unroll
     for (int a = 0; a < 8; ++a)
       if (!(a & b)) {
-        const R lo = v[a], hi = v[a | b];
-        v[a] = hi + lo;
-        v[a | b] = hi - lo;
+        const V lo = v[a], hi = v[a | b];
+        v[a] = add_(hi, lo);
+        v[a | b] = sub_(hi, lo);
       }
 }
 
 // r[a] = sum_m P_m(s_a) F[m] (transpose of modal_fwd)
-template <typename R>
-__device__ __forceinline__ void modal_bwd(R v[8]) {
+template <typename V>
+__device__ __forceinline__ void modal_bwd(V v[8]) {
 #pragma unroll
   for (int b = 1; b < 8; b <<= 1)
 #pragma unroll
     for (int a = 0; a < 8; ++a)
       if (!(a & b)) {
-        const R s = v[a], d = v[a | b];
-        v[a] = s - d;
-        v[a | b] = s + d;
+        const V s = v[a], d = v[a | b];
+        v[a] = sub_(s, d);
+        v[a | b] = add_(s, d);
       }
 }
 
-// One monomial group: G (3x3 gradient coefficients), weight w = <phi^2>,
-// slot[d] = monomial receiving column d of the energy gradient (-1: none).
-template <typename R>
-__device__ __forceinline__ void group_term(const R G[3][3], R lam, R mu, R w, const R g[3], const int slot[3],
-                                           R F[3][8]) {
-  const R tr = G[0][0] + G[1][1] + G[2][2];
+// One monomial group: the nonzero gradient columns of the group (G[c][d],
+// d with slot[d] >= 0; the others are zero), weight w = <phi^2>, slot[d] =
+// monomial receiving column d of the energy gradient (-1: none).
+// S_cd = delta_cd lambda tr(G) + mu (G_cd + G_dc); F[c][slot d] += w S_cd g_d.
+template <typename V, typename R>
+__device__ __forceinline__ void group_term(const V G[3][3], V lam, V mu, R w, const V g[3], const int slot[3],
+                                           V F[3][8]) {
+  V tr = bc_<V>(R(0));
+  bool first = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (slot[d] >= 0) {
+      tr = first ? G[d][d] : add_(tr, G[d][d]);
+      first = false;
+    }
+  const V lt = mul_(lam, tr);
 #pragma unroll
   for (int c = 0; c < 3; ++c)
 #pragma unroll
     for (int d = 0; d < 3; ++d)
       if (slot[d] >= 0) {
-        const R S = (c == d ? lam * tr : R(0)) + mu * (G[c][d] + G[d][c]);
-        F[c][slot[d]] += w * S * g[d];
+        const V sym = slot[c] >= 0 ? add_(G[c][d], G[d][c]) : G[c][d];
+        const V S = c == d ? fma_(mu, sym, lt) : mul_(mu, sym);
+        F[c][slot[d]] = fma_(mul_(bc_<V>(w), S), g[d], F[c][slot[d]]);
       }
 }
 
-// u[c][a] (nodal displacement of one element) -> K_e u_e in place; ih* are
-// the element's inverse sizes (2 ih = 2/h exactly: scaling by two is exact).
-template <typename R>
-__device__ __forceinline__ void hex8_apply(R u[3][8], R lam, R mu, R hx, R hy, R hz, R ihx, R ihy, R ihz) {
-  const R g[3] = {R(2) * ihx, R(2) * ihy, R(2) * ihz};
-  const R g8[3] = {g[0] * R(0.125), g[1] * R(0.125), g[2] * R(0.125)};
+// u[c][a] (nodal displacement of one element, or of an element pair) ->
+// K_e u_e in place; ih* are the inverse sizes (2 ih = 2/h exactly: scaling by
+// two is exact).
+template <typename V, typename R>
+__device__ __forceinline__ void hex8_apply(V u[3][8], V lam, V mu, V hx, V hy, V hz, V ihx, V ihy, V ihz) {
+  const V g[3] = {mul_(bc_<V>(R(2)), ihx), mul_(bc_<V>(R(2)), ihy), mul_(bc_<V>(R(2)), ihz)};
+  const V g8[3] = {mul_(g[0], bc_<V>(R(0.125))), mul_(g[1], bc_<V>(R(0.125))), mul_(g[2], bc_<V>(R(0.125)))};
 #pragma unroll
   for (int c = 0; c < 3; ++c) modal_fwd(u[c]);
-  R F[3][8];
+  V F[3][8];
 #pragma unroll
   for (int c = 0; c < 3; ++c)
 #pragma unroll
-    for (int m = 0; m < 8; ++m) F[c][m] = 0;
+    for (int m = 0; m < 8; ++m) F[c][m] = bc_<V>(R(0));
   const R third = R(1) / R(3), ninth = R(1) / R(9);
-  R G[3][3];
+  V G[3][3];
   {  // constant gradient: columns from the linear monomials xi, eta, zeta
     const int slot[3] = {1, 2, 4};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      G[c][0] = g8[0] * u[c][1];
-      G[c][1] = g8[1] * u[c][2];
-      G[c][2] = g8[2] * u[c][4];
+      G[c][0] = mul_(g8[0], u[c][1]);
+      G[c][1] = mul_(g8[1], u[c][2]);
+      G[c][2] = mul_(g8[2], u[c][4]);
     }
-    group_term(G, lam, mu, R(1), g, slot, F);
+    group_term<V, R>(G, lam, mu, R(1), g, slot, F);
   }
   {  // terms linear in xi: d/deta of (xi eta), d/dzeta of (zeta xi)
     const int slot[3] = {-1, 3, 5};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      G[c][0] = 0;
-      G[c][1] = g8[1] * u[c][3];
-      G[c][2] = g8[2] * u[c][5];
+      G[c][1] = mul_(g8[1], u[c][3]);
+      G[c][2] = mul_(g8[2], u[c][5]);
     }
-    group_term(G, lam, mu, third, g, slot, F);
+    group_term<V, R>(G, lam, mu, third, g, slot, F);
   }
   {  // linear in eta: d/dxi of (xi eta), d/dzeta of (eta zeta)
     const int slot[3] = {3, -1, 6};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      G[c][0] = g8[0] * u[c][3];
-      G[c][1] = 0;
-      G[c][2] = g8[2] * u[c][6];
+      G[c][0] = mul_(g8[0], u[c][3]);
+      G[c][2] = mul_(g8[2], u[c][6]);
     }
-    group_term(G, lam, mu, third, g, slot, F);
+    group_term<V, R>(G, lam, mu, third, g, slot, F);
   }
   {  // linear in zeta: d/dxi of (zeta xi), d/deta of (eta zeta)
     const int slot[3] = {5, 6, -1};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      G[c][0] = g8[0] * u[c][5];
-      G[c][1] = g8[1] * u[c][6];
-      G[c][2] = 0;
+      G[c][0] = mul_(g8[0], u[c][5]);
+      G[c][1] = mul_(g8[1], u[c][6]);
     }
-    group_term(G, lam, mu, third, g, slot, F);
+    group_term<V, R>(G, lam, mu, third, g, slot, F);
   }
 #pragma unroll
   for (int d = 0; d < 3; ++d) {  // bilinear monomials from (xi eta zeta)
     int slot[3] = {-1, -1, -1};
     slot[d] = 7;
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int e = 0; e < 3; ++e) G[c][e] = (e == d) ? g8[d] * u[c][7] : R(0);
-    group_term(G, lam, mu, ninth, g, slot, F);
+    for (int c = 0; c < 3; ++c) G[c][d] = mul_(g8[d], u[c][7]);
+    group_term<V, R>(G, lam, mu, ninth, g, slot, F);
   }
-  const R s = R(0.125) * hx * hy * hz;
+  const V s = mul_(mul_(mul_(bc_<V>(R(0.125)), hx), hy), hz);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     modal_bwd(F[c]);
 #pragma unroll
-    for (int a = 0; a < 8; ++a) u[c][a] = s * F[c][a];
+    for (int a = 0; a < 8; ++a) u[c][a] = mul_(s, F[c][a]);
   }
 }
 
@@ -206,7 +218,7 @@ __global__ void __launch_bounds__(TX *TY) hex8_matvec_kernel(const MvArgs<R> A) 
 #pragma unroll
         for (int a = 0; a < 8; ++a)
           r[c][a] = su_at((k + (a >> 2)) & 1, c, ty + ((a >> 1) & 1), tx + (a & 1));
-      hex8_apply(r, s_mt[m * M_COLS + M_LAM], s_mt[m * M_COLS + M_MU], hx, hy, g.h[2][k], ihx, ihy, g.ih[2][k]);
+      hex8_apply<R, R>(r, s_mt[m * M_COLS + M_LAM], s_mt[m * M_COLS + M_MU], hx, hy, g.h[2][k], ihx, ihy, g.ih[2][k]);
     } else {
 #pragma unroll
       for (int c = 0; c < 3; ++c)
@@ -256,24 +268,29 @@ __global__ void __launch_bounds__(TX *TY) hex8_matvec_kernel(const MvArgs<R> A) 
   }
 }
 
-// ---- the same matvec with TMA-staged planes: per node plane one thread
-// copies the three components of u (36 x (TY+1) node boxes from x rounded
-// down to a multiple of 4), the constraint bits of those nodes (48-byte rows
-// from x rounded down to 16), the voxel IDs of the element layer and the
-// plane's z record into four mbarrier-tracked shared-memory stages while the
-// threads work on earlier planes. Elements, gather and arithmetic are those
-// of hex8_matvec_kernel, term for term: the results are identical.
+// ---- the same matvec with TMA-staged planes and two elements per thread.
+// A CTA of 32 x TY threads covers 64 x TY elements (thread tx: elements
+// X0 + 2 tx and X0 + 2 tx + 1 of row Y0 + ty, X0 = 63 bx - 1, Y0 = (TY-1) by
+// - 1) and owns the 63 x (TY-1) node columns inside them. Per node plane one
+// thread copies the three components of u (68 x (TY+1) node boxes from x
+// rounded down to a multiple of 4), the constraint bits of those nodes and
+// the voxel IDs of the element layer (80-byte rows from x rounded down to 16)
+// and the plane's z record into four mbarrier-tracked shared-memory stages
+// while the threads work on earlier planes. The element arithmetic is the
+// pair form of hex8_apply (packed FP32), the node sums those of
+// hex8_matvec_kernel, term for term: the results are identical.
 constexpr int kMvStages = 4, kMvAhead = 3;
-template <typename R, int TX, int TY>
+constexpr int kMvElems = 64;  // elements per warp row
+template <typename R, int TY>
 struct MvStage {
-  EmBox<R, TY + 1, TX + 4> U[3];         // nodes X0 .. X0+TX, Y0 .. Y0+TY (from x rounded to 4)
-  EmBox<uint8_t, TY + 1, TX + 16> M;     // constraint bits of the same nodes (from x rounded to 16)
-  EmBox<uint8_t, TY, TX + 16> V;         // voxel IDs of elements X0 .. X0+TX-1, Y0 .. Y0+TY-1
-  EmBox<R, 1, 4> Z;                      // hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
+  EmBox<R, TY + 1, kMvElems + 4> U[3];         // nodes X0 .. X0+64, Y0 .. Y0+TY (from x rounded to 4)
+  EmBox<uint8_t, TY + 1, kMvElems + 16> M;     // constraint bits of the same nodes (from x rounded to 16)
+  EmBox<uint8_t, TY, kMvElems + 16> V;         // voxel IDs of elements X0 .. X0+63, Y0 .. Y0+TY-1
+  EmBox<R, 1, 4> Z;                            // hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
 };
-template <typename R, int TX, int TY>
+template <typename R, int TY>
 __host__ __device__ constexpr size_t mv_stage_offset(int nmat) {
-  return (((size_t)(nmat + 1) * M_COLS + 24 * TY * TX) * sizeof(R) + 127) & ~size_t(127);
+  return (((size_t)(nmat + 1) * M_COLS + 24 * TY * kMvElems) * sizeof(R) + 127) & ~size_t(127);
 }
 
 template <typename R>
@@ -284,21 +301,24 @@ struct MvTmaArgs {
   int *err;
 };
 
-template <typename R, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) hex8_matvec_tma_kernel(const __grid_constant__ MvTmaArgs<R> TA) {
+template <typename R, int TY>
+__global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
+    hex8_matvec_tma_kernel(const __grid_constant__ MvTmaArgs<R> TA) {
+  using R2 = typename Pair2<R>::T;
+  constexpr int EX = kMvElems;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const MvArgs<R> &A = TA.a;
   const Geo<R> &g = A.g;
   R *s_mt = reinterpret_cast<R *>(smem);
-  R *sr = s_mt + (g.nmat + 1) * M_COLS;  // [24][TY][TX]
-  MvStage<R, TX, TY> *stg = reinterpret_cast<MvStage<R, TX, TY> *>(smem + mv_stage_offset<R, TX, TY>(g.nmat));
+  R *sr = s_mt + (g.nmat + 1) * M_COLS;  // [24][TY][EX]
+  MvStage<R, TY> *stg = reinterpret_cast<MvStage<R, TY> *>(smem + mv_stage_offset<R, TY>(g.nmat));
   __shared__ uint64_t bars[kMvStages];
   __shared__ int s_abort;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const bool leader = tid == 0;
   if (leader) {
-    bool ok = (smem_u32(stg) & 127u) == 0 && (sizeof(MvStage<R, TX, TY>) & 127u) == 0 &&
+    bool ok = (smem_u32(stg) & 127u) == 0 && (sizeof(MvStage<R, TY>) & 127u) == 0 &&
               ((size_t)&TA.tmU[0] & 63u) == 0 && ((size_t)&TA.tmM & 63u) == 0 && ((size_t)&TA.tmV & 63u) == 0;
     s_abort = ok ? 0 : 1;
     if (!ok) atomicExch(TA.err, 2);
@@ -309,22 +329,27 @@ __global__ void __launch_bounds__(TX *TY) hex8_matvec_tma_kernel(const __grid_co
   __syncthreads();
   if (s_abort) return;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const int X0 = blockIdx.x * (TX - 1) - 1, Y0 = blockIdx.y * (TY - 1) - 1;
+  const int X0 = blockIdx.x * (EX - 1) - 1, Y0 = blockIdx.y * (TY - 1) - 1;
   const int xr = X0 & 3, xu0 = X0 - xr;      // u boxes
   const int xmr = X0 & 15, xm0 = X0 - xmr;   // mask and voxel boxes
-  const int ex = X0 + tx, ey = Y0 + ty;
-  const bool elem_xy = ex >= 0 && ex < nx && ey >= 0 && ey < ny;
-  const int X = ex + 1, Y = ey + 1;
-  const bool own = tx < TX - 1 && ty < TY - 1 && X <= nx && Y <= ny;
-  const R hx = elem_xy ? g.h[0][ex] : R(1), hy = elem_xy ? g.h[1][ey] : R(1);
-  const R ihx = elem_xy ? g.ih[0][ex] : R(1), ihy = elem_xy ? g.ih[1][ey] : R(1);
+  const int ea = X0 + 2 * tx, ey = Y0 + ty;  // elements ea (.x) and ea + 1 (.y)
+  const bool ey_ok = ey >= 0 && ey < ny;
+  const bool va = ey_ok && ea >= 0 && ea < nx, vb = ey_ok && ea + 1 >= 0 && ea + 1 < nx;
+  // owned nodes (ea + 1, ey + 1) and (ea + 2, ey + 1); the last lane's second
+  // node belongs to the next tile
+  const int XA = ea + 1, Y = ey + 1;
+  const bool rowown = ty < TY - 1 && Y <= ny;
+  const bool oa = rowown && XA <= nx, ob = rowown && tx < 31 && XA + 1 <= nx;
+  const R2 hx = {va ? g.h[0][ea] : R(1), vb ? g.h[0][ea + 1] : R(1)};
+  const R2 ihx = {va ? g.ih[0][ea] : R(1), vb ? g.ih[0][ea + 1] : R(1)};
+  const R2 hy = bc_<R2>(ey_ok ? g.h[1][ey] : R(1)), ihy = bc_<R2>(ey_ok ? g.ih[1][ey] : R(1));
   const unsigned fixed_bytes =
-      (unsigned)(3 * (TY + 1) * (TX + 4) * (int)sizeof(R) + (TY + 1) * (TX + 16) + 4 * (int)sizeof(R));
-  const unsigned vox_bytes = (unsigned)(TY * (TX + 16));
+      (unsigned)(3 * (TY + 1) * (EX + 4) * (int)sizeof(R) + (TY + 1) * (EX + 16) + 4 * (int)sizeof(R));
+  const unsigned vox_bytes = (unsigned)(TY * (EX + 16));
   auto issue = [&](int k) {
     if (k > nz) return;
     const int s = k % kMvStages;
-    MvStage<R, TX, TY> &S = stg[s];
+    MvStage<R, TY> &S = stg[s];
     mbar_arrive_expect_tx(&bars[s], fixed_bytes + (k < nz ? vox_bytes : 0u));
 #pragma unroll
     for (int c = 0; c < 3; ++c) tma_load_3d(&S.U[c].v[0][0], &TA.tmU[c], xu0, Y0, k, &bars[s]);
@@ -332,17 +357,18 @@ __global__ void __launch_bounds__(TX *TY) hex8_matvec_tma_kernel(const __grid_co
     if (k < nz) tma_load_3d(&S.V.v[0][0], &TA.tmV, xm0, Y0, k, &bars[s]);
     bulk_load(&S.Z.v[0][0], TA.zt + 4 * (size_t)k, 4 * sizeof(R), &bars[s]);
   };
-  auto sr_at = [&](int slot, int qy, int qx) -> R & { return sr[(slot * TY + qy) * TX + qx]; };
+  auto sr_at = [&](int slot, int qy, int qx) -> R & { return sr[(slot * TY + qy) * EX + qx]; };
   // u at box position (qy, qx) of a stage with its constrained components zeroed
-  auto u_at = [&](const MvStage<R, TX, TY> &S, int c, int qy, int qx) -> R {
+  auto u_at = [&](const MvStage<R, TY> &S, int c, int qy, int qx) -> R {
     const uint8_t mk = S.M.v[qy][qx - xr + xmr];
     return ((mk >> c) & 1) ? R(0) : S.U[c].v[qy][qx];
   };
   if (leader)
     for (int q = 0; q < kMvAhead; ++q) issue(q);
-  R acc[3] = {0, 0, 0};
+  R2 acc[3] = {bc_<R2>(R(0)), bc_<R2>(R(0)), bc_<R2>(R(0))};
   double dot = 0.0;
-  const int cu = tx + xr;  // element corner (ex, ey) column in the u boxes
+  const int cu = 2 * tx + xr;  // element corner (ea, ey) column in the u boxes
+  const int c2 = min(2 * tx + 2, EX - 1);  // sr column of element ea + 2 (the last lane reads a valid, unused column)
   for (int k = 0; k < nz; ++k) {
     {
       bool ok = mbar_wait(&bars[k % kMvStages], (unsigned)(k / kMvStages) & 1u);
@@ -362,59 +388,85 @@ __global__ void __launch_bounds__(TX *TY) hex8_matvec_tma_kernel(const __grid_co
       fence_proxy_async_smem();
       issue(k + kMvAhead);
     }
-    const MvStage<R, TX, TY> &S0 = stg[k % kMvStages];
-    const MvStage<R, TX, TY> &S1 = stg[(k + 1) % kMvStages];
-    R r[3][8];
-    if (elem_xy) {
-      const int m = S0.V.v[ty][tx + xmr];
+    const MvStage<R, TY> &S0 = stg[k % kMvStages];
+    const MvStage<R, TY> &S1 = stg[(k + 1) % kMvStages];
+    R2 r[3][8];
+    if (va || vb) {
+      const int ma = va ? (int)S0.V.v[ty][2 * tx + xmr] : 0, mb = vb ? (int)S0.V.v[ty][2 * tx + 1 + xmr] : 0;
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
-          r[c][a] = u_at((a >> 2) ? S1 : S0, c, ty + ((a >> 1) & 1), cu + (a & 1));
-      hex8_apply(r, s_mt[m * M_COLS + M_LAM], s_mt[m * M_COLS + M_MU], hx, hy, S0.Z.v[0][0], ihx, ihy,
-                 S0.Z.v[0][1]);
+        for (int a = 0; a < 8; ++a) {
+          const MvStage<R, TY> &S = (a >> 2) ? S1 : S0;
+          const int qy = ty + ((a >> 1) & 1), qx = cu + (a & 1);
+          r[c][a] = R2{u_at(S, c, qy, qx), u_at(S, c, qy, qx + 1)};
+        }
+      hex8_apply<R2, R>(r, R2{s_mt[ma * M_COLS + M_LAM], s_mt[mb * M_COLS + M_LAM]},
+                        R2{s_mt[ma * M_COLS + M_MU], s_mt[mb * M_COLS + M_MU]}, hx, hy, bc_<R2>(S0.Z.v[0][0]), ihx,
+                        ihy, bc_<R2>(S0.Z.v[0][1]));
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int a = 0; a < 8; ++a) r[c][a] = R2{va ? r[c][a].x : R(0), vb ? r[c][a].y : R(0)};
     } else {
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int a = 0; a < 8; ++a) r[c][a] = 0;
+        for (int a = 0; a < 8; ++a) r[c][a] = bc_<R2>(R(0));
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int a = 0; a < 8; ++a) sr_at(c * 8 + a, ty, tx) = r[c][a];
+      for (int a = 0; a < 8; ++a) stv_(&sr_at(c * 8 + a, ty, 2 * tx), r[c][a]);
     __syncthreads();
-    if (own) {
-      const long long id = g.nid(X, Y, k);
-      const uint8_t mk = S0.M.v[ty + 1][cu + 1 - xr + xmr];
+    if (oa || ob) {
+      const long long id = g.nid(XA, Y, k);
       R part = 0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const R bottom = (sr_at(c * 8 + 3, ty, tx) + sr_at(c * 8 + 2, ty, tx + 1)) +
-                         (sr_at(c * 8 + 1, ty + 1, tx) + sr_at(c * 8 + 0, ty + 1, tx + 1));
-        const R top = (sr_at(c * 8 + 7, ty, tx) + sr_at(c * 8 + 6, ty, tx + 1)) +
-                      (sr_at(c * 8 + 5, ty + 1, tx) + sr_at(c * 8 + 4, ty + 1, tx + 1));
-        const R uc = S0.U[c].v[ty + 1][cu + 1];
-        const R yv = ((mk >> c) & 1) ? uc : acc[c] + bottom;
-        A.y[c][id] = yv;
-        part += yv * uc;
+        // node A (ea+1) sums elements ea, ea+1 (sr columns 2tx, 2tx+1); node B (ea+2) ea+1, ea+2
+        const R2 bottom = add_(add_(R2{sr_at(c * 8 + 3, ty, 2 * tx), sr_at(c * 8 + 3, ty, 2 * tx + 1)},
+                                    R2{sr_at(c * 8 + 2, ty, 2 * tx + 1), sr_at(c * 8 + 2, ty, c2)}),
+                               add_(R2{sr_at(c * 8 + 1, ty + 1, 2 * tx), sr_at(c * 8 + 1, ty + 1, 2 * tx + 1)},
+                                    R2{sr_at(c * 8 + 0, ty + 1, 2 * tx + 1), sr_at(c * 8 + 0, ty + 1, c2)}));
+        const R2 top = add_(add_(R2{sr_at(c * 8 + 7, ty, 2 * tx), sr_at(c * 8 + 7, ty, 2 * tx + 1)},
+                                 R2{sr_at(c * 8 + 6, ty, 2 * tx + 1), sr_at(c * 8 + 6, ty, c2)}),
+                            add_(R2{sr_at(c * 8 + 5, ty + 1, 2 * tx), sr_at(c * 8 + 5, ty + 1, 2 * tx + 1)},
+                                 R2{sr_at(c * 8 + 4, ty + 1, 2 * tx + 1), sr_at(c * 8 + 4, ty + 1, c2)}));
+        const uint8_t mka = S0.M.v[ty + 1][cu + 1 - xr + xmr], mkb = S0.M.v[ty + 1][cu + 2 - xr + xmr];
+        const R ua = S0.U[c].v[ty + 1][cu + 1], ub = S0.U[c].v[ty + 1][cu + 2];
+        const R2 sum = add_(acc[c], bottom);
+        const R ya = ((mka >> c) & 1) ? ua : sum.x, yb = ((mkb >> c) & 1) ? ub : sum.y;
+        if (oa) {
+          A.y[c][id] = ya;
+          part += ya * ua;
+        }
+        if (ob) {
+          A.y[c][id + 1] = yb;
+          part += yb * ub;
+        }
         acc[c] = top;
       }
       dot += (double)part;
     }
   }
-  if (own) {  // the top node plane: plane nz is still staged (nothing was issued after it)
-    const MvStage<R, TX, TY> &S = stg[nz % kMvStages];
-    const long long id = g.nid(X, Y, nz);
-    const uint8_t mk = S.M.v[ty + 1][cu + 1 - xr + xmr];
+  if (oa || ob) {  // the top node plane: plane nz is still staged (nothing was issued after it)
+    const MvStage<R, TY> &S = stg[nz % kMvStages];
+    const long long id = g.nid(XA, Y, nz);
     R part = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const R uc = S.U[c].v[ty + 1][cu + 1];
-      const R yv = ((mk >> c) & 1) ? uc : acc[c];
-      A.y[c][id] = yv;
-      part += yv * uc;
+      const uint8_t mka = S.M.v[ty + 1][cu + 1 - xr + xmr], mkb = S.M.v[ty + 1][cu + 2 - xr + xmr];
+      const R ua = S.U[c].v[ty + 1][cu + 1], ub = S.U[c].v[ty + 1][cu + 2];
+      const R ya = ((mka >> c) & 1) ? ua : acc[c].x, yb = ((mkb >> c) & 1) ? ub : acc[c].y;
+      if (oa) {
+        A.y[c][id] = ya;
+        part += ya * ua;
+      }
+      if (ob) {
+        A.y[c][id + 1] = yb;
+        part += yb * ub;
+      }
     }
     dot += (double)part;
   }
@@ -452,12 +504,14 @@ __global__ void __launch_bounds__(256) hex8_node_kernel(Geo<R> g, const uint8_t 
         const int m = g.cell(ei, ej, ek);
         if (m < 0) continue;
         const R h[3] = {g.h[0][ei], g.h[1][ej], g.h[2][ek]};
+        const R ih[3] = {g.ih[0][ei], g.ih[1][ej], g.ih[2][ek]};  // inverse sizes (no divisions)
         const R V = h[0] * h[1] * h[2];
         const R lam = s_mt[m * M_COLS + M_LAM], mu = s_mt[m * M_COLS + M_MU];
         if (MODE == 0) {
-          const R lap = R(1) / (h[0] * h[0]) + R(1) / (h[1] * h[1]) + R(1) / (h[2] * h[2]);
+          const R lap = ih[0] * ih[0] + ih[1] * ih[1] + ih[2] * ih[2];
 #pragma unroll
-          for (int c = 0; c < 3; ++c) acc[c] += (lam + mu) * V / (R(9) * h[c] * h[c]) + mu * V * lap / R(9);
+          for (int c = 0; c < 3; ++c)
+            acc[c] += (lam + mu) * V * (ih[c] * ih[c]) * (R(1) / R(9)) + mu * V * lap * (R(1) / R(9));
         } else {
           R t[8];
 #pragma unroll
@@ -473,7 +527,7 @@ __global__ void __launch_bounds__(256) hex8_node_kernel(Geo<R> g, const uint8_t 
             const R br = t[0] + s[d1] * t[lin[d1]] * (R(1) / R(3)) + s[d2] * t[lin[d2]] * (R(1) / R(3)) +
                          s[d1] * s[d2] * t[lin[d1] | lin[d2]] * (R(1) / R(9));
             // t holds 8x the monomial coefficients: fold 1/8 here
-            acc[c] += beta * V * (R(2) / h[c]) * s[c] * R(0.125) * R(0.125) * br;
+            acc[c] += beta * V * (R(2) * ih[c]) * s[c] * R(0.125) * R(0.125) * br;
           }
         }
       }
@@ -505,7 +559,7 @@ __global__ void __launch_bounds__(256) von_mises_kernel(Geo<R> g, const R *u0, c
   const int k = blockIdx.z;
   if (i >= g.nx || j >= g.ny) return;
   const R *u[3] = {u0, u1, u2};
-  const R h[3] = {g.h[0][i], g.h[1][j], g.h[2][k]};
+  const R qh[3] = {R(0.25) * g.ih[0][i], R(0.25) * g.ih[1][j], R(0.25) * g.ih[2][k]};  // (2/h) / 8
   R G[3][3];
   R tm = 0;
 #pragma unroll
@@ -514,9 +568,9 @@ __global__ void __launch_bounds__(256) von_mises_kernel(Geo<R> g, const R *u0, c
 #pragma unroll
     for (int a = 0; a < 8; ++a) v[a] = u[c][g.nid(i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1))];
     modal_fwd(v);
-    G[c][0] = v[1] * R(0.25) / h[0];  // (2/h) * (sum / 8)
-    G[c][1] = v[2] * R(0.25) / h[1];
-    G[c][2] = v[4] * R(0.25) / h[2];
+    G[c][0] = v[1] * qh[0];  // (2/h) * (sum / 8)
+    G[c][1] = v[2] * qh[1];
+    G[c][2] = v[4] * qh[2];
   }
 #pragma unroll
   for (int a = 0; a < 8; ++a) tm += T[g.nid(i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1))] - T_ref;
