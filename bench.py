@@ -356,9 +356,13 @@ def serving_arm(args, workers=4):
     plain = S.DesignRunner(specs, workers=1, use_graph=False, autotune=False)
     plain.run(specs[0], 0)
     rep_plain = S.serve(specs, [0.0] * len(specs), plain.run, workers=1, footprint=S.footprint_bytes)
-    same = all(abs(rep["records"][q].result["joule_J"] / rep_plain["records"][q].result["joule_J"] - 1) < 1e-5
-               and rep["records"][q].result["cg_iters"] == rep_plain["records"][q].result["cg_iters"]
-               for q in range(len(specs)))
+    # the served form runs the autotuned tile heights, the plain form the
+    # default ones: results agree to FP32 rounding (Joule energy to 1e-5, the
+    # PCG iteration count to 2 %), not bit for bit
+    def close(a, b):
+        return (abs(a["joule_J"] / b["joule_J"] - 1) < 1e-5 and abs(a["T_max"] - b["T_max"]) < 1e-6 * b["T_max"]
+                and abs(a["cg_iters"] - b["cg_iters"]) <= max(2, 0.02 * b["cg_iters"]))
+    same = all(close(rep["records"][q].result, rep_plain["records"][q].result) for q in range(len(specs)))
     cells = sum(s.cells for s in specs)
     return {"variant": "burst-length-scaled (%d EM steps per request, not the 2 ns burst), ~80%% offered load"
                        % specs[0].em_steps,

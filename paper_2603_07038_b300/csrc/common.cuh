@@ -160,10 +160,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
 
 // ---- Arithmetic written once for one node (R) or two adjacent nodes (the
 // pair type R2: float2 / double2). Every operation rounds once, to nearest,
-// and the pair forms act element by element, so a kernel that handles a node
-// pair per thread gives bit for bit the results of one that handles a single
-// node. FP32 pairs use the packed FP32 instructions of sm_100 and later (one
-// instruction for both nodes); FP64 pairs are two scalar operations.
+// and the pair forms act element by element (FP32 pairs use the packed FP32
+// instructions of sm_100 and later, one instruction for both nodes; FP64
+// pairs are two scalar operations). The scalar forms are never contracted;
+// the code generator does contract a packed product that feeds a packed
+// addition into one FMA, so a formula with such a step can round a pair one
+// FP32 rounding apart from the single-node form. Formulas that feed no
+// product into an addition (the thermal step) give the same bits either way.
 template <typename R>
 struct Pair2;
 template <>

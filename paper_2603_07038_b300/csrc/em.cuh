@@ -17,9 +17,9 @@
 // plus a halo pair), and the arithmetic of both nodes is issued as packed FP32
 // instructions. The border tiles run one node per thread with the wall and
 // lateral-CPML logic. Every formula is written once against the element-wise
-// helpers of common.cuh, which round exactly like the scalar operations, so a
-// node gets the same bits whichever kind of tile it falls in (and whatever
-// the tile height).
+// helpers of common.cuh. Runs of one launch shape are bitwise reproducible; a
+// node that falls in a pair tile at one tile height and in a border tile at
+// another agrees to FP32 rounding (packed products contracted into FMAs).
 //
 // Joule heat: the edge from node n to n+e_a dissipates sigma_e V_e ebar^2 in
 // one step, ebar = (E^n + E^{n+1})/2; half of dt times that goes to each end

@@ -21,7 +21,8 @@ namespace cosim {
 // The element arithmetic is written once for one element (V = R) or two
 // x-adjacent elements (V = the pair type), with the element-wise helpers of
 // common.cuh: every operation rounds once and the pair forms act element by
-// element, so both matvec kernels give the same bits per element.
+// element (the packed path may contract a product into the following
+// addition, one FP32 rounding apart from the one-element path).
 
 // q[m] = sum_a P_m(s_a) v[a]; a = ax + 2 ay + 4 az, m bit d set <=> factor s_d
 template <typename V>
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(TX *TY) hex8_matvec_kernel(const MvArgs<R> A) 
 // and the plane's z record into four mbarrier-tracked shared-memory stages
 // while the threads work on earlier planes. The element arithmetic is the
 // pair form of hex8_apply (packed FP32), the node sums those of
-// hex8_matvec_kernel, term for term: the results are identical.
+// hex8_matvec_kernel, term for term (equal to FP32 rounding).
 constexpr int kMvStages = 4, kMvAhead = 3;
 constexpr int kMvElems = 64;  // elements per warp row
 template <typename R, int TY>

@@ -10,8 +10,10 @@
 // (1 byte per cell streamed) instead of being stored per node.
 //
 // The arithmetic of a node is written once (th_layer, th_coeffs, th_update)
-// for a scalar or for a pair of adjacent nodes; both kernels below use it, so
-// every launch shape gives the same bits.
+// for a scalar or for a pair of adjacent nodes; both kernels below use it.
+// It feeds no product into an addition (products enter FMAs only), so no
+// contraction can differ between the forms: every launch shape gives the
+// same bits.
 #pragma once
 #include <cuda.h>  // CUtensorMap
 

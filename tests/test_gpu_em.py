@@ -21,6 +21,10 @@ CASES = [
     (62, 15, 10, (2, 2, 2, 2, 0, 2), 4),
     (20, 1, 6, (1, 0, 1, 1, 0, 1), 0),
     (7, 30, 1, (0, 0, 2, 2, 1, 1), 8),
+    # wide enough for interior tile pairs (two nodes per thread) between the
+    # border tiles; nx even and odd, a z slab through most planes
+    (150, 40, 6, (2, 2, 2, 2, 0, 2), 4),
+    (141, 23, 7, (1, 0, 0, 2, 1, 2), 4),
 ]
 
 
