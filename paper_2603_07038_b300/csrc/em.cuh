@@ -853,8 +853,21 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
     auto psi_z = [&](int type, int slot, int s) -> Psi<R2> {
       return psi_pre<R, R2>(A, 2, type, slot, s, s >= 0 ? ((long long)s * (ny + 1) + j) * g.px + ia : 0);
     };
-    auto chi_z = [&](int type, int slot, const Psi<R2> &p, R2 v) -> R2 {
-      return psi_apply<R, R2>(A, bc_<R2>(s_cp[(2 * 2 + type) * kMaxSlab + p.s]), 2, type, slot, p, v, own);
+    // chi of the z derivative (b - a) ih for each node of the pair, in the
+    // scalar forms: the compensated update relies on every step being
+    // rounded separately, which packed code does not guarantee (a packed
+    // product feeding an addition is contracted into an FMA)
+    auto chi_z = [&](int type, int slot, const Psi<R2> &p, R2 b, R2 a, R ih) -> R2 {
+      const R omb = s_cp[(2 * 2 + type) * kMaxSlab + p.s];
+      Psi<R> px, py;
+      px.s = py.s = p.s;
+      px.q = p.q;
+      py.q = p.q + 1;
+      px.c.hi = p.c.hi.x, py.c.hi = p.c.hi.y;
+      px.c.d = p.c.d.x, py.c.d = p.c.d.y;
+      if constexpr (sizeof(R) == 4) px.c.lo = p.c.lo.x, py.c.lo = p.c.lo.y;
+      return R2{psi_apply<R, R>(A, omb, 2, type, slot, px, dif_(b.x, a.x, ih), own),
+                psi_apply<R, R>(A, omb, 2, type, slot, py, dif_(b.y, a.y, ih), own)};
     };
 
     // ---- H^{n+1/2}
@@ -862,9 +875,10 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
     if (kz) {
       const Psi<R2> pHx = psi_z(1, 0, szH), pHy = psi_z(1, 1, szH);
       const R2 d1 = dif_(ez_jp, ez, ihy), d2 = dif_(ey_up, ey, ihz);
-      Hx = h_update(hx_o, hdx, hxm, u10, hx0, u11, szH >= 0 ? sub_(d1, chi_z(1, 0, pHx, d2)) : sub_(d1, d2));
+      Hx = h_update(hx_o, hdx, hxm, u10, hx0, u11, szH >= 0 ? sub_(d1, chi_z(1, 0, pHx, ey_up, ey, ihzs)) : sub_(d1, d2));
       const R2 f1 = dif_(ex_up, ex, ihz), f2 = dif_(ez_ip, ez, ihx);
-      Hy = h_update(hy_o, hdy, hym, u01, hy0, u11, szH >= 0 ? sub_(chi_z(1, 1, pHy, f1), f2) : sub_(f1, f2));
+      Hy = h_update(hy_o, hdy, hym, u01, hy0, u11,
+                    szH >= 0 ? sub_(chi_z(1, 1, pHy, ex_up, ex, ihzs), f2) : sub_(f1, f2));
     }
     const R2 Hz = h_update(hz_o, hdz, hzm, u11_b, hz0, u11, sub_(dif_(ey_ip, ey, ihx), dif_(ex_jp, ex, ihy)));
     sHxz[par][0][ty][tx] = Hx;
@@ -917,7 +931,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
     R2 exn = ex, eyn = ey, ezn = ez, qx = z2, qy = z2, qz = z2;
     if (ty > 0 && !fix_z) {  // Ex (owners and the halo lane, whose x-edge share lane 1 needs)
       const R2 d1 = dif_(Hz, sHxz[par][1][ty - 1][tx], idy), d2 = dif_(Hy, hy_km1, idz);
-      const R2 curl = szE >= 0 ? sub_(d1, chi_z(0, 0, psi_z(0, 0, szE), d2)) : sub_(d1, d2);
+      const R2 curl = szE >= 0 ? sub_(d1, chi_z(0, 0, psi_z(0, 0, szE), Hy, hy_km1, idzs)) : sub_(d1, d2);
       R2 Ss = fma_(hzm, pxs_b, mul_(hz0, pxs_a));
       if (CPL) {
         const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_ip));
@@ -929,7 +943,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
     }
     if (!fix_z) {  // Ey (every row: the halo row's y-edge share goes to row ty+1)
       const R2 d1 = dif_(Hx, hx_km1, idz), d2 = dif_(Hz, hz_l, idx);
-      const R2 curl = szE >= 0 ? sub_(chi_z(0, 1, psi_z(0, 1, szE), d1), d2) : sub_(d1, d2);
+      const R2 curl = szE >= 0 ? sub_(chi_z(0, 1, psi_z(0, 1, szE), Hx, hx_km1, idzs), d2) : sub_(d1, d2);
       R2 Ss = fma_(hzm, pys_b, mul_(hz0, pys_a));
       if (CPL) {
         const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_jp));
