@@ -1107,22 +1107,21 @@ static cosim_status mech_alloc(cosim_ctx *c) {
 static cosim_status upload_mask(cosim_ctx *c, const cosim_stress_opts *o) {
   if (o->bc < 0 || o->bc > 2) return fail(c, COSIM_ERR_INVALID, "bad mechanical support");
   if (o->bc == COSIM_MECH_MASK && !o->node_mask) return fail(c, COSIM_ERR_INVALID, "node_mask is NULL");
-  std::vector<uint8_t> m(c->npad, 0);
-  auto at = [&](int i, int j, int k) -> uint8_t & { return m[(size_t)k * c->plane + (size_t)j * c->px + i]; };
-  if (o->bc == COSIM_MECH_CLAMPED_BOTTOM) {
-    for (int j = 0; j <= c->ny; ++j)
-      for (int i = 0; i <= c->nx; ++i) at(i, j, 0) = 7;
-  } else if (o->bc == COSIM_MECH_KINEMATIC_MOUNT) {
-    const int ic = c->nx / 2, jc = c->ny / 2;
-    at(ic, jc, 0) |= 7;
-    at(c->nx, jc, 0) |= 6;
-    at(ic, c->ny, 0) |= 4;
-  } else {
-    for (int k = 0; k <= c->nz; ++k)
-      for (int j = 0; j <= c->ny; ++j)
-        for (int i = 0; i <= c->nx; ++i)
-          at(i, j, k) = o->node_mask[((size_t)k * (c->ny + 1) + j) * (c->nx + 1) + i] & 7;
+  if (o->bc != COSIM_MECH_MASK) {  // built-in supports: written on the device, no host round trip
+    CHECK_CUDA(c, cudaMemsetAsync(c->mask, 0, c->npad, c->stream));
+    const int nb = o->bc == COSIM_MECH_CLAMPED_BOTTOM ? (int)std::min<long long>(
+                                                            ((long long)(c->nx + 1) * (c->ny + 1) + 255) / 256, 4096)
+                                                      : 1;
+    support_mask_kernel<<<nb, 256, 0, c->stream>>>(c->mask, c->nx, c->ny, c->px, o->bc); ++c->launches;
+    CHECK_LAUNCH(c);
+    return COSIM_OK;
   }
+  std::vector<uint8_t> m(c->npad, 0);
+  for (int k = 0; k <= c->nz; ++k)
+    for (int j = 0; j <= c->ny; ++j)
+      for (int i = 0; i <= c->nx; ++i)
+        m[(size_t)k * c->plane + (size_t)j * c->px + i] =
+            o->node_mask[((size_t)k * (c->ny + 1) + j) * (c->nx + 1) + i] & 7;
   CHECK_CUDA(c, cudaMemcpyAsync(c->mask, m.data(), c->npad, cudaMemcpyHostToDevice, c->stream));
   CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
   return COSIM_OK;

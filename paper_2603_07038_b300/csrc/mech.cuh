@@ -814,4 +814,21 @@ __global__ void __launch_bounds__(256) umag_kernel(long long n, const R *u0, con
     out[q] = sqrt(u0[q] * u0[q] + u1[q] * u1[q] + u2[q] * u2[q]);
 }
 
+// Fixed-component bits of the built-in supports (bit c: component c held at
+// zero), written into a zeroed padded mask: clamped bottom (bc 0, every z = 0
+// node) or the three-node kinematic mount (bc 1: the bottom centre fixed in
+// x, y, z, the +x edge node in y, z and the +y edge node in z, six DOFs).
+__global__ void __launch_bounds__(256) support_mask_kernel(uint8_t *mask, int nx, int ny, int px, int bc) {
+  if (bc == 0) {
+    const long long n = (long long)(nx + 1) * (ny + 1);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+      mask[(q / (nx + 1)) * px + q % (nx + 1)] = 7;
+  } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int ic = nx / 2, jc = ny / 2;
+    mask[(long long)jc * px + ic] |= 7;
+    mask[(long long)jc * px + nx] |= 6;
+    mask[(long long)ny * px + ic] |= 4;
+  }
+}
+
 }  // namespace cosim
