@@ -195,11 +195,6 @@ __device__ __forceinline__ V psi_apply(const EmArgs<R> &A, V omb, int d, int typ
   }
 }
 
-// single node: the state of derivative axis d, slab position s (or none)
-template <typename R>
-__device__ __forceinline__ Psi<R> psi_node(const EmArgs<R> &A, int d, int type, int slot, int s, int i, int j, int k) {
-  return psi_pre<R, R>(A, d, type, slot, s, s >= 0 ? psi_index(A, d, s, i, j, k) : 0);
-}
 // (dF1 + psi1) - (dF2 + psi2) of one curl component of a single node: the
 // first derivative's state is in slot 1, the second's in slot 0
 template <typename R>
@@ -439,6 +434,18 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
   const R hdx = mul_(half_dt, idx), hdy = mul_(half_dt, idy);
   const R dtWx_y = mul_(dt, add_(hym, hy0)), dtWy_x = mul_(dt, add_(hxm, hx0));
   const R lqx = mul_(R(0.25), hx0), lqy = mul_(R(0.25), hy0);
+  // this node's element of the slab arrays (the layout of psi_index) in the
+  // index type: x and y slabs at plane 0 plus kk planes, z slab at position
+  // 0 plus s positions (each slab array is smaller than a padded node array)
+  const I qx0 = (I)j * (I)A.sn[0] + (I)sxE, qxs = (I)(ny + 1) * (I)A.sn[0];
+  const I qy0 = (I)syE * (I)g.px + (I)i, qys = (I)A.sn[1] * (I)g.px;
+  const I qz0 = (I)j * (I)g.px + (I)i, qzs = (I)(ny + 1) * (I)g.px;
+  auto qof = [&](int d, int s, int kk) -> long long {
+    return d == 0 ? (long long)(qx0 + (I)kk * qxs) : d == 1 ? (long long)(qy0 + (I)kk * qys) : (long long)(qz0 + (I)s * qzs);
+  };
+  auto psi_at = [&](int d, int type, int slot, int s, int kk) -> Psi<R> {
+    return psi_pre<R, R>(A, d, type, slot, s, s >= 0 ? qof(d, s, kk) : 0);
+  };
 
   // The H side's CPML states of plane kk (d, slot; slab position s or -1):
   // Hx (y: slot 1, z: slot 0), Hy (z: slot 1, x: slot 0), Hz (x: slot 1,
@@ -466,7 +473,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
         int d, slot;
         const int sp = h_state(e, kk, d, slot);
         if (sp >= 0) {
-          const long long q = psi_index(A, d, sp, i, j, kk);
+          const long long q = qof(d, sp, kk);
           cp_async<4>(r + 3 * e, A.xHo[d][slot] + q, true);
           cp_async<4>(r + 3 * e + 1, A.lHo[d][slot] + q, true);
           cp_async<4>(r + 3 * e + 2, A.dHo[d][slot] + q, true);
@@ -555,7 +562,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
       for (int e = 0; e < kPsiH; ++e) {
         int d, slot;
         ph[e].s = h_state(e, k, d, slot);
-        ph[e].q = ph[e].s >= 0 ? psi_index(A, d, ph[e].s, i, j, k) : 0;
+        ph[e].q = ph[e].s >= 0 ? qof(d, ph[e].s, k) : 0;
         ph[e].c.hi = r[3 * e];
         ph[e].c.lo = r[3 * e + 1];
         ph[e].c.d = r[3 * e + 2];
@@ -565,7 +572,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
       for (int e = 0; e < kPsiH; ++e) {
         int d, slot;
         const int sp = h_state(e, k, d, slot);
-        ph[e] = psi_node(A, d, 1, slot, sp, i, j, k);
+        ph[e] = psi_at(d, 1, slot, sp, k);
       }
     }
     const Psi<R> &pHx1 = ph[0], &pHx2 = ph[1], &pHy1 = ph[2], &pHy2 = ph[3], &pHz1 = ph[4], &pHz2 = ph[5];
@@ -586,9 +593,9 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
     // the E side's CPML states, in flight across the barrier
     const bool ex_on = need_ex && !(fix_y || fix_z), ey_on = need_ey && !(fix_x || fix_z);
     const bool ez_on = own && kz && !(fix_x || fix_y);
-    const Psi<R> pEx1 = psi_node(A, 1, 0, 1, ex_on ? syE : -1, i, j, k), pEx2 = psi_node(A, 2, 0, 0, ex_on ? szE : -1, i, j, k);
-    const Psi<R> pEy1 = psi_node(A, 2, 0, 1, ey_on ? szE : -1, i, j, k), pEy2 = psi_node(A, 0, 0, 0, ey_on ? sxE : -1, i, j, k);
-    const Psi<R> pEz1 = psi_node(A, 0, 0, 1, ez_on ? sxE : -1, i, j, k), pEz2 = psi_node(A, 1, 0, 0, ez_on ? syE : -1, i, j, k);
+    const Psi<R> pEx1 = psi_at(1, 0, 1, ex_on ? syE : -1, k), pEx2 = psi_at(2, 0, 0, ex_on ? szE : -1, k);
+    const Psi<R> pEy1 = psi_at(2, 0, 1, ey_on ? szE : -1, k), pEy2 = psi_at(0, 0, 0, ey_on ? sxE : -1, k);
+    const Psi<R> pEz1 = psi_at(0, 0, 1, ez_on ? sxE : -1, k), pEz2 = psi_at(1, 0, 0, ez_on ? syE : -1, k);
     // the one barrier of the plane: H of this plane and the y-edge Joule
     // shares of the previous one are visible; every thread is past its reads
     // of plane k-1's stage
