@@ -170,8 +170,9 @@ __device__ __forceinline__ V psi_apply(const EmArgs<R> &A, V omb, int d, int typ
     }
     return chi;
   } else {
-    // (hi + lo + D)(1 - omb) with Knuth's TwoSum for the additions, an FMA
-    // product error for omb * hi, and a final renormalisation (Fast2Sum).
+    // (hi + lo + D)(1 - omb) with Knuth's TwoSum for hi + D, an FMA product
+    // error for omb * sh, Dekker's Fast2Sum for sh - omb sh (exact: omb is in
+    // [0, 1), so |omb sh| <= |sh|) and a final renormalisation (Fast2Sum).
     const V hi = p.c.hi, lo = p.c.lo;
     const V D = sub_(deriv, p.c.d);
     const V sh = add_(hi, D);
@@ -181,8 +182,7 @@ __device__ __forceinline__ V psi_apply(const EmArgs<R> &A, V omb, int d, int typ
     const V pr = mul_(omb, sh);
     const V pe = fma_(omb, sh, neg_(pr));
     const V s2 = sub_(sh, pr);
-    const V bv2 = sub_(s2, sh);
-    const V e2 = add_(sub_(sh, sub_(s2, bv2)), sub_(neg_(pr), bv2));
+    const V e2 = sub_(neg_(pr), sub_(s2, sh));
     const V l2 = sub_(sub_(add_(l1, e2), pe), mul_(omb, l1));
     const V h3 = add_(s2, l2);
     const V l3 = sub_(l2, sub_(h3, s2));
@@ -353,8 +353,9 @@ __device__ __forceinline__ void em_abort(uint64_t *bars, int k, int nz, int *err
 // tile by owns the nodes i = xs .. min(xs + 30, xe - 1), j = (TY-1) by ..
 // (TY-1) by + TY - 2; thread (tx, ty) holds node (xs - 1 + tx, (TY-1) by - 1
 // + ty). Nodes outside the grid, on the walls and inside the CPML slabs are
-// all handled here.
-template <typename R, typename I, int TY, bool CPL>
+// all handled here. XS / YS: the tile may hold nodes of an x / y slab (when
+// false, that axis's CPML code is left out of the instantiation).
+template <typename R, typename I, int TY, bool CPL, bool XS, bool YS>
 __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
                                                EmStage<R, 32, TY> *stg, R (*sHxz)[2][TY][32], R (*sQy)[TY][32],
                                                uint64_t *bars, int *s_abort, int xs, int xe, int by) {
@@ -424,8 +425,8 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
   const bool fix_x = (i == 0 && A.fixlo[0]) || (i == nx && A.fixhi[0]);
   const bool fix_y = (j == 0 && A.fixlo[1]) || (j == ny && A.fixhi[1]);
   // CPML slab positions along x and y (E: nodes, H: cells); none inside
-  const int sxE = slab_index(i, nx, A.slo[0], A.shi[0]);
-  const int syE = slab_index(j, ny, A.slo[1], A.shi[1]);
+  const int sxE = XS ? slab_index(i, nx, A.slo[0], A.shi[0]) : -1;
+  const int syE = YS ? slab_index(j, ny, A.slo[1], A.shi[1]) : -1;
   const int sxH = in_x ? sxE : -1;
   const int syH = in_y ? syE : -1;
   const R dt = A.dt;
@@ -1064,10 +1065,11 @@ __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
     // right parts of the interior rows, then the rows above them
     const int nbx = A.nbx, below = A.iby0 * nbx, w = A.nl + A.nr, mid = (A.iby1 - A.iby0) * w;
     int xs, xe = A.g.nx + 1, by;
-    if (b < below) {
-      by = b / nbx;
-      xs = (TX - 1) * (b - by * nbx);
-    } else if ((b -= below) < mid) {
+    auto *sb = reinterpret_cast<EmStage<R, TX, TY> *>(stg);
+    auto *sh = reinterpret_cast<R(*)[2][TY][TX]>(&sHxz[0][0][0][0]);
+    auto *sq = reinterpret_cast<R(*)[TY][TX]>(&sQy[0][0][0]);
+    if (b >= below && b - below < mid) {  // beside the interior pairs: no y slab row
+      b -= below;
       by = b / w;
       const int c = b - by * w;
       by += A.iby0;
@@ -1077,16 +1079,24 @@ __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
       } else {
         xs = A.xb1 + (TX - 1) * (c - A.nl);
       }
+      em_tile_border<R, I, TY, CPL, true, false>(A, s_cp, s_mt, sb, sh, sq, s_bar, &s_abort, xs, xe, by);
     } else {
-      b -= mid;
-      by = b / nbx;
-      xs = (TX - 1) * (b - by * nbx);
-      by += A.iby1;
+      if (b >= below) {
+        b -= below + mid;
+        by = b / nbx;
+        xs = (TX - 1) * (b - by * nbx);
+        by += A.iby1;
+      } else {
+        by = b / nbx;
+        xs = (TX - 1) * (b - by * nbx);
+      }
+      // nodes i = xs - 1 .. xs + 30: does the tile reach an x slab?
+      const bool xsl = (A.slo[0] > 0 && xs - 1 <= A.slo[0]) || (A.shi[0] > 0 && xs + TX - 2 >= A.g.nx - A.shi[0]);
+      if (xsl)
+        em_tile_border<R, I, TY, CPL, true, true>(A, s_cp, s_mt, sb, sh, sq, s_bar, &s_abort, xs, xe, by);
+      else
+        em_tile_border<R, I, TY, CPL, false, true>(A, s_cp, s_mt, sb, sh, sq, s_bar, &s_abort, xs, xe, by);
     }
-    em_tile_border<R, I, TY, CPL>(A, s_cp, s_mt, reinterpret_cast<EmStage<R, TX, TY> *>(stg),
-                                  reinterpret_cast<R(*)[2][TY][TX]>(&sHxz[0][0][0][0]),
-                                  reinterpret_cast<R(*)[TY][TX]>(&sQy[0][0][0]),
-                                  s_bar, &s_abort, xs, xe, by);
   } else {
     b -= A.n_border;
     const int py = b / A.npx, px = b - py * A.npx;
