@@ -1189,22 +1189,28 @@ static cosim_status pcg_run(cosim_ctx *c, double rtol, int64_t maxit, int every,
   // keeps small thermal loads out of the FP32 subnormal range, where the
   // residual products would underflow long before the tolerance is met.
   double scale = 1.0, bb = 0.0;
-  for (int pass = 0; pass < 2; ++pass) {
-    cg_init_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, F[0], F[1], F[2], D[0], D[1], D[2], U[0], U[1], U[2],
-                                                         Rv[0], Rv[1], Rv[2], Pv[0], Pv[1], Pv[2], pa, pb, (R)scale);
-    ++c->launches;
-    CHECK_LAUNCH(c);
-    reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pa, kRedBlocks, &c->cg->rz[0]); ++c->launches;
-    reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pb, kRedBlocks, &c->cg->bb); ++c->launches;
-    CHECK_LAUNCH(c);
+  sumsq3_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, F[0], F[1], F[2], pb); ++c->launches;
+  CHECK_LAUNCH(c);
+  reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pb, kRedBlocks, &c->cg->bb); ++c->launches;
+  CHECK_LAUNCH(c);
+  CHECK_CUDA(c, cudaMemcpyAsync(c->host_scal, &c->cg->bb, 8, cudaMemcpyDeviceToHost, c->stream));
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  bb = c->host_scal[0];
+  if (!std::isfinite(bb)) return fail(c, COSIM_ERR_NONFINITE, "non-finite right-hand side");
+  if (bb > 0) scale = std::ldexp(1.0, -(int)std::lround(0.5 * std::log2(bb / (3.0 * (double)(c->nx + 1) *
+                                                                                    (c->ny + 1) * (c->nz + 1)))));
+  cg_init_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, F[0], F[1], F[2], D[0], D[1], D[2], U[0], U[1], U[2],
+                                                       Rv[0], Rv[1], Rv[2], Pv[0], Pv[1], Pv[2], pa, pb, (R)scale);
+  ++c->launches;
+  CHECK_LAUNCH(c);
+  reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pa, kRedBlocks, &c->cg->rz[0]); ++c->launches;
+  reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pb, kRedBlocks, &c->cg->bb); ++c->launches;
+  CHECK_LAUNCH(c);
+  if (scale != 1.0) {  // the scaled right-hand side's norm for the relative residual
     CHECK_CUDA(c, cudaMemcpyAsync(c->host_scal, &c->cg->bb, 8, cudaMemcpyDeviceToHost, c->stream));
     CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
     bb = c->host_scal[0];
     if (!std::isfinite(bb)) return fail(c, COSIM_ERR_NONFINITE, "non-finite right-hand side");
-    if (pass == 1 || !(bb > 0)) break;
-    const int e = -(int)std::lround(0.5 * std::log2(bb / (3.0 * (double)(c->nx + 1) * (c->ny + 1) * (c->nz + 1))));
-    if (e == 0) break;
-    scale = std::ldexp(1.0, e);
   }
   int64_t it = 0;
   *relres = bb > 0 ? 1.0 : 0.0;

@@ -498,8 +498,22 @@ __global__ void __launch_bounds__(256) hex8_node_kernel(Geo<R> g, const uint8_t 
   const int k = blockIdx.z;
   if (i > g.nx || j > g.ny) return;
   R acc[3] = {0, 0, 0};
+  // MODE 1: the 3 x 3 x 3 nodal dT around the node, read once for its 8
+  // elements (zero outside the grid, where no element reads it)
+  R tn[27];
+  if (MODE == 1) {
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      const int ni = i - 1 + q % 3, nj = j - 1 + (q / 3) % 3, nk = k - 1 + q / 9;
+      tn[q] = (ni >= 0 && ni <= g.nx && nj >= 0 && nj <= g.ny && nk >= 0 && nk <= g.nz) ? T[g.nid(ni, nj, nk)] - T_ref
+                                                                                         : R(0);
+    }
+  }
+#pragma unroll
   for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
     for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
       for (int dx = 0; dx < 2; ++dx) {
         const int ei = i - 1 + dx, ej = j - 1 + dy, ek = k - 1 + dz;
         const int m = g.cell(ei, ej, ek);
@@ -516,8 +530,7 @@ __global__ void __launch_bounds__(256) hex8_node_kernel(Geo<R> g, const uint8_t 
         } else {
           R t[8];
 #pragma unroll
-          for (int a = 0; a < 8; ++a)
-            t[a] = T[g.nid(ei + (a & 1), ej + ((a >> 1) & 1), ek + ((a >> 2) & 1))] - T_ref;
+          for (int a = 0; a < 8; ++a) t[a] = tn[(dz + (a >> 2)) * 9 + (dy + ((a >> 1) & 1)) * 3 + dx + (a & 1)];
           modal_fwd(t);
           const R s[3] = {R(1 - 2 * dx), R(1 - 2 * dy), R(1 - 2 * dz)};  // node's corner signs
           const int lin[3] = {1, 2, 4};
@@ -620,6 +633,20 @@ __global__ void __launch_bounds__(256) cg_init_kernel(long long n, const R *f0, 
     part_rz[blockIdx.x] = rz;
     part_bb[blockIdx.x] = bb;
   }
+}
+
+// partial sums of f.f (each node's three-component term in the context
+// precision, accumulated in FP64)
+template <typename R>
+__global__ void __launch_bounds__(256) sumsq3_kernel(long long n, const R *f0, const R *f1, const R *f2,
+                                                      double *part) {
+  double ss = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const R a0 = f0[q], a1 = f1[q], a2 = f2[q];
+    ss += (double)(a0 * a0 + a1 * a1 + a2 * a2);
+  }
+  ss = block_sum(ss);
+  if (threadIdx.x == 0) part[blockIdx.x] = ss;
 }
 
 // x += alpha p, r -= alpha q, alpha = rz/pq; partial sums of r.(D^-1 r) and r.r
