@@ -498,22 +498,8 @@ __global__ void __launch_bounds__(256) hex8_node_kernel(Geo<R> g, const uint8_t 
   const int k = blockIdx.z;
   if (i > g.nx || j > g.ny) return;
   R acc[3] = {0, 0, 0};
-  // MODE 1: the 3 x 3 x 3 nodal dT around the node, read once for its 8
-  // elements (zero outside the grid, where no element reads it)
-  R tn[27];
-  if (MODE == 1) {
-#pragma unroll
-    for (int q = 0; q < 27; ++q) {
-      const int ni = i - 1 + q % 3, nj = j - 1 + (q / 3) % 3, nk = k - 1 + q / 9;
-      tn[q] = (ni >= 0 && ni <= g.nx && nj >= 0 && nj <= g.ny && nk >= 0 && nk <= g.nz) ? T[g.nid(ni, nj, nk)] - T_ref
-                                                                                         : R(0);
-    }
-  }
-#pragma unroll
   for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
     for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
       for (int dx = 0; dx < 2; ++dx) {
         const int ei = i - 1 + dx, ej = j - 1 + dy, ek = k - 1 + dz;
         const int m = g.cell(ei, ej, ek);
@@ -530,7 +516,8 @@ __global__ void __launch_bounds__(256) hex8_node_kernel(Geo<R> g, const uint8_t 
         } else {
           R t[8];
 #pragma unroll
-          for (int a = 0; a < 8; ++a) t[a] = tn[(dz + (a >> 2)) * 9 + (dy + ((a >> 1) & 1)) * 3 + dx + (a & 1)];
+          for (int a = 0; a < 8; ++a)
+            t[a] = T[g.nid(ei + (a & 1), ej + ((a >> 1) & 1), ek + ((a >> 2) & 1))] - T_ref;
           modal_fwd(t);
           const R s[3] = {R(1 - 2 * dx), R(1 - 2 * dy), R(1 - 2 * dz)};  // node's corner signs
           const int lin[3] = {1, 2, 4};
