@@ -268,9 +268,12 @@ static cosim_status validate(const cosim_grid_desc *d, const cosim_options *o, s
         !(q.nu > -1 && q.nu < 0.5))
       return why = "material " + std::to_string(m) + " has out-of-range constants", COSIM_ERR_INVALID;
   }
-  const size_t nc = (size_t)d->nx * d->ny * d->nz;
-  for (size_t q = 0; q < nc; ++q)
-    if (d->mat[q] >= d->nmat) return why = "voxel material id >= nmat", COSIM_ERR_INVALID;
+  if (d->nmat < 256) {  // a branch-free maximum (vectorised): one pass over the voxels at memory speed
+    const size_t nc = (size_t)d->nx * d->ny * d->nz;
+    uint8_t mx = 0;
+    for (size_t q = 0; q < nc; ++q) mx = d->mat[q] > mx ? d->mat[q] : mx;
+    if (mx >= d->nmat) return why = "voxel material id >= nmat", COSIM_ERR_INVALID;
+  }
   bool any_cpml = false;
   for (int f = 0; f < 6; ++f) {
     if (d->em_bc[f] < 0 || d->em_bc[f] > 2) return why = "bad em_bc", COSIM_ERR_INVALID;
