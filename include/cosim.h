@@ -261,6 +261,24 @@ enum {
 cosim_status cosim_read_fields(cosim_ctx *ctx, int32_t field, int32_t dtype, void *dst, size_t bytes,
                                int32_t dst_is_device);
 
+/* Start copying one field into dst (same layout, dtype and size rules as
+ * cosim_read_fields) without waiting for it: the field is converted into a
+ * context-owned staging buffer on the context's stream, in order after the
+ * work enqueued so far, and copied to dst on a second stream of the context,
+ * so the copy overlaps the work enqueued next. Later calls may change the
+ * field: the value read is the one the enqueued work had produced. dst must
+ * stay valid, and must not be read, until cosim_wait_reads returns; pinned
+ * host memory lets the copy run asynchronously. A second asynchronous read
+ * first waits for the previous one's copy (one staging buffer). Caller owns
+ * dst. */
+cosim_status cosim_read_fields_async(cosim_ctx *ctx, int32_t field, int32_t dtype, void *dst, size_t bytes,
+                                     int32_t dst_is_device);
+
+/* Wait until every copy started by cosim_read_fields_async has landed in
+ * its dst; reports a CUDA error of those copies or a bounded-wait timeout of
+ * the context's kernels. */
+cosim_status cosim_wait_reads(cosim_ctx *ctx);
+
 /* Overwrite one field from src (same layout and size rules). Entries that are
  * not unknowns (edges beyond the last cell, tangential E on PEC walls) are
  * stored as zero. Writable: E, H, T, Q, P, UX..UZ. */

@@ -34,7 +34,8 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 
 
 EXPORTED = ["cosim_create", "cosim_set_sources", "cosim_em_steps", "cosim_joule_accumulate",
             "cosim_thermal_steps", "cosim_stress_solve", "cosim_stress_apply", "cosim_read_fields",
-            "cosim_write_fields", "cosim_query", "cosim_last_error", "cosim_destroy"]
+            "cosim_write_fields", "cosim_query", "cosim_last_error", "cosim_destroy", "cosim_read_fields_async",
+            "cosim_wait_reads"]
 
 
 class CosimError(RuntimeError):
@@ -124,6 +125,10 @@ def load():
     L.cosim_read_fields.restype = st
     L.cosim_write_fields.argtypes = [P, C.c_int32, C.c_int32, P, C.c_size_t, C.c_int32]
     L.cosim_write_fields.restype = st
+    L.cosim_read_fields_async.argtypes = [P, C.c_int32, C.c_int32, P, C.c_size_t, C.c_int32]
+    L.cosim_read_fields_async.restype = st
+    L.cosim_wait_reads.argtypes = [P]
+    L.cosim_wait_reads.restype = st
     L.cosim_query.argtypes = [P, C.c_int32, C.POINTER(C.c_double)]
     L.cosim_query.restype = st
     L.cosim_last_error.argtypes = [P]
@@ -315,6 +320,26 @@ def cosim_read_fields(ctx, field, dst):
         dt = COSIM_FP64 if dst.dtype == torch.float64 else COSIM_FP32
         _check(load().cosim_read_fields(ctx, field, dt, dst.data_ptr(), dst.numel() * dst.element_size(), 1), ctx)
     return dst
+
+
+def cosim_read_fields_async(ctx, field, dst):
+    """Start reading a field into dst (pinned numpy array or torch CUDA tensor);
+    dst is filled once cosim_wait_reads(ctx) returns."""
+    if isinstance(dst, np.ndarray):
+        assert dst.flags.c_contiguous
+        dt = COSIM_FP64 if dst.dtype == np.float64 else COSIM_FP32
+        _check(load().cosim_read_fields_async(ctx, field, dt, dst.ctypes.data, dst.nbytes, 0), ctx)
+    else:
+        import torch
+        assert dst.is_cuda and dst.is_contiguous()
+        dt = COSIM_FP64 if dst.dtype == torch.float64 else COSIM_FP32
+        _check(load().cosim_read_fields_async(ctx, field, dt, dst.data_ptr(), dst.numel() * dst.element_size(), 1),
+               ctx)
+    return dst
+
+
+def cosim_wait_reads(ctx):
+    _check(load().cosim_wait_reads(ctx), ctx)
 
 
 def cosim_write_fields(ctx, field, src):

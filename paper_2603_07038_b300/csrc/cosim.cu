@@ -50,6 +50,12 @@ struct cosim_ctx {
   double cpml_order = 3, cpml_eps_r = 1, h_conv[6] = {0, 0, 0, 0, 0, 0}, T_amb = 300, T_init = 300;
   double dt = 0, dt_th_limit = -1, thermal_safety = 0.9;
   cudaStream_t stream = nullptr;
+  // asynchronous field reads: staging buffer, copy stream, events
+  void *rd_stage = nullptr;
+  size_t rd_bytes = 0;
+  cudaStream_t rd_stream = nullptr;
+  cudaEvent_t rd_packed = nullptr, rd_done = nullptr;
+  bool rd_pending = false;
   cosim_allocator alloc{};
   bool has_alloc = false;
   // device memory
@@ -592,6 +598,12 @@ static void drop_graph(cosim_ctx *c);
 extern "C" void cosim_destroy(cosim_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->rd_stream) {
+    cudaStreamSynchronize(c->rd_stream);
+    cudaEventDestroy(c->rd_packed);
+    cudaEventDestroy(c->rd_done);
+    cudaStreamDestroy(c->rd_stream);
+  }
   drop_graph(c);
   for (auto &a : c->allocs) {
     if (c->has_alloc)
@@ -1473,6 +1485,36 @@ static void launch_pack(cosim_ctx *c, const void *src, void *dst, bool cells, do
   pack_kernel<S, D><<<kRedBlocks, 256, 0, c->stream>>>((const S *)src, (D *)dst, nx1, ny1, nz1, px, add); ++c->launches;
 }
 
+// the dense copy of a field in dtype at out (device), on the context's stream
+static cosim_status pack_field(cosim_ctx *c, int32_t field, int32_t dtype, void *out) {
+  int eb;
+  bool cells, sdbl;
+  void *src = field_ptr(c, field, &eb, &cells, &sdbl);
+  if (field == COSIM_F_Q) {
+    cosim_status fs = joule_flush(c);
+    if (fs != COSIM_OK) return fs;
+  }
+  const double add = field == COSIM_F_T ? c->T_init : 0.0;
+  if (sdbl && dtype == COSIM_FP64) launch_pack<double, double>(c, src, out, cells, add);
+  else if (sdbl) launch_pack<double, float>(c, src, out, cells, add);
+  else if (dtype == COSIM_FP64) launch_pack<float, double>(c, src, out, cells, add);
+  else launch_pack<float, float>(c, src, out, cells, add);
+  CHECK_LAUNCH(c);
+  return COSIM_OK;
+}
+
+// argument checks shared by the read calls: the field exists and dst has its size
+static cosim_status check_read(cosim_ctx *c, int32_t field, int32_t dtype, const void *dst, size_t bytes) {
+  int eb;
+  bool cells, sdbl;
+  if (!field_ptr(c, field, &eb, &cells, &sdbl)) return fail(c, COSIM_ERR_INVALID, "unknown field, or field not computed yet");
+  if (dtype != COSIM_FP64 && dtype != COSIM_FP32) return fail(c, COSIM_ERR_INVALID, "bad dtype");
+  const size_t n = cells ? (size_t)c->nx * c->ny * c->nz : (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
+  const size_t ob = dtype == COSIM_FP64 ? 8 : 4;
+  if (!dst || bytes != n * ob) return fail(c, COSIM_ERR_INVALID, "dst size mismatch");
+  return COSIM_OK;
+}
+
 // A kernel whose bounded wait for staged data expired sets c->dev_err; report it
 // (and clear it) at the next synchronising call.
 static cosim_status check_device_wait(cosim_ctx *c) {
@@ -1487,27 +1529,48 @@ static cosim_status check_device_wait(cosim_ctx *c) {
 extern "C" cosim_status cosim_read_fields(cosim_ctx *c, int32_t field, int32_t dtype, void *dst, size_t bytes,
                                           int32_t dst_is_device) {
   if (!c) return COSIM_ERR_INVALID;
-  int eb;
-  bool cells, sdbl;
-  void *src = field_ptr(c, field, &eb, &cells, &sdbl);
-  if (!src) return fail(c, COSIM_ERR_INVALID, "unknown field, or field not computed yet");
-  if (dtype != COSIM_FP64 && dtype != COSIM_FP32) return fail(c, COSIM_ERR_INVALID, "bad dtype");
-  const size_t n = cells ? (size_t)c->nx * c->ny * c->nz : (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
-  const size_t ob = dtype == COSIM_FP64 ? 8 : 4;
-  if (!dst || bytes != n * ob) return fail(c, COSIM_ERR_INVALID, "dst size mismatch");
-  if (field == COSIM_F_Q) {
-    cosim_status fs = joule_flush(c);
-    if (fs != COSIM_OK) return fs;
-  }
+  cosim_status st = check_read(c, field, dtype, dst, bytes);
+  if (st != COSIM_OK) return st;
   void *out = dst_is_device ? dst : c->scratch;
-  const double add = field == COSIM_F_T ? c->T_init : 0.0;
-  if (sdbl && dtype == COSIM_FP64) launch_pack<double, double>(c, src, out, cells, add);
-  else if (sdbl) launch_pack<double, float>(c, src, out, cells, add);
-  else if (dtype == COSIM_FP64) launch_pack<float, double>(c, src, out, cells, add);
-  else launch_pack<float, float>(c, src, out, cells, add);
-  CHECK_LAUNCH(c);
+  if ((st = pack_field(c, field, dtype, out)) != COSIM_OK) return st;
   if (!dst_is_device) CHECK_CUDA(c, cudaMemcpyAsync(dst, c->scratch, bytes, cudaMemcpyDeviceToHost, c->stream));
   CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  return check_device_wait(c);
+}
+
+extern "C" cosim_status cosim_read_fields_async(cosim_ctx *c, int32_t field, int32_t dtype, void *dst, size_t bytes,
+                                                int32_t dst_is_device) {
+  if (!c) return COSIM_ERR_INVALID;
+  cosim_status st = check_read(c, field, dtype, dst, bytes);
+  if (st != COSIM_OK) return st;
+  if (!c->rd_stream) {
+    CHECK_CUDA(c, cudaStreamCreateWithFlags(&c->rd_stream, cudaStreamNonBlocking));
+    CHECK_CUDA(c, cudaEventCreateWithFlags(&c->rd_packed, cudaEventDisableTiming));
+    CHECK_CUDA(c, cudaEventCreateWithFlags(&c->rd_done, cudaEventDisableTiming));
+  }
+  if (c->rd_bytes < bytes) {  // the largest read so far: node-sized FP64 at most
+    const size_t cap = (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1) * 8;
+    if (c->rd_pending) CHECK_CUDA(c, cudaEventSynchronize(c->rd_done));
+    ALLOC(c, c->rd_stage, cap);
+    c->rd_bytes = cap;
+  }
+  // the staging buffer is free once the previous copy has landed
+  if (c->rd_pending) CHECK_CUDA(c, cudaStreamWaitEvent(c->stream, c->rd_done, 0));
+  if ((st = pack_field(c, field, dtype, c->rd_stage)) != COSIM_OK) return st;
+  CHECK_CUDA(c, cudaEventRecord(c->rd_packed, c->stream));
+  CHECK_CUDA(c, cudaStreamWaitEvent(c->rd_stream, c->rd_packed, 0));
+  CHECK_CUDA(c, cudaMemcpyAsync(dst, c->rd_stage, bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->rd_stream));
+  CHECK_CUDA(c, cudaEventRecord(c->rd_done, c->rd_stream));
+  c->rd_pending = true;
+  return COSIM_OK;
+}
+
+extern "C" cosim_status cosim_wait_reads(cosim_ctx *c) {
+  if (!c) return COSIM_ERR_INVALID;
+  if (!c->rd_pending) return COSIM_OK;
+  CHECK_CUDA(c, cudaEventSynchronize(c->rd_done));
+  c->rd_pending = false;
   return check_device_wait(c);
 }
 

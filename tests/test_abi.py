@@ -101,4 +101,6 @@ def test_null_handle_calls_are_invalid(lib):
     assert lib.cosim_thermal_steps(None, 1, 0.0) == api.COSIM_ERR_INVALID
     v = C.c_double()
     assert lib.cosim_query(None, 0, C.byref(v)) == api.COSIM_ERR_INVALID
+    assert lib.cosim_read_fields_async(None, 0, 0, None, 0, 0) == api.COSIM_ERR_INVALID
+    assert lib.cosim_wait_reads(None) == api.COSIM_ERR_INVALID
     lib.cosim_destroy(None)

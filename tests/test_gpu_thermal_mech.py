@@ -161,3 +161,29 @@ def test_stress_solve_fp32_tiny_loads(dT_scale):
     # rise is represented to FP32 relative precision)
     assert rel_l2(u, interleaved_to_soa(ref["u"])) < 1e-4
     ctx.close()
+
+
+def test_async_reads_match_sync_reads():
+    """cosim_read_fields_async: the copy holds the field as of the call (a
+    later write does not reach it), overlaps a stress solve, and a second
+    asynchronous read reuses the staging buffer after the first has landed."""
+    import torch
+    p, o, ctx, fixed = _thermal_load_problem(FP32, api.COSIM_MECH_CLAMPED_BOTTOM)
+    T_ref = ctx.read(api.COSIM_F_T)
+    T_host = torch.empty(p.n_nodes, dtype=torch.float32).pin_memory().numpy()
+    T_dev = torch.empty(p.n_nodes, dtype=torch.float64, device="cuda")
+    api.cosim_read_fields_async(ctx.h, api.COSIM_F_T, T_host)
+    api.cosim_read_fields_async(ctx.h, api.COSIM_F_T, T_dev)
+    ctx.write(api.COSIM_F_T, np.full(p.n_nodes, 400.0))  # after the reads were enqueued
+    ctx.stress_solve(bc=api.COSIM_MECH_CLAMPED_BOTTOM, T_ref=300.0, rtol=1e-6, check_every=8)
+    VM_host = torch.empty(p.n_cells, dtype=torch.float32).pin_memory().numpy()
+    api.cosim_read_fields_async(ctx.h, api.COSIM_F_VM, VM_host)
+    api.cosim_wait_reads(ctx.h)
+    api.cosim_wait_reads(ctx.h)  # nothing pending: returns at once
+    assert np.array_equal(T_host, T_ref.astype(np.float32))
+    assert np.array_equal(T_dev.cpu().numpy(), T_ref)
+    assert np.array_equal(VM_host, ctx.read(api.COSIM_F_VM).astype(np.float32))
+    assert np.all(ctx.read(api.COSIM_F_T) == 400.0)
+    with pytest.raises(api.CosimError):
+        api.cosim_read_fields_async(ctx.h, api.COSIM_F_T, np.empty(3, np.float32))
+    ctx.close()
