@@ -269,8 +269,11 @@ cosim_status cosim_read_fields(cosim_ctx *ctx, int32_t field, int32_t dtype, voi
  * field: the value read is the one the enqueued work had produced. dst must
  * stay valid, and must not be read, until cosim_wait_reads returns; pinned
  * host memory lets the copy run asynchronously. A second asynchronous read
- * first waits for the previous one's copy (one staging buffer). Caller owns
- * dst. */
+ * first waits for the previous one's copy (one staging buffer). The first
+ * call allocates that buffer (8 bytes per node) through the context's
+ * allocator and creates the copy stream. Errors: COSIM_ERR_INVALID (unknown
+ * field, bad dtype, NULL dst or wrong size; nothing is enqueued),
+ * COSIM_ERR_OOM, COSIM_ERR_CUDA. Caller owns dst. */
 cosim_status cosim_read_fields_async(cosim_ctx *ctx, int32_t field, int32_t dtype, void *dst, size_t bytes,
                                      int32_t dst_is_device);
 
