@@ -53,11 +53,12 @@ __device__ __forceinline__ void modal_bwd(V v[8]) {
 }
 
 // One monomial group: the nonzero gradient columns of the group (G[c][d],
-// d with slot[d] >= 0; the others are zero), weight w = <phi^2>, slot[d] =
-// monomial receiving column d of the energy gradient (-1: none).
-// S_cd = delta_cd lambda tr(G) + mu (G_cd + G_dc); F[c][slot d] += w S_cd g_d.
+// d with slot[d] >= 0; the others are zero), slot[d] = monomial receiving
+// column d of the energy gradient (-1: none), wg[d] = w g_d s with the
+// group's weight w = <phi^2> and the element's volume factor s.
+// S_cd = delta_cd lambda tr(G) + mu (G_cd + G_dc); F[c][slot d] += S_cd wg_d.
 template <typename V, typename R>
-__device__ __forceinline__ void group_term(const V G[3][3], V lam, V mu, R w, const V g[3], const int slot[3],
+__device__ __forceinline__ void group_term(const V G[3][3], V lam, V mu, const V wg[3], const int slot[3],
                                            V F[3][8]) {
   V tr = bc_<V>(R(0));
   bool first = true;
@@ -75,7 +76,7 @@ __device__ __forceinline__ void group_term(const V G[3][3], V lam, V mu, R w, co
       if (slot[d] >= 0) {
         const V sym = slot[c] >= 0 ? add_(G[c][d], G[d][c]) : G[c][d];
         const V S = c == d ? fma_(mu, sym, lt) : mul_(mu, sym);
-        F[c][slot[d]] = fma_(mul_(bc_<V>(w), S), g[d], F[c][slot[d]]);
+        F[c][slot[d]] = fma_(S, wg[d], F[c][slot[d]]);
       }
 }
 
@@ -94,6 +95,12 @@ __device__ __forceinline__ void hex8_apply(V u[3][8], V lam, V mu, V hx, V hy, V
 #pragma unroll
     for (int m = 0; m < 8; ++m) F[c][m] = bc_<V>(R(0));
   const R third = R(1) / R(3), ninth = R(1) / R(9);
+  // the volume factor s = hx hy hz / 8 and the group weights folded into the
+  // gradient factors once: w1 (w = 1), w3 (1/3), w9 (1/9)
+  const V s = mul_(mul_(mul_(bc_<V>(R(0.125)), hx), hy), hz);
+  const V w1[3] = {mul_(g[0], s), mul_(g[1], s), mul_(g[2], s)};
+  const V w3[3] = {mul_(w1[0], bc_<V>(third)), mul_(w1[1], bc_<V>(third)), mul_(w1[2], bc_<V>(third))};
+  const V w9[3] = {mul_(w1[0], bc_<V>(ninth)), mul_(w1[1], bc_<V>(ninth)), mul_(w1[2], bc_<V>(ninth))};
   V G[3][3];
   {  // constant gradient: columns from the linear monomials xi, eta, zeta
     const int slot[3] = {1, 2, 4};
@@ -103,7 +110,7 @@ __device__ __forceinline__ void hex8_apply(V u[3][8], V lam, V mu, V hx, V hy, V
       G[c][1] = mul_(g8[1], u[c][2]);
       G[c][2] = mul_(g8[2], u[c][4]);
     }
-    group_term<V, R>(G, lam, mu, R(1), g, slot, F);
+    group_term<V, R>(G, lam, mu, w1, slot, F);
   }
   {  // terms linear in xi: d/deta of (xi eta), d/dzeta of (zeta xi)
     const int slot[3] = {-1, 3, 5};
@@ -112,7 +119,7 @@ __device__ __forceinline__ void hex8_apply(V u[3][8], V lam, V mu, V hx, V hy, V
       G[c][1] = mul_(g8[1], u[c][3]);
       G[c][2] = mul_(g8[2], u[c][5]);
     }
-    group_term<V, R>(G, lam, mu, third, g, slot, F);
+    group_term<V, R>(G, lam, mu, w3, slot, F);
   }
   {  // linear in eta: d/dxi of (xi eta), d/dzeta of (eta zeta)
     const int slot[3] = {3, -1, 6};
@@ -121,7 +128,7 @@ __device__ __forceinline__ void hex8_apply(V u[3][8], V lam, V mu, V hx, V hy, V
       G[c][0] = mul_(g8[0], u[c][3]);
       G[c][2] = mul_(g8[2], u[c][6]);
     }
-    group_term<V, R>(G, lam, mu, third, g, slot, F);
+    group_term<V, R>(G, lam, mu, w3, slot, F);
   }
   {  // linear in zeta: d/dxi of (zeta xi), d/deta of (eta zeta)
     const int slot[3] = {5, 6, -1};
@@ -130,7 +137,7 @@ __device__ __forceinline__ void hex8_apply(V u[3][8], V lam, V mu, V hx, V hy, V
       G[c][0] = mul_(g8[0], u[c][5]);
       G[c][1] = mul_(g8[1], u[c][6]);
     }
-    group_term<V, R>(G, lam, mu, third, g, slot, F);
+    group_term<V, R>(G, lam, mu, w3, slot, F);
   }
 #pragma unroll
   for (int d = 0; d < 3; ++d) {  // bilinear monomials from (xi eta zeta)
@@ -138,14 +145,13 @@ __device__ __forceinline__ void hex8_apply(V u[3][8], V lam, V mu, V hx, V hy, V
     slot[d] = 7;
 #pragma unroll
     for (int c = 0; c < 3; ++c) G[c][d] = mul_(g8[d], u[c][7]);
-    group_term<V, R>(G, lam, mu, ninth, g, slot, F);
+    group_term<V, R>(G, lam, mu, w9, slot, F);
   }
-  const V s = mul_(mul_(mul_(bc_<V>(R(0.125)), hx), hy), hz);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     modal_bwd(F[c]);
 #pragma unroll
-    for (int a = 0; a < 8; ++a) u[c][a] = mul_(s, F[c][a]);
+    for (int a = 0; a < 8; ++a) u[c][a] = F[c][a];
   }
 }
 
