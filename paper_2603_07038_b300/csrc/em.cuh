@@ -30,7 +30,7 @@
 // accumulator that is folded into the FP64 total every few steps (FP64 runs at
 // a small fraction of the FP32 rate on this GPU, so none is used per step).
 //
-// Inputs of planes k+1..k+3 are copied to shared memory by TMA (one thread
+// Inputs of planes k+1..k+2 are copied to shared memory by TMA (one thread
 // issues a box per array and plane, completion tracked by one mbarrier per
 // stage, four stages) while plane k is computed. Waits on those barriers are
 // bounded: a copy that never arrives sets an error word instead of hanging.
@@ -309,7 +309,7 @@ __host__ __device__ constexpr size_t em_stage_bytes() {
 #define COSIM_EM_STAGES 4
 #endif
 #ifndef COSIM_EM_AHEAD
-#define COSIM_EM_AHEAD 3
+#define COSIM_EM_AHEAD 2
 #endif
 #ifndef COSIM_EM_MIN_CTAS
 #define COSIM_EM_MIN_CTAS 2  // resident CTAs of 8 warps per SM the FP32 kernel is compiled for (scaled for other heights)
