@@ -329,6 +329,8 @@ __global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? (kThNP == 1 ? 3 :
   if (leader)
     for (int q = 0; q < kThAhead; ++q) issue(q);
   bool ok0 = mbar_wait(&bars[0], 0u);
+  // unrolled by the stage count: stage slots and carried sums resolve at compile time
+#pragma unroll 4
   for (int k = 0; k <= nz; ++k) {
     {  // plane k landed one iteration earlier (or above, for k = 0); wait for plane k+1
       const bool ok = (k + 1 > nz || mbar_wait(&bars[(k + 1) & (kThStages - 1)], (unsigned)((k + 1) / kThStages) & 1u)) && ok0;
