@@ -104,7 +104,8 @@ struct cosim_ctx {
   CUtensorMap tmV[2], tmV2[2];  // voxel IDs (x, y, z), boxes em_vox_box_x / em2_vox_box_x x (TY+1) x 1 per tile height
   int em_ty = kEmTY;   // EM tile height of FP32 plain steps
   int th_by = 0;       // thermal step kernel: 0 = TMA-staged tiles, 4/8/16 = classic block height
-  CUtensorMap thT[2], thP, thV;  // the TMA thermal kernel's T (per buffer), P and voxel boxes
+  CUtensorMap thT[2][2], thP[2], thV[2];  // the TMA thermal kernel's T (per tile width, buffer), P and voxel boxes
+  int th_np = 1;                           // node pairs per thread of the TMA thermal kernel (1 or 2)
   CUtensorMap mvU[3], mvM, mvV;  // the TMA matvec's boxes of the CG direction Pv, the constraint bits, voxels
   void *zt = nullptr;  // per node plane k: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1) (zero outside)
   int vpx = 0;         // voxel row pitch
@@ -316,9 +317,12 @@ static cudaError_t set_smem_limits() {
   if ((e = cudaFuncSetAttribute(hex8_matvec_tma_kernel<R, kMvTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 mvt)) != cudaSuccess)
     return e;
-  const int th = (int)(th_stage_offset<R>(kMaxMat) + kThStages * sizeof(ThStage<R>) + 128);
-  if ((e = cudaFuncSetAttribute(thermal_tma_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, th)) !=
-      cudaSuccess)
+  const int th1 = (int)(th_stage_offset<R>(kMaxMat) + kThStages * sizeof(ThStage<R, 1>) + 128);
+  const int th2 = (int)(th_stage_offset<R>(kMaxMat) + kThStages * sizeof(ThStage<R, 2>) + 128);
+  if ((e = cudaFuncSetAttribute(thermal_tma_kernel<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, th1)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(thermal_tma_kernel<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, th2)) !=
+          cudaSuccess)
     return e;
   if constexpr (sizeof(R) == 4) {
     const int em4 = (int)em_smem_bytes<R, kEmTYSmall>(kMaxMat);
@@ -552,9 +556,21 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
               COSIM_OK)
         return st;
   for (int p = 0; p < 2; ++p)
-    if ((st = encode_node_map(c, &c->thT[p], c->T[p], kThTY + 2, kThBoxT)) != COSIM_OK) return st;
-  if ((st = encode_node_map(c, &c->thP, c->P, kThTY, kThTX)) != COSIM_OK) return st;
-  if ((st = encode_voxel_map(c, &c->thV, kThTY + 1, kThBoxV)) != COSIM_OK) return st;
+    for (int q = 0; q < 2; ++q)
+      if ((st = encode_node_map(c, &c->thT[q][p], c->T[p], kThTY + 2, th_box_t(q + 1))) != COSIM_OK) return st;
+  for (int q = 0; q < 2; ++q) {
+    if ((st = encode_node_map(c, &c->thP[q], c->P, kThTY, th_tx(q + 1))) != COSIM_OK) return st;
+    if ((st = encode_voxel_map(c, &c->thV[q], kThTY + 1, th_box_v(q + 1))) != COSIM_OK) return st;
+  }
+  // two node pairs per thread once their grid fills the GPU about two and a
+  // half times at two CTAs per SM (measured crossover near 768 x 768 nodes);
+  // one pair (three CTAs per SM) on smaller grids
+  {
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long ctas2 = (long long)((c->nx + 1 + th_tx(2) - 1) / th_tx(2)) * ((c->ny + 1 + kThTY - 1) / kThTY);
+    c->th_np = ctas2 >= 5LL * nsm ? 2 : 1;
+  }
   ALLOC(c, c->scratch, c->npad * 8);
   const int mv_blocks = ((c->nx + 1) + kMvTX - 2) / (kMvTX - 1) * (((c->ny + 1) + kMvTY - 2) / (kMvTY - 1));
   c->npart = std::max(kRedBlocks, mv_blocks);
@@ -708,13 +724,19 @@ static cosim_status launch_thermal(cosim_ctx *c, R dt, bool count = true) {
   if (c->th_by == 0) {
     ThTmaArgs<R> T;
     T.a = A;
-    T.tmT = c->thT[c->tpar];
-    T.tmP = c->thP;
-    T.tmV = c->thV;
+    const int q = c->th_np - 1;
+    T.tmT = c->thT[q][c->tpar];
+    T.tmP = c->thP[q];
+    T.tmV = c->thV[q];
     T.err = c->dev_err;
-    const dim3 blk(32, kThTY), grd((c->nx + 1 + kThTX - 1) / kThTX, (c->ny + 1 + kThTY - 1) / kThTY);
-    const size_t smem = th_stage_offset<R>((int)c->mats.size()) + kThStages * sizeof(ThStage<R>) + 128;
-    thermal_tma_kernel<R><<<grd, blk, smem, c->stream>>>(T);
+    const dim3 blk(32, kThTY), grd((c->nx + 1 + th_tx(c->th_np) - 1) / th_tx(c->th_np), (c->ny + 1 + kThTY - 1) / kThTY);
+    if (c->th_np == 2) {
+      const size_t smem = th_stage_offset<R>((int)c->mats.size()) + kThStages * sizeof(ThStage<R, 2>) + 128;
+      thermal_tma_kernel<R, 2><<<grd, blk, smem, c->stream>>>(T);
+    } else {
+      const size_t smem = th_stage_offset<R>((int)c->mats.size()) + kThStages * sizeof(ThStage<R, 1>) + 128;
+      thermal_tma_kernel<R, 1><<<grd, blk, smem, c->stream>>>(T);
+    }
   } else {
     const dim3 blk(32, c->th_by), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + c->th_by - 1) / c->th_by);
     thermal_kernel<R, 0><<<grd, blk, (c->mats.size() + 1) * sizeof(typename Pair2<R>::T), c->stream>>>(A);

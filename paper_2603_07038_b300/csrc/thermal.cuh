@@ -229,9 +229,9 @@ __global__ void __launch_bounds__(512) thermal_kernel(const ThArgs<R> A) {  // b
   }
 }
 
-// ---- the same step with TMA-staged planes and kThNP node pairs per thread.
-// A CTA of 32 x kThTY threads owns a kThTX x kThTY tile of node columns
-// (thread tx: nodes i0 + 2 kThNP tx .. i0 + 2 kThNP tx + 2 kThNP - 1 of row
+// ---- the same step with TMA-staged planes and NP node pairs per thread.
+// A CTA of 32 x kThTY threads owns a th_tx(NP) x kThTY tile of node columns
+// (thread tx: nodes i0 + 2 NP tx .. i0 + 2 NP tx + 2 NP - 1 of row
 // j0 + ty; no halo compute: the update of a node reads only old
 // temperatures) and marches in z. Per plane one thread copies into shared
 // memory the temperature with a one-node halo (x from i0 - 4, the 16-byte
@@ -242,20 +242,19 @@ __global__ void __launch_bounds__(512) thermal_kernel(const ThArgs<R> A) {  // b
 // then remove). More nodes per thread share the per-plane waits, barrier and
 // addressing; each pair's arithmetic is the pair form of th_layer /
 // th_coeffs / th_update.
-#ifndef COSIM_TH_NP
-#define COSIM_TH_NP 2
-#endif
-constexpr int kThNP = COSIM_TH_NP;    // node pairs per thread
-constexpr int kThTY = 8, kThTX = 64 * kThNP;
+// NP node pairs per thread (1 or 2, chosen per grid: two pairs amortise the
+// per-plane work better, one pair keeps more CTAs in flight on small grids).
+constexpr int kThTY = 8;
 constexpr int kThStages = 4, kThAhead = 3;
-constexpr int kThBoxT = kThTX + 8;   // temperature box width: columns i0-4 .. i0+kThTX+3
-constexpr int kThBoxV = kThTX + 32;  // voxel box width: columns i0-16 .. i0+kThTX+15
-template <typename R>
+__host__ __device__ constexpr int th_tx(int np) { return 64 * np; }         // nodes per tile row
+__host__ __device__ constexpr int th_box_t(int np) { return 64 * np + 8; }  // T box: columns i0-4 .. i0+TX+3
+__host__ __device__ constexpr int th_box_v(int np) { return 64 * np + 32; } // voxel box: columns i0-16 .. i0+TX+15
+template <typename R, int NP>
 struct ThStage {
-  EmBox<R, kThTY + 2, kThBoxT> T;        // rows j0-1 .. j0+kThTY
-  EmBox<R, kThTY, kThTX> P;              // the tile's nodes
-  EmBox<uint8_t, kThTY + 1, kThBoxV> V;  // voxel rows j0-1 .. j0+kThTY-1
-  EmBox<R, 1, 4> Z;                      // hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
+  EmBox<R, kThTY + 2, th_box_t(NP)> T;        // rows j0-1 .. j0+kThTY
+  EmBox<R, kThTY, th_tx(NP)> P;               // the tile's nodes
+  EmBox<uint8_t, kThTY + 1, th_box_v(NP)> V;  // voxel rows j0-1 .. j0+kThTY-1
+  EmBox<R, 1, 4> Z;                           // hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
 };
 template <typename R>
 __host__ __device__ constexpr size_t th_stage_offset(int nmat) {
@@ -265,27 +264,27 @@ __host__ __device__ constexpr size_t th_stage_offset(int nmat) {
 template <typename R>
 struct ThTmaArgs {
   ThArgs<R> a;                // geometry, T in / out, P, z records, dt, films
-  CUtensorMap tmT, tmP, tmV;  // boxes kThBoxT x (kThTY+2), kThTX x kThTY, kThBoxV x (kThTY+1) (one plane)
+  CUtensorMap tmT, tmP, tmV;  // boxes th_box_t x (kThTY+2), th_tx x kThTY, th_box_v x (kThTY+1) (one plane)
   int *err;
 };
 
-template <typename R>
-__global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? (kThNP == 1 ? 3 : 2) : (kThNP == 1 ? 2 : 1))
+template <typename R, int NP>
+__global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? (NP == 1 ? 3 : 2) : (NP == 1 ? 2 : 1))
     thermal_tma_kernel(const __grid_constant__ ThTmaArgs<R> TA) {
   using R2 = typename Pair2<R>::T;
-  constexpr int NP = kThNP;
+  constexpr int kThTX = th_tx(NP), kThBoxT = th_box_t(NP), kThBoxV = th_box_v(NP);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const ThArgs<R> &A = TA.a;
   const Geo<R> &g = A.g;
   R2 *s_kc = reinterpret_cast<R2 *>(smem);
-  ThStage<R> *stg = reinterpret_cast<ThStage<R> *>(smem + th_stage_offset<R>(g.nmat));
+  ThStage<R, NP> *stg = reinterpret_cast<ThStage<R, NP> *>(smem + th_stage_offset<R>(g.nmat));
   __shared__ uint64_t bars[kThStages];
   __shared__ int s_abort;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const bool leader = tx == 0 && ty == 0;
   if (leader) {
-    bool ok = (smem_u32(stg) & 127u) == 0 && (sizeof(ThStage<R>) & 127u) == 0 && ((size_t)&TA.tmT & 63u) == 0 &&
+    bool ok = (smem_u32(stg) & 127u) == 0 && (sizeof(ThStage<R, NP>) & 127u) == 0 && ((size_t)&TA.tmT & 63u) == 0 &&
               ((size_t)&TA.tmP & 63u) == 0 && ((size_t)&TA.tmV & 63u) == 0;
     s_abort = ok ? 0 : 1;
     if (!ok) atomicExch(TA.err, 2);
@@ -305,7 +304,7 @@ __global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? (kThNP == 1 ? 3 :
   auto issue = [&](int k) {
     if (k > nz) return;
     const int s = k & (kThStages - 1);
-    ThStage<R> &S = stg[s];
+    ThStage<R, NP> &S = stg[s];
     mbar_arrive_expect_tx(&bars[s], stage_bytes);
     tma_load_3d(&S.T.v[0][0], &TA.tmT, i0 - 4, j0 - 1, k, &bars[s]);
     if (has_p) tma_load_3d(&S.P.v[0][0], &TA.tmP, i0, j0, k, &bars[s]);
@@ -350,8 +349,8 @@ __global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? (kThNP == 1 ? 3 :
       fence_proxy_async_smem();
       issue(k + kThAhead);
     }
-    const ThStage<R> &S0 = stg[k & (kThStages - 1)];
-    const ThStage<R> &S1 = stg[(k + 1) & (kThStages - 1)];
+    const ThStage<R, NP> &S0 = stg[k & (kThStages - 1)];
+    const ThStage<R, NP> &S1 = stg[(k + 1) & (kThStages - 1)];
     const R hz = S0.Z.v[0][0], ihz = S0.Z.v[0][1], hzm = S0.Z.v[0][3];
     // {k, rho_cp} of the voxels ia-1 .. ia+2NP-1 in rows j-1 (a) and j (b)
     R2 a[2 * NP + 1], b[2 * NP + 1];
