@@ -1306,7 +1306,7 @@ static cosim_status stress_solve_t(cosim_ctx *c, const cosim_stress_opts *o, cos
   const auto t0 = std::chrono::steady_clock::now();
   const Geo<R> g = make_geo<R>(c);
   const size_t smem = c->mats.size() * M_COLS * sizeof(R);
-  const dim3 blk(32, 8), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + 7) / 8, c->nz + 1);
+  const dim3 blk(32, 8), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + 7) / 8);  // node columns (the kernels march in z)
   R *const *U = (R *const *)c->U;
   R *const *F = (R *const *)c->F;
   R *const *D = (R *const *)c->Dinv;

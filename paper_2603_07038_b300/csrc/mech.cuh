@@ -492,6 +492,14 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
 //   beta = (3 lambda + 2 mu) alpha_L, dT trilinear from nodal T - T_ref; with the
 //   monomial coefficients t of dT, int dN_a/dx_c dT dV = V (2/h_c)(s_c/8)
 //   [t_0 + s_d1 t_d1/3 + s_d2 t_d2/3 + s_d1 s_d2 t_d1d2/9], (d1, d2) the other axes.
+//
+// A thread owns the node column (i, j) and marches k = 0..nz: the four
+// elements of layer k are formed once and give the node of plane k its terms
+// as their bottom corner (dz = 1) and the node of plane k+1 its terms as
+// their top corner (dz = 0, carried in registers), and the nodal dT of a
+// plane's 3 x 3 neighbourhood is read once and kept for the next layer. Each
+// node adds the same terms in the same order as an 8-element gather
+// (layer k-1 first, then layer k; dy, dx inner).
 template <typename R, int MODE>
 __global__ void __launch_bounds__(256) hex8_node_kernel(Geo<R> g, const uint8_t *mask, const R *T, R T_ref,
                                                          R *o0, R *o1, R *o2) {
@@ -501,53 +509,83 @@ __global__ void __launch_bounds__(256) hex8_node_kernel(Geo<R> g, const uint8_t 
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i > g.nx || j > g.ny) return;
-  R acc[3] = {0, 0, 0};
-  for (int dz = 0; dz < 2; ++dz)
-    for (int dy = 0; dy < 2; ++dy)
-      for (int dx = 0; dx < 2; ++dx) {
-        const int ei = i - 1 + dx, ej = j - 1 + dy, ek = k - 1 + dz;
-        const int m = g.cell(ei, ej, ek);
-        if (m < 0) continue;
-        const R h[3] = {g.h[0][ei], g.h[1][ej], g.h[2][ek]};
-        const R ih[3] = {g.ih[0][ei], g.ih[1][ej], g.ih[2][ek]};  // inverse sizes (no divisions)
-        const R V = h[0] * h[1] * h[2];
-        const R lam = s_mt[m * M_COLS + M_LAM], mu = s_mt[m * M_COLS + M_MU];
-        if (MODE == 0) {
-          const R lap = ih[0] * ih[0] + ih[1] * ih[1] + ih[2] * ih[2];
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  if (i > nx || j > ny) return;
+  // dT of node plane k (tp) and k+1 (tq) at (i-1+qx, j-1+qy), q = qx + 3 qy
+  R tp[9], tq[9];
+  auto load_plane = [&](int kk, R t9[9]) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-            acc[c] += (lam + mu) * V * (ih[c] * ih[c]) * (R(1) / R(9)) + mu * V * lap * (R(1) / R(9));
-        } else {
-          R t[8];
+    for (int q = 0; q < 9; ++q) {
+      const int ni = i - 1 + q % 3, nj = j - 1 + q / 3;
+      t9[q] = (ni >= 0 && ni <= nx && nj >= 0 && nj <= ny) ? T[g.nid(ni, nj, kk)] - T_ref : R(0);
+    }
+  };
+  if (MODE == 1) load_plane(0, tp);
+  R carry[3] = {0, 0, 0};  // top-corner terms of layer k-1 for the node of plane k
+  R *out[3] = {o0, o1, o2};
+  for (int k = 0; k <= nz; ++k) {
+    R acc[3] = {carry[0], carry[1], carry[2]};
+    carry[0] = carry[1] = carry[2] = R(0);
+    if (k < nz) {
+      if (MODE == 1) load_plane(k + 1, tq);
 #pragma unroll
-          for (int a = 0; a < 8; ++a)
-            t[a] = T[g.nid(ei + (a & 1), ej + ((a >> 1) & 1), ek + ((a >> 2) & 1))] - T_ref;
-          modal_fwd(t);
-          const R s[3] = {R(1 - 2 * dx), R(1 - 2 * dy), R(1 - 2 * dz)};  // node's corner signs
-          const int lin[3] = {1, 2, 4};
-          const R beta = s_mt[m * M_COLS + M_BETA];
+      for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const int d1 = (c + 1) % 3, d2 = (c + 2) % 3;
-            const R br = t[0] + s[d1] * t[lin[d1]] * (R(1) / R(3)) + s[d2] * t[lin[d2]] * (R(1) / R(3)) +
-                         s[d1] * s[d2] * t[lin[d1] | lin[d2]] * (R(1) / R(9));
-            // t holds 8x the monomial coefficients: fold 1/8 here
-            acc[c] += beta * V * (R(2) * ih[c]) * s[c] * R(0.125) * R(0.125) * br;
+        for (int dx = 0; dx < 2; ++dx) {
+          const int ei = i - 1 + dx, ej = j - 1 + dy;
+          const int m = g.cell(ei, ej, k);
+          if (m < 0) continue;
+          const R h[3] = {g.h[0][ei], g.h[1][ej], g.h[2][k]};
+          const R ih[3] = {g.ih[0][ei], g.ih[1][ej], g.ih[2][k]};  // inverse sizes (no divisions)
+          const R V = h[0] * h[1] * h[2];
+          const R lam = s_mt[m * M_COLS + M_LAM], mu = s_mt[m * M_COLS + M_MU];
+          if (MODE == 0) {
+            const R lap = ih[0] * ih[0] + ih[1] * ih[1] + ih[2] * ih[2];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              acc[c] += (lam + mu) * V * (ih[c] * ih[c]) * (R(1) / R(9)) + mu * V * lap * (R(1) / R(9));
+              carry[c] += (lam + mu) * V * (ih[c] * ih[c]) * (R(1) / R(9)) + mu * V * lap * (R(1) / R(9));
+            }
+          } else {
+            R t[8];  // corner a = (ax, ay, az): node (ei + ax, ej + ay, k + az)
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+              const int q = (dx + (a & 1)) + 3 * (dy + ((a >> 1) & 1));
+              t[a] = (a >> 2) ? tq[q] : tp[q];
+            }
+            modal_fwd(t);
+            const int lin[3] = {1, 2, 4};
+            const R beta = s_mt[m * M_COLS + M_BETA];
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz) {  // dz = 1: the node of plane k; dz = 0: the node of plane k+1
+              const R s[3] = {R(1 - 2 * dx), R(1 - 2 * dy), R(1 - 2 * dz)};  // node's corner signs
+              R *dst = dz ? acc : carry;
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                const int d1 = (c + 1) % 3, d2 = (c + 2) % 3;
+                const R br = t[0] + s[d1] * t[lin[d1]] * (R(1) / R(3)) + s[d2] * t[lin[d2]] * (R(1) / R(3)) +
+                             s[d1] * s[d2] * t[lin[d1] | lin[d2]] * (R(1) / R(9));
+                // t holds 8x the monomial coefficients: fold 1/8 here
+                dst[c] += beta * V * (R(2) * ih[c]) * s[c] * R(0.125) * R(0.125) * br;
+              }
+            }
           }
         }
-      }
-  const long long id = g.nid(i, j, k);
-  const uint8_t mk = mask[id];
-  R *out[3] = {o0, o1, o2};
+    }
+    const long long id = g.nid(i, j, k);
+    const uint8_t mk = mask[id];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const bool fixed = (mk >> c) & 1;
-    if (MODE == 0)
-      out[c][id] = fixed ? R(1) : R(1) / acc[c];
-    else
-      out[c][id] = fixed ? R(0) : acc[c];
+    for (int c = 0; c < 3; ++c) {
+      const bool fixed = (mk >> c) & 1;
+      if (MODE == 0)
+        out[c][id] = fixed ? R(1) : R(1) / acc[c];
+      else
+        out[c][id] = fixed ? R(0) : acc[c];
+    }
+    if (MODE == 1 && k < nz) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) tp[q] = tq[q];
+    }
   }
 }
 
