@@ -740,10 +740,22 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long n, const CgSca
 // x *= s for the three components (undoes the right-hand-side scaling)
 template <typename R>
 __global__ void __launch_bounds__(256) scale3_kernel(long long n, R *x0, R *x1, R *x2, R s) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-    x0[q] *= s;
-    x1[q] *= s;
-    x2[q] *= s;
+  const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  if constexpr (sizeof(R) == 4) {  // four nodes per access (n is a multiple of 4)
+    float4 *X[3] = {reinterpret_cast<float4 *>(x0), reinterpret_cast<float4 *>(x1), reinterpret_cast<float4 *>(x2)};
+    for (long long v = first; v < (n >> 2); v += stride)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float4 x = X[c][v];
+        x.x *= s, x.y *= s, x.z *= s, x.w *= s;
+        X[c][v] = x;
+      }
+  } else {
+    for (long long q = first; q < n; q += stride) {
+      x0[q] *= s;
+      x1[q] *= s;
+      x2[q] *= s;
+    }
   }
 }
 
@@ -868,8 +880,19 @@ __global__ void __launch_bounds__(256) add_correction_kernel(long long n, double
 // |u| per node
 template <typename R>
 __global__ void __launch_bounds__(256) umag_kernel(long long n, const R *u0, const R *u1, const R *u2, R *out) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
-    out[q] = sqrt(u0[q] * u0[q] + u1[q] * u1[q] + u2[q] * u2[q]);
+  const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  if constexpr (sizeof(R) == 4) {  // four nodes per access (n is a multiple of 4)
+    for (long long v = first; v < (n >> 2); v += stride) {
+      const float4 a = reinterpret_cast<const float4 *>(u0)[v], b = reinterpret_cast<const float4 *>(u1)[v],
+                   c = reinterpret_cast<const float4 *>(u2)[v];
+      reinterpret_cast<float4 *>(out)[v] = make_float4(sqrt(a.x * a.x + b.x * b.x + c.x * c.x),
+                                                       sqrt(a.y * a.y + b.y * b.y + c.y * c.y),
+                                                       sqrt(a.z * a.z + b.z * b.z + c.z * c.z),
+                                                       sqrt(a.w * a.w + b.w * b.w + c.w * c.w));
+    }
+  } else {
+    for (long long q = first; q < n; q += stride) out[q] = sqrt(u0[q] * u0[q] + u1[q] * u1[q] + u2[q] * u2[q]);
+  }
 }
 
 // Fixed-component bits of the built-in supports (bit c: component c held at
