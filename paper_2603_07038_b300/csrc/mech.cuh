@@ -649,40 +649,14 @@ __global__ void __launch_bounds__(256) cg_init_kernel(long long n, const R *f0, 
   // scale: a power of two that brings the right-hand side to order one
   // (exact: the iteration is then the unscaled one times that factor)
   double rz = 0, bb = 0;
-  const long long stride = (long long)gridDim.x * blockDim.x, first = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if constexpr (sizeof(R) == 4) {  // four nodes per access (n is a multiple of 4)
-    const R *F[3] = {f0, f1, f2}, *Dd[3] = {d0, d1, d2};
-    R *X[3] = {x0, x1, x2}, *Rr[3] = {r0, r1, r2}, *P[3] = {p0, p1, p2};
-    for (long long v = first; v < (n >> 2); v += stride) {
-      float4 a[3], z[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float4 f = reinterpret_cast<const float4 *>(F[c])[v], d = reinterpret_cast<const float4 *>(Dd[c])[v];
-        a[c] = make_float4(scale * f.x, scale * f.y, scale * f.z, scale * f.w);
-        z[c] = make_float4(d.x * a[c].x, d.y * a[c].y, d.z * a[c].z, d.w * a[c].w);
-        reinterpret_cast<float4 *>(X[c])[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-        reinterpret_cast<float4 *>(Rr[c])[v] = a[c];
-        reinterpret_cast<float4 *>(P[c])[v] = z[c];
-      }
-      rz += (double)(a[0].x * z[0].x + a[1].x * z[1].x + a[2].x * z[2].x);
-      rz += (double)(a[0].y * z[0].y + a[1].y * z[1].y + a[2].y * z[2].y);
-      rz += (double)(a[0].z * z[0].z + a[1].z * z[1].z + a[2].z * z[2].z);
-      rz += (double)(a[0].w * z[0].w + a[1].w * z[1].w + a[2].w * z[2].w);
-      bb += (double)(a[0].x * a[0].x + a[1].x * a[1].x + a[2].x * a[2].x);
-      bb += (double)(a[0].y * a[0].y + a[1].y * a[1].y + a[2].y * a[2].y);
-      bb += (double)(a[0].z * a[0].z + a[1].z * a[1].z + a[2].z * a[2].z);
-      bb += (double)(a[0].w * a[0].w + a[1].w * a[1].w + a[2].w * a[2].w);
-    }
-  } else {
-    for (long long q = first; q < n; q += stride) {
-      const R a0 = scale * f0[q], a1 = scale * f1[q], a2 = scale * f2[q];
-      const R z0 = d0[q] * a0, z1 = d1[q] * a1, z2 = d2[q] * a2;
-      x0[q] = 0; x1[q] = 0; x2[q] = 0;
-      r0[q] = a0; r1[q] = a1; r2[q] = a2;
-      p0[q] = z0; p1[q] = z1; p2[q] = z2;
-      rz += (double)(a0 * z0 + a1 * z1 + a2 * z2);
-      bb += (double)(a0 * a0 + a1 * a1 + a2 * a2);
-    }
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const R a0 = scale * f0[q], a1 = scale * f1[q], a2 = scale * f2[q];
+    const R z0 = d0[q] * a0, z1 = d1[q] * a1, z2 = d2[q] * a2;
+    x0[q] = 0; x1[q] = 0; x2[q] = 0;
+    r0[q] = a0; r1[q] = a1; r2[q] = a2;
+    p0[q] = z0; p1[q] = z1; p2[q] = z2;
+    rz += (double)(a0 * z0 + a1 * z1 + a2 * z2);
+    bb += (double)(a0 * a0 + a1 * a1 + a2 * a2);
   }
   rz = block_sum(rz);
   bb = block_sum(bb);
