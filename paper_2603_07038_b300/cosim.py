@@ -371,17 +371,43 @@ def cosim_destroy(ctx):
 
 
 def cosim_sum_f64_noalloc(x, n=None, out=None, stream=None):
-    """Sum of a CUDA float64 tensor without any device allocation by the library.
-    out: None (returns a Python float via host memory) or a CUDA float64 tensor
-    of one element that receives the sum on the device."""
+    """Sum of the first n elements of a CUDA float64 tensor without any device
+    allocation by the library.
+
+    x must be a contiguous float64 CUDA tensor and 0 <= n <= x.numel() (n
+    defaults to x.numel()); out is None (the sum is returned as a Python float
+    through host memory) or a float64 CUDA tensor on x's device that receives
+    the sum in its first element. The call runs on x's device and is ordered on
+    `stream`, by default the caller's current torch stream of that device, so
+    it sees the work already queued there. Every check runs before the library
+    is called: a tensor of another dtype, a strided view or an n beyond the
+    tensor would make the kernel read outside the caller's buffer."""
+    import torch
+
+    if x.dtype != torch.float64:
+        raise TypeError(f"cosim_sum_f64_noalloc: x must be float64, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError("cosim_sum_f64_noalloc: x must be contiguous")
     n = x.numel() if n is None else int(n)
-    s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
-    if out is None:
-        v = C.c_double()
-        _check(load().cosim_sum_f64_noalloc(x.data_ptr(), n, C.addressof(v), 0, s), None)
-        return v.value
-    _check(load().cosim_sum_f64_noalloc(x.data_ptr(), n, out.data_ptr(), 1, s), None)
-    return out
+    if not 0 <= n <= x.numel():
+        raise ValueError(f"cosim_sum_f64_noalloc: n = {n} outside [0, {x.numel()}]")
+    if not x.is_cuda:
+        raise ValueError("cosim_sum_f64_noalloc: x must be a CUDA tensor")
+    if out is not None:
+        if out.dtype != torch.float64 or not out.is_cuda or out.numel() < 1:
+            raise ValueError("cosim_sum_f64_noalloc: out must be a float64 CUDA tensor with at least one element")
+        if out.device != x.device:
+            raise ValueError("cosim_sum_f64_noalloc: out must be on x's device")
+    with torch.cuda.device(x.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        s = stream if isinstance(stream, int) else stream.cuda_stream
+        if out is None:
+            v = C.c_double()
+            _check(load().cosim_sum_f64_noalloc(x.data_ptr(), n, C.addressof(v), 0, s), None)
+            return v.value
+        _check(load().cosim_sum_f64_noalloc(x.data_ptr(), n, out.data_ptr(), 1, s), None)
+        return out
 
 
 # ---------------------------------------------------------------- convenience

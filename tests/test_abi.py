@@ -104,3 +104,20 @@ def test_null_handle_calls_are_invalid(lib):
     assert lib.cosim_read_fields_async(None, 0, 0, None, 0, 0) == api.COSIM_ERR_INVALID
     assert lib.cosim_wait_reads(None) == api.COSIM_ERR_INVALID
     lib.cosim_destroy(None)
+
+
+def test_noalloc_sum_wrapper_rejects_bad_tensors_before_the_call():
+    """the wrapper refuses, on the host, every tensor the kernel would read out
+    of bounds (wrong dtype, strided view, n past the end) or on the wrong
+    device, before it touches the library"""
+    import torch
+    with pytest.raises(TypeError):
+        api.cosim_sum_f64_noalloc(torch.zeros(8, dtype=torch.float32))
+    with pytest.raises(ValueError):
+        api.cosim_sum_f64_noalloc(torch.zeros(8, 2, dtype=torch.float64)[:, 0])
+    with pytest.raises(ValueError):
+        api.cosim_sum_f64_noalloc(torch.zeros(8, dtype=torch.float64), n=9)
+    with pytest.raises(ValueError):
+        api.cosim_sum_f64_noalloc(torch.zeros(8, dtype=torch.float64), n=-1)
+    with pytest.raises(ValueError):  # a host tensor
+        api.cosim_sum_f64_noalloc(torch.zeros(8, dtype=torch.float64))
