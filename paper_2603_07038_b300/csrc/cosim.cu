@@ -32,6 +32,9 @@ constexpr int kEmTX = 32, kEmTY = 8, kEmTYSmall = 4;
 constexpr int em_ty_index(int ty) { return ty == kEmTY ? 0 : 1; }
 constexpr int kMvTX = 32, kMvTY = 8;  // matvec tile
 constexpr int kRedBlocks = 1184;      // fixed grid of the vector kernels (8 x 148)
+// dynamic shared memory a kernel may opt in to: the 227 KB of a CTA less
+// 1 KB for its static shared variables
+constexpr size_t kMaxSmemOptin = 232448 - 1024;
 constexpr int kSrcPadLo = 4, kSrcPadHi = 16;  // zero ints around the source-row offsets
 thread_local std::string g_create_error;
 
@@ -106,7 +109,9 @@ struct cosim_ctx {
   int th_by = 0;       // thermal step kernel: 0 = TMA-staged tiles, 4/8/16 = classic block height
   CUtensorMap thT[2][2], thP[2], thV[2];  // the TMA thermal kernel's T (per tile width, buffer), P and voxel boxes
   int th_np = 1;                           // node pairs per thread of the TMA thermal kernel (1 or 2)
-  CUtensorMap mvU[3], mvM, mvV;  // the TMA matvec's boxes of the CG direction Pv, the constraint bits, voxels
+  // the TMA matvec's boxes: the two CG direction buffers (Pv, Pv2), the
+  // residual, the inverse diagonal, the constraint bits, the voxels
+  CUtensorMap mvU[2][3], mvR[3], mvD[3], mvM, mvV;
   void *zt = nullptr;  // per node plane k: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1) (zero outside)
   int vpx = 0;         // voxel row pitch
   int4 *src_ent = nullptr;
@@ -115,7 +120,7 @@ struct cosim_ctx {
   // mechanics (allocated on first use)
   bool mech_ready = false;
   uint8_t *mask = nullptr;
-  void *U[3]{}, *F[3]{}, *Rv[3]{}, *Pv[3]{}, *Qv[3]{}, *Dinv[3]{};
+  void *U[3]{}, *F[3]{}, *Rv[3]{}, *Pv[3]{}, *Pv2[3]{}, *Qv[3]{}, *Dinv[3]{};  // Pv2: the other direction buffer
   void *VM = nullptr, *UMAG = nullptr;
   CgScalars *cg = nullptr;
   // FP64 geometry (aliases of the tables above for FP64 contexts) and the
@@ -313,9 +318,12 @@ static cudaError_t set_smem_limits() {
                             (const void *)em_step_kernel<R, long long, kEmTX, kEmTY, true>};
   for (const void *k : kernels)
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, em)) != cudaSuccess) return e;
-  const int mvt = (int)(mv_stage_offset<R, kMvTY>(kMaxMat) + kMvStages * sizeof(MvStage<R, kMvTY>) + 128);
-  if ((e = cudaFuncSetAttribute(hex8_matvec_tma_kernel<R, kMvTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                mvt)) != cudaSuccess)
+  const int mvt = (int)std::min(mv_smem_bytes<R, kMvTY, false>(kMaxMat), kMaxSmemOptin);
+  const int mvd = (int)std::min(mv_smem_bytes<R, kMvTY, true>(kMaxMat), kMaxSmemOptin);
+  if ((e = cudaFuncSetAttribute(hex8_matvec_tma_kernel<R, kMvTY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                mvt)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(hex8_matvec_tma_kernel<R, kMvTY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                mvd)) != cudaSuccess)
     return e;
   const int th1 = (int)(th_stage_offset<R>(kMaxMat) + kThStages * sizeof(ThStage<R, 1>) + 128);
   const int th2 = (int)(th_stage_offset<R>(kMaxMat) + kThStages * sizeof(ThStage<R, 2>) + 128);
@@ -1120,6 +1128,7 @@ static cosim_status mech_alloc(cosim_ctx *c) {
     ALLOC(c, c->F[a], c->npad * c->rsz);
     ALLOC(c, c->Rv[a], c->npad * c->rsz);
     ALLOC(c, c->Pv[a], c->npad * c->rsz);
+    ALLOC(c, c->Pv2[a], c->npad * c->rsz);
     ALLOC(c, c->Qv[a], c->npad * c->rsz);
     ALLOC(c, c->Dinv[a], c->npad * c->rsz);
   }
@@ -1128,7 +1137,11 @@ static cosim_status mech_alloc(cosim_ctx *c) {
   ALLOC(c, c->cg, sizeof(CgScalars));
   cosim_status st;
   for (int a = 0; a < 3; ++a)
-    if ((st = encode_node_map(c, &c->mvU[a], c->Pv[a], kMvTY + 1, kMvElems + 4)) != COSIM_OK) return st;
+    if ((st = encode_node_map(c, &c->mvU[0][a], c->Pv[a], kMvTY + 1, kMvElems + 4)) != COSIM_OK ||
+        (st = encode_node_map(c, &c->mvU[1][a], c->Pv2[a], kMvTY + 1, kMvElems + 4)) != COSIM_OK ||
+        (st = encode_node_map(c, &c->mvR[a], c->Rv[a], kMvTY + 1, kMvElems + 4)) != COSIM_OK ||
+        (st = encode_node_map(c, &c->mvD[a], c->Dinv[a], kMvTY + 1, kMvElems + 4)) != COSIM_OK)
+      return st;
   {
     const cuuint64_t dims[3] = {(cuuint64_t)c->nx + 1, (cuuint64_t)c->ny + 1, (cuuint64_t)c->nz + 1};
     const cuuint64_t strides[2] = {(cuuint64_t)c->px, (cuuint64_t)c->plane};
@@ -1176,18 +1189,21 @@ static cosim_status matvec_g(cosim_ctx *c, const Geo<R> &g, void *const u[3], vo
   A.partial = partial;
   const dim3 blk(kMvTX, kMvTY);
   const dim3 grd((c->nx + 1 + kMvTX - 2) / (kMvTX - 1), (c->ny + 1 + kMvTY - 2) / (kMvTY - 1));
-  // the CG direction in the context precision has TMA descriptors: staged kernel
-  if (sizeof(R) == (size_t)c->rsz && u[0] == c->Pv[0] && u[1] == c->Pv[1] && u[2] == c->Pv[2]) {
-    MvTmaArgs<R> T;
+  // the CG direction buffers in the context precision have TMA descriptors: staged kernel
+  const int buf = (u[0] == c->Pv[0] && u[1] == c->Pv[1] && u[2] == c->Pv[2])    ? 0
+                  : (u[0] == c->Pv2[0] && u[1] == c->Pv2[1] && u[2] == c->Pv2[2]) ? 1
+                                                                                  : -1;
+  if (sizeof(R) == (size_t)c->rsz && buf >= 0) {
+    MvTmaArgs<R> T{};
     T.a = A;
-    for (int a = 0; a < 3; ++a) T.tmU[a] = c->mvU[a];
+    for (int a = 0; a < 3; ++a) T.tmU[a] = c->mvU[buf][a];
     T.tmM = c->mvM;
     T.tmV = c->mvV;
     T.zt = (const R *)c->zt;
     T.err = c->dev_err;
-    const size_t smem = mv_stage_offset<R, kMvTY>((int)c->mats.size()) + kMvStages * sizeof(MvStage<R, kMvTY>) + 128;
+    const size_t smem = mv_smem_bytes<R, kMvTY, false>((int)c->mats.size());
     const dim3 grd2((c->nx + 1 + kMvElems - 2) / (kMvElems - 1), (c->ny + 1 + kMvTY - 2) / (kMvTY - 1));
-    hex8_matvec_tma_kernel<R, kMvTY><<<grd2, blk, smem, c->stream>>>(T); ++c->launches;
+    hex8_matvec_tma_kernel<R, kMvTY, false><<<grd2, blk, smem, c->stream>>>(T); ++c->launches;
   } else {
     const size_t smem =
         ((size_t)c->mats.size() * M_COLS + 2 * 3 * (kMvTY + 1) * (kMvTX + 1) + 24 * kMvTY * kMvTX) * sizeof(R);
@@ -1200,6 +1216,44 @@ static cosim_status matvec_g(cosim_ctx *c, const Geo<R> &g, void *const u[3], vo
 template <typename R>
 static cosim_status matvec_t(cosim_ctx *c, void *const u[3], void *const y[3], double *partial) {
   return matvec_g<R>(c, make_geo<R>(c), u, y, partial);
+}
+
+// The PCG's fused direction update and product (hex8_matvec_tma_kernel, DIR):
+// p_new = D^-1 r + beta p_old with p_old in direction buffer `from` (Pv or
+// Pv2) and beta from the r.z pair of `parity`, written to the other buffer;
+// Qv = K p_new with the p.Kp partial sums. Needs the DIR stages in shared
+// memory (mv_dir_fits).
+template <typename R>
+static bool mv_dir_fits(const cosim_ctx *c) {
+  return mv_smem_bytes<R, kMvTY, true>((int)c->mats.size()) <= kMaxSmemOptin;
+}
+template <typename R>
+static cosim_status matvec_dir(cosim_ctx *c, int from, int parity, double *partial) {
+  void *const *pnew = from ? c->Pv : c->Pv2;
+  MvTmaArgs<R> T{};
+  T.a.g = make_geo<R>(c);
+  for (int a = 0; a < 3; ++a) {
+    T.a.u[a] = (const R *)pnew[a];
+    T.a.y[a] = (R *)c->Qv[a];
+    T.tmU[a] = c->mvU[from][a];
+    T.tmR[a] = c->mvR[a];
+    T.tmD[a] = c->mvD[a];
+    T.pn[a] = (R *)pnew[a];
+  }
+  T.a.mask = c->mask;
+  T.a.partial = partial;
+  T.tmM = c->mvM;
+  T.tmV = c->mvV;
+  T.sc = c->cg;
+  T.parity = parity;
+  T.zt = (const R *)c->zt;
+  T.err = c->dev_err;
+  const size_t smem = mv_smem_bytes<R, kMvTY, true>((int)c->mats.size());
+  const dim3 blk(kMvTX, kMvTY);
+  const dim3 grd((c->nx + 1 + kMvElems - 2) / (kMvElems - 1), (c->ny + 1 + kMvTY - 2) / (kMvTY - 1));
+  hex8_matvec_tma_kernel<R, kMvTY, true><<<grd, blk, smem, c->stream>>>(T); ++c->launches;
+  CHECK_LAUNCH(c);
+  return COSIM_OK;
 }
 
 // CTAs of the TMA matvec (the one the PCG uses: its p.Kp partial sums)
@@ -1216,7 +1270,8 @@ static cosim_status pcg_run(cosim_ctx *c, double rtol, int64_t maxit, int every,
   R *const *U = (R *const *)c->U;
   R *const *F = (R *const *)c->F;
   R *const *Rv = (R *const *)c->Rv;
-  R *const *Pv = (R *const *)c->Pv;
+  R *const *Pb[2] = {(R *const *)c->Pv, (R *const *)c->Pv2};  // the two direction buffers
+  R *const *Pv = Pb[0];
   R *const *Qv = (R *const *)c->Qv;
   R *const *D = (R *const *)c->Dinv;
   const long long n = c->npad;
@@ -1253,14 +1308,26 @@ static cosim_status pcg_run(cosim_ctx *c, double rtol, int64_t maxit, int every,
   *relres = bb > 0 ? 1.0 : 0.0;
   *converged = !(bb > 0);
   const int nmv = mv_blocks(c);
+  // from the second iteration on, the direction update p = D^-1 r + beta p
+  // runs inside the product (p alternates between the two buffers);
+  // otherwise (the stages do not fit) a separate pass updates p in place
+  const bool fuse = mv_dir_fits<R>(c);
+  int cur = 0;  // buffer of this iteration's direction (cg_init wrote Pv)
   while (bb > 0) {
     const int parity = (int)(it & 1);
-    void *pv[3] = {Pv[0], Pv[1], Pv[2]}, *qv[3] = {Qv[0], Qv[1], Qv[2]};
-    cosim_status st = matvec_t<R>(c, pv, qv, pa);
+    cosim_status st;
+    if (it == 0 || !fuse) {
+      void *pv[3] = {Pb[cur][0], Pb[cur][1], Pb[cur][2]}, *qv[3] = {Qv[0], Qv[1], Qv[2]};
+      st = matvec_t<R>(c, pv, qv, pa);
+    } else {
+      st = matvec_dir<R>(c, cur, parity ^ 1, pa);
+      cur ^= 1;
+    }
     if (st != COSIM_OK) return st;
+    R *const *P = Pb[cur];
     reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pa, nmv, &c->cg->pq); ++c->launches;
     cg_update_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, c->cg, parity, U[0], U[1], U[2], Rv[0], Rv[1], Rv[2],
-                                                           Pv[0], Pv[1], Pv[2], Qv[0], Qv[1], Qv[2], D[0], D[1],
+                                                           P[0], P[1], P[2], Qv[0], Qv[1], Qv[2], D[0], D[1],
                                                            D[2], pa, pb); ++c->launches;
     reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pa, kRedBlocks, &c->cg->rz[parity ^ 1]); ++c->launches;
     reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pb, kRedBlocks, &c->cg->rr); ++c->launches;
@@ -1278,9 +1345,11 @@ static cosim_status pcg_run(cosim_ctx *c, double rtol, int64_t maxit, int every,
       }
       if (it >= maxit) break;
     }
-    cg_direction_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, c->cg, parity, Pv[0], Pv[1], Pv[2], Rv[0], Rv[1],
-                                                              Rv[2], D[0], D[1], D[2]); ++c->launches;
-    CHECK_LAUNCH(c);
+    if (!fuse) {
+      cg_direction_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, c->cg, parity, Pv[0], Pv[1], Pv[2], Rv[0], Rv[1],
+                                                                Rv[2], D[0], D[1], D[2]); ++c->launches;
+      CHECK_LAUNCH(c);
+    }
   }
   *iters = it;
   if (scale != 1.0) {

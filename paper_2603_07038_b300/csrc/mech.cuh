@@ -284,49 +284,90 @@ __global__ void __launch_bounds__(TX *TY) hex8_matvec_kernel(const MvArgs<R> A) 
 // the voxel IDs of the element layer (80-byte rows from x rounded down to 16)
 // and the plane's z record into four mbarrier-tracked shared-memory stages
 // while the threads work on earlier planes. The element arithmetic is the
-// pair form of hex8_apply (packed FP32), the node sums those of
-// hex8_matvec_kernel, term for term (equal to FP32 rounding).
+// pair form of hex8_apply (packed FP32). The nodal forces are gathered
+// without a full shared-memory copy of the element forces: a node's two
+// elements along x are summed in the thread (node ea+1) or with the next
+// lane's element through a shuffle (node ea+2); the corners facing the row
+// below (y) go through a small shared array to the thread row that owns
+// that node row; the top corners of a layer stay in registers for the next
+// plane. The sums are grouped as in hex8_matvec_kernel, term for term (equal
+// to FP32 rounding).
+//
+// DIR: the Jacobi-PCG direction update p = D^-1 r + beta p_old (beta =
+// r.z / r.z of the previous iteration) is fused into the staging: the
+// residual, the inverse diagonal and the previous direction of each plane
+// are copied instead of p, the new direction of the whole staged box is
+// formed in shared memory once the plane has landed, the product uses it,
+// and the owners write it to the other direction buffer (p is
+// double-buffered: neighbouring CTAs still read the old one).
 constexpr int kMvStages = 4, kMvAhead = 3;
 constexpr int kMvElems = 64;  // elements per warp row
+template <typename R, int TY, bool DIR>
+struct MvStage;
 template <typename R, int TY>
-struct MvStage {
+struct MvStage<R, TY, false> {
   EmBox<R, TY + 1, kMvElems + 4> U[3];         // nodes X0 .. X0+64, Y0 .. Y0+TY (from x rounded to 4)
   EmBox<uint8_t, TY + 1, kMvElems + 16> M;     // constraint bits of the same nodes (from x rounded to 16)
   EmBox<uint8_t, TY, kMvElems + 16> V;         // voxel IDs of elements X0 .. X0+63, Y0 .. Y0+TY-1
   EmBox<R, 1, 4> Z;                            // hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
 };
 template <typename R, int TY>
+struct MvStage<R, TY, true> : MvStage<R, TY, false> {  // U: p_old as copied, then the new p
+  EmBox<R, TY + 1, kMvElems + 4> Rr[3];        // residual of the same nodes
+  EmBox<R, TY + 1, kMvElems + 4> Dd[3];        // inverse Jacobi diagonal of the same nodes
+};
+// shared memory: the material table, then the exchange array of the row
+// sums (6 pairs per thread), then the stages (128-byte aligned)
+template <typename R, int TY>
 __host__ __device__ constexpr size_t mv_stage_offset(int nmat) {
-  return (((size_t)(nmat + 1) * M_COLS + 24 * TY * kMvElems) * sizeof(R) + 127) & ~size_t(127);
+  return (((size_t)(nmat + 1) * M_COLS + 12 * TY * 32) * sizeof(R) + 127) & ~size_t(127);
 }
+template <typename R, int TY, bool DIR>
+__host__ __device__ constexpr size_t mv_smem_bytes(int nmat) {
+  return mv_stage_offset<R, TY>(nmat) + kMvStages * sizeof(MvStage<R, TY, DIR>) + 128;
+}
+
+struct CgScalars {  // device-resident scalars of the Jacobi-PCG, FP64
+  double rz[2];     // r.z of the current / next iteration (ping-pong by parity)
+  double pq;        // p.Kp
+  double rr;        // r.r
+  double bb;        // f.f
+};
 
 template <typename R>
 struct MvTmaArgs {
-  MvArgs<R> a;
+  MvArgs<R> a;                 // u: the staged input (DIR: the new direction), y, mask, partial sums of u.y
   CUtensorMap tmU[3], tmM, tmV;
+  CUtensorMap tmR[3], tmD[3];  // DIR: residual, inverse diagonal
+  R *pn[3];                    // DIR: the new direction, written at the owned nodes
+  const CgScalars *sc;         // DIR: beta = sc->rz[parity ^ 1] / sc->rz[parity]
+  int parity;
   const R *zt;
   int *err;
 };
 
-template <typename R, int TY>
+template <typename R, int TY, bool DIR>
 __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
     hex8_matvec_tma_kernel(const __grid_constant__ MvTmaArgs<R> TA) {
   using R2 = typename Pair2<R>::T;
-  constexpr int EX = kMvElems;
+  using Stage = MvStage<R, TY, DIR>;
+  constexpr int EX = kMvElems, BX = kMvElems + 4;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const MvArgs<R> &A = TA.a;
   const Geo<R> &g = A.g;
   R *s_mt = reinterpret_cast<R *>(smem);
-  R *sr = s_mt + (g.nmat + 1) * M_COLS;  // [24][TY][EX]
-  MvStage<R, TY> *stg = reinterpret_cast<MvStage<R, TY> *>(smem + mv_stage_offset<R, TY>(g.nmat));
+  // ay = 0 corner sums of each thread's node pair, [c * 2 + az][ty][tx], read by thread row ty - 1
+  R2 *s_lo = reinterpret_cast<R2 *>(s_mt + (g.nmat + 1) * M_COLS);
+  Stage *stg = reinterpret_cast<Stage *>(smem + mv_stage_offset<R, TY>(g.nmat));
   __shared__ uint64_t bars[kMvStages];
   __shared__ int s_abort;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const bool leader = tid == 0;
   if (leader) {
-    bool ok = (smem_u32(stg) & 127u) == 0 && (sizeof(MvStage<R, TY>) & 127u) == 0 &&
-              ((size_t)&TA.tmU[0] & 63u) == 0 && ((size_t)&TA.tmM & 63u) == 0 && ((size_t)&TA.tmV & 63u) == 0;
+    bool ok = (smem_u32(stg) & 127u) == 0 && (sizeof(Stage) & 127u) == 0 && ((size_t)&TA.tmU[0] & 63u) == 0 &&
+              ((size_t)&TA.tmM & 63u) == 0 && ((size_t)&TA.tmV & 63u) == 0 && ((size_t)&TA.tmR[0] & 63u) == 0 &&
+              ((size_t)&TA.tmD[0] & 63u) == 0;
     s_abort = ok ? 0 : 1;
     if (!ok) atomicExch(TA.err, 2);
     for (int q = 0; q < kMvStages; ++q) mbar_init(&bars[q], 1);
@@ -350,39 +391,73 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
   const R2 hx = {va ? g.h[0][ea] : R(1), vb ? g.h[0][ea + 1] : R(1)};
   const R2 ihx = {va ? g.ih[0][ea] : R(1), vb ? g.ih[0][ea + 1] : R(1)};
   const R2 hy = bc_<R2>(ey_ok ? g.h[1][ey] : R(1)), ihy = bc_<R2>(ey_ok ? g.ih[1][ey] : R(1));
-  const unsigned fixed_bytes =
-      (unsigned)(3 * (TY + 1) * (EX + 4) * (int)sizeof(R) + (TY + 1) * (EX + 16) + 4 * (int)sizeof(R));
+  const unsigned fixed_bytes = (unsigned)((DIR ? 9 : 3) * (TY + 1) * BX * (int)sizeof(R) + (TY + 1) * (EX + 16) +
+                                          4 * (int)sizeof(R));
   const unsigned vox_bytes = (unsigned)(TY * (EX + 16));
   auto issue = [&](int k) {
     if (k > nz) return;
     const int s = k % kMvStages;
-    MvStage<R, TY> &S = stg[s];
+    Stage &S = stg[s];
     mbar_arrive_expect_tx(&bars[s], fixed_bytes + (k < nz ? vox_bytes : 0u));
 #pragma unroll
     for (int c = 0; c < 3; ++c) tma_load_3d(&S.U[c].v[0][0], &TA.tmU[c], xu0, Y0, k, &bars[s]);
+    if constexpr (DIR) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        tma_load_3d(&S.Rr[c].v[0][0], &TA.tmR[c], xu0, Y0, k, &bars[s]);
+        tma_load_3d(&S.Dd[c].v[0][0], &TA.tmD[c], xu0, Y0, k, &bars[s]);
+      }
+    }
     tma_load_3d(&S.M.v[0][0], &TA.tmM, xm0, Y0, k, &bars[s]);
     if (k < nz) tma_load_3d(&S.V.v[0][0], &TA.tmV, xm0, Y0, k, &bars[s]);
     bulk_load(&S.Z.v[0][0], TA.zt + 4 * (size_t)k, 4 * sizeof(R), &bars[s]);
   };
-  auto sr_at = [&](int slot, int qy, int qx) -> R & { return sr[(slot * TY + qy) * EX + qx]; };
+  // DIR: the new direction of every staged node of plane kk, in place of the
+  // old one (positions outside the grid arrived as zeros and stay zero); the
+  // proxy fence orders these writes before the stage's next TMA fill
+  R beta = R(0);
+  if constexpr (DIR) beta = (R)(TA.sc->rz[TA.parity ^ 1] / TA.sc->rz[TA.parity]);
+  auto convert = [&](int kk) {
+    if constexpr (DIR) {
+      Stage &S = stg[kk % kMvStages];
+      for (int q = tid; q < (TY + 1) * BX; q += 32 * TY) {
+        const int qy = q / BX, qx = q - qy * BX;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          S.U[c].v[qy][qx] = fma_(S.Dd[c].v[qy][qx], S.Rr[c].v[qy][qx], mul_(beta, S.U[c].v[qy][qx]));
+      }
+      fence_proxy_async_smem();
+    }
+  };
   // u at box position (qy, qx) of a stage with its constrained components zeroed
-  auto u_at = [&](const MvStage<R, TY> &S, int c, int qy, int qx) -> R {
+  auto u_at = [&](const Stage &S, int c, int qy, int qx) -> R {
     const uint8_t mk = S.M.v[qy][qx - xr + xmr];
     return ((mk >> c) & 1) ? R(0) : S.U[c].v[qy][qx];
   };
   if (leader)
     for (int q = 0; q < kMvAhead; ++q) issue(q);
+  if constexpr (DIR) {
+    if (!mbar_wait(&bars[0], 0u)) s_abort = 1;  // plane 0 is converted before the loop
+    __syncthreads();
+    if (s_abort) {
+      if (leader) {
+        for (int q = 0; q < kMvAhead && q <= nz; ++q) mbar_wait(&bars[q % kMvStages], (unsigned)(q / kMvStages) & 1u);
+        atomicExch(TA.err, 1);
+      }
+      return;
+    }
+    convert(0);
+  }
   R2 acc[3] = {bc_<R2>(R(0)), bc_<R2>(R(0)), bc_<R2>(R(0))};
   double dot = 0.0;
   const int cu = 2 * tx + xr;  // element corner (ea, ey) column in the u boxes
-  const int c2 = min(2 * tx + 2, EX - 1);  // sr column of element ea + 2 (the last lane reads a valid, unused column)
   for (int k = 0; k < nz; ++k) {
     {
       bool ok = mbar_wait(&bars[k % kMvStages], (unsigned)(k / kMvStages) & 1u);
       ok = mbar_wait(&bars[(k + 1) % kMvStages], (unsigned)((k + 1) / kMvStages) & 1u) && ok;
       if (!ok) s_abort = 1;
     }
-    __syncthreads();  // planes k, k+1 landed; every thread is done with plane k-1 and with sr
+    __syncthreads();  // planes k, k+1 landed; every thread is done with plane k-1 and with s_lo
     if (s_abort) {
       if (leader) {
         for (int q = k; q <= k + kMvAhead && q <= nz; ++q)
@@ -395,8 +470,12 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
       fence_proxy_async_smem();
       issue(k + kMvAhead);
     }
-    const MvStage<R, TY> &S0 = stg[k % kMvStages];
-    const MvStage<R, TY> &S1 = stg[(k + 1) % kMvStages];
+    if constexpr (DIR) {
+      convert(k + 1);
+      __syncthreads();  // the new direction of plane k+1 is in place
+    }
+    const Stage &S0 = stg[k % kMvStages];
+    const Stage &S1 = stg[(k + 1) % kMvStages];
     R2 r[3][8];
     if (va || vb) {
       const int ma = va ? (int)S0.V.v[ty][2 * tx + xmr] : 0, mb = vb ? (int)S0.V.v[ty][2 * tx + 1 + xmr] : 0;
@@ -404,7 +483,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
       for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
-          const MvStage<R, TY> &S = (a >> 2) ? S1 : S0;
+          const Stage &S = (a >> 2) ? S1 : S0;
           const int qy = ty + ((a >> 1) & 1), qx = cu + (a & 1);
           r[c][a] = R2{u_at(S, c, qy, qx), u_at(S, c, qy, qx + 1)};
         }
@@ -421,25 +500,29 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
 #pragma unroll
         for (int a = 0; a < 8; ++a) r[c][a] = bc_<R2>(R(0));
     }
+    // corner a = ax + 2 ay + 4 az. Node A (ea+1) takes corner ax=1 of element
+    // ea and ax=0 of ea+1; node B (ea+2) ax=1 of ea+1 and ax=0 of the next
+    // lane's element ea+2. The ay=1 sums stay here (this row's nodes), the
+    // ay=0 sums go to the thread row below's nodes through s_lo.
+    R2 hi[3][2];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int a = 0; a < 8; ++a) stv_(&sr_at(c * 8 + a, ty, 2 * tx), r[c][a]);
+      for (int az = 0; az < 2; ++az) {
+        const int b = 4 * az;
+        const R n2 = __shfl_down_sync(0xffffffffu, r[c][b + 2].x, 1);
+        const R n0 = __shfl_down_sync(0xffffffffu, r[c][b + 0].x, 1);
+        hi[c][az] = add_(R2{r[c][b + 3].x, r[c][b + 3].y}, R2{r[c][b + 2].y, n2});
+        s_lo[((c * 2 + az) * TY + ty) * 32 + tx] = add_(R2{r[c][b + 1].x, r[c][b + 1].y}, R2{r[c][b + 0].y, n0});
+      }
     __syncthreads();
     if (oa || ob) {
       const long long id = g.nid(XA, Y, k);
       R part = 0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        // node A (ea+1) sums elements ea, ea+1 (sr columns 2tx, 2tx+1); node B (ea+2) ea+1, ea+2
-        const R2 bottom = add_(add_(R2{sr_at(c * 8 + 3, ty, 2 * tx), sr_at(c * 8 + 3, ty, 2 * tx + 1)},
-                                    R2{sr_at(c * 8 + 2, ty, 2 * tx + 1), sr_at(c * 8 + 2, ty, c2)}),
-                               add_(R2{sr_at(c * 8 + 1, ty + 1, 2 * tx), sr_at(c * 8 + 1, ty + 1, 2 * tx + 1)},
-                                    R2{sr_at(c * 8 + 0, ty + 1, 2 * tx + 1), sr_at(c * 8 + 0, ty + 1, c2)}));
-        const R2 top = add_(add_(R2{sr_at(c * 8 + 7, ty, 2 * tx), sr_at(c * 8 + 7, ty, 2 * tx + 1)},
-                                 R2{sr_at(c * 8 + 6, ty, 2 * tx + 1), sr_at(c * 8 + 6, ty, c2)}),
-                            add_(R2{sr_at(c * 8 + 5, ty + 1, 2 * tx), sr_at(c * 8 + 5, ty + 1, 2 * tx + 1)},
-                                 R2{sr_at(c * 8 + 4, ty + 1, 2 * tx + 1), sr_at(c * 8 + 4, ty + 1, c2)}));
+        const R2 bottom = add_(hi[c][0], s_lo[((c * 2) * TY + ty + 1) * 32 + tx]);
+        const R2 top = add_(hi[c][1], s_lo[((c * 2 + 1) * TY + ty + 1) * 32 + tx]);
         const uint8_t mka = S0.M.v[ty + 1][cu + 1 - xr + xmr], mkb = S0.M.v[ty + 1][cu + 2 - xr + xmr];
         const R ua = S0.U[c].v[ty + 1][cu + 1], ub = S0.U[c].v[ty + 1][cu + 2];
         const R2 sum = add_(acc[c], bottom);
@@ -447,10 +530,12 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
         if (oa) {
           A.y[c][id] = ya;
           part += ya * ua;
+          if constexpr (DIR) TA.pn[c][id] = ua;
         }
         if (ob) {
           A.y[c][id + 1] = yb;
           part += yb * ub;
+          if constexpr (DIR) TA.pn[c][id + 1] = ub;
         }
         acc[c] = top;
       }
@@ -458,7 +543,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
     }
   }
   if (oa || ob) {  // the top node plane: plane nz is still staged (nothing was issued after it)
-    const MvStage<R, TY> &S = stg[nz % kMvStages];
+    const Stage &S = stg[nz % kMvStages];
     const long long id = g.nid(XA, Y, nz);
     R part = 0;
 #pragma unroll
@@ -469,10 +554,12 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
       if (oa) {
         A.y[c][id] = ya;
         part += ya * ua;
+        if constexpr (DIR) TA.pn[c][id] = ua;
       }
       if (ob) {
         A.y[c][id + 1] = yb;
         part += yb * ub;
+        if constexpr (DIR) TA.pn[c][id + 1] = ub;
       }
     }
     dot += (double)part;
@@ -634,12 +721,6 @@ __global__ void __launch_bounds__(256) von_mises_kernel(Geo<R> g, const R *u0, c
 // Grid-stride with a fixed grid: the per-CTA partial sums, and therefore the
 // reductions, are deterministic. Dot products accumulate in FP64.
 
-struct CgScalars {  // device-resident scalars, FP64
-  double rz[2];     // r.z of the current / next iteration (ping-pong by parity)
-  double pq;        // p.Kp
-  double rr;        // r.r
-  double bb;        // f.f
-};
 
 template <typename R>
 __global__ void __launch_bounds__(256) cg_init_kernel(long long n, const R *f0, const R *f1, const R *f2,
