@@ -251,7 +251,9 @@ enum {
   COSIM_F_VM = 12,    /* von Mises stress [Pa], cell-sized */
   COSIM_F_UMAG = 13,  /* |u| [m], node-sized */
   COSIM_F_FX = 14, COSIM_F_FY = 15, COSIM_F_FZ = 16, /* thermal load [N], node-sized */
-  COSIM_NUM_FIELDS = 17
+  COSIM_F_DT = 17,    /* temperature rise T - T_init [K], node-sized: the stored state itself, so
+                         small rises keep their full precision (COSIM_F_T adds T_init) */
+  COSIM_NUM_FIELDS = 18
 };
 
 /* Copy one field into dst (dense layout above), converting to dtype
@@ -284,7 +286,7 @@ cosim_status cosim_wait_reads(cosim_ctx *ctx);
 
 /* Overwrite one field from src (same layout and size rules). Entries that are
  * not unknowns (edges beyond the last cell, tangential E on PEC walls) are
- * stored as zero. Writable: E, H, T, Q, P, UX..UZ. */
+ * stored as zero. Writable: E, H, T, DT, Q, P, UX..UZ. */
 cosim_status cosim_write_fields(cosim_ctx *ctx, int32_t field, int32_t dtype, const void *src, size_t bytes,
                                 int32_t src_is_device);
 

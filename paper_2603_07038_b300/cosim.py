@@ -25,7 +25,8 @@ COSIM_COUPLED_THERMAL = 2
 COSIM_JOULE_RESET, COSIM_JOULE_FINALIZE_AVG_POWER, COSIM_JOULE_FINALIZE_ENERGY = 0, 1, 2
 COSIM_MECH_CLAMPED_BOTTOM, COSIM_MECH_KINEMATIC_MOUNT, COSIM_MECH_MASK = 0, 1, 2
 (COSIM_F_EX, COSIM_F_EY, COSIM_F_EZ, COSIM_F_HX, COSIM_F_HY, COSIM_F_HZ, COSIM_F_T, COSIM_F_Q, COSIM_F_P,
- COSIM_F_UX, COSIM_F_UY, COSIM_F_UZ, COSIM_F_VM, COSIM_F_UMAG, COSIM_F_FX, COSIM_F_FY, COSIM_F_FZ) = range(17)
+ COSIM_F_UX, COSIM_F_UY, COSIM_F_UZ, COSIM_F_VM, COSIM_F_UMAG, COSIM_F_FX, COSIM_F_FY, COSIM_F_FZ,
+ COSIM_F_DT) = range(18)
 (COSIM_Q_DT_EM, COSIM_Q_DT_TH_LIMIT, COSIM_Q_STEP, COSIM_Q_BYTES_RESIDENT, COSIM_Q_JOULE_STEPS,
  COSIM_Q_N_CELLS, COSIM_Q_N_NODES, COSIM_Q_PRECISION, COSIM_Q_LAUNCHES, COSIM_Q_EM_TILE_Y,
  COSIM_Q_TH_BLOCK_Y) = range(11)

@@ -1558,7 +1558,7 @@ static void *field_ptr(cosim_ctx *c, int f, int *elem_bytes, bool *cells, bool *
   switch (f) {
     case COSIM_F_EX: case COSIM_F_EY: case COSIM_F_EZ: return c->E[c->par][f];
     case COSIM_F_HX: case COSIM_F_HY: case COSIM_F_HZ: return c->H[c->par][f - 3];
-    case COSIM_F_T: return c->T[c->tpar];
+    case COSIM_F_T: case COSIM_F_DT: return c->T[c->tpar];
     case COSIM_F_Q: *is_double = true; *elem_bytes = 8; return c->Q;
     case COSIM_F_P: return c->P;
     case COSIM_F_UX: case COSIM_F_UY: case COSIM_F_UZ: return c->mech_ready ? c->U[f - COSIM_F_UX] : nullptr;

@@ -429,11 +429,6 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
       fence_proxy_async_smem();
     }
   };
-  // u at box position (qy, qx) of a stage with its constrained components zeroed
-  auto u_at = [&](const Stage &S, int c, int qy, int qx) -> R {
-    const uint8_t mk = S.M.v[qy][qx - xr + xmr];
-    return ((mk >> c) & 1) ? R(0) : S.U[c].v[qy][qx];
-  };
   if (leader)
     for (int q = 0; q < kMvAhead; ++q) issue(q);
   if constexpr (DIR) {
@@ -480,13 +475,19 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
     if (va || vb) {
       const int ma = va ? (int)S0.V.v[ty][2 * tx + xmr] : 0, mb = vb ? (int)S0.V.v[ty][2 * tx + 1 + xmr] : 0;
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
+      for (int q = 0; q < 4; ++q) {  // corner rows (ay, az) = (q & 1, q >> 1): nodes cu .. cu + 2 of one staged row
+        const Stage &S = (q >> 1) ? S1 : S0;
+        const int qy = ty + (q & 1), mx = cu - xr + xmr;
+        const unsigned m0 = S.M.v[qy][mx], m1 = S.M.v[qy][mx + 1], m2 = S.M.v[qy][mx + 2];
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          const Stage &S = (a >> 2) ? S1 : S0;
-          const int qy = ty + ((a >> 1) & 1), qx = cu + (a & 1);
-          r[c][a] = R2{u_at(S, c, qy, qx), u_at(S, c, qy, qx + 1)};
+        for (int c = 0; c < 3; ++c) {
+          const R v0 = ((m0 >> c) & 1) ? R(0) : S.U[c].v[qy][cu];
+          const R v1 = ((m1 >> c) & 1) ? R(0) : S.U[c].v[qy][cu + 1];
+          const R v2 = ((m2 >> c) & 1) ? R(0) : S.U[c].v[qy][cu + 2];
+          r[c][2 * q] = R2{v0, v1};
+          r[c][2 * q + 1] = R2{v1, v2};
         }
+      }
       hex8_apply<R2, R>(r, R2{s_mt[ma * M_COLS + M_LAM], s_mt[mb * M_COLS + M_LAM]},
                         R2{s_mt[ma * M_COLS + M_MU], s_mt[mb * M_COLS + M_MU]}, hx, hy, bc_<R2>(S0.Z.v[0][0]), ihx,
                         ihy, bc_<R2>(S0.Z.v[0][1]));

@@ -39,6 +39,8 @@ def test_paper_setup_coupled_window(ref, precision, tol):
     assert field_rel_l2(Hg, o.H)[0] < tol
     assert rel_l2(ctx.read(api.COSIM_F_Q), o.Q) < 10 * tol
     assert rel_l2(ctx.read(api.COSIM_F_P), o.P) < 10 * tol
-    # temperature rises are ~1e-9 K in this short window: compare absolutely
-    assert np.abs(ctx.read(api.COSIM_F_T) - p.T_init - o.theta).max() < 1e-12 + 1e-3 * np.abs(o.theta).max()
+    # temperature rises are ~1e-9 K in this short window: compare the stored
+    # rise (COSIM_F_DT), which keeps its own precision, element by element
+    assert np.abs(o.theta).max() > 0
+    assert rel_l2(ctx.read(api.COSIM_F_DT), o.theta) < 10 * tol
     ctx.close()
