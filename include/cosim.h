@@ -127,9 +127,16 @@ cosim_status cosim_set_sources(cosim_ctx *ctx, int32_t n, const cosim_source *sr
  * area-weighted over the edge's voxels as for sigma0; forms the step's Joule
  * power P^{n+1} = D_sigma(T^n) ebar^2 per node (readable as COSIM_F_P, W);
  * and advances the temperature one forward-Euler step of Eq. 5 with the EM
- * time step and that power (convective faces included). Two launches per
- * step. Combines with COSIM_ACCUM_JOULE. */
+ * time step and that power (convective faces included). Two launches per step
+ * (the EM step, then the thermal step). Combines with COSIM_ACCUM_JOULE. */
 #define COSIM_COUPLED_THERMAL 2u
+/* Flag for cosim_em_steps (implies COSIM_COUPLED_THERMAL): the same coupled
+ * step in one launch, the EM kernel taking each node's thermal step once the
+ * node's power is complete. Equal to the two-launch form to rounding (the
+ * last share of the power enters the update separately). The paper has no
+ * counterpart; it is a launch-shape choice (the two-launch form measured
+ * faster on B300). */
+#define COSIM_COUPLED_FUSED 4u
 
 /* Advance the Maxwell system nsteps leapfrog steps (Eqs. 1-3 in E/H form):
  * H^{n+1/2} = H^{n-1/2} - dt/mu curl E^n;
@@ -140,8 +147,37 @@ cosim_status cosim_set_sources(cosim_ctx *ctx, int32_t n, const cosim_source *sr
  * zero on PEC walls. With COSIM_ACCUM_JOULE each step adds, for every edge,
  * sigma_e V_e ((E^n + E^{n+1})/2)^2 dt / 2 to the Joule energy of both end
  * nodes (P_total = D_sigma e^2, Sec. II-A). One kernel launch per step (two
- * with COSIM_COUPLED_THERMAL). flags: COSIM_ACCUM_JOULE, COSIM_COUPLED_THERMAL. */
+ * with COSIM_COUPLED_THERMAL). flags: COSIM_ACCUM_JOULE, COSIM_COUPLED_THERMAL,
+ * COSIM_COUPLED_FUSED. */
 cosim_status cosim_em_steps(cosim_ctx *ctx, int64_t nsteps, uint32_t flags);
+
+/* Peak of the coupled marching since the last reset of cosim_coupled_march. */
+typedef struct {
+  double T_max;   /* highest nodal temperature seen at a check step [K] (T_init if none) */
+  int64_t step;   /* the EM step count (as COSIM_Q_STEP) at that check step; -1 if none */
+  int64_t peaks;  /* check steps that set a new peak (each replaced the snapshot) */
+} cosim_peak_report;
+
+/* Synchronized marching with peak-temperature snapshots. Sec. IV-A takes the
+ * static mechanical solves at peak-temperature snapshots of the coupled
+ * electro-thermal marching (Sec. II-A); this call runs nsteps steps of
+ * cosim_em_steps(ctx, ., flags | COSIM_COUPLED_THERMAL) and, after every
+ * check_every-th step counted from the start of the call and after its last
+ * step, compares that step's maximum nodal temperature (a maximum over the
+ * owned nodes taken in the step kernel: deterministic, independent of
+ * arrival order) with the highest one recorded; a higher one replaces it,
+ * with the step count, and the whole temperature field is copied into the
+ * peak snapshot (COSIM_F_T_PEAK; cosim_stress_solve with temperature =
+ * COSIM_STRESS_T_PEAK takes its load from it). All on the device, no host
+ * synchronisation until rep (nullable) is filled at the end. reset != 0 (and
+ * the first call on a context) forgets the recorded peak first and sets the
+ * snapshot to the current temperature. flags: COSIM_ACCUM_JOULE and
+ * COSIM_COUPLED_FUSED (optional).
+ * Errors: COSIM_ERR_INVALID (nsteps < 0, check_every <= 0, unknown flags),
+ * COSIM_ERR_OOM (first call: 40 bytes + one node-sized field), COSIM_ERR_CUDA,
+ * COSIM_ERR_TIMEOUT (a bounded in-kernel wait expired). */
+cosim_status cosim_coupled_march(cosim_ctx *ctx, int64_t nsteps, uint32_t flags, int64_t check_every, int32_t reset,
+                                 cosim_peak_report *rep);
 
 /* Record nsteps EM steps (flags as for cosim_em_steps) into a CUDA graph held
  * by the context, without running them. nsteps must be a positive multiple of
@@ -211,7 +247,10 @@ typedef struct {
   int32_t refine;            /* 1: FP64 iterative refinement around the context-precision CG */
   double inner_rtol;         /* refine: relative tolerance of each inner CG solve (<= 0: 1e-4) */
   int32_t max_refine;        /* refine: outer step cap (<= 0: 30) */
+  int32_t temperature;       /* load from COSIM_STRESS_T_CURRENT (0) or COSIM_STRESS_T_PEAK (1): the peak
+                                snapshot of cosim_coupled_march (COSIM_ERR_INVALID if none was taken) */
 } cosim_stress_opts;
+enum { COSIM_STRESS_T_CURRENT = 0, COSIM_STRESS_T_PEAK = 1 };
 
 typedef struct {
   int64_t iters;             /* CG iterations (summed over inner solves when refining) */
@@ -253,7 +292,8 @@ enum {
   COSIM_F_FX = 14, COSIM_F_FY = 15, COSIM_F_FZ = 16, /* thermal load [N], node-sized */
   COSIM_F_DT = 17,    /* temperature rise T - T_init [K], node-sized: the stored state itself, so
                          small rises keep their full precision (COSIM_F_T adds T_init) */
-  COSIM_NUM_FIELDS = 18
+  COSIM_F_T_PEAK = 18, /* the peak snapshot of cosim_coupled_march [K], node-sized, read only */
+  COSIM_NUM_FIELDS = 19
 };
 
 /* Copy one field into dst (dense layout above), converting to dtype

@@ -22,11 +22,13 @@ COSIM_FP64, COSIM_FP32 = 0, 1
 COSIM_BC_PEC, COSIM_BC_PMC, COSIM_BC_CPML = 0, 1, 2
 COSIM_ACCUM_JOULE = 1
 COSIM_COUPLED_THERMAL = 2
+COSIM_COUPLED_FUSED = 4
 COSIM_JOULE_RESET, COSIM_JOULE_FINALIZE_AVG_POWER, COSIM_JOULE_FINALIZE_ENERGY = 0, 1, 2
 COSIM_MECH_CLAMPED_BOTTOM, COSIM_MECH_KINEMATIC_MOUNT, COSIM_MECH_MASK = 0, 1, 2
 (COSIM_F_EX, COSIM_F_EY, COSIM_F_EZ, COSIM_F_HX, COSIM_F_HY, COSIM_F_HZ, COSIM_F_T, COSIM_F_Q, COSIM_F_P,
  COSIM_F_UX, COSIM_F_UY, COSIM_F_UZ, COSIM_F_VM, COSIM_F_UMAG, COSIM_F_FX, COSIM_F_FY, COSIM_F_FZ,
- COSIM_F_DT) = range(18)
+ COSIM_F_DT, COSIM_F_T_PEAK) = range(19)
+COSIM_STRESS_T_CURRENT, COSIM_STRESS_T_PEAK = 0, 1
 (COSIM_Q_DT_EM, COSIM_Q_DT_TH_LIMIT, COSIM_Q_STEP, COSIM_Q_BYTES_RESIDENT, COSIM_Q_JOULE_STEPS,
  COSIM_Q_N_CELLS, COSIM_Q_N_NODES, COSIM_Q_PRECISION, COSIM_Q_LAUNCHES, COSIM_Q_EM_TILE_Y,
  COSIM_Q_TH_BLOCK_Y) = range(11)
@@ -36,7 +38,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 
 EXPORTED = ["cosim_create", "cosim_set_sources", "cosim_em_steps", "cosim_joule_accumulate",
             "cosim_thermal_steps", "cosim_stress_solve", "cosim_stress_apply", "cosim_read_fields",
             "cosim_write_fields", "cosim_query", "cosim_last_error", "cosim_destroy", "cosim_read_fields_async",
-            "cosim_wait_reads"]
+            "cosim_wait_reads", "cosim_coupled_march"]
 
 
 class CosimError(RuntimeError):
@@ -81,7 +83,12 @@ class cosim_options(C.Structure):
 class cosim_stress_opts(C.Structure):
     _fields_ = [("bc", C.c_int32), ("node_mask", C.POINTER(C.c_uint8)), ("T_ref", C.c_double),
                 ("rtol", C.c_double), ("maxit", C.c_int64), ("check_every", C.c_int32),
-                ("refine", C.c_int32), ("inner_rtol", C.c_double), ("max_refine", C.c_int32)]
+                ("refine", C.c_int32), ("inner_rtol", C.c_double), ("max_refine", C.c_int32),
+                ("temperature", C.c_int32)]
+
+
+class cosim_peak_report(C.Structure):
+    _fields_ = [("T_max", C.c_double), ("step", C.c_int64), ("peaks", C.c_int64)]
 
 
 class cosim_stress_report(C.Structure):
@@ -108,6 +115,8 @@ def load():
     L.cosim_set_sources.restype = st
     L.cosim_em_steps.argtypes = [P, C.c_int64, C.c_uint32]
     L.cosim_em_steps.restype = st
+    L.cosim_coupled_march.argtypes = [P, C.c_int64, C.c_uint32, C.c_int64, C.c_int32, C.POINTER(cosim_peak_report)]
+    L.cosim_coupled_march.restype = st
     L.cosim_em_graph_capture.argtypes = [P, C.c_int64, C.c_uint32]
     L.cosim_em_graph_capture.restype = st
     L.cosim_em_graph_launch.argtypes = [P, C.c_int64]
@@ -283,8 +292,11 @@ def _stress_opts(bc, node_mask, T_ref, rtol, maxit, check_every):
 
 def cosim_stress_solve(ctx, bc=COSIM_MECH_CLAMPED_BOTTOM, node_mask=None, T_ref=300.0, rtol=1e-9,
                        maxit=200000, check_every=32, allow_not_converged=False, refine=False, inner_rtol=0.0,
-                       max_refine=0):
+                       max_refine=0, temperature=COSIM_STRESS_T_CURRENT):
+    """temperature: COSIM_STRESS_T_CURRENT (the current field) or
+    COSIM_STRESS_T_PEAK (the peak snapshot of cosim_coupled_march)."""
     o, keep = _stress_opts(bc, node_mask, T_ref, rtol, maxit, check_every)
+    o.temperature = temperature
     o.refine = 1 if refine else 0
     o.inner_rtol = inner_rtol
     o.max_refine = max_refine
@@ -294,6 +306,15 @@ def cosim_stress_solve(ctx, bc=COSIM_MECH_CLAMPED_BOTTOM, node_mask=None, T_ref=
         _check(st, ctx)
     return dict(iters=rep.iters, relres=rep.relres, seconds=rep.seconds, status=st,
                 refine_steps=rep.refine_steps)
+
+
+def cosim_coupled_march(ctx, nsteps, check_every=1, accumulate_joule=True, reset=False, fused=False):
+    """nsteps synchronized electro-thermal steps with peak-temperature
+    snapshots every check_every steps; returns the peak report as a dict."""
+    r = cosim_peak_report()
+    flags = (COSIM_ACCUM_JOULE if accumulate_joule else 0) | (COSIM_COUPLED_FUSED if fused else 0)
+    _check(load().cosim_coupled_march(ctx, int(nsteps), flags, int(check_every), 1 if reset else 0, C.byref(r)), ctx)
+    return dict(T_max=r.T_max, step=r.step, peaks=r.peaks)
 
 
 def cosim_stress_apply(ctx, u, bc=COSIM_MECH_CLAMPED_BOTTOM, node_mask=None):
@@ -434,15 +455,19 @@ class Context:
     def set_sources(self, tables):
         cosim_set_sources(self.h, tables)
 
-    def em_steps(self, n, accumulate_joule=True, coupled=False):
+    def em_steps(self, n, accumulate_joule=True, coupled=False, fused=False):
         """coupled: the synchronized electro-thermal marching (sigma(T), a
-        thermal step with the EM dt after every EM step)."""
+        thermal step with the EM dt after every EM step); fused: that thermal
+        step inside the EM launch."""
         cosim_em_steps(self.h, n, (COSIM_ACCUM_JOULE if accumulate_joule else 0)
-                       | (COSIM_COUPLED_THERMAL if coupled else 0))
+                       | (COSIM_COUPLED_THERMAL if coupled else 0) | (COSIM_COUPLED_FUSED if fused else 0))
 
-    def em_graph_capture(self, n, accumulate_joule=True, coupled=False):
+    def coupled_march(self, n, check_every=1, accumulate_joule=True, reset=False, fused=False):
+        return cosim_coupled_march(self.h, n, check_every, accumulate_joule, reset, fused)
+
+    def em_graph_capture(self, n, accumulate_joule=True, coupled=False, fused=False):
         cosim_em_graph_capture(self.h, n, (COSIM_ACCUM_JOULE if accumulate_joule else 0)
-                               | (COSIM_COUPLED_THERMAL if coupled else 0))
+                               | (COSIM_COUPLED_THERMAL if coupled else 0) | (COSIM_COUPLED_FUSED if fused else 0))
 
     def em_graph_launch(self, count=1):
         cosim_em_graph_launch(self.h, count)

@@ -35,6 +35,7 @@ constexpr int kRedBlocks = 1184;      // fixed grid of the vector kernels (8 x 1
 // dynamic shared memory a kernel may opt in to: the 227 KB of a CTA less
 // 1 KB for its static shared variables
 constexpr size_t kMaxSmemOptin = 232448 - 1024;
+constexpr uint32_t kEmFlags = COSIM_ACCUM_JOULE | COSIM_COUPLED_THERMAL | COSIM_COUPLED_FUSED;
 constexpr int kSrcPadLo = 4, kSrcPadHi = 16;  // zero ints around the source-row offsets
 thread_local std::string g_create_error;
 
@@ -90,6 +91,13 @@ struct cosim_ctx {
   bool g_accum = false, g_coupled = false;
   int g_par = 0, g_tpar = 0;
   long long launches = 0;  // kernels launched by this context
+  // peak-temperature snapshots of the coupled marching (cosim_coupled_march):
+  // pk[5] (see peak_check_kernel), the snapshot of T at the recorded peak,
+  // the check interval (0: not tracking) and the step count tracking started at
+  unsigned long long *pk = nullptr;
+  void *T_peak = nullptr;
+  int64_t pk_check_every = 0;
+  long long pk_base = 0;
   double *Q = nullptr;      // Joule energy per node, FP64
   void *Qs = nullptr;       // short-window Joule accumulator (context precision)
   bool qs_dirty = false;    // Qs may hold energy not yet folded into Q
@@ -312,10 +320,12 @@ static cudaError_t set_smem_limits() {
       cudaFuncSetAttribute(hex8_matvec_kernel<R, kMvTX, kMvTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, mv);
   if (e != cudaSuccess) return e;
   const int em = (int)em_smem_bytes<R, kEmTY>(kMaxMat);
-  const void *kernels[4] = {(const void *)em_step_kernel<R, int, kEmTX, kEmTY, false>,
-                            (const void *)em_step_kernel<R, long long, kEmTX, kEmTY, false>,
-                            (const void *)em_step_kernel<R, int, kEmTX, kEmTY, true>,
-                            (const void *)em_step_kernel<R, long long, kEmTX, kEmTY, true>};
+  const void *kernels[6] = {(const void *)em_step_kernel<R, int, kEmTX, kEmTY, false, false>,
+                            (const void *)em_step_kernel<R, long long, kEmTX, kEmTY, false, false>,
+                            (const void *)em_step_kernel<R, int, kEmTX, kEmTY, true, false>,
+                            (const void *)em_step_kernel<R, long long, kEmTX, kEmTY, true, false>,
+                            (const void *)em_step_kernel<R, int, kEmTX, kEmTY, true, true>,
+                            (const void *)em_step_kernel<R, long long, kEmTX, kEmTY, true, true>};
   for (const void *k : kernels)
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, em)) != cudaSuccess) return e;
   const int mvt = (int)std::min(mv_smem_bytes<R, kMvTY, false>(kMaxMat), kMaxSmemOptin);
@@ -334,8 +344,8 @@ static cudaError_t set_smem_limits() {
     return e;
   if constexpr (sizeof(R) == 4) {
     const int em4 = (int)em_smem_bytes<R, kEmTYSmall>(kMaxMat);
-    const void *small[2] = {(const void *)em_step_kernel<R, int, kEmTX, kEmTYSmall, false>,
-                            (const void *)em_step_kernel<R, long long, kEmTX, kEmTYSmall, false>};
+    const void *small[2] = {(const void *)em_step_kernel<R, int, kEmTX, kEmTYSmall, false, false>,
+                            (const void *)em_step_kernel<R, long long, kEmTX, kEmTYSmall, false, false>};
     for (const void *k : small)
       if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, em4)) != cudaSuccess) return e;
   }
@@ -726,12 +736,13 @@ static ThArgs<R> th_args(cosim_ctx *c);
 // flipped here): th_by = 0 launches the TMA-staged kernel, 4/8/16 the classic
 // kernel with that block height. Every choice gives identical results.
 template <typename R>
-static cosim_status launch_thermal(cosim_ctx *c, R dt, bool count = true) {
+static cosim_status launch_thermal(cosim_ctx *c, R dt, bool count = true, unsigned long long *peak = nullptr) {
   ThArgs<R> A = th_args<R>(c);
   A.dt = dt;
-  if (c->th_by == 0) {
+  if (c->th_by == 0 || peak != nullptr) {  // (peak tracking: the TMA kernel, same bits as the others)
     ThTmaArgs<R> T;
     T.a = A;
+    T.peak = peak;
     const int q = c->th_np - 1;
     T.tmT = c->thT[q][c->tpar];
     T.tmP = c->thP[q];
@@ -754,18 +765,20 @@ static cosim_status launch_thermal(cosim_ctx *c, R dt, bool count = true) {
   return COSIM_OK;
 }
 
-template <typename R, typename I, int TY, bool CPL>
+template <typename R, typename I, int TY, bool CPL, bool TH = false>
 static void launch_em(const dim3 &grd, const dim3 &blk, size_t smem, cudaStream_t st, const EmArgs<R> &A) {
-  em_step_kernel<R, I, kEmTX, TY, CPL><<<grd, blk, smem, st>>>(A);
+  em_step_kernel<R, I, kEmTX, TY, CPL, TH><<<grd, blk, smem, st>>>(A);
 }
 
 // coupled: the synchronized marching of Sec. II-A (sigma(T^n) in the EM step,
-// then one thermal step with the EM dt and that step's Joule power).
+// then one thermal step with the EM dt and that step's Joule power); fused:
+// that thermal step inside the EM launch instead of a launch of its own.
 // probe: the autotuner's timing launches: every launch reads the current
 // E/H/CPML buffers and writes the spare ones, nothing else changes (no
 // parity flip, no accumulation, no counters), so the state stays as it was.
 template <typename R, int TY>
-static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool coupled, bool probe = false) {
+static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool coupled, bool fused = false,
+                                  bool probe = false) {
   constexpr int t = em_ty_index(TY);
   EmArgs<R> A;
   A.g = make_geo<R>(c);
@@ -848,9 +861,20 @@ static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool
     A.tmT2 = c->tmT2[t][c->tpar];
     A.Pout = (R *)c->P;
     A.inv_dt = (R)(1.0 / c->dt);
+    A.Tth = (R *)c->T[c->tpar ^ 1];
+    A.T_amb = (R)(c->T_amb - c->T_init);
+    for (int f = 0; f < 6; ++f) A.hconv[f] = (R)c->h_conv[f];
+    // peak tracking (cosim_coupled_march): the step's maximum rise on check steps
+    A.peak = (coupled && c->pk_check_every > 0 &&
+              ((c->step + 1 - c->pk_base) % c->pk_check_every == 0 || s == nsteps - 1))
+                 ? c->pk
+                 : nullptr;
     const bool small = c->npad < (1LL << 31);
     if constexpr (TY == kEmTY) {
-      if (coupled)
+      if (coupled && fused)
+        small ? launch_em<R, int, TY, true, true>(grd, blk, smem, c->stream, A)
+              : launch_em<R, long long, TY, true, true>(grd, blk, smem, c->stream, A);
+      else if (coupled)
         small ? launch_em<R, int, TY, true>(grd, blk, smem, c->stream, A)
               : launch_em<R, long long, TY, true>(grd, blk, smem, c->stream, A);
       else
@@ -863,10 +887,20 @@ static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool
     CHECK_LAUNCH(c);
     if (probe) continue;
     ++c->launches;
-    if (coupled) {  // T^{n+1} = T^n + dt/C (-M_kk T^n + P^{n+1}) with the EM dt (Eq. 5)
-      const cosim_status ts = launch_thermal<R>(c, (R)c->dt);
-      if (ts != COSIM_OK) return ts;
+    // coupled: the launch also took the thermal step T^{n+1} = T^n + dt/C
+    // (-M_kk T^n + P^{n+1}) with the EM dt (Eq. 5) into the other buffer
+    if (coupled) {
+      if (!fused) {  // the thermal step as its own launch (tracking the step's maximum on check steps)
+        const cosim_status ts = launch_thermal<R>(c, (R)c->dt, true, A.peak);
+        if (ts != COSIM_OK) return ts;
+      }
       c->tpar ^= 1;
+      if (A.peak != nullptr) {  // a check step: compare with the recorded peak, copy T if higher
+        peak_check_kernel<<<1, 1, 0, c->stream>>>(c->pk, c->step + 1); ++c->launches;
+        peak_snapshot_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(c->npad, c->pk, (const R *)c->T[c->tpar],
+                                                                   (R *)c->T_peak); ++c->launches;
+        CHECK_LAUNCH(c);
+      }
     }
     c->par ^= 1;
     c->step++;
@@ -884,18 +918,18 @@ static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool
 }
 
 template <typename R>
-static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum, bool coupled) {
+static cosim_status em_steps_t(cosim_ctx *c, int64_t nsteps, bool accum, bool coupled, bool fused) {
   if constexpr (sizeof(R) == 4)
-    if (!coupled && c->em_ty == kEmTYSmall) return em_steps_tile<R, kEmTYSmall>(c, nsteps, accum, coupled);
-  return em_steps_tile<R, kEmTY>(c, nsteps, accum, coupled);
+    if (!coupled && c->em_ty == kEmTYSmall) return em_steps_tile<R, kEmTYSmall>(c, nsteps, accum, false);
+  return em_steps_tile<R, kEmTY>(c, nsteps, accum, coupled, coupled && fused);
 }
 
-static cosim_status em_steps_any(cosim_ctx *c, int64_t nsteps, bool acc, bool coupled) {
+static cosim_status em_steps_any(cosim_ctx *c, int64_t nsteps, bool acc, bool coupled, bool fused = false) {
   // groups of at most 2^30 steps keep the per-launch offset an int
   while (nsteps > 0) {
     const int64_t n = std::min<int64_t>(nsteps, 1LL << 30);
     const cosim_status st =
-        c->prec == COSIM_FP64 ? em_steps_t<double>(c, n, acc, coupled) : em_steps_t<float>(c, n, acc, coupled);
+        c->prec == COSIM_FP64 ? em_steps_t<double>(c, n, acc, coupled, fused) : em_steps_t<float>(c, n, acc, coupled, fused);
     if (st != COSIM_OK) return st;
     nsteps -= n;
   }
@@ -904,9 +938,50 @@ static cosim_status em_steps_any(cosim_ctx *c, int64_t nsteps, bool acc, bool co
 
 extern "C" cosim_status cosim_em_steps(cosim_ctx *c, int64_t nsteps, uint32_t flags) {
   if (!c) return COSIM_ERR_INVALID;
-  if (nsteps < 0 || (flags & ~(COSIM_ACCUM_JOULE | COSIM_COUPLED_THERMAL)))
-    return fail(c, COSIM_ERR_INVALID, "bad nsteps or flags");
-  return em_steps_any(c, nsteps, flags & COSIM_ACCUM_JOULE, flags & COSIM_COUPLED_THERMAL);
+  if (nsteps < 0 || (flags & ~kEmFlags)) return fail(c, COSIM_ERR_INVALID, "bad nsteps or flags");
+  return em_steps_any(c, nsteps, flags & COSIM_ACCUM_JOULE, flags & (COSIM_COUPLED_THERMAL | COSIM_COUPLED_FUSED),
+                      flags & COSIM_COUPLED_FUSED);
+}
+
+static cosim_status check_device_wait(cosim_ctx *c);
+
+// image -> value of ordered_bits (host side)
+static double from_ordered(unsigned long long b) {
+  b = (b >> 63) ? (b & ~(1ull << 63)) : ~b;
+  double v;
+  std::memcpy(&v, &b, 8);
+  return v;
+}
+
+extern "C" cosim_status cosim_coupled_march(cosim_ctx *c, int64_t nsteps, uint32_t flags, int64_t check_every,
+                                            int32_t reset, cosim_peak_report *rep) {
+  if (!c) return COSIM_ERR_INVALID;
+  if (nsteps < 0 || check_every <= 0) return fail(c, COSIM_ERR_INVALID, "nsteps < 0 or check_every <= 0");
+  if (flags & ~kEmFlags) return fail(c, COSIM_ERR_INVALID, "unknown flags");
+  if (!c->pk) {
+    ALLOC(c, c->pk, 5 * sizeof(unsigned long long));
+    ALLOC(c, c->T_peak, c->npad * c->rsz);
+    reset = 1;
+  }
+  if (reset) {
+    CHECK_CUDA(c, cudaMemsetAsync(c->pk, 0, 5 * sizeof(unsigned long long), c->stream));
+    CHECK_CUDA(c, cudaMemcpyAsync(c->T_peak, c->T[c->tpar], c->npad * c->rsz, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  c->pk_check_every = check_every;
+  c->pk_base = c->step;
+  cosim_status st = em_steps_any(c, nsteps, (flags & COSIM_ACCUM_JOULE) != 0, true, (flags & COSIM_COUPLED_FUSED) != 0);
+  c->pk_check_every = 0;
+  if (st != COSIM_OK) return st;
+  if (rep) {
+    unsigned long long h[5];
+    CHECK_CUDA(c, cudaMemcpyAsync(h, c->pk, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+    if ((st = check_device_wait(c)) != COSIM_OK) return st;
+    rep->peaks = (int64_t)h[3];
+    rep->step = h[3] ? (int64_t)h[4] : -1;
+    rep->T_max = h[3] ? from_ordered(h[1]) + c->T_init : c->T_init;
+  }
+  return COSIM_OK;
 }
 
 static void drop_graph(cosim_ctx *c) {
@@ -918,7 +993,7 @@ static void drop_graph(cosim_ctx *c) {
 extern "C" cosim_status cosim_em_graph_capture(cosim_ctx *c, int64_t nsteps, uint32_t flags) {
   if (!c) return COSIM_ERR_INVALID;
   if (nsteps <= 0 || nsteps % kJouleWindow != 0 || nsteps > (1LL << 30) ||
-      (flags & ~(COSIM_ACCUM_JOULE | COSIM_COUPLED_THERMAL)))
+      (flags & ~kEmFlags))
     return fail(c, COSIM_ERR_INVALID, "graph steps must be a positive multiple of 32 (the Joule window), <= 2^30");
   if (c->stream == nullptr) return fail(c, COSIM_ERR_INVALID, "graph capture needs a non-default stream");
   const bool acc = flags & COSIM_ACCUM_JOULE;
@@ -932,9 +1007,9 @@ extern "C" cosim_status cosim_em_graph_capture(cosim_ctx *c, int64_t nsteps, uin
   const int par = c->par;
   const bool dirty = c->qs_dirty;
   CHECK_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  const bool cpl = flags & COSIM_COUPLED_THERMAL;
+  const bool cpl = flags & (COSIM_COUPLED_THERMAL | COSIM_COUPLED_FUSED);
   const int tpar = c->tpar;
-  cosim_status st = em_steps_any(c, nsteps, acc, cpl);
+  cosim_status st = em_steps_any(c, nsteps, acc, cpl, (flags & COSIM_COUPLED_FUSED) != 0);
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
   const long long captured = c->launches - launches;
@@ -1381,6 +1456,8 @@ static cosim_status stress_solve_t(cosim_ctx *c, const cosim_stress_opts *o, cos
   R *const *D = (R *const *)c->Dinv;
   const long long n = c->npad;
   const R Tref = (R)(o->T_ref - c->T_init);  // device T is the rise over T_init
+  // the temperature the load is taken from: the current field or the peak snapshot
+  const R *Tsrc = (const R *)(o->temperature == COSIM_STRESS_T_PEAK ? c->T_peak : c->T[c->tpar]);
   hex8_node_kernel<R, 0><<<grd, blk, smem, c->stream>>>(g, c->mask, nullptr, Tref, D[0], D[1], D[2]); ++c->launches;
   CHECK_LAUNCH(c);
   const double rtol = o->rtol > 0 ? o->rtol : 1e-9;
@@ -1391,8 +1468,7 @@ static cosim_status stress_solve_t(cosim_ctx *c, const cosim_stress_opts *o, cos
   bool converged = false;
   cosim_status result = COSIM_OK;
   if (!o->refine) {
-    hex8_node_kernel<R, 1><<<grd, blk, smem, c->stream>>>(g, c->mask, (const R *)c->T[c->tpar], Tref, F[0], F[1],
-                                                          F[2]); ++c->launches;
+    hex8_node_kernel<R, 1><<<grd, blk, smem, c->stream>>>(g, c->mask, Tsrc, Tref, F[0], F[1], F[2]); ++c->launches;
     CHECK_LAUNCH(c);
     cosim_status st = pcg_run<R>(c, rtol, maxit, every, &iters, &relres, &converged);
     if (st != COSIM_OK) return st;
@@ -1404,7 +1480,7 @@ static cosim_status stress_solve_t(cosim_ctx *c, const cosim_stress_opts *o, cos
     const Geo<double> g64 = make_geo64(c);
     const size_t smem64 = c->mats.size() * M_COLS * sizeof(double);
     double *T64 = (double *)c->scratch;  // temperature rise in FP64
-    const R *Tc = (const R *)c->T[c->tpar];
+    const R *Tc = Tsrc;
     cast3_kernel<R, double><<<kRedBlocks, 256, 0, c->stream>>>(n, Tc, Tc, Tc, T64, T64, T64); ++c->launches;
     hex8_node_kernel<double, 1><<<grd, blk, smem64, c->stream>>>(g64, c->mask, T64, o->T_ref - c->T_init, c->F64[0],
                                                                  c->F64[1], c->F64[2]); ++c->launches;
@@ -1455,7 +1531,7 @@ static cosim_status stress_solve_t(cosim_ctx *c, const cosim_stress_opts *o, cos
     c->err = o->refine ? "refinement did not reach rtol" : "CG reached maxit";
   }
   const dim3 grc((c->nx + 31) / 32, (c->ny + 7) / 8, c->nz);
-  von_mises_kernel<R><<<grc, blk, smem, c->stream>>>(g, U[0], U[1], U[2], (const R *)c->T[c->tpar], Tref, (R *)c->VM); ++c->launches;
+  von_mises_kernel<R><<<grc, blk, smem, c->stream>>>(g, U[0], U[1], U[2], Tsrc, Tref, (R *)c->VM); ++c->launches;
   umag_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, U[0], U[1], U[2], (R *)c->UMAG); ++c->launches;
   CHECK_LAUNCH(c);
   CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1472,6 +1548,10 @@ extern "C" cosim_status cosim_stress_solve(cosim_ctx *c, const cosim_stress_opts
   if (!c) return COSIM_ERR_INVALID;
   if (!o) return fail(c, COSIM_ERR_INVALID, "opts is NULL");
   if (c->nz < 1) return fail(c, COSIM_ERR_INVALID, "grid too thin");
+  if (o->temperature != COSIM_STRESS_T_CURRENT && o->temperature != COSIM_STRESS_T_PEAK)
+    return fail(c, COSIM_ERR_INVALID, "bad temperature source");
+  if (o->temperature == COSIM_STRESS_T_PEAK && !c->T_peak)
+    return fail(c, COSIM_ERR_INVALID, "no peak snapshot: run cosim_coupled_march first");
   cosim_status st = mech_alloc(c);
   if (st != COSIM_OK) return st;
   if ((st = upload_mask(c, o)) != COSIM_OK) return st;
@@ -1559,6 +1639,7 @@ static void *field_ptr(cosim_ctx *c, int f, int *elem_bytes, bool *cells, bool *
     case COSIM_F_EX: case COSIM_F_EY: case COSIM_F_EZ: return c->E[c->par][f];
     case COSIM_F_HX: case COSIM_F_HY: case COSIM_F_HZ: return c->H[c->par][f - 3];
     case COSIM_F_T: case COSIM_F_DT: return c->T[c->tpar];
+    case COSIM_F_T_PEAK: return c->T_peak;
     case COSIM_F_Q: *is_double = true; *elem_bytes = 8; return c->Q;
     case COSIM_F_P: return c->P;
     case COSIM_F_UX: case COSIM_F_UY: case COSIM_F_UZ: return c->mech_ready ? c->U[f - COSIM_F_UX] : nullptr;
@@ -1585,7 +1666,7 @@ static cosim_status pack_field(cosim_ctx *c, int32_t field, int32_t dtype, void 
     cosim_status fs = joule_flush(c);
     if (fs != COSIM_OK) return fs;
   }
-  const double add = field == COSIM_F_T ? c->T_init : 0.0;
+  const double add = (field == COSIM_F_T || field == COSIM_F_T_PEAK) ? c->T_init : 0.0;
   if (sdbl && dtype == COSIM_FP64) launch_pack<double, double>(c, src, out, cells, add);
   else if (sdbl) launch_pack<double, float>(c, src, out, cells, add);
   else if (dtype == COSIM_FP64) launch_pack<float, double>(c, src, out, cells, add);
@@ -1668,7 +1749,8 @@ extern "C" cosim_status cosim_wait_reads(cosim_ctx *c) {
 extern "C" cosim_status cosim_write_fields(cosim_ctx *c, int32_t field, int32_t dtype, const void *src, size_t bytes,
                                            int32_t src_is_device) {
   if (!c) return COSIM_ERR_INVALID;
-  if (field == COSIM_F_VM || field == COSIM_F_UMAG || (field >= COSIM_F_FX && field <= COSIM_F_FZ))
+  if (field == COSIM_F_VM || field == COSIM_F_UMAG || (field >= COSIM_F_FX && field <= COSIM_F_FZ) ||
+      field == COSIM_F_T_PEAK)
     return fail(c, COSIM_ERR_INVALID, "field is not writable");
   if (field >= COSIM_F_UX && field <= COSIM_F_UZ) {
     cosim_status st = mech_alloc(c);
@@ -1739,8 +1821,8 @@ static cosim_status autotune_t(cosim_ctx *c, int *em_ty, int *th_by) {
   // EM tile height (FP32 plain steps): probe launches leave the state as it is
   int best_ty = kEmTY;
   if constexpr (sizeof(R) == 4) {
-    const float t8 = time_ms([&](int n) { return em_steps_tile<R, kEmTY>(c, n, false, false, true); }, 5);
-    const float t4 = time_ms([&](int n) { return em_steps_tile<R, kEmTYSmall>(c, n, false, false, true); }, 5);
+    const float t8 = time_ms([&](int n) { return em_steps_tile<R, kEmTY>(c, n, false, false, false, true); }, 5);
+    const float t4 = time_ms([&](int n) { return em_steps_tile<R, kEmTYSmall>(c, n, false, false, false, true); }, 5);
     if (st == COSIM_OK && t4 < t8) best_ty = kEmTYSmall;
   }
   // thermal step kernel (TMA tiles, or the classic kernel with 4/8/16-row

@@ -42,6 +42,7 @@
 #include <cuda.h>  // CUtensorMap
 
 #include "common.cuh"
+#include "thermal.cuh"
 
 namespace cosim {
 
@@ -105,6 +106,15 @@ struct EmArgs {
   CUtensorMap tmT, tmT2;
   R *Pout;
   R inv_dt;
+  // the thermal step of the coupled path (Eq. 5 with the EM dt), fused into
+  // the same launch: T^{n+1} - T_init written to Tth (the other temperature
+  // buffer); T_amb as a rise over T_init; per-face film coefficients; the
+  // maximum of the written rises goes to *peak as an order-preserving
+  // integer image (null: not tracked)
+  R *Tth;
+  R T_amb;
+  R hconv[6];
+  unsigned long long *peak;
   const R *zt;      // per node plane: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
   int *err;         // set to 1 when a bounded wait for a staged plane gave up
 };
@@ -247,11 +257,40 @@ __device__ __forceinline__ V h_update(V h_old, V hd, V ha, V ua, V hb, V ub, V c
   return fma_(neg_(mul_(hd, fma_(ha, ua, mul_(hb, ub)))), curl, h_old);
 }
 
-// sigma dt/2 of a voxel at the edge temperature rise te (coupled steps):
-// sigma0 dt/2 / (1 + alpha (T_init + te - T0)) = M_SDT2 / (M_TC0 + M_TCR te)
+// The sum over an edge's four voxels of w_c sigma_c(T) dt/2, with a_c = w_c
+// M_SDT2_c and d_c = M_TC0_c + M_TCR_c te, over a common denominator so that
+// one reciprocal serves the edge instead of one per voxel:
+//   sum a_c / d_c = ((a1 d2 + a2 d1) d3 d4 + (a3 d4 + a4 d3) d1 d2) / (d1 d2 d3 d4).
+// (Every d_c is positive: 1 for temperature-independent materials and for the
+// zero row that stands for voxels outside the grid.)
 template <typename V>
-__device__ __forceinline__ V sig_t(V sdt2, V tcr, V tc0, V te) {
-  return mul_(sdt2, rcp_(fma_(tcr, te, tc0)));
+__device__ __forceinline__ V sig_sum4(V a1, V d1, V a2, V d2, V a3, V d3, V a4, V d4) {
+  const V p12 = mul_(d1, d2), p34 = mul_(d3, d4);
+  const V n12 = fma_(a1, d2, mul_(a2, d1)), n34 = fma_(a3, d4, mul_(a4, d3));
+  return mul_(fma_(n12, p34, mul_(n34, p12)), rcp_(mul_(p12, p34)));
+}
+
+// Peak-temperature snapshots of the coupled marching. pk[0]: the maximum
+// rise of the current check step (image); pk[1]: the highest recorded; pk[2]:
+// 1 if the check step set a new peak; pk[3]: the number of peaks recorded;
+// pk[4]: the step count of the recorded peak.
+__global__ void peak_check_kernel(unsigned long long *pk, long long step) {
+  const bool up = pk[0] > pk[1];
+  if (up) {
+    pk[1] = pk[0];
+    pk[3] += 1;
+    pk[4] = (unsigned long long)step;
+  }
+  pk[2] = up ? 1ull : 0ull;
+  pk[0] = 0;  // the smallest image: the next check step starts afresh
+}
+// copy the temperature field into the snapshot when the check set a new peak
+template <typename R>
+__global__ void __launch_bounds__(256) peak_snapshot_kernel(long long n, const unsigned long long *pk, const R *T,
+                                                            R *Tpk) {
+  if (pk[2] == 0) return;
+  const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  for (long long q = first; q < n; q += stride) Tpk[q] = T[q];
 }
 
 // derivative (b - a) / h
@@ -355,7 +394,7 @@ __device__ __forceinline__ void em_abort(uint64_t *bars, int k, int nz, int *err
 // + ty). Nodes outside the grid, on the walls and inside the CPML slabs are
 // all handled here. XS / YS: the tile may hold nodes of an x / y slab (when
 // false, that axis's CPML code is left out of the instantiation).
-template <typename R, typename I, int TY, bool CPL, bool XS, bool YS>
+template <typename R, typename I, int TY, bool CPL, bool TH, bool XS, bool YS>
 __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
                                                EmStage<R, 32, TY> *stg, R (*sHxz)[2][TY][32], R (*sQy)[TY][32],
                                                uint64_t *bars, int *s_abort, int xs, int xe, int by) {
@@ -496,8 +535,75 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
   R pxe_b = 0, pxs_b = 0, pye_b = 0, pys_b = 0, u11_b = 0;
   R q_pend = 0;  // Joule sum of node (i, j, k-1) still missing the y-edge share from j-1
   R e_pend = 0;  // the same without the accumulator's earlier energy (this step's only)
-  int b01 = vd, b10 = vd, b11 = vd;  // coupled steps: material rows of layer k-1
-  auto sig = [&](int row, R te) -> R { return sig_t(s_mt[row + M_SDT2], s_mt[row + M_TCR], s_mt[row + M_TC0], te); };
+  int b00 = vd, b01 = vd, b10 = vd, b11 = vd;  // coupled steps: material rows of layer k-1
+  // coupled steps: sigma dt/2 of voxel `row` (returned) and its denominator
+  // M_TC0 + M_TCR te (in d), for sig_sum4
+  auto sgd = [&](int row, R te, R &d) -> R {
+    d = fma_(s_mt[row + M_TCR], te, s_mt[row + M_TC0]);
+    return s_mt[row + M_SDT2];
+  };
+  // TH (coupled steps with the thermal step in the same launch): node (i, j,
+  // k-1) takes its step at the start of plane k, from plane k-1's stage
+  // (still resident until plane k's barrier: its temperatures and z record),
+  // T at plane k, the layer sums of voxel layer k-2 (carried) and k-1 (rows
+  // b), and its Joule energy of the step without the y-edge share of row j-1;
+  // that share becomes visible with plane k's barrier and completes T^{n+1}
+  // and P^{n+1}. The node column's constants (th_column) come from the tile's
+  // own geometry: only the lateral film and the inverse sizes of cells i-1,
+  // j-1 are kept.
+  static_assert(CPL || !TH, "the fused thermal step belongs to coupled steps");
+  R fxy_th = 0, ihxm_th = 0, ihym_th = 0;
+  if (TH) {
+    const ThCol<R> c0 = th_column_h(g, A.hconv, i, j);
+    fxy_th = c0.fxy;
+    ihxm_th = (act && i > 0) ? g.ih[0][i - 1] : R(0);
+    ihym_th = (act && j > 0) ? g.ih[1][j - 1] : R(0);
+  }
+  auto tcol_of = [&]() -> ThCol<R> {
+    ThCol<R> c;
+    c.hxm = hxm, c.hx0 = hx0, c.hym = hym, c.hy0 = hy0;
+    c.qxm = mul_(R(0.25), ihxm_th), c.qx0 = mul_(R(0.25), ihx);
+    c.qym = mul_(R(0.25), ihym_th), c.qy0 = mul_(R(0.25), ihy);
+    c.fxy = fxy_th;
+    c.az = mul_(R(0.25), mul_(add_(hxm, hx0), add_(hym, hy0)));
+    return c;
+  };
+  ThLayer<R> tl_lo = th_layer_zero<R, R>();  // sums of voxel layer k-2
+  R th_m2 = 0, gz_th = 0;                    // T of (i, j, k-2); the conductance of the z edge below node k-1
+  R t_max = R(-3.0e38);
+  // the thermal step of node (i, j, kk) from plane kk's stage Sm (its
+  // temperatures and z record), T at plane kk+1 (tkp), the layer sums of voxel
+  // layers kk-1 (tl_lo) and kk (up), and the step's power without the y-edge
+  // share of row j-1 (e_pend): returns T + dt/C (flux + P_partial) in tpart and
+  // dt/C in dtc; the share is added once the plane's barrier has made it visible
+  auto th_partial = [&](const EmStage<R, TX, TY> &Sm, int kk, const ThLayer<R> &up, R tkp, R &tpart, R &dtc) {
+    const int cx = tx + xr;
+    const ThCoeffs<R> q = th_coeffs<R, R>(tcol_of(), tl_lo, up, Sm.Z.v[0][0], Sm.Z.v[0][1], Sm.Z.v[0][3], kk == 0,
+                                          kk == nz, A.hconv, gz_th);
+    const R tc = Sm.T.v[ty][cx];
+    if (own) {
+      dtc = mul_(A.dt, rcp_(q.C));
+      const R p = mul_(e_pend, A.inv_dt);
+      R f = fma_(q.Gxm, sub_(Sm.T.v[ty][cx - 1], tc), p);  // owners: tx, ty >= 1, so cx - 1, ty - 1 exist
+      f = fma_(q.Gxp, sub_(Sm.T.v[ty][cx + 1], tc), f);
+      f = fma_(q.Gym, sub_(Sm.T.v[ty - 1][cx], tc), f);
+      f = fma_(q.Gyp, sub_(Sm.T.v[ty + 1][cx], tc), f);
+      f = fma_(q.Gzm, sub_(th_m2, tc), f);
+      f = fma_(q.Gzp, sub_(tkp, tc), f);
+      f = fma_(q.film, sub_(A.T_amb, tc), f);
+      tpart = fma_(dtc, f, tc);
+    }
+    th_m2 = tc;
+    tl_lo = up;
+  };
+  // the share of row j-1 (energy) completes node kk's step and power
+  auto th_finish = [&](I idn, R share, R tpart, R dtc) {
+    const R pw = mul_(add_(e_pend, share), A.inv_dt);
+    A.Pout[idn] = pw;
+    const R tn = fma_(dtc, mul_(share, A.inv_dt), tpart);
+    A.Tth[idn] = tn;
+    t_max = fmax(t_max, tn);
+  };
 
   for (int k = 0; k <= nz; ++k) {
     if (leader) {  // the stage of plane k-1 is free: every thread passed the last barrier
@@ -537,11 +643,18 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
     const R q_old = accum ? S0.Qs.v[ty][cx] : R(0);
     // coupled steps: temperature rise at this node and its +x, +y, +z neighbours
     R th = 0, th_ip = 0, th_jp = 0, th_kp = 0;
+    R t_part = 0, t_dtc = 0;  // node (i, j, k-1)'s thermal step without the y-edge share of row j-1
     if (CPL) {
       th = S0.T.v[ty][cx];
       th_ip = S0.T.v[ty][cx + 1];
       th_jp = S0.T.v[ty + 1][cx];
       th_kp = kz ? S1.T.v[ty][cx] : R(0);
+      if (TH && k > 0) {  // plane k-1's stage is resident until this plane's barrier
+        const ThLayer<R> up = th_layer<R>(s_mt[b00 + M_K], s_mt[b01 + M_K], s_mt[b10 + M_K], s_mt[b11 + M_K],
+                                          s_mt[b00 + M_RHOCP], s_mt[b01 + M_RHOCP], s_mt[b10 + M_RHOCP],
+                                          s_mt[b11 + M_RHOCP], tcol_of());
+        th_partial(stg[(k - 1) & (kEmStages - 1)], k - 1, up, th, t_part, t_dtc);
+      }
     }
 
     // material constants of voxel layer k
@@ -616,7 +729,8 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
         A.Qs[id - plane] = s;
       }
     }
-    if (CPL && own && k > 0) A.Pout[id - plane] = mul_(add_(e_pend, sQy[par ^ 1][ty - 1][tx]), A.inv_dt);
+    if (TH && own && k > 0) th_finish(id - plane, sQy[par ^ 1][ty - 1][tx], t_part, t_dtc);
+    if (CPL && !TH && own && k > 0) A.Pout[id - plane] = mul_(add_(e_pend, sQy[par ^ 1][ty - 1][tx]), A.inv_dt);
 
     // ---- source current on this node's edges (three scalars selected by
     // axis: a dynamically indexed array would live in local memory)
@@ -644,8 +758,10 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
       R Ss = fma_(hzm, pxs_b, mul_(hz0, pxs_a));
       if (CPL) {
         const R te = mul_(R(0.5), add_(th, th_ip));
-        Ss = fma_(hzm, fma_(hym, sig(b01, te), mul_(hy0, sig(b11, te))),
-                  mul_(hz0, fma_(hym, sig(a01, te), mul_(hy0, sig(a11, te)))));
+        R d1, d2, d3, d4;
+        const R a1 = mul_(mul_(hzm, hym), sgd(b01, te, d1)), a2 = mul_(mul_(hzm, hy0), sgd(b11, te, d2));
+        const R a3 = mul_(mul_(hz0, hym), sgd(a01, te, d3)), a4 = mul_(mul_(hz0, hy0), sgd(a11, te, d4));
+        Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
       }
       exn = e_update<R, R>(ex, mul_(dtWx_y, add_(hzm, hz0)), sub_(curl, Jx), fma_(hzm, pxe_b, mul_(hz0, pxe_a)), Ss,
                            lqx, &qx);
@@ -655,8 +771,10 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
       R Ss = fma_(hzm, pys_b, mul_(hz0, pys_a));
       if (CPL) {
         const R te = mul_(R(0.5), add_(th, th_jp));
-        Ss = fma_(hzm, fma_(hxm, sig(b10, te), mul_(hx0, sig(b11, te))),
-                  mul_(hz0, fma_(hxm, sig(a10, te), mul_(hx0, sig(a11, te)))));
+        R d1, d2, d3, d4;
+        const R a1 = mul_(mul_(hzm, hxm), sgd(b10, te, d1)), a2 = mul_(mul_(hzm, hx0), sgd(b11, te, d2));
+        const R a3 = mul_(mul_(hz0, hxm), sgd(a10, te, d3)), a4 = mul_(mul_(hz0, hx0), sgd(a11, te, d4));
+        Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
       }
       eyn = e_update<R, R>(ey, mul_(dtWy_x, add_(hzm, hz0)), sub_(curl, Jy), fma_(hzm, pye_b, mul_(hz0, pye_a)), Ss,
                            lqy, &qy);
@@ -668,8 +786,10 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
       R Ss = fma_(hym, fma_(hxm, s00, mul_(hx0, s01)), mul_(hy0, fma_(hxm, s10, mul_(hx0, s11))));
       if (CPL) {
         const R te = mul_(R(0.5), add_(th, th_kp));
-        Ss = fma_(hym, fma_(hxm, sig(a00, te), mul_(hx0, sig(a01, te))),
-                  mul_(hy0, fma_(hxm, sig(a10, te), mul_(hx0, sig(a11, te)))));
+        R d1, d2, d3, d4;
+        const R a1 = mul_(mul_(hym, hxm), sgd(a00, te, d1)), a2 = mul_(mul_(hym, hx0), sgd(a01, te, d2));
+        const R a3 = mul_(mul_(hy0, hxm), sgd(a10, te, d3)), a4 = mul_(mul_(hy0, hx0), sgd(a11, te, d4));
+        Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
       }
       ezn = e_update<R, R>(ez, mul_(dtWx_y, add_(hxm, hx0)), sub_(curl, Jz), Se, Ss, mul_(R(0.25), hz0), &qz);
     }
@@ -695,6 +815,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
     pys_b = pys_a;
     u11_b = u11;
     if (CPL) {
+      b00 = a00;
       b01 = a01;
       b10 = a10;
       b11 = a11;
@@ -711,7 +832,13 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
       A.Qs[id] = s;
     }
   }
-  if (CPL && own) A.Pout[id0 + (I)nz * plane] = mul_(add_(e_pend, sQy[nz & 1][ty - 1][tx]), A.inv_dt);
+  if (CPL && !TH && own) A.Pout[id0 + (I)nz * plane] = mul_(add_(e_pend, sQy[nz & 1][ty - 1][tx]), A.inv_dt);
+  if (TH) {  // node (i, j, nz): no voxel layer above; plane nz's stage is resident (nothing is issued after it)
+    R t_part = 0, t_dtc = 0;
+    th_partial(stg[nz & (kEmStages - 1)], nz, th_layer_zero<R, R>(), R(0), t_part, t_dtc);
+    if (own) th_finish(id0 + (I)nz * plane, sQy[nz & 1][ty - 1][tx], t_part, t_dtc);
+    if (A.peak != nullptr) peak_max(t_max, A.peak);
+  }
 }
 
 // ---- interior tile pairs: two nodes per thread. The pair tile starting at
@@ -721,7 +848,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
 // +x/+y neighbours and its voxels lie inside the grid, off the lateral walls
 // and outside the x/y CPML slabs; only the z slab and walls remain, decided
 // per plane for the whole CTA.
-template <typename R, typename I, int TY, bool CPL>
+template <typename R, typename I, int TY, bool CPL, bool TH>
 __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
                                              EmStage<R, kEm2Nodes, TY> *stg, typename Pair2<R>::T (*sHxz)[2][TY][32],
                                              typename Pair2<R>::T (*sQy)[TY][32], uint64_t *bars, int *s_abort, int xs,
@@ -790,11 +917,65 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
   R2 hx_km1 = z2, hy_km1 = z2, qz_km1 = z2;
   R2 pxe_b = z2, pxs_b = z2, pye_b = z2, pys_b = z2, u11_b = z2;
   R2 q_pend = z2, e_pend = z2;
-  int p0b = vd, p0c = vd, p1a = vd, p1b = vd, p1c = vd;  // coupled steps: material rows of layer k-1
-  // sigma dt/2 of the voxels ra (node .x) and rb (node .y) at the edge temperatures te
-  auto sigp = [&](int ra, int rb, R2 te) -> R2 {
-    return sig_t(R2{s_mt[ra + M_SDT2], s_mt[rb + M_SDT2]}, R2{s_mt[ra + M_TCR], s_mt[rb + M_TCR]},
-                 R2{s_mt[ra + M_TC0], s_mt[rb + M_TC0]}, te);
+  int p0a = vd, p0b = vd, p0c = vd, p1a = vd, p1b = vd, p1c = vd;  // coupled steps: material rows of layer k-1
+  // sigma dt/2 of the voxels ra (node .x) and rb (node .y) (returned) and their
+  // denominators at the edge temperatures te (in d), for sig_sum4
+  auto sgdp = [&](int ra, int rb, R2 te, R2 &d) -> R2 {
+    d = fma_(R2{s_mt[ra + M_TCR], s_mt[rb + M_TCR]}, te, R2{s_mt[ra + M_TC0], s_mt[rb + M_TC0]});
+    return R2{s_mt[ra + M_SDT2], s_mt[rb + M_SDT2]};
+  };
+  // coupled steps, the fused thermal step of the node pair at plane k-1 (see
+  // the border tiles)
+  // the node columns' constants from the tile's geometry (interior pairs lie
+  // off the lateral walls: no lateral film); the inverse sizes of cells ia-1
+  // and j-1 are kept
+  static_assert(CPL || !TH, "the fused thermal step belongs to coupled steps");
+  R2 ihxm_th = z2;
+  R ihym_th = 0;
+  if (TH) {
+    ihxm_th = R2{g.ih[0][ia - 1], g.ih[0][ia]};
+    ihym_th = g.ih[1][j - 1];
+  }
+  auto tcol_of = [&]() -> ThCol<R2> {
+    ThCol<R2> c;
+    c.hxm = hxm, c.hx0 = hx0, c.hym = hym, c.hy0 = hy0;
+    c.qxm = mul_(bc_<R2>(R(0.25)), ihxm_th), c.qx0 = mul_(bc_<R2>(R(0.25)), ihx);
+    c.qym = bc_<R2>(mul_(R(0.25), ihym_th)), c.qy0 = mul_(bc_<R2>(R(0.25)), ihy);
+    c.fxy = z2;
+    c.az = mul_(bc_<R2>(R(0.25)), mul_(add_(hxm, hx0), add_(hym, hy0)));
+    return c;
+  };
+  ThLayer<R2> tl_lo = th_layer_zero<R2, R>();  // sums of voxel layer k-2
+  R2 th_m2 = z2, gz_th = z2;                   // T of the pair at plane k-2; the z-edge conductance below
+  R t_max = R(-3.0e38);
+  // the pair's thermal step at plane kk without the y-edge share of row j-1
+  // (see the border tiles)
+  auto th_partial = [&](const EmStage<R, kEm2Nodes, TY> &Sm, int kk, const ThLayer<R2> &up, R2 tkp, R2 &tpart,
+                        R2 &dtc) {
+    const ThCoeffs<R2> q = th_coeffs<R2, R>(tcol_of(), tl_lo, up, Sm.Z.v[0][0], Sm.Z.v[0][1], Sm.Z.v[0][3], kk == 0,
+                                            kk == nz, A.hconv, gz_th);
+    const R2 tc = ldv_<R2>(&Sm.T.v[ty][cx]);
+    if (own) {
+      dtc = mul_(bc_<R2>(A.dt), rcp_(q.C));
+      const R2 p = mul_(e_pend, bc_<R2>(A.inv_dt));
+      R2 f = fma_(q.Gxm, sub_(R2{Sm.T.v[ty][cx - 1], tc.x}, tc), p);  // owners: tx, ty >= 1
+      f = fma_(q.Gxp, sub_(R2{tc.y, Sm.T.v[ty][cx + 2]}, tc), f);
+      f = fma_(q.Gym, sub_(ldv_<R2>(&Sm.T.v[ty - 1][cx]), tc), f);
+      f = fma_(q.Gyp, sub_(ldv_<R2>(&Sm.T.v[ty + 1][cx]), tc), f);
+      f = fma_(q.Gzm, sub_(th_m2, tc), f);
+      f = fma_(q.Gzp, sub_(tkp, tc), f);
+      f = fma_(q.film, sub_(bc_<R2>(A.T_amb), tc), f);
+      tpart = fma_(dtc, f, tc);
+    }
+    th_m2 = tc;
+    tl_lo = up;
+  };
+  auto th_finish = [&](I idn, R2 share, R2 tpart, R2 dtc) {
+    const R2 inv = bc_<R2>(A.inv_dt);
+    stv_(A.Pout + idn, mul_(add_(e_pend, share), inv));
+    const R2 tn = fma_(dtc, mul_(share, inv), tpart);
+    stv_(A.Tth + idn, tn);
+    t_max = fmax(t_max, fmax(tn.x, tn.y));
   };
 
   for (int k = 0; k <= nz; ++k) {
@@ -837,11 +1018,20 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
              hz_o = ldv_<R2>(&S0.H[2].v[ty][cx]);
     const R2 q_old = accum ? ldv_<R2>(&S0.Qs.v[ty][cx]) : z2;
     R2 th = z2, th_ip = z2, th_jp = z2, th_kp = z2;
+    R2 t_part = z2, t_dtc = z2;  // the pair's thermal step at plane k-1 without the y-edge share of row j-1
     if (CPL) {
       th = ldv_<R2>(&S0.T.v[ty][cx]);
       th_ip = R2{th.y, S0.T.v[ty][cx + 2]};
       th_jp = ldv_<R2>(&S0.T.v[ty + 1][cx]);
       th_kp = kz ? ldv_<R2>(&S1.T.v[ty][cx]) : z2;
+      if (TH && k > 0) {  // plane k-1's stage is resident until this plane's barrier
+        const ThLayer<R2> up = th_layer<R2>(
+            R2{s_mt[p0a + M_K], s_mt[p0b + M_K]}, R2{s_mt[p0b + M_K], s_mt[p0c + M_K]},
+            R2{s_mt[p1a + M_K], s_mt[p1b + M_K]}, R2{s_mt[p1b + M_K], s_mt[p1c + M_K]},
+            R2{s_mt[p0a + M_RHOCP], s_mt[p0b + M_RHOCP]}, R2{s_mt[p0b + M_RHOCP], s_mt[p0c + M_RHOCP]},
+            R2{s_mt[p1a + M_RHOCP], s_mt[p1b + M_RHOCP]}, R2{s_mt[p1b + M_RHOCP], s_mt[p1c + M_RHOCP]}, tcol_of());
+        th_partial(stg[(k - 1) & (kEmStages - 1)], k - 1, up, th, t_part, t_dtc);
+      }
     }
 
     R e0a, s0a, u0a, k0a, e0b, s0b, u0b, k0b, e0c, s0c, u0c, k0c;
@@ -912,7 +1102,9 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
         stv_(A.Qs + (id - plane), s);
       }
     }
-    if (CPL && own && k > 0) stv_(A.Pout + (id - plane), mul_(add_(e_pend, sQy[par ^ 1][ty - 1][tx]), bc_<R2>(A.inv_dt)));
+    if (TH && own && k > 0) th_finish(id - plane, sQy[par ^ 1][ty - 1][tx], t_part, t_dtc);
+    if (CPL && !TH && own && k > 0)
+      stv_(A.Pout + (id - plane), mul_(add_(e_pend, sQy[par ^ 1][ty - 1][tx]), bc_<R2>(A.inv_dt)));
 
     // ---- source currents on the pair's edges
     R2 Jx = z2, Jy = z2, Jz = z2;
@@ -943,8 +1135,10 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
       R2 Ss = fma_(hzm, pxs_b, mul_(hz0, pxs_a));
       if (CPL) {
         const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_ip));
-        Ss = fma_(hzm, fma_(hym, sigp(p0b, p0c, te), mul_(hy0, sigp(p1b, p1c, te))),
-                  mul_(hz0, fma_(hym, sigp(r0b, r0c, te), mul_(hy0, sigp(r1b, r1c, te)))));
+        R2 d1, d2, d3, d4;
+        const R2 a1 = mul_(mul_(hzm, hym), sgdp(p0b, p0c, te, d1)), a2 = mul_(mul_(hzm, hy0), sgdp(p1b, p1c, te, d2));
+        const R2 a3 = mul_(mul_(hz0, hym), sgdp(r0b, r0c, te, d3)), a4 = mul_(mul_(hz0, hy0), sgdp(r1b, r1c, te, d4));
+        Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
       }
       exn = e_update<R2, R>(ex, mul_(dtWx_y, add_(hzm, hz0)), sub_(curl, Jx), fma_(hzm, pxe_b, mul_(hz0, pxe_a)), Ss,
                             lqx, &qx);
@@ -955,8 +1149,10 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
       R2 Ss = fma_(hzm, pys_b, mul_(hz0, pys_a));
       if (CPL) {
         const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_jp));
-        Ss = fma_(hzm, fma_(hxm, sigp(p1a, p1b, te), mul_(hx0, sigp(p1b, p1c, te))),
-                  mul_(hz0, fma_(hxm, sigp(r1a, r1b, te), mul_(hx0, sigp(r1b, r1c, te)))));
+        R2 d1, d2, d3, d4;
+        const R2 a1 = mul_(mul_(hzm, hxm), sgdp(p1a, p1b, te, d1)), a2 = mul_(mul_(hzm, hx0), sgdp(p1b, p1c, te, d2));
+        const R2 a3 = mul_(mul_(hz0, hxm), sgdp(r1a, r1b, te, d3)), a4 = mul_(mul_(hz0, hx0), sgdp(r1b, r1c, te, d4));
+        Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
       }
       eyn = e_update<R2, R>(ey, mul_(dtWy_x, add_(hzm, hz0)), sub_(curl, Jy), fma_(hzm, pye_b, mul_(hz0, pye_a)), Ss,
                             lqy, &qy);
@@ -967,8 +1163,10 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
       R2 Ss = fma_(hym, fma_(hxm, s00, mul_(hx0, s01)), mul_(hy0, fma_(hxm, s10, mul_(hx0, s11))));
       if (CPL) {
         const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_kp));
-        Ss = fma_(hym, fma_(hxm, sigp(r0a, r0b, te), mul_(hx0, sigp(r0b, r0c, te))),
-                  mul_(hy0, fma_(hxm, sigp(r1a, r1b, te), mul_(hx0, sigp(r1b, r1c, te)))));
+        R2 d1, d2, d3, d4;
+        const R2 a1 = mul_(mul_(hym, hxm), sgdp(r0a, r0b, te, d1)), a2 = mul_(mul_(hym, hx0), sgdp(r0b, r0c, te, d2));
+        const R2 a3 = mul_(mul_(hy0, hxm), sgdp(r1a, r1b, te, d3)), a4 = mul_(mul_(hy0, hx0), sgdp(r1b, r1c, te, d4));
+        Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
       }
       ezn = e_update<R2, R>(ez, mul_(dtWx_y, add_(hxm, hx0)), sub_(curl, Jz), Se, Ss, bc_<R2>(mul_(R(0.25), hz0s)),
                             &qz);
@@ -995,7 +1193,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
     pys_b = pys_a;
     u11_b = u11;
     if (CPL) {
-      p0b = r0b, p0c = r0c, p1a = r1a, p1b = r1b, p1c = r1c;
+      p0a = r0a, p0b = r0b, p0c = r0c, p1a = r1a, p1b = r1b, p1c = r1c;
     }
   }
   __syncthreads();
@@ -1013,7 +1211,14 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
       stv_(A.Qs + id, s);
     }
   }
-  if (CPL && own) stv_(A.Pout + (id0 + (I)nz * plane), mul_(add_(e_pend, sQy[nz & 1][ty - 1][tx]), bc_<R2>(A.inv_dt)));
+  if (CPL && !TH && own)
+    stv_(A.Pout + (id0 + (I)nz * plane), mul_(add_(e_pend, sQy[nz & 1][ty - 1][tx]), bc_<R2>(A.inv_dt)));
+  if (TH) {  // the pair at plane nz: no voxel layer above; plane nz's stage is resident
+    R2 t_part = z2, t_dtc = z2;
+    th_partial(stg[nz & (kEmStages - 1)], nz, th_layer_zero<R2, R>(), z2, t_part, t_dtc);
+    if (own) th_finish(id0 + (I)nz * plane, sQy[nz & 1][ty - 1][tx], t_part, t_dtc);
+    if (A.peak != nullptr) peak_max(t_max, A.peak);
+  }
 }
 
 // Resident CTAs per SM the kernel is compiled for: FP32 8-row tiles at
@@ -1022,7 +1227,9 @@ __host__ __device__ constexpr int em_min_ctas(int rsz, int ty) { return rsz == 4
 
 // One launch per step: CTAs 0 .. n_border-1 take the border tiles (the frame
 // around the interior rectangle, row by row), the rest the interior pairs.
-template <typename R, typename I, int TX, int TY, bool CPL>
+// CPL: the coupled step (sigma(T), Joule power of the step); TH: with the
+// thermal step of Eq. 5 in the same launch (else a thermal launch follows).
+template <typename R, typename I, int TX, int TY, bool CPL, bool TH>
 __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
     em_step_kernel(const __grid_constant__ EmArgs<R> A) {
   static_assert(TX == 32, "a tile row is one warp: x neighbours are exchanged by shuffles");
@@ -1079,7 +1286,7 @@ __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
       } else {
         xs = A.xb1 + (TX - 1) * (c - A.nl);
       }
-      em_tile_border<R, I, TY, CPL, true, false>(A, s_cp, s_mt, sb, sh, sq, s_bar, &s_abort, xs, xe, by);
+      em_tile_border<R, I, TY, CPL, TH, true, false>(A, s_cp, s_mt, sb, sh, sq, s_bar, &s_abort, xs, xe, by);
     } else {
       if (b >= below) {
         b -= below + mid;
@@ -1093,14 +1300,14 @@ __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
       // nodes i = xs - 1 .. xs + 30: does the tile reach an x slab?
       const bool xsl = (A.slo[0] > 0 && xs - 1 <= A.slo[0]) || (A.shi[0] > 0 && xs + TX - 2 >= A.g.nx - A.shi[0]);
       if (xsl)
-        em_tile_border<R, I, TY, CPL, true, true>(A, s_cp, s_mt, sb, sh, sq, s_bar, &s_abort, xs, xe, by);
+        em_tile_border<R, I, TY, CPL, TH, true, true>(A, s_cp, s_mt, sb, sh, sq, s_bar, &s_abort, xs, xe, by);
       else
-        em_tile_border<R, I, TY, CPL, false, true>(A, s_cp, s_mt, sb, sh, sq, s_bar, &s_abort, xs, xe, by);
+        em_tile_border<R, I, TY, CPL, TH, false, true>(A, s_cp, s_mt, sb, sh, sq, s_bar, &s_abort, xs, xe, by);
     }
   } else {
     b -= A.n_border;
     const int py = b / A.npx, px = b - py * A.npx;
-    em_tile_pair<R, I, TY, CPL>(A, s_cp, s_mt, reinterpret_cast<EmStage<R, kEm2Nodes, TY> *>(stg), sHxz, sQy, s_bar,
+    em_tile_pair<R, I, TY, CPL, TH>(A, s_cp, s_mt, reinterpret_cast<EmStage<R, kEm2Nodes, TY> *>(stg), sHxz, sQy, s_bar,
                                 &s_abort, A.xb0 + 62 * px, A.iby0 + py);
   }
 }

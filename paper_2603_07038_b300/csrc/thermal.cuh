@@ -61,7 +61,7 @@ struct ThCol {
 };
 
 template <typename R>
-__device__ __forceinline__ ThCol<R> th_column(const Geo<R> &g, const ThArgs<R> &A, int i, int j) {
+__device__ __forceinline__ ThCol<R> th_column_h(const Geo<R> &g, const R *hconv, int i, int j) {
   const int nx = g.nx, ny = g.ny;
   const bool in = i >= 0 && i <= nx && j >= 0 && j <= ny;
   ThCol<R> c;
@@ -73,11 +73,15 @@ __device__ __forceinline__ ThCol<R> th_column(const Geo<R> &g, const ThArgs<R> &
   c.qx0 = (in && i < nx) ? mul_(R(0.25), g.ih[0][i]) : R(0);
   c.qym = (in && j > 0) ? mul_(R(0.25), g.ih[1][j - 1]) : R(0);
   c.qy0 = (in && j < ny) ? mul_(R(0.25), g.ih[1][j]) : R(0);
-  const R hcx = add_(i == 0 ? A.hconv[0] : R(0), i == nx ? A.hconv[1] : R(0));
-  const R hcy = add_(j == 0 ? A.hconv[2] : R(0), j == ny ? A.hconv[3] : R(0));
+  const R hcx = add_(i == 0 ? hconv[0] : R(0), i == nx ? hconv[1] : R(0));
+  const R hcy = add_(j == 0 ? hconv[2] : R(0), j == ny ? hconv[3] : R(0));
   c.fxy = mul_(R(0.25), fma_(hcx, add_(c.hym, c.hy0), mul_(hcy, add_(c.hxm, c.hx0))));
   c.az = mul_(R(0.25), mul_(add_(c.hxm, c.hx0), add_(c.hym, c.hy0)));
   return c;
+}
+template <typename R>
+__device__ __forceinline__ ThCol<R> th_column(const Geo<R> &g, const ThArgs<R> &A, int i, int j) {
+  return th_column_h(g, A.hconv, i, j);
 }
 
 template <typename R>
@@ -266,7 +270,21 @@ struct ThTmaArgs {
   ThArgs<R> a;                // geometry, T in / out, P, z records, dt, films
   CUtensorMap tmT, tmP, tmV;  // boxes th_box_t x (kThTY+2), th_tx x kThTY, th_box_v x (kThTY+1) (one plane)
   int *err;
+  unsigned long long *peak;   // the maximum of the written T (its ordered_bits image) goes here; null: not tracked
 };
+
+// Order-preserving integer image of a value (larger value, larger image): an
+// atomic maximum over the images is the maximum of the values in any order.
+__device__ __forceinline__ unsigned long long ordered_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | (1ull << 63));
+}
+// warp maximum of v into *peak (every lane of the warp calls it)
+template <typename R>
+__device__ __forceinline__ void peak_max(R v, unsigned long long *peak) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(peak, ordered_bits((double)v));
+}
 
 template <typename R, int NP>
 __global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? (NP == 1 ? 3 : 2) : (NP == 1 ? 2 : 1))
@@ -320,6 +338,7 @@ __global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? (NP == 1 ? 3 : 2)
   R *tp = A.Tn + (n_act > 0 ? g.nid(ia, j, 0) : 0);
   ThLayer<R2> lo[NP];
   R2 T_km1[NP], gz[NP];
+  R t_max = R(-3.0e38);  // the largest T written (peak tracking)
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
     lo[q] = th_layer_zero<R2, R>();
@@ -377,15 +396,19 @@ __global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? (NP == 1 ? 3 : 2)
       const R2 Tip = {Tc[q].y, q == NP - 1 ? T_right : Tc[q + 1].x};
       const R2 p = has_p ? ldv_<R2>(&S0.P.v[ty][2 * NP * tx + 2 * q]) : bc_<R2>(R(0));
       const R2 Tn = th_update<R2, R>(cf, Tc[q], Tim, Tip, Tjm, Tjp, T_km1[q], Tkp, p, A.T_amb, A.dt);
-      if (n_act >= 2 * q + 2)
+      if (n_act >= 2 * q + 2) {
         stv_(tp + 2 * q, Tn);
-      else if (n_act == 2 * q + 1)
+        t_max = fmax(t_max, fmax(Tn.x, Tn.y));
+      } else if (n_act == 2 * q + 1) {
         tp[2 * q] = Tn.x;
+        t_max = fmax(t_max, Tn.x);
+      }
       T_km1[q] = Tc[q];
       lo[q] = up;
     }
     tp += g.plane;
   }
+  if (TA.peak != nullptr) peak_max(t_max, TA.peak);
 }
 
 // Joule finalisation: op 1 -> P = Q * inv_t (burst-averaged power per node);

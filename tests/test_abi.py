@@ -40,7 +40,7 @@ def test_binding_struct_layouts_match_header(tmp_path):
     structs = {"cosim_material": api.cosim_material, "cosim_grid_desc": api.cosim_grid_desc,
                "cosim_source": api.cosim_source, "cosim_allocator": api.cosim_allocator,
                "cosim_options": api.cosim_options, "cosim_stress_opts": api.cosim_stress_opts,
-               "cosim_stress_report": api.cosim_stress_report}
+               "cosim_stress_report": api.cosim_stress_report, "cosim_peak_report": api.cosim_peak_report}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cosim.h"', "int main(void){"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')

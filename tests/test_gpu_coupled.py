@@ -29,9 +29,10 @@ def _seed(o, ctx, p, seed):
     ctx.write(api.COSIM_F_T, T)
 
 
+@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("precision,tol", [(FP64, 1e-11), (FP32, 2e-5)])
 @pytest.mark.parametrize("case", [0, 1])
-def test_coupled_steps_random_state(precision, tol, case):
+def test_coupled_steps_random_state(precision, tol, case, fused):
     bc, L = [((0,) * 6, 0), ((2, 2, 0, 2, 0, 2), 3)][case]
     p = hetero_problem(23, 14, 9, seed=30 + case, em_bc=bc, cpml=L)
     o = oracle.OracleSim(p)
@@ -40,7 +41,7 @@ def test_coupled_steps_random_state(precision, tol, case):
     th0 = o.theta.copy()
     steps = 12
     o.coupled_steps(steps)
-    ctx.em_steps(steps, coupled=True)
+    ctx.em_steps(steps, coupled=True, fused=fused)
     Eg, Hg = read_eh(ctx)
     assert field_rel_l2(Eg, o.E)[0] < tol
     assert field_rel_l2(Hg, o.H)[0] < tol
@@ -73,8 +74,9 @@ def test_coupled_feedback_changes_the_fields():
     ctx2.close()
 
 
+@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("precision", [FP64, FP32])
-def test_coupled_graph_replay_equals_plain(precision):
+def test_coupled_graph_replay_equals_plain(precision, fused):
     p = W.tiny_package()
     s = torch.cuda.Stream()
     a = api.Context(p, precision=precision, stream=s)
@@ -83,8 +85,8 @@ def test_coupled_graph_replay_equals_plain(precision):
     for c in (a, b):
         c.set_sources(tables)
         c.write(api.COSIM_F_T, p.T_init + 30.0 * np.random.default_rng(3).random(p.n_nodes))
-    a.em_steps(128, coupled=True)
-    b.em_graph_capture(64, coupled=True)
+    a.em_steps(128, coupled=True, fused=fused)
+    b.em_graph_capture(64, coupled=True, fused=fused)
     b.em_graph_launch(2)
     for f in (api.COSIM_F_EZ, api.COSIM_F_HX, api.COSIM_F_T, api.COSIM_F_P, api.COSIM_F_Q):
         assert np.array_equal(a.read(f), b.read(f)), f
