@@ -53,6 +53,7 @@ def parse():
     a.add_argument("--no-e2e", action="store_true")
     a.add_argument("--no-cpu", action="store_true")
     a.add_argument("--no-serve", action="store_true")
+    a.add_argument("--no-batch", action="store_true")
     a.add_argument("--no-cg-solve", action="store_true")
     a.add_argument("--serve-n", type=int, default=16)
     a.add_argument("--serve-em-steps", type=int, default=512)
@@ -295,6 +296,8 @@ def gpu_arm(args, rank, world):
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(args, p)
     ctx.close()
+    if rank == 0 and not args.no_batch:
+        out["batched"] = batched_arm(args)
     if rank == 0 and not args.no_serve:
         out["serving"] = serving_arm(args)
     return out
@@ -336,6 +339,98 @@ def stress_cg_solve(ctx, p, stream, rise=60.0, rtol=1e-9, maxit=20000):
             "precision": "FP32 Jacobi-PCG (FP64 dots) in FP64 iterative refinement; relres_fp64 is the true "
                          "residual ||f - K u|| / ||f|| of the FP64 system",
             "load": "synthetic %.0f K hot spot, bottom clamped" % rise}
+
+
+def batched_arm(args, n=64, win=32, windows=3, seed=4, streams=4):
+    """The batched-design workload (after the timed region): n seeded package
+    designs, grids drawn uniformly from 128^3, 256^2 x 64, 384^2 x 64 and
+    512^2 x 96 cells, TSV pitch 4-8 voxels, per-design port lines and PRBS
+    bursts, FP32 fields with FP64 Joule totals, each advanced `windows`
+    32-step windows of EM steps with Joule accumulation, in four forms:
+      sequential: one design at a time, each replaying its own captured graph;
+      batch: one launch per step over every design's tiles (captured graph);
+      batch_persistent: the same with a persistent launch taking the tiles
+        from a device counter, largest designs first (captured graph);
+      streams: the designs spread over `streams` CUDA streams, each replaying
+        its own graph (the serving loop's form).
+    Rates are cell-steps of all designs per second; the projection to the
+    2 ns burst (314,701 steps per design at this dt) gives designs/hour of
+    EM bursts. One warm-up window per form."""
+    import torch
+
+    import workloads as W
+    from paper_2603_07038_b300 import cosim as api
+    from paper_2603_07038_b300 import serving as S
+    specs = S.design_mix(n, seed=seed, em_steps=win * windows)
+    probs = [W.layered_package(sp.nx, sp.ny, seed=100 + sp.seed, nz=sp.nz, tsv_pitch=sp.tsv_pitch, n_lines=8)
+             for sp in specs]
+    cells = sum(p.n_cells for p in probs)
+    total = 4 * (windows + 1) * win
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    out = {"designs": n, "cells_total": cells, "steps_timed": windows * win,
+           "grids": {f"{a}x{b}x{c}": sum(1 for sp in specs if (sp.nx, sp.ny, sp.nz) == (a, b, c))
+                     for a, b, c in S.DESIGN_GRIDS}}
+
+    def make(stream_of):
+        ctxs = []
+        for d, (sp, p) in enumerate(zip(specs, probs)):
+            c = api.Context(p, precision=api.COSIM_FP32, stream=stream_of(d), use_torch_allocator=True)
+            c.set_sources(p.source_tables(c.dt, total, sp.t0))
+            c.joule(api.COSIM_JOULE_RESET, want_total=False)
+            ctxs.append(c)
+        return ctxs
+
+    def timed(run, sync_streams):
+        run(1)  # warm-up window
+        torch.cuda.synchronize()
+        t0, t1 = ev(), ev()
+        base = sync_streams[0]
+        t0.record(base)
+        for st in sync_streams[1:]:
+            st.wait_event(t0)
+        run(windows)
+        for st in sync_streams[1:]:
+            e = ev()
+            e.record(st)
+            base.wait_event(e)
+        t1.record(base)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) * 1e-3
+
+    rates = {}
+    s0 = torch.cuda.Stream()
+    ctxs = make(lambda d: s0)
+    for c in ctxs:
+        c.em_graph_capture(win)
+    sec = timed(lambda w: [c.em_graph_launch(w) for c in ctxs], [s0])
+    rates["sequential"] = cells * windows * win / sec / 1e9
+    for name, pers in (("batch", False), ("batch_persistent", True)):
+        b = api.Batch(ctxs, persistent=pers)
+        b.graph_capture(win)
+        sec = timed(lambda w, b=b: b.graph_launch(w), [s0])
+        rates[name] = cells * windows * win / sec / 1e9
+        b.close()
+    dt = ctxs[0].dt
+    for c in ctxs:
+        c.close()
+    del ctxs
+    torch.cuda.empty_cache()
+    sts = [torch.cuda.Stream() for _ in range(streams)]
+    ctxs = make(lambda d: sts[d % streams])
+    for c in ctxs:
+        c.em_graph_capture(win)
+    sec = timed(lambda w: [c.em_graph_launch(w) for c in ctxs], sts)
+    rates["streams"] = cells * windows * win / sec / 1e9
+    for c in ctxs:
+        c.close()
+    del ctxs
+    torch.cuda.empty_cache()
+    burst = int(round(2e-9 / dt))
+    out["gcell_steps_s"] = {k: round(v, 3) for k, v in rates.items()}
+    out["em_burst_designs_per_hour"] = {k: round(3600.0 * v * 1e9 / (cells / n * burst), 1) for k, v in rates.items()}
+    out["note"] = ("designs/hour of 2 ns EM bursts (%d steps per design) projected from the timed windows; "
+                   "the batch forms are one launch per step for all %d designs" % (burst, n))
+    return out
 
 
 def serving_arm(args, workers=4):

@@ -194,6 +194,52 @@ cosim_status cosim_em_graph_capture(cosim_ctx *ctx, int64_t nsteps, uint32_t fla
  * E/H parity or Joule window position differs from the captured one. */
 cosim_status cosim_em_graph_launch(cosim_ctx *ctx, int64_t count);
 
+/* A batch of contexts (independent package designs of one precision on one
+ * GPU, each with its own grid, materials and sources) stepped together: one
+ * kernel launch per EM step covers the tiles of every design. The paper has
+ * no counterpart; this is how the library serves many design variants at
+ * once. Each design's results are those of cosim_em_steps on it alone: the
+ * same tiles and formulas, bit for bit in FP64; in FP32 equal to rounding
+ * (the batch kernel is compiled apart, and the code generator may contract a
+ * packed product into the following addition differently there). */
+typedef struct cosim_batch cosim_batch;
+
+/* Create a batch of n distinct contexts. They must have the same precision
+ * and share one stream (the batch launches on it, so that their own calls
+ * and the batch's stay ordered), and their sources must be set before: a
+ * later cosim_set_sources on a member makes the batch calls fail with
+ * COSIM_ERR_INVALID (destroy and recreate the batch). persistent != 0: each
+ * step is one persistent launch of about as many CTAs as fit on the GPU at
+ * once, taking the designs' tiles from a device counter, largest designs
+ * first; otherwise one CTA per tile of every design. The batch holds device
+ * memory of its own (cudaMalloc: about 28 KB per FP32 design for the
+ * per-design step arguments and TMA descriptors) but no field state: the
+ * contexts keep theirs. Errors: COSIM_ERR_INVALID (NULL, n < 1, a repeated
+ * context, mixed precisions or streams), COSIM_ERR_CUDA; cosim_batch_last_error(NULL)
+ * then describes the failure. */
+cosim_status cosim_batch_create(cosim_ctx *const *ctxs, int32_t n, int32_t persistent, cosim_batch **out);
+
+/* Advance every design of the batch nsteps EM steps, as cosim_em_steps(ctx,
+ * nsteps, flags) would (flags: COSIM_ACCUM_JOULE only). The designs must sit
+ * at the same E/H parity and, with COSIM_ACCUM_JOULE, the same position in
+ * the 32-step Joule window (else COSIM_ERR_INVALID). Asynchronous on the
+ * batch's stream; discards the members' own captured graphs. */
+cosim_status cosim_batch_em_steps(cosim_batch *b, int64_t nsteps, uint32_t flags);
+
+/* Record nsteps batch steps (a positive multiple of 32, at most 2^30; with
+ * COSIM_ACCUM_JOULE on a window boundary) into a CUDA graph held by the
+ * batch, and replay it count times: identical to cosim_batch_em_steps(b,
+ * nsteps, flags) called count times. The stream must be a non-default stream. */
+cosim_status cosim_batch_graph_capture(cosim_batch *b, int64_t nsteps, uint32_t flags);
+cosim_status cosim_batch_graph_launch(cosim_batch *b, int64_t count);
+
+/* The batch's last error in words ("" if none); b may be NULL: then the last
+ * failed cosim_batch_create of this thread. Valid until the next call. */
+const char *cosim_batch_last_error(const cosim_batch *b);
+
+/* Synchronise the batch's stream and free the batch (not its contexts). */
+void cosim_batch_destroy(cosim_batch *b);
+
 /* Flags for cosim_autotune. FORCE: time the variants again even if this
  * grid shape was tuned before in this process. FIXED: no timing; take the
  * shapes from *em_tile_y (8, or 4 for FP32) and *th_block_y (0, 4, 8, 16). */
@@ -344,6 +390,45 @@ enum {
   COSIM_Q_TH_BLOCK_Y = 10     /* thermal step kernel in use: 0 TMA-staged tiles, 4/8/16 classic block height */
 };
 cosim_status cosim_query(const cosim_ctx *ctx, int32_t what, double *out);
+
+/* Context options for cosim_set_option. */
+enum {
+  COSIM_OPT_WAIT_CYCLES = 0  /* bound, in SM clock cycles, of every in-kernel wait for staged data
+                                (default 2^31, about a second at 2 GHz; >= 1000) */
+};
+/* Set a context option (value in the option's unit). A wait that runs out
+ * abandons its kernel's work and makes the next synchronising call return
+ * COSIM_ERR_TIMEOUT; the context stays usable. Discards a captured EM graph.
+ * COSIM_ERR_INVALID for an unknown option or a value out of range. The paper
+ * has no counterpart. */
+cosim_status cosim_set_option(cosim_ctx *ctx, int32_t what, double value);
+
+/* Health check of the bounded waits: one small kernel waits for a barrier
+ * phase that nothing completes, runs out after the context's wait bound and
+ * takes the solver kernels' error path. Returns COSIM_ERR_TIMEOUT when that
+ * path works (and clears the error, so the context stays usable); any other
+ * status is a failure of the check (COSIM_ERR_TIMEOUT left from earlier work
+ * is reported, and cleared, before the check runs). Synchronises the stream.
+ * The paper has no counterpart. */
+cosim_status cosim_wait_selftest(cosim_ctx *ctx);
+
+/* Checkpoints of the marching state: E and H with the CPML auxiliaries of the
+ * current step, the Joule energy (FP64 total and the short window), the
+ * temperature, the thermal source, the step and window counters and the
+ * device source time index, in one opaque blob (a header, then raw arrays).
+ * The geometry, materials, sources, options and the mechanical solution are
+ * not part of it. Stepping on after cosim_checkpoint_load gives the same bits
+ * as the saving context stepping on (with the same sources and options). The
+ * paper has no counterpart.
+ * size: the blob's bytes at the context's present state. */
+cosim_status cosim_checkpoint_size(const cosim_ctx *ctx, size_t *bytes);
+/* Write the blob to dst (device memory if dst_is_device, else host; caller
+ * owns it; bytes must equal cosim_checkpoint_size). Synchronises the stream. */
+cosim_status cosim_checkpoint_save(cosim_ctx *ctx, void *dst, size_t bytes, int32_t dst_is_device);
+/* Restore a blob written by a context of the same grid, precision and CPML
+ * set-up (COSIM_ERR_INVALID otherwise, context unchanged). Discards a captured
+ * EM graph. Synchronises the stream. */
+cosim_status cosim_checkpoint_load(cosim_ctx *ctx, const void *src, size_t bytes, int32_t src_is_device);
 
 /* Human-readable description of the context's last error ("" if none).
  * Valid until the next call on the context. ctx may be NULL: then the last

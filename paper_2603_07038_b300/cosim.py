@@ -29,6 +29,7 @@ COSIM_MECH_CLAMPED_BOTTOM, COSIM_MECH_KINEMATIC_MOUNT, COSIM_MECH_MASK = 0, 1, 2
  COSIM_F_UX, COSIM_F_UY, COSIM_F_UZ, COSIM_F_VM, COSIM_F_UMAG, COSIM_F_FX, COSIM_F_FY, COSIM_F_FZ,
  COSIM_F_DT, COSIM_F_T_PEAK) = range(19)
 COSIM_STRESS_T_CURRENT, COSIM_STRESS_T_PEAK = 0, 1
+COSIM_OPT_WAIT_CYCLES = 0
 (COSIM_Q_DT_EM, COSIM_Q_DT_TH_LIMIT, COSIM_Q_STEP, COSIM_Q_BYTES_RESIDENT, COSIM_Q_JOULE_STEPS,
  COSIM_Q_N_CELLS, COSIM_Q_N_NODES, COSIM_Q_PRECISION, COSIM_Q_LAUNCHES, COSIM_Q_EM_TILE_Y,
  COSIM_Q_TH_BLOCK_Y) = range(11)
@@ -38,7 +39,10 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 
 EXPORTED = ["cosim_create", "cosim_set_sources", "cosim_em_steps", "cosim_joule_accumulate",
             "cosim_thermal_steps", "cosim_stress_solve", "cosim_stress_apply", "cosim_read_fields",
             "cosim_write_fields", "cosim_query", "cosim_last_error", "cosim_destroy", "cosim_read_fields_async",
-            "cosim_wait_reads", "cosim_coupled_march"]
+            "cosim_wait_reads", "cosim_coupled_march", "cosim_batch_create", "cosim_batch_em_steps",
+            "cosim_batch_graph_capture", "cosim_batch_graph_launch", "cosim_batch_last_error", "cosim_batch_destroy",
+            "cosim_set_option", "cosim_wait_selftest", "cosim_checkpoint_size", "cosim_checkpoint_save",
+            "cosim_checkpoint_load"]
 
 
 class CosimError(RuntimeError):
@@ -145,6 +149,28 @@ def load():
     L.cosim_last_error.restype = C.c_char_p
     L.cosim_destroy.argtypes = [P]
     L.cosim_destroy.restype = None
+    L.cosim_batch_create.argtypes = [C.POINTER(P), C.c_int32, C.c_int32, C.POINTER(P)]
+    L.cosim_batch_create.restype = st
+    L.cosim_batch_em_steps.argtypes = [P, C.c_int64, C.c_uint32]
+    L.cosim_batch_em_steps.restype = st
+    L.cosim_batch_graph_capture.argtypes = [P, C.c_int64, C.c_uint32]
+    L.cosim_batch_graph_capture.restype = st
+    L.cosim_batch_graph_launch.argtypes = [P, C.c_int64]
+    L.cosim_batch_graph_launch.restype = st
+    L.cosim_batch_last_error.argtypes = [P]
+    L.cosim_batch_last_error.restype = C.c_char_p
+    L.cosim_batch_destroy.argtypes = [P]
+    L.cosim_batch_destroy.restype = None
+    L.cosim_set_option.argtypes = [P, C.c_int32, C.c_double]
+    L.cosim_set_option.restype = st
+    L.cosim_wait_selftest.argtypes = [P]
+    L.cosim_wait_selftest.restype = st
+    L.cosim_checkpoint_size.argtypes = [P, C.POINTER(C.c_size_t)]
+    L.cosim_checkpoint_size.restype = st
+    L.cosim_checkpoint_save.argtypes = [P, P, C.c_size_t, C.c_int32]
+    L.cosim_checkpoint_save.restype = st
+    L.cosim_checkpoint_load.argtypes = [P, P, C.c_size_t, C.c_int32]
+    L.cosim_checkpoint_load.restype = st
     L.cosim_sum_f64_noalloc.argtypes = [P, C.c_int64, P, C.c_int32, P]
     L.cosim_sum_f64_noalloc.restype = st
     _lib = L
@@ -317,6 +343,41 @@ def cosim_coupled_march(ctx, nsteps, check_every=1, accumulate_joule=True, reset
     return dict(T_max=r.T_max, step=r.step, peaks=r.peaks)
 
 
+def cosim_set_option(ctx, what, value):
+    _check(load().cosim_set_option(ctx, int(what), float(value)), ctx)
+
+
+def cosim_wait_selftest(ctx):
+    """the status of the bounded-wait health check (COSIM_ERR_TIMEOUT when the
+    timeout path works)"""
+    return load().cosim_wait_selftest(ctx)
+
+
+def cosim_checkpoint_save(ctx, dst=None):
+    """the checkpoint blob: into a new host uint8 array (dst None) or into a
+    CUDA uint8 tensor of the right size"""
+    n = C.c_size_t()
+    _check(load().cosim_checkpoint_size(ctx, C.byref(n)), ctx)
+    if dst is None:
+        out = np.empty(n.value, np.uint8)
+        _check(load().cosim_checkpoint_save(ctx, out.ctypes.data, n.value, 0), ctx)
+        return out
+    if dst.numel() != n.value or not dst.is_cuda or not dst.is_contiguous():
+        raise ValueError(f"dst must be a contiguous CUDA tensor of {n.value} bytes")
+    _check(load().cosim_checkpoint_save(ctx, dst.data_ptr(), n.value, 1), ctx)
+    return dst
+
+
+def cosim_checkpoint_load(ctx, blob):
+    if isinstance(blob, np.ndarray):
+        b = np.ascontiguousarray(blob, np.uint8)
+        _check(load().cosim_checkpoint_load(ctx, b.ctypes.data, b.nbytes, 0), ctx)
+    else:
+        if not blob.is_cuda or not blob.is_contiguous():
+            raise ValueError("blob must be a host array or a contiguous CUDA tensor")
+        _check(load().cosim_checkpoint_load(ctx, blob.data_ptr(), blob.numel() * blob.element_size(), 1), ctx)
+
+
 def cosim_stress_apply(ctx, u, bc=COSIM_MECH_CLAMPED_BOTTOM, node_mask=None):
     """u: (3, n_nodes) array of the context precision (numpy: host, torch CUDA: device) -> K u."""
     o, keep = _stress_opts(bc, node_mask, 300.0, 0.0, 0, 0)
@@ -432,6 +493,46 @@ def cosim_sum_f64_noalloc(x, n=None, out=None, stream=None):
         return out
 
 
+def _bcheck(status, b):
+    if status != COSIM_OK:
+        m = load().cosim_batch_last_error(b)
+        raise CosimError(status, m.decode() if m else "")
+
+
+class Batch:
+    """A batch of contexts stepped together (cosim_batch_*): one launch per EM
+    step over the tiles of every design. The contexts must share one stream
+    and precision and have their sources set; they stay owned by the caller."""
+
+    def __init__(self, contexts, persistent=True):
+        self.contexts = list(contexts)
+        arr = (C.c_void_p * len(self.contexts))(*[c.h for c in self.contexts])
+        h = C.c_void_p()
+        _bcheck(load().cosim_batch_create(arr, len(self.contexts), 1 if persistent else 0, C.byref(h)), None)
+        self.h = h
+
+    def em_steps(self, n, accumulate_joule=True):
+        _bcheck(load().cosim_batch_em_steps(self.h, int(n), COSIM_ACCUM_JOULE if accumulate_joule else 0), self.h)
+
+    def graph_capture(self, n, accumulate_joule=True):
+        _bcheck(load().cosim_batch_graph_capture(self.h, int(n), COSIM_ACCUM_JOULE if accumulate_joule else 0),
+                self.h)
+
+    def graph_launch(self, count=1):
+        _bcheck(load().cosim_batch_graph_launch(self.h, int(count)), self.h)
+
+    def close(self):
+        if self.h:
+            load().cosim_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------- convenience
 
 class Context:
@@ -468,6 +569,15 @@ class Context:
     def em_graph_capture(self, n, accumulate_joule=True, coupled=False, fused=False):
         cosim_em_graph_capture(self.h, n, (COSIM_ACCUM_JOULE if accumulate_joule else 0)
                                | (COSIM_COUPLED_THERMAL if coupled else 0) | (COSIM_COUPLED_FUSED if fused else 0))
+
+    def checkpoint(self, dst=None):
+        return cosim_checkpoint_save(self.h, dst)
+
+    def restore(self, blob):
+        cosim_checkpoint_load(self.h, blob)
+
+    def set_option(self, what, value):
+        cosim_set_option(self.h, what, value)
 
     def em_graph_launch(self, count=1):
         cosim_em_graph_launch(self.h, count)

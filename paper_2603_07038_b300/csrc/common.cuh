@@ -98,6 +98,10 @@ __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)_
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned arrivals) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(arrivals) : "memory");
 }
+// end the life of an initialised barrier (before its memory is initialised again)
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
 // make barrier initialisation visible to the async proxy
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
 // order this thread's earlier shared-memory accesses before later async-proxy (TMA) ones
@@ -148,13 +152,14 @@ struct alignas(128) EmBox {
 };
 
 // Wait for the phase of parity `parity` to complete; gives up (returns false)
-// after about a second of SM clock so that a lost copy cannot hang the GPU.
+// after `limit` SM clock cycles (by default about a second) so that a lost
+// copy cannot hang the GPU.
 constexpr long long kWaitCycles = 2LL << 30;
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long limit = kWaitCycles) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 

@@ -79,6 +79,7 @@ struct cosim_ctx {
   // the same for the interior tile pairs (boxes em2_box_x wide)
   CUtensorMap tmE2[2][2][3], tmH2[2][2][3], tmQ2[2], tmT2[2][2];
   int *dev_err = nullptr;  // device word: a bounded in-kernel wait gave up
+  long long wait_cycles = kWaitCycles;  // the bound of those waits (cosim_set_option)
   int slo[3]{}, shi[3]{}, sn[3]{};
   long long psi_len[3]{};
   int par = 0;
@@ -91,6 +92,7 @@ struct cosim_ctx {
   bool g_accum = false, g_coupled = false;
   int g_par = 0, g_tpar = 0;
   long long launches = 0;  // kernels launched by this context
+  long long src_version = 0;  // changes with every cosim_set_sources
   // peak-temperature snapshots of the coupled marching (cosim_coupled_march):
   // pk[5] (see peak_check_kernel), the snapshot of T at the recorded peak,
   // the check interval (0: not tracking) and the step count tracking started at
@@ -327,6 +329,10 @@ static cudaError_t set_smem_limits() {
                             (const void *)em_step_kernel<R, int, kEmTX, kEmTY, true, true>,
                             (const void *)em_step_kernel<R, long long, kEmTX, kEmTY, true, true>};
   for (const void *k : kernels)
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, em)) != cudaSuccess) return e;
+  const void *batch[2] = {(const void *)em_batch_kernel<R, int, kEmTX, kEmTY>,
+                          (const void *)em_batch_kernel<R, long long, kEmTX, kEmTY>};
+  for (const void *k : batch)
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, em)) != cudaSuccess) return e;
   const int mvt = (int)std::min(mv_smem_bytes<R, kMvTY, false>(kMaxMat), kMaxSmemOptin);
   const int mvd = (int)std::min(mv_smem_bytes<R, kMvTY, true>(kMaxMat), kMaxSmemOptin);
@@ -673,6 +679,7 @@ extern "C" cosim_status cosim_set_sources(cosim_ctx *c, int32_t n, const cosim_s
   if (!c) return COSIM_ERR_INVALID;
   if (n < 0 || (n > 0 && !src)) return fail(c, COSIM_ERR_INVALID, "bad source list");
   drop_graph(c);  // a captured graph holds the source table pointers
+  ++c->src_version;  // (and so does a design batch)
   struct Ent { int row, i, axis, s; };
   std::vector<Ent> ents;
   long long amp_len = 0;
@@ -748,6 +755,8 @@ static cosim_status launch_thermal(cosim_ctx *c, R dt, bool count = true, unsign
     T.tmP = c->thP[q];
     T.tmV = c->thV[q];
     T.err = c->dev_err;
+  T.wait = c->wait_cycles;
+    T.wait = c->wait_cycles;
     const dim3 blk(32, kThTY), grd((c->nx + 1 + th_tx(c->th_np) - 1) / th_tx(c->th_np), (c->ny + 1 + kThTY - 1) / kThTY);
     if (c->th_np == 2) {
       const size_t smem = th_stage_offset<R>((int)c->mats.size()) + kThStages * sizeof(ThStage<R, 2>) + 128;
@@ -776,11 +785,13 @@ static void launch_em(const dim3 &grd, const dim3 &blk, size_t smem, cudaStream_
 // probe: the autotuner's timing launches: every launch reads the current
 // E/H/CPML buffers and writes the spare ones, nothing else changes (no
 // parity flip, no accumulation, no counters), so the state stays as it was.
+// The step arguments of a context that do not change from step to step:
+// geometry, walls, CPML, tiling, sources, Joule accumulator, descriptors of
+// the voxels and the Joule window (tile height TY).
 template <typename R, int TY>
-static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool coupled, bool fused = false,
-                                  bool probe = false) {
+static EmArgs<R> em_args_base(cosim_ctx *c, bool accum) {
   constexpr int t = em_ty_index(TY);
-  EmArgs<R> A;
+  EmArgs<R> A{};
   A.g = make_geo<R>(c);
   for (int a = 0; a < 3; ++a) {
     A.slo[a] = c->slo[a];
@@ -825,38 +836,55 @@ static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool
   A.tmV2 = c->tmV2[t];
   A.zt = (const R *)c->zt;
   A.err = c->dev_err;
+  A.wait = c->wait_cycles;
+  return A;
+}
+
+// The arguments of one step: the E/H buffers read (parity o) and written,
+// their descriptors, the source time offset s within the call, the Joule fold.
+template <typename R, int TY>
+static void em_args_step(cosim_ctx *c, EmArgs<R> &A, int o, int s, bool fold) {
+  constexpr int t = em_ty_index(TY);
+  const int n = o ^ 1;
+  for (int a = 0; a < 3; ++a) {
+    A.Eo[a] = (const R *)c->E[o][a];
+    A.En[a] = (R *)c->E[n][a];
+    A.Ho[a] = (const R *)c->H[o][a];
+    A.Hn[a] = (R *)c->H[n][a];
+    for (int s2 = 0; s2 < 2; ++s2) {
+      A.xEo[a][s2] = (const R *)c->xE[o][a][s2];
+      A.dEo[a][s2] = (const R *)c->dE[o][a][s2];
+      A.xEn[a][s2] = (R *)c->xE[n][a][s2];
+      A.dEn[a][s2] = (R *)c->dE[n][a][s2];
+      A.xHo[a][s2] = (const R *)c->xH[o][a][s2];
+      A.dHo[a][s2] = (const R *)c->dH[o][a][s2];
+      A.xHn[a][s2] = (R *)c->xH[n][a][s2];
+      A.dHn[a][s2] = (R *)c->dH[n][a][s2];
+      A.lEo[a][s2] = (const R *)c->lE[o][a][s2];
+      A.lEn[a][s2] = (R *)c->lE[n][a][s2];
+      A.lHo[a][s2] = (const R *)c->lH[o][a][s2];
+      A.lHn[a][s2] = (R *)c->lH[n][a][s2];
+    }
+    A.tmE[a] = c->tmE[t][o][a];
+    A.tmE2[a] = c->tmE2[t][o][a];
+    A.tmH2[a] = c->tmH2[t][o][a];
+    A.tmH[a] = c->tmH[t][o][a];
+  }
+  A.step_base = c->dstep;
+  A.step_off = s;
+  A.fold = fold;
+}
+
+template <typename R, int TY>
+static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool coupled, bool fused = false,
+                                  bool probe = false) {
+  EmArgs<R> A = em_args_base<R, TY>(c, accum);
   const dim3 blk(kEmTX, TY);
   const dim3 grd(A.n_border + A.npx * (A.iby1 - A.iby0));
   const size_t smem = em_smem_bytes<R, TY>((int)c->mats.size());
+  constexpr int t = em_ty_index(TY);
   for (int64_t s = 0; s < nsteps; ++s) {
-    const int o = c->par, n = c->par ^ 1;
-    for (int a = 0; a < 3; ++a) {
-      A.Eo[a] = (const R *)c->E[o][a];
-      A.En[a] = (R *)c->E[n][a];
-      A.Ho[a] = (const R *)c->H[o][a];
-      A.Hn[a] = (R *)c->H[n][a];
-      for (int s2 = 0; s2 < 2; ++s2) {
-        A.xEo[a][s2] = (const R *)c->xE[o][a][s2];
-        A.dEo[a][s2] = (const R *)c->dE[o][a][s2];
-        A.xEn[a][s2] = (R *)c->xE[n][a][s2];
-        A.dEn[a][s2] = (R *)c->dE[n][a][s2];
-        A.xHo[a][s2] = (const R *)c->xH[o][a][s2];
-        A.dHo[a][s2] = (const R *)c->dH[o][a][s2];
-        A.xHn[a][s2] = (R *)c->xH[n][a][s2];
-        A.dHn[a][s2] = (R *)c->dH[n][a][s2];
-        A.lEo[a][s2] = (const R *)c->lE[o][a][s2];
-        A.lEn[a][s2] = (R *)c->lE[n][a][s2];
-        A.lHo[a][s2] = (const R *)c->lH[o][a][s2];
-        A.lHn[a][s2] = (R *)c->lH[n][a][s2];
-      }
-      A.tmE[a] = c->tmE[t][o][a];
-      A.tmE2[a] = c->tmE2[t][o][a];
-      A.tmH2[a] = c->tmH2[t][o][a];
-      A.tmH[a] = c->tmH[t][o][a];
-    }
-    A.step_base = c->dstep;
-    A.step_off = (int)s;
-    A.fold = accum && ((c->n_acc + 1) % kJouleWindow == 0);
+    em_args_step<R, TY>(c, A, c->par, (int)s, accum && ((c->n_acc + 1) % kJouleWindow == 0));
     A.tmT = c->tmT[t][c->tpar];
     A.tmT2 = c->tmT2[t][c->tpar];
     A.Pout = (R *)c->P;
@@ -1057,6 +1085,309 @@ extern "C" cosim_status cosim_em_graph_launch(cosim_ctx *c, int64_t count) {
     }
   }
   return COSIM_OK;
+}
+
+// ---------------------------------------------------------------- design batches
+
+struct cosim_batch {
+  std::vector<cosim_ctx *> ctx;  // in tile order: the contexts with the most nodes first
+  std::vector<long long> src_version;
+  int prec = COSIM_FP32;
+  cudaStream_t stream = nullptr;
+  bool persistent = false;
+  // groups of up to kBatchMax consecutive contexts, one launch each per step
+  struct Group {
+    int first = 0, n = 0, total = 0, grid = 0;
+    bool wide = false;               // some context needs 64-bit node offsets
+    size_t smem = 0;
+    std::vector<unsigned char> args;  // EmBatchArgs<R>[8]: [accum][parity][fold]
+  };
+  std::vector<Group> groups;
+  unsigned *work = nullptr;      // two tile counters per group (persistent launches)
+  long long **dsteps = nullptr;  // the contexts' device source time counters
+  long long n_launch = 0;        // persistent steps so far (which counter is next)
+  cudaGraphExec_t gexec = nullptr;
+  int64_t g_nsteps = 0;
+  bool g_accum = false;
+  int g_par = 0;
+  long long g_launches = 0;
+  std::string err;
+};
+
+static cosim_status bfail(cosim_batch *b, cosim_status s, const std::string &m) {
+  b->err = m;
+  return s;
+}
+#define BCHECK(b, call)                                                       \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      (b)->err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+      return COSIM_ERR_CUDA;                                                  \
+    }                                                                         \
+  } while (0)
+
+// advance every context's device source time counter after a group of steps
+__global__ void batch_step_advance_kernel(long long *const *steps, int n, long long nsteps) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d < n) *steps[d] += nsteps;
+}
+
+template <typename R>
+static cosim_status batch_build(cosim_batch *b) {
+  const int n = (int)b->ctx.size();
+  std::vector<long long *> st(n);
+  int dev = 0, nsm = 0;
+  BCHECK(b, cudaGetDevice(&dev));
+  BCHECK(b, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  for (int first = 0; first < n; first += kBatchMax) {
+    cosim_batch::Group g;
+    g.first = first;
+    g.n = std::min(kBatchMax, n - first);
+    g.args.assign(8 * sizeof(EmBatchArgs<R>), 0);
+    EmBatchArgs<R> *P = reinterpret_cast<EmBatchArgs<R> *>(g.args.data());
+    for (int d = 0; d < g.n; ++d) {
+      cosim_ctx *c = b->ctx[first + d];
+      for (int acc = 0; acc < 2; ++acc) {
+        const EmArgs<R> base = em_args_base<R, kEmTY>(c, acc != 0);
+        for (int o = 0; o < 2; ++o)
+          for (int f = 0; f < 2; ++f) {
+            EmArgs<R> A = base;
+            em_args_step<R, kEmTY>(c, A, o, 0, f != 0);
+            P[4 * acc + 2 * o + f].a[d] = A;
+          }
+      }
+      const EmArgs<R> &A = P[0].a[d];
+      const int tiles = A.n_border + A.npx * (A.iby1 - A.iby0);
+      for (int v = 0; v < 8; ++v) P[v].cta_start[d + 1] = P[v].cta_start[d] + tiles;
+      st[first + d] = c->dstep;
+      g.smem = std::max(g.smem, em_smem_bytes<R, kEmTY>((int)c->mats.size()));
+      g.wide = g.wide || c->npad >= (1LL << 31);
+    }
+    for (int v = 0; v < 8; ++v) P[v].n = g.n;
+    g.total = P[0].cta_start[g.n];
+    g.grid = g.total;
+    if (b->persistent) {  // about the CTAs that are resident at once
+      int occ = 0;
+      BCHECK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &occ, g.wide ? (const void *)em_batch_kernel<R, long long, kEmTX, kEmTY>
+                                 : (const void *)em_batch_kernel<R, int, kEmTX, kEmTY>,
+                    kEmTX * kEmTY, g.smem));
+      g.grid = std::max(1, std::min(g.total, nsm * std::max(occ, 1)));
+    }
+    b->groups.push_back(std::move(g));
+  }
+  BCHECK(b, cudaMalloc((void **)&b->work, 2 * b->groups.size() * sizeof(unsigned)));
+  BCHECK(b, cudaMalloc((void **)&b->dsteps, n * sizeof(long long *)));
+  BCHECK(b, cudaMemset(b->work, 0, 2 * b->groups.size() * sizeof(unsigned)));
+  BCHECK(b, cudaMemcpy(b->dsteps, st.data(), n * sizeof(long long *), cudaMemcpyHostToDevice));
+  return COSIM_OK;
+}
+
+extern "C" cosim_status cosim_batch_create(cosim_ctx *const *ctxs, int32_t n, int32_t persistent,
+                                           cosim_batch **out) {
+  if (!out) return COSIM_ERR_INVALID;
+  *out = nullptr;
+  if (!ctxs || n < 1) return COSIM_ERR_INVALID;
+  cosim_batch *b = new cosim_batch();
+  std::vector<std::pair<int, cosim_ctx *>> order;
+  for (int d = 0; d < n; ++d) {
+    cosim_ctx *c = ctxs[d];
+    if (!c || c->prec != ctxs[0]->prec || c->stream != ctxs[0]->stream) {
+      delete b;
+      return COSIM_ERR_INVALID;
+    }
+    for (int q = 0; q < d; ++q)
+      if (ctxs[q] == c) {
+        delete b;
+        return COSIM_ERR_INVALID;
+      }
+    order.emplace_back(-(int)((long long)(c->nx + 1) * (c->ny + 1) * (c->nz + 1) / 1024), c);
+  }
+  // the largest designs first: in a persistent launch their tiles are taken
+  // first and the small designs' tiles fill the tail
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<int, cosim_ctx *> &a, const std::pair<int, cosim_ctx *> &b2) {
+                     return a.first < b2.first;
+                   });
+  for (auto &pc : order) {
+    b->ctx.push_back(pc.second);
+    b->src_version.push_back(pc.second->src_version);
+  }
+  b->prec = ctxs[0]->prec;
+  b->stream = ctxs[0]->stream;
+  b->persistent = persistent != 0;
+  const cosim_status st = b->prec == COSIM_FP64 ? batch_build<double>(b) : batch_build<float>(b);
+  if (st != COSIM_OK) {
+    g_create_error = b->err;
+    cosim_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return COSIM_OK;
+}
+
+// the contexts must step together: same E/H parity, same Joule window
+// position, sources unchanged since the batch was built
+static cosim_status batch_check(cosim_batch *b, bool accum) {
+  cosim_ctx *c0 = b->ctx[0];
+  for (size_t d = 0; d < b->ctx.size(); ++d) {
+    cosim_ctx *c = b->ctx[d];
+    if (c->src_version != b->src_version[d])
+      return bfail(b, COSIM_ERR_INVALID, "a context's sources changed after the batch was created");
+    if (c->par != c0->par || (accum && c->n_acc % kJouleWindow != c0->n_acc % kJouleWindow))
+      return bfail(b, COSIM_ERR_INVALID, "the contexts are at different E/H parities or Joule window positions");
+  }
+  return COSIM_OK;
+}
+
+template <typename R>
+static cosim_status batch_steps_t(cosim_batch *b, int64_t nsteps, bool accum) {
+  const int n = (int)b->ctx.size();
+  cosim_ctx *c0 = b->ctx[0];
+  const dim3 blk(kEmTX, kEmTY);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const bool fold = accum && ((c0->n_acc + 1) % kJouleWindow == 0);
+    const int variant = 4 * (accum ? 1 : 0) + 2 * c0->par + (fold ? 1 : 0);
+    const int cnt = (int)(b->n_launch & 1);
+    if (b->persistent) ++b->n_launch;
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+      const cosim_batch::Group &g = b->groups[gi];
+      const EmBatchArgs<R> &P = reinterpret_cast<const EmBatchArgs<R> *>(g.args.data())[variant];
+      unsigned *w = b->persistent ? b->work + 2 * gi + cnt : nullptr;
+      unsigned *wn = b->persistent ? b->work + 2 * gi + (cnt ^ 1) : nullptr;
+      if (g.wide)
+        em_batch_kernel<R, long long, kEmTX, kEmTY><<<g.grid, blk, g.smem, b->stream>>>(P, (int)s, w, wn);
+      else
+        em_batch_kernel<R, int, kEmTX, kEmTY><<<g.grid, blk, g.smem, b->stream>>>(P, (int)s, w, wn);
+      BCHECK(b, cudaGetLastError());
+    }
+    for (cosim_ctx *c : b->ctx) {
+      c->par ^= 1;
+      c->step++;
+      if (accum) {
+        c->n_acc++;
+        c->qs_dirty = !fold;
+      }
+    }
+    c0->launches += (long long)b->groups.size();
+  }
+  if (nsteps > 0) {
+    batch_step_advance_kernel<<<(n + 127) / 128, 128, 0, b->stream>>>(b->dsteps, n, nsteps);
+    BCHECK(b, cudaGetLastError());
+    ++c0->launches;
+  }
+  return COSIM_OK;
+}
+
+static cosim_status batch_steps(cosim_batch *b, int64_t nsteps, bool accum) {
+  while (nsteps > 0) {  // groups of at most 2^30 steps keep the step offset an int
+    const int64_t q = std::min<int64_t>(nsteps, 1LL << 30);
+    const cosim_status st = b->prec == COSIM_FP64 ? batch_steps_t<double>(b, q, accum) : batch_steps_t<float>(b, q, accum);
+    if (st != COSIM_OK) return st;
+    nsteps -= q;
+  }
+  return COSIM_OK;
+}
+
+extern "C" cosim_status cosim_batch_em_steps(cosim_batch *b, int64_t nsteps, uint32_t flags) {
+  if (!b) return COSIM_ERR_INVALID;
+  if (nsteps < 0 || (flags & ~COSIM_ACCUM_JOULE)) return bfail(b, COSIM_ERR_INVALID, "bad nsteps or flags");
+  const bool acc = flags & COSIM_ACCUM_JOULE;
+  const cosim_status st = batch_check(b, acc);
+  if (st != COSIM_OK) return st;
+  for (cosim_ctx *c : b->ctx) drop_graph(c);  // (a context's own graph assumes its own step sequence)
+  return batch_steps(b, nsteps, acc);
+}
+
+static void batch_drop_graph(cosim_batch *b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  b->g_nsteps = 0;
+}
+
+extern "C" cosim_status cosim_batch_graph_capture(cosim_batch *b, int64_t nsteps, uint32_t flags) {
+  if (!b) return COSIM_ERR_INVALID;
+  if (nsteps <= 0 || nsteps % kJouleWindow != 0 || nsteps > (1LL << 30) || (flags & ~COSIM_ACCUM_JOULE))
+    return bfail(b, COSIM_ERR_INVALID, "graph steps must be a positive multiple of 32 (the Joule window), <= 2^30");
+  if (b->stream == nullptr) return bfail(b, COSIM_ERR_INVALID, "graph capture needs a non-default stream");
+  const bool acc = flags & COSIM_ACCUM_JOULE;
+  cosim_status st = batch_check(b, acc);
+  if (st != COSIM_OK) return st;
+  if (acc && b->ctx[0]->n_acc % kJouleWindow != 0)
+    return bfail(b, COSIM_ERR_INVALID, "capture with Joule accumulation must start on a 32-step window boundary");
+  batch_drop_graph(b);
+  BCHECK(b, cudaStreamSynchronize(b->stream));
+  // capturing records the launches without running them: the contexts'
+  // bookkeeping is restored afterwards and applied per replay
+  struct Saved { long long step, n_acc, launches; int par; bool dirty; };
+  std::vector<Saved> sv;
+  for (cosim_ctx *c : b->ctx) sv.push_back({c->step, c->n_acc, c->launches, c->par, c->qs_dirty});
+  const long long nl = b->n_launch, l0 = b->ctx[0]->launches;
+  BCHECK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  st = batch_steps(b, nsteps, acc);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+  const long long captured = b->ctx[0]->launches - l0;
+  for (size_t d = 0; d < b->ctx.size(); ++d) {
+    cosim_ctx *c = b->ctx[d];
+    c->step = sv[d].step, c->n_acc = sv[d].n_acc, c->launches = sv[d].launches, c->par = sv[d].par;
+    c->qs_dirty = sv[d].dirty;
+  }
+  b->n_launch = nl;
+  if (st != COSIM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess || graph == nullptr) {
+    cudaGetLastError();
+    return bfail(b, COSIM_ERR_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(e));
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&b->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    b->gexec = nullptr;
+    cudaGetLastError();
+    return bfail(b, COSIM_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+  }
+  b->g_nsteps = nsteps;
+  b->g_accum = acc;
+  b->g_par = b->ctx[0]->par;
+  b->g_launches = captured;
+  return COSIM_OK;
+}
+
+extern "C" cosim_status cosim_batch_graph_launch(cosim_batch *b, int64_t count) {
+  if (!b) return COSIM_ERR_INVALID;
+  if (!b->gexec) return bfail(b, COSIM_ERR_INVALID, "no captured graph");
+  if (count < 0) return bfail(b, COSIM_ERR_INVALID, "count < 0");
+  cosim_status st = batch_check(b, b->g_accum);
+  if (st != COSIM_OK) return st;
+  if (b->ctx[0]->par != b->g_par || (b->g_accum && b->ctx[0]->n_acc % kJouleWindow != 0))
+    return bfail(b, COSIM_ERR_INVALID, "the contexts' parity or Joule window differs from the captured one");
+  for (int64_t q = 0; q < count; ++q) {
+    BCHECK(b, cudaGraphLaunch(b->gexec, b->stream));
+    for (cosim_ctx *c : b->ctx) {
+      c->step += b->g_nsteps;
+      if (b->g_accum) {
+        c->n_acc += b->g_nsteps;
+        c->qs_dirty = false;  // the last step of a 32-step window folds
+      }
+    }
+    b->ctx[0]->launches += b->g_launches;
+  }
+  return COSIM_OK;
+}
+
+extern "C" const char *cosim_batch_last_error(const cosim_batch *b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+extern "C" void cosim_batch_destroy(cosim_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  cudaFree(b->work);
+  cudaFree(b->dsteps);
+  delete b;
 }
 
 // move the short-window Joule energy into the FP64 total (Q += Qs, Qs = 0)
@@ -1276,6 +1607,8 @@ static cosim_status matvec_g(cosim_ctx *c, const Geo<R> &g, void *const u[3], vo
     T.tmV = c->mvV;
     T.zt = (const R *)c->zt;
     T.err = c->dev_err;
+  T.wait = c->wait_cycles;
+    T.wait = c->wait_cycles;
     const size_t smem = mv_smem_bytes<R, kMvTY, false>((int)c->mats.size());
     const dim3 grd2((c->nx + 1 + kMvElems - 2) / (kMvElems - 1), (c->ny + 1 + kMvTY - 2) / (kMvTY - 1));
     hex8_matvec_tma_kernel<R, kMvTY, false><<<grd2, blk, smem, c->stream>>>(T); ++c->launches;
@@ -1323,6 +1656,7 @@ static cosim_status matvec_dir(cosim_ctx *c, int from, int parity, double *parti
   T.parity = parity;
   T.zt = (const R *)c->zt;
   T.err = c->dev_err;
+  T.wait = c->wait_cycles;
   const size_t smem = mv_smem_bytes<R, kMvTY, true>((int)c->mats.size());
   const dim3 blk(kMvTX, kMvTY);
   const dim3 grd((c->nx + 1 + kMvElems - 2) / (kMvElems - 1), (c->ny + 1 + kMvTY - 2) / (kMvTY - 1));
@@ -1886,6 +2220,134 @@ extern "C" cosim_status cosim_autotune(cosim_ctx *c, uint32_t flags, int32_t *em
   c->th_by = by;
   if (em_tile_y) *em_tile_y = ty;
   if (th_block_y) *th_block_y = by;
+  return COSIM_OK;
+}
+
+// ---------------------------------------------------------------- options, health check, checkpoints
+
+extern "C" cosim_status cosim_set_option(cosim_ctx *c, int32_t what, double value) {
+  if (!c) return COSIM_ERR_INVALID;
+  if (what == COSIM_OPT_WAIT_CYCLES) {
+    if (!(value >= 1000.0 && value <= 9.0e18)) return fail(c, COSIM_ERR_INVALID, "wait bound out of range");
+    c->wait_cycles = (long long)value;
+    drop_graph(c);  // a captured graph holds the old bound
+    return COSIM_OK;
+  }
+  return fail(c, COSIM_ERR_INVALID, "unknown option");
+}
+
+// One CTA waits for a barrier phase that needs two arrivals and gets one:
+// the bounded wait runs out after `limit` cycles and takes the solver
+// kernels' error path (the context's error word).
+__global__ void wait_selftest_kernel(int *err, long long limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 2);
+    fence_mbar_init();
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&bar)) : "memory");
+    if (!mbar_wait(&bar, 0u, limit)) atomicExch(err, 1);
+  }
+}
+
+extern "C" cosim_status cosim_wait_selftest(cosim_ctx *c) {
+  if (!c) return COSIM_ERR_INVALID;
+  cosim_status st = check_device_wait(c);  // an earlier expiry is reported first
+  if (st != COSIM_OK) return st;
+  wait_selftest_kernel<<<1, 32, 0, c->stream>>>(c->dev_err, c->wait_cycles); ++c->launches;
+  CHECK_LAUNCH(c);
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  return check_device_wait(c);
+}
+
+// Checkpoint layout: this header, then the arrays in a fixed order (E and H
+// of the current parity, the CPML auxiliaries present, the short Joule
+// window, the FP64 Joule total, the temperature, the thermal source).
+struct CkHeader {
+  char magic[8];
+  int32_t version, prec, nx, ny, nz, px, L, par, tpar, qs_dirty;
+  int64_t npad, psi_len[3], step, n_acc, dstep;
+};
+
+static std::vector<std::pair<void *, size_t>> ck_arrays(cosim_ctx *c, int par, int tpar) {
+  std::vector<std::pair<void *, size_t>> v;
+  const size_t nb = (size_t)c->npad * c->rsz;
+  for (int a = 0; a < 3; ++a) v.emplace_back(c->E[par][a], nb);
+  for (int a = 0; a < 3; ++a) v.emplace_back(c->H[par][a], nb);
+  for (int a = 0; a < 3; ++a)
+    for (int s2 = 0; s2 < 2; ++s2)
+      if (c->psi_len[a] > 0) {
+        const size_t pb = (size_t)c->psi_len[a] * c->rsz;
+        v.emplace_back(c->xE[par][a][s2], pb);
+        v.emplace_back(c->dE[par][a][s2], pb);
+        v.emplace_back(c->xH[par][a][s2], pb);
+        v.emplace_back(c->dH[par][a][s2], pb);
+        if (c->lE[par][a][s2]) v.emplace_back(c->lE[par][a][s2], pb);
+        if (c->lH[par][a][s2]) v.emplace_back(c->lH[par][a][s2], pb);
+      }
+  v.emplace_back(c->Qs, nb);
+  v.emplace_back(c->Q, (size_t)c->npad * 8);
+  v.emplace_back(c->T[tpar], nb);
+  v.emplace_back(c->P, nb);
+  return v;
+}
+
+extern "C" cosim_status cosim_checkpoint_size(const cosim_ctx *c, size_t *bytes) {
+  if (!c || !bytes) return COSIM_ERR_INVALID;
+  size_t n = sizeof(CkHeader);
+  for (auto &a : ck_arrays(const_cast<cosim_ctx *>(c), c->par, c->tpar)) n += a.second;
+  *bytes = n;
+  return COSIM_OK;
+}
+
+extern "C" cosim_status cosim_checkpoint_save(cosim_ctx *c, void *dst, size_t bytes, int32_t dst_is_device) {
+  if (!c) return COSIM_ERR_INVALID;
+  size_t need = 0;
+  cosim_checkpoint_size(c, &need);
+  if (!dst || bytes != need) return fail(c, COSIM_ERR_INVALID, "checkpoint buffer size mismatch");
+  CkHeader h{};
+  std::memcpy(h.magic, "COSIMCK1", 8);
+  h.version = 1, h.prec = c->prec, h.nx = c->nx, h.ny = c->ny, h.nz = c->nz, h.px = c->px, h.L = c->L;
+  h.par = c->par, h.tpar = c->tpar, h.qs_dirty = c->qs_dirty ? 1 : 0;
+  h.npad = c->npad, h.step = c->step, h.n_acc = c->n_acc;
+  for (int a = 0; a < 3; ++a) h.psi_len[a] = c->psi_len[a];
+  const cudaMemcpyKind kd = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  long long dstep = 0;
+  CHECK_CUDA(c, cudaMemcpyAsync(&dstep, c->dstep, 8, cudaMemcpyDeviceToHost, c->stream));
+  char *o = (char *)dst + sizeof(CkHeader);
+  for (auto &a : ck_arrays(c, c->par, c->tpar)) {
+    CHECK_CUDA(c, cudaMemcpyAsync(o, a.first, a.second, kd, c->stream));
+    o += a.second;
+  }
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  h.dstep = dstep;
+  CHECK_CUDA(c, cudaMemcpy(dst, &h, sizeof h, dst_is_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+  return check_device_wait(c);
+}
+
+extern "C" cosim_status cosim_checkpoint_load(cosim_ctx *c, const void *src, size_t bytes, int32_t src_is_device) {
+  if (!c) return COSIM_ERR_INVALID;
+  if (!src || bytes < sizeof(CkHeader)) return fail(c, COSIM_ERR_INVALID, "checkpoint too short");
+  CkHeader h{};
+  CHECK_CUDA(c, cudaMemcpy(&h, src, sizeof h, src_is_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+  bool same = std::memcmp(h.magic, "COSIMCK1", 8) == 0 && h.version == 1 && h.prec == c->prec && h.nx == c->nx &&
+              h.ny == c->ny && h.nz == c->nz && h.px == c->px && h.L == c->L && h.npad == c->npad &&
+              (h.par == 0 || h.par == 1) && (h.tpar == 0 || h.tpar == 1);
+  for (int a = 0; a < 3; ++a) same = same && h.psi_len[a] == c->psi_len[a];
+  if (!same) return fail(c, COSIM_ERR_INVALID, "checkpoint of another grid, precision or CPML set-up");
+  size_t need = sizeof(CkHeader);
+  for (auto &a : ck_arrays(c, h.par, h.tpar)) need += a.second;
+  if (bytes != need) return fail(c, COSIM_ERR_INVALID, "checkpoint size mismatch");
+  drop_graph(c);
+  const cudaMemcpyKind kd = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const char *p = (const char *)src + sizeof(CkHeader);
+  for (auto &a : ck_arrays(c, h.par, h.tpar)) {
+    CHECK_CUDA(c, cudaMemcpyAsync(a.first, p, a.second, kd, c->stream));
+    p += a.second;
+  }
+  const long long dstep = h.dstep;
+  CHECK_CUDA(c, cudaMemcpyAsync(c->dstep, &dstep, 8, cudaMemcpyHostToDevice, c->stream));
+  CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->par = h.par, c->tpar = h.tpar, c->qs_dirty = h.qs_dirty != 0, c->step = h.step, c->n_acc = h.n_acc;
   return COSIM_OK;
 }
 

@@ -117,6 +117,7 @@ struct EmArgs {
   unsigned long long *peak;
   const R *zt;      // per node plane: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1)
   int *err;         // set to 1 when a bounded wait for a staged plane gave up
+  long long wait;   // the bound of those waits, in SM clock cycles
 };
 
 // index of position p (node or cell) of an axis inside its CPML slabs, or -1
@@ -377,14 +378,15 @@ __host__ __device__ constexpr size_t em_smem_bytes(int nmat) {
 // Bounded waits for the planes a CTA reads at plane k: plane k+1 (plane k was
 // waited for one plane earlier, plane 0 before the loop). Sets *s_abort when
 // a copy did not arrive in time.
-__device__ __forceinline__ void em_wait_next(uint64_t *bars, int k, int nz, int *s_abort) {
-  if (k + 1 <= nz && !mbar_wait(&bars[(k + 1) & (kEmStages - 1)], (unsigned)((k + 1) / kEmStages) & 1u))
+__device__ __forceinline__ void em_wait_next(uint64_t *bars, int k, int nz, int *s_abort, long long lim) {
+  if (k + 1 <= nz && !mbar_wait(&bars[(k + 1) & (kEmStages - 1)], (unsigned)((k + 1) / kEmStages) & 1u, lim))
     *s_abort = 1;
 }
 // after a failed wait at plane k: let the copies issued so far (planes up to
 // k + kEmAhead) land (bounded), flag the error and let the CTA leave
-__device__ __forceinline__ void em_abort(uint64_t *bars, int k, int nz, int *err) {
-  for (int q = k; q <= k + kEmAhead && q <= nz; ++q) mbar_wait(&bars[q & (kEmStages - 1)], (unsigned)(q / kEmStages) & 1u);
+__device__ __forceinline__ void em_abort(uint64_t *bars, int k, int nz, int *err, long long lim) {
+  for (int q = k; q <= k + kEmAhead && q <= nz; ++q)
+    mbar_wait(&bars[q & (kEmStages - 1)], (unsigned)(q / kEmStages) & 1u, lim);
   atomicExch(err, 1);
 }
 
@@ -397,7 +399,7 @@ __device__ __forceinline__ void em_abort(uint64_t *bars, int k, int nz, int *err
 template <typename R, typename I, int TY, bool CPL, bool TH, bool XS, bool YS>
 __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
                                                EmStage<R, 32, TY> *stg, R (*sHxz)[2][TY][32], R (*sQy)[TY][32],
-                                               uint64_t *bars, int *s_abort, int xs, int xe, int by) {
+                                               uint64_t *bars, int *s_abort, int xs, int xe, int by, int step_off) {
   constexpr int TX = 32;
   const Geo<R> &g = A.g;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -528,7 +530,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
     for (int q = 0; q < kEmAhead; ++q) issue(q);
   }
   prefetch_h(0);
-  if (!mbar_wait(&bars[0], 0u)) *s_abort = 1;
+  if (!mbar_wait(&bars[0], 0u, A.wait)) *s_abort = 1;
   R hx_km1 = 0, hy_km1 = 0, qz_km1 = 0;
   // layer k-1 partial sums of the x / y edges and 1/mu of voxel (i, j, k-1);
   // zero below the grid
@@ -610,7 +612,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
       fence_proxy_async_smem();
       issue(k + kEmAhead);
     }
-    em_wait_next(bars, k, nz, s_abort);
+    em_wait_next(bars, k, nz, s_abort, A.wait);
     prefetch_h(k + 1);
     const int par = k & 1;  // parity of the double-buffered exchange arrays
     const I id = id0 + (I)k * plane;
@@ -716,7 +718,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
     __syncthreads();
     if (*s_abort) {  // a copy did not arrive in time: drain what is in flight (bounded), flag, leave
       if constexpr (sizeof(R) == 4) cp_async_wait<0>();
-      if (leader) em_abort(bars, k, nz, A.err);
+      if (leader) em_abort(bars, k, nz, A.err, A.wait);
       return;
     }
     // Joule energy of node (i, j, k-1): its y-edge share from j-1 is now visible
@@ -737,7 +739,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
     R Jx = 0, Jy = 0, Jz = 0;
     for (int e = r0; e < r1; ++e) {
       const int4 s = A.src_ent[e];
-      const long long step = *A.step_base + A.step_off;
+      const long long step = *A.step_base + step_off;
       if (s.x == i && step < A.amp_len) {
         const R a = A.src_amp[(long long)s.z * A.amp_len + step];
         Jx = add_(Jx, s.y == 0 ? a : R(0));
@@ -852,7 +854,7 @@ template <typename R, typename I, int TY, bool CPL, bool TH>
 __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
                                              EmStage<R, kEm2Nodes, TY> *stg, typename Pair2<R>::T (*sHxz)[2][TY][32],
                                              typename Pair2<R>::T (*sQy)[TY][32], uint64_t *bars, int *s_abort, int xs,
-                                             int by) {
+                                             int by, int step_off) {
   using R2 = typename Pair2<R>::T;
   constexpr int BX = em2_box_x(), BV = em2_vox_box_x();
   const Geo<R> &g = A.g;
@@ -913,7 +915,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
 #pragma unroll
     for (int q = 0; q < kEmAhead; ++q) issue(q);
   }
-  if (!mbar_wait(&bars[0], 0u)) *s_abort = 1;
+  if (!mbar_wait(&bars[0], 0u, A.wait)) *s_abort = 1;
   R2 hx_km1 = z2, hy_km1 = z2, qz_km1 = z2;
   R2 pxe_b = z2, pxs_b = z2, pye_b = z2, pys_b = z2, u11_b = z2;
   R2 q_pend = z2, e_pend = z2;
@@ -983,7 +985,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
       fence_proxy_async_smem();
       issue(k + kEmAhead);
     }
-    em_wait_next(bars, k, nz, s_abort);
+    em_wait_next(bars, k, nz, s_abort, A.wait);
     const int par = k & 1;  // parity of the double-buffered exchange arrays
     const I id = id0 + (I)k * plane;
     const EmStage<R, kEm2Nodes, TY> &S0 = stg[k & (kEmStages - 1)];
@@ -1086,7 +1088,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
     // the one barrier of the plane (see the border tiles)
     __syncthreads();
     if (*s_abort) {
-      if (leader) em_abort(bars, k, nz, A.err);
+      if (leader) em_abort(bars, k, nz, A.err, A.wait);
       return;
     }
     if (accum && own && k > 0) {
@@ -1110,7 +1112,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
     R2 Jx = z2, Jy = z2, Jz = z2;
     for (int e = r0; e < r1; ++e) {
       const int4 s = A.src_ent[e];
-      const long long step = *A.step_base + A.step_off;
+      const long long step = *A.step_base + step_off;
       if ((s.x == ia || s.x == ia + 1) && step < A.amp_len) {
         const R a = A.src_amp[(long long)s.z * A.amp_len + step];
         if (s.x == ia) {
@@ -1225,29 +1227,26 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
 // COSIM_EM_MIN_CTAS (scaled for other heights), FP64 one.
 __host__ __device__ constexpr int em_min_ctas(int rsz, int ty) { return rsz == 4 ? COSIM_EM_MIN_CTAS * 8 / ty : 1; }
 
-// One launch per step: CTAs 0 .. n_border-1 take the border tiles (the frame
-// around the interior rectangle, row by row), the rest the interior pairs.
+// One CTA's share of a step: tile b of the context described by A (tiles
+// 0 .. n_border-1 are the border tiles, the frame around the interior
+// rectangle row by row; the rest the interior pairs). smem: the dynamic
+// shared window, 128-byte aligned; sHxz, sQy, s_bar, s_abort: the CTA's
+// static exchange arrays, stage barriers (initialised here) and abort flag.
 // CPL: the coupled step (sigma(T), Joule power of the step); TH: with the
 // thermal step of Eq. 5 in the same launch (else a thermal launch follows).
 template <typename R, typename I, int TX, int TY, bool CPL, bool TH>
-__global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
-    em_step_kernel(const __grid_constant__ EmArgs<R> A) {
+__device__ __forceinline__ void em_cta(const EmArgs<R> &A, int b, int step_off, unsigned char *smem,
+                                       typename Pair2<R>::T (*sHxz)[2][TY][TX], typename Pair2<R>::T (*sQy)[TY][TX],
+                                       uint64_t *s_bar, int *s_abort) {
   static_assert(TX == 32, "a tile row is one warp: x neighbours are exchanged by shuffles");
-  using R2 = typename Pair2<R>::T;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  // the launch adds 128 bytes so that the tables and stages can start on a
-  // 128-byte boundary of the shared window (TMA destinations must)
-  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   R *s_cp = reinterpret_cast<R *>(smem);
   R *s_mt = s_cp + kCpmlTable;
   unsigned char *stg = smem + em_stage_offset<R>(A.g.nmat);
-  // double-buffered by plane parity, so that a plane needs one barrier
-  __shared__ R2 sHxz[2][2][TY][TX];  // Hx, Hz of the plane, read by the +y neighbour
-  __shared__ R2 sQy[2][TY][TX];      // Joule share of the y-edge, read by the +y neighbour one plane later
-  __shared__ uint64_t s_bar[kEmStages];  // one transaction barrier per stage
-  __shared__ int s_abort;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
-    // TMA preconditions checked once per CTA: 128-byte aligned destinations
+    // (a CTA that took an earlier tile read these stages: order those reads
+    // before the copies of this tile)
+    fence_proxy_async_smem();
+    // TMA preconditions checked once per tile: 128-byte aligned destinations
     // and 64-byte aligned descriptors; otherwise flag the error and leave
     // without issuing a copy
     bool ok = (smem_u32(stg) & 127u) == 0 && (sizeof(EmStage<R, TX, TY>) & 127u) == 0 &&
@@ -1257,7 +1256,7 @@ __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
            ((size_t)&A.tmE2[c] & 63u) == 0 && ((size_t)&A.tmH2[c] & 63u) == 0;
     ok = ok && ((size_t)&A.tmQ & 63u) == 0 && ((size_t)&A.tmQ2 & 63u) == 0 && ((size_t)&A.tmV & 63u) == 0 &&
          ((size_t)&A.tmV2 & 63u) == 0 && ((size_t)&A.tmT & 63u) == 0 && ((size_t)&A.tmT2 & 63u) == 0;
-    s_abort = ok ? 0 : 1;
+    *s_abort = ok ? 0 : 1;
     if (!ok) atomicExch(A.err, 2);
     for (int q = 0; q < kEmStages; ++q) mbar_init(&s_bar[q], 1);
     fence_mbar_init();
@@ -1265,8 +1264,7 @@ __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
   stage_table(s_mt, A.g.mtab, (A.g.nmat + 1) * M_COLS);
   stage_table(s_cp, A.cpml, kCpmlTable);
   __syncthreads();
-  if (s_abort) return;
-  int b = (int)blockIdx.x;
+  if (*s_abort) return;
   if (b < A.n_border) {
     // border tile b: the rows below the interior rows, then the left and
     // right parts of the interior rows, then the rows above them
@@ -1286,7 +1284,7 @@ __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
       } else {
         xs = A.xb1 + (TX - 1) * (c - A.nl);
       }
-      em_tile_border<R, I, TY, CPL, TH, true, false>(A, s_cp, s_mt, sb, sh, sq, s_bar, &s_abort, xs, xe, by);
+      em_tile_border<R, I, TY, CPL, TH, true, false>(A, s_cp, s_mt, sb, sh, sq, s_bar, s_abort, xs, xe, by, step_off);
     } else {
       if (b >= below) {
         b -= below + mid;
@@ -1300,15 +1298,94 @@ __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
       // nodes i = xs - 1 .. xs + 30: does the tile reach an x slab?
       const bool xsl = (A.slo[0] > 0 && xs - 1 <= A.slo[0]) || (A.shi[0] > 0 && xs + TX - 2 >= A.g.nx - A.shi[0]);
       if (xsl)
-        em_tile_border<R, I, TY, CPL, TH, true, true>(A, s_cp, s_mt, sb, sh, sq, s_bar, &s_abort, xs, xe, by);
+        em_tile_border<R, I, TY, CPL, TH, true, true>(A, s_cp, s_mt, sb, sh, sq, s_bar, s_abort, xs, xe, by, step_off);
       else
-        em_tile_border<R, I, TY, CPL, TH, false, true>(A, s_cp, s_mt, sb, sh, sq, s_bar, &s_abort, xs, xe, by);
+        em_tile_border<R, I, TY, CPL, TH, false, true>(A, s_cp, s_mt, sb, sh, sq, s_bar, s_abort, xs, xe, by,
+                                                       step_off);
     }
   } else {
     b -= A.n_border;
     const int py = b / A.npx, px = b - py * A.npx;
     em_tile_pair<R, I, TY, CPL, TH>(A, s_cp, s_mt, reinterpret_cast<EmStage<R, kEm2Nodes, TY> *>(stg), sHxz, sQy, s_bar,
-                                &s_abort, A.xb0 + 62 * px, A.iby0 + py);
+                                    s_abort, A.xb0 + 62 * px, A.iby0 + py, step_off);
+  }
+}
+
+// One launch per step of one context: CTA b takes tile b.
+template <typename R, typename I, int TX, int TY, bool CPL, bool TH>
+__global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
+    em_step_kernel(const __grid_constant__ EmArgs<R> A) {
+  using R2 = typename Pair2<R>::T;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // the launch adds 128 bytes so that the tables and stages can start on a
+  // 128-byte boundary of the shared window (TMA destinations must)
+  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  // double-buffered by plane parity, so that a plane needs one barrier
+  __shared__ R2 sHxz[2][2][TY][TX];  // Hx, Hz of the plane, read by the +y neighbour
+  __shared__ R2 sQy[2][TY][TX];      // Joule share of the y-edge, read by the +y neighbour one plane later
+  __shared__ uint64_t s_bar[kEmStages];  // one transaction barrier per stage
+  __shared__ int s_abort;
+  em_cta<R, I, TX, TY, CPL, TH>(A, (int)blockIdx.x, A.step_off, smem, sHxz, sQy, s_bar, &s_abort);
+}
+
+// A group of up to kBatchMax contexts (independent package designs) for one
+// launch of a batch step: their arguments for the step's E/H parity and
+// Joule fold, by value in the kernel's parameter space (8 designs fill most
+// of the 32 KB a launch may pass), and cta_start[d], the first tile of design
+// d in the group's tile order (cta_start[n] = all tiles).
+constexpr int kBatchMax = 8;
+template <typename R>
+struct EmBatchArgs {
+  EmArgs<R> a[kBatchMax];
+  int cta_start[kBatchMax + 1];
+  int n;
+};
+
+// One launch per step of a group of designs. work == null: CTA b takes tile
+// b. Otherwise the launch is persistent: a grid of about the resident CTAs
+// takes tiles in order from the counter *work (tiles of the larger designs
+// first, so that the small ones fill the tail), and zeroes *next_work, the
+// counter of the group's next launch (launches alternate between two
+// counters, so that no launch resets a counter in use). The stage barriers
+// are invalidated after each tile and initialised again for the next.
+template <typename R, typename I, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
+    em_batch_kernel(const __grid_constant__ EmBatchArgs<R> P, int step_off, unsigned *work, unsigned *next_work) {
+  using R2 = typename Pair2<R>::T;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  __shared__ R2 sHxz[2][2][TY][TX];
+  __shared__ R2 sQy[2][TY][TX];
+  __shared__ uint64_t s_bar[kEmStages];
+  __shared__ int s_abort, s_tile;
+  const bool t0 = threadIdx.x == 0 && threadIdx.y == 0;
+  const int n = P.n, total = P.cta_start[n];
+  auto design = [&](int b) -> int {  // the last d with cta_start[d] <= b
+    int d = 0;
+    while (d + 1 < n && P.cta_start[d + 1] <= b) ++d;
+    return d;
+  };
+  // One call site for both modes: the tile code is then compiled once for the
+  // batch kernel. (The slot is a run-time index into the parameter space; a
+  // compile-time index per slot, one inlined tile body each, made the
+  // compiler outline the bodies with kilobyte stack frames.)
+  const bool persistent = work != nullptr;
+  if (persistent && blockIdx.x == 0 && t0) *next_work = 0u;
+  int b = (int)blockIdx.x;
+  while (true) {
+    if (persistent) {
+      if (t0) s_tile = (int)atomicAdd(work, 1u);
+      __syncthreads();
+      b = s_tile;
+      if (b >= total) return;
+    }
+    const int d = design(b);
+    em_cta<R, I, TX, TY, false, false>(P.a[d], b - P.cta_start[d], step_off, smem, sHxz, sQy, s_bar, &s_abort);
+    if (!persistent) return;
+    __syncthreads();  // every thread is past the tile's waits and its reads of s_tile
+    if (s_abort) return;
+    if (t0)
+      for (int q = 0; q < kEmStages; ++q) mbar_inval(&s_bar[q]);
   }
 }
 

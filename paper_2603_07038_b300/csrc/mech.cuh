@@ -344,6 +344,7 @@ struct MvTmaArgs {
   int parity;
   const R *zt;
   int *err;
+  long long wait;              // bound of the waits for staged planes, SM clock cycles
 };
 
 template <typename R, int TY, bool DIR>
@@ -432,11 +433,12 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
   if (leader)
     for (int q = 0; q < kMvAhead; ++q) issue(q);
   if constexpr (DIR) {
-    if (!mbar_wait(&bars[0], 0u)) s_abort = 1;  // plane 0 is converted before the loop
+    if (!mbar_wait(&bars[0], 0u, TA.wait)) s_abort = 1;  // plane 0 is converted before the loop
     __syncthreads();
     if (s_abort) {
       if (leader) {
-        for (int q = 0; q < kMvAhead && q <= nz; ++q) mbar_wait(&bars[q % kMvStages], (unsigned)(q / kMvStages) & 1u);
+        for (int q = 0; q < kMvAhead && q <= nz; ++q)
+          mbar_wait(&bars[q % kMvStages], (unsigned)(q / kMvStages) & 1u, TA.wait);
         atomicExch(TA.err, 1);
       }
       return;
@@ -448,15 +450,15 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
   const int cu = 2 * tx + xr;  // element corner (ea, ey) column in the u boxes
   for (int k = 0; k < nz; ++k) {
     {
-      bool ok = mbar_wait(&bars[k % kMvStages], (unsigned)(k / kMvStages) & 1u);
-      ok = mbar_wait(&bars[(k + 1) % kMvStages], (unsigned)((k + 1) / kMvStages) & 1u) && ok;
+      bool ok = mbar_wait(&bars[k % kMvStages], (unsigned)(k / kMvStages) & 1u, TA.wait);
+      ok = mbar_wait(&bars[(k + 1) % kMvStages], (unsigned)((k + 1) / kMvStages) & 1u, TA.wait) && ok;
       if (!ok) s_abort = 1;
     }
     __syncthreads();  // planes k, k+1 landed; every thread is done with plane k-1 and with s_lo
     if (s_abort) {
       if (leader) {
         for (int q = k; q <= k + kMvAhead && q <= nz; ++q)
-          mbar_wait(&bars[q % kMvStages], (unsigned)(q / kMvStages) & 1u);
+          mbar_wait(&bars[q % kMvStages], (unsigned)(q / kMvStages) & 1u, TA.wait);
         atomicExch(TA.err, 1);
       }
       return;

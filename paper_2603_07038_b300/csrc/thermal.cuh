@@ -270,6 +270,7 @@ struct ThTmaArgs {
   ThArgs<R> a;                // geometry, T in / out, P, z records, dt, films
   CUtensorMap tmT, tmP, tmV;  // boxes th_box_t x (kThTY+2), th_tx x kThTY, th_box_v x (kThTY+1) (one plane)
   int *err;
+  long long wait;             // bound of the waits for staged planes, SM clock cycles
   unsigned long long *peak;   // the maximum of the written T (its ordered_bits image) goes here; null: not tracked
 };
 
@@ -346,20 +347,22 @@ __global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? (NP == 1 ? 3 : 2)
   }
   if (leader)
     for (int q = 0; q < kThAhead; ++q) issue(q);
-  bool ok0 = mbar_wait(&bars[0], 0u);
+  bool ok0 = mbar_wait(&bars[0], 0u, TA.wait);
   // unrolled by twice the stage count: stage slots and carried sums resolve
   // at compile time (measured: 4 -> 0.473, 8 -> 0.453 ms per full-package step)
 #pragma unroll 8
   for (int k = 0; k <= nz; ++k) {
     {  // plane k landed one iteration earlier (or above, for k = 0); wait for plane k+1
-      const bool ok = (k + 1 > nz || mbar_wait(&bars[(k + 1) & (kThStages - 1)], (unsigned)((k + 1) / kThStages) & 1u)) && ok0;
+      const bool ok =
+          (k + 1 > nz || mbar_wait(&bars[(k + 1) & (kThStages - 1)], (unsigned)((k + 1) / kThStages) & 1u, TA.wait)) &&
+          ok0;
       if (!ok) s_abort = 1;
     }
     __syncthreads();  // every thread is done with plane k-1: its stage can be refilled
     if (s_abort) {
       if (leader) {
         for (int q = k; q < k + kThAhead && q <= nz; ++q)  // the planes issued so far
-          mbar_wait(&bars[q & (kThStages - 1)], (unsigned)(q / kThStages) & 1u);
+          mbar_wait(&bars[q & (kThStages - 1)], (unsigned)(q / kThStages) & 1u, TA.wait);
         atomicExch(TA.err, 1);
       }
       return;
