@@ -57,6 +57,9 @@ def parse():
     a.add_argument("--no-cg-solve", action="store_true")
     a.add_argument("--serve-n", type=int, default=16)
     a.add_argument("--serve-em-steps", type=int, default=512)
+    a.add_argument("--serve-config5", action="store_true",
+                   help="only the serving trace of the full design mix with 10%% full-scale packages "
+                        "(several minutes); prints its JSON object")
     return a.parse_args()
 
 
@@ -433,15 +436,20 @@ def batched_arm(args, n=64, win=32, windows=3, seed=4, streams=4):
     return out
 
 
-def serving_arm(args, workers=4):
+def serving_arm(args, workers=4, config5=False):
     """Continuous batching of a seeded design trace (after the timed region).
     Burst-length-scaled variant: designs from the batched mix at half lateral
-    size, args.serve_em_steps EM steps (graph-replayed), 2000 thermal steps
-    and a converged stress solve (1e-6) per request; Poisson arrivals at 80 %
-    of the capacity measured on the first designs run back to back. Latencies
-    include queueing."""
+    size (config5: at full size, with 10 % of the requests the full-scale
+    1024 x 1024 x 128 package), args.serve_em_steps EM steps (graph-replayed),
+    2000 thermal steps and a converged stress solve (1e-6) per request;
+    Poisson arrivals at 80 % of the capacity measured on the first designs run
+    back to back. Latencies include queueing."""
     from paper_2603_07038_b300 import serving as S
-    specs = S.design_mix(args.serve_n, seed=11, em_steps=args.serve_em_steps, thermal_steps=2000, scale=0.5)
+    if config5:
+        specs = S.design_mix(args.serve_n, seed=12, em_steps=args.serve_em_steps, thermal_steps=2000,
+                             big_fraction=0.1)
+    else:
+        specs = S.design_mix(args.serve_n, seed=11, em_steps=args.serve_em_steps, thermal_steps=2000, scale=0.5)
     specs = [dataclasses.replace(s, cg_maxit=100000) for s in specs]
     runner = S.DesignRunner(specs, workers=workers)
     runner.run(specs[0], 0)  # warm-up: module load, allocator pools
@@ -470,6 +478,9 @@ def serving_arm(args, workers=4):
     cells = sum(s.cells for s in specs)
     return {"variant": "burst-length-scaled (%d EM steps per request, not the 2 ns burst), ~80%% offered load"
                        % specs[0].em_steps,
+            "mix": "config-5 mix: full-size design grids, %d of %d requests 1024x1024x128" % (
+                sum(1 for sp in specs if (sp.nx, sp.ny, sp.nz) == S.FULL_GRID), len(specs))
+                   if config5 else "design grids at half lateral size",
             "requests": len(specs), "workers": workers, "arrival_rate_per_s": round(rate, 3),
             "p50_s": round(rep["p50_s"], 4), "p99_s": round(rep["p99_s"], 4),
             "designs_per_hour": round(rep["designs_per_hour"], 1), "makespan_s": round(rep["makespan_s"], 3),
@@ -687,6 +698,13 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(reference_arm(args)))
+        return
+    if args.serve_config5:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2603_07038_b300 import build as B
+        B.build()
+        print(json.dumps({"serving_config5": serving_arm(args, config5=True)}))
         return
     if world > 1:
         import torch

@@ -49,14 +49,25 @@ class DesignSpec:
         return self.nx * self.ny * self.nz
 
 
+# the full-scale package grid that the serving trace mixes in
+FULL_GRID = (1024, 1024, 128)
+
+
 def design_mix(n: int, seed: int = 0, em_steps: int = 256, thermal_steps: int = 100, scale: float = 1.0,
-               grids: Sequence = DESIGN_GRIDS) -> list[DesignSpec]:
+               grids: Sequence = DESIGN_GRIDS, big_fraction: float = 0.0) -> list[DesignSpec]:
     """n seeded designs: grid drawn uniformly from ``grids`` (lateral size
-    multiplied by ``scale``), TSV pitch uniform in 4..8 voxels (40-80 um)."""
+    multiplied by ``scale``), TSV pitch uniform in 4..8 voxels (40-80 um);
+    with probability ``big_fraction`` a request is the full-scale
+    1024 x 1024 x 128 package instead (not scaled)."""
     rng = np.random.default_rng(seed)
     out = []
     for s in range(n):
+        big = big_fraction > 0 and rng.random() < big_fraction
         nx, ny, nz = grids[int(rng.integers(0, len(grids)))]
+        if big:
+            out.append(DesignSpec(seed=s, nx=FULL_GRID[0], ny=FULL_GRID[1], nz=FULL_GRID[2],
+                                  tsv_pitch=int(rng.integers(4, 9)), em_steps=em_steps, thermal_steps=thermal_steps))
+            continue
         nx, ny = max(48, int(round(nx * scale))), max(48, int(round(ny * scale)))
         out.append(DesignSpec(seed=s, nx=nx, ny=ny, nz=nz, tsv_pitch=int(rng.integers(4, 9)),
                               em_steps=em_steps, thermal_steps=thermal_steps))
