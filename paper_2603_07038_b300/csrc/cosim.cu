@@ -1629,8 +1629,8 @@ static cosim_status matvec_t(cosim_ctx *c, void *const u[3], void *const y[3], d
 // The PCG's fused direction update and product (hex8_matvec_tma_kernel, DIR):
 // p_new = D^-1 r + beta p_old with p_old in direction buffer `from` (Pv or
 // Pv2) and beta from the r.z pair of `parity`, written to the other buffer;
-// Qv = K p_new with the p.Kp partial sums. Needs the DIR stages in shared
-// memory (mv_dir_fits).
+// U += alpha p_old with the previous iteration's alpha; Qv = K p_new with the
+// p.Kp partial sums. Needs the DIR stages in shared memory (mv_dir_fits).
 template <typename R>
 static bool mv_dir_fits(const cosim_ctx *c) {
   return mv_smem_bytes<R, kMvTY, true>((int)c->mats.size()) <= kMaxSmemOptin;
@@ -1647,6 +1647,8 @@ static cosim_status matvec_dir(cosim_ctx *c, int from, int parity, double *parti
     T.tmR[a] = c->mvR[a];
     T.tmD[a] = c->mvD[a];
     T.pn[a] = (R *)pnew[a];
+    T.x[a] = (R *)c->U[a];  // the previous direction's step lands in the solution here
+    T.po[a] = (const R *)(from ? c->Pv2 : c->Pv)[a];
   }
   T.a.mask = c->mask;
   T.a.partial = partial;
@@ -1735,9 +1737,17 @@ static cosim_status pcg_run(cosim_ctx *c, double rtol, int64_t maxit, int every,
     if (st != COSIM_OK) return st;
     R *const *P = Pb[cur];
     reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pa, nmv, &c->cg->pq); ++c->launches;
-    cg_update_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, c->cg, parity, U[0], U[1], U[2], Rv[0], Rv[1], Rv[2],
-                                                           P[0], P[1], P[2], Qv[0], Qv[1], Qv[2], D[0], D[1],
-                                                           D[2], pa, pb); ++c->launches;
+    // fused: the solution's update x += alpha p waits for the next product
+    // (or the final axpy), so this pass streams r, q and D only
+    if (fuse)
+      cg_update_kernel<R, false><<<kRedBlocks, 256, 0, c->stream>>>(n, c->cg, parity, U[0], U[1], U[2], Rv[0], Rv[1],
+                                                                    Rv[2], P[0], P[1], P[2], Qv[0], Qv[1], Qv[2],
+                                                                    D[0], D[1], D[2], pa, pb);
+    else
+      cg_update_kernel<R, true><<<kRedBlocks, 256, 0, c->stream>>>(n, c->cg, parity, U[0], U[1], U[2], Rv[0], Rv[1],
+                                                                   Rv[2], P[0], P[1], P[2], Qv[0], Qv[1], Qv[2], D[0],
+                                                                   D[1], D[2], pa, pb);
+    ++c->launches;
     reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pa, kRedBlocks, &c->cg->rz[parity ^ 1]); ++c->launches;
     reduce_final_kernel<<<1, 1024, 0, c->stream>>>(pb, kRedBlocks, &c->cg->rr); ++c->launches;
     CHECK_LAUNCH(c);
@@ -1761,6 +1771,12 @@ static cosim_status pcg_run(cosim_ctx *c, double rtol, int64_t maxit, int every,
     }
   }
   *iters = it;
+  if (fuse && it > 0) {  // the last direction's step (the products applied the earlier ones)
+    cg_axpy_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, c->cg, (int)((it - 1) & 1), U[0], U[1], U[2], Pb[cur][0],
+                                                         Pb[cur][1], Pb[cur][2]);
+    ++c->launches;
+    CHECK_LAUNCH(c);
+  }
   if (scale != 1.0) {
     scale3_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, U[0], U[1], U[2], (R)(1.0 / scale)); ++c->launches;
     CHECK_LAUNCH(c);

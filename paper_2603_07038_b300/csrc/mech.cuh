@@ -297,9 +297,10 @@ __global__ void __launch_bounds__(TX *TY) hex8_matvec_kernel(const MvArgs<R> A) 
 // r.z / r.z of the previous iteration) is fused into the staging: the
 // residual, the inverse diagonal and the previous direction of each plane
 // are copied instead of p, the new direction of the whole staged box is
-// formed in shared memory once the plane has landed, the product uses it,
-// and the owners write it to the other direction buffer (p is
-// double-buffered: neighbouring CTAs still read the old one).
+// formed in shared memory two planes ahead of its first use (so that the
+// plane's first barrier also publishes it), the product uses it, and the
+// owners write it to the other direction buffer (p is double-buffered:
+// neighbouring CTAs still read the old one).
 constexpr int kMvStages = 4, kMvAhead = 3;
 constexpr int kMvElems = 64;  // elements per warp row
 template <typename R, int TY, bool DIR>
@@ -340,6 +341,9 @@ struct MvTmaArgs {
   CUtensorMap tmU[3], tmM, tmV;
   CUtensorMap tmR[3], tmD[3];  // DIR: residual, inverse diagonal
   R *pn[3];                    // DIR: the new direction, written at the owned nodes
+  R *x[3];                     // DIR: the iterate, x += alpha p_old at the owned nodes (alpha of the previous
+                               // iteration, sc->rz[parity] / sc->pq); null: left to the update pass
+  const R *po[3];              // DIR with x: p_old in global memory (the buffer the stages copy)
   const CgScalars *sc;         // DIR: beta = sc->rz[parity ^ 1] / sc->rz[parity]
   int parity;
   const R *zt;
@@ -416,8 +420,12 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
   // DIR: the new direction of every staged node of plane kk, in place of the
   // old one (positions outside the grid arrived as zeros and stay zero); the
   // proxy fence orders these writes before the stage's next TMA fill
-  R beta = R(0);
-  if constexpr (DIR) beta = (R)(TA.sc->rz[TA.parity ^ 1] / TA.sc->rz[TA.parity]);
+  R beta = R(0), alpha = R(0);
+  if constexpr (DIR) {
+    beta = (R)(TA.sc->rz[TA.parity ^ 1] / TA.sc->rz[TA.parity]);
+    alpha = (R)(TA.sc->rz[TA.parity] / TA.sc->pq);  // (the previous iteration's step length)
+  }
+  const bool with_x = DIR && TA.x[0] != nullptr;
   auto convert = [&](int kk) {
     if constexpr (DIR) {
       Stage &S = stg[kk % kMvStages];
@@ -432,8 +440,10 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
   };
   if (leader)
     for (int q = 0; q < kMvAhead; ++q) issue(q);
-  if constexpr (DIR) {
-    if (!mbar_wait(&bars[0], 0u, TA.wait)) s_abort = 1;  // plane 0 is converted before the loop
+  if constexpr (DIR) {  // planes 0 and 1 are converted before the loop (nz >= 1)
+    bool ok = mbar_wait(&bars[0], 0u, TA.wait);
+    ok = mbar_wait(&bars[1], 0u, TA.wait) && ok;
+    if (!ok) s_abort = 1;
     __syncthreads();
     if (s_abort) {
       if (leader) {
@@ -444,6 +454,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
       return;
     }
     convert(0);
+    convert(1);
   }
   R2 acc[3] = {bc_<R2>(R(0)), bc_<R2>(R(0)), bc_<R2>(R(0))};
   double dot = 0.0;
@@ -452,9 +463,14 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
     {
       bool ok = mbar_wait(&bars[k % kMvStages], (unsigned)(k / kMvStages) & 1u, TA.wait);
       ok = mbar_wait(&bars[(k + 1) % kMvStages], (unsigned)((k + 1) / kMvStages) & 1u, TA.wait) && ok;
+      // DIR: plane k+2 is converted in this iteration, for use from the next
+      if (DIR && k + 2 <= nz)
+        ok = mbar_wait(&bars[(k + 2) % kMvStages], (unsigned)((k + 2) / kMvStages) & 1u, TA.wait) && ok;
       if (!ok) s_abort = 1;
     }
-    __syncthreads();  // planes k, k+1 landed; every thread is done with plane k-1 and with s_lo
+    // planes k, k+1 (and k+2) landed, k and k+1 converted; every thread is
+    // done with plane k-1 and with s_lo
+    __syncthreads();
     if (s_abort) {
       if (leader) {
         for (int q = k; q <= k + kMvAhead && q <= nz; ++q)
@@ -467,12 +483,25 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
       fence_proxy_async_smem();
       issue(k + kMvAhead);
     }
-    if constexpr (DIR) {
-      convert(k + 1);
-      __syncthreads();  // the new direction of plane k+1 is in place
-    }
+    // DIR: the new direction of plane k+2 (its stage is read from the next
+    // iteration on, after that iteration's barrier)
+    if constexpr (DIR)
+      if (k + 2 <= nz) convert(k + 2);
     const Stage &S0 = stg[k % kMvStages];
     const Stage &S1 = stg[(k + 1) % kMvStages];
+    // DIR with x: the owned nodes' x and p_old of this plane, requested now and
+    // used in the owner phase (the element arithmetic hides their latency)
+    R xo[3][2], pv[3][2];
+    if (with_x && (oa || ob)) {
+      const long long id = g.nid(XA, Y, k);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        xo[c][0] = oa ? TA.x[c][id] : R(0);
+        pv[c][0] = oa ? TA.po[c][id] : R(0);
+        xo[c][1] = ob ? TA.x[c][id + 1] : R(0);
+        pv[c][1] = ob ? TA.po[c][id + 1] : R(0);
+      }
+    }
     R2 r[3][8];
     if (va || vb) {
       const int ma = va ? (int)S0.V.v[ty][2 * tx + xmr] : 0, mb = vb ? (int)S0.V.v[ty][2 * tx + 1 + xmr] : 0;
@@ -533,12 +562,18 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
         if (oa) {
           A.y[c][id] = ya;
           part += ya * ua;
-          if constexpr (DIR) TA.pn[c][id] = ua;
+          if constexpr (DIR) {
+            TA.pn[c][id] = ua;
+            if (with_x) TA.x[c][id] = fma_(alpha, pv[c][0], xo[c][0]);
+          }
         }
         if (ob) {
           A.y[c][id + 1] = yb;
           part += yb * ub;
-          if constexpr (DIR) TA.pn[c][id + 1] = ub;
+          if constexpr (DIR) {
+            TA.pn[c][id + 1] = ub;
+            if (with_x) TA.x[c][id + 1] = fma_(alpha, pv[c][1], xo[c][1]);
+          }
         }
         acc[c] = top;
       }
@@ -557,12 +592,18 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
       if (oa) {
         A.y[c][id] = ya;
         part += ya * ua;
-        if constexpr (DIR) TA.pn[c][id] = ua;
+        if constexpr (DIR) {
+          TA.pn[c][id] = ua;
+          if (with_x) TA.x[c][id] = fma_(alpha, TA.po[c][id], TA.x[c][id]);
+        }
       }
       if (ob) {
         A.y[c][id + 1] = yb;
         part += yb * ub;
-        if constexpr (DIR) TA.pn[c][id + 1] = ub;
+        if constexpr (DIR) {
+          TA.pn[c][id + 1] = ub;
+          if (with_x) TA.x[c][id + 1] = fma_(alpha, TA.po[c][id + 1], TA.x[c][id + 1]);
+        }
       }
     }
     dot += (double)part;
@@ -776,11 +817,12 @@ __global__ void __launch_bounds__(256) sumsq3_kernel(long long n, const R *f0, c
   if (threadIdx.x == 0) part[blockIdx.x] = ss;
 }
 
-// x += alpha p, r -= alpha q, alpha = rz/pq; partial sums of r.(D^-1 r) and r.r
-// (each node's three-component terms in the context precision, accumulated in
-// FP64). FP32 vectors are streamed four nodes per load (n is a multiple of 4:
-// the padded node arrays have rows of a multiple of 32).
-template <typename R>
+// x += alpha p (X; otherwise the next product applies it), r -= alpha q,
+// alpha = rz/pq; partial sums of r.(D^-1 r) and r.r (each node's
+// three-component terms in the context precision, accumulated in FP64). FP32
+// vectors are streamed four nodes per load (n is a multiple of 4: the padded
+// node arrays have rows of a multiple of 32).
+template <typename R, bool X>
 __global__ void __launch_bounds__(256) cg_update_kernel(long long n, const CgScalars *sc, int parity, R *x0, R *x1,
                                                          R *x2, R *r0, R *r1, R *r2, const R *p0, const R *p1,
                                                          const R *p2, const R *q0, const R *q1, const R *q2,
@@ -790,18 +832,22 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long n, const CgSca
   double rz = 0, rr = 0;
   const long long stride = (long long)gridDim.x * blockDim.x, first = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if constexpr (sizeof(R) == 4) {
-    R *X[3] = {x0, x1, x2}, *Rr[3] = {r0, r1, r2};
+    R *Xv[3] = {x0, x1, x2}, *Rr[3] = {r0, r1, r2};
     const R *P[3] = {p0, p1, p2}, *Q[3] = {q0, q1, q2}, *D[3] = {d0, d1, d2};
     for (long long v = first; v < (n >> 2); v += stride) {
       float4 a[3], dd[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float4 pv = reinterpret_cast<const float4 *>(P[c])[v], qv = reinterpret_cast<const float4 *>(Q[c])[v];
-        float4 xv = reinterpret_cast<const float4 *>(X[c])[v], rv = reinterpret_cast<const float4 *>(Rr[c])[v];
+        const float4 qv = reinterpret_cast<const float4 *>(Q[c])[v];
+        float4 rv = reinterpret_cast<const float4 *>(Rr[c])[v];
         dd[c] = reinterpret_cast<const float4 *>(D[c])[v];
-        xv.x += alpha * pv.x, xv.y += alpha * pv.y, xv.z += alpha * pv.z, xv.w += alpha * pv.w;
+        if constexpr (X) {
+          const float4 pv = reinterpret_cast<const float4 *>(P[c])[v];
+          float4 xv = reinterpret_cast<const float4 *>(Xv[c])[v];
+          xv.x += alpha * pv.x, xv.y += alpha * pv.y, xv.z += alpha * pv.z, xv.w += alpha * pv.w;
+          reinterpret_cast<float4 *>(Xv[c])[v] = xv;
+        }
         rv.x -= alpha * qv.x, rv.y -= alpha * qv.y, rv.z -= alpha * qv.z, rv.w -= alpha * qv.w;
-        reinterpret_cast<float4 *>(X[c])[v] = xv;
         reinterpret_cast<float4 *>(Rr[c])[v] = rv;
         a[c] = rv;
       }
@@ -816,9 +862,11 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long n, const CgSca
     }
   } else {
     for (long long q = first; q < n; q += stride) {
-      x0[q] += alpha * p0[q];
-      x1[q] += alpha * p1[q];
-      x2[q] += alpha * p2[q];
+      if constexpr (X) {
+        x0[q] += alpha * p0[q];
+        x1[q] += alpha * p1[q];
+        x2[q] += alpha * p2[q];
+      }
       const R a0 = r0[q] - alpha * q0[q], a1 = r1[q] - alpha * q1[q], a2 = r2[q] - alpha * q2[q];
       r0[q] = a0; r1[q] = a1; r2[q] = a2;
       rz += (double)(a0 * d0[q] * a0 + a1 * d1[q] * a1 + a2 * d2[q] * a2);
@@ -830,6 +878,34 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long n, const CgSca
   if (threadIdx.x == 0) {
     part_rz[blockIdx.x] = rz;
     part_rr[blockIdx.x] = rr;
+  }
+}
+
+// x += alpha p, alpha = rz[parity] / pq: the last direction's step when the
+// products applied the earlier ones (FP32: four nodes per access)
+template <typename R>
+__global__ void __launch_bounds__(256) cg_axpy_kernel(long long n, const CgScalars *sc, int parity, R *x0, R *x1,
+                                                       R *x2, const R *p0, const R *p1, const R *p2) {
+  const R alpha = (R)(sc->rz[parity] / sc->pq);
+  const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  if constexpr (sizeof(R) == 4) {
+    float4 *X[3] = {reinterpret_cast<float4 *>(x0), reinterpret_cast<float4 *>(x1), reinterpret_cast<float4 *>(x2)};
+    const float4 *P[3] = {reinterpret_cast<const float4 *>(p0), reinterpret_cast<const float4 *>(p1),
+                          reinterpret_cast<const float4 *>(p2)};
+    for (long long v = first; v < (n >> 2); v += stride)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float4 x = X[c][v];
+        const float4 p = P[c][v];
+        x.x += alpha * p.x, x.y += alpha * p.y, x.z += alpha * p.z, x.w += alpha * p.w;
+        X[c][v] = x;
+      }
+  } else {
+    for (long long q = first; q < n; q += stride) {
+      x0[q] += alpha * p0[q];
+      x1[q] += alpha * p1[q];
+      x2[q] += alpha * p2[q];
+    }
   }
 }
 

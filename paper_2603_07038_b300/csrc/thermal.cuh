@@ -287,8 +287,20 @@ __device__ __forceinline__ void peak_max(R v, unsigned long long *peak) {
   if ((threadIdx.x & 31) == 0) atomicMax(peak, ordered_bits((double)v));
 }
 
+// resident CTAs per SM the kernel is compiled for (FP32 one / two pairs)
+#ifndef COSIM_TH1_MIN_CTAS
+#define COSIM_TH1_MIN_CTAS 3
+#endif
+#ifndef COSIM_TH2_MIN_CTAS
+#define COSIM_TH2_MIN_CTAS 2
+#endif
+#ifndef COSIM_TH_UNROLL
+#define COSIM_TH_UNROLL 8
+#endif
+constexpr int kThUnroll = COSIM_TH_UNROLL;  // plane-loop unroll (twice the stage count by default)
 template <typename R, int NP>
-__global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? (NP == 1 ? 3 : 2) : (NP == 1 ? 2 : 1))
+__global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? (NP == 1 ? COSIM_TH1_MIN_CTAS : COSIM_TH2_MIN_CTAS)
+                                                             : (NP == 1 ? 2 : 1))
     thermal_tma_kernel(const __grid_constant__ ThTmaArgs<R> TA) {
   using R2 = typename Pair2<R>::T;
   constexpr int kThTX = th_tx(NP), kThBoxT = th_box_t(NP), kThBoxV = th_box_v(NP);
@@ -350,7 +362,7 @@ __global__ void __launch_bounds__(32 * kThTY, sizeof(R) == 4 ? (NP == 1 ? 3 : 2)
   bool ok0 = mbar_wait(&bars[0], 0u, TA.wait);
   // unrolled by twice the stage count: stage slots and carried sums resolve
   // at compile time (measured: 4 -> 0.473, 8 -> 0.453 ms per full-package step)
-#pragma unroll 8
+#pragma unroll kThUnroll
   for (int k = 0; k <= nz; ++k) {
     {  // plane k landed one iteration earlier (or above, for k = 0); wait for plane k+1
       const bool ok =
