@@ -39,12 +39,12 @@ N_EM, N_TH, N_CG = 96, 3, 3
 N_CPL = 32  # coupled EM + thermal steps timed after the main region
 METRIC = "Gcell-updates/s & % HBM roofline (EM+thermal); stress-CG s/solve; designs/hr, p50/p99"
 UNIT = "Gcell-updates/s"
-def workload_name(nx, ny):
+def workload_name(nx, ny, nz=128):
     """The workload label: the full-scale package at the default size, else
     the reduced grid that was actually run."""
-    if (nx, ny) == (1024, 1024):
+    if (nx, ny, nz) == (1024, 1024, 128):
         return "full-scale layered package 1024x1024x128 (134M cells), FP32"
-    return f"layered package {nx}x{ny}x128 ({nx * ny * 128 / 1e6:.0f}M cells, reduced), FP32"
+    return f"layered package {nx}x{ny}x{nz} ({nx * ny * nz / 1e6:.0f}M cells, reduced), FP32"
 
 
 def parse():
@@ -55,6 +55,7 @@ def parse():
     a.add_argument("--impl", default="cosim", choices=["cosim", "reference"])
     a.add_argument("--nx", type=int, default=1024)
     a.add_argument("--ny", type=int, default=1024)
+    a.add_argument("--nz", type=int, default=128, help="layers of the package (>= 64; reduced grids for profiling)")
     a.add_argument("--no-e2e", action="store_true")
     a.add_argument("--no-cpu", action="store_true")
     a.add_argument("--no-serve", action="store_true")
@@ -156,7 +157,7 @@ def kernel_source_hash(paths):
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(kernel_srcs, nx, ny):
+def traffic_from_profile(kernel_srcs, nx, ny, nz):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel source (em.cuh and the common.cuh it includes) and on
     this workload (the 1024 x 1024 x 128 package); else None."""
@@ -164,7 +165,7 @@ def traffic_from_profile(kernel_srcs, nx, ny):
     try:
         t = json.load(open(path))
         h = kernel_source_hash(kernel_srcs)
-        if t.get("em_step_kernel", {}).get("source_sha256_16") == h and (nx, ny) == (1024, 1024):
+        if t.get("em_step_kernel", {}).get("source_sha256_16") == h and (nx, ny, nz) == (1024, 1024, 128):
             return t["em_step_kernel"]["dram_bytes_per_launch"]
     except Exception:
         pass
@@ -199,7 +200,7 @@ def gpu_arm(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     api.load()
-    p = W.layered_package(args.nx, args.ny, seed=2 + rank)
+    p = W.layered_package(args.nx, args.ny, seed=2 + rank, nz=args.nz)
     stream = torch.cuda.current_stream()
     total_em = (args.warmup + args.steps + 4) * N_EM
     ctx = api.Context(p, precision=api.COSIM_FP32, stream=stream, use_torch_allocator=True)
@@ -280,12 +281,12 @@ def gpu_arm(args, rank, world):
     peak = peaks["hbm_gbs"] if peaks else 6400.0
     achieved = alg / (em_launch_ms * 1e-3) / 1e9
     csrc = os.path.join(ROOT, "paper_2603_07038_b300", "csrc")
-    traffic = traffic_from_profile([os.path.join(csrc, "em.cuh"), os.path.join(csrc, "common.cuh")], args.nx, args.ny)
+    traffic = traffic_from_profile([os.path.join(csrc, "em.cuh"), os.path.join(csrc, "common.cuh")], args.nx, args.ny, args.nz)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded layered package generator)",
-        "config": {"workload": workload_name(args.nx, args.ny), "nx": args.nx, "ny": args.ny, "nz": 128, "cells": p.n_cells,
+        "config": {"workload": workload_name(args.nx, args.ny, args.nz), "nx": args.nx, "ny": args.ny, "nz": args.nz, "cells": p.n_cells,
                    "nodes": p.n_nodes, "step": f"{N_EM} EM steps + Joule + {N_TH} thermal steps + "
                                            f"stress slice ({N_CG} PCG iterations); value counts the EM cell-steps "
                                            f"and thermal node-steps over the whole step's time",
@@ -677,7 +678,7 @@ def cpu_baseline(args, p, samples=6):
 
 def reference_arm(args):
     import workloads as W
-    p = W.layered_package(args.nx, args.ny, seed=2)
+    p = W.layered_package(args.nx, args.ny, seed=2, nz=args.nz)
     ob = OracleBaseline(p)
     try:
         for _ in range(args.warmup):
@@ -695,7 +696,7 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(upd / (v * 1e9) * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded layered package generator)",
-            "config": {"workload": workload_name(args.nx, args.ny), "nx": args.nx, "ny": args.ny, "nz": 128,
+            "config": {"workload": workload_name(args.nx, args.ny, args.nz), "nx": args.nx, "ny": args.ny, "nz": args.nz,
                        "step": f"{N_EM} EM steps + {N_TH} thermal steps + {N_CG} CG iterations; ms_per_step is "
                                f"extrapolated from the per-point times of each sample"},
             "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": ob.procs, "kind": "oracle",

@@ -755,7 +755,6 @@ static cosim_status launch_thermal(cosim_ctx *c, R dt, bool count = true, unsign
     T.tmP = c->thP[q];
     T.tmV = c->thV[q];
     T.err = c->dev_err;
-  T.wait = c->wait_cycles;
     T.wait = c->wait_cycles;
     const dim3 blk(32, kThTY), grd((c->nx + 1 + th_tx(c->th_np) - 1) / th_tx(c->th_np), (c->ny + 1 + kThTY - 1) / kThTY);
     if (c->th_np == 2) {
