@@ -79,7 +79,7 @@ __device__ __forceinline__ void stage_table(R *dst, const R *src, int n) {
 // address). Completion is tracked with commit/wait groups.
 template <int N>
 __device__ __forceinline__ void cp_async(void *smem, const void *gmem, bool ok) {
-  static_assert(N == 4 || N == 8, "cp.async size");
+  static_assert(N == 4 || N == 8 || N == 16, "cp.async size");
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   const int n = ok ? N : 0;
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(s), "l"(gmem), "n"(N), "r"(n) : "memory");

@@ -541,7 +541,10 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
       ALLOC(c, c->E[p][a], c->npad * c->rsz);
       ALLOC(c, c->H[p][a], c->npad * c->rsz);
       for (int s2 = 0; s2 < 2; ++s2)
-        if (c->psi_len[a] > 0) {
+        if (c->psi_len[a] > 0 && a < 2) {  // x / y slabs: one 16-byte record per element
+          ALLOC(c, c->xE[p][a][s2], c->psi_len[a] * 16);
+          ALLOC(c, c->xH[p][a][s2], c->psi_len[a] * 16);
+        } else if (c->psi_len[a] > 0) {  // z slab: chi (high part), previous derivative, chi low part
           ALLOC(c, c->xE[p][a][s2], c->psi_len[a] * c->rsz);
           ALLOC(c, c->dE[p][a][s2], c->psi_len[a] * c->rsz);
           ALLOC(c, c->xH[p][a][s2], c->psi_len[a] * c->rsz);
@@ -2290,14 +2293,11 @@ static std::vector<std::pair<void *, size_t>> ck_arrays(cosim_ctx *c, int par, i
   for (int a = 0; a < 3; ++a) v.emplace_back(c->H[par][a], nb);
   for (int a = 0; a < 3; ++a)
     for (int s2 = 0; s2 < 2; ++s2)
-      if (c->psi_len[a] > 0) {
-        const size_t pb = (size_t)c->psi_len[a] * c->rsz;
-        v.emplace_back(c->xE[par][a][s2], pb);
-        v.emplace_back(c->dE[par][a][s2], pb);
-        v.emplace_back(c->xH[par][a][s2], pb);
-        v.emplace_back(c->dH[par][a][s2], pb);
-        if (c->lE[par][a][s2]) v.emplace_back(c->lE[par][a][s2], pb);
-        if (c->lH[par][a][s2]) v.emplace_back(c->lH[par][a][s2], pb);
+      if (c->psi_len[a] > 0) {  // x / y: records; z: separate arrays
+        const size_t pb = (size_t)c->psi_len[a] * (a < 2 ? 16 : c->rsz);
+        for (void *q : {c->xE[par][a][s2], c->dE[par][a][s2], c->xH[par][a][s2], c->dH[par][a][s2],
+                        c->lE[par][a][s2], c->lH[par][a][s2]})
+          if (q) v.emplace_back(q, pb);
       }
   v.emplace_back(c->Qs, nb);
   v.emplace_back(c->Q, (size_t)c->npad * 8);
@@ -2321,7 +2321,7 @@ extern "C" cosim_status cosim_checkpoint_save(cosim_ctx *c, void *dst, size_t by
   if (!dst || bytes != need) return fail(c, COSIM_ERR_INVALID, "checkpoint buffer size mismatch");
   CkHeader h{};
   std::memcpy(h.magic, "COSIMCK1", 8);
-  h.version = 1, h.prec = c->prec, h.nx = c->nx, h.ny = c->ny, h.nz = c->nz, h.px = c->px, h.L = c->L;
+  h.version = 2, h.prec = c->prec, h.nx = c->nx, h.ny = c->ny, h.nz = c->nz, h.px = c->px, h.L = c->L;
   h.par = c->par, h.tpar = c->tpar, h.qs_dirty = c->qs_dirty ? 1 : 0;
   h.npad = c->npad, h.step = c->step, h.n_acc = c->n_acc;
   for (int a = 0; a < 3; ++a) h.psi_len[a] = c->psi_len[a];
@@ -2344,7 +2344,7 @@ extern "C" cosim_status cosim_checkpoint_load(cosim_ctx *c, const void *src, siz
   if (!src || bytes < sizeof(CkHeader)) return fail(c, COSIM_ERR_INVALID, "checkpoint too short");
   CkHeader h{};
   CHECK_CUDA(c, cudaMemcpy(&h, src, sizeof h, src_is_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
-  bool same = std::memcmp(h.magic, "COSIMCK1", 8) == 0 && h.version == 1 && h.prec == c->prec && h.nx == c->nx &&
+  bool same = std::memcmp(h.magic, "COSIMCK1", 8) == 0 && h.version == 2 && h.prec == c->prec && h.nx == c->nx &&
               h.ny == c->ny && h.nz == c->nz && h.px == c->px && h.L == c->L && h.npad == c->npad &&
               (h.par == 0 || h.par == 1) && (h.tpar == 0 || h.tpar == 1);
   for (int a = 0; a < 3; ++a) same = same && h.psi_len[a] == c->psi_len[a];

@@ -61,8 +61,14 @@ struct EmArgs {
   // to -dF for slowly varying fields, so dF + psi cancels and FP32 kept no bits
   // of the residue; chi is that residue itself. Near the inner edge of a layer
   // b is close to 1 and chi sums the derivative changes of thousands of steps,
-  // so in FP32 it is carried as an unevaluated pair chi = hi + lo (lEo..lHn,
-  // null in FP64 contexts) updated with error-free transformations.
+  // so in FP32 it is carried as an unevaluated pair chi = hi + lo updated
+  // with error-free transformations. The x and y slabs (d = 0, 1: the border
+  // tiles) keep one 16-byte record per element in xEo..xHn: FP32 {chi hi,
+  // chi lo, dF^{n-1}, unused}, FP64 {chi, dF^{n-1}}, so that a state takes one
+  // vector load, store or copy; dEo..lHn are null there. The z slab (d = 2,
+  // mostly read by the pair tiles as x-adjacent node pairs) keeps separate
+  // arrays: chi (hi) in xEo.., dF^{n-1} in dEo.., chi lo in lEo.. (null in
+  // FP64 contexts).
   const R *xEo[3][2], *dEo[3][2], *lEo[3][2];
   R *xEn[3][2], *dEn[3][2], *lEn[3][2];
   const R *xHo[3][2], *dHo[3][2], *lHo[3][2];
@@ -140,6 +146,40 @@ __device__ __forceinline__ long long psi_index(const EmArgs<R> &A, int d, int s,
   return ((long long)s * (A.g.ny + 1) + j) * A.g.px + i;
 }
 
+// The record layout of the x / y slab states: kPsiRec values of R per
+// element (16 bytes), read and written as one vector.
+template <typename R>
+struct PsiVec;
+template <>
+struct PsiVec<float> {
+  using T = float4;
+};
+template <>
+struct PsiVec<double> {
+  using T = double2;
+};
+template <typename R>
+constexpr int kPsiRec = 16 / (int)sizeof(R);
+template <typename R>
+__device__ __forceinline__ void ld_rec(const R *p, R &hi, R &lo, R &d) {
+  const typename PsiVec<R>::T v = *reinterpret_cast<const typename PsiVec<R>::T *>(p);
+  if constexpr (sizeof(R) == 4) {
+    hi = v.x, lo = v.y, d = v.z;
+  } else {
+    hi = v.x, lo = R(0), d = v.y;
+  }
+}
+template <typename R>
+__device__ __forceinline__ void st_rec(R *p, R hi, R lo, R d) {
+  typename PsiVec<R>::T v;
+  if constexpr (sizeof(R) == 4) {
+    v = make_float4(hi, lo, d, 0.0f);
+  } else {
+    v = make_double2(hi, d);
+  }
+  *reinterpret_cast<typename PsiVec<R>::T *>(p) = v;
+}
+
 // CPML state of one derivative at element q of the slab arrays of axis d,
 // slot `slot` (V: one node, or an x-adjacent node pair at an even q): chi,
 // its low part (FP32 contexts) and the previous derivative. The loads of a
@@ -161,9 +201,15 @@ __device__ __forceinline__ Psi<V> psi_pre(const EmArgs<R> &A, int d, int type, i
   p.s = s;
   p.q = q;
   if (s >= 0) {
-    p.c.hi = ldv_<V>((type == 0 ? A.xEo[d][slot] : A.xHo[d][slot]) + q);
-    p.c.d = ldv_<V>((type == 0 ? A.dEo[d][slot] : A.dHo[d][slot]) + q);
-    if constexpr (sizeof(R) == 4) p.c.lo = ldv_<V>((type == 0 ? A.lEo[d][slot] : A.lHo[d][slot]) + q);
+    if (d < 2) {  // a record (single nodes only: the pair tiles hold no x / y slab node)
+      static_assert(sizeof(V) == sizeof(R) || sizeof(V) == 2 * sizeof(R), "one node or a node pair");
+      if constexpr (sizeof(V) == sizeof(R))
+        ld_rec<R>((type == 0 ? A.xEo[d][slot] : A.xHo[d][slot]) + q * kPsiRec<R>, p.c.hi, p.c.lo, p.c.d);
+    } else {
+      p.c.hi = ldv_<V>((type == 0 ? A.xEo[d][slot] : A.xHo[d][slot]) + q);
+      p.c.d = ldv_<V>((type == 0 ? A.dEo[d][slot] : A.dHo[d][slot]) + q);
+      if constexpr (sizeof(R) == 4) p.c.lo = ldv_<V>((type == 0 ? A.lEo[d][slot] : A.lHo[d][slot]) + q);
+    }
   }
   return p;
 }
@@ -174,6 +220,7 @@ __device__ __forceinline__ Psi<V> psi_pre(const EmArgs<R> &A, int d, int type, i
 template <typename R, typename V>
 __device__ __forceinline__ V psi_apply(const EmArgs<R> &A, V omb, int d, int type, int slot, const Psi<V> &p, V deriv,
                                        bool write) {
+  static_assert(sizeof(V) == sizeof(R), "one node at a time");
   if (p.s < 0) return deriv;
   const long long q = p.q;
   R *xn = type == 0 ? A.xEn[d][slot] : A.xHn[d][slot];
@@ -182,8 +229,12 @@ __device__ __forceinline__ V psi_apply(const EmArgs<R> &A, V omb, int d, int typ
     const V t = add_(p.c.hi, sub_(deriv, p.c.d));
     const V chi = fma_(neg_(omb), t, t);
     if (write) {
-      stv_(xn + q, chi);
-      stv_(dn + q, deriv);
+      if (d < 2) {
+        st_rec<R>(xn + q * kPsiRec<R>, chi, R(0), deriv);
+      } else {
+        stv_(xn + q, chi);
+        stv_(dn + q, deriv);
+      }
     }
     return chi;
   } else {
@@ -204,9 +255,13 @@ __device__ __forceinline__ V psi_apply(const EmArgs<R> &A, V omb, int d, int typ
     const V h3 = add_(s2, l2);
     const V l3 = sub_(l2, sub_(h3, s2));
     if (write) {
-      stv_(xn + q, h3);
-      stv_((type == 0 ? A.lEn[d][slot] : A.lHn[d][slot]) + q, l3);
-      stv_(dn + q, deriv);
+      if (d < 2) {
+        st_rec<R>(xn + q * kPsiRec<R>, h3, l3, deriv);
+      } else {
+        stv_(xn + q, h3);
+        stv_((type == 0 ? A.lEn[d][slot] : A.lHn[d][slot]) + q, l3);
+        stv_(dn + q, deriv);
+      }
     }
     return h3;
   }
@@ -366,11 +421,11 @@ static_assert((kEmStages & (kEmStages - 1)) == 0, "stage count must be a power o
 static_assert(kEmAhead >= 2 && kEmAhead <= kEmStages - 1, "prefetch distance must leave the stage of plane k-1 free");
 // Border tiles (FP32) keep the H side's CPML states of the next plane in a
 // per-thread shared-memory ring filled by cp.async: 2 planes x 6 states x
-// (chi high, chi low, previous derivative).
+// one 16-byte slot (chi high, chi low, previous derivative, unused).
 constexpr int kPsiH = 6;
 template <typename R, int TY>
 __host__ __device__ constexpr size_t em_psi_ring_bytes() {
-  return sizeof(R) == 4 ? (size_t)32 * TY * 2 * kPsiH * 3 * sizeof(R) : 0;
+  return sizeof(R) == 4 ? (size_t)32 * TY * 2 * kPsiH * 4 * sizeof(R) : 0;
 }
 template <typename R, int TY>
 __host__ __device__ constexpr size_t em_smem_bytes(int nmat) {
@@ -512,19 +567,23 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
       default: d = 1, slot = 0; return hz_on ? syH : -1;
     }
   };
-  R *ring = reinterpret_cast<R *>(stg + kEmStages) + (ty * 32 + tx) * (2 * kPsiH * 3);
+  R *ring = reinterpret_cast<R *>(stg + kEmStages) + (ty * 32 + tx) * (2 * kPsiH * 4);
   auto prefetch_h = [&](int kk) {
     if constexpr (sizeof(R) == 4) {
-      R *r = ring + (kk & 1) * (kPsiH * 3);
+      R *r = ring + (kk & 1) * (kPsiH * 4);
 #pragma unroll
       for (int e = 0; e < kPsiH; ++e) {
         int d, slot;
         const int sp = h_state(e, kk, d, slot);
         if (sp >= 0) {
           const long long q = qof(d, sp, kk);
-          cp_async<4>(r + 3 * e, A.xHo[d][slot] + q, true);
-          cp_async<4>(r + 3 * e + 1, A.lHo[d][slot] + q, true);
-          cp_async<4>(r + 3 * e + 2, A.dHo[d][slot] + q, true);
+          if (d < 2) {  // the record
+            cp_async<16>(r + 4 * e, A.xHo[d][slot] + q * kPsiRec<R>, true);
+          } else {
+            cp_async<4>(r + 4 * e, A.xHo[d][slot] + q, true);
+            cp_async<4>(r + 4 * e + 1, A.lHo[d][slot] + q, true);
+            cp_async<4>(r + 4 * e + 2, A.dHo[d][slot] + q, true);
+          }
         }
       }
       cp_async_commit();
@@ -683,18 +742,19 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
       Psi<R> ph[kPsiH];
       if constexpr (sizeof(R) == 4) {  // this plane's states landed in the ring (the group of plane k+1 may still fly)
         cp_async_wait<1>();
-        const R *r = ring + (k & 1) * (kPsiH * 3);
-  #pragma unroll
+        const R *r = ring + (k & 1) * (kPsiH * 4);
+#pragma unroll
         for (int e = 0; e < kPsiH; ++e) {
           int d, slot;
           ph[e].s = h_state(e, k, d, slot, PL);
           ph[e].q = ph[e].s >= 0 ? qof(d, ph[e].s, k) : 0;
-          ph[e].c.hi = r[3 * e];
-          ph[e].c.lo = r[3 * e + 1];
-          ph[e].c.d = r[3 * e + 2];
+          const float4 v = *reinterpret_cast<const float4 *>(r + 4 * e);
+          ph[e].c.hi = v.x;
+          ph[e].c.lo = v.y;
+          ph[e].c.d = v.z;
         }
       } else {
-  #pragma unroll
+#pragma unroll
         for (int e = 0; e < kPsiH; ++e) {
           int d, slot;
           const int sp = h_state(e, k, d, slot, PL);
