@@ -90,6 +90,12 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// a compile-time flag passed to a generic lambda
+template <bool B>
+struct BoolTag {
+  static constexpr bool value = B;
+};
+
 // ---- Tensor-memory-accelerator (TMA) copies tracked by a shared-memory
 // mbarrier (PTX ISA: cp.async.bulk.tensor, mbarrier). The CTA is its own
 // cluster, so its shared::cta addresses are valid shared::cluster addresses.

@@ -126,12 +126,6 @@ struct EmArgs {
   long long wait;   // the bound of those waits, in SM clock cycles
 };
 
-// a compile-time flag passed to a generic lambda
-template <bool B>
-struct BoolTag {
-  static constexpr bool value = B;
-};
-
 // index of position p (node or cell) of an axis inside its CPML slabs, or -1
 __device__ __forceinline__ int slab_index(int p, int n, int lo, int hi) {
   if (lo > 0 && p <= lo) return p;
@@ -677,221 +671,221 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
   // false when the CTA must leave.
   auto plane_body = [&](const int k, auto plain_tag) -> bool {
     constexpr bool PL = decltype(plain_tag)::value;
-      if (leader) {  // the stage of plane k-1 is free: every thread passed the last barrier
-        fence_proxy_async_smem();
-        issue(k + kEmAhead);
-      }
-      em_wait_next(bars, k, nz, s_abort, A.wait);
-      prefetch_h(k + 1);
-      const int par = k & 1;  // parity of the double-buffered exchange arrays
-      const I id = id0 + (I)k * plane;
-      const EmStage<R, TX, TY> &S0 = stg[k & (kEmStages - 1)];
-      const EmStage<R, TX, TY> &S1 = stg[(k + 1) & (kEmStages - 1)];
-      R hz0, ihz, idz, hzm;
-      load4(&S0.Z.v[0][0], hz0, ihz, idz, hzm);
-      // material rows of voxel layer k (the layer above node plane k)
-      const bool kz = PL || k < nz;
-      const int a00 = (kz && cx0 && cy0) ? (int)S0.V.v[ty][cv] * M_COLS : vd;
-      const int a01 = (kz && cx1 && cy0) ? (int)S0.V.v[ty][cv + 1] * M_COLS : vd;
-      const int a10 = (kz && cx0 && cy1) ? (int)S0.V.v[ty + 1][cv] * M_COLS : vd;
-      const int a11 = (kz && cx1 && cy1) ? (int)S0.V.v[ty + 1][cv + 1] * M_COLS : vd;
-      int r0 = 0, r1 = 0;  // source entries of row (k, j)
-      if (has_src && act) {
-        const int base = k * (ny + 1) + j0, sr = (base & 3) + ty;
-        r0 = S0.S.v[0][sr];
-        r1 = S0.S.v[0][sr + 1];
-      }
-      const R hdz = mul_(half_dt, idz);
-      const bool fix_z = !PL && ((k == 0 && A.fixlo[2]) || (k == nz && A.fixhi[2]));
-      const int szE = PL ? -1 : slab_index(k, nz, A.slo[2], A.shi[2]);
+    if (leader) {  // the stage of plane k-1 is free: every thread passed the last barrier
+      fence_proxy_async_smem();
+      issue(k + kEmAhead);
+    }
+    em_wait_next(bars, k, nz, s_abort, A.wait);
+    prefetch_h(k + 1);
+    const int par = k & 1;  // parity of the double-buffered exchange arrays
+    const I id = id0 + (I)k * plane;
+    const EmStage<R, TX, TY> &S0 = stg[k & (kEmStages - 1)];
+    const EmStage<R, TX, TY> &S1 = stg[(k + 1) & (kEmStages - 1)];
+    R hz0, ihz, idz, hzm;
+    load4(&S0.Z.v[0][0], hz0, ihz, idz, hzm);
+    // material rows of voxel layer k (the layer above node plane k)
+    const bool kz = PL || k < nz;
+    const int a00 = (kz && cx0 && cy0) ? (int)S0.V.v[ty][cv] * M_COLS : vd;
+    const int a01 = (kz && cx1 && cy0) ? (int)S0.V.v[ty][cv + 1] * M_COLS : vd;
+    const int a10 = (kz && cx0 && cy1) ? (int)S0.V.v[ty + 1][cv] * M_COLS : vd;
+    const int a11 = (kz && cx1 && cy1) ? (int)S0.V.v[ty + 1][cv + 1] * M_COLS : vd;
+    int r0 = 0, r1 = 0;  // source entries of row (k, j)
+    if (has_src && act) {
+      const int base = k * (ny + 1) + j0, sr = (base & 3) + ty;
+      r0 = S0.S.v[0][sr];
+      r1 = S0.S.v[0][sr + 1];
+    }
+    const R hdz = mul_(half_dt, idz);
+    const bool fix_z = !PL && ((k == 0 && A.fixlo[2]) || (k == nz && A.fixhi[2]));
+    const int szE = PL ? -1 : slab_index(k, nz, A.slo[2], A.shi[2]);
 
-      const int cx = tx + xr;  // this node's column in the staged boxes
-      const R ex = S0.E[0].v[ty][cx], ey = S0.E[1].v[ty][cx], ez = S0.E[2].v[ty][cx];
-      const R ex_up = S1.E[0].v[ty][cx], ey_up = S1.E[1].v[ty][cx];
-      const R ez_jp = S0.E[2].v[ty + 1][cx], ex_jp = S0.E[0].v[ty + 1][cx];
-      const R ez_ip = S0.E[2].v[ty][cx + 1], ey_ip = S0.E[1].v[ty][cx + 1];
-      const R hx_o = S0.H[0].v[ty][cx], hy_o = S0.H[1].v[ty][cx], hz_o = S0.H[2].v[ty][cx];
-      const R q_old = accum ? S0.Qs.v[ty][cx] : R(0);
-      // coupled steps: temperature rise at this node and its +x, +y, +z neighbours
-      R th = 0, th_ip = 0, th_jp = 0, th_kp = 0;
-      R t_part = 0, t_dtc = 0;  // node (i, j, k-1)'s thermal step without the y-edge share of row j-1
-      if (CPL) {
-        th = S0.T.v[ty][cx];
-        th_ip = S0.T.v[ty][cx + 1];
-        th_jp = S0.T.v[ty + 1][cx];
-        th_kp = kz ? S1.T.v[ty][cx] : R(0);
-        if (TH && (PL || k > 0)) {  // plane k-1's stage is resident until this plane's barrier
-          const ThLayer<R> up = th_layer<R>(s_mt[b00 + M_K], s_mt[b01 + M_K], s_mt[b10 + M_K], s_mt[b11 + M_K],
-                                            s_mt[b00 + M_RHOCP], s_mt[b01 + M_RHOCP], s_mt[b10 + M_RHOCP],
-                                            s_mt[b11 + M_RHOCP], tcol_of());
-          th_partial(stg[(k - 1) & (kEmStages - 1)], k - 1, up, th, t_part, t_dtc);
-        }
+    const int cx = tx + xr;  // this node's column in the staged boxes
+    const R ex = S0.E[0].v[ty][cx], ey = S0.E[1].v[ty][cx], ez = S0.E[2].v[ty][cx];
+    const R ex_up = S1.E[0].v[ty][cx], ey_up = S1.E[1].v[ty][cx];
+    const R ez_jp = S0.E[2].v[ty + 1][cx], ex_jp = S0.E[0].v[ty + 1][cx];
+    const R ez_ip = S0.E[2].v[ty][cx + 1], ey_ip = S0.E[1].v[ty][cx + 1];
+    const R hx_o = S0.H[0].v[ty][cx], hy_o = S0.H[1].v[ty][cx], hz_o = S0.H[2].v[ty][cx];
+    const R q_old = accum ? S0.Qs.v[ty][cx] : R(0);
+    // coupled steps: temperature rise at this node and its +x, +y, +z neighbours
+    R th = 0, th_ip = 0, th_jp = 0, th_kp = 0;
+    R t_part = 0, t_dtc = 0;  // node (i, j, k-1)'s thermal step without the y-edge share of row j-1
+    if (CPL) {
+      th = S0.T.v[ty][cx];
+      th_ip = S0.T.v[ty][cx + 1];
+      th_jp = S0.T.v[ty + 1][cx];
+      th_kp = kz ? S1.T.v[ty][cx] : R(0);
+      if (TH && (PL || k > 0)) {  // plane k-1's stage is resident until this plane's barrier
+        const ThLayer<R> up = th_layer<R>(s_mt[b00 + M_K], s_mt[b01 + M_K], s_mt[b10 + M_K], s_mt[b11 + M_K],
+                                          s_mt[b00 + M_RHOCP], s_mt[b01 + M_RHOCP], s_mt[b10 + M_RHOCP],
+                                          s_mt[b11 + M_RHOCP], tcol_of());
+        th_partial(stg[(k - 1) & (kEmStages - 1)], k - 1, up, th, t_part, t_dtc);
       }
+    }
 
-      // material constants of voxel layer k
-      // (columns M_EPS, M_SDT2, M_IMU, M_K are adjacent: one vector load per voxel)
-      R e00, s00, u00, k00, e01, s01, u01, k01, e10, s10, u10, k10, e11, s11, u11, k11;
-      load4(s_mt + a00, e00, s00, u00, k00);
-      load4(s_mt + a01, e01, s01, u01, k01);
-      load4(s_mt + a10, e10, s10, u10, k10);
-      load4(s_mt + a11, e11, s11, u11, k11);
+    // material constants of voxel layer k
+    // (columns M_EPS, M_SDT2, M_IMU, M_K are adjacent: one vector load per voxel)
+    R e00, s00, u00, k00, e01, s01, u01, k01, e10, s10, u10, k10, e11, s11, u11, k11;
+    load4(s_mt + a00, e00, s00, u00, k00);
+    load4(s_mt + a01, e01, s01, u01, k01);
+    load4(s_mt + a10, e10, s10, u10, k10);
+    load4(s_mt + a11, e11, s11, u11, k11);
 
-      // ---- H^{n+1/2} at (i,j,k); dt/mu of a face is the series mean over the
-      // two voxels its dual edge crosses
-      const bool hx_on = act && in_y && kz, hy_on = act && in_x && kz, hz_on = act && in_x && in_y;
-      Psi<R> ph[kPsiH];
-      if constexpr (sizeof(R) == 4) {  // this plane's states landed in the ring (the group of plane k+1 may still fly)
-        cp_async_wait<1>();
-        const R *r = ring + (k & 1) * (kPsiH * 4);
+    // ---- H^{n+1/2} at (i,j,k); dt/mu of a face is the series mean over the
+    // two voxels its dual edge crosses
+    const bool hx_on = act && in_y && kz, hy_on = act && in_x && kz, hz_on = act && in_x && in_y;
+    Psi<R> ph[kPsiH];
+    if constexpr (sizeof(R) == 4) {  // this plane's states landed in the ring (the group of plane k+1 may still fly)
+      cp_async_wait<1>();
+      const R *r = ring + (k & 1) * (kPsiH * 4);
 #pragma unroll
-        for (int e = 0; e < kPsiH; ++e) {
-          int d, slot;
-          ph[e].s = h_state(e, k, d, slot, PL);
-          ph[e].q = ph[e].s >= 0 ? qof(d, ph[e].s, k) : 0;
-          const float4 v = *reinterpret_cast<const float4 *>(r + 4 * e);
-          ph[e].c.hi = v.x;
-          ph[e].c.lo = v.y;
-          ph[e].c.d = v.z;
-        }
+      for (int e = 0; e < kPsiH; ++e) {
+        int d, slot;
+        ph[e].s = h_state(e, k, d, slot, PL);
+        ph[e].q = ph[e].s >= 0 ? qof(d, ph[e].s, k) : 0;
+        const float4 v = *reinterpret_cast<const float4 *>(r + 4 * e);
+        ph[e].c.hi = v.x;
+        ph[e].c.lo = v.y;
+        ph[e].c.d = v.z;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < kPsiH; ++e) {
+        int d, slot;
+        const int sp = h_state(e, k, d, slot, PL);
+        ph[e] = psi_at(d, 1, slot, sp, k);
+      }
+    }
+    const Psi<R> &pHx1 = ph[0], &pHx2 = ph[1], &pHy1 = ph[2], &pHy2 = ph[3], &pHz1 = ph[4], &pHz2 = ph[5];
+    R Hx = 0, Hy = 0, Hz = 0;
+    if (hx_on)  // Hx: (curl E)_x = dEz/dy - dEy/dz, voxels (i-1..i, j, k)
+      Hx = h_update(hx_o, hdx, hxm, u10, hx0, u11,
+                    curl_psi(A, s_cp, 1, 1, pHx1, 2, pHx2, dif_(ez_jp, ez, ihy), dif_(ey_up, ey, ihz), own));
+    if (hy_on)  // Hy: dEx/dz - dEz/dx, voxels (i, j-1..j, k)
+      Hy = h_update(hy_o, hdy, hym, u01, hy0, u11,
+                    curl_psi(A, s_cp, 1, 2, pHy1, 0, pHy2, dif_(ex_up, ex, ihz), dif_(ez_ip, ez, ihx), own));
+    if (hz_on)  // Hz: dEy/dx - dEx/dy, voxels (i, j, k-1..k)
+      Hz = h_update(hz_o, hdz, hzm, u11_b, hz0, u11,
+                    curl_psi(A, s_cp, 1, 0, pHz1, 1, pHz2, dif_(ey_ip, ey, ihx), dif_(ex_jp, ex, ihy), own));
+    sHxz[par][0][ty][tx] = Hx;
+    sHxz[par][1][ty][tx] = Hz;
+    const R hy_l = __shfl_up_sync(0xffffffffu, Hy, 1);  // H of node i-1 (same warp)
+    const R hz_l = __shfl_up_sync(0xffffffffu, Hz, 1);
+    // the E side's CPML states, in flight across the barrier
+    const bool ex_on = need_ex && !(fix_y || fix_z), ey_on = need_ey && !(fix_x || fix_z);
+    const bool ez_on = own && kz && !(fix_x || fix_y);
+    const Psi<R> pEx1 = psi_at(1, 0, 1, ex_on ? syE : -1, k), pEx2 = psi_at(2, 0, 0, ex_on ? szE : -1, k);
+    const Psi<R> pEy1 = psi_at(2, 0, 1, ey_on ? szE : -1, k), pEy2 = psi_at(0, 0, 0, ey_on ? sxE : -1, k);
+    const Psi<R> pEz1 = psi_at(0, 0, 1, ez_on ? sxE : -1, k), pEz2 = psi_at(1, 0, 0, ez_on ? syE : -1, k);
+    // the one barrier of the plane: H of this plane and the y-edge Joule
+    // shares of the previous one are visible; every thread is past its reads
+    // of plane k-1's stage
+    __syncthreads();
+    if (*s_abort) {  // a copy did not arrive in time: drain what is in flight (bounded), flag, leave
+      if constexpr (sizeof(R) == 4) cp_async_wait<0>();
+      if (leader) em_abort(bars, k, nz, A.err, A.wait);
+      return false;
+    }
+    // Joule energy of node (i, j, k-1): its y-edge share from j-1 is now visible
+    if (accum && own && (PL || k > 0)) {
+      const R s = add_(q_pend, sQy[par ^ 1][ty - 1][tx]);
+      if (A.fold) {
+        A.Q[id - plane] += (double)s;
+        A.Qs[id - plane] = R(0);
       } else {
-#pragma unroll
-        for (int e = 0; e < kPsiH; ++e) {
-          int d, slot;
-          const int sp = h_state(e, k, d, slot, PL);
-          ph[e] = psi_at(d, 1, slot, sp, k);
-        }
+        A.Qs[id - plane] = s;
       }
-      const Psi<R> &pHx1 = ph[0], &pHx2 = ph[1], &pHy1 = ph[2], &pHy2 = ph[3], &pHz1 = ph[4], &pHz2 = ph[5];
-      R Hx = 0, Hy = 0, Hz = 0;
-      if (hx_on)  // Hx: (curl E)_x = dEz/dy - dEy/dz, voxels (i-1..i, j, k)
-        Hx = h_update(hx_o, hdx, hxm, u10, hx0, u11,
-                      curl_psi(A, s_cp, 1, 1, pHx1, 2, pHx2, dif_(ez_jp, ez, ihy), dif_(ey_up, ey, ihz), own));
-      if (hy_on)  // Hy: dEx/dz - dEz/dx, voxels (i, j-1..j, k)
-        Hy = h_update(hy_o, hdy, hym, u01, hy0, u11,
-                      curl_psi(A, s_cp, 1, 2, pHy1, 0, pHy2, dif_(ex_up, ex, ihz), dif_(ez_ip, ez, ihx), own));
-      if (hz_on)  // Hz: dEy/dx - dEx/dy, voxels (i, j, k-1..k)
-        Hz = h_update(hz_o, hdz, hzm, u11_b, hz0, u11,
-                      curl_psi(A, s_cp, 1, 0, pHz1, 1, pHz2, dif_(ey_ip, ey, ihx), dif_(ex_jp, ex, ihy), own));
-      sHxz[par][0][ty][tx] = Hx;
-      sHxz[par][1][ty][tx] = Hz;
-      const R hy_l = __shfl_up_sync(0xffffffffu, Hy, 1);  // H of node i-1 (same warp)
-      const R hz_l = __shfl_up_sync(0xffffffffu, Hz, 1);
-      // the E side's CPML states, in flight across the barrier
-      const bool ex_on = need_ex && !(fix_y || fix_z), ey_on = need_ey && !(fix_x || fix_z);
-      const bool ez_on = own && kz && !(fix_x || fix_y);
-      const Psi<R> pEx1 = psi_at(1, 0, 1, ex_on ? syE : -1, k), pEx2 = psi_at(2, 0, 0, ex_on ? szE : -1, k);
-      const Psi<R> pEy1 = psi_at(2, 0, 1, ey_on ? szE : -1, k), pEy2 = psi_at(0, 0, 0, ey_on ? sxE : -1, k);
-      const Psi<R> pEz1 = psi_at(0, 0, 1, ez_on ? sxE : -1, k), pEz2 = psi_at(1, 0, 0, ez_on ? syE : -1, k);
-      // the one barrier of the plane: H of this plane and the y-edge Joule
-      // shares of the previous one are visible; every thread is past its reads
-      // of plane k-1's stage
-      __syncthreads();
-      if (*s_abort) {  // a copy did not arrive in time: drain what is in flight (bounded), flag, leave
-        if constexpr (sizeof(R) == 4) cp_async_wait<0>();
-        if (leader) em_abort(bars, k, nz, A.err, A.wait);
-        return false;
-      }
-      // Joule energy of node (i, j, k-1): its y-edge share from j-1 is now visible
-      if (accum && own && (PL || k > 0)) {
-        const R s = add_(q_pend, sQy[par ^ 1][ty - 1][tx]);
-        if (A.fold) {
-          A.Q[id - plane] += (double)s;
-          A.Qs[id - plane] = R(0);
-        } else {
-          A.Qs[id - plane] = s;
-        }
-      }
-      if (TH && own && (PL || k > 0)) th_finish(id - plane, sQy[par ^ 1][ty - 1][tx], t_part, t_dtc);
-      if (CPL && !TH && own && (PL || k > 0)) A.Pout[id - plane] = mul_(add_(e_pend, sQy[par ^ 1][ty - 1][tx]), A.inv_dt);
+    }
+    if (TH && own && (PL || k > 0)) th_finish(id - plane, sQy[par ^ 1][ty - 1][tx], t_part, t_dtc);
+    if (CPL && !TH && own && (PL || k > 0)) A.Pout[id - plane] = mul_(add_(e_pend, sQy[par ^ 1][ty - 1][tx]), A.inv_dt);
 
-      // ---- source current on this node's edges (three scalars selected by
-      // axis: a dynamically indexed array would live in local memory)
-      R Jx = 0, Jy = 0, Jz = 0;
-      for (int e = r0; e < r1; ++e) {
-        const int4 s = A.src_ent[e];
-        const long long step = *A.step_base + step_off;
-        if (s.x == i && step < A.amp_len) {
-          const R a = A.src_amp[(long long)s.z * A.amp_len + step];
-          Jx = add_(Jx, s.y == 0 ? a : R(0));
-          Jy = add_(Jy, s.y == 1 ? a : R(0));
-          Jz = add_(Jz, s.y == 2 ? a : R(0));
-        }
+    // ---- source current on this node's edges (three scalars selected by
+    // axis: a dynamically indexed array would live in local memory)
+    R Jx = 0, Jy = 0, Jz = 0;
+    for (int e = r0; e < r1; ++e) {
+      const int4 s = A.src_ent[e];
+      const long long step = *A.step_base + step_off;
+      if (s.x == i && step < A.amp_len) {
+        const R a = A.src_amp[(long long)s.z * A.amp_len + step];
+        Jx = add_(Jx, s.y == 0 ? a : R(0));
+        Jy = add_(Jy, s.y == 1 ? a : R(0));
+        Jz = add_(Jz, s.y == 2 ? a : R(0));
       }
+    }
 
-      // ---- E^{n+1} on the node's edges and their Joule shares. Layer-k partial
-      // sums of the x / y edges (voxel pairs across y / x); the layer k-1 halves
-      // were formed one plane earlier.
-      const R pxe_a = fma_(hym, e01, mul_(hy0, e11)), pxs_a = fma_(hym, s01, mul_(hy0, s11));
-      const R pye_a = fma_(hxm, e10, mul_(hx0, e11)), pys_a = fma_(hxm, s10, mul_(hx0, s11));
-      R exn = ex, eyn = ey, ezn = ez, qx = 0, qy = 0, qz = 0;
-      if (ex_on) {  // Ex: dHz/dy - dHy/dz, voxels (i, j-1..j, k-1..k)
-        const R curl = curl_psi(A, s_cp, 0, 1, pEx1, 2, pEx2, dif_(Hz, sHxz[par][1][ty - 1][tx], idy), dif_(Hy, hy_km1, idz),
-                                own);
-        R Ss = fma_(hzm, pxs_b, mul_(hz0, pxs_a));
-        if (CPL) {
-          const R te = mul_(R(0.5), add_(th, th_ip));
-          R d1, d2, d3, d4;
-          const R a1 = mul_(mul_(hzm, hym), sgd(b01, te, d1)), a2 = mul_(mul_(hzm, hy0), sgd(b11, te, d2));
-          const R a3 = mul_(mul_(hz0, hym), sgd(a01, te, d3)), a4 = mul_(mul_(hz0, hy0), sgd(a11, te, d4));
-          Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
-        }
-        exn = e_update<R, R>(ex, mul_(dtWx_y, add_(hzm, hz0)), sub_(curl, Jx), fma_(hzm, pxe_b, mul_(hz0, pxe_a)), Ss,
-                             lqx, &qx);
-      }
-      if (ey_on) {  // Ey: dHx/dz - dHz/dx, voxels (i-1..i, j, k-1..k)
-        const R curl = curl_psi(A, s_cp, 0, 2, pEy1, 0, pEy2, dif_(Hx, hx_km1, idz), dif_(Hz, hz_l, idx), own);
-        R Ss = fma_(hzm, pys_b, mul_(hz0, pys_a));
-        if (CPL) {
-          const R te = mul_(R(0.5), add_(th, th_jp));
-          R d1, d2, d3, d4;
-          const R a1 = mul_(mul_(hzm, hxm), sgd(b10, te, d1)), a2 = mul_(mul_(hzm, hx0), sgd(b11, te, d2));
-          const R a3 = mul_(mul_(hz0, hxm), sgd(a10, te, d3)), a4 = mul_(mul_(hz0, hx0), sgd(a11, te, d4));
-          Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
-        }
-        eyn = e_update<R, R>(ey, mul_(dtWy_x, add_(hzm, hz0)), sub_(curl, Jy), fma_(hzm, pye_b, mul_(hz0, pye_a)), Ss,
-                             lqy, &qy);
-      }
-      if (ez_on) {  // Ez: dHy/dx - dHx/dy, voxels (i-1..i, j-1..j, k)
-        const R curl = curl_psi(A, s_cp, 0, 0, pEz1, 1, pEz2, dif_(Hy, hy_l, idx), dif_(Hx, sHxz[par][0][ty - 1][tx], idy),
-                                own);
-        const R Se = fma_(hym, fma_(hxm, e00, mul_(hx0, e01)), mul_(hy0, fma_(hxm, e10, mul_(hx0, e11))));
-        R Ss = fma_(hym, fma_(hxm, s00, mul_(hx0, s01)), mul_(hy0, fma_(hxm, s10, mul_(hx0, s11))));
-        if (CPL) {
-          const R te = mul_(R(0.5), add_(th, th_kp));
-          R d1, d2, d3, d4;
-          const R a1 = mul_(mul_(hym, hxm), sgd(a00, te, d1)), a2 = mul_(mul_(hym, hx0), sgd(a01, te, d2));
-          const R a3 = mul_(mul_(hy0, hxm), sgd(a10, te, d3)), a4 = mul_(mul_(hy0, hx0), sgd(a11, te, d4));
-          Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
-        }
-        ezn = e_update<R, R>(ez, mul_(dtWx_y, add_(hxm, hx0)), sub_(curl, Jz), Se, Ss, mul_(R(0.25), hz0), &qz);
-      }
-      const R qx_l = __shfl_up_sync(0xffffffffu, qx, 1);  // x-edge share from node i-1
-      sQy[par][ty][tx] = qy;
-
-      if (own) {
-        A.Hn[0][id] = Hx;
-        A.Hn[1][id] = Hy;
-        A.Hn[2][id] = Hz;
-        A.En[0][id] = exn;
-        A.En[1][id] = eyn;
-        if (kz) A.En[2][id] = ezn;
-      }
-      e_pend = add_(add_(add_(qx, qx_l), qy), add_(qz, qz_km1));
-      q_pend = add_(q_old, e_pend);
-      hx_km1 = Hx;
-      hy_km1 = Hy;
-      qz_km1 = qz;
-      pxe_b = pxe_a;
-      pxs_b = pxs_a;
-      pye_b = pye_a;
-      pys_b = pys_a;
-      u11_b = u11;
+    // ---- E^{n+1} on the node's edges and their Joule shares. Layer-k partial
+    // sums of the x / y edges (voxel pairs across y / x); the layer k-1 halves
+    // were formed one plane earlier.
+    const R pxe_a = fma_(hym, e01, mul_(hy0, e11)), pxs_a = fma_(hym, s01, mul_(hy0, s11));
+    const R pye_a = fma_(hxm, e10, mul_(hx0, e11)), pys_a = fma_(hxm, s10, mul_(hx0, s11));
+    R exn = ex, eyn = ey, ezn = ez, qx = 0, qy = 0, qz = 0;
+    if (ex_on) {  // Ex: dHz/dy - dHy/dz, voxels (i, j-1..j, k-1..k)
+      const R curl = curl_psi(A, s_cp, 0, 1, pEx1, 2, pEx2, dif_(Hz, sHxz[par][1][ty - 1][tx], idy), dif_(Hy, hy_km1, idz),
+                              own);
+      R Ss = fma_(hzm, pxs_b, mul_(hz0, pxs_a));
       if (CPL) {
-        b00 = a00;
-        b01 = a01;
-        b10 = a10;
-        b11 = a11;
+        const R te = mul_(R(0.5), add_(th, th_ip));
+        R d1, d2, d3, d4;
+        const R a1 = mul_(mul_(hzm, hym), sgd(b01, te, d1)), a2 = mul_(mul_(hzm, hy0), sgd(b11, te, d2));
+        const R a3 = mul_(mul_(hz0, hym), sgd(a01, te, d3)), a4 = mul_(mul_(hz0, hy0), sgd(a11, te, d4));
+        Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
       }
+      exn = e_update<R, R>(ex, mul_(dtWx_y, add_(hzm, hz0)), sub_(curl, Jx), fma_(hzm, pxe_b, mul_(hz0, pxe_a)), Ss,
+                           lqx, &qx);
+    }
+    if (ey_on) {  // Ey: dHx/dz - dHz/dx, voxels (i-1..i, j, k-1..k)
+      const R curl = curl_psi(A, s_cp, 0, 2, pEy1, 0, pEy2, dif_(Hx, hx_km1, idz), dif_(Hz, hz_l, idx), own);
+      R Ss = fma_(hzm, pys_b, mul_(hz0, pys_a));
+      if (CPL) {
+        const R te = mul_(R(0.5), add_(th, th_jp));
+        R d1, d2, d3, d4;
+        const R a1 = mul_(mul_(hzm, hxm), sgd(b10, te, d1)), a2 = mul_(mul_(hzm, hx0), sgd(b11, te, d2));
+        const R a3 = mul_(mul_(hz0, hxm), sgd(a10, te, d3)), a4 = mul_(mul_(hz0, hx0), sgd(a11, te, d4));
+        Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
+      }
+      eyn = e_update<R, R>(ey, mul_(dtWy_x, add_(hzm, hz0)), sub_(curl, Jy), fma_(hzm, pye_b, mul_(hz0, pye_a)), Ss,
+                           lqy, &qy);
+    }
+    if (ez_on) {  // Ez: dHy/dx - dHx/dy, voxels (i-1..i, j-1..j, k)
+      const R curl = curl_psi(A, s_cp, 0, 0, pEz1, 1, pEz2, dif_(Hy, hy_l, idx), dif_(Hx, sHxz[par][0][ty - 1][tx], idy),
+                              own);
+      const R Se = fma_(hym, fma_(hxm, e00, mul_(hx0, e01)), mul_(hy0, fma_(hxm, e10, mul_(hx0, e11))));
+      R Ss = fma_(hym, fma_(hxm, s00, mul_(hx0, s01)), mul_(hy0, fma_(hxm, s10, mul_(hx0, s11))));
+      if (CPL) {
+        const R te = mul_(R(0.5), add_(th, th_kp));
+        R d1, d2, d3, d4;
+        const R a1 = mul_(mul_(hym, hxm), sgd(a00, te, d1)), a2 = mul_(mul_(hym, hx0), sgd(a01, te, d2));
+        const R a3 = mul_(mul_(hy0, hxm), sgd(a10, te, d3)), a4 = mul_(mul_(hy0, hx0), sgd(a11, te, d4));
+        Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
+      }
+      ezn = e_update<R, R>(ez, mul_(dtWx_y, add_(hxm, hx0)), sub_(curl, Jz), Se, Ss, mul_(R(0.25), hz0), &qz);
+    }
+    const R qx_l = __shfl_up_sync(0xffffffffu, qx, 1);  // x-edge share from node i-1
+    sQy[par][ty][tx] = qy;
+
+    if (own) {
+      A.Hn[0][id] = Hx;
+      A.Hn[1][id] = Hy;
+      A.Hn[2][id] = Hz;
+      A.En[0][id] = exn;
+      A.En[1][id] = eyn;
+      if (kz) A.En[2][id] = ezn;
+    }
+    e_pend = add_(add_(add_(qx, qx_l), qy), add_(qz, qz_km1));
+    q_pend = add_(q_old, e_pend);
+    hx_km1 = Hx;
+    hy_km1 = Hy;
+    qz_km1 = qz;
+    pxe_b = pxe_a;
+    pxs_b = pxs_a;
+    pye_b = pye_a;
+    pys_b = pys_a;
+    u11_b = u11;
+    if (CPL) {
+      b00 = a00;
+      b01 = a01;
+      b10 = a10;
+      b11 = a11;
+    }
     return true;
   };
   for (int k = 0; k <= nz; ++k) {
@@ -1062,222 +1056,222 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
   // must leave (a copy did not arrive in time).
   auto plane_body = [&](const int k, auto plain_tag) -> bool {
     constexpr bool PL = decltype(plain_tag)::value;
-      if (leader) {
-        fence_proxy_async_smem();
-        issue(k + kEmAhead);
-      }
-      em_wait_next(bars, k, nz, s_abort, A.wait);
-      const int par = k & 1;  // parity of the double-buffered exchange arrays
-      const I id = id0 + (I)k * plane;
-      const EmStage<R, kEm2Nodes, TY> &S0 = stg[k & (kEmStages - 1)];
-      const EmStage<R, kEm2Nodes, TY> &S1 = stg[(k + 1) & (kEmStages - 1)];
-      R hz0s, ihzs, idzs, hzms;
-      load4(&S0.Z.v[0][0], hz0s, ihzs, idzs, hzms);
-      const R2 hz0 = bc_<R2>(hz0s), ihz = bc_<R2>(ihzs), idz = bc_<R2>(idzs), hzm = bc_<R2>(hzms);
-      const bool kz = PL || k < nz;
-      // voxels ia-1 (a), ia (b), ia+1 (c) of rows j-1 (0) and j (1) in layer k;
-      // at k = nz the zero-filled box gives material 0, which the zero layer
-      // height then removes
-      const int r0a = (int)S0.V.v[ty][cv] * M_COLS, r0b = (int)S0.V.v[ty][cv + 1] * M_COLS,
-                r0c = (int)S0.V.v[ty][cv + 2] * M_COLS;
-      const int r1a = (int)S0.V.v[ty + 1][cv] * M_COLS, r1b = (int)S0.V.v[ty + 1][cv + 1] * M_COLS,
-                r1c = (int)S0.V.v[ty + 1][cv + 2] * M_COLS;
-      int r0 = 0, r1 = 0;  // source entries of row (k, j)
-      if (has_src) {
-        const int base = k * (ny + 1) + j0, sr = (base & 3) + ty;
-        r0 = S0.S.v[0][sr];
-        r1 = S0.S.v[0][sr + 1];
-      }
-      const R2 hdz = bc_<R2>(mul_(half_dt, idzs));
-      const bool fix_z = !PL && ((k == 0 && A.fixlo[2]) || (k == nz && A.fixhi[2]));
-      const int szE = PL ? -1 : slab_index(k, nz, A.slo[2], A.shi[2]);
-      const int szH = kz ? szE : -1;
+    if (leader) {
+      fence_proxy_async_smem();
+      issue(k + kEmAhead);
+    }
+    em_wait_next(bars, k, nz, s_abort, A.wait);
+    const int par = k & 1;  // parity of the double-buffered exchange arrays
+    const I id = id0 + (I)k * plane;
+    const EmStage<R, kEm2Nodes, TY> &S0 = stg[k & (kEmStages - 1)];
+    const EmStage<R, kEm2Nodes, TY> &S1 = stg[(k + 1) & (kEmStages - 1)];
+    R hz0s, ihzs, idzs, hzms;
+    load4(&S0.Z.v[0][0], hz0s, ihzs, idzs, hzms);
+    const R2 hz0 = bc_<R2>(hz0s), ihz = bc_<R2>(ihzs), idz = bc_<R2>(idzs), hzm = bc_<R2>(hzms);
+    const bool kz = PL || k < nz;
+    // voxels ia-1 (a), ia (b), ia+1 (c) of rows j-1 (0) and j (1) in layer k;
+    // at k = nz the zero-filled box gives material 0, which the zero layer
+    // height then removes
+    const int r0a = (int)S0.V.v[ty][cv] * M_COLS, r0b = (int)S0.V.v[ty][cv + 1] * M_COLS,
+              r0c = (int)S0.V.v[ty][cv + 2] * M_COLS;
+    const int r1a = (int)S0.V.v[ty + 1][cv] * M_COLS, r1b = (int)S0.V.v[ty + 1][cv + 1] * M_COLS,
+              r1c = (int)S0.V.v[ty + 1][cv + 2] * M_COLS;
+    int r0 = 0, r1 = 0;  // source entries of row (k, j)
+    if (has_src) {
+      const int base = k * (ny + 1) + j0, sr = (base & 3) + ty;
+      r0 = S0.S.v[0][sr];
+      r1 = S0.S.v[0][sr + 1];
+    }
+    const R2 hdz = bc_<R2>(mul_(half_dt, idzs));
+    const bool fix_z = !PL && ((k == 0 && A.fixlo[2]) || (k == nz && A.fixhi[2]));
+    const int szE = PL ? -1 : slab_index(k, nz, A.slo[2], A.shi[2]);
+    const int szH = kz ? szE : -1;
 
-      const R2 ex = ldv_<R2>(&S0.E[0].v[ty][cx]), ey = ldv_<R2>(&S0.E[1].v[ty][cx]), ez = ldv_<R2>(&S0.E[2].v[ty][cx]);
-      const R2 ex_up = ldv_<R2>(&S1.E[0].v[ty][cx]), ey_up = ldv_<R2>(&S1.E[1].v[ty][cx]);
-      const R2 ez_jp = ldv_<R2>(&S0.E[2].v[ty + 1][cx]), ex_jp = ldv_<R2>(&S0.E[0].v[ty + 1][cx]);
-      const R2 ez_ip = {ez.y, S0.E[2].v[ty][cx + 2]}, ey_ip = {ey.y, S0.E[1].v[ty][cx + 2]};
-      const R2 hx_o = ldv_<R2>(&S0.H[0].v[ty][cx]), hy_o = ldv_<R2>(&S0.H[1].v[ty][cx]),
-               hz_o = ldv_<R2>(&S0.H[2].v[ty][cx]);
-      const R2 q_old = accum ? ldv_<R2>(&S0.Qs.v[ty][cx]) : z2;
-      R2 th = z2, th_ip = z2, th_jp = z2, th_kp = z2;
-      R2 t_part = z2, t_dtc = z2;  // the pair's thermal step at plane k-1 without the y-edge share of row j-1
-      if (CPL) {
-        th = ldv_<R2>(&S0.T.v[ty][cx]);
-        th_ip = R2{th.y, S0.T.v[ty][cx + 2]};
-        th_jp = ldv_<R2>(&S0.T.v[ty + 1][cx]);
-        th_kp = kz ? ldv_<R2>(&S1.T.v[ty][cx]) : z2;
-        if (TH && (PL || k > 0)) {  // plane k-1's stage is resident until this plane's barrier
-          const ThLayer<R2> up = th_layer<R2>(
-              R2{s_mt[p0a + M_K], s_mt[p0b + M_K]}, R2{s_mt[p0b + M_K], s_mt[p0c + M_K]},
-              R2{s_mt[p1a + M_K], s_mt[p1b + M_K]}, R2{s_mt[p1b + M_K], s_mt[p1c + M_K]},
-              R2{s_mt[p0a + M_RHOCP], s_mt[p0b + M_RHOCP]}, R2{s_mt[p0b + M_RHOCP], s_mt[p0c + M_RHOCP]},
-              R2{s_mt[p1a + M_RHOCP], s_mt[p1b + M_RHOCP]}, R2{s_mt[p1b + M_RHOCP], s_mt[p1c + M_RHOCP]}, tcol_of());
-          th_partial(stg[(k - 1) & (kEmStages - 1)], k - 1, up, th, t_part, t_dtc);
-        }
+    const R2 ex = ldv_<R2>(&S0.E[0].v[ty][cx]), ey = ldv_<R2>(&S0.E[1].v[ty][cx]), ez = ldv_<R2>(&S0.E[2].v[ty][cx]);
+    const R2 ex_up = ldv_<R2>(&S1.E[0].v[ty][cx]), ey_up = ldv_<R2>(&S1.E[1].v[ty][cx]);
+    const R2 ez_jp = ldv_<R2>(&S0.E[2].v[ty + 1][cx]), ex_jp = ldv_<R2>(&S0.E[0].v[ty + 1][cx]);
+    const R2 ez_ip = {ez.y, S0.E[2].v[ty][cx + 2]}, ey_ip = {ey.y, S0.E[1].v[ty][cx + 2]};
+    const R2 hx_o = ldv_<R2>(&S0.H[0].v[ty][cx]), hy_o = ldv_<R2>(&S0.H[1].v[ty][cx]),
+             hz_o = ldv_<R2>(&S0.H[2].v[ty][cx]);
+    const R2 q_old = accum ? ldv_<R2>(&S0.Qs.v[ty][cx]) : z2;
+    R2 th = z2, th_ip = z2, th_jp = z2, th_kp = z2;
+    R2 t_part = z2, t_dtc = z2;  // the pair's thermal step at plane k-1 without the y-edge share of row j-1
+    if (CPL) {
+      th = ldv_<R2>(&S0.T.v[ty][cx]);
+      th_ip = R2{th.y, S0.T.v[ty][cx + 2]};
+      th_jp = ldv_<R2>(&S0.T.v[ty + 1][cx]);
+      th_kp = kz ? ldv_<R2>(&S1.T.v[ty][cx]) : z2;
+      if (TH && (PL || k > 0)) {  // plane k-1's stage is resident until this plane's barrier
+        const ThLayer<R2> up = th_layer<R2>(
+            R2{s_mt[p0a + M_K], s_mt[p0b + M_K]}, R2{s_mt[p0b + M_K], s_mt[p0c + M_K]},
+            R2{s_mt[p1a + M_K], s_mt[p1b + M_K]}, R2{s_mt[p1b + M_K], s_mt[p1c + M_K]},
+            R2{s_mt[p0a + M_RHOCP], s_mt[p0b + M_RHOCP]}, R2{s_mt[p0b + M_RHOCP], s_mt[p0c + M_RHOCP]},
+            R2{s_mt[p1a + M_RHOCP], s_mt[p1b + M_RHOCP]}, R2{s_mt[p1b + M_RHOCP], s_mt[p1c + M_RHOCP]}, tcol_of());
+        th_partial(stg[(k - 1) & (kEmStages - 1)], k - 1, up, th, t_part, t_dtc);
       }
+    }
 
-      R e0a, s0a, u0a, k0a, e0b, s0b, u0b, k0b, e0c, s0c, u0c, k0c;
-      R e1a, s1a, u1a, k1a, e1b, s1b, u1b, k1b, e1c, s1c, u1c, k1c;
-      load4(s_mt + r0a, e0a, s0a, u0a, k0a);
-      load4(s_mt + r0b, e0b, s0b, u0b, k0b);
-      load4(s_mt + r0c, e0c, s0c, u0c, k0c);
-      load4(s_mt + r1a, e1a, s1a, u1a, k1a);
-      load4(s_mt + r1b, e1b, s1b, u1b, k1b);
-      load4(s_mt + r1c, e1c, s1c, u1c, k1c);
-      // the voxels (i-1+dx, j-1+dy) of each node as pairs <dy><dx>
-      const R2 e00 = {e0a, e0b}, e01 = {e0b, e0c}, e10 = {e1a, e1b}, e11 = {e1b, e1c};
-      const R2 s00 = {s0a, s0b}, s01 = {s0b, s0c}, s10 = {s1a, s1b}, s11 = {s1b, s1c};
-      const R2 u01 = {u0b, u0c}, u10 = {u1a, u1b}, u11 = {u1b, u1c};
+    R e0a, s0a, u0a, k0a, e0b, s0b, u0b, k0b, e0c, s0c, u0c, k0c;
+    R e1a, s1a, u1a, k1a, e1b, s1b, u1b, k1b, e1c, s1c, u1c, k1c;
+    load4(s_mt + r0a, e0a, s0a, u0a, k0a);
+    load4(s_mt + r0b, e0b, s0b, u0b, k0b);
+    load4(s_mt + r0c, e0c, s0c, u0c, k0c);
+    load4(s_mt + r1a, e1a, s1a, u1a, k1a);
+    load4(s_mt + r1b, e1b, s1b, u1b, k1b);
+    load4(s_mt + r1c, e1c, s1c, u1c, k1c);
+    // the voxels (i-1+dx, j-1+dy) of each node as pairs <dy><dx>
+    const R2 e00 = {e0a, e0b}, e01 = {e0b, e0c}, e10 = {e1a, e1b}, e11 = {e1b, e1c};
+    const R2 s00 = {s0a, s0b}, s01 = {s0b, s0c}, s10 = {s1a, s1b}, s11 = {s1b, s1c};
+    const R2 u01 = {u0b, u0c}, u10 = {u1a, u1b}, u11 = {u1b, u1c};
 
-      // CPML states of the z slab for the node pair (derivative axis z)
-      auto psi_z = [&](int type, int slot, int s) -> Psi<R2> {
-        return psi_pre<R, R2>(A, 2, type, slot, s, s >= 0 ? ((long long)s * (ny + 1) + j) * g.px + ia : 0);
-      };
-      // chi of the z derivative (b - a) ih for each node of the pair, in the
-      // scalar forms: the compensated update relies on every step being
-      // rounded separately, which packed code does not guarantee (a packed
-      // product feeding an addition is contracted into an FMA)
-      auto chi_z = [&](int type, int slot, const Psi<R2> &p, R2 b, R2 a, R ih) -> R2 {
-        const R omb = s_cp[(2 * 2 + type) * kMaxSlab + p.s];
-        Psi<R> px, py;
-        px.s = py.s = p.s;
-        px.q = p.q;
-        py.q = p.q + 1;
-        px.c.hi = p.c.hi.x, py.c.hi = p.c.hi.y;
-        px.c.d = p.c.d.x, py.c.d = p.c.d.y;
-        if constexpr (sizeof(R) == 4) px.c.lo = p.c.lo.x, py.c.lo = p.c.lo.y;
-        return R2{psi_apply<R, R>(A, omb, 2, type, slot, px, dif_(b.x, a.x, ih), own),
-                  psi_apply<R, R>(A, omb, 2, type, slot, py, dif_(b.y, a.y, ih), own)};
-      };
+    // CPML states of the z slab for the node pair (derivative axis z)
+    auto psi_z = [&](int type, int slot, int s) -> Psi<R2> {
+      return psi_pre<R, R2>(A, 2, type, slot, s, s >= 0 ? ((long long)s * (ny + 1) + j) * g.px + ia : 0);
+    };
+    // chi of the z derivative (b - a) ih for each node of the pair, in the
+    // scalar forms: the compensated update relies on every step being
+    // rounded separately, which packed code does not guarantee (a packed
+    // product feeding an addition is contracted into an FMA)
+    auto chi_z = [&](int type, int slot, const Psi<R2> &p, R2 b, R2 a, R ih) -> R2 {
+      const R omb = s_cp[(2 * 2 + type) * kMaxSlab + p.s];
+      Psi<R> px, py;
+      px.s = py.s = p.s;
+      px.q = p.q;
+      py.q = p.q + 1;
+      px.c.hi = p.c.hi.x, py.c.hi = p.c.hi.y;
+      px.c.d = p.c.d.x, py.c.d = p.c.d.y;
+      if constexpr (sizeof(R) == 4) px.c.lo = p.c.lo.x, py.c.lo = p.c.lo.y;
+      return R2{psi_apply<R, R>(A, omb, 2, type, slot, px, dif_(b.x, a.x, ih), own),
+                psi_apply<R, R>(A, omb, 2, type, slot, py, dif_(b.y, a.y, ih), own)};
+    };
 
-      // ---- H^{n+1/2}
-      R2 Hx = z2, Hy = z2;
-      if (kz) {
-        const Psi<R2> pHx = psi_z(1, 0, szH), pHy = psi_z(1, 1, szH);
-        const R2 d1 = dif_(ez_jp, ez, ihy), d2 = dif_(ey_up, ey, ihz);
-        Hx = h_update(hx_o, hdx, hxm, u10, hx0, u11, szH >= 0 ? sub_(d1, chi_z(1, 0, pHx, ey_up, ey, ihzs)) : sub_(d1, d2));
-        const R2 f1 = dif_(ex_up, ex, ihz), f2 = dif_(ez_ip, ez, ihx);
-        Hy = h_update(hy_o, hdy, hym, u01, hy0, u11,
-                      szH >= 0 ? sub_(chi_z(1, 1, pHy, ex_up, ex, ihzs), f2) : sub_(f1, f2));
+    // ---- H^{n+1/2}
+    R2 Hx = z2, Hy = z2;
+    if (kz) {
+      const Psi<R2> pHx = psi_z(1, 0, szH), pHy = psi_z(1, 1, szH);
+      const R2 d1 = dif_(ez_jp, ez, ihy), d2 = dif_(ey_up, ey, ihz);
+      Hx = h_update(hx_o, hdx, hxm, u10, hx0, u11, szH >= 0 ? sub_(d1, chi_z(1, 0, pHx, ey_up, ey, ihzs)) : sub_(d1, d2));
+      const R2 f1 = dif_(ex_up, ex, ihz), f2 = dif_(ez_ip, ez, ihx);
+      Hy = h_update(hy_o, hdy, hym, u01, hy0, u11,
+                    szH >= 0 ? sub_(chi_z(1, 1, pHy, ex_up, ex, ihzs), f2) : sub_(f1, f2));
+    }
+    const R2 Hz = h_update(hz_o, hdz, hzm, u11_b, hz0, u11, sub_(dif_(ey_ip, ey, ihx), dif_(ex_jp, ex, ihy)));
+    sHxz[par][0][ty][tx] = Hx;
+    sHxz[par][1][ty][tx] = Hz;
+    const R2 hy_l = {__shfl_up_sync(0xffffffffu, Hy.y, 1), Hy.x};  // H of nodes ia-1, ia
+    const R2 hz_l = {__shfl_up_sync(0xffffffffu, Hz.y, 1), Hz.x};
+    // the one barrier of the plane (see the border tiles)
+    __syncthreads();
+    if (*s_abort) {
+      if (leader) em_abort(bars, k, nz, A.err, A.wait);
+      return false;
+    }
+    if (accum && own && (PL || k > 0)) {
+      const R2 s = add_(q_pend, sQy[par ^ 1][ty - 1][tx]);
+      if (A.fold) {
+        double2 *qp = reinterpret_cast<double2 *>(A.Q + (id - plane));
+        double2 qv = *qp;
+        qv.x += (double)s.x;
+        qv.y += (double)s.y;
+        *qp = qv;
+        stv_(A.Qs + (id - plane), z2);
+      } else {
+        stv_(A.Qs + (id - plane), s);
       }
-      const R2 Hz = h_update(hz_o, hdz, hzm, u11_b, hz0, u11, sub_(dif_(ey_ip, ey, ihx), dif_(ex_jp, ex, ihy)));
-      sHxz[par][0][ty][tx] = Hx;
-      sHxz[par][1][ty][tx] = Hz;
-      const R2 hy_l = {__shfl_up_sync(0xffffffffu, Hy.y, 1), Hy.x};  // H of nodes ia-1, ia
-      const R2 hz_l = {__shfl_up_sync(0xffffffffu, Hz.y, 1), Hz.x};
-      // the one barrier of the plane (see the border tiles)
-      __syncthreads();
-      if (*s_abort) {
-        if (leader) em_abort(bars, k, nz, A.err, A.wait);
-        return false;
-      }
-      if (accum && own && (PL || k > 0)) {
-        const R2 s = add_(q_pend, sQy[par ^ 1][ty - 1][tx]);
-        if (A.fold) {
-          double2 *qp = reinterpret_cast<double2 *>(A.Q + (id - plane));
-          double2 qv = *qp;
-          qv.x += (double)s.x;
-          qv.y += (double)s.y;
-          *qp = qv;
-          stv_(A.Qs + (id - plane), z2);
+    }
+    if (TH && own && (PL || k > 0)) th_finish(id - plane, sQy[par ^ 1][ty - 1][tx], t_part, t_dtc);
+    if (CPL && !TH && own && (PL || k > 0))
+      stv_(A.Pout + (id - plane), mul_(add_(e_pend, sQy[par ^ 1][ty - 1][tx]), bc_<R2>(A.inv_dt)));
+
+    // ---- source currents on the pair's edges
+    R2 Jx = z2, Jy = z2, Jz = z2;
+    for (int e = r0; e < r1; ++e) {
+      const int4 s = A.src_ent[e];
+      const long long step = *A.step_base + step_off;
+      if ((s.x == ia || s.x == ia + 1) && step < A.amp_len) {
+        const R a = A.src_amp[(long long)s.z * A.amp_len + step];
+        if (s.x == ia) {
+          Jx.x = add_(Jx.x, s.y == 0 ? a : R(0));
+          Jy.x = add_(Jy.x, s.y == 1 ? a : R(0));
+          Jz.x = add_(Jz.x, s.y == 2 ? a : R(0));
         } else {
-          stv_(A.Qs + (id - plane), s);
+          Jx.y = add_(Jx.y, s.y == 0 ? a : R(0));
+          Jy.y = add_(Jy.y, s.y == 1 ? a : R(0));
+          Jz.y = add_(Jz.y, s.y == 2 ? a : R(0));
         }
       }
-      if (TH && own && (PL || k > 0)) th_finish(id - plane, sQy[par ^ 1][ty - 1][tx], t_part, t_dtc);
-      if (CPL && !TH && own && (PL || k > 0))
-        stv_(A.Pout + (id - plane), mul_(add_(e_pend, sQy[par ^ 1][ty - 1][tx]), bc_<R2>(A.inv_dt)));
+    }
 
-      // ---- source currents on the pair's edges
-      R2 Jx = z2, Jy = z2, Jz = z2;
-      for (int e = r0; e < r1; ++e) {
-        const int4 s = A.src_ent[e];
-        const long long step = *A.step_base + step_off;
-        if ((s.x == ia || s.x == ia + 1) && step < A.amp_len) {
-          const R a = A.src_amp[(long long)s.z * A.amp_len + step];
-          if (s.x == ia) {
-            Jx.x = add_(Jx.x, s.y == 0 ? a : R(0));
-            Jy.x = add_(Jy.x, s.y == 1 ? a : R(0));
-            Jz.x = add_(Jz.x, s.y == 2 ? a : R(0));
-          } else {
-            Jx.y = add_(Jx.y, s.y == 0 ? a : R(0));
-            Jy.y = add_(Jy.y, s.y == 1 ? a : R(0));
-            Jz.y = add_(Jz.y, s.y == 2 ? a : R(0));
-          }
-        }
-      }
-
-      // ---- E^{n+1} and the Joule shares
-      const R2 pxe_a = fma_(hym, e01, mul_(hy0, e11)), pxs_a = fma_(hym, s01, mul_(hy0, s11));
-      const R2 pye_a = fma_(hxm, e10, mul_(hx0, e11)), pys_a = fma_(hxm, s10, mul_(hx0, s11));
-      R2 exn = ex, eyn = ey, ezn = ez, qx = z2, qy = z2, qz = z2;
-      if (ty > 0 && !fix_z) {  // Ex (owners and the halo lane, whose x-edge share lane 1 needs)
-        const R2 d1 = dif_(Hz, sHxz[par][1][ty - 1][tx], idy), d2 = dif_(Hy, hy_km1, idz);
-        const R2 curl = szE >= 0 ? sub_(d1, chi_z(0, 0, psi_z(0, 0, szE), Hy, hy_km1, idzs)) : sub_(d1, d2);
-        R2 Ss = fma_(hzm, pxs_b, mul_(hz0, pxs_a));
-        if (CPL) {
-          const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_ip));
-          R2 d1, d2, d3, d4;
-          const R2 a1 = mul_(mul_(hzm, hym), sgdp(p0b, p0c, te, d1)), a2 = mul_(mul_(hzm, hy0), sgdp(p1b, p1c, te, d2));
-          const R2 a3 = mul_(mul_(hz0, hym), sgdp(r0b, r0c, te, d3)), a4 = mul_(mul_(hz0, hy0), sgdp(r1b, r1c, te, d4));
-          Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
-        }
-        exn = e_update<R2, R>(ex, mul_(dtWx_y, add_(hzm, hz0)), sub_(curl, Jx), fma_(hzm, pxe_b, mul_(hz0, pxe_a)), Ss,
-                              lqx, &qx);
-      }
-      if (!fix_z) {  // Ey (every row: the halo row's y-edge share goes to row ty+1)
-        const R2 d1 = dif_(Hx, hx_km1, idz), d2 = dif_(Hz, hz_l, idx);
-        const R2 curl = szE >= 0 ? sub_(chi_z(0, 1, psi_z(0, 1, szE), Hx, hx_km1, idzs), d2) : sub_(d1, d2);
-        R2 Ss = fma_(hzm, pys_b, mul_(hz0, pys_a));
-        if (CPL) {
-          const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_jp));
-          R2 d1, d2, d3, d4;
-          const R2 a1 = mul_(mul_(hzm, hxm), sgdp(p1a, p1b, te, d1)), a2 = mul_(mul_(hzm, hx0), sgdp(p1b, p1c, te, d2));
-          const R2 a3 = mul_(mul_(hz0, hxm), sgdp(r1a, r1b, te, d3)), a4 = mul_(mul_(hz0, hx0), sgdp(r1b, r1c, te, d4));
-          Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
-        }
-        eyn = e_update<R2, R>(ey, mul_(dtWy_x, add_(hzm, hz0)), sub_(curl, Jy), fma_(hzm, pye_b, mul_(hz0, pye_a)), Ss,
-                              lqy, &qy);
-      }
-      if (ty > 0 && kz) {  // Ez
-        const R2 curl = sub_(dif_(Hy, hy_l, idx), dif_(Hx, sHxz[par][0][ty - 1][tx], idy));
-        const R2 Se = fma_(hym, fma_(hxm, e00, mul_(hx0, e01)), mul_(hy0, fma_(hxm, e10, mul_(hx0, e11))));
-        R2 Ss = fma_(hym, fma_(hxm, s00, mul_(hx0, s01)), mul_(hy0, fma_(hxm, s10, mul_(hx0, s11))));
-        if (CPL) {
-          const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_kp));
-          R2 d1, d2, d3, d4;
-          const R2 a1 = mul_(mul_(hym, hxm), sgdp(r0a, r0b, te, d1)), a2 = mul_(mul_(hym, hx0), sgdp(r0b, r0c, te, d2));
-          const R2 a3 = mul_(mul_(hy0, hxm), sgdp(r1a, r1b, te, d3)), a4 = mul_(mul_(hy0, hx0), sgdp(r1b, r1c, te, d4));
-          Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
-        }
-        ezn = e_update<R2, R>(ez, mul_(dtWx_y, add_(hxm, hx0)), sub_(curl, Jz), Se, Ss, bc_<R2>(mul_(R(0.25), hz0s)),
-                              &qz);
-      }
-      const R2 qx_l = {__shfl_up_sync(0xffffffffu, qx.y, 1), qx.x};  // x-edge shares from nodes ia-1, ia
-      sQy[par][ty][tx] = qy;
-
-      if (own) {
-        stv_(A.Hn[0] + id, Hx);
-        stv_(A.Hn[1] + id, Hy);
-        stv_(A.Hn[2] + id, Hz);
-        stv_(A.En[0] + id, exn);
-        stv_(A.En[1] + id, eyn);
-        if (kz) stv_(A.En[2] + id, ezn);
-      }
-      e_pend = add_(add_(add_(qx, qx_l), qy), add_(qz, qz_km1));
-      q_pend = add_(q_old, e_pend);
-      hx_km1 = Hx;
-      hy_km1 = Hy;
-      qz_km1 = qz;
-      pxe_b = pxe_a;
-      pxs_b = pxs_a;
-      pye_b = pye_a;
-      pys_b = pys_a;
-      u11_b = u11;
+    // ---- E^{n+1} and the Joule shares
+    const R2 pxe_a = fma_(hym, e01, mul_(hy0, e11)), pxs_a = fma_(hym, s01, mul_(hy0, s11));
+    const R2 pye_a = fma_(hxm, e10, mul_(hx0, e11)), pys_a = fma_(hxm, s10, mul_(hx0, s11));
+    R2 exn = ex, eyn = ey, ezn = ez, qx = z2, qy = z2, qz = z2;
+    if (ty > 0 && !fix_z) {  // Ex (owners and the halo lane, whose x-edge share lane 1 needs)
+      const R2 d1 = dif_(Hz, sHxz[par][1][ty - 1][tx], idy), d2 = dif_(Hy, hy_km1, idz);
+      const R2 curl = szE >= 0 ? sub_(d1, chi_z(0, 0, psi_z(0, 0, szE), Hy, hy_km1, idzs)) : sub_(d1, d2);
+      R2 Ss = fma_(hzm, pxs_b, mul_(hz0, pxs_a));
       if (CPL) {
-        p0a = r0a, p0b = r0b, p0c = r0c, p1a = r1a, p1b = r1b, p1c = r1c;
+        const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_ip));
+        R2 d1, d2, d3, d4;
+        const R2 a1 = mul_(mul_(hzm, hym), sgdp(p0b, p0c, te, d1)), a2 = mul_(mul_(hzm, hy0), sgdp(p1b, p1c, te, d2));
+        const R2 a3 = mul_(mul_(hz0, hym), sgdp(r0b, r0c, te, d3)), a4 = mul_(mul_(hz0, hy0), sgdp(r1b, r1c, te, d4));
+        Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
       }
+      exn = e_update<R2, R>(ex, mul_(dtWx_y, add_(hzm, hz0)), sub_(curl, Jx), fma_(hzm, pxe_b, mul_(hz0, pxe_a)), Ss,
+                            lqx, &qx);
+    }
+    if (!fix_z) {  // Ey (every row: the halo row's y-edge share goes to row ty+1)
+      const R2 d1 = dif_(Hx, hx_km1, idz), d2 = dif_(Hz, hz_l, idx);
+      const R2 curl = szE >= 0 ? sub_(chi_z(0, 1, psi_z(0, 1, szE), Hx, hx_km1, idzs), d2) : sub_(d1, d2);
+      R2 Ss = fma_(hzm, pys_b, mul_(hz0, pys_a));
+      if (CPL) {
+        const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_jp));
+        R2 d1, d2, d3, d4;
+        const R2 a1 = mul_(mul_(hzm, hxm), sgdp(p1a, p1b, te, d1)), a2 = mul_(mul_(hzm, hx0), sgdp(p1b, p1c, te, d2));
+        const R2 a3 = mul_(mul_(hz0, hxm), sgdp(r1a, r1b, te, d3)), a4 = mul_(mul_(hz0, hx0), sgdp(r1b, r1c, te, d4));
+        Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
+      }
+      eyn = e_update<R2, R>(ey, mul_(dtWy_x, add_(hzm, hz0)), sub_(curl, Jy), fma_(hzm, pye_b, mul_(hz0, pye_a)), Ss,
+                            lqy, &qy);
+    }
+    if (ty > 0 && kz) {  // Ez
+      const R2 curl = sub_(dif_(Hy, hy_l, idx), dif_(Hx, sHxz[par][0][ty - 1][tx], idy));
+      const R2 Se = fma_(hym, fma_(hxm, e00, mul_(hx0, e01)), mul_(hy0, fma_(hxm, e10, mul_(hx0, e11))));
+      R2 Ss = fma_(hym, fma_(hxm, s00, mul_(hx0, s01)), mul_(hy0, fma_(hxm, s10, mul_(hx0, s11))));
+      if (CPL) {
+        const R2 te = mul_(bc_<R2>(R(0.5)), add_(th, th_kp));
+        R2 d1, d2, d3, d4;
+        const R2 a1 = mul_(mul_(hym, hxm), sgdp(r0a, r0b, te, d1)), a2 = mul_(mul_(hym, hx0), sgdp(r0b, r0c, te, d2));
+        const R2 a3 = mul_(mul_(hy0, hxm), sgdp(r1a, r1b, te, d3)), a4 = mul_(mul_(hy0, hx0), sgdp(r1b, r1c, te, d4));
+        Ss = sig_sum4(a1, d1, a2, d2, a3, d3, a4, d4);
+      }
+      ezn = e_update<R2, R>(ez, mul_(dtWx_y, add_(hxm, hx0)), sub_(curl, Jz), Se, Ss, bc_<R2>(mul_(R(0.25), hz0s)),
+                            &qz);
+    }
+    const R2 qx_l = {__shfl_up_sync(0xffffffffu, qx.y, 1), qx.x};  // x-edge shares from nodes ia-1, ia
+    sQy[par][ty][tx] = qy;
+
+    if (own) {
+      stv_(A.Hn[0] + id, Hx);
+      stv_(A.Hn[1] + id, Hy);
+      stv_(A.Hn[2] + id, Hz);
+      stv_(A.En[0] + id, exn);
+      stv_(A.En[1] + id, eyn);
+      if (kz) stv_(A.En[2] + id, ezn);
+    }
+    e_pend = add_(add_(add_(qx, qx_l), qy), add_(qz, qz_km1));
+    q_pend = add_(q_old, e_pend);
+    hx_km1 = Hx;
+    hy_km1 = Hy;
+    qz_km1 = qz;
+    pxe_b = pxe_a;
+    pxs_b = pxs_a;
+    pye_b = pye_a;
+    pys_b = pys_a;
+    u11_b = u11;
+    if (CPL) {
+      p0a = r0a, p0b = r0b, p0c = r0c, p1a = r1a, p1b = r1b, p1c = r1c;
+    }
     return true;
   };
   for (int k = 0; k <= nz; ++k) {
