@@ -763,7 +763,8 @@ __global__ void __launch_bounds__(256) von_mises_kernel(Geo<R> g, const R *u0, c
 
 // ---- Jacobi-PCG vector kernels over the padded SoA node arrays (padding is 0).
 // Grid-stride with a fixed grid: the per-CTA partial sums, and therefore the
-// reductions, are deterministic. Dot products accumulate in FP64.
+// reductions, are deterministic. Dot products accumulate in FP64 (FP32
+// contexts: over partial sums of four nodes formed in FP32).
 
 
 template <typename R>
@@ -774,14 +775,42 @@ __global__ void __launch_bounds__(256) cg_init_kernel(long long n, const R *f0, 
   // scale: a power of two that brings the right-hand side to order one
   // (exact: the iteration is then the unscaled one times that factor)
   double rz = 0, bb = 0;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-    const R a0 = scale * f0[q], a1 = scale * f1[q], a2 = scale * f2[q];
-    const R z0 = d0[q] * a0, z1 = d1[q] * a1, z2 = d2[q] * a2;
-    x0[q] = 0; x1[q] = 0; x2[q] = 0;
-    r0[q] = a0; r1[q] = a1; r2[q] = a2;
-    p0[q] = z0; p1[q] = z1; p2[q] = z2;
-    rz += (double)(a0 * z0 + a1 * z1 + a2 * z2);
-    bb += (double)(a0 * a0 + a1 * a1 + a2 * a2);
+  const long long stride = (long long)gridDim.x * blockDim.x, first = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if constexpr (sizeof(R) == 4) {  // four nodes per access (n is a multiple of 4), one FP64 addition per group
+    const R *F[3] = {f0, f1, f2}, *Dg[3] = {d0, d1, d2};
+    R *Xv[3] = {x0, x1, x2}, *Rv[3] = {r0, r1, r2}, *Pv[3] = {p0, p1, p2};
+    for (long long v = first; v < (n >> 2); v += stride) {
+      float4 a[3], z[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float4 f = reinterpret_cast<const float4 *>(F[c])[v], d = reinterpret_cast<const float4 *>(Dg[c])[v];
+        a[c] = make_float4(scale * f.x, scale * f.y, scale * f.z, scale * f.w);
+        z[c] = make_float4(d.x * a[c].x, d.y * a[c].y, d.z * a[c].z, d.w * a[c].w);
+        reinterpret_cast<float4 *>(Xv[c])[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<float4 *>(Rv[c])[v] = a[c];
+        reinterpret_cast<float4 *>(Pv[c])[v] = z[c];
+      }
+      const float zx = a[0].x * z[0].x + a[1].x * z[1].x + a[2].x * z[2].x;
+      const float zy = a[0].y * z[0].y + a[1].y * z[1].y + a[2].y * z[2].y;
+      const float zz = a[0].z * z[0].z + a[1].z * z[1].z + a[2].z * z[2].z;
+      const float zw = a[0].w * z[0].w + a[1].w * z[1].w + a[2].w * z[2].w;
+      const float sx = a[0].x * a[0].x + a[1].x * a[1].x + a[2].x * a[2].x;
+      const float sy = a[0].y * a[0].y + a[1].y * a[1].y + a[2].y * a[2].y;
+      const float sz = a[0].z * a[0].z + a[1].z * a[1].z + a[2].z * a[2].z;
+      const float sw = a[0].w * a[0].w + a[1].w * a[1].w + a[2].w * a[2].w;
+      rz += (double)((zx + zy) + (zz + zw));
+      bb += (double)((sx + sy) + (sz + sw));
+    }
+  } else {
+    for (long long q = first; q < n; q += stride) {
+      const R a0 = scale * f0[q], a1 = scale * f1[q], a2 = scale * f2[q];
+      const R z0 = d0[q] * a0, z1 = d1[q] * a1, z2 = d2[q] * a2;
+      x0[q] = 0; x1[q] = 0; x2[q] = 0;
+      r0[q] = a0; r1[q] = a1; r2[q] = a2;
+      p0[q] = z0; p1[q] = z1; p2[q] = z2;
+      rz += (double)(a0 * z0 + a1 * z1 + a2 * z2);
+      bb += (double)(a0 * a0 + a1 * a1 + a2 * a2);
+    }
   }
   rz = block_sum(rz);
   bb = block_sum(bb);
@@ -792,7 +821,7 @@ __global__ void __launch_bounds__(256) cg_init_kernel(long long n, const R *f0, 
 }
 
 // partial sums of f.f (each node's three-component term in the context
-// precision, accumulated in FP64)
+// precision; FP32 contexts sum four nodes in FP32 per FP64 addition)
 template <typename R>
 __global__ void __launch_bounds__(256) sumsq3_kernel(long long n, const R *f0, const R *f1, const R *f2,
                                                       double *part) {
@@ -802,10 +831,9 @@ __global__ void __launch_bounds__(256) sumsq3_kernel(long long n, const R *f0, c
     for (long long v = first; v < (n >> 2); v += stride) {
       const float4 a = reinterpret_cast<const float4 *>(f0)[v], b = reinterpret_cast<const float4 *>(f1)[v],
                    c = reinterpret_cast<const float4 *>(f2)[v];
-      ss += (double)(a.x * a.x + b.x * b.x + c.x * c.x);
-      ss += (double)(a.y * a.y + b.y * b.y + c.y * c.y);
-      ss += (double)(a.z * a.z + b.z * b.z + c.z * c.z);
-      ss += (double)(a.w * a.w + b.w * b.w + c.w * c.w);
+      const float sx = a.x * a.x + b.x * b.x + c.x * c.x, sy = a.y * a.y + b.y * b.y + c.y * c.y;
+      const float sz = a.z * a.z + b.z * b.z + c.z * c.z, sw = a.w * a.w + b.w * b.w + c.w * c.w;
+      ss += (double)((sx + sy) + (sz + sw));  // one FP64 addition per four nodes
     }
   } else {
     for (long long q = first; q < n; q += stride) {
@@ -819,9 +847,10 @@ __global__ void __launch_bounds__(256) sumsq3_kernel(long long n, const R *f0, c
 
 // x += alpha p (X; otherwise the next product applies it), r -= alpha q,
 // alpha = rz/pq; partial sums of r.(D^-1 r) and r.r (each node's
-// three-component terms in the context precision, accumulated in FP64). FP32
-// vectors are streamed four nodes per load (n is a multiple of 4: the padded
-// node arrays have rows of a multiple of 32).
+// three-component terms in the context precision; FP32 contexts sum the
+// terms of each group of four nodes in FP32, and the groups are accumulated
+// in FP64). FP32 vectors are streamed four nodes per load (n is a multiple of
+// 4: the padded node arrays have rows of a multiple of 32).
 template <typename R, bool X>
 __global__ void __launch_bounds__(256) cg_update_kernel(long long n, const CgScalars *sc, int parity, R *x0, R *x1,
                                                          R *x2, R *r0, R *r1, R *r2, const R *p0, const R *p1,
@@ -851,14 +880,19 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long n, const CgSca
         reinterpret_cast<float4 *>(Rr[c])[v] = rv;
         a[c] = rv;
       }
-      rz += (double)(a[0].x * dd[0].x * a[0].x + a[1].x * dd[1].x * a[1].x + a[2].x * dd[2].x * a[2].x);
-      rz += (double)(a[0].y * dd[0].y * a[0].y + a[1].y * dd[1].y * a[1].y + a[2].y * dd[2].y * a[2].y);
-      rz += (double)(a[0].z * dd[0].z * a[0].z + a[1].z * dd[1].z * a[1].z + a[2].z * dd[2].z * a[2].z);
-      rz += (double)(a[0].w * dd[0].w * a[0].w + a[1].w * dd[1].w * a[1].w + a[2].w * dd[2].w * a[2].w);
-      rr += (double)(a[0].x * a[0].x + a[1].x * a[1].x + a[2].x * a[2].x);
-      rr += (double)(a[0].y * a[0].y + a[1].y * a[1].y + a[2].y * a[2].y);
-      rr += (double)(a[0].z * a[0].z + a[1].z * a[1].z + a[2].z * a[2].z);
-      rr += (double)(a[0].w * a[0].w + a[1].w * a[1].w + a[2].w * a[2].w);
+      // the four nodes' terms summed in FP32, one FP64 addition per group
+      // (FP64 arithmetic is slow on this part: per-node FP64 additions made
+      // the pass bound by them rather than by DRAM)
+      const float zx = a[0].x * dd[0].x * a[0].x + a[1].x * dd[1].x * a[1].x + a[2].x * dd[2].x * a[2].x;
+      const float zy = a[0].y * dd[0].y * a[0].y + a[1].y * dd[1].y * a[1].y + a[2].y * dd[2].y * a[2].y;
+      const float zz = a[0].z * dd[0].z * a[0].z + a[1].z * dd[1].z * a[1].z + a[2].z * dd[2].z * a[2].z;
+      const float zw = a[0].w * dd[0].w * a[0].w + a[1].w * dd[1].w * a[1].w + a[2].w * dd[2].w * a[2].w;
+      const float sx = a[0].x * a[0].x + a[1].x * a[1].x + a[2].x * a[2].x;
+      const float sy = a[0].y * a[0].y + a[1].y * a[1].y + a[2].y * a[2].y;
+      const float sz = a[0].z * a[0].z + a[1].z * a[1].z + a[2].z * a[2].z;
+      const float sw = a[0].w * a[0].w + a[1].w * a[1].w + a[2].w * a[2].w;
+      rz += (double)((zx + zy) + (zz + zw));
+      rr += (double)((sx + sy) + (sz + sw));
     }
   } else {
     for (long long q = first; q < n; q += stride) {
