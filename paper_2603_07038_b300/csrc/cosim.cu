@@ -737,7 +737,6 @@ extern "C" cosim_status cosim_set_sources(cosim_ctx *c, int32_t n, const cosim_s
 
 // ---------------------------------------------------------------- EM
 
-constexpr int kJouleWindow = 32;  // EM steps per short-window Joule accumulation
 
 template <typename R>
 static ThArgs<R> th_args(cosim_ctx *c);
@@ -843,9 +842,10 @@ static EmArgs<R> em_args_base(cosim_ctx *c, bool accum) {
 }
 
 // The arguments of one step: the E/H buffers read (parity o) and written,
-// their descriptors, the source time offset s within the call, the Joule fold.
+// their descriptors, the source time offset s within the call, the step's
+// Joule window position (-1: not accumulating).
 template <typename R, int TY>
-static void em_args_step(cosim_ctx *c, EmArgs<R> &A, int o, int s, bool fold) {
+static void em_args_step(cosim_ctx *c, EmArgs<R> &A, int o, int s, int fold) {
   constexpr int t = em_ty_index(TY);
   const int n = o ^ 1;
   for (int a = 0; a < 3; ++a) {
@@ -886,7 +886,9 @@ static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool
   const size_t smem = em_smem_bytes<R, TY>((int)c->mats.size());
   constexpr int t = em_ty_index(TY);
   for (int64_t s = 0; s < nsteps; ++s) {
-    em_args_step<R, TY>(c, A, c->par, (int)s, accum && ((c->n_acc + 1) % kJouleWindow == 0));
+    // the step's position in the Joule window: each node plane folds once per
+    // window, the planes spread over its steps
+    em_args_step<R, TY>(c, A, c->par, (int)s, accum ? (int)(c->n_acc % kJouleWindow) : -1);
     A.tmT = c->tmT[t][c->tpar];
     A.tmT2 = c->tmT2[t][c->tpar];
     A.Pout = (R *)c->P;
@@ -936,7 +938,7 @@ static cosim_status em_steps_tile(cosim_ctx *c, int64_t nsteps, bool accum, bool
     c->step++;
     if (accum) {
       c->n_acc++;
-      c->qs_dirty = !A.fold;
+      c->qs_dirty = true;  // some planes hold energy of their current window
     }
   }
   if (nsteps > 0 && !probe) {
@@ -1083,7 +1085,7 @@ extern "C" cosim_status cosim_em_graph_launch(cosim_ctx *c, int64_t count) {
     c->launches += c->g_launches;
     if (c->g_accum) {
       c->n_acc += c->g_nsteps;
-      c->qs_dirty = false;  // the last step of a 32-step window folds
+      c->qs_dirty = true;
     }
   }
   return COSIM_OK;
@@ -1102,7 +1104,7 @@ struct cosim_batch {
     int first = 0, n = 0, total = 0, grid = 0;
     bool wide = false;               // some context needs 64-bit node offsets
     size_t smem = 0;
-    std::vector<unsigned char> args;  // EmBatchArgs<R>[8]: [accum][parity][fold]
+    std::vector<unsigned char> args;  // EmBatchArgs<R>[4]: [accum][parity] (the fold is a launch parameter)
   };
   std::vector<Group> groups;
   unsigned *work = nullptr;      // two tile counters per group (persistent launches)
@@ -1146,27 +1148,26 @@ static cosim_status batch_build(cosim_batch *b) {
     cosim_batch::Group g;
     g.first = first;
     g.n = std::min(kBatchMax, n - first);
-    g.args.assign(8 * sizeof(EmBatchArgs<R>), 0);
+    g.args.assign(4 * sizeof(EmBatchArgs<R>), 0);
     EmBatchArgs<R> *P = reinterpret_cast<EmBatchArgs<R> *>(g.args.data());
     for (int d = 0; d < g.n; ++d) {
       cosim_ctx *c = b->ctx[first + d];
       for (int acc = 0; acc < 2; ++acc) {
         const EmArgs<R> base = em_args_base<R, kEmTY>(c, acc != 0);
-        for (int o = 0; o < 2; ++o)
-          for (int f = 0; f < 2; ++f) {
-            EmArgs<R> A = base;
-            em_args_step<R, kEmTY>(c, A, o, 0, f != 0);
-            P[4 * acc + 2 * o + f].a[d] = A;
-          }
+        for (int o = 0; o < 2; ++o) {
+          EmArgs<R> A = base;
+          em_args_step<R, kEmTY>(c, A, o, 0, -1);
+          P[2 * acc + o].a[d] = A;
+        }
       }
       const EmArgs<R> &A = P[0].a[d];
       const int tiles = A.n_border + A.npx * (A.iby1 - A.iby0);
-      for (int v = 0; v < 8; ++v) P[v].cta_start[d + 1] = P[v].cta_start[d] + tiles;
+      for (int v = 0; v < 4; ++v) P[v].cta_start[d + 1] = P[v].cta_start[d] + tiles;
       st[first + d] = c->dstep;
       g.smem = std::max(g.smem, em_smem_bytes<R, kEmTY>((int)c->mats.size()));
       g.wide = g.wide || c->npad >= (1LL << 31);
     }
-    for (int v = 0; v < 8; ++v) P[v].n = g.n;
+    for (int v = 0; v < 4; ++v) P[v].n = g.n;
     g.total = P[0].cta_start[g.n];
     g.grid = g.total;
     if (b->persistent) {  // about the CTAs that are resident at once
@@ -1249,8 +1250,8 @@ static cosim_status batch_steps_t(cosim_batch *b, int64_t nsteps, bool accum) {
   cosim_ctx *c0 = b->ctx[0];
   const dim3 blk(kEmTX, kEmTY);
   for (int64_t s = 0; s < nsteps; ++s) {
-    const bool fold = accum && ((c0->n_acc + 1) % kJouleWindow == 0);
-    const int variant = 4 * (accum ? 1 : 0) + 2 * c0->par + (fold ? 1 : 0);
+    const int fold = accum ? (int)(c0->n_acc % kJouleWindow) : -1;  // window position (the kernel parameter)
+    const int variant = 2 * (accum ? 1 : 0) + c0->par;
     const int cnt = (int)(b->n_launch & 1);
     if (b->persistent) ++b->n_launch;
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
@@ -1259,9 +1260,9 @@ static cosim_status batch_steps_t(cosim_batch *b, int64_t nsteps, bool accum) {
       unsigned *w = b->persistent ? b->work + 2 * gi + cnt : nullptr;
       unsigned *wn = b->persistent ? b->work + 2 * gi + (cnt ^ 1) : nullptr;
       if (g.wide)
-        em_batch_kernel<R, long long, kEmTX, kEmTY><<<g.grid, blk, g.smem, b->stream>>>(P, (int)s, w, wn);
+        em_batch_kernel<R, long long, kEmTX, kEmTY><<<g.grid, blk, g.smem, b->stream>>>(P, (int)s, fold, w, wn);
       else
-        em_batch_kernel<R, int, kEmTX, kEmTY><<<g.grid, blk, g.smem, b->stream>>>(P, (int)s, w, wn);
+        em_batch_kernel<R, int, kEmTX, kEmTY><<<g.grid, blk, g.smem, b->stream>>>(P, (int)s, fold, w, wn);
       BCHECK(b, cudaGetLastError());
     }
     for (cosim_ctx *c : b->ctx) {
@@ -1269,7 +1270,7 @@ static cosim_status batch_steps_t(cosim_batch *b, int64_t nsteps, bool accum) {
       c->step++;
       if (accum) {
         c->n_acc++;
-        c->qs_dirty = !fold;
+        c->qs_dirty = true;
       }
     }
     c0->launches += (long long)b->groups.size();
@@ -1373,7 +1374,7 @@ extern "C" cosim_status cosim_batch_graph_launch(cosim_batch *b, int64_t count) 
       c->step += b->g_nsteps;
       if (b->g_accum) {
         c->n_acc += b->g_nsteps;
-        c->qs_dirty = false;  // the last step of a 32-step window folds
+        c->qs_dirty = true;
       }
     }
     b->ctx[0]->launches += b->g_launches;

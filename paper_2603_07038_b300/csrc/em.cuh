@@ -88,8 +88,12 @@ struct EmArgs {
   const long long *step_base;
   int step_off;
   // Joule energy: each step adds to the short-window accumulator Qs (context
-  // precision); on fold steps the owner moves Qs into the FP64 total Q instead,
-  // so FP64 arithmetic runs once per window rather than every step.
+  // precision); once per window of kJouleWindow steps the owner moves a node's
+  // Qs into the FP64 total Q instead, so FP64 arithmetic runs once per window
+  // rather than every step. The folds are spread over the window by plane:
+  // fold = the step's position p in the window (-1: no fold, the kernel
+  // parameter of batch launches instead), and node plane k folds when
+  // (p + k) mod kJouleWindow = kJouleWindow - 1, so no step carries all of it.
   R *Qs;                      // null: not accumulating
   double *Q;
   int fold;
@@ -125,6 +129,14 @@ struct EmArgs {
   int *err;         // set to 1 when a bounded wait for a staged plane gave up
   long long wait;   // the bound of those waits, in SM clock cycles
 };
+
+// EM steps per short-window Joule accumulation (a power of two), and whether
+// node plane kk folds its window at the step of window position `fold`
+constexpr int kJouleWindow = 32;
+static_assert((kJouleWindow & (kJouleWindow - 1)) == 0, "the Joule window is a power of two");
+__device__ __forceinline__ bool plane_folds(int fold, int kk) {
+  return fold >= 0 && ((fold + kk) & (kJouleWindow - 1)) == kJouleWindow - 1;
+}
 
 // index of position p (node or cell) of an axis inside its CPML slabs, or -1
 __device__ __forceinline__ int slab_index(int p, int n, int lo, int hi) {
@@ -454,7 +466,8 @@ __device__ __forceinline__ void em_abort(uint64_t *bars, int k, int nz, int *err
 template <typename R, typename I, int TY, bool CPL, bool TH, bool XS, bool YS>
 __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
                                                EmStage<R, 32, TY> *stg, R (*sHxz)[2][TY][32], R (*sQy)[TY][32],
-                                               uint64_t *bars, int *s_abort, int xs, int xe, int by, int step_off) {
+                                               uint64_t *bars, int *s_abort, int xs, int xe, int by, int step_off,
+                                               int fold) {
   constexpr int TX = 32;
   const Geo<R> &g = A.g;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -788,7 +801,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
     // Joule energy of node (i, j, k-1): its y-edge share from j-1 is now visible
     if (accum && own && (PL || k > 0)) {
       const R s = add_(q_pend, sQy[par ^ 1][ty - 1][tx]);
-      if (A.fold) {
+      if (plane_folds(fold, k - 1)) {
         A.Q[id - plane] += (double)s;
         A.Qs[id - plane] = R(0);
       } else {
@@ -896,7 +909,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
   if (accum && own) {  // Joule energy of the top plane k = nz
     const I id = id0 + (I)nz * plane;
     const R s = add_(q_pend, sQy[nz & 1][ty - 1][tx]);
-    if (A.fold) {
+    if (plane_folds(fold, nz)) {
       A.Q[id] += (double)s;
       A.Qs[id] = R(0);
     } else {
@@ -923,7 +936,7 @@ template <typename R, typename I, int TY, bool CPL, bool TH>
 __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
                                              EmStage<R, kEm2Nodes, TY> *stg, typename Pair2<R>::T (*sHxz)[2][TY][32],
                                              typename Pair2<R>::T (*sQy)[TY][32], uint64_t *bars, int *s_abort, int xs,
-                                             int by, int step_off) {
+                                             int by, int step_off, int fold) {
   using R2 = typename Pair2<R>::T;
   constexpr int BX = em2_box_x(), BV = em2_vox_box_x();
   const Geo<R> &g = A.g;
@@ -1168,7 +1181,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
     }
     if (accum && own && (PL || k > 0)) {
       const R2 s = add_(q_pend, sQy[par ^ 1][ty - 1][tx]);
-      if (A.fold) {
+      if (plane_folds(fold, k - 1)) {
         double2 *qp = reinterpret_cast<double2 *>(A.Q + (id - plane));
         double2 qv = *qp;
         qv.x += (double)s.x;
@@ -1282,7 +1295,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
   if (accum && own) {  // Joule energy of the top plane k = nz
     const I id = id0 + (I)nz * plane;
     const R2 s = add_(q_pend, sQy[nz & 1][ty - 1][tx]);
-    if (A.fold) {
+    if (plane_folds(fold, nz)) {
       double2 *qp = reinterpret_cast<double2 *>(A.Q + id);
       double2 qv = *qp;
       qv.x += (double)s.x;
@@ -1315,7 +1328,7 @@ __host__ __device__ constexpr int em_min_ctas(int rsz, int ty) { return rsz == 4
 // CPL: the coupled step (sigma(T), Joule power of the step); TH: with the
 // thermal step of Eq. 5 in the same launch (else a thermal launch follows).
 template <typename R, typename I, int TX, int TY, bool CPL, bool TH>
-__device__ __forceinline__ void em_cta(const EmArgs<R> &A, int b, int step_off, unsigned char *smem,
+__device__ __forceinline__ void em_cta(const EmArgs<R> &A, int b, int step_off, int fold, unsigned char *smem,
                                        typename Pair2<R>::T (*sHxz)[2][TY][TX], typename Pair2<R>::T (*sQy)[TY][TX],
                                        uint64_t *s_bar, int *s_abort) {
   static_assert(TX == 32, "a tile row is one warp: x neighbours are exchanged by shuffles");
@@ -1364,7 +1377,8 @@ __device__ __forceinline__ void em_cta(const EmArgs<R> &A, int b, int step_off, 
       } else {
         xs = A.xb1 + (TX - 1) * (c - A.nl);
       }
-      em_tile_border<R, I, TY, CPL, TH, true, false>(A, s_cp, s_mt, sb, sh, sq, s_bar, s_abort, xs, xe, by, step_off);
+      em_tile_border<R, I, TY, CPL, TH, true, false>(A, s_cp, s_mt, sb, sh, sq, s_bar, s_abort, xs, xe, by, step_off,
+                                                     fold);
     } else {
       if (b >= below) {
         b -= below + mid;
@@ -1378,16 +1392,17 @@ __device__ __forceinline__ void em_cta(const EmArgs<R> &A, int b, int step_off, 
       // nodes i = xs - 1 .. xs + 30: does the tile reach an x slab?
       const bool xsl = (A.slo[0] > 0 && xs - 1 <= A.slo[0]) || (A.shi[0] > 0 && xs + TX - 2 >= A.g.nx - A.shi[0]);
       if (xsl)
-        em_tile_border<R, I, TY, CPL, TH, true, true>(A, s_cp, s_mt, sb, sh, sq, s_bar, s_abort, xs, xe, by, step_off);
+        em_tile_border<R, I, TY, CPL, TH, true, true>(A, s_cp, s_mt, sb, sh, sq, s_bar, s_abort, xs, xe, by, step_off,
+                                                      fold);
       else
         em_tile_border<R, I, TY, CPL, TH, false, true>(A, s_cp, s_mt, sb, sh, sq, s_bar, s_abort, xs, xe, by,
-                                                       step_off);
+                                                       step_off, fold);
     }
   } else {
     b -= A.n_border;
     const int py = b / A.npx, px = b - py * A.npx;
     em_tile_pair<R, I, TY, CPL, TH>(A, s_cp, s_mt, reinterpret_cast<EmStage<R, kEm2Nodes, TY> *>(stg), sHxz, sQy, s_bar,
-                                    s_abort, A.xb0 + 62 * px, A.iby0 + py, step_off);
+                                    s_abort, A.xb0 + 62 * px, A.iby0 + py, step_off, fold);
   }
 }
 
@@ -1405,12 +1420,12 @@ __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
   __shared__ R2 sQy[2][TY][TX];      // Joule share of the y-edge, read by the +y neighbour one plane later
   __shared__ uint64_t s_bar[kEmStages];  // one transaction barrier per stage
   __shared__ int s_abort;
-  em_cta<R, I, TX, TY, CPL, TH>(A, (int)blockIdx.x, A.step_off, smem, sHxz, sQy, s_bar, &s_abort);
+  em_cta<R, I, TX, TY, CPL, TH>(A, (int)blockIdx.x, A.step_off, A.fold, smem, sHxz, sQy, s_bar, &s_abort);
 }
 
 // A group of up to kBatchMax contexts (independent package designs) for one
 // launch of a batch step: their arguments for the step's E/H parity and
-// Joule fold, by value in the kernel's parameter space (8 designs fill most
+// Joule accumulation, by value in the kernel's parameter space (8 designs fill most
 // of the 32 KB a launch may pass), and cta_start[d], the first tile of design
 // d in the group's tile order (cta_start[n] = all tiles).
 constexpr int kBatchMax = 8;
@@ -1427,10 +1442,12 @@ struct EmBatchArgs {
 // first, so that the small ones fill the tail), and zeroes *next_work, the
 // counter of the group's next launch (launches alternate between two
 // counters, so that no launch resets a counter in use). The stage barriers
-// are invalidated after each tile and initialised again for the next.
+// are invalidated after each tile and initialised again for the next. fold:
+// the step's Joule window position (-1: no fold), as EmArgs::fold.
 template <typename R, typename I, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
-    em_batch_kernel(const __grid_constant__ EmBatchArgs<R> P, int step_off, unsigned *work, unsigned *next_work) {
+    em_batch_kernel(const __grid_constant__ EmBatchArgs<R> P, int step_off, int fold, unsigned *work,
+                    unsigned *next_work) {
   using R2 = typename Pair2<R>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -1460,7 +1477,7 @@ __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
       if (b >= total) return;
     }
     const int d = design(b);
-    em_cta<R, I, TX, TY, false, false>(P.a[d], b - P.cta_start[d], step_off, smem, sHxz, sQy, s_bar, &s_abort);
+    em_cta<R, I, TX, TY, false, false>(P.a[d], b - P.cta_start[d], step_off, fold, smem, sHxz, sQy, s_bar, &s_abort);
     if (!persistent) return;
     __syncthreads();  // every thread is past the tile's waits and its reads of s_tile
     if (s_abort) return;
