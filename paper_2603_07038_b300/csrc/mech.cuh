@@ -458,6 +458,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
   }
   R2 acc[3] = {bc_<R2>(R(0)), bc_<R2>(R(0)), bc_<R2>(R(0))};
   double dot = 0.0;
+  R part4 = 0;  // the thread's u.y terms of up to four planes, one FP64 addition per four
   const int cu = 2 * tx + xr;  // element corner (ea, ey) column in the u boxes
   for (int k = 0; k < nz; ++k) {
     {
@@ -577,7 +578,11 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
         }
         acc[c] = top;
       }
-      dot += (double)part;
+      part4 += part;
+      if ((k & 3) == 3) {
+        dot += (double)part4;
+        part4 = 0;
+      }
     }
   }
   if (oa || ob) {  // the top node plane: plane nz is still staged (nothing was issued after it)
@@ -606,8 +611,9 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 2 : 1)
         }
       }
     }
-    dot += (double)part;
+    part4 += part;
   }
+  dot += (double)part4;
   if (A.partial != nullptr) {
     const double s = block_sum(dot);
     if (tid == 0) A.partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
