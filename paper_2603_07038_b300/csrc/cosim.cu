@@ -1405,6 +1405,32 @@ __global__ void __launch_bounds__(256) joule_flush_kernel(long long n, double *Q
   }
 }
 
+// op 1 of the finalisation as one streaming pass over the padded node arrays:
+// P = (Q + Qs) * inv_t, the burst-averaged power per node, with the pending
+// short-window energy Qs added on the fly (Qs null: none pending); Q and Qs
+// are left as they are. FP32 contexts form P in FP32 (Q rounded to FP32
+// first, then one addition and one multiplication; P is stored in FP32
+// anyway): FP64 arithmetic is slow on this part, and one FP64 multiplication
+// per node bound this pass. FP32 contexts stream four nodes per access (n is
+// a multiple of 4; the padding gives 0).
+template <typename R>
+__global__ void __launch_bounds__(256) joule_power_kernel(long long n, const double *Q, const R *Qs, R *P,
+                                                          double inv_t) {
+  const long long stride = (long long)gridDim.x * blockDim.x, first = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if constexpr (sizeof(R) == 4) {
+    const float it = (float)inv_t;
+    for (long long v = first; v < (n >> 2); v += stride) {
+      const float4 w = Qs != nullptr ? reinterpret_cast<const float4 *>(Qs)[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const double2 q01 = reinterpret_cast<const double2 *>(Q)[2 * v], q23 = reinterpret_cast<const double2 *>(Q)[2 * v + 1];
+      reinterpret_cast<float4 *>(P)[v] =
+          make_float4(((float)q01.x + w.x) * it, ((float)q01.y + w.y) * it, ((float)q23.x + w.z) * it,
+                      ((float)q23.y + w.w) * it);
+    }
+  } else {
+    for (long long q = first; q < n; q += stride) P[q] = (Q[q] + (Qs != nullptr ? Qs[q] : R(0))) * inv_t;
+  }
+}
+
 static cosim_status joule_flush(cosim_ctx *c) {
   if (!c->qs_dirty) return COSIM_OK;
   if (c->prec == COSIM_FP64)
@@ -1435,6 +1461,16 @@ static cosim_status joule_t(cosim_ctx *c, int op) {
   const dim3 blk(32, 8), grd((c->nx + 1 + 31) / 32, (c->ny + 1 + 7) / 8);
   const size_t smem = c->mats.size() * M_COLS * sizeof(R);
   const double inv_t = c->n_acc > 0 ? 1.0 / (c->n_acc * c->dt) : 0.0;
+  if (op == COSIM_JOULE_FINALIZE_AVG_POWER) {  // the pending window added on the fly, not folded
+    joule_power_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(c->npad, c->Q, c->qs_dirty ? (const R *)c->Qs : nullptr,
+                                                             (R *)c->P, inv_t); ++c->launches;
+    CHECK_LAUNCH(c);
+    return COSIM_OK;
+  }
+  {
+    cosim_status fs = joule_flush(c);
+    if (fs != COSIM_OK) return fs;
+  }
   joule_finalize_kernel<R><<<grd, blk, smem, c->stream>>>(make_geo<R>(c), c->Q, (R *)c->P, (R *)c->T[c->tpar],
                                                           inv_t, op); ++c->launches;
   CHECK_LAUNCH(c);
@@ -1452,13 +1488,10 @@ extern "C" cosim_status cosim_joule_accumulate(cosim_ctx *c, int32_t op, double 
     c->n_acc = 0;
     return COSIM_OK;
   }
-  {
-    cosim_status fs = joule_flush(c);
-    if (fs != COSIM_OK) return fs;
-  }
   cosim_status st = c->prec == COSIM_FP64 ? joule_t<double>(c, op) : joule_t<float>(c, op);
   if (st != COSIM_OK) return st;
   if (total) {
+    if ((st = joule_flush(c)) != COSIM_OK) return st;  // the total sums Q only
     st = sum_q(c, total);
     if (st != COSIM_OK) return st;
     if (!std::isfinite(*total)) return fail(c, COSIM_ERR_NONFINITE, "non-finite Joule energy");
