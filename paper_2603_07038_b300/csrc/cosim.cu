@@ -1974,14 +1974,24 @@ extern "C" cosim_status cosim_stress_apply(cosim_ctx *c, const cosim_stress_opts
 // ---------------------------------------------------------------- field I/O
 
 // dense <-> padded copies with type conversion. For E/H fields on write,
-// entries that are not unknowns are stored as zero.
+// entries that are not unknowns are stored as zero. A block walks whole rows
+// (no per-element index division); a temperature offset is added in the
+// output precision when both sides are FP32 (the FP64 addition per element
+// it replaces is slow on this part; the sum of two FP32 values rounds once).
 template <typename S, typename D>
 __global__ void pack_kernel(const S *src, D *dst, int nx1, int ny1, int nz1, int px, double add) {
-  const long long n = (long long)nx1 * ny1 * nz1;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % nx1);
-    const long long r = q / nx1;
-    dst[q] = add != 0.0 ? (D)((double)src[r * px + i] + add) : (D)src[r * px + i];
+  const long long rows = (long long)ny1 * nz1;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const S *s = src + r * px;
+    D *d = dst + r * nx1;
+    for (int i = threadIdx.x; i < nx1; i += blockDim.x) {
+      if (add == 0.0)
+        d[i] = (D)s[i];
+      else if constexpr (sizeof(S) == 4 && sizeof(D) == 4)
+        d[i] = s[i] + (float)add;
+      else
+        d[i] = (D)((double)s[i] + add);
+    }
   }
 }
 
@@ -2008,12 +2018,13 @@ struct FieldMask {  // which node-sized entries of an E/H field are unknowns
 
 template <typename S, typename D>
 __global__ void unpack_kernel(const S *src, D *dst, int nx1, int ny1, int nz1, int px, FieldMask fm, double sub) {
-  const long long n = (long long)nx1 * ny1 * nz1;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % nx1);
-    const long long r = q / nx1;
+  const long long rows = (long long)ny1 * nz1;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {  // a block walks whole rows
     const int j = (int)(r % ny1), k = (int)(r / ny1);
-    dst[r * px + i] = fm.keep(i, j, k) ? (sub != 0.0 ? (D)((double)src[q] - sub) : (D)src[q]) : D(0);
+    const S *s = src + r * nx1;
+    D *d = dst + r * px;
+    for (int i = threadIdx.x; i < nx1; i += blockDim.x)
+      d[i] = fm.keep(i, j, k) ? (sub != 0.0 ? (D)((double)s[i] - sub) : (D)s[i]) : D(0);
   }
 }
 
