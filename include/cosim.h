@@ -262,7 +262,8 @@ cosim_status cosim_autotune(cosim_ctx *ctx, uint32_t flags, int32_t *em_tile_y, 
 /* Joule accumulator operations:
  *   COSIM_JOULE_RESET: zero the per-node energy and the accumulated step count;
  *   COSIM_JOULE_FINALIZE_AVG_POWER: thermal source P_i = Q_i / (n_steps dt_em)
- *     [W per node] (burst-averaged power driving Eq. 5);
+ *     [W per node] (burst-averaged power driving Eq. 5); FP32 contexts form
+ *     it in FP32 from Q_i rounded to FP32 (P is stored in FP32);
  *   COSIM_JOULE_FINALIZE_ENERGY: T_i += Q_i / C_i (the burst's energy
  *     deposited adiabatically, C_i the node heat capacity).
  * total_joule_energy_out (nullable): sum_i Q_i [J], deterministic FP64 sum
