@@ -1807,13 +1807,14 @@ static cosim_status pcg_run(cosim_ctx *c, double rtol, int64_t maxit, int every,
     }
   }
   *iters = it;
-  if (fuse && it > 0) {  // the last direction's step (the products applied the earlier ones)
+  const bool last_step = fuse && it > 0;
+  if (last_step) {  // the last direction's step (the products applied the earlier ones), with the final scale
     cg_axpy_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, c->cg, (int)((it - 1) & 1), U[0], U[1], U[2], Pb[cur][0],
-                                                         Pb[cur][1], Pb[cur][2]);
+                                                         Pb[cur][1], Pb[cur][2], (R)(1.0 / scale));
     ++c->launches;
     CHECK_LAUNCH(c);
   }
-  if (scale != 1.0) {
+  if (scale != 1.0 && !last_step) {
     scale3_kernel<R><<<kRedBlocks, 256, 0, c->stream>>>(n, U[0], U[1], U[2], (R)(1.0 / scale)); ++c->launches;
     CHECK_LAUNCH(c);
   }

@@ -660,11 +660,23 @@ __global__ void __launch_bounds__(256) hex8_node_kernel(Geo<R> g, const uint8_t 
   if (MODE == 1) load_plane(0, tp);
   R carry[3] = {0, 0, 0};  // top-corner terms of layer k-1 for the node of plane k
   R *out[3] = {o0, o1, o2};
+  // the column's lateral cell sizes, read once (the stores below could alias
+  // the geometry arrays for the compiler, which would then reload them)
+  R hxc[2], ihxc[2], hyc[2], ihyc[2];
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    const int ei = i - 1 + d, ej = j - 1 + d;
+    hxc[d] = (ei >= 0 && ei < nx) ? g.h[0][ei] : R(0);
+    ihxc[d] = (ei >= 0 && ei < nx) ? g.ih[0][ei] : R(0);
+    hyc[d] = (ej >= 0 && ej < ny) ? g.h[1][ej] : R(0);
+    ihyc[d] = (ej >= 0 && ej < ny) ? g.ih[1][ej] : R(0);
+  }
   for (int k = 0; k <= nz; ++k) {
     R acc[3] = {carry[0], carry[1], carry[2]};
     carry[0] = carry[1] = carry[2] = R(0);
     if (k < nz) {
       if (MODE == 1) load_plane(k + 1, tq);
+      const R hzk = g.h[2][k], ihzk = g.ih[2][k];
 #pragma unroll
       for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
@@ -672,8 +684,8 @@ __global__ void __launch_bounds__(256) hex8_node_kernel(Geo<R> g, const uint8_t 
           const int ei = i - 1 + dx, ej = j - 1 + dy;
           const int m = g.cell(ei, ej, k);
           if (m < 0) continue;
-          const R h[3] = {g.h[0][ei], g.h[1][ej], g.h[2][k]};
-          const R ih[3] = {g.ih[0][ei], g.ih[1][ej], g.ih[2][k]};  // inverse sizes (no divisions)
+          const R h[3] = {hxc[dx], hyc[dy], hzk};
+          const R ih[3] = {ihxc[dx], ihyc[dy], ihzk};  // inverse sizes (no divisions)
           const R V = h[0] * h[1] * h[2];
           const R lam = s_mt[m * M_COLS + M_LAM], mu = s_mt[m * M_COLS + M_MU];
           if (MODE == 0) {
@@ -925,8 +937,10 @@ __global__ void __launch_bounds__(256) cg_update_kernel(long long n, const CgSca
 // products applied the earlier ones (FP32: four nodes per access)
 template <typename R>
 __global__ void __launch_bounds__(256) cg_axpy_kernel(long long n, const CgScalars *sc, int parity, R *x0, R *x1,
-                                                       R *x2, const R *p0, const R *p1, const R *p2) {
+                                                       R *x2, const R *p0, const R *p1, const R *p2, R s) {
+  // s: the solution's final scale (1: none), applied in the same pass
   const R alpha = (R)(sc->rz[parity] / sc->pq);
+  const bool scaled = s != R(1);
   const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
   if constexpr (sizeof(R) == 4) {
     float4 *X[3] = {reinterpret_cast<float4 *>(x0), reinterpret_cast<float4 *>(x1), reinterpret_cast<float4 *>(x2)};
@@ -938,13 +952,16 @@ __global__ void __launch_bounds__(256) cg_axpy_kernel(long long n, const CgScala
         float4 x = X[c][v];
         const float4 p = P[c][v];
         x.x += alpha * p.x, x.y += alpha * p.y, x.z += alpha * p.z, x.w += alpha * p.w;
+        if (scaled) x.x *= s, x.y *= s, x.z *= s, x.w *= s;
         X[c][v] = x;
       }
   } else {
     for (long long q = first; q < n; q += stride) {
-      x0[q] += alpha * p0[q];
-      x1[q] += alpha * p1[q];
-      x2[q] += alpha * p2[q];
+      R a = x0[q] + alpha * p0[q], b = x1[q] + alpha * p1[q], c = x2[q] + alpha * p2[q];
+      if (scaled) a *= s, b *= s, c *= s;
+      x0[q] = a;
+      x1[q] = b;
+      x2[q] = c;
     }
   }
 }
