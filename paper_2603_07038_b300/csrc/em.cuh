@@ -932,7 +932,7 @@ __device__ __forceinline__ void em_tile_border(const EmArgs<R> &A, const R *s_cp
 // +x/+y neighbours and its voxels lie inside the grid, off the lateral walls
 // and outside the x/y CPML slabs; only the z slab and walls remain, decided
 // per plane for the whole CTA.
-template <typename R, typename I, int TY, bool CPL, bool TH>
+template <typename R, typename I, int TY, bool CPL, bool TH, bool ES>
 __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, const R *s_mt,
                                              EmStage<R, kEm2Nodes, TY> *stg, typename Pair2<R>::T (*sHxz)[2][TY][32],
                                              typename Pair2<R>::T (*sQy)[TY][32], uint64_t *bars, int *s_abort, int xs,
@@ -1095,6 +1095,31 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
       r0 = S0.S.v[0][sr];
       r1 = S0.S.v[0][sr + 1];
     }
+    // ---- source currents on the pair's edges. ES (plain single-context
+    // steps) forms them here, before the H update, so that the E update after
+    // the barrier is one block; the coupled and batch kernels (more live
+    // state: measured slower) keep them after the barrier.
+    R2 Jx = z2, Jy = z2, Jz = z2;
+    auto add_sources = [&]() {
+      for (int e = r0; e < r1; ++e) {
+        const int4 s = A.src_ent[e];
+        const long long step = *A.step_base + step_off;
+        if ((s.x == ia || s.x == ia + 1) && step < A.amp_len) {
+          const R a = A.src_amp[(long long)s.z * A.amp_len + step];
+          if (s.x == ia) {
+            Jx.x = add_(Jx.x, s.y == 0 ? a : R(0));
+            Jy.x = add_(Jy.x, s.y == 1 ? a : R(0));
+            Jz.x = add_(Jz.x, s.y == 2 ? a : R(0));
+          } else {
+            Jx.y = add_(Jx.y, s.y == 0 ? a : R(0));
+            Jy.y = add_(Jy.y, s.y == 1 ? a : R(0));
+            Jz.y = add_(Jz.y, s.y == 2 ? a : R(0));
+          }
+        }
+      }
+    };
+    if constexpr (ES) add_sources();
+
     const R2 hdz = bc_<R2>(mul_(half_dt, idzs));
     const bool fix_z = !PL && ((k == 0 && A.fixlo[2]) || (k == nz && A.fixhi[2]));
     const int szE = PL ? -1 : slab_index(k, nz, A.slo[2], A.shi[2]);
@@ -1196,24 +1221,7 @@ __device__ __forceinline__ void em_tile_pair(const EmArgs<R> &A, const R *s_cp, 
     if (CPL && !TH && own && (PL || k > 0))
       stv_(A.Pout + (id - plane), mul_(add_(e_pend, sQy[par ^ 1][ty - 1][tx]), bc_<R2>(A.inv_dt)));
 
-    // ---- source currents on the pair's edges
-    R2 Jx = z2, Jy = z2, Jz = z2;
-    for (int e = r0; e < r1; ++e) {
-      const int4 s = A.src_ent[e];
-      const long long step = *A.step_base + step_off;
-      if ((s.x == ia || s.x == ia + 1) && step < A.amp_len) {
-        const R a = A.src_amp[(long long)s.z * A.amp_len + step];
-        if (s.x == ia) {
-          Jx.x = add_(Jx.x, s.y == 0 ? a : R(0));
-          Jy.x = add_(Jy.x, s.y == 1 ? a : R(0));
-          Jz.x = add_(Jz.x, s.y == 2 ? a : R(0));
-        } else {
-          Jx.y = add_(Jx.y, s.y == 0 ? a : R(0));
-          Jy.y = add_(Jy.y, s.y == 1 ? a : R(0));
-          Jz.y = add_(Jz.y, s.y == 2 ? a : R(0));
-        }
-      }
-    }
+    if constexpr (!ES) add_sources();
 
     // ---- E^{n+1} and the Joule shares
     const R2 pxe_a = fma_(hym, e01, mul_(hy0, e11)), pxs_a = fma_(hym, s01, mul_(hy0, s11));
@@ -1326,8 +1334,9 @@ __host__ __device__ constexpr int em_min_ctas(int rsz, int ty) { return rsz == 4
 // shared window, 128-byte aligned; sHxz, sQy, s_bar, s_abort: the CTA's
 // static exchange arrays, stage barriers (initialised here) and abort flag.
 // CPL: the coupled step (sigma(T), Joule power of the step); TH: with the
-// thermal step of Eq. 5 in the same launch (else a thermal launch follows).
-template <typename R, typename I, int TX, int TY, bool CPL, bool TH>
+// thermal step of Eq. 5 in the same launch (else a thermal launch follows);
+// ES: the pair tiles form the source currents before the H update.
+template <typename R, typename I, int TX, int TY, bool CPL, bool TH, bool ES = !CPL>
 __device__ __forceinline__ void em_cta(const EmArgs<R> &A, int b, int step_off, int fold, unsigned char *smem,
                                        typename Pair2<R>::T (*sHxz)[2][TY][TX], typename Pair2<R>::T (*sQy)[TY][TX],
                                        uint64_t *s_bar, int *s_abort) {
@@ -1401,7 +1410,7 @@ __device__ __forceinline__ void em_cta(const EmArgs<R> &A, int b, int step_off, 
   } else {
     b -= A.n_border;
     const int py = b / A.npx, px = b - py * A.npx;
-    em_tile_pair<R, I, TY, CPL, TH>(A, s_cp, s_mt, reinterpret_cast<EmStage<R, kEm2Nodes, TY> *>(stg), sHxz, sQy, s_bar,
+    em_tile_pair<R, I, TY, CPL, TH, ES>(A, s_cp, s_mt, reinterpret_cast<EmStage<R, kEm2Nodes, TY> *>(stg), sHxz, sQy, s_bar,
                                     s_abort, A.xb0 + 62 * px, A.iby0 + py, step_off, fold);
   }
 }
@@ -1477,7 +1486,8 @@ __global__ void __launch_bounds__(TX *TY, em_min_ctas(sizeof(R), TY))
       if (b >= total) return;
     }
     const int d = design(b);
-    em_cta<R, I, TX, TY, false, false>(P.a[d], b - P.cta_start[d], step_off, fold, smem, sHxz, sQy, s_bar, &s_abort);
+    em_cta<R, I, TX, TY, false, false, false>(P.a[d], b - P.cta_start[d], step_off, fold, smem, sHxz, sQy, s_bar,
+                                              &s_abort);
     if (!persistent) return;
     __syncthreads();  // every thread is past the tile's waits and its reads of s_tile
     if (s_abort) return;
