@@ -272,6 +272,18 @@ static double cpml_sigma(const cosim_ctx *c, int a, double pos, const std::vecto
 
 // ---------------------------------------------------------------- create
 
+constexpr size_t kHostVoxelCheck = (size_t)1 << 24;  // voxels checked on the host (larger grids: on the device)
+
+// the largest voxel ID of the pitched voxel array (rows of nx IDs, pitch vpx)
+__global__ void __launch_bounds__(256) voxel_max_kernel(const uint8_t *mat, int nx, long long rows, int vpx,
+                                                        unsigned *out) {
+  unsigned mx = 0;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x)
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) mx = max(mx, (unsigned)mat[r * vpx + i]);
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx != 0) atomicMax(out, mx);
+}
+
 static cosim_status validate(const cosim_grid_desc *d, const cosim_options *o, std::string &why) {
   if (!d) return why = "desc is NULL", COSIM_ERR_INVALID;
   if (d->nx < 1 || d->ny < 1 || d->nz < 1) return why = "grid sizes must be >= 1", COSIM_ERR_INVALID;
@@ -290,7 +302,11 @@ static cosim_status validate(const cosim_grid_desc *d, const cosim_options *o, s
         !(q.nu > -1 && q.nu < 0.5))
       return why = "material " + std::to_string(m) + " has out-of-range constants", COSIM_ERR_INVALID;
   }
-  if (d->nmat < 256) {  // a branch-free maximum (vectorised): one pass over the voxels at memory speed
+  // Every voxel ID below nmat. Grids up to kHostVoxelCheck voxels are checked
+  // here, before any device work; larger ones on the device after the
+  // upload (a host pass over a full package's 134 M IDs took milliseconds of
+  // every cosim_create).
+  if (d->nmat < 256 && (size_t)d->nx * d->ny * d->nz <= kHostVoxelCheck) {
     const size_t nc = (size_t)d->nx * d->ny * d->nz;
     uint8_t mx = 0;
     for (size_t q = 0; q < nc; ++q) mx = d->mat[q] > mx ? d->mat[q] : mx;
@@ -394,6 +410,8 @@ static cosim_status encode_voxel_map(cosim_ctx *c, CUtensorMap *m, int rows, int
 }
 
 
+static void free_one(cosim_ctx *c, void *p);
+
 static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const cosim_options *o) {
   c->nx = d->nx;
   c->ny = d->ny;
@@ -491,6 +509,18 @@ static cosim_status create_impl(cosim_ctx *c, const cosim_grid_desc *d, const co
   ALLOC(c, c->mat, (size_t)c->vpx * c->ny * c->nz);
   CHECK_CUDA(c, cudaMemcpy2DAsync(c->mat, c->vpx, d->mat, c->nx, c->nx, (size_t)c->ny * c->nz,
                                   cudaMemcpyHostToDevice, c->stream));
+  if (d->nmat < 256 && (size_t)d->nx * d->ny * d->nz > kHostVoxelCheck) {  // the largest voxel ID, on the device
+    unsigned *dmax = nullptr;
+    ALLOC(c, dmax, sizeof(unsigned));
+    voxel_max_kernel<<<kRedBlocks, 256, 0, c->stream>>>(c->mat, c->nx, (long long)c->ny * c->nz, c->vpx, dmax);
+    ++c->launches;
+    CHECK_LAUNCH(c);
+    unsigned mx = 0;
+    CHECK_CUDA(c, cudaMemcpyAsync(&mx, dmax, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+    free_one(c, dmax);
+    if (mx >= (unsigned)d->nmat) return fail(c, COSIM_ERR_INVALID, "voxel material id >= nmat");
+  }
   // per node plane k: hz(k), 1/hz(k), 1/dual_z(k), hz(k-1), zero where the
   // cell does not exist; one 16/32-byte record copied per plane by the EM kernel
   {

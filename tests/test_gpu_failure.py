@@ -80,6 +80,25 @@ def test_allocation_failure_at_create_returns_every_block():
         assert not a.live  # what was handed out before the failure came back
 
 
+def test_invalid_material_id_rejected_on_device():
+    """Grids above 2^24 voxels have their IDs checked on the device after the
+    upload (smaller ones on the host, tests/test_abi.py): a bad ID is reported
+    as COSIM_ERR_INVALID and every block handed out comes back."""
+    build()
+    p = W.uniform_box(260, 260, 250, em_bc=(0,) * 6)
+    assert p.n_cells > 1 << 24
+    p.mat[200, 100, 17] = 7
+    a = FlakyAllocator()
+    with pytest.raises(api.CosimError) as e:
+        api.cosim_create(p, api.COSIM_FP32, allocator=a)
+    assert e.value.status == api.COSIM_ERR_INVALID and "material id" in str(e.value)
+    assert not a.live
+    p.mat[200, 100, 17] = 0  # the same grid with valid IDs is created
+    h, keep = api.cosim_create(p, api.COSIM_FP32, allocator=a)
+    api.cosim_destroy(h)
+    assert not a.live
+
+
 def test_allocation_failure_later_leaves_context_valid():
     build()
     p = W.tiny_package()
