@@ -62,13 +62,15 @@ class PRBSBurst:
     def __call__(self, t):
         t = np.asarray(t, dtype=np.float64)
         tb = 1.0 / self.bit_rate
+        nb = len(self.bits)
+        # the CDF at every bit edge t_q = t_start + q t_bit, q = 0..n_bits, once
+        # (bit b spans edges b and b+1), the bits' terms summed in order
+        tq = (self.t_start + np.arange(nb + 1) * tb).reshape((nb + 1,) + (1,) * t.ndim)
+        edges = ndtr((t - tq) / self.edge_sigma)  # edge q in edges[q]
+        lvl = 2.0 * self.bits.astype(np.float64) - 1.0
         out = np.zeros_like(t)
-        phi = ndtr
-        for b, bit in enumerate(self.bits):
-            lo = self.t_start + b * tb
-            hi = lo + tb
-            lvl = 2.0 * float(bit) - 1.0
-            out += lvl * (phi((t - lo) / self.edge_sigma) - phi((t - hi) / self.edge_sigma))
+        for b in range(nb):
+            out += lvl[b] * (edges[b] - edges[b + 1])
         return self.j0 * out
 
 
