@@ -82,6 +82,29 @@ def test_tiny_package_source_burst(precision, tol):
     ctx.close()
 
 
+@pytest.mark.parametrize("precision,tol", [(FP64, 1e-11), (FP32, 1e-4)])
+def test_average_power_with_pending_joule_window(precision, tol):
+    """FINALIZE_AVG_POWER straight after 70 accumulating steps (two full
+    32-step windows and a partial one, nothing read in between): the power
+    adds the pending window on the fly, and the energy read afterwards is
+    complete"""
+    p = W.tiny_package()
+    o = oracle.OracleSim(p)
+    ctx = context(p, precision, o.dt)
+    steps = 70
+    tables = [(a, e, v * 50.0) for a, e, v in p.source_tables(o.dt, steps)]
+    o.set_sources(tables)
+    ctx.set_sources(tables)
+    o.em_steps(steps)
+    ctx.em_steps(steps)
+    ctx.joule(api.COSIM_JOULE_FINALIZE_AVG_POWER, want_total=False)
+    o.joule_finalize_avg_power()
+    assert np.abs(o.P).max() > 0
+    assert rel_l2(ctx.read(api.COSIM_F_P), o.P) < tol
+    assert rel_l2(ctx.read(api.COSIM_F_Q), o.Q) < tol
+    ctx.close()
+
+
 def test_em_steps_deterministic_bitwise():
     p = hetero_problem(37, 11, 9, seed=3, em_bc=(2, 2, 2, 2, 0, 2), cpml=4)
     outs = []
