@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from workloads.waveforms import GaussianPulseTrain, Jitter, Ricker, Scaled, Sine
+from workloads.waveforms import GaussianPulseTrain, Jitter, PRBSBurst, Ricker, Scaled, Sine, prbs7_bits
 
 
 def test_ricker_closed_form():
@@ -16,6 +16,29 @@ def test_ricker_closed_form():
     t = np.linspace(0, 80e-12, 200001)
     assert abs(np.trapezoid(r(t), t)) < 1e-6 * np.trapezoid(np.abs(r(t)), t)  # zero mean
     assert np.abs(r(np.array([15e-12, 65e-12]))).max() < 1e-3 * 2.0  # confined to ~20-60 ps
+
+
+def test_prbs_burst_closed_form():
+    """the NRZ PRBS7 burst: J0 sum_b (2 bit_b - 1) [Phi((t - t_b)/s) - Phi((t - t_{b+1})/s)],
+    t_b = t_start + b t_bit, written out with math.erfc per sample; the
+    plateaus sit at +-J0 between edges"""
+    import math
+    w = PRBSBurst(j0=2.5, seed=4)
+    assert np.array_equal(w.bits, prbs7_bits(4, w.n_bits))
+    t = np.linspace(0.0, 2.4e-9, 401)
+    tb = 1.0 / w.bit_rate
+
+    def phi(x):
+        return 0.5 * math.erfc(-x / math.sqrt(2.0))
+
+    want = np.array([w.j0 * sum((2.0 * float(bit) - 1.0) * (phi((x - (w.t_start + b * tb)) / w.edge_sigma)
+                                                           - phi((x - (w.t_start + (b + 1) * tb)) / w.edge_sigma))
+                                for b, bit in enumerate(w.bits)) for x in t])
+    assert np.abs(w(t) - want).max() < 1e-12 * w.j0
+    # bit centres lie 2.5 edge widths from both edges: each neighbouring
+    # transition pulls the level by 2 Phi(-2.5) = 1.2 % of the swing
+    mid = w.t_start + (np.arange(w.n_bits) + 0.5) * tb
+    assert np.allclose(w(mid), w.j0 * (2.0 * w.bits - 1.0), rtol=0, atol=2.6e-2 * w.j0)
 
 
 def test_sine_and_window():
